@@ -1,0 +1,273 @@
+"""CPU oracle for SCLaP, contraction, projection and the multilevel driver.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with
+the CUDA library; the two only see the same seeded inputs.
+
+The arithmetic lives in ``sclap_oracle.c`` (plain C, one thread); this module
+compiles it with gcc on first use and wraps it with ctypes.  Function names
+and argument order follow the C file, which cites the paper section each
+routine follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sclap_oracle.c")
+_HDR = os.path.join(_HERE, "sclap_oracle.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "libsclap_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, EGRAPH, EOVERFLOW, ENOMEM = 0, 1, 2, 3, 4
+MAX_LEVELS = 64
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with code {code}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc -O2, plain C99)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    stale = force or not os.path.exists(_SO) or any(
+        os.path.getmtime(p) > os.path.getmtime(_SO) for p in (_SRC, _HDR))
+    if stale:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp,
+                               _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class MLParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("eps", C.c_double), ("U", C.c_int64),
+                ("cluster_rounds", C.c_int32), ("refine_rounds", C.c_int32),
+                ("subrounds", C.c_int32), ("n_stop", C.c_int64),
+                ("max_levels", C.c_int32), ("init_seeds", C.c_int32),
+                ("init_rounds", C.c_int32), ("seed", C.c_uint64)]
+
+
+class MLStats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("n", C.c_int64 * MAX_LEVELS),
+                ("nnz", C.c_int64 * MAX_LEVELS),
+                ("cluster_rounds_done", C.c_int32 * MAX_LEVELS),
+                ("refine_rounds_done", C.c_int32 * MAX_LEVELS),
+                ("U", C.c_int64), ("lmax", C.c_int64), ("init_best", C.c_int32),
+                ("init_cut", C.c_int64), ("init_maxbw", C.c_int64),
+                ("cut", C.c_int64), ("maxbw", C.c_int64)]
+
+
+_P64 = C.POINTER(C.c_int64)
+_P32 = C.POINTER(C.c_int32)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.or_mix64.restype = C.c_uint64
+            L.or_mix64.argtypes = [C.c_uint64]
+            L.or_colour.restype = C.c_uint32
+            L.or_colour.argtypes = [C.c_uint64, C.c_int32, C.c_int64, C.c_int32]
+            L.or_tie.restype = C.c_uint32
+            L.or_tie.argtypes = [C.c_uint64, C.c_int32, C.c_int64, C.c_int64]
+            L.or_lmax.restype = C.c_int64
+            L.or_lmax.argtypes = [C.c_int64, C.c_int32, C.c_double]
+            g = [C.c_int64, _P64, _P32, _P32, _P32]
+            L.or_validate.argtypes = g
+            L.or_cluster.argtypes = g + [C.c_int64, C.c_int32, C.c_int32, C.c_uint64, _P32,
+                                         _P32, _P32, _P64]
+            L.or_refine_bound.argtypes = g + [C.c_int32, C.c_int64, C.c_int32, C.c_int32,
+                                              C.c_uint64, _P32, _P32, _P64]
+            L.or_refine.argtypes = g + [C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                                        C.c_uint64, _P32, _P64, _P64, _P32, _P64]
+            L.or_contract.argtypes = g + [_P32, _P64, _P64, C.POINTER(_P64), C.POINTER(_P32),
+                                          C.POINTER(_P32), C.POINTER(_P32), _P32]
+            L.or_free.argtypes = [C.c_void_p]
+            L.or_project.argtypes = [C.c_int64, _P32, _P32, _P32]
+            L.or_cut.restype = C.c_int64
+            L.or_cut.argtypes = [C.c_int64, _P64, _P32, _P32, _P32]
+            L.or_block_weights.argtypes = [C.c_int64, _P32, _P32, C.c_int32, _P64]
+            L.or_initial_partition.argtypes = g + [C.c_int32, C.c_int64, C.c_int32, C.c_int32,
+                                                   C.c_int32, C.c_uint64, _P32, _P64, _P64, _P32]
+            L.or_multilevel.argtypes = g + [C.POINTER(MLParams), _P32, C.POINTER(MLStats)]
+            _lib = L
+    return _lib
+
+
+def _p64(a):
+    return a.ctypes.data_as(_P64)
+
+
+def _p32(a):
+    return a.ctypes.data_as(_P32)
+
+
+def _graph_args(g):
+    xadj = np.ascontiguousarray(g["xadj"], dtype=np.int64)
+    adjncy = np.ascontiguousarray(g["adjncy"], dtype=np.int32)
+    adjwgt = np.ascontiguousarray(g["adjwgt"], dtype=np.int32)
+    vwgt = np.ascontiguousarray(g["vwgt"], dtype=np.int32)
+    n = len(xadj) - 1
+    keep = (xadj, adjncy, adjwgt, vwgt)
+    return keep, [n, _p64(xadj), _p32(adjncy), _p32(adjwgt), _p32(vwgt)]
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise OracleError(rc, what)
+
+
+def mix64(z: int) -> int:
+    return int(lib().or_mix64(z & (2**64 - 1)))
+
+
+def colour(seed: int, rnd: int, v: int, S: int) -> int:
+    return int(lib().or_colour(seed, rnd, v, S))
+
+
+def tie(seed: int, rnd: int, v: int, L: int) -> int:
+    return int(lib().or_tie(seed, rnd, v, L))
+
+
+def lmax(cV: int, k: int, eps: float) -> int:
+    return int(lib().or_lmax(cV, k, eps))
+
+
+def validate(g) -> int:
+    keep, a = _graph_args(g)
+    return int(lib().or_validate(*a))
+
+
+def cluster(g, U, rounds, subrounds, seed, constraint_part=None, return_moves=False):
+    keep, a = _graph_args(g)
+    n = a[0]
+    lab = np.empty(n, np.int32)
+    rd = C.c_int32(0)
+    mv = np.zeros(max(rounds, 1), np.int64)
+    cp = None if constraint_part is None else np.ascontiguousarray(constraint_part, np.int32)
+    rc = lib().or_cluster(*a, U, rounds, subrounds, seed, None if cp is None else _p32(cp),
+                          _p32(lab), C.byref(rd), _p64(mv))
+    _check(rc, "cluster")
+    if return_moves:
+        return lab, rd.value, mv[:rd.value].copy()
+    return lab, rd.value
+
+
+def refine_bound(g, nblocks, B, rounds, subrounds, seed, part, return_moves=False):
+    keep, a = _graph_args(g)
+    p = np.array(part, dtype=np.int32, copy=True)
+    rd = C.c_int32(0)
+    mv = np.zeros(max(rounds, 1), np.int64)
+    rc = lib().or_refine_bound(*a, nblocks, B, rounds, subrounds, seed, _p32(p), C.byref(rd),
+                               _p64(mv))
+    _check(rc, "refine_bound")
+    if return_moves:
+        return p, rd.value, mv[:rd.value].copy()
+    return p, rd.value
+
+
+def refine(g, k, eps, rounds, subrounds, seed, part):
+    """Returns (part, cut, block_weights, rounds_done)."""
+    keep, a = _graph_args(g)
+    p = np.array(part, dtype=np.int32, copy=True)
+    cut = C.c_int64(0)
+    bw = np.zeros(k, np.int64)
+    rd = C.c_int32(0)
+    rc = lib().or_refine(*a, k, eps, rounds, subrounds, seed, _p32(p), C.byref(cut), _p64(bw),
+                         C.byref(rd), None)
+    _check(rc, "refine")
+    return p, cut.value, bw, rd.value
+
+
+def contract(g, labels):
+    """Returns (coarse graph dict, f2c)."""
+    keep, a = _graph_args(g)
+    n = a[0]
+    lab = np.ascontiguousarray(labels, np.int32)
+    f2c = np.empty(n, np.int32)
+    cn, cnnz = C.c_int64(0), C.c_int64(0)
+    px, pa, pw, pv = _P64(), _P32(), _P32(), _P32()
+    rc = lib().or_contract(*a, _p32(lab), C.byref(cn), C.byref(cnnz), C.byref(px), C.byref(pa),
+                           C.byref(pw), C.byref(pv), _p32(f2c))
+    _check(rc, "contract")
+    n2, m2 = cn.value, cnnz.value
+    out = {
+        "xadj": np.ctypeslib.as_array(px, shape=(n2 + 1,)).copy(),
+        "adjncy": np.ctypeslib.as_array(pa, shape=(max(m2, 1),))[:m2].copy(),
+        "adjwgt": np.ctypeslib.as_array(pw, shape=(max(m2, 1),))[:m2].copy(),
+        "vwgt": np.ctypeslib.as_array(pv, shape=(max(n2, 1),))[:n2].copy(),
+    }
+    for p in (px, pa, pw, pv):
+        lib().or_free(C.cast(p, C.c_void_p))
+    return out, f2c
+
+
+def project(f2c, coarse_part):
+    f2c = np.ascontiguousarray(f2c, np.int32)
+    cp = np.ascontiguousarray(coarse_part, np.int32)
+    out = np.empty(len(f2c), np.int32)
+    lib().or_project(len(f2c), _p32(f2c), _p32(cp), _p32(out))
+    return out
+
+
+def cut(g, part) -> int:
+    keep, a = _graph_args(g)
+    p = np.ascontiguousarray(part, np.int32)
+    return int(lib().or_cut(a[0], a[1], a[2], a[3], _p32(p)))
+
+
+def block_weights(g, part, k):
+    vw = np.ascontiguousarray(g["vwgt"], np.int32)
+    p = np.ascontiguousarray(part, np.int32)
+    bw = np.zeros(k, np.int64)
+    lib().or_block_weights(len(vw), _p32(vw), _p32(p), k, _p64(bw))
+    return bw
+
+
+def initial_partition(g, k, B, P, rounds, subrounds, seed):
+    """Returns (part, cuts[P], maxbw[P], best)."""
+    keep, a = _graph_args(g)
+    part = np.empty(a[0], np.int32)
+    cuts = np.zeros(P, np.int64)
+    mx = np.zeros(P, np.int64)
+    best = C.c_int32(0)
+    rc = lib().or_initial_partition(*a, k, B, P, rounds, subrounds, seed, _p32(part),
+                                    _p64(cuts), _p64(mx), C.byref(best))
+    _check(rc, "initial_partition")
+    return part, cuts, mx, best.value
+
+
+def default_params(k, eps=0.03, seed=1, **kw):
+    p = dict(k=k, eps=eps, U=0, cluster_rounds=3, refine_rounds=6, subrounds=4, n_stop=2000,
+             max_levels=32, init_seeds=8, init_rounds=6, seed=seed)
+    p.update(kw)
+    return p
+
+
+def multilevel(g, params: dict):
+    """Returns (part, stats dict)."""
+    keep, a = _graph_args(g)
+    part = np.empty(a[0], np.int32)
+    mp = MLParams(**params)
+    st = MLStats()
+    rc = lib().or_multilevel(*a, C.byref(mp), _p32(part), C.byref(st))
+    _check(rc, "multilevel")
+    L = st.levels
+    stats = dict(levels=L, n=list(st.n[:L]), nnz=list(st.nnz[:L]),
+                 cluster_rounds_done=list(st.cluster_rounds_done[:L]),
+                 refine_rounds_done=list(st.refine_rounds_done[:L]), U=st.U, lmax=st.lmax,
+                 init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
+                 cut=st.cut, maxbw=st.maxbw)
+    return part, stats

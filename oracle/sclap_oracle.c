@@ -1,0 +1,691 @@
+/*
+ * sclap_oracle.c -- plain, slow, single-threaded CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, by the smoke check and by
+ * the CPU-baseline leg of the benchmark; never by the product path.
+ *
+ * The code follows the paper's description step by step, with no blocking,
+ * fusion or reordering beyond what the (deterministic) reading states:
+ *
+ *  - Sec. III.A: a node is moved to the eligible neighbouring block with the
+ *    strongest connection; a block is eligible if it is not overloaded once
+ *    the node has moved (bound U while clustering, L_max while refining);
+ *    a node of an overloaded block ignores its own block.
+ *  - Sec. IV.B: exact block weights when refining.
+ *  - Sec. IV.C: contraction through the prefix-sum map q and C(v) = q(label).
+ *  - Sec. IV.E: l rounds per coarsening level, initial partition of the
+ *    coarsest graph, projection and r rounds per uncoarsening level.
+ *
+ * Deterministic reading (the paper visits nodes sequentially in random or
+ * degree order and breaks ties randomly):
+ *  R1  every round has S synchronous sub-rounds, a fresh random split of the
+ *      nodes per round (the paper visits the nodes in a new random order
+ *      each round): with h = mix64(seed ^ ((round+1) << 32) ^ v), node v
+ *      belongs to sub-round colour(v) = (h >> 32) mod S and proposes against
+ *      the state at the start of its sub-round.
+ *  R2  candidates are the labels of v's neighbours other than its own; label
+ *      L is eligible iff W(L) + c(v) <= B.  The best candidate maximises
+ *      omega(v,L), then minimises tie(v,L) = high 32 bits of mix64(h ^ L),
+ *      then L.
+ *      v proposes iff gain = omega(v,best) - omega(v,own) > 0, or, when
+ *      refining, iff its own block is overloaded (then gain may be <= 0).
+ *  R3  departures from an overloaded block are admitted in (gain desc,
+ *      id asc) order while the weight departed before them is below the
+ *      excess W(own) - B.
+ *  R4  proposals to a target T surviving R3 are admitted in (gain desc,
+ *      id asc) order iff c(v) == 0 or the inclusive prefix of c in that
+ *      order is <= B - W(T) (weights at sub-round start).
+ *  R5  admitted moves are applied together; a round ends early after the
+ *      first round without moves.
+ * mix64 is the SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+ */
+#include "sclap_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* hashing (R1, R2)                                                     */
+/* ------------------------------------------------------------------ */
+
+uint64_t or_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* h(v, round): the per-round hash of node v that fixes its sub-round and
+ * seeds its tie-breaks (R1, R2). */
+static uint64_t node_hash(uint64_t seed, int32_t round, int64_t v)
+{
+    return or_mix64(seed ^ ((uint64_t)(round + 1) << 32) ^ (uint64_t)v);
+}
+
+uint32_t or_colour(uint64_t seed, int32_t round, int64_t v, int32_t S)
+{
+    return (uint32_t)(node_hash(seed, round, v) >> 32) % (uint32_t)S;
+}
+
+uint32_t or_tie(uint64_t seed, int32_t round, int64_t v, int64_t L)
+{
+    return (uint32_t)(or_mix64(node_hash(seed, round, v) ^ (uint64_t)L) >> 32);
+}
+
+/* Sec. II.A: L_max := (1 + eps) * ceil(c(V) / k), rounded down to an integer
+ * because all weights are integers. */
+int64_t or_lmax(int64_t cV, int32_t k, double eps)
+{
+    int64_t avg = (cV + k - 1) / k;
+    return (int64_t)floor((1.0 + eps) * (double)avg);
+}
+
+/* ------------------------------------------------------------------ */
+/* graph validation (Sec. II.A: undirected, omega > 0, c >= 0)          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t u, v;
+    int32_t w;
+} edge_rec;
+
+static int cmp_edge(const void *a, const void *b)
+{
+    const edge_rec *x = (const edge_rec *)a, *y = (const edge_rec *)b;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    return 0;
+}
+
+int or_validate(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                const int32_t *adjwgt, const int32_t *vwgt)
+{
+    if (n < 0) return OR_EINVAL;
+    if (xadj[0] != 0) return OR_EGRAPH;
+    for (int64_t v = 0; v < n; v++)
+        if (xadj[v + 1] < xadj[v]) return OR_EGRAPH;
+    int64_t nnz = xadj[n];
+    for (int64_t v = 0; v < n; v++)
+        if (vwgt[v] < 0) return OR_EGRAPH;
+    edge_rec *e = (edge_rec *)malloc(sizeof(edge_rec) * (size_t)(nnz ? nnz : 1));
+    if (!e) return OR_ENOMEM;
+    int rc = OR_OK;
+    for (int64_t v = 0; v < n && rc == OR_OK; v++)
+        for (int64_t i = xadj[v]; i < xadj[v + 1]; i++) {
+            int64_t u = adjncy[i];
+            if (u < 0 || u >= n || u == v || adjwgt[i] <= 0) { rc = OR_EGRAPH; break; }
+            e[i].u = v; e[i].v = u; e[i].w = adjwgt[i];
+        }
+    if (rc == OR_OK) {
+        qsort(e, (size_t)nnz, sizeof(edge_rec), cmp_edge);
+        for (int64_t i = 1; i < nnz; i++)
+            if (e[i].u == e[i - 1].u && e[i].v == e[i - 1].v) { rc = OR_EGRAPH; break; }
+    }
+    if (rc == OR_OK) {
+        /* symmetry: every (v,u,w) has its mirror (u,v,w) */
+        for (int64_t i = 0; i < nnz; i++) {
+            edge_rec key = {e[i].v, e[i].u, 0};
+            edge_rec *m = (edge_rec *)bsearch(&key, e, (size_t)nnz, sizeof(edge_rec), cmp_edge);
+            if (!m || m->w != e[i].w) { rc = OR_EGRAPH; break; }
+        }
+    }
+    free(e);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* one synchronous round of size-constrained label propagation          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t v;
+    int64_t target, own;
+    int64_t gain;
+    int64_t c;
+    int keep;
+} proposal;
+
+static int cmp_by_source(const void *a, const void *b)
+{
+    const proposal *x = (const proposal *)a, *y = (const proposal *)b;
+    if (x->own != y->own) return x->own < y->own ? -1 : 1;
+    if (x->gain != y->gain) return x->gain > y->gain ? -1 : 1;
+    return x->v < y->v ? -1 : (x->v > y->v);
+}
+
+static int cmp_by_target(const void *a, const void *b)
+{
+    const proposal *x = (const proposal *)a, *y = (const proposal *)b;
+    if (x->target != y->target) return x->target < y->target ? -1 : 1;
+    if (x->gain != y->gain) return x->gain > y->gain ? -1 : 1;
+    return x->v < y->v ? -1 : (x->v > y->v);
+}
+
+typedef struct {
+    int64_t *acc;       /* omega(v, L) for the node being visited, size nW */
+    int64_t *touched;   /* labels with acc != 0                             */
+    proposal *props;
+} lp_ws;
+
+/* One round (R1-R5).  lab: label per node; W: weight per label (nW labels);
+ * B: U (clustering) or L_max (refinement).  Returns the moves applied. */
+static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                        const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
+                        int64_t *W, int64_t B, int refine, const int32_t *cp,
+                        uint64_t seed, int32_t round, int32_t S, lp_ws *ws)
+{
+    int64_t moves = 0;
+    for (int32_t j = 0; j < S; j++) {
+        int64_t np = 0;
+        /* --- every node of colour j proposes against the current state --- */
+        for (int64_t v = 0; v < n; v++) {
+            if ((int32_t)or_colour(seed, round, v, S) != j) continue;
+            if (xadj[v + 1] == xadj[v]) continue;  /* no neighbours: never moves */
+            int64_t nt = 0;
+            for (int64_t i = xadj[v]; i < xadj[v + 1]; i++) {
+                int64_t u = adjncy[i];
+                if (cp && cp[u] != cp[v]) continue;  /* V-cycle restriction */
+                int64_t L = lab[u];
+                if (ws->acc[L] == 0) ws->touched[nt++] = L;
+                ws->acc[L] += adjwgt[i];
+            }
+            int64_t own = lab[v];
+            int64_t w_own = ws->acc[own];
+            int overloaded = refine && W[own] > B;
+            int64_t best = -1;
+            uint32_t best_tie = 0;
+            for (int64_t t = 0; t < nt; t++) {
+                int64_t L = ws->touched[t];
+                if (L == own) continue;
+                if (W[L] + vwgt[v] > B) continue; /* not eligible */
+                uint32_t tl = or_tie(seed, round, v, L);
+                int better;
+                if (best < 0) better = 1;
+                else if (ws->acc[L] != ws->acc[best]) better = ws->acc[L] > ws->acc[best];
+                else if (tl != best_tie) better = tl < best_tie;
+                else better = L < best;
+                if (better) { best = L; best_tie = tl; }
+            }
+            if (best >= 0) {
+                int64_t gain = ws->acc[best] - w_own;
+                if (gain > 0 || overloaded) {
+                    proposal *p = &ws->props[np++];
+                    p->v = v; p->target = best; p->own = own; p->gain = gain;
+                    p->c = vwgt[v]; p->keep = 1;
+                }
+            }
+            for (int64_t t = 0; t < nt; t++) ws->acc[ws->touched[t]] = 0;
+        }
+        /* --- R3: departures from overloaded blocks (refinement only) --- */
+        if (refine && np > 0) {
+            qsort(ws->props, (size_t)np, sizeof(proposal), cmp_by_source);
+            int64_t i = 0;
+            while (i < np) {
+                int64_t b = ws->props[i].own, e = i;
+                while (e < np && ws->props[e].own == b) e++;
+                if (W[b] > B) {
+                    int64_t excess = W[b] - B, departed = 0;
+                    for (int64_t q = i; q < e; q++) {
+                        if (departed < excess) departed += ws->props[q].c;
+                        else ws->props[q].keep = 0;
+                    }
+                }
+                i = e;
+            }
+        }
+        /* --- R4: capacity arbitration per target --- */
+        if (np > 0) qsort(ws->props, (size_t)np, sizeof(proposal), cmp_by_target);
+        int64_t i = 0;
+        while (i < np) {
+            int64_t T = ws->props[i].target, e = i;
+            while (e < np && ws->props[e].target == T) e++;
+            int64_t cap = B - W[T], sum = 0;
+            for (int64_t q = i; q < e; q++) {
+                proposal *p = &ws->props[q];
+                if (!p->keep) continue;
+                sum += p->c;
+                if (!(p->c == 0 || sum <= cap)) p->keep = 0;
+            }
+            i = e;
+        }
+        /* --- R5: apply the admitted moves together --- */
+        for (int64_t q = 0; q < np; q++) {
+            proposal *p = &ws->props[q];
+            if (!p->keep) continue;
+            lab[p->v] = (int32_t)p->target;
+            W[p->target] += p->c;
+            W[p->own] -= p->c;
+            moves++;
+        }
+    }
+    return moves;
+}
+
+static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                  const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
+                  int64_t *W, int64_t nW, int64_t B, int refine, const int32_t *cp,
+                  uint64_t seed, int32_t rounds, int32_t S, int32_t *rounds_done,
+                  int64_t *moves_per_round)
+{
+    lp_ws ws;
+    ws.acc = (int64_t *)calloc((size_t)(nW ? nW : 1), sizeof(int64_t));
+    ws.touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nW ? nW : 1));
+    ws.props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
+    if (!ws.acc || !ws.touched || !ws.props) {
+        free(ws.acc); free(ws.touched); free(ws.props);
+        return OR_ENOMEM;
+    }
+    int32_t done = 0;
+    for (int32_t r = 0; r < rounds; r++) {
+        int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, refine, cp,
+                             seed, r, S, &ws);
+        if (moves_per_round) moves_per_round[r] = m;
+        done = r + 1;
+        if (m == 0) break;
+    }
+    if (rounds_done) *rounds_done = done;
+    free(ws.acc); free(ws.touched); free(ws.props);
+    return OR_OK;
+}
+
+static int64_t total_weight(int64_t n, const int32_t *vwgt, int32_t *maxc)
+{
+    int64_t s = 0;
+    int32_t m = 0;
+    for (int64_t v = 0; v < n; v++) {
+        s += vwgt[v];
+        if (vwgt[v] > m) m = vwgt[v];
+    }
+    if (maxc) *maxc = m;
+    return s;
+}
+
+/* Sec. III.A, clustering form: every node starts in its own cluster (label
+ * = node id); cluster weights stay <= U. */
+int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+               const int32_t *adjwgt, const int32_t *vwgt, int64_t U,
+               int32_t rounds, int32_t S, uint64_t seed,
+               const int32_t *constraint_part, int32_t *labels_out,
+               int32_t *rounds_done, int64_t *moves_per_round)
+{
+    int32_t maxc;
+    if (rounds < 0 || S < 1) return OR_EINVAL;
+    total_weight(n, vwgt, &maxc);
+    if (U < maxc) return OR_EINVAL;
+    int64_t *W = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    if (!W) return OR_ENOMEM;
+    for (int64_t v = 0; v < n; v++) { labels_out[v] = (int32_t)v; W[v] = vwgt[v]; }
+    int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, labels_out, W, n, U, 0,
+                    constraint_part, seed, rounds, S, rounds_done, moves_per_round);
+    free(W);
+    return rc;
+}
+
+/* Sec. III.A, local-search form with an explicit bound B on every block. */
+int or_refine_bound(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                    const int32_t *adjwgt, const int32_t *vwgt, int32_t nblocks,
+                    int64_t B, int32_t rounds, int32_t S, uint64_t seed,
+                    int32_t *part, int32_t *rounds_done, int64_t *moves_per_round)
+{
+    if (nblocks < 1 || rounds < 0 || S < 1) return OR_EINVAL;
+    for (int64_t v = 0; v < n; v++)
+        if (part[v] < 0 || part[v] >= nblocks) return OR_EINVAL;
+    int64_t *W = (int64_t *)calloc((size_t)nblocks, sizeof(int64_t));
+    if (!W) return OR_ENOMEM;
+    for (int64_t v = 0; v < n; v++) W[part[v]] += vwgt[v];
+    int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, part, W, nblocks, B, 1, NULL,
+                    seed, rounds, S, rounds_done, moves_per_round);
+    free(W);
+    return rc;
+}
+
+int or_refine(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+              const int32_t *adjwgt, const int32_t *vwgt, int32_t k, double eps,
+              int32_t rounds, int32_t S, uint64_t seed, int32_t *part,
+              int64_t *cut_out, int64_t *block_w_out, int32_t *rounds_done,
+              int64_t *moves_per_round)
+{
+    if (k < 1 || eps < 0) return OR_EINVAL;
+    int64_t B = or_lmax(total_weight(n, vwgt, NULL), k, eps);
+    int rc = or_refine_bound(n, xadj, adjncy, adjwgt, vwgt, k, B, rounds, S, seed,
+                             part, rounds_done, moves_per_round);
+    if (rc) return rc;
+    if (cut_out) *cut_out = or_cut(n, xadj, adjncy, adjwgt, part);
+    if (block_w_out) or_block_weights(n, vwgt, part, k, block_w_out);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* contraction (Sec. III, Sec. IV.C) and projection                     */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t cu, cv;
+    int64_t w;
+} triple;
+
+static int cmp_triple(const void *a, const void *b)
+{
+    const triple *x = (const triple *)a, *y = (const triple *)b;
+    if (x->cu != y->cu) return x->cu < y->cu ? -1 : 1;
+    if (x->cv != y->cv) return x->cv < y->cv ? -1 : 1;
+    return 0;
+}
+
+/* Each cluster becomes one node whose weight is the cluster's weight; two
+ * coarse nodes are adjacent iff their clusters are, with the summed weight
+ * of the edges between them.  Coarse ids: q maps the distinct cluster ids in
+ * ascending order onto 0..n'-1 (the prefix-sum construction of Sec. IV.C),
+ * C(v) = q(label(v)).  Output rows ascending, neighbours ascending. */
+int or_contract(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                const int32_t *adjwgt, const int32_t *vwgt, const int32_t *labels,
+                int64_t *cn_out, int64_t *cnnz_out, int64_t **cxadj_out,
+                int32_t **cadjncy_out, int32_t **cadjwgt_out, int32_t **cvwgt_out,
+                int32_t *f2c)
+{
+    for (int64_t v = 0; v < n; v++)
+        if (labels[v] < 0 || labels[v] >= n) return OR_EINVAL;
+    int64_t *q = (int64_t *)calloc(n > 0 ? (size_t)n : 1u, sizeof(int64_t));
+    if (!q) return OR_ENOMEM;
+    for (int64_t v = 0; v < n; v++) q[labels[v]] = 1;      /* mark used ids */
+    int64_t cn = 0;
+    for (int64_t L = 0; L < n; L++) {                        /* prefix sum    */
+        int64_t used = q[L];
+        q[L] = used ? cn : -1;
+        cn += used;
+    }
+    for (int64_t v = 0; v < n; v++) f2c[v] = (int32_t)q[labels[v]];
+    free(q);
+
+    int32_t *cvwgt = (int32_t *)calloc((size_t)(cn ? cn : 1), sizeof(int32_t));
+    int64_t *cxadj = (int64_t *)calloc((size_t)cn + 1, sizeof(int64_t));
+    int64_t nnz = xadj[n];
+    triple *t = (triple *)malloc(sizeof(triple) * (size_t)(nnz ? nnz : 1));
+    if (!cvwgt || !cxadj || !t) { free(cvwgt); free(cxadj); free(t); return OR_ENOMEM; }
+    for (int64_t v = 0; v < n; v++) cvwgt[f2c[v]] += vwgt[v];
+    int64_t nt = 0;
+    for (int64_t v = 0; v < n; v++)
+        for (int64_t i = xadj[v]; i < xadj[v + 1]; i++) {
+            int64_t cu = f2c[v], cv = f2c[adjncy[i]];
+            if (cu == cv) continue;                 /* edge inside a cluster */
+            t[nt].cu = cu; t[nt].cv = cv; t[nt].w = adjwgt[i];
+            nt++;
+        }
+    if (nt > 0) qsort(t, (size_t)nt, sizeof(triple), cmp_triple);
+    int64_t m = 0;                                   /* reduce equal pairs */
+    for (int64_t i = 0; i < nt; i++) {
+        if (m > 0 && t[m - 1].cu == t[i].cu && t[m - 1].cv == t[i].cv) t[m - 1].w += t[i].w;
+        else t[m++] = t[i];
+    }
+    int32_t *cadj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m ? m : 1));
+    int32_t *cw = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m ? m : 1));
+    if (!cadj || !cw) { free(cadj); free(cw); free(cvwgt); free(cxadj); free(t); return OR_ENOMEM; }
+    for (int64_t i = 0; i < m; i++) {
+        cxadj[t[i].cu + 1]++;
+        cadj[i] = (int32_t)t[i].cv;
+        cw[i] = (int32_t)t[i].w;
+    }
+    for (int64_t c = 0; c < cn; c++) cxadj[c + 1] += cxadj[c];
+    free(t);
+    *cn_out = cn; *cnnz_out = m;
+    *cxadj_out = cxadj; *cadjncy_out = cadj; *cadjwgt_out = cw; *cvwgt_out = cvwgt;
+    return OR_OK;
+}
+
+void or_free(void *p) { free(p); }
+
+/* Uncoarsening: a fine node takes the block of its coarse representative. */
+void or_project(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_part,
+                int32_t *fine_part)
+{
+    for (int64_t v = 0; v < n_fine; v++) fine_part[v] = coarse_part[f2c[v]];
+}
+
+/* Sec. II.A: cut = total weight of edges whose endpoints lie in different
+ * blocks (each undirected edge is stored twice, hence the halving). */
+int64_t or_cut(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+               const int32_t *adjwgt, const int32_t *part)
+{
+    int64_t s = 0;
+    for (int64_t v = 0; v < n; v++)
+        for (int64_t i = xadj[v]; i < xadj[v + 1]; i++)
+            if (part[adjncy[i]] != part[v]) s += adjwgt[i];
+    return s / 2;
+}
+
+void or_block_weights(int64_t n, const int32_t *vwgt, const int32_t *part,
+                      int32_t k, int64_t *bw)
+{
+    for (int32_t b = 0; b < k; b++) bw[b] = 0;
+    for (int64_t v = 0; v < n; v++) bw[part[v]] += vwgt[v];
+}
+
+/* ------------------------------------------------------------------ */
+/* initial partition of the coarsest graph (stands in for KaFFPaE)      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t v;
+    int32_t c;
+    uint32_t h;
+} lpt_item;
+
+static int cmp_lpt(const void *a, const void *b)
+{
+    const lpt_item *x = (const lpt_item *)a, *y = (const lpt_item *)b;
+    if (x->c != y->c) return x->c > y->c ? -1 : 1;   /* heavier first */
+    if (x->h != y->h) return x->h < y->h ? -1 : 1;   /* seeded shuffle */
+    return x->v < y->v ? -1 : (x->v > y->v);
+}
+
+/* Reading (the paper runs an evolutionary algorithm here): P individuals.
+ * Individual t: nodes in (c desc, h_t(v) asc, v asc) order, each placed in
+ * the currently lightest block (lowest id on ties); h_t(v) = high 32 bits of
+ * mix64(s_t ^ v), s_t = mix64(seed ^ (0xD1B54A32D192ED03 * (t+1))).  All P
+ * individuals are then refined together, as one SCLaP refinement over the
+ * disjoint union of P copies of the graph (copy t: nodes t*n + v, blocks
+ * t*k .. t*k+k-1, bound B, seed `seed`).  The best individual has the
+ * lowest cut among those with max block weight <= B (lowest t on ties);
+ * with none feasible, the smallest max block weight, then cut, then t. */
+int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                         const int32_t *adjwgt, const int32_t *vwgt, int32_t k,
+                         int64_t B, int32_t P, int32_t rounds, int32_t S,
+                         uint64_t seed, int32_t *part_out, int64_t *cuts_out,
+                         int64_t *maxbw_out, int32_t *best_out)
+{
+    if (k < 1 || P < 1) return OR_EINVAL;
+    int64_t nnz = xadj[n];
+    int64_t un = n * P, unnz = nnz * P;
+    int64_t *ux = (int64_t *)malloc(sizeof(int64_t) * (size_t)(un + 1));
+    int32_t *ua = (int32_t *)malloc(sizeof(int32_t) * (size_t)(unnz ? unnz : 1));
+    int32_t *uw = (int32_t *)malloc(sizeof(int32_t) * (size_t)(unnz ? unnz : 1));
+    int32_t *uc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
+    int32_t *up = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
+    lpt_item *it = (lpt_item *)malloc(sizeof(lpt_item) * (size_t)(n ? n : 1));
+    int64_t *bw = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int rc = OR_OK;
+    if (!ux || !ua || !uw || !uc || !up || !it || !bw) { rc = OR_ENOMEM; goto out; }
+
+    for (int32_t t = 0; t < P; t++) {           /* the disjoint union */
+        for (int64_t v = 0; v < n; v++) {
+            ux[t * n + v] = t * nnz + xadj[v];
+            uc[t * n + v] = vwgt[v];
+        }
+        for (int64_t i = 0; i < nnz; i++) {
+            ua[t * nnz + i] = (int32_t)(adjncy[i] + t * n);
+            uw[t * nnz + i] = adjwgt[i];
+        }
+    }
+    ux[un] = unnz;
+
+    for (int32_t t = 0; t < P; t++) {           /* LPT start per individual */
+        uint64_t st = or_mix64(seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(t + 1)));
+        for (int64_t v = 0; v < n; v++) {
+            it[v].v = v; it[v].c = vwgt[v];
+            it[v].h = (uint32_t)(or_mix64(st ^ (uint64_t)v) >> 32);
+        }
+        if (n > 0) qsort(it, (size_t)n, sizeof(lpt_item), cmp_lpt);
+        for (int32_t b = 0; b < k; b++) bw[b] = 0;
+        for (int64_t i = 0; i < n; i++) {
+            int32_t bb = 0;
+            for (int32_t b = 1; b < k; b++)
+                if (bw[b] < bw[bb]) bb = b;
+            up[t * n + it[i].v] = t * k + bb;
+            bw[bb] += it[i].c;
+        }
+    }
+
+    rc = or_refine_bound(un, ux, ua, uw, uc, k * P, B, rounds, S, seed, up, NULL, NULL);
+    if (rc) goto out;
+
+    int32_t best = -1;
+    int64_t best_cut = 0, best_max = 0;
+    for (int32_t t = 0; t < P; t++) {
+        int64_t cut = 0;
+        for (int64_t v = 0; v < n; v++)
+            for (int64_t i = xadj[v]; i < xadj[v + 1]; i++)
+                if (up[t * n + adjncy[i]] != up[t * n + v]) cut += adjwgt[i];
+        cut /= 2;
+        for (int32_t b = 0; b < k; b++) bw[b] = 0;
+        for (int64_t v = 0; v < n; v++) bw[up[t * n + v] - t * k] += vwgt[v];
+        int64_t mx = 0;
+        for (int32_t b = 0; b < k; b++) if (bw[b] > mx) mx = bw[b];
+        if (cuts_out) cuts_out[t] = cut;
+        if (maxbw_out) maxbw_out[t] = mx;
+        int better;
+        if (best < 0) better = 1;
+        else {
+            int f_new = mx <= B, f_old = best_max <= B;
+            if (f_new != f_old) better = f_new;
+            else if (f_new) better = cut < best_cut;
+            else better = mx < best_max || (mx == best_max && cut < best_cut);
+        }
+        if (better) { best = t; best_cut = cut; best_max = mx; }
+    }
+    for (int64_t v = 0; v < n; v++) part_out[v] = up[(int64_t)best * n + v] - best * k;
+    if (best_out) *best_out = best;
+out:
+    free(ux); free(ua); free(uw); free(uc); free(up); free(it); free(bw);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* multilevel driver (Sec. IV.E)                                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t n;
+    int64_t *xadj;
+    int32_t *adjncy, *adjwgt, *vwgt;
+    int32_t *f2c;   /* map to the next coarser level (NULL on the coarsest) */
+    int own;        /* arrays malloc'ed here (all levels but the input) */
+} level;
+
+static uint64_t level_seed(uint64_t seed, int32_t l)
+{
+    return or_mix64(seed ^ (0x9E3779B97F4A7C15ULL * (uint64_t)(l + 1)));
+}
+
+int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                  const int32_t *adjwgt, const int32_t *vwgt,
+                  const or_ml_params *p, int32_t *part_out, or_ml_stats *st)
+{
+    if (p->k < 1 || p->eps < 0 || p->cluster_rounds < 0 || p->refine_rounds < 0 ||
+        p->subrounds < 1 || p->init_seeds < 1 || p->init_rounds < 0)
+        return OR_EINVAL;
+    int32_t maxc;
+    int64_t cV = total_weight(n, vwgt, &maxc);
+    int64_t lmax = or_lmax(cV, p->k, p->eps);
+    int64_t U = p->U > 0 ? p->U : (maxc > cV / (10 * (int64_t)p->k) ? maxc : cV / (10 * (int64_t)p->k));
+    if (U < maxc) return OR_EINVAL;
+    int32_t maxl = p->max_levels > 0 ? p->max_levels : 32;
+    if (maxl > OR_MAX_LEVELS) maxl = OR_MAX_LEVELS;
+
+    level lv[OR_MAX_LEVELS];
+    memset(lv, 0, sizeof(lv));
+    lv[0].n = n; lv[0].xadj = (int64_t *)xadj; lv[0].adjncy = (int32_t *)adjncy;
+    lv[0].adjwgt = (int32_t *)adjwgt; lv[0].vwgt = (int32_t *)vwgt;
+    int32_t L = 0, rc = OR_OK;
+    memset(st, 0, sizeof(*st));
+
+    /* coarsening: l rounds of clustering, then contraction, recursively */
+    while (lv[L].n >= p->n_stop && L + 1 < maxl) {
+        level *g = &lv[L];
+        int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n ? g->n : 1));
+        g->f2c = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n ? g->n : 1));
+        if (!lab || !g->f2c) { free(lab); rc = OR_ENOMEM; goto out; }
+        int32_t rd = 0;
+        rc = or_cluster(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, U, p->cluster_rounds,
+                        p->subrounds, level_seed(p->seed, L), NULL, lab, &rd, NULL);
+        if (rc) { free(lab); goto out; }
+        st->cluster_rounds_done[L] = rd;
+        level *c = &lv[L + 1];
+        int64_t cnnz;
+        rc = or_contract(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, lab, &c->n, &cnnz,
+                         &c->xadj, &c->adjncy, &c->adjwgt, &c->vwgt, g->f2c);
+        free(lab);
+        if (rc) goto out;
+        c->own = 1;
+        if (c->n == g->n) {                       /* no shrink: drop the level */
+            free(c->xadj); free(c->adjncy); free(c->adjwgt); free(c->vwgt);
+            memset(c, 0, sizeof(*c));
+            free(g->f2c); g->f2c = NULL;
+            break;
+        }
+        L++;
+        if (20 * c->n > 19 * g->n) break;          /* stalled (< 5% shrink) */
+    }
+
+    /* initial partition of the coarsest graph */
+    {
+        level *g = &lv[L];
+        int32_t *cp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n ? g->n : 1));
+        int64_t *cuts = (int64_t *)malloc(sizeof(int64_t) * (size_t)p->init_seeds);
+        int64_t *mx = (int64_t *)malloc(sizeof(int64_t) * (size_t)p->init_seeds);
+        if (!cp || !cuts || !mx) { free(cp); free(cuts); free(mx); rc = OR_ENOMEM; goto out; }
+        int32_t best = 0;
+        rc = or_initial_partition(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, p->k, lmax,
+                                  p->init_seeds, p->init_rounds, p->subrounds,
+                                  level_seed(p->seed, L), cp, cuts, mx, &best);
+        if (rc) { free(cp); free(cuts); free(mx); goto out; }
+        st->init_best = best; st->init_cut = cuts[best]; st->init_maxbw = mx[best];
+        free(cuts); free(mx);
+        /* uncoarsening: project, then r rounds of refinement per level */
+        int32_t *cur = cp;
+        for (int32_t l = L - 1; l >= 0; l--) {
+            level *f = &lv[l];
+            int32_t *fp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(f->n ? f->n : 1));
+            if (!fp) { free(cur); rc = OR_ENOMEM; goto out; }
+            or_project(f->n, f->f2c, cur, fp);
+            free(cur);
+            cur = fp;
+            int32_t rd = 0;
+            rc = or_refine_bound(f->n, f->xadj, f->adjncy, f->adjwgt, f->vwgt, p->k, lmax,
+                                 p->refine_rounds, p->subrounds, level_seed(p->seed, l), cur,
+                                 &rd, NULL);
+            if (rc) { free(cur); goto out; }
+            st->refine_rounds_done[l] = rd;
+        }
+        memcpy(part_out, cur, sizeof(int32_t) * (size_t)n);
+        free(cur);
+    }
+    st->levels = L + 1;
+    for (int32_t l = 0; l <= L; l++) { st->n[l] = lv[l].n; st->nnz[l] = lv[l].xadj[lv[l].n]; }
+    st->U = U; st->lmax = lmax;
+    st->cut = or_cut(n, xadj, adjncy, adjwgt, part_out);
+    {
+        int64_t *bw = (int64_t *)calloc((size_t)p->k, sizeof(int64_t));
+        if (!bw) { rc = OR_ENOMEM; goto out; }
+        or_block_weights(n, vwgt, part_out, p->k, bw);
+        st->maxbw = 0;
+        for (int32_t b = 0; b < p->k; b++) if (bw[b] > st->maxbw) st->maxbw = bw[b];
+        free(bw);
+    }
+out:
+    for (int32_t l = 0; l < OR_MAX_LEVELS; l++) {
+        free(lv[l].f2c);
+        if (lv[l].own) { free(lv[l].xadj); free(lv[l].adjncy); free(lv[l].adjwgt); free(lv[l].vwgt); }
+    }
+    return rc;
+}

@@ -1,0 +1,231 @@
+"""Seeded synthetic graph generators (inputs only; none of the method's arithmetic).
+
+Both the CUDA path and the CPU oracle consume the arrays these functions return:
+a graph is generated once, on one device, and the same bytes are handed to both.
+All randomness is counter based -- a SplitMix64 output function applied to
+(seed, stream, index) -- and written with plain torch integer ops, so one
+function serves CPU and GPU without a stateful generator.
+
+A graph is a dict of torch tensors in CSR form (both directions of every
+undirected edge stored, no self-loops, no duplicate entries):
+  xadj   int64 [n+1]   row offsets
+  adjncy int32 [nnz]   neighbour ids
+  adjwgt int32 [nnz]   edge weights  (> 0)
+  vwgt   int32 [n]     node weights  (>= 0)
+The workloads stand in for the paper's social and web graphs (Table I), which
+are not available here: Chung-Lu power-law graphs and R-MAT graphs.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+_M64 = (1 << 64) - 1
+
+
+def _s64(x: int) -> int:
+    """uint64 constant -> the int64 with the same bits."""
+    x &= _M64
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+_C1 = _s64(0xBF58476D1CE4E5B9)
+_C2 = _s64(0x94D049BB133111EB)
+_GOLD = _s64(0x9E3779B97F4A7C15)
+
+
+def _lsr(z: torch.Tensor, s: int) -> torch.Tensor:
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def hash64(z: torch.Tensor) -> torch.Tensor:
+    """SplitMix64 output function on int64 tensors holding uint64 bits."""
+    z = (z ^ _lsr(z, 30)) * _C1
+    z = (z ^ _lsr(z, 27)) * _C2
+    return z ^ _lsr(z, 31)
+
+
+def _stream_key(seed: int, stream: int) -> int:
+    z = (seed * 0x9E3779B97F4A7C15 + stream * 0xD1B54A32D192ED03 + 0x632BE59BD9B4E019) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return _s64(z ^ (z >> 31))
+
+
+def rand_bits(seed: int, stream: int, idx: torch.Tensor) -> torch.Tensor:
+    """64 random bits per index (int64 tensor)."""
+    return hash64((idx * _GOLD) ^ _stream_key(seed, stream))
+
+
+def rand_uniform(seed: int, stream: int, idx: torch.Tensor) -> torch.Tensor:
+    """Uniform doubles in [0, 1) with 53 random bits each."""
+    return _lsr(rand_bits(seed, stream, idx), 11).to(torch.float64) * (2.0 ** -53)
+
+
+def rand_below(seed: int, stream: int, idx: torch.Tensor, bound: int) -> torch.Tensor:
+    """Integers in [0, bound) (63-bit draw reduced mod bound)."""
+    return _lsr(rand_bits(seed, stream, idx), 1) % bound
+
+
+def permutation(n: int, seed: int, stream: int, device) -> torch.Tensor:
+    """A seeded permutation of 0..n-1 (sort by hash, ties impossible to matter)."""
+    idx = torch.arange(n, dtype=torch.int64, device=device)
+    key = _lsr(rand_bits(seed, stream, idx), 1)
+    return torch.argsort(key, stable=True)
+
+
+def csr_from_edges(n: int, u: torch.Tensor, v: torch.Tensor, w: torch.Tensor | None = None,
+                   vwgt: torch.Tensor | None = None) -> dict:
+    """Undirected edge list -> symmetric CSR.  Self-loops are dropped and duplicate
+    pairs are merged (their weights summed)."""
+    device = u.device
+    u = u.to(torch.int64)
+    v = v.to(torch.int64)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    if w is None:
+        w = torch.ones_like(u)
+    else:
+        w = w.to(torch.int64)[keep]
+    a = torch.minimum(u, v)
+    b = torch.maximum(u, v)
+    key = a * n + b
+    ukey, inv = torch.unique(key, return_inverse=True)
+    uw = torch.zeros(ukey.numel(), dtype=torch.int64, device=device)
+    uw.index_add_(0, inv, w)
+    a = ukey // n
+    b = ukey % n
+    src = torch.cat([a, b])
+    dst = torch.cat([b, a])
+    ww = torch.cat([uw, uw])
+    order = torch.argsort(src * n + dst)
+    src, dst, ww = src[order], dst[order], ww[order]
+    deg = torch.bincount(src, minlength=n)
+    xadj = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    xadj[1:] = torch.cumsum(deg, 0)
+    if vwgt is None:
+        vwgt = torch.ones(n, dtype=torch.int32, device=device)
+    if ww.numel() and int(ww.max()) > 2**31 - 1:
+        raise ValueError("edge weight does not fit int32")
+    return {"xadj": xadj, "adjncy": dst.to(torch.int32).contiguous(),
+            "adjwgt": ww.to(torch.int32).contiguous(), "vwgt": vwgt.to(torch.int32).contiguous()}
+
+
+def _chung_lu_pairs(n, gamma, mean_deg, seed, stream0, m_target, device, w=None):
+    """Sample endpoint pairs with P(endpoint = i) proportional to the expected
+    degree w_i ~ (i + i0)^(-1/(gamma-1)); i0 is chosen so that the largest expected
+    degree is about sqrt(n * mean_deg)."""
+    beta = 1.0 / (gamma - 1.0)
+    dmax = math.sqrt(n * mean_deg)
+    idx = torch.arange(n, dtype=torch.float64, device=device)
+    # choose i0 with (i0)^-beta / mean((i+i0)^-beta) ~= dmax / mean_deg
+    lo, hi = 0.0, float(n)
+    for _ in range(60):
+        i0 = 0.5 * (lo + hi)
+        ww = (idx + i0) ** (-beta)
+        ratio = float(ww[0] / ww.mean())
+        if ratio > dmax / mean_deg:
+            lo = i0
+        else:
+            hi = i0
+    ww = (idx + max(i0, 1e-9)) ** (-beta) if w is None else w
+    iw = torch.clamp((ww / ww.max() * (1 << 40)).to(torch.int64), min=1)
+    cum = torch.cumsum(iw, 0)
+    total = int(cum[-1])
+    got = None
+    drawn = 0
+    stream = stream0
+    while True:
+        need = m_target - (0 if got is None else got.numel())
+        if need <= 0:
+            break
+        batch = need
+        s = torch.arange(drawn, drawn + batch, dtype=torch.int64, device=device)
+        ra = rand_below(seed, stream, s, total)
+        rb = rand_below(seed, stream + 1, s, total)
+        a = torch.searchsorted(cum, ra, right=True)
+        b = torch.searchsorted(cum, rb, right=True)
+        drawn += batch
+        keep = a != b
+        a, b = a[keep], b[keep]
+        key = torch.minimum(a, b) * n + torch.maximum(a, b)
+        got = torch.unique(key if got is None else torch.cat([got, key]))
+    return got
+
+
+def chung_lu(n: int = 16384, gamma: float = 2.1, mean_deg: float = 16.0, seed: int = 1,
+             device="cpu") -> dict:
+    """Chung-Lu power-law graph with about n*mean_deg/2 distinct undirected edges,
+    node ids permuted by a seeded permutation, unit weights."""
+    m_target = int(n * mean_deg / 2)
+    key = _chung_lu_pairs(n, gamma, mean_deg, seed, 10, m_target, device)
+    a, b = key // n, key % n
+    perm = permutation(n, seed, 20, device)
+    return csr_from_edges(n, perm[a], perm[b])
+
+
+def rmat(scale: int = 22, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
+         c: float = 0.19, seed: int = 1, device="cpu", chunk: int = 1 << 24) -> dict:
+    """R-MAT graph (Graph500 style): 2^scale nodes, edge_factor * 2^scale samples,
+    quadrant probabilities a, b, c, d = 1-a-b-c, random vertex relabelling,
+    symmetrised, duplicates merged into unit-weight edges, self-loops dropped."""
+    n = 1 << scale
+    m = edge_factor * n
+    perm = permutation(n, seed, 1, device)
+    keys = []
+    for start in range(0, m, chunk):
+        cnt = min(chunk, m - start)
+        s = torch.arange(start, start + cnt, dtype=torch.int64, device=device)
+        src = torch.zeros(cnt, dtype=torch.int64, device=device)
+        dst = torch.zeros(cnt, dtype=torch.int64, device=device)
+        for lvl in range(scale):
+            u = rand_uniform(seed, 100 + lvl, s)
+            bit_dst = ((u >= a) & (u < a + b)) | (u >= a + b + c)
+            bit_src = u >= a + b
+            src |= bit_src.to(torch.int64) << lvl
+            dst |= bit_dst.to(torch.int64) << lvl
+        src, dst = perm[src], perm[dst]
+        keep = src != dst
+        src, dst = src[keep], dst[keep]
+        keys.append(torch.unique(torch.minimum(src, dst) * n + torch.maximum(src, dst)))
+        del s, src, dst
+    key = torch.unique(torch.cat(keys))
+    del keys
+    u, v = key // n, key % n
+    del key
+    g = csr_from_edges(n, u, v)
+    return g
+
+
+def path_graph(n: int, weights=None) -> dict:
+    u = torch.arange(n - 1)
+    v = u + 1
+    w = None if weights is None else torch.tensor(weights, dtype=torch.int64)
+    return csr_from_edges(n, u, v, w)
+
+
+def random_graph(n: int, m: int, seed: int, max_w: int = 1, max_c: int = 1, device="cpu",
+                 min_c: int = 1) -> dict:
+    """Small Erdos-Renyi-like multigraph collapsed to a simple graph; weights uniform
+    in 1..max_w (edges) and min_c..max_c (nodes)."""
+    s = torch.arange(m, dtype=torch.int64, device=device)
+    u = rand_below(seed, 1, s, n)
+    v = rand_below(seed, 2, s, n)
+    w = rand_below(seed, 3, s, max_w) + 1
+    c = rand_below(seed, 4, torch.arange(n, dtype=torch.int64, device=device),
+                   max_c - min_c + 1) + min_c
+    return csr_from_edges(n, u, v, w, c.to(torch.int32))
+
+
+def to_numpy(g: dict) -> dict:
+    return {k: v.detach().cpu().numpy() for k, v in g.items()}
+
+
+def to_device(g: dict, device) -> dict:
+    return {k: v.to(device).contiguous() for k, v in g.items()}
+
+
+def num_edges(g: dict) -> int:
+    """Undirected edges m (= nnz / 2)."""
+    return int(g["adjncy"].numel()) // 2
