@@ -1,0 +1,233 @@
+/*
+ * sclap.h -- C ABI of libsclap: size-constrained label propagation (SCLaP),
+ * cluster contraction, projection and the multilevel driver on one NVIDIA
+ * GB300 GPU (sm_103a).
+ *
+ * Method: Meyerhenke, Sanders, Schulz, "Parallel Graph Partitioning for
+ * Complex Networks" (2014).  Problem statement (Sec. II.A): an undirected
+ * graph G = (V, E, c, omega) with node weights c >= 0 and edge weights
+ * omega > 0; k blocks with c(V_i) <= L_max := (1+eps) * ceil(c(V)/k); the
+ * objective is the total weight of cut edges.  A size-constrained clustering
+ * bounds every cluster by U (Sec. II.A, Sec. III.A).
+ *
+ * Deterministic reading used by every entry point (the paper visits nodes
+ * sequentially in random order and breaks ties randomly):
+ *  - mix64 is the SplitMix64 output function; h(v, r) = mix64(seed ^
+ *    ((r + 1) << 32) ^ v) for round r.
+ *  - Every round has S synchronous sub-rounds; node v acts in sub-round
+ *    (h(v, r) >> 32) mod S and proposes against the state at the start of
+ *    that sub-round.
+ *  - v's candidates are its neighbours' labels other than its own; label L
+ *    is eligible iff W(L) + c(v) <= B (B = U when clustering, L_max when
+ *    refining).  The best candidate maximises omega(v, L), then minimises
+ *    tie = high 32 bits of mix64(h(v, r) ^ L), then L.  v proposes iff
+ *    omega(v, best) - omega(v, own) > 0, or when refining iff its own block
+ *    is overloaded (Sec. III.A, last paragraph).
+ *  - Departures from an overloaded block are admitted in (gain desc, id asc)
+ *    order while the weight already departed is below the excess.  Then each
+ *    target T admits its proposals in (gain desc, id asc) order iff c(v) == 0
+ *    or the inclusive prefix of c is <= B - W(T).  Admitted moves are applied
+ *    together.  A run stops after `rounds` rounds or after a round without
+ *    moves.
+ *
+ * Graph layout (CSR, both directions of every edge stored):
+ *   xadj   int64 [n+1]  row offsets, xadj[0] = 0, non-decreasing
+ *   adjncy int32 [nnz]  neighbour ids; every row strictly ascending, no
+ *                       self-loops
+ *   adjwgt int32 [nnz]  omega > 0, symmetric
+ *   vwgt   int32 [n]    c >= 0
+ * Arrays are device pointers unless an entry point says otherwise; inputs are
+ * read-only and caller-owned.  Output arrays are caller-allocated device
+ * memory of the stated size; scalar outputs are host pointers (NULL allowed)
+ * and are valid when the call returns.  All work is enqueued on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) and every entry point
+ * synchronises that stream before it returns.
+ *
+ * Errors: every entry point returns SCLAP_OK or one of the codes below; on
+ * error no output is valid and `part_inout` arguments are restored.
+ */
+#ifndef SCLAP_H
+#define SCLAP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum sclap_status {
+    SCLAP_OK = 0,
+    SCLAP_EINVAL = 1,     /* bad scalar argument (k < 1, eps < 0, U < max c, ...)   */
+    SCLAP_EGRAPH = 2,     /* graph fails validation                                  */
+    SCLAP_EOVERFLOW = 3,  /* c(V) or the sum of omega exceeds INT32_MAX              */
+    SCLAP_ENOMEM = 4,     /* device allocation failed                                */
+    SCLAP_ECUDA = 5,      /* CUDA runtime error                                      */
+    SCLAP_ETIMEOUT = 6,   /* a bounded device wait gave up                           */
+    SCLAP_ENOTIMPL = 7
+};
+
+typedef struct {
+    int64_t n, nnz;               /* nodes; nnz = 2m directed entries            */
+    const int64_t *xadj;          /* [n+1]                                       */
+    const int32_t *adjncy;        /* [nnz]                                       */
+    const int32_t *adjwgt;        /* [nnz]                                       */
+    const int32_t *vwgt;          /* [n]                                         */
+} sclap_graph;
+
+/* A graph whose arrays the library allocated (device memory); release it with
+ * sclap_graph_free. */
+typedef struct {
+    int64_t n, nnz;
+    int64_t *xadj;
+    int32_t *adjncy, *adjwgt, *vwgt;
+} sclap_graph_owned;
+
+/* Multilevel parameters (Sec. IV.E).  sclap_ml_defaults fills the paper's
+ * `fast` round counts (l = 3, r = 6, Sec. V.A) with S = 4, n_stop = 2000. */
+typedef struct {
+    int32_t k;              /* blocks                                            */
+    double eps;             /* imbalance                                         */
+    int64_t U;              /* cluster bound; <= 0: max(max c(v), c(V)/(10k))    */
+    int32_t cluster_rounds; /* l: SCLaP rounds per coarsening level              */
+    int32_t refine_rounds;  /* r: SCLaP rounds per uncoarsening level            */
+    int32_t subrounds;      /* S                                                 */
+    int64_t n_stop;         /* coarsen while the current level has >= n_stop nodes */
+    int32_t max_levels;     /* hierarchy depth cap (<= 64; <= 0: 32)             */
+    int32_t init_seeds;     /* P individuals in the initial partition           */
+    int32_t init_rounds;    /* refinement rounds inside the initial partition   */
+    uint64_t seed;
+} sclap_ml_params;
+
+#define SCLAP_MAX_LEVELS 64
+typedef struct {
+    int32_t levels;                            /* graphs in the hierarchy        */
+    int64_t n[SCLAP_MAX_LEVELS];
+    int64_t nnz[SCLAP_MAX_LEVELS];
+    int32_t cluster_rounds_done[SCLAP_MAX_LEVELS];
+    int32_t refine_rounds_done[SCLAP_MAX_LEVELS];
+    int64_t U, lmax;
+    int32_t init_best;                         /* chosen individual              */
+    int64_t init_cut, init_maxbw;
+    int64_t cut, maxbw;                        /* final partition               */
+} sclap_ml_stats;
+
+/* Size-constrained clustering, Sec. III.A ("label propagation with size
+ * constraints") and Sec. IV.A-B.  Every node starts in its own cluster
+ * (label = id); afterwards every cluster weight is <= U.
+ *   U               >= max_v c(v), else SCLAP_EINVAL
+ *   rounds (l)      >= 0;  subrounds (S) >= 1
+ *   constraint_part NULL, or device int32[n]: clusters stay inside the blocks
+ *                   of this partition (iterated V-cycles, Sec. IV.D)
+ *   labels_out      device int32[n]: cluster id (a node id) per node
+ *   rounds_done     host, rounds executed (the last one may have 0 moves)
+ * Needs c(V) <= INT32_MAX and sum(adjwgt) <= INT32_MAX (SCLAP_EOVERFLOW). */
+int sclap_cluster(const sclap_graph *g, int64_t U, int32_t rounds, int32_t subrounds,
+                  uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
+                  int32_t *rounds_done, void *stream);
+
+/* SCLaP as local search on a k-partition, Sec. III.A (bound L_max, the
+ * overloaded-block rule) and Sec. IV.B (exact block weights).
+ *   part_inout  device int32[n], values in [0, k); refined in place
+ *   cut_out     host int64: cut of the result (Sec. II.A)
+ *   block_w_out host int64[k]: block weights of the result
+ * Needs every weighted degree <= INT32_MAX (SCLAP_EOVERFLOW). */
+int sclap_refine(const sclap_graph *g, int32_t k, double eps, int32_t rounds,
+                 int32_t subrounds, uint64_t seed, int32_t *part_inout, int64_t *cut_out,
+                 int64_t *block_w_out, int32_t *rounds_done, void *stream);
+
+/* Same as sclap_refine with an explicit bound B on every one of `nblocks`
+ * blocks (used for batched runs over disjoint unions of graphs). */
+int sclap_refine_bound(const sclap_graph *g, int32_t nblocks, int64_t B, int32_t rounds,
+                       int32_t subrounds, uint64_t seed, int32_t *part_inout,
+                       int32_t *rounds_done, void *stream);
+
+/* Cluster contraction, Sec. III ("contracting a clustering") and Sec. IV.C:
+ * coarse id q(L) = rank of L among the distinct labels (ascending), f2c(v) =
+ * q(label(v)); coarse node weight = cluster weight; coarse edge weight = sum
+ * of omega between the two clusters; intra-cluster edges dropped.  Output is
+ * canonical: rows ascending, neighbours strictly ascending, symmetric.
+ *   labels      device int32[n], values in [0, n)
+ *   coarse_out  filled with library-allocated device arrays (free with
+ *               sclap_graph_free)
+ *   f2c_out     device int32[n] */
+int contract_graph(const sclap_graph *g, const int32_t *labels, sclap_graph_owned *coarse_out,
+                   int32_t *f2c_out, void *stream);
+
+/* Uncoarsening, Sec. III and Sec. IV.C: fine_part_out[v] = coarse_part[f2c[v]].
+ * All three arrays are device memory; no validation beyond n_fine >= 0. */
+int project_partition(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_part,
+                      int32_t *fine_part_out, void *stream);
+
+/* Cut (Sec. II.A) and block weights of a partition.
+ *   part        device int32[n] in [0, k)
+ *   cut_out     host int64;  block_w_out host int64[k] (NULL allowed) */
+int sclap_cut(const sclap_graph *g, const int32_t *part, int32_t k, int64_t *cut_out,
+              int64_t *block_w_out, void *stream);
+
+/* Initial partition of a (coarsest) graph; stands in for the paper's
+ * evolutionary initial partitioner (Sec. II.C, Sec. IV.E).  P individuals:
+ * individual t places the nodes in (c desc, h_t(v) asc, v asc) order into
+ * the lightest block, h_t(v) = high 32 bits of mix64(s_t ^ v), s_t =
+ * mix64(seed ^ (0xD1B54A32D192ED03 * (t + 1))); all individuals are then
+ * refined for `rounds` rounds as one SCLaP refinement over the disjoint union
+ * of P copies (copy t: nodes t*n+v, blocks t*k..t*k+k-1, bound B, `seed`).
+ * Best = lowest cut with max block <= B (lowest t on ties), else smallest
+ * max block, then cut, then t.
+ *   part_out  device int32[n];  cuts_out, maxbw_out host int64[P] (NULL ok);
+ *   best_out  host int32 */
+int sclap_initial_partition(const sclap_graph *g, int32_t k, int64_t B, int32_t P,
+                            int32_t rounds, int32_t subrounds, uint64_t seed,
+                            int32_t *part_out, int64_t *cuts_out, int64_t *maxbw_out,
+                            int32_t *best_out, void *stream);
+
+/* The multilevel partitioner, Sec. IV.E: l rounds of clustering and a
+ * contraction per level while n >= n_stop (stop also when a level shrinks by
+ * less than 5%, when it does not shrink at all, or at max_levels); the
+ * initial partition above on the coarsest graph with level seed; then per
+ * finer level projection and r rounds of refinement.  Level l uses seed
+ * s_l = mix64(seed ^ (0x9E3779B97F4A7C15 * (l + 1))) for both forms.
+ *   g         graph arrays may be HOST or DEVICE memory (detected per call;
+ *             host arrays are copied to the device inside the call)
+ *   part_out  int32[n], host or device (detected), block per node
+ *   stats_out host, may be NULL */
+int partition_multilevel(const sclap_graph *g, const sclap_ml_params *p, int32_t *part_out,
+                         sclap_ml_stats *stats_out, void *stream);
+
+void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed);
+
+/* Copies a library-owned graph into caller-allocated device arrays of sizes
+ * n+1, nnz, nnz and n (enqueued on `stream`, synchronised before return). */
+int sclap_graph_copy_out(const sclap_graph_owned *g, int64_t *xadj, int32_t *adjncy,
+                         int32_t *adjwgt, int32_t *vwgt, void *stream);
+
+/* Releases the arrays of a graph returned by contract_graph. */
+void sclap_graph_free(sclap_graph_owned *g);
+
+const char *sclap_strerror(int code);
+
+/* Graph validation on entry (on by default): monotone xadj, ids in range, rows
+ * strictly ascending (hence no duplicates), no self-loops, symmetric equal
+ * weights, omega > 0, c >= 0.  Returns the previous setting. */
+int sclap_set_validation(int on);
+
+/* Instrumentation.  When enabled, the library brackets every launch of the
+ * neighbour-aggregation (propose) kernel with CUDA events on its stream and
+ * counts the algorithmic bytes it must move (12 B per scanned entry: adjncy,
+ * adjwgt, the neighbour-label gather; 24 B per visited node: xadj, label,
+ * vwgt, proposal, label write-back).  sclap_prof_read synchronises the device
+ * and returns the totals since the last reset. */
+typedef struct {
+    int64_t propose_launches;
+    double propose_ms;            /* sum of event-timed launch durations          */
+    double propose_bytes;         /* algorithmic bytes of those launches          */
+    int64_t entries_scanned;      /* directed entries aggregated                  */
+    int64_t nodes_visited;
+    int64_t kernel_launches;      /* every kernel this library launched           */
+} sclap_prof;
+void sclap_prof_enable(int on);
+void sclap_prof_reset(void);
+int sclap_prof_read(sclap_prof *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

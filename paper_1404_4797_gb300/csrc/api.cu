@@ -1,0 +1,737 @@
+// api.cu -- the C ABI (include/sclap.h): argument checks, graph validation,
+// overflow checks, the initial partitioner and the multilevel driver.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "contract.cuh"
+#include "lp.cuh"
+#include "prims.cuh"
+
+using namespace sclap;
+
+namespace {
+
+bool g_validate = true;
+
+template <class F>
+int guarded(F &&f) {
+    try {
+        f();
+        return SCLAP_OK;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        return SCLAP_ENOMEM;
+    } catch (...) {
+        return SCLAP_ECUDA;
+    }
+}
+
+cudaStream_t as_stream(void *p) { return reinterpret_cast<cudaStream_t>(p); }
+
+DGraph view(const sclap_graph *g) {
+    return DGraph{g->n, g->nnz, g->xadj, g->adjncy, g->adjwgt, g->vwgt};
+}
+
+// Sec. II.A: L_max = (1 + eps) * ceil(c(V) / k), rounded down.
+int64_t lmax_of(int64_t cV, int32_t k, double eps) {
+    int64_t avg = (cV + k - 1) / k;
+    return (int64_t)std::floor((1.0 + eps) * (double)avg);
+}
+
+uint64_t level_seed(uint64_t seed, int l) {
+    return mix64(seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(l + 1)));
+}
+
+// identity labels (clustering with zero rounds)
+__global__ void k_identity(int64_t n, int32_t *lab) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        lab[v] = (int32_t)v;
+}
+
+void identity_labels(int64_t n, int32_t *lab, cudaStream_t s) {
+    if (n <= 0) return;
+    k_identity<<<dev_info().sms * 4, 256, 0, s>>>(n, lab);
+    LAUNCHED();
+}
+
+// ---------------------------------------------------------------- validation
+
+__global__ void k_validate_nodes(DGraph g, int *bad) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (g.xadj[v + 1] < g.xadj[v] || g.vwgt[v] < 0) atomicOr(bad, 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        if (g.xadj[0] != 0 || g.xadj[g.n] != g.nnz) atomicOr(bad, 1);
+}
+
+__device__ __forceinline__ int64_t ub64(const int64_t *a, int64_t lo, int64_t hi, int64_t x) {
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Entry checks (xadj already known to be monotone): ids in range, no
+// self-loops, omega > 0, rows strictly ascending, mirror entry present with
+// the same weight.
+__global__ void k_validate_entries(DGraph g, int *bad) {
+    const int64_t runs = ceil_div<int64_t>(g.nnz, 16);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < runs;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = r * 16, e1 = min64(g.nnz, e + 16);
+        int64_t v = ub64(g.xadj, 0, g.n + 1, e) - 1;
+        for (; e < e1; e++) {
+            while (e >= g.xadj[v + 1]) v++;
+            int32_t u = g.adjncy[e];
+            int32_t w = g.adjwgt[e];
+            if (u < 0 || u >= g.n || u == v || w <= 0) { atomicOr(bad, 1); return; }
+            if (e > g.xadj[v] && g.adjncy[e - 1] >= u) { atomicOr(bad, 1); return; }
+            // mirror (u, v) by binary search in row u
+            int64_t lo = g.xadj[u], hi = g.xadj[u + 1];
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (g.adjncy[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= g.xadj[u + 1] || g.adjncy[lo] != v || g.adjwgt[lo] != w) {
+                atomicOr(bad, 1);
+                return;
+            }
+        }
+    }
+}
+
+void validate_graph(const DGraph &g, Scratch &sc) {
+    if (g.n < 0 || g.nnz < 0 || g.n > INT32_MAX) fail(SCLAP_EINVAL, "graph size");
+    if (g.n > 0 && (!g.xadj || !g.vwgt)) fail(SCLAP_EINVAL, "null graph array");
+    if (g.nnz > 0 && (!g.adjncy || !g.adjwgt)) fail(SCLAP_EINVAL, "null graph array");
+    if (!g_validate || g.n == 0) return;
+    cudaStream_t s = sc.stream();
+    int *bad = sc.zeros<int>(1);
+    int grid = dev_info().sms * 8;
+    k_validate_nodes<<<grid, 256, 0, s>>>(g, bad);
+    LAUNCHED();
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h) fail(SCLAP_EGRAPH, "xadj / vwgt");
+    if (g.nnz > 0) {
+        k_validate_entries<<<grid, 256, 0, s>>>(g, bad);
+        LAUNCHED();
+        CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h) fail(SCLAP_EGRAPH, "adjacency");
+    }
+}
+
+__global__ void k_check_range(int64_t n, const int32_t *a, int64_t hi, int *bad) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (a[v] < 0 || a[v] >= hi) atomicOr(bad, 1);
+}
+
+bool in_range(int64_t n, const int32_t *a, int64_t hi, Scratch &sc) {
+    if (n == 0) return true;
+    cudaStream_t s = sc.stream();
+    int *bad = sc.zeros<int>(1);
+    k_check_range<<<dev_info().sms * 4, 256, 0, s>>>(n, a, hi, bad);
+    LAUNCHED();
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return h == 0;
+}
+
+// ---------------------------------------------------------------- initial partition
+
+__global__ void k_union(DGraph g, int64_t P, int64_t *ux, int32_t *ua, int32_t *uw, int32_t *uc) {
+    const int64_t un = g.n * P, unnz = g.nnz * P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = i / g.n, v = i % g.n;
+        ux[i] = t * g.nnz + g.xadj[v];
+        uc[i] = g.vwgt[v];
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < unnz;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = i / g.nnz, e = i % g.nnz;
+        ua[i] = (int32_t)(g.adjncy[e] + t * g.n);
+        uw[i] = g.adjwgt[e];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ux[un] = unnz;
+}
+
+// LPT order keys: first pass h_t(v), second pass (t, Cmax - c).
+__global__ void k_lpt_keys1(int64_t n, int64_t P, uint64_t seed, uint64_t *key, int32_t *idx) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * P;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = i / n, v = i % n;
+        uint64_t st = mix64(seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(t + 1)));
+        key[i] = mix64(st ^ (uint64_t)v) >> 32;
+        idx[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_lpt_keys2(int64_t n, int64_t P, const int32_t *idx, const int32_t *vwgt, int cb,
+                             int64_t cmax, uint64_t *key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * P;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = idx[i];
+        int64_t t = u / n, v = u % n;
+        key[i] = ((uint64_t)t << cb) | (uint64_t)(cmax - vwgt[v]);
+    }
+}
+
+// One block per individual t: nodes in sorted order go to the lightest block
+// (lowest id on ties).  Sequential by nature; one warp does the argmin.
+__global__ void k_lpt_assign(int64_t n, int32_t k, const int32_t *order, const int32_t *vwgt,
+                             int32_t *upart) {
+    extern __shared__ int64_t bw[];
+    const int64_t t = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int b = lane; b < k; b += 32) bw[b] = 0;
+    __syncwarp();
+    const int32_t *ord = order + t * n;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t u = ord[i];
+        int64_t v = u - t * n;
+        int64_t bestw = INT64_MAX;
+        int bestb = 0x7fffffff;
+        for (int b = lane; b < k; b += 32)
+            if (bw[b] < bestw) { bestw = bw[b]; bestb = b; }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            int64_t ow = __shfl_xor_sync(0xffffffffu, bestw, d);
+            int ob = __shfl_xor_sync(0xffffffffu, bestb, d);
+            if (ow < bestw || (ow == bestw && ob < bestb)) { bestw = ow; bestb = ob; }
+        }
+        if (lane == 0) {
+            upart[u] = (int32_t)(t * k + bestb);
+            bw[bestb] += vwgt[v];
+        }
+        __syncwarp();
+    }
+}
+
+// Best individual: lowest cut among those with max block <= B (lowest t on
+// ties); otherwise smallest max block, then cut, then t.
+__global__ void k_pick_best(int64_t P, int32_t k, int64_t B, const int64_t *cut, const int64_t *bw,
+                            int64_t *maxbw_out, int32_t *best_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t best = -1;
+    int64_t bc = 0, bm = 0;
+    for (int64_t t = 0; t < P; t++) {
+        int64_t mx = 0;
+        for (int b = 0; b < k; b++) mx = max(mx, bw[t * k + b]);
+        maxbw_out[t] = mx;
+        bool better;
+        if (best < 0) better = true;
+        else {
+            bool fn = mx <= B, fo = bm <= B;
+            if (fn != fo) better = fn;
+            else if (fn) better = cut[t] < bc;
+            else better = mx < bm || (mx == bm && cut[t] < bc);
+        }
+        if (better) { best = (int32_t)t; bc = cut[t]; bm = mx; }
+    }
+    *best_out = best;
+}
+
+__global__ void k_extract(int64_t n, int32_t k, const int32_t *best, const int32_t *upart,
+                          int32_t *part) {
+    const int64_t t = *best;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        part[v] = upart[t * n + v] - (int32_t)(t * k);
+}
+
+struct InitResult {
+    int32_t best;
+    std::vector<int64_t> cuts, maxbw;
+};
+
+InitResult initial_impl(const DGraph &g, int32_t k, int64_t B, int32_t P, int32_t rounds,
+                        int32_t S, uint64_t seed, int32_t *part_out, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    const int grid = dev_info().sms * 8;
+    const int64_t n = g.n;
+    const int64_t un = n * P, unnz = g.nnz * P;
+    if (un > INT32_MAX) fail(SCLAP_EINVAL, "initial partition too large");
+    int64_t *ux = sc.get<int64_t>(un + 1);
+    int32_t *ua = sc.get<int32_t>(unnz);
+    int32_t *uw = sc.get<int32_t>(unnz);
+    int32_t *uc = sc.get<int32_t>(un);
+    int32_t *up = sc.get<int32_t>(un);
+    InitResult res;
+    res.cuts.assign(P, 0);
+    res.maxbw.assign(P, 0);
+    if (n == 0) {
+        res.best = 0;
+        return res;
+    }
+    k_union<<<grid, 256, 0, s>>>(g, P, ux, ua, uw, uc);
+    LAUNCHED();
+    // LPT order per individual: (t, c desc, h asc, v asc) by two stable sorts
+    uint64_t *key = sc.get<uint64_t>(un);
+    int32_t *idx = sc.get<int32_t>(un);
+    k_lpt_keys1<<<grid, 256, 0, s>>>(n, P, seed, key, idx);
+    LAUNCHED();
+    radix_sort_pairs(key, idx, un, 32, sc);
+    GraphTotals tot = graph_totals(g, sc);
+    const int cb = std::max(1, bit_width_u64((uint64_t)tot.maxc));
+    const int tb = std::max(1, bit_width_u64((uint64_t)(P - 1)));
+    k_lpt_keys2<<<grid, 256, 0, s>>>(n, P, idx, g.vwgt, cb, tot.maxc, key);
+    LAUNCHED();
+    radix_sort_pairs(key, idx, un, cb + tb, sc);
+    k_lpt_assign<<<P, 32, k * sizeof(int64_t), s>>>(n, k, idx, g.vwgt, up);
+    LAUNCHED();
+    // refine all individuals together on the disjoint union
+    DGraph ug{un, unnz, ux, ua, uw, uc};
+    LPConfig cfg{};
+    cfg.g = ug;
+    cfg.lab = up;
+    cfg.nW = (int64_t)k * P;
+    cfg.B = B;
+    cfg.refine = true;
+    cfg.cp = nullptr;
+    cfg.seed = seed;
+    cfg.rounds = rounds;
+    cfg.S = S;
+    cfg.max_deg = tot.max_deg;
+    lp_run(cfg, sc, nullptr, nullptr);
+    int64_t *d_cut = sc.get<int64_t>(P);
+    int64_t *d_bw = sc.get<int64_t>((int64_t)k * P);
+    cut_impl(ug, up, (int64_t)k * P, P, n, d_cut, d_bw, sc);
+    int64_t *d_max = sc.get<int64_t>(P);
+    int32_t *d_best = sc.get<int32_t>(1);
+    k_pick_best<<<1, 32, 0, s>>>(P, k, B, d_cut, d_bw, d_max, d_best);
+    LAUNCHED();
+    k_extract<<<grid, 256, 0, s>>>(n, k, d_best, up, part_out);
+    LAUNCHED();
+    CK(cudaMemcpyAsync(res.cuts.data(), d_cut, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(res.maxbw.data(), d_max, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&res.best, d_best, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return res;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void check_totals_cluster(const GraphTotals &t) {
+    if (t.cV > INT32_MAX || t.sum_w > INT32_MAX) fail(SCLAP_EOVERFLOW, "c(V) or sum(omega)");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char *sclap_strerror(int code) {
+    switch (code) {
+        case SCLAP_OK: return "ok";
+        case SCLAP_EINVAL: return "invalid argument";
+        case SCLAP_EGRAPH: return "graph failed validation";
+        case SCLAP_EOVERFLOW: return "weights exceed the 32-bit range";
+        case SCLAP_ENOMEM: return "out of device memory";
+        case SCLAP_ECUDA: return "CUDA error";
+        case SCLAP_ETIMEOUT: return "device wait timed out";
+        case SCLAP_ENOTIMPL: return "not implemented";
+        default: return "unknown error";
+    }
+}
+
+int sclap_set_validation(int on) {
+    int old = g_validate ? 1 : 0;
+    g_validate = on != 0;
+    return old;
+}
+
+void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed) {
+    std::memset(p, 0, sizeof(*p));
+    p->k = k;
+    p->eps = eps;
+    p->U = 0;
+    p->cluster_rounds = 3;
+    p->refine_rounds = 6;
+    p->subrounds = 4;
+    p->n_stop = 2000;
+    p->max_levels = 32;
+    p->init_seeds = 8;
+    p->init_rounds = 6;
+    p->seed = seed;
+}
+
+int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subrounds,
+                  uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
+                  int32_t *rounds_done, void *stream) {
+    return guarded([&] {
+        if (!gp || !labels_out) fail(SCLAP_EINVAL, "null");
+        if (rounds < 0 || subrounds < 1 || subrounds > 32) fail(SCLAP_EINVAL, "rounds");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        DGraph g = view(gp);
+        validate_graph(g, sc);
+        GraphTotals t = graph_totals(g, sc);
+        if (U < t.maxc) fail(SCLAP_EINVAL, "U < max c(v)");
+        check_totals_cluster(t);
+        LPConfig cfg{};
+        cfg.g = g;
+        cfg.lab = labels_out;
+        cfg.nW = g.n;
+        cfg.B = U;
+        cfg.refine = false;
+        cfg.cp = constraint_part;
+        cfg.seed = seed;
+        cfg.rounds = rounds;
+        cfg.S = subrounds;
+        cfg.max_deg = t.max_deg;
+        int rd = 0;
+        if (rounds > 0 && g.n > 0) rd = lp_run(cfg, sc, nullptr, nullptr);
+        else identity_labels(g.n, labels_out, s);
+        CK(cudaStreamSynchronize(s));
+        if (rounds_done) *rounds_done = rd;
+    });
+}
+
+int sclap_refine_bound(const sclap_graph *gp, int32_t nblocks, int64_t B, int32_t rounds,
+                       int32_t subrounds, uint64_t seed, int32_t *part_inout,
+                       int32_t *rounds_done, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    int32_t *backup = nullptr;
+    int rc = guarded([&] {
+        if (!gp || !part_inout) fail(SCLAP_EINVAL, "null");
+        if (nblocks < 1 || rounds < 0 || subrounds < 1 || subrounds > 32) fail(SCLAP_EINVAL, "args");
+        Scratch sc(s);
+        DGraph g = view(gp);
+        validate_graph(g, sc);
+        if (!in_range(g.n, part_inout, nblocks, sc)) fail(SCLAP_EINVAL, "part out of range");
+        GraphTotals t = graph_totals(g, sc);
+        if (t.max_wdeg > INT32_MAX) fail(SCLAP_EOVERFLOW, "weighted degree");
+        CK(cudaMalloc(&backup, (g.n ? g.n : 1) * sizeof(int32_t)));
+        CK(cudaMemcpyAsync(backup, part_inout, g.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        LPConfig cfg{};
+        cfg.g = g;
+        cfg.lab = part_inout;
+        cfg.nW = nblocks;
+        cfg.B = B;
+        cfg.refine = true;
+        cfg.seed = seed;
+        cfg.rounds = rounds;
+        cfg.S = subrounds;
+        cfg.max_deg = t.max_deg;
+        int rd = lp_run(cfg, sc, nullptr, nullptr);
+        CK(cudaStreamSynchronize(s));
+        if (rounds_done) *rounds_done = rd;
+    });
+    if (rc != SCLAP_OK && backup && gp) {
+        cudaMemcpyAsync(part_inout, backup, gp->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    if (backup) cudaFree(backup);
+    return rc;
+}
+
+int sclap_refine(const sclap_graph *gp, int32_t k, double eps, int32_t rounds, int32_t subrounds,
+                 uint64_t seed, int32_t *part_inout, int64_t *cut_out, int64_t *block_w_out,
+                 int32_t *rounds_done, void *stream) {
+    if (!gp || k < 1 || !(eps >= 0)) return SCLAP_EINVAL;
+    int64_t cV = 0;
+    int rc = guarded([&] {
+        Scratch sc(as_stream(stream));
+        DGraph g = view(gp);
+        validate_graph(g, sc);
+        cV = graph_totals(g, sc).cV;
+    });
+    if (rc) return rc;
+    rc = sclap_refine_bound(gp, k, lmax_of(cV, k, eps), rounds, subrounds, seed, part_inout,
+                            rounds_done, stream);
+    if (rc) return rc;
+    if (cut_out || block_w_out) {
+        int64_t cut = 0;
+        rc = sclap_cut(gp, part_inout, k, &cut, block_w_out, stream);
+        if (cut_out) *cut_out = cut;
+    }
+    return rc;
+}
+
+int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cut_out,
+              int64_t *block_w_out, void *stream) {
+    return guarded([&] {
+        if (!gp || !part || k < 1) fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        DGraph g = view(gp);
+        int64_t *d_cut = sc.get<int64_t>(1);
+        int64_t *d_bw = sc.get<int64_t>(k);
+        cut_impl(g, part, k, 1, g.n, d_cut, d_bw, sc);
+        int64_t c = 0;
+        CK(cudaMemcpyAsync(&c, d_cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        if (block_w_out)
+            CK(cudaMemcpyAsync(block_w_out, d_bw, k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (cut_out) *cut_out = c;
+    });
+}
+
+int contract_graph(const sclap_graph *gp, const int32_t *labels, sclap_graph_owned *coarse_out,
+                   int32_t *f2c_out, void *stream) {
+    return guarded([&] {
+        if (!gp || !labels || !coarse_out || !f2c_out) fail(SCLAP_EINVAL, "null");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        DGraph g = view(gp);
+        validate_graph(g, sc);
+        if (!in_range(g.n, labels, g.n, sc)) fail(SCLAP_EINVAL, "label out of range");
+        GraphTotals t = graph_totals(g, sc);
+        check_totals_cluster(t);
+        CoarseGraph cg;
+        contract_impl(g, labels, f2c_out, &cg, nullptr, sc);
+        CK(cudaStreamSynchronize(s));
+        coarse_out->n = cg.n;
+        coarse_out->nnz = cg.nnz;
+        coarse_out->xadj = cg.xadj;
+        coarse_out->adjncy = cg.adjncy;
+        coarse_out->adjwgt = cg.adjwgt;
+        coarse_out->vwgt = cg.vwgt;
+    });
+}
+
+int sclap_graph_copy_out(const sclap_graph_owned *g, int64_t *xadj, int32_t *adjncy,
+                         int32_t *adjwgt, int32_t *vwgt, void *stream) {
+    return guarded([&] {
+        if (!g || !xadj || (g->n > 0 && !vwgt) || (g->nnz > 0 && (!adjncy || !adjwgt)))
+            fail(SCLAP_EINVAL, "null");
+        cudaStream_t s = as_stream(stream);
+        CK(cudaMemcpyAsync(xadj, g->xadj, (g->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        if (g->nnz > 0) {
+            CK(cudaMemcpyAsync(adjncy, g->adjncy, g->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(adjwgt, g->adjwgt, g->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        }
+        if (g->n > 0)
+            CK(cudaMemcpyAsync(vwgt, g->vwgt, g->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    });
+}
+
+void sclap_graph_free(sclap_graph_owned *g) {
+    if (!g) return;
+    cudaFree(g->xadj);
+    cudaFree(g->adjncy);
+    cudaFree(g->adjwgt);
+    cudaFree(g->vwgt);
+    std::memset(g, 0, sizeof(*g));
+}
+
+int project_partition(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_part,
+                      int32_t *fine_part_out, void *stream) {
+    return guarded([&] {
+        if (n_fine < 0) fail(SCLAP_EINVAL, "n");
+        if (n_fine > 0 && (!f2c || !coarse_part || !fine_part_out)) fail(SCLAP_EINVAL, "null");
+        cudaStream_t s = as_stream(stream);
+        project_impl(n_fine, f2c, coarse_part, fine_part_out, s);
+        CK(cudaStreamSynchronize(s));
+    });
+}
+
+int sclap_initial_partition(const sclap_graph *gp, int32_t k, int64_t B, int32_t P, int32_t rounds,
+                            int32_t subrounds, uint64_t seed, int32_t *part_out, int64_t *cuts_out,
+                            int64_t *maxbw_out, int32_t *best_out, void *stream) {
+    return guarded([&] {
+        if (!gp || !part_out || k < 1 || P < 1 || rounds < 0 || subrounds < 1 || subrounds > 32)
+            fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        DGraph g = view(gp);
+        validate_graph(g, sc);
+        GraphTotals t = graph_totals(g, sc);
+        if (t.max_wdeg > INT32_MAX) fail(SCLAP_EOVERFLOW, "weighted degree");
+        InitResult r = initial_impl(g, k, B, P, rounds, subrounds, seed, part_out, sc);
+        if (cuts_out) std::memcpy(cuts_out, r.cuts.data(), P * sizeof(int64_t));
+        if (maxbw_out) std::memcpy(maxbw_out, r.maxbw.data(), P * sizeof(int64_t));
+        if (best_out) *best_out = r.best;
+    });
+}
+
+int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_t *part_out,
+                         sclap_ml_stats *st_out, void *stream) {
+    return guarded([&] {
+        if (!gp || !p || !part_out) fail(SCLAP_EINVAL, "null");
+        if (p->k < 1 || !(p->eps >= 0) || p->cluster_rounds < 0 || p->refine_rounds < 0 ||
+            p->subrounds < 1 || p->subrounds > 32 || p->init_seeds < 1 || p->init_rounds < 0)
+            fail(SCLAP_EINVAL, "params");
+        cudaStream_t s = as_stream(stream);
+        Scratch top(s);
+        const int64_t n = gp->n, nnz = gp->nnz;
+        if (n < 0 || nnz < 0 || n > INT32_MAX) fail(SCLAP_EINVAL, "size");
+        DGraph g0 = view(gp);
+        if (n > 0 && !is_device_ptr(gp->xadj)) {
+            // host input: copy the graph to the device inside the call
+            int64_t *x = top.get<int64_t>(n + 1);
+            int32_t *a = top.get<int32_t>(nnz);
+            int32_t *w = top.get<int32_t>(nnz);
+            int32_t *c = top.get<int32_t>(n);
+            CK(cudaMemcpyAsync(x, gp->xadj, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            if (nnz) {
+                CK(cudaMemcpyAsync(a, gp->adjncy, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(w, gp->adjwgt, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            }
+            CK(cudaMemcpyAsync(c, gp->vwgt, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            g0 = DGraph{n, nnz, x, a, w, c};
+        }
+        const bool part_on_device = is_device_ptr(part_out);
+        validate_graph(g0, top);
+        GraphTotals t0 = graph_totals(g0, top);
+        check_totals_cluster(t0);
+        const int64_t lmax = lmax_of(t0.cV, p->k, p->eps);
+        const int64_t U = p->U > 0 ? p->U : std::max<int64_t>(t0.maxc, t0.cV / (10 * (int64_t)p->k));
+        if (U < t0.maxc) fail(SCLAP_EINVAL, "U < max c(v)");
+        int maxl = p->max_levels > 0 ? p->max_levels : 32;
+        if (maxl > SCLAP_MAX_LEVELS) maxl = SCLAP_MAX_LEVELS;
+
+        sclap_ml_stats st;
+        std::memset(&st, 0, sizeof(st));
+        std::vector<DGraph> G{g0};
+        std::vector<int32_t *> F;  // f2c per level
+        std::vector<int64_t> maxdeg{t0.max_deg};
+        int L = 0;
+        while (G[L].n >= p->n_stop && L + 1 < maxl && G[L].n > 0) {
+            const DGraph &g = G[L];
+            Scratch tmp(s);
+            int32_t *lab = tmp.get<int32_t>(g.n);
+            LPConfig cfg{};
+            cfg.g = g;
+            cfg.lab = lab;
+            cfg.nW = g.n;
+            cfg.B = U;
+            cfg.refine = false;
+            cfg.seed = level_seed(p->seed, L);
+            cfg.rounds = p->cluster_rounds;
+            cfg.S = p->subrounds;
+            cfg.max_deg = maxdeg[L];
+            int rd = 0;
+            if (cfg.rounds > 0) rd = lp_run(cfg, tmp, nullptr, nullptr);
+            else identity_labels(g.n, lab, s);
+            st.cluster_rounds_done[L] = rd;
+            int32_t *f2c = top.get<int32_t>(g.n);
+            CoarseGraph cg;
+            contract_impl(g, lab, f2c, &cg, &top, tmp);
+            if (cg.n == g.n) break;  // no shrink: the level is dropped
+            F.push_back(f2c);
+            DGraph c{cg.n, cg.nnz, cg.xadj, cg.adjncy, cg.adjwgt, cg.vwgt};
+            G.push_back(c);
+            maxdeg.push_back(graph_totals(c, tmp).max_deg);
+            L++;
+            if (20 * G[L].n > 19 * G[L - 1].n) break;  // stalled (< 5% shrink)
+        }
+        // initial partition of the coarsest graph
+        int32_t *cur = top.get<int32_t>(G[L].n);
+        InitResult ir = initial_impl(G[L], p->k, lmax, p->init_seeds, p->init_rounds, p->subrounds,
+                                     level_seed(p->seed, L), cur, top);
+        st.init_best = ir.best;
+        st.init_cut = ir.cuts.empty() ? 0 : ir.cuts[ir.best];
+        st.init_maxbw = ir.maxbw.empty() ? 0 : ir.maxbw[ir.best];
+        // uncoarsening: projection and r rounds of refinement per level
+        for (int l = L - 1; l >= 0; l--) {
+            int32_t *fp = top.get<int32_t>(G[l].n);
+            project_impl(G[l].n, F[l], cur, fp, s);
+            cur = fp;
+            Scratch tmp(s);
+            LPConfig cfg{};
+            cfg.g = G[l];
+            cfg.lab = cur;
+            cfg.nW = p->k;
+            cfg.B = lmax;
+            cfg.refine = true;
+            cfg.seed = level_seed(p->seed, l);
+            cfg.rounds = p->refine_rounds;
+            cfg.S = p->subrounds;
+            cfg.max_deg = maxdeg[l];
+            st.refine_rounds_done[l] = lp_run(cfg, tmp, nullptr, nullptr);
+        }
+        // final cut and balance
+        int64_t *d_cut = top.get<int64_t>(1);
+        int64_t *d_bw = top.get<int64_t>(p->k);
+        cut_impl(g0, cur, p->k, 1, n, d_cut, d_bw, top);
+        std::vector<int64_t> bw(p->k);
+        CK(cudaMemcpyAsync(&st.cut, d_cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(bw.data(), d_bw, p->k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(part_out, cur, n * sizeof(int32_t),
+                           part_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int64_t x : bw) st.maxbw = std::max(st.maxbw, x);
+        st.levels = L + 1;
+        for (int l = 0; l <= L; l++) {
+            st.n[l] = G[l].n;
+            st.nnz[l] = G[l].nnz;
+        }
+        st.U = U;
+        st.lmax = lmax;
+        if (st_out) *st_out = st;
+    });
+}
+
+// ---------------------------------------------------------------- profiling
+
+void sclap_prof_enable(int on) {
+    ProfState &P = prof();
+    P.on = on != 0;
+    if (P.on && !P.d_counts) {
+        cudaMalloc(&P.d_counts, 2 * sizeof(unsigned long long));
+        cudaMemset(P.d_counts, 0, 2 * sizeof(unsigned long long));
+    }
+}
+
+void sclap_prof_reset(void) {
+    ProfState &P = prof();
+    cudaDeviceSynchronize();
+    for (auto &pr : P.pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    P.pending.clear();
+    P.propose_launches = 0;
+    P.propose_ms = 0;
+    if (P.d_counts) cudaMemset(P.d_counts, 0, 2 * sizeof(unsigned long long));
+}
+
+int sclap_prof_read(sclap_prof *out) {
+    return guarded([&] {
+        ProfState &P = prof();
+        CK(cudaDeviceSynchronize());
+        for (auto &pr : P.pending) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+            P.propose_ms += ms;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        P.pending.clear();
+        unsigned long long c[2] = {0, 0};
+        if (P.d_counts) CK(cudaMemcpy(c, P.d_counts, sizeof(c), cudaMemcpyDeviceToHost));
+        out->propose_launches = P.propose_launches;
+        out->propose_ms = P.propose_ms;
+        out->entries_scanned = (int64_t)c[0];
+        out->nodes_visited = (int64_t)c[1];
+        out->propose_bytes = 12.0 * (double)c[0] + 24.0 * (double)c[1];
+        out->kernel_launches = P.kernel_launches;
+    });
+}
+
+}  // extern "C"
+

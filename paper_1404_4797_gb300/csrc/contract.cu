@@ -1,0 +1,384 @@
+// contract.cu -- cluster contraction (Sec. III "contracting a clustering",
+// Sec. IV.C): the prefix-sum map q over used cluster ids, C(v) = q(label(v)),
+// coarse node weights, and the quotient edges.  Quotient edges are reduced
+// in two stages: a shared-memory hash table merges equal (C(u), C(v)) pairs
+// inside fixed 2048-entry slices of the fine rows (rows grouped by coarse
+// node), then a radix sort by (C(u), C(v)) and a reduce-by-key produce the
+// canonical sorted CSR.  Also projection (uncoarsening) and cut/balance.
+#include "contract.cuh"
+#include "prims.cuh"
+
+namespace sclap {
+
+constexpr int kCThreads = 256;
+constexpr int kCEntries = 2048;
+constexpr int kCSlots = 4096;
+constexpr int kCBits = 12;
+constexpr uint64_t kCEmpty = ~0ull;
+
+__global__ void k_mark(int64_t n, const int32_t *lab, int32_t *mark) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        mark[lab[v]] = 1;
+}
+
+struct ArrayI32 {
+    const int32_t *p;
+    __device__ int64_t operator()(int64_t i) const { return p[i]; }
+};
+
+// f2c, coarse node weights, member counts and coarse "work" (sum of degrees).
+__global__ void k_f2c(DGraph g, const int32_t *lab, const int64_t *q, int32_t *f2c, int32_t *cvwgt,
+                      int32_t *ccnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = (int32_t)q[lab[v]];
+        f2c[v] = c;
+        atomicAdd(&cvwgt[c], g.vwgt[v]);
+        if (g.xadj[v + 1] > g.xadj[v]) atomicAdd(&ccnt[c], 1);
+    }
+}
+
+// members of coarse node c (nodes with >= 1 entry) at [mstart[c], mstart[c+1]).
+__global__ void k_members(DGraph g, const int32_t *f2c, const int64_t *mstart, int32_t *fill,
+                          int32_t *members) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (g.xadj[v + 1] == g.xadj[v]) continue;
+        int32_t c = f2c[v];
+        members[mstart[c] + atomicAdd(&fill[c], 1)] = (int32_t)v;
+    }
+}
+
+struct MemberDeg {
+    const int64_t *xadj;
+    const int32_t *members;
+    __device__ int64_t operator()(int64_t i) const {
+        int32_t v = members[i];
+        return xadj[v + 1] - xadj[v];
+    }
+};
+
+struct AggSm {
+    unsigned long long keys[kCSlots];
+    int32_t vals[kCSlots];
+    int32_t dl[kCEntries];
+    int32_t rel[kCEntries + 2];      // member start relative to the slice, clamped
+    int64_t ebase[kCEntries + 1];    // xadj[v] - mpre[i]: entry index = ebase + e
+    int32_t cid[kCEntries + 1];
+    int64_t m0;
+    unsigned long long out_base;
+    int ndl, nm;
+};
+
+__device__ __forceinline__ int64_t upper_bound_i64(const int64_t *a, int64_t lo, int64_t hi,
+                                                    int64_t x) {
+    // first index in [lo, hi) with a[i] > x
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Slice t covers concatenated member entries [t*kCEntries, (t+1)*kCEntries).
+__global__ void __launch_bounds__(kCThreads)
+    k_aggregate(DGraph g, const int32_t *members, int64_t nmem, const int64_t *mpre,
+                int64_t total, const int32_t *f2c, int cbits, unsigned long long *out_keys,
+                int32_t *out_w, unsigned long long *out_cnt) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    AggSm &sm = *reinterpret_cast<AggSm *>(smraw);
+    for (int i = threadIdx.x; i < kCSlots; i += kCThreads) {
+        sm.keys[i] = kCEmpty;
+        sm.vals[i] = 0;
+    }
+    const int64_t slices = ceil_div<int64_t>(total, kCEntries);
+    for (int64_t t = blockIdx.x; t < slices; t += gridDim.x) {
+        const int64_t e0 = t * kCEntries;
+        const int64_t e1 = min64(total, e0 + kCEntries);
+        if (threadIdx.x == 0) {
+            int64_t m0 = upper_bound_i64(mpre, 0, nmem, e0) - 1;
+            int64_t m1 = upper_bound_i64(mpre, m0, nmem, e1 - 1);  // one past the last member
+            sm.m0 = m0;
+            sm.nm = (int)(m1 - m0);
+            sm.out_base = 0;
+            sm.ndl = 0;
+        }
+        __syncthreads();
+        const int64_t m0 = sm.m0;
+        const int nm = sm.nm;
+        for (int i = threadIdx.x; i < nm; i += kCThreads) {
+            int64_t mi = m0 + i;
+            int32_t v = members[mi];
+            int64_t p = mpre[mi];
+            sm.rel[i] = (int32_t)max64(0, p - e0);
+            sm.ebase[i] = g.xadj[v] - p;
+            sm.cid[i] = f2c[v];
+        }
+        __syncthreads();
+        const int32_t len = (int32_t)(e1 - e0);
+        for (int32_t le = threadIdx.x; le < len; le += kCThreads) {
+            // member slot: largest i with rel[i] <= le
+            int lo = 0, hi = nm;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (sm.rel[mid] <= le) lo = mid;
+                else hi = mid;
+            }
+            int64_t idx = sm.ebase[lo] + e0 + le;
+            int32_t cu = sm.cid[lo];
+            int32_t cv = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
+            if (cu == cv) continue;  // edge inside a cluster
+            int32_t w = __ldg(&g.adjwgt[idx]);
+            uint64_t key = ((uint64_t)(uint32_t)cu << cbits) | (uint32_t)cv;
+            uint32_t slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCBits));
+            for (int probe = 0; probe < kCSlots; probe++) {  // never full: load <= 1/2
+                unsigned long long prev = atomicCAS(&sm.keys[slot], kCEmpty, key);
+                if (prev == kCEmpty || prev == key) {
+                    atomicAdd(&sm.vals[slot], w);
+                    if (prev == kCEmpty) sm.dl[atomicAdd(&sm.ndl, 1)] = (int32_t)slot;
+                    break;
+                }
+                slot = (slot + 1) & (kCSlots - 1);
+            }
+        }
+        __syncthreads();
+        const int ndl = sm.ndl;
+        if (threadIdx.x == 0 && ndl) sm.out_base = atomicAdd(out_cnt, (unsigned long long)ndl);
+        __syncthreads();
+        const int64_t ob = (int64_t)sm.out_base;
+        for (int i = threadIdx.x; i < ndl; i += kCThreads) {
+            int32_t slot = sm.dl[i];
+            out_keys[ob + i] = sm.keys[slot];
+            out_w[ob + i] = sm.vals[slot];
+            sm.keys[slot] = kCEmpty;
+            sm.vals[slot] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+struct FlagNew {
+    const unsigned long long *k;
+    __device__ int64_t operator()(int64_t i) const { return (i == 0 || k[i] != k[i - 1]) ? 1 : 0; }
+};
+
+__global__ void k_reduce_by_key(const unsigned long long *keys, const int32_t *w, int64_t P,
+                                const int64_t *pos, int cbits, int32_t *adjncy, int32_t *adjwgt,
+                                int32_t *cdeg) {
+    const uint64_t mask = (cbits >= 64) ? ~0ull : ((1ull << cbits) - 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        int64_t p = pos[i] - 1 + ((i == 0 || keys[i - 1] != k) ? 1 : 0);
+        // pos is the exclusive scan of "new key" flags; the unique index of i
+        // is pos[i] if i starts a run, else pos[i] - 1.
+        atomicAdd(&adjwgt[p], w[i]);
+        if (i == 0 || keys[i - 1] != k) {
+            adjncy[p] = (int32_t)(k & mask);
+            atomicAdd(&cdeg[(int64_t)(k >> cbits)], 1);
+        }
+    }
+}
+
+struct ArrayI32to64 {
+    const int32_t *p;
+    __device__ int64_t operator()(int64_t i) const { return p[i]; }
+};
+
+__global__ void k_finish_xadj(const int64_t *pre, int64_t n, int64_t total, int64_t *xadj) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        xadj[i] = i < n ? pre[i] : total;
+}
+
+void contract_impl(const DGraph &g, const int32_t *lab, int32_t *f2c, CoarseGraph *out,
+                   Scratch *out_sc, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    const int sms = dev_info().sms;
+    const int grid = sms * 4;
+    auto out_alloc = [&](size_t bytes) -> void * {
+        if (bytes == 0) bytes = 16;
+        if (out_sc) return out_sc->get<unsigned char>(bytes);
+        void *p = nullptr;
+        CK(cudaMalloc(&p, bytes));
+        return p;
+    };
+    *out = CoarseGraph{};
+    if (g.n == 0) {
+        out->xadj = (int64_t *)out_alloc(sizeof(int64_t));
+        CK(cudaMemsetAsync(out->xadj, 0, sizeof(int64_t), s));
+        out->adjncy = (int32_t *)out_alloc(4);
+        out->adjwgt = (int32_t *)out_alloc(4);
+        out->vwgt = (int32_t *)out_alloc(4);
+        return;
+    }
+    // q: rank of each used label
+    int32_t *mark = sc.zeros<int32_t>(g.n);
+    k_mark<<<grid, 256, 0, s>>>(g.n, lab, mark);
+    LAUNCHED();
+    int64_t *q = sc.get<int64_t>(g.n);
+    int64_t *d_n2 = sc.get<int64_t>(1);
+    exclusive_scan(ArrayI32{mark}, g.n, q, d_n2, sc);
+    int64_t n2 = 0;
+    CK(cudaMemcpyAsync(&n2, d_n2, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+
+    int32_t *cvwgt = (int32_t *)out_alloc(n2 * sizeof(int32_t));
+    CK(cudaMemsetAsync(cvwgt, 0, n2 * sizeof(int32_t), s));
+    int32_t *ccnt = sc.zeros<int32_t>(n2);
+    k_f2c<<<grid, 256, 0, s>>>(g, lab, q, f2c, cvwgt, ccnt);
+    LAUNCHED();
+    int64_t *mstart = sc.get<int64_t>(n2);
+    int64_t *d_nmem = sc.get<int64_t>(1);
+    exclusive_scan(ArrayI32{ccnt}, n2, mstart, d_nmem, sc);
+    int64_t nmem = 0;
+    CK(cudaMemcpyAsync(&nmem, d_nmem, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int32_t *members = sc.get<int32_t>(nmem);
+    int32_t *fill = sc.zeros<int32_t>(n2);
+    k_members<<<grid, 256, 0, s>>>(g, f2c, mstart, fill, members);
+    LAUNCHED();
+    int64_t *mpre = sc.get<int64_t>(nmem + 1);
+    exclusive_scan(MemberDeg{g.xadj, members}, nmem, mpre, mpre + nmem, sc);
+
+    // stage 1: slice-wise hash aggregation of quotient edges
+    const int cbits = std::max(1, bit_width_u64((uint64_t)(n2 > 1 ? n2 - 1 : 1)));
+    const int64_t total = g.nnz;  // every entry belongs to some member row
+    unsigned long long *pk = sc.get<unsigned long long>(total);
+    int32_t *pw = sc.get<int32_t>(total);
+    unsigned long long *d_P = sc.zeros<unsigned long long>(1);
+    if (total > 0) {
+        CK(cudaFuncSetAttribute(k_aggregate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(AggSm)));
+        int occ = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aggregate, kCThreads, sizeof(AggSm)));
+        k_aggregate<<<sms * std::max(1, occ), kCThreads, sizeof(AggSm), s>>>(
+            g, members, nmem, mpre, total, f2c, cbits, pk, pw, d_P);
+        LAUNCHED();
+    }
+    unsigned long long P = 0;
+    CK(cudaMemcpyAsync(&P, d_P, sizeof(P), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+
+    // stage 2: sort by (C(u), C(v)) and reduce equal keys
+    radix_sort_pairs((uint64_t *)pk, pw, (int64_t)P, 2 * cbits, sc);
+    int64_t *pos = sc.get<int64_t>((int64_t)P + 1);
+    exclusive_scan(FlagNew{pk}, (int64_t)P, pos, pos + P, sc);
+    int64_t m2 = 0;
+    CK(cudaMemcpyAsync(&m2, pos + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int32_t *adjncy = (int32_t *)out_alloc(m2 * sizeof(int32_t));
+    int32_t *adjwgt = (int32_t *)out_alloc(m2 * sizeof(int32_t));
+    CK(cudaMemsetAsync(adjwgt, 0, (m2 ? m2 : 1) * sizeof(int32_t), s));
+    int32_t *cdeg = sc.zeros<int32_t>(n2);
+    if (P > 0) {
+        k_reduce_by_key<<<grid, 256, 0, s>>>(pk, pw, (int64_t)P, pos, cbits, adjncy, adjwgt, cdeg);
+        LAUNCHED();
+    }
+    int64_t *cpre = sc.get<int64_t>(n2);
+    exclusive_scan(ArrayI32to64{cdeg}, n2, cpre, nullptr, sc);
+    int64_t *xadj = (int64_t *)out_alloc((n2 + 1) * sizeof(int64_t));
+    k_finish_xadj<<<grid, 256, 0, s>>>(cpre, n2, m2, xadj);
+    LAUNCHED();
+    out->n = n2;
+    out->nnz = m2;
+    out->xadj = xadj;
+    out->adjncy = adjncy;
+    out->adjwgt = adjwgt;
+    out->vwgt = cvwgt;
+}
+
+// ---------------------------------------------------------------- projection
+
+__global__ void k_project(int64_t n, const int32_t *f2c, const int32_t *cp, int32_t *fp) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        fp[v] = cp[f2c[v]];
+}
+
+void project_impl(int64_t n, const int32_t *f2c, const int32_t *cp, int32_t *fp, cudaStream_t s) {
+    if (n <= 0) return;
+    int grid = (int)std::min<int64_t>(ceil_div<int64_t>(n, 256), dev_info().sms * 8);
+    k_project<<<grid, 256, 0, s>>>(n, f2c, cp, fp);
+    LAUNCHED();
+}
+
+// ---------------------------------------------------------------- cut / balance
+
+// Each thread scans a run of kCutRun consecutive entries; the row of the
+// first entry comes from a binary search over xadj.
+constexpr int kCutRun = 16;
+
+__global__ void k_cut(DGraph g, const int32_t *part, int64_t n_group, int64_t groups,
+                      unsigned long long *cut) {
+    const int64_t runs = ceil_div<int64_t>(g.nnz, kCutRun);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < runs;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = r * kCutRun;
+        const int64_t e1 = min64(g.nnz, e + kCutRun);
+        int64_t v = upper_bound_i64(g.xadj, 0, g.n + 1, e) - 1;
+        int64_t vend = g.xadj[v + 1];
+        int32_t pv = part[v];
+        int64_t grp = groups > 1 ? v / n_group : 0;
+        int64_t acc = 0;
+        for (; e < e1; e++) {
+            while (e >= vend) {
+                v++;
+                vend = g.xadj[v + 1];
+                pv = part[v];
+                int64_t ng = groups > 1 ? v / n_group : 0;
+                if (ng != grp) {
+                    if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
+                    acc = 0;
+                    grp = ng;
+                }
+            }
+            if (part[g.adjncy[e]] != pv) acc += g.adjwgt[e];
+        }
+        if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
+    }
+}
+
+__global__ void k_halve(unsigned long long *cut, int64_t groups) {
+    for (int64_t t = threadIdx.x; t < groups; t += blockDim.x) cut[t] /= 2;
+}
+
+__global__ void k_bw(DGraph g, const int32_t *part, int64_t nblocks, unsigned long long *bw) {
+    extern __shared__ unsigned long long lbw[];
+    const bool local = nblocks <= 2048;
+    if (local)
+        for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) lbw[b] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (local) atomicAdd(&lbw[part[v]], (unsigned long long)g.vwgt[v]);
+        else atomicAdd(&bw[part[v]], (unsigned long long)g.vwgt[v]);
+    }
+    __syncthreads();
+    if (local)
+        for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x)
+            if (lbw[b]) atomicAdd(&bw[b], lbw[b]);
+}
+
+void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t groups,
+              int64_t n_group, int64_t *d_cut, int64_t *d_bw, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    const int grid = dev_info().sms * 8;
+    CK(cudaMemsetAsync(d_cut, 0, groups * sizeof(int64_t), s));
+    if (d_bw) CK(cudaMemsetAsync(d_bw, 0, nblocks * sizeof(int64_t), s));
+    if (g.nnz > 0) {
+        k_cut<<<grid, 256, 0, s>>>(g, part, n_group, groups, (unsigned long long *)d_cut);
+        LAUNCHED();
+        k_halve<<<1, 256, 0, s>>>((unsigned long long *)d_cut, groups);
+        LAUNCHED();
+    }
+    if (d_bw && g.n > 0) {
+        size_t shm = nblocks <= 2048 ? nblocks * sizeof(unsigned long long) : 0;
+        k_bw<<<grid, 256, shm, s>>>(g, part, nblocks, (unsigned long long *)d_bw);
+        LAUNCHED();
+    }
+}
+
+}  // namespace sclap

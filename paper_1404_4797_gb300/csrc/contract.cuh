@@ -1,0 +1,30 @@
+// contract.cuh -- cluster contraction, projection and cut on the GPU.
+#pragma once
+
+#include "common.cuh"
+
+namespace sclap {
+
+struct CoarseGraph {
+    int64_t n = 0, nnz = 0;
+    int64_t *xadj = nullptr;
+    int32_t *adjncy = nullptr, *adjwgt = nullptr, *vwgt = nullptr;
+};
+
+// Contracts the clustering `lab` of g (Sec. III, Sec. IV.C).  Output arrays
+// come from out_sc when given, else from cudaMalloc (caller frees).  f2c is
+// written for every fine node.
+void contract_impl(const DGraph &g, const int32_t *lab, int32_t *f2c, CoarseGraph *out,
+                   Scratch *out_sc, Scratch &tmp);
+
+void project_impl(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_part,
+                  int32_t *fine_part, cudaStream_t s);
+
+// cut and block weights.  groups > 1: nodes [t*n_group, (t+1)*n_group) form
+// group t (disjoint copies); cut_out[t] and block weights are per group with
+// k blocks each (block ids t*k .. t*k+k-1).  Results are device arrays.
+void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t groups,
+              int64_t n_group, int64_t *d_cut /* [groups] */, int64_t *d_bw /* [nblocks] */,
+              Scratch &sc);
+
+}  // namespace sclap

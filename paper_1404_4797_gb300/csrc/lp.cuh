@@ -1,0 +1,27 @@
+// lp.cuh -- size-constrained label propagation on the GPU (both forms).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace sclap {
+
+struct LPConfig {
+    DGraph g;
+    int32_t *lab;          // device labels (cluster ids or blocks), updated in place
+    int64_t nW;            // number of labels: n (clustering) or nblocks (refinement)
+    int64_t B;             // U or L_max
+    bool refine;           // refinement form (overloaded-block rule) vs clustering
+    const int32_t *cp;     // V-cycle constraint partition (clustering only) or null
+    uint64_t seed;
+    int32_t rounds, S;
+    int64_t max_deg;       // maximum degree of g (sizes the hub tables)
+};
+
+// Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)
+// receives the number of moves of every executed round.  W0 (optional,
+// device, nW entries) receives the final label weights.
+int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves, int64_t *W_out);
+
+}  // namespace sclap

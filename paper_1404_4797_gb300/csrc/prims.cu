@@ -1,0 +1,261 @@
+// prims.cu -- scratch pool, launch accounting, radix sort, graph reductions.
+#include <atomic>
+#include <mutex>
+
+#include "prims.cuh"
+
+namespace sclap {
+
+// ---------------------------------------------------------------- accounting
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static ProfState g_prof;
+ProfState &prof() {
+    g_prof.kernel_launches = g_launches.load();
+    return g_prof;
+}
+
+void prof_begin(cudaStream_t s, cudaEvent_t *b, cudaEvent_t *e) {
+    *b = *e = nullptr;
+    if (!g_prof.on) return;
+    CK(cudaEventCreate(b));
+    CK(cudaEventCreate(e));
+    CK(cudaEventRecord(*b, s));
+}
+
+void prof_end(cudaStream_t s, cudaEvent_t b, cudaEvent_t e) {
+    if (!b) return;
+    CK(cudaEventRecord(e, s));
+    g_prof.pending.emplace_back(b, e);
+    g_prof.propose_launches++;
+}
+
+// ---------------------------------------------------------------- device info / pool
+
+static std::mutex g_mu;
+static DevInfo g_dev[64];
+static bool g_dev_ok[64];
+static cudaMemPool_t g_pool[64];
+
+const DevInfo &dev_info() {
+    int d = 0;
+    CK(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_dev_ok[d]) {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d));
+        g_dev[d] = DevInfo{d, sms};
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = d;
+        CK(cudaMemPoolCreate(&g_pool[d], &props));
+        uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
+        CK(cudaMemPoolSetAttribute(g_pool[d], cudaMemPoolAttrReleaseThreshold, &thr));
+        g_dev_ok[d] = true;
+    }
+    return g_dev[d];
+}
+
+void *scratch_alloc(size_t bytes, cudaStream_t s) {
+    const DevInfo &di = dev_info();
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, g_pool[di.device], s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(SCLAP_ENOMEM, "scratch allocation");
+    }
+    CK(e);
+    return p;
+}
+
+void scratch_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------- radix sort
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) {
+    return (uint32_t)(k >> shift) & (kRadix - 1);
+}
+
+// Per-tile digit histogram, written digit-major: hist[d * tiles + tile].
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_hist(const uint64_t *keys, int64_t n, int shift, int64_t tiles, int64_t *hist) {
+    __shared__ int cnt[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += kSortThreads) cnt[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int j = 0; j < kSortRounds; j++) {
+        int64_t i = base + (int64_t)j * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[digit_of(keys[i], shift)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
+        hist[(int64_t)d * tiles + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter.  Warp w owns tile items [w*32*R, (w+1)*32*R) and walks them
+// in order (round-major, lane-minor), so ranks respect the input order.
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_scatter(const uint64_t *keys, const int32_t *vals, uint64_t *okeys, int32_t *ovals,
+                   int64_t n, int shift, int64_t tiles, const int64_t *offs) {
+    __shared__ int wc[kSortWarps][kRadix];
+    __shared__ int64_t goff[kRadix];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wc[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
+        goff[d] = offs[(int64_t)d * tiles + blockIdx.x];
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortRounds;
+    const unsigned lt = (1u << lane) - 1;
+    uint64_t k[kSortRounds];
+    int32_t v[kSortRounds];
+    int rk[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; r++) {
+        int64_t i = wbase + r * 32 + lane;
+        bool ok = i < n;
+        k[r] = ok ? keys[i] : 0;
+        v[r] = ok ? vals[i] : 0;
+        uint32_t d = ok ? digit_of(k[r], shift) : kRadix;  // kRadix: padding
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int base = (d < kRadix) ? wc[warp][d] : 0;
+        __syncwarp();
+        if (d < kRadix && (peers & lt) == 0) wc[warp][d] = base + __popc(peers);
+        __syncwarp();
+        rk[r] = base + __popc(peers & lt);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        int run = 0;
+        for (int w = 0; w < kSortWarps; w++) {
+            int t = wc[w][d];
+            wc[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; r++) {
+        int64_t i = wbase + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = digit_of(k[r], shift);
+            int64_t dst = goff[d] + wc[warp][d] + rk[r];
+            okeys[dst] = k[r];
+            ovals[dst] = v[r];
+        }
+    }
+}
+
+void radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, Scratch &sc) {
+    if (n <= 1 || nbits <= 0) return;
+    cudaStream_t s = sc.stream();
+    int64_t tiles = ceil_div<int64_t>(n, kSortTile);
+    uint64_t *k2 = sc.get<uint64_t>(n);
+    int32_t *v2 = sc.get<int32_t>(n);
+    int64_t *hist = sc.get<int64_t>(tiles * kRadix);
+    int64_t *offs = sc.get<int64_t>(tiles * kRadix);
+    uint64_t *ka = keys, *kb = k2;
+    int32_t *va = vals, *vb = v2;
+    int passes = 0;
+    for (int shift = 0; shift < nbits; shift += 8, passes++) {
+        k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, n, shift, tiles, hist);
+        LAUNCHED();
+        exclusive_scan(ArrayI64{hist}, tiles * kRadix, offs, nullptr, sc);
+        k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, tiles,
+                                                                offs);
+        LAUNCHED();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        CK(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(vals, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+// ---------------------------------------------------------------- graph totals
+
+__global__ void k_totals(DGraph g, unsigned long long *acc /* [5] */) {
+    int64_t cV = 0, maxc = 0, sw = 0, maxwd = 0, maxd = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = g.vwgt[v];
+        cV += c;
+        maxc = max(maxc, c);
+        int64_t b = g.xadj[v], e = g.xadj[v + 1];
+        maxd = max(maxd, e - b);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nnz;
+         i += (int64_t)gridDim.x * blockDim.x)
+        sw += g.adjwgt[i];
+    // weighted degree: one warp per node would be exact but slow; bound it by
+    // a per-row sum computed with a thread per node (only rows <= 4096 long
+    // are summed here; longer rows are summed by k_row_wsum below).
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = g.xadj[v], e = g.xadj[v + 1];
+        if (e - b > 4096) continue;
+        int64_t s = 0;
+        for (int64_t i = b; i < e; i++) s += g.adjwgt[i];
+        maxwd = max(maxwd, s);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        cV += __shfl_down_sync(0xffffffffu, cV, d);
+        sw += __shfl_down_sync(0xffffffffu, sw, d);
+        maxc = max(maxc, __shfl_down_sync(0xffffffffu, maxc, d));
+        maxwd = max(maxwd, __shfl_down_sync(0xffffffffu, maxwd, d));
+        maxd = max(maxd, __shfl_down_sync(0xffffffffu, maxd, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], (unsigned long long)cV);
+        atomicMax(&acc[1], (unsigned long long)maxc);
+        atomicAdd(&acc[2], (unsigned long long)sw);
+        atomicMax(&acc[3], (unsigned long long)maxwd);
+        atomicMax(&acc[4], (unsigned long long)maxd);
+    }
+}
+
+// Weighted degree of long rows: one block per such row.
+__global__ void k_row_wsum(DGraph g, unsigned long long *acc) {
+    for (int64_t v = blockIdx.x; v < g.n; v += gridDim.x) {
+        int64_t b = g.xadj[v], e = g.xadj[v + 1];
+        if (e - b <= 4096) continue;
+        int64_t s = 0;
+        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) s += g.adjwgt[i];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+        __shared__ int64_t part[32];
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+            atomicMax(&acc[3], (unsigned long long)t);
+        }
+        __syncthreads();
+    }
+}
+
+GraphTotals graph_totals(const DGraph &g, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    unsigned long long *acc = sc.zeros<unsigned long long>(5);
+    int sms = dev_info().sms;
+    if (g.n > 0) {
+        k_totals<<<sms * 4, 256, 0, s>>>(g, acc);
+        LAUNCHED();
+        k_row_wsum<<<sms * 2, 256, 0, s>>>(g, acc);
+        LAUNCHED();
+    }
+    unsigned long long h[5];
+    CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GraphTotals{(int64_t)h[0], (int64_t)h[1], (int64_t)h[2], (int64_t)h[3], (int64_t)h[4]};
+}
+
+}  // namespace sclap

@@ -1,0 +1,148 @@
+// prims.cuh -- device-wide building blocks written for this library:
+// block/warp scans, an exclusive scan over functor-generated int64 values,
+// a stable LSD radix sort of (uint64 key, int32 value) pairs, and reductions.
+#pragma once
+
+#include "common.cuh"
+
+namespace sclap {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// ---------------------------------------------------------------- block scan
+
+// Exclusive scan of one value per thread over the block; returns the thread's
+// exclusive prefix and writes the block total to *total (all threads).
+template <int NT, typename T>
+__device__ __forceinline__ T block_exclusive_scan(T x, T *total, T *smem /* >= NT/32 + 1 */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = (lane < NT / 32) ? smem[lane] : T(0);
+        T wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < NT / 32) smem[lane] = wi - w;  // exclusive warp offsets
+        if (lane == NT / 32 - 1) smem[NT / 32] = wi;
+    }
+    __syncthreads();
+    T res = smem[warp] + inc - x;
+    *total = smem[NT / 32];
+    __syncthreads();
+    return res;
+}
+
+// ---------------------------------------------------------------- device-wide exclusive scan
+
+template <typename F>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, int64_t n, int64_t *sums) {
+    __shared__ int64_t sm[kScanThreads / 32 + 1];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        int64_t i = base + (int64_t)j * kScanThreads + threadIdx.x;
+        if (i < n) acc += (int64_t)f(i);
+    }
+    int64_t tot;
+    block_exclusive_scan<kScanThreads>(acc, &tot, sm);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Blocked layout: thread t owns items [t*kScanItems, (t+1)*kScanItems) of the tile.
+template <typename F>
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_apply(F f, int64_t n, const int64_t *offs, int64_t *out, int64_t *total) {
+    __shared__ int64_t sm[kScanThreads / 32 + 1];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        int64_t i = base + j;
+        v[j] = i < n ? (int64_t)f(i) : 0;
+        acc += v[j];
+    }
+    int64_t tot;
+    int64_t pre = block_exclusive_scan<kScanThreads>(acc, &tot, sm) + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        int64_t i = base + j;
+        if (i < n) out[i] = pre;
+        pre += v[j];
+    }
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) *total = pre;
+}
+
+struct ArrayI64 {
+    const int64_t *p;
+    __device__ int64_t operator()(int64_t i) const { return p[i]; }
+};
+
+// out[i] = sum_{j<i} f(j) for i in [0, n); *d_total (device, optional) = sum of all.
+template <typename F>
+void exclusive_scan(F f, int64_t n, int64_t *out, int64_t *d_total, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    if (n <= 0) {
+        if (d_total) CK(cudaMemsetAsync(d_total, 0, sizeof(int64_t), s));
+        return;
+    }
+    int64_t tiles = ceil_div<int64_t>(n, kScanTile);
+    if (tiles == 1) {
+        k_scan_apply<<<1, kScanThreads, 0, s>>>(f, n, nullptr, out, d_total);
+        LAUNCHED();
+        return;
+    }
+    int64_t *sums = sc.get<int64_t>(tiles);
+    int64_t *offs = sc.get<int64_t>(tiles);
+    k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, s>>>(f, n, sums);
+    LAUNCHED();
+    exclusive_scan(ArrayI64{sums}, tiles, offs, nullptr, sc);
+    k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, s>>>(f, n, offs, out, d_total);
+    LAUNCHED();
+}
+
+// ---------------------------------------------------------------- radix sort
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 16;                       // items per lane
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
+constexpr int kRadix = 256;
+
+// Sorts (keys, vals) stably by key bits [0, nbits).  keys/vals are sorted in
+// place (alt buffers are scratch).
+void radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, Scratch &sc);
+
+// Number of significant bits of x (0 for x == 0).
+inline int bit_width_u64(uint64_t x) {
+    int b = 0;
+    while (x) { b++; x >>= 1; }
+    return b;
+}
+
+// ---------------------------------------------------------------- reductions
+
+// Device-side sums / maxima used for validation and bounds (results to host).
+struct GraphTotals {
+    int64_t cV;          // sum of c
+    int64_t maxc;        // max c
+    int64_t sum_w;       // sum of omega over all directed entries
+    int64_t max_wdeg;    // max weighted degree
+    int64_t max_deg;     // max degree
+};
+GraphTotals graph_totals(const DGraph &g, Scratch &sc);
+
+}  // namespace sclap

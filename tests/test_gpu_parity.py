@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element, on seeded inputs.  Integer work: bit-exact equality is the bar."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1404_4797_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+S = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global S
+    import paper_1404_4797_gb300 as mod
+    mod.lib()
+    S = mod
+    yield
+
+
+def dev(g):
+    return I.to_device(g, "cuda")
+
+
+def star(n_leaves, w=1):
+    u = torch.zeros(n_leaves, dtype=torch.int64)
+    v = torch.arange(1, n_leaves + 1, dtype=torch.int64)
+    return I.csr_from_edges(n_leaves + 1, u, v, torch.full((n_leaves,), w, dtype=torch.int64))
+
+
+GRAPHS = {
+    "chunglu2k": lambda: I.chung_lu(2048, 2.1, 8.0, seed=3),
+    "weighted": lambda: I.random_graph(3000, 12000, seed=5, max_w=20, max_c=9),
+    "rmat14": lambda: I.rmat(14, 16, seed=2),
+    "star5k": lambda: star(5000),                # hub beyond shared memory
+    "sparse": lambda: I.random_graph(4000, 1500, seed=9),  # many isolated nodes
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("Sr", [1, 4])
+def test_cluster_matches_oracle(name, Sr):
+    g = GRAPHS[name]()
+    gn = I.to_numpy(g)
+    cV = int(gn["vwgt"].sum())
+    U = max(int(gn["vwgt"].max()), cV // 40)
+    want, rd_w = oracle.cluster(gn, U, 5, Sr, 11)
+    got, rd_g = S.sclap_cluster(dev(g), U, 5, Sr, 11)
+    assert rd_g == rd_w
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_cluster_unit_U_and_constraint():
+    g = GRAPHS["weighted"]()
+    gn = I.to_numpy(g)
+    got, rd = S.sclap_cluster(dev(I.random_graph(500, 2000, seed=1)), 1, 3, 4, 1)
+    assert rd == 1 and np.array_equal(got.cpu().numpy(), np.arange(500))
+    cp = (np.arange(gn["vwgt"].size) * 7919 % 3).astype(np.int32)
+    U = int(gn["vwgt"].sum()) // 30
+    want, _ = oracle.cluster(gn, U, 4, 4, 5, constraint_part=cp)
+    got, _ = S.sclap_cluster(dev(g), U, 4, 4, 5, torch.from_numpy(cp).cuda())
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("name", ["chunglu2k", "weighted", "rmat14", "star5k"])
+@pytest.mark.parametrize("k", [2, 16, 64, 100])
+def test_refine_matches_oracle(name, k):
+    g = GRAPHS[name]()
+    gn = I.to_numpy(g)
+    n = gn["vwgt"].size
+    p0 = (np.arange(n, dtype=np.int64) * 2654435761 % k).astype(np.int32)
+    want, cut_w, bw_w, rd_w = oracle.refine(gn, k, 0.03, 6, 4, 21, p0)
+    got, cut_g, bw_g, rd_g = S.sclap_refine(dev(g), k, 0.03, 6, 4, 21, torch.from_numpy(p0).cuda())
+    assert rd_g == rd_w
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert cut_g == cut_w and np.array_equal(bw_g.numpy(), bw_w)
+
+
+def test_refine_overloaded_start_matches_oracle():
+    g = GRAPHS["weighted"]()
+    gn = I.to_numpy(g)
+    n = gn["vwgt"].size
+    p0 = np.zeros(n, np.int32)
+    p0[: n // 5] = 1
+    p0[n // 5: n // 4] = 2
+    for k in (4, 80):
+        want, cut_w, bw_w, rd_w = oracle.refine(gn, k, 0.03, 8, 4, 3, p0)
+        got, cut_g, bw_g, rd_g = S.sclap_refine(dev(g), k, 0.03, 8, 4, 3,
+                                                torch.from_numpy(p0).cuda())
+        assert np.array_equal(got.cpu().numpy(), want), k
+        assert cut_g == cut_w and rd_g == rd_w
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_contract_matches_oracle(name):
+    g = GRAPHS[name]()
+    gn = I.to_numpy(g)
+    cV = int(gn["vwgt"].sum())
+    lab, _ = oracle.cluster(gn, max(int(gn["vwgt"].max()), cV // 50), 3, 4, 2)
+    want, f2c_w = oracle.contract(gn, lab)
+    got, f2c_g = S.contract_graph(dev(g), torch.from_numpy(lab).cuda())
+    assert np.array_equal(f2c_g.cpu().numpy(), f2c_w)
+    for key in ("xadj", "adjncy", "adjwgt", "vwgt"):
+        assert np.array_equal(got[key].cpu().numpy(), want[key]), key
+
+
+def test_contract_identity_and_single_cluster():
+    g = GRAPHS["weighted"]()
+    gn = I.to_numpy(g)
+    n = gn["vwgt"].size
+    for lab in (np.arange(n, dtype=np.int32), np.full(n, 17, np.int32)):
+        want, f2c_w = oracle.contract(gn, lab)
+        got, f2c_g = S.contract_graph(dev(g), torch.from_numpy(lab).cuda())
+        assert np.array_equal(f2c_g.cpu().numpy(), f2c_w)
+        for key in ("xadj", "adjncy", "adjwgt", "vwgt"):
+            assert np.array_equal(got[key].cpu().numpy(), want[key]), key
+
+
+def test_project_matches_oracle():
+    f2c = (np.arange(10007, dtype=np.int64) * 31 % 977).astype(np.int32)
+    cp = (np.arange(977) % 7).astype(np.int32)
+    got = S.project_partition(torch.from_numpy(f2c).cuda(), torch.from_numpy(cp).cuda())
+    assert np.array_equal(got.cpu().numpy(), oracle.project(f2c, cp))
+
+
+@pytest.mark.parametrize("name", ["chunglu2k", "weighted"])
+def test_initial_partition_matches_oracle(name):
+    g = GRAPHS[name]()
+    gn = I.to_numpy(g)
+    k = 8
+    B = oracle.lmax(int(gn["vwgt"].sum()), k, 0.03)
+    want, cw, mw, bw = oracle.initial_partition(gn, k, B, 8, 6, 4, 99)
+    got, cg, mg, bg = S.sclap_initial_partition(dev(g), k, B, 8, 6, 4, 99)
+    assert bg == bw
+    assert np.array_equal(cg.numpy(), cw) and np.array_equal(mg.numpy(), mw)
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_multilevel_config1_matches_oracle():
+    # Chung-Lu n = 16,384, ~131k edges, exponent 2.1, mean degree 16; k = 4,
+    # eps = 0.03, U = max(max c, c(V)/(10k)), 10 rounds per level, n_stop 2000.
+    g = I.chung_lu(16384, 2.1, 16.0, seed=1)
+    params = oracle.default_params(4, 0.03, seed=1, cluster_rounds=10, refine_rounds=10,
+                                   n_stop=2000)
+    want, ws = oracle.multilevel(I.to_numpy(g), params)
+    got, gs = S.partition_multilevel(dev(g), params)
+    assert gs == ws
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert gs["maxbw"] <= gs["lmax"]
+
+
+def test_multilevel_host_buffers_match_device():
+    g = I.chung_lu(8192, 2.1, 12.0, seed=4)
+    params = oracle.default_params(8, 0.03, seed=4, n_stop=500)
+    gh = {k: v.pin_memory() for k, v in g.items()}
+    out_h = torch.empty(8192, dtype=torch.int32).pin_memory()
+    got_h, sh = S.partition_multilevel(gh, params, part_out=out_h)
+    got_d, sd = S.partition_multilevel(dev(g), params)
+    want, ws = oracle.multilevel(I.to_numpy(g), params)
+    assert sh == sd == ws
+    assert np.array_equal(got_h.numpy(), want) and np.array_equal(got_d.cpu().numpy(), want)
+
+
+def test_multilevel_weighted_matches_oracle():
+    g = I.random_graph(20000, 90000, seed=12, max_w=50, max_c=20)
+    params = oracle.default_params(16, 0.05, seed=3, n_stop=1000)
+    want, ws = oracle.multilevel(I.to_numpy(g), params)
+    got, gs = S.partition_multilevel(dev(g), params)
+    assert gs == ws
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_repeatable_runs_are_identical():
+    g = dev(I.rmat(15, 16, seed=8))
+    params = oracle.default_params(16, 0.03, seed=5, n_stop=2000)
+    a, sa = S.partition_multilevel(g, params)
+    b, sb = S.partition_multilevel(g, params)
+    assert sa == sb and torch.equal(a, b)
+
+
+def test_edge_cases():
+    empty = {"xadj": torch.zeros(1, dtype=torch.int64), "adjncy": torch.zeros(0, dtype=torch.int32),
+             "adjwgt": torch.zeros(0, dtype=torch.int32), "vwgt": torch.zeros(0, dtype=torch.int32)}
+    lab, rd = S.sclap_cluster(dev(empty), 1, 3, 4, 1)
+    assert lab.numel() == 0 and rd == 0
+    # isolated nodes only
+    iso = {"xadj": torch.zeros(11, dtype=torch.int64), "adjncy": torch.zeros(0, dtype=torch.int32),
+           "adjwgt": torch.zeros(0, dtype=torch.int32), "vwgt": torch.ones(10, dtype=torch.int32)}
+    lab, rd = S.sclap_cluster(dev(iso), 3, 3, 4, 1)
+    assert torch.equal(lab.cpu(), torch.arange(10, dtype=torch.int32)) and rd == 1
+    cg, f2c = S.contract_graph(dev(iso), lab)
+    assert cg["xadj"].numel() == 11 and cg["adjncy"].numel() == 0
+    # k = 1 refinement never moves
+    g = dev(GRAPHS["weighted"]())
+    p, cut, bw, rd = S.sclap_refine(g, 1, 0.03, 4, 4, 1, torch.zeros(3000, dtype=torch.int32,
+                                                                      device="cuda"))
+    assert cut == 0 and rd == 1 and int(p.abs().sum()) == 0
+
+
+def test_errors_are_reported():
+    g = dev(GRAPHS["weighted"]())
+    with pytest.raises(S.SclapError) as e:
+        S.sclap_cluster(g, 1, 3, 4, 1)             # U < max c(v)
+    assert e.value.code == S.EINVAL
+    bad = {k: v.clone() for k, v in g.items()}
+    bad["adjwgt"][0] += 1                          # asymmetric
+    with pytest.raises(S.SclapError) as e:
+        S.sclap_cluster(bad, 10**6, 3, 4, 1)
+    assert e.value.code == S.EGRAPH
+    p = torch.full((3000,), 5, dtype=torch.int32, device="cuda")
+    with pytest.raises(S.SclapError) as e:
+        S.sclap_refine(g, 4, 0.03, 3, 4, 1, p)     # block id out of range
+    assert e.value.code == S.EINVAL
+    big = {k: v.clone() for k, v in g.items()}
+    big["vwgt"][:] = 2**30                          # c(V) overflows int32
+    with pytest.raises(S.SclapError) as e:
+        S.sclap_cluster(big, 2**31 - 1, 3, 4, 1)
+    assert e.value.code == S.EOVERFLOW
