@@ -1,0 +1,317 @@
+"""Benchmark: the multilevel SCLaP partitioner on the R-MAT scale-22 workload.
+
+One step = one full pass of the hot path: clustering rounds and contraction on
+every coarsening level, the initial partition of the coarsest graph, projection
+and refinement rounds on every level back to the input graph.
+
+Workload: R-MAT scale 22 (a, b, c = 0.57, 0.19, 0.19), edge factor 16,
+symmetrised, duplicates and self-loops dropped (~4.19M nodes, ~64M undirected
+edges), unit int32 weights, k = 16, eps = 0.03, l = 3 clustering and r = 6
+refinement rounds per level (the paper's `fast` round counts), S = 4
+sub-rounds, coarsening to < 2000 nodes, 8 initial individuals.
+
+Metric: G edges/s = m_undirected / partition time (the paper reports partition
+time; edges per second is its time-per-edge convention inverted).  The JSON
+line also reports the neighbour-aggregation kernel against the HBM roofline,
+the end-to-end number through the C ABI with host buffers, and the CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica of the step
+(the single-GPU path has no exchange step), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("SCLaP edges/sec (GTEPS) and % HBM roofline; multilevel partition time at fixed "
+          "cut/balance")
+WORKLOAD = dict(workload="R-MAT scale 22, edge factor 16, a=0.57 b=0.19 c=0.19, unit weights, "
+                         "k=16, eps=0.03, l=3, r=6, S=4, n_stop=2000, 8 initial individuals",
+                scale=22, edge_factor=16, k=16, eps=0.03, cluster_rounds=3, refine_rounds=6,
+                subrounds=4, n_stop=2000, init_seeds=8, seed=1)
+# bounded sample for the CPU oracle: same generator and parameters, 1/16 of the nodes
+SAMPLE_SCALE = 18
+
+
+def params_for(cfg, seed=None):
+    return dict(k=cfg["k"], eps=cfg["eps"], U=0, cluster_rounds=cfg["cluster_rounds"],
+                refine_rounds=cfg["refine_rounds"], subrounds=cfg["subrounds"],
+                n_stop=cfg["n_stop"], max_levels=32, init_seeds=cfg["init_seeds"],
+                init_rounds=cfg["refine_rounds"], seed=cfg["seed"] if seed is None else seed)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_traffic():
+    """Per-launch DRAM bytes of the propose kernel from the committed ncu summary
+    (profiles/propose_traffic.json), if one matches the current kernel build."""
+    p = os.path.join(ROOT, "profiles", "propose_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d
+    except (OSError, ValueError):
+        return None
+
+
+def run_reference(args, cfg):
+    """The oracle (plain single-threaded C) on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1404_4797_gb300 import inputs as I
+    g = I.to_numpy(I.rmat(SAMPLE_SCALE, cfg["edge_factor"], seed=cfg["seed"]))
+    m = int(g["adjncy"].size) // 2
+    params = params_for(cfg)
+    for _ in range(args.warmup):
+        oracle.multilevel(g, params)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        part, st = oracle.multilevel(g, params)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = m / dt / 1e9
+    sample = (f"R-MAT scale {SAMPLE_SCALE} (same generator and parameters as the workload, "
+              f"n={len(g['vwgt'])}, m={m}), full multilevel partition per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {k: cfg[k] for k in cfg},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "cut": st["cut"], "maxbw": st["maxbw"], "lmax": st["lmax"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(cfg, budget_s=20.0):
+    """Times the oracle's multilevel partition on the bounded sample (rank 0, N=1)."""
+    import oracle
+    from paper_1404_4797_gb300 import inputs as I
+    g = I.to_numpy(I.rmat(SAMPLE_SCALE, cfg["edge_factor"], seed=cfg["seed"]))
+    m = int(g["adjncy"].size) // 2
+    params = params_for(cfg)
+    reps, total = 0, 0.0
+    while total < budget_s and reps < 5:
+        t0 = time.perf_counter()
+        oracle.multilevel(g, params)
+        total += time.perf_counter() - t0
+        reps += 1
+    dt = total / reps
+    return {"value": m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"R-MAT scale {SAMPLE_SCALE} (same generator/parameters, n={len(g['vwgt'])}, "
+                      f"m={m}); {reps} full multilevel partitions, single thread, "
+                      f"{dt:.2f} s each"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling)")
+    ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
+    args = ap.parse_args()
+    cfg = dict(WORKLOAD)
+    if args.scale:
+        cfg["scale"] = args.scale
+        cfg["workload"] = cfg["workload"].replace("scale 22", f"scale {args.scale}")
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import paper_1404_4797_gb300 as S
+    from paper_1404_4797_gb300 import inputs as I
+
+    S.lib()
+    g = I.rmat(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"], device=dev)
+    n = g["vwgt"].numel()
+    m = I.num_edges(g)
+    params = params_for(cfg)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    part = torch.empty(n, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        S.partition_multilevel(g, params, part_out=part)
+
+    # ---- device-resident timed region
+    S.prof_enable(True)
+    S.prof_reset()
+    launches0 = S.prof_read()["kernel_launches"]
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                          else local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, st = S.partition_multilevel(g, params, part_out=part)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = S.prof_read()
+    S.prof_enable(False)
+    launches = (prof["kernel_launches"] - launches0) // max(1, args.steps)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * m / (ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    gh = {k: v.cpu().pin_memory() for k, v in g.items()} if not args.no_e2e else g
+    ph = torch.empty(n, dtype=torch.int32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in gh.values())
+    d2h = ph.numel() * ph.element_size()
+    if not args.no_e2e:
+        S.partition_multilevel(gh, params, part_out=ph)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            _, st_e = S.partition_multilevel(gh, params, part_out=ph)
+        torch.cuda.synchronize(dev)
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        if ws > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": ws * m / (e2e_ms / 1e3) / 1e9, "unit": "GTEPS", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- roofline of the dominant kernel (neighbour aggregation / propose)
+    peak, peak_kind = measured_peaks()
+    per_launch_ms = prof["propose_ms"] / max(1, prof["propose_launches"])
+    per_launch_bytes = prof["propose_bytes"] / max(1, prof["propose_launches"])
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    tr = stored_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_propose (normal-degree nodes)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": tr.get("dram_bytes_per_launch") if tr else None,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "launches": prof["propose_launches"], "ms_per_launch": per_launch_ms,
+                "share_of_step": prof["propose_ms"] / (ms * args.steps) if ms > 0 else None}
+
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {**cfg, "n": n, "m": m, "l2": "inputs larger than L2 (CSR %.2f GB)" %
+                       (h2d / 1e9), "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "cut": st["cut"], "maxbw": st["maxbw"], "lmax": st["lmax"], "levels": st["n"],
+            "sclap_entries_per_s": prof["entries_scanned"] / (prof["propose_ms"] / 1e3)
+            if prof["propose_ms"] > 0 else None}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

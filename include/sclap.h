@@ -118,6 +118,10 @@ typedef struct {
  *   constraint_part NULL, or device int32[n]: clusters stay inside the blocks
  *                   of this partition (iterated V-cycles, Sec. IV.D)
  *   labels_out      device int32[n]: cluster id (a node id) per node
+ * Nodes without neighbours never move; after the rounds they are packed in id
+ * order (per block of constraint_part) into clusters: with U' = U - cmax + 1
+ * (cmax: their largest weight) and P(v) the weight of the earlier ones, v
+ * joins group floor(P(v) / U') labelled by its smallest id (weight <= U).
  *   rounds_done     host, rounds executed (the last one may have 0 moves)
  * Needs c(V) <= INT32_MAX and sum(adjwgt) <= INT32_MAX (SCLAP_EOVERFLOW). */
 int sclap_cluster(const sclap_graph *g, int64_t U, int32_t rounds, int32_t subrounds,

@@ -37,6 +37,8 @@
  *      order is <= B - W(T) (weights at sub-round start).
  *  R5  admitted moves are applied together; a round ends early after the
  *      first round without moves.
+ *  R6  clustering only: nodes without neighbours are packed into clusters
+ *      of weight <= U after the rounds (see pack_isolated).
  * mix64 is the SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
  */
 #include "sclap_oracle.h"
@@ -301,6 +303,60 @@ static int64_t total_weight(int64_t n, const int32_t *vwgt, int32_t *maxc)
     return s;
 }
 
+typedef struct {
+    int64_t v;
+    int32_t block;
+} iso_item;
+
+static int cmp_iso(const void *a, const void *b)
+{
+    const iso_item *x = (const iso_item *)a, *y = (const iso_item *)b;
+    if (x->block != y->block) return x->block < y->block ? -1 : 1;
+    return x->v < y->v ? -1 : (x->v > y->v);
+}
+
+/* Reading R6 (the paper is silent on nodes without neighbours): label
+ * propagation never moves them, so each would stay a singleton cluster and
+ * coarsening would stall on graphs with many of them.  After the rounds the
+ * nodes without neighbours are packed in id order, separately per block of the
+ * constraint partition when one is given: with U' = U - cmax + 1 (cmax the
+ * largest weight among them) and P(v) the total weight of the earlier ones in
+ * the same block, v joins group floor(P(v) / U'); a group's label is its
+ * smallest node id.  A group weighs at most U' - 1 + cmax = U. */
+static int pack_isolated(int64_t n, const int64_t *xadj, const int32_t *vwgt, int64_t U,
+                         const int32_t *cp, int32_t *lab)
+{
+    int64_t ni = 0;
+    int32_t cmax = 0;
+    for (int64_t v = 0; v < n; v++)
+        if (xadj[v + 1] == xadj[v]) {
+            ni++;
+            if (vwgt[v] > cmax) cmax = vwgt[v];
+        }
+    if (ni == 0) return OR_OK;
+    iso_item *it = (iso_item *)malloc(sizeof(iso_item) * (size_t)ni);
+    if (!it) return OR_ENOMEM;
+    ni = 0;
+    for (int64_t v = 0; v < n; v++)
+        if (xadj[v + 1] == xadj[v]) {
+            it[ni].v = v;
+            it[ni].block = cp ? cp[v] : 0;
+            ni++;
+        }
+    qsort(it, (size_t)ni, sizeof(iso_item), cmp_iso);
+    int64_t Up = U - cmax + 1;
+    int64_t P = 0, group = -1, rep = 0;
+    for (int64_t i = 0; i < ni; i++) {
+        if (i == 0 || it[i].block != it[i - 1].block) { P = 0; group = -1; }
+        int64_t gi = P / Up;
+        if (gi != group) { group = gi; rep = it[i].v; }
+        lab[it[i].v] = (int32_t)rep;
+        P += vwgt[it[i].v];
+    }
+    free(it);
+    return OR_OK;
+}
+
 /* Sec. III.A, clustering form: every node starts in its own cluster (label
  * = node id); cluster weights stay <= U. */
 int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
@@ -319,7 +375,8 @@ int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, labels_out, W, n, U, 0,
                     constraint_part, seed, rounds, S, rounds_done, moves_per_round);
     free(W);
-    return rc;
+    if (rc) return rc;
+    return pack_isolated(n, xadj, vwgt, U, constraint_part, labels_out);
 }
 
 /* Sec. III.A, local-search form with an explicit bound B on every block. */

@@ -381,7 +381,7 @@ int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subr
                   uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
                   int32_t *rounds_done, void *stream) {
     return guarded([&] {
-        if (!gp || !labels_out) fail(SCLAP_EINVAL, "null");
+        if (!gp || (!labels_out && gp->n > 0)) fail(SCLAP_EINVAL, "null");
         if (rounds < 0 || subrounds < 1 || subrounds > 32) fail(SCLAP_EINVAL, "rounds");
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
@@ -404,6 +404,7 @@ int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subr
         int rd = 0;
         if (rounds > 0 && g.n > 0) rd = lp_run(cfg, sc, nullptr, nullptr);
         else identity_labels(g.n, labels_out, s);
+        pack_isolated(g, constraint_part, U, labels_out, sc);
         CK(cudaStreamSynchronize(s));
         if (rounds_done) *rounds_done = rd;
     });
@@ -415,7 +416,7 @@ int sclap_refine_bound(const sclap_graph *gp, int32_t nblocks, int64_t B, int32_
     cudaStream_t s = as_stream(stream);
     int32_t *backup = nullptr;
     int rc = guarded([&] {
-        if (!gp || !part_inout) fail(SCLAP_EINVAL, "null");
+        if (!gp || (!part_inout && gp->n > 0)) fail(SCLAP_EINVAL, "null");
         if (nblocks < 1 || rounds < 0 || subrounds < 1 || subrounds > 32) fail(SCLAP_EINVAL, "args");
         Scratch sc(s);
         DGraph g = view(gp);
@@ -473,7 +474,7 @@ int sclap_refine(const sclap_graph *gp, int32_t k, double eps, int32_t rounds, i
 int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cut_out,
               int64_t *block_w_out, void *stream) {
     return guarded([&] {
-        if (!gp || !part || k < 1) fail(SCLAP_EINVAL, "args");
+        if (!gp || (!part && gp->n > 0) || k < 1) fail(SCLAP_EINVAL, "args");
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
         DGraph g = view(gp);
@@ -492,7 +493,7 @@ int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cu
 int contract_graph(const sclap_graph *gp, const int32_t *labels, sclap_graph_owned *coarse_out,
                    int32_t *f2c_out, void *stream) {
     return guarded([&] {
-        if (!gp || !labels || !coarse_out || !f2c_out) fail(SCLAP_EINVAL, "null");
+        if (!gp || !coarse_out || (gp->n > 0 && (!labels || !f2c_out))) fail(SCLAP_EINVAL, "null");
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
         DGraph g = view(gp);
@@ -553,7 +554,8 @@ int sclap_initial_partition(const sclap_graph *gp, int32_t k, int64_t B, int32_t
                             int32_t subrounds, uint64_t seed, int32_t *part_out, int64_t *cuts_out,
                             int64_t *maxbw_out, int32_t *best_out, void *stream) {
     return guarded([&] {
-        if (!gp || !part_out || k < 1 || P < 1 || rounds < 0 || subrounds < 1 || subrounds > 32)
+        if (!gp || (!part_out && gp->n > 0) || k < 1 || P < 1 || rounds < 0 || subrounds < 1 ||
+            subrounds > 32)
             fail(SCLAP_EINVAL, "args");
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
@@ -571,7 +573,7 @@ int sclap_initial_partition(const sclap_graph *gp, int32_t k, int64_t B, int32_t
 int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_t *part_out,
                          sclap_ml_stats *st_out, void *stream) {
     return guarded([&] {
-        if (!gp || !p || !part_out) fail(SCLAP_EINVAL, "null");
+        if (!gp || !p || (!part_out && gp->n > 0)) fail(SCLAP_EINVAL, "null");
         if (p->k < 1 || !(p->eps >= 0) || p->cluster_rounds < 0 || p->refine_rounds < 0 ||
             p->subrounds < 1 || p->subrounds > 32 || p->init_seeds < 1 || p->init_rounds < 0)
             fail(SCLAP_EINVAL, "params");
@@ -627,6 +629,7 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
             int rd = 0;
             if (cfg.rounds > 0) rd = lp_run(cfg, tmp, nullptr, nullptr);
             else identity_labels(g.n, lab, s);
+            pack_isolated(g, nullptr, U, lab, tmp);
             st.cluster_rounds_done[L] = rd;
             int32_t *f2c = top.get<int32_t>(g.n);
             CoarseGraph cg;

@@ -837,6 +837,124 @@ __global__ void k_block_weights(DGraph g, const int32_t *lab, int64_t *W, int64_
             if (lw[i]) atomicAdd((unsigned long long *)&W[i], lw[i]);
 }
 
+// ---------------------------------------------------------------- isolated nodes
+
+// The paper is silent on nodes without neighbours: label propagation never
+// moves them, so they would stay singleton clusters and stall coarsening.
+// After the rounds they are packed in id order (per block of cp when given):
+// with U' = U - cmax + 1 (cmax: largest weight among them) and P(v) the weight
+// of the earlier ones in the same block, v joins group floor(P(v) / U'), whose
+// label is its smallest id; a group weighs at most U.
+
+struct IsoFlag {
+    const int64_t *xadj;
+    __device__ int64_t operator()(int64_t v) const { return xadj[v + 1] == xadj[v] ? 1 : 0; }
+};
+
+__global__ void k_iso_compact(DGraph g, const int64_t *pos, const int32_t *cp, int32_t *iso,
+                              uint64_t *key, unsigned long long *cmax) {
+    unsigned long long m = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (g.xadj[v + 1] != g.xadj[v]) continue;
+        int64_t i = pos[v];
+        iso[i] = (int32_t)v;
+        key[i] = cp ? (uint64_t)((uint32_t)cp[v] ^ 0x80000000u) : 0;
+        m = max(m, (unsigned long long)g.vwgt[v]);
+    }
+    if (m) atomicMax(cmax, m);
+}
+
+struct IsoWeight {
+    const int32_t *iso, *vwgt;
+    __device__ int64_t operator()(int64_t i) const { return vwgt[iso[i]]; }
+};
+
+struct SegStart {
+    const uint64_t *key;
+    __device__ int64_t operator()(int64_t i) const { return (i == 0 || key[i] != key[i - 1]) ? 1 : 0; }
+};
+
+__global__ void k_iso_segbase(int64_t ni, const uint64_t *key, const int64_t *P, const int64_t *sidx,
+                              int64_t *segP) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (i == 0 || key[i] != key[i - 1]) segP[sidx[i]] = P[i];
+}
+
+struct GroupStart {
+    const uint64_t *key;
+    const int64_t *P, *sidx, *segP;
+    int64_t Up;
+    __device__ int64_t group(int64_t i) const {
+        int64_t s = sidx[i] + ((i == 0 || key[i] != key[i - 1]) ? 1 : 0) - 1;
+        return (P[i] - segP[s]) / Up;
+    }
+    __device__ int64_t operator()(int64_t i) const {
+        if (i == 0 || key[i] != key[i - 1]) return 1;
+        return group(i) != group(i - 1) ? 1 : 0;
+    }
+};
+
+__global__ void k_iso_label(int64_t ni, const int32_t *iso, GroupStart gs, const int64_t *gidx,
+                            int32_t *rep, int32_t *lab, int pass) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t st = gs(i);
+        int64_t gi = gidx[i] + st - 1;
+        if (pass == 0) {
+            if (st) rep[gi] = iso[i];
+        } else {
+            lab[iso[i]] = rep[gi];
+        }
+    }
+}
+
+void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    if (g.n == 0) return;
+    const int grid = dev_info().sms * 4;
+    int64_t *pos = sc.get<int64_t>(g.n);
+    int64_t *d_ni = sc.get<int64_t>(1);
+    exclusive_scan(IsoFlag{g.xadj}, g.n, pos, d_ni, sc);
+    int64_t ni = 0;
+    CK(cudaMemcpyAsync(&ni, d_ni, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ni == 0) return;
+    int32_t *iso = sc.get<int32_t>(ni);
+    uint64_t *key = sc.get<uint64_t>(ni);
+    unsigned long long *d_cmax = sc.zeros<unsigned long long>(1);
+    k_iso_compact<<<grid, 256, 0, s>>>(g, pos, cp, iso, key, d_cmax);
+    LAUNCHED();
+    if (cp) radix_sort_pairs(key, iso, ni, 32, sc);  // stable: id order within a block
+    unsigned long long cmax = 0;
+    CK(cudaMemcpyAsync(&cmax, d_cmax, sizeof(cmax), cudaMemcpyDeviceToHost, s));
+    int64_t *P = sc.get<int64_t>(ni);
+    exclusive_scan(IsoWeight{iso, g.vwgt}, ni, P, nullptr, sc);
+    int64_t *sidx = sc.get<int64_t>(ni);
+    int64_t *d_ns = sc.get<int64_t>(1);
+    exclusive_scan(SegStart{key}, ni, sidx, d_ns, sc);
+    CK(cudaStreamSynchronize(s));
+    int64_t ns = 0;
+    CK(cudaMemcpyAsync(&ns, d_ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int64_t *segP = sc.get<int64_t>(ns);
+    k_iso_segbase<<<grid, 256, 0, s>>>(ni, key, P, sidx, segP);
+    LAUNCHED();
+    GroupStart gs{key, P, sidx, segP, U - (int64_t)cmax + 1};
+    int64_t *gidx = sc.get<int64_t>(ni);
+    int64_t *d_ng = sc.get<int64_t>(1);
+    exclusive_scan(gs, ni, gidx, d_ng, sc);
+    int64_t ng = 0;
+    CK(cudaMemcpyAsync(&ng, d_ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int32_t *rep = sc.get<int32_t>(ng);
+    k_iso_label<<<grid, 256, 0, s>>>(ni, iso, gs, gidx, rep, lab, 0);
+    LAUNCHED();
+    k_iso_label<<<grid, 256, 0, s>>>(ni, iso, gs, gidx, rep, lab, 1);
+    LAUNCHED();
+}
+
 // ---------------------------------------------------------------- host driver
 
 static size_t hash_smem() { return sizeof(HashSm); }

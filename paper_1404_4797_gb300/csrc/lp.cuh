@@ -24,4 +24,8 @@ struct LPConfig {
 // device, nW entries) receives the final label weights.
 int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves, int64_t *W_out);
 
+// Clustering only: packs the nodes without neighbours into clusters of weight
+// <= U in id order (per block of cp when given); see pack_isolated in lp.cu.
+void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, Scratch &sc);
+
 }  // namespace sclap

@@ -65,6 +65,21 @@ def test_cluster_unit_U_and_constraint():
     assert np.array_equal(got.cpu().numpy(), want)
 
 
+def test_cluster_isolated_packing_with_constraint():
+    g = GRAPHS["sparse"]()
+    gn = I.to_numpy(g)
+    gn["vwgt"] = (np.arange(gn["vwgt"].size) % 5 + 1).astype(np.int32)
+    g = {k: torch.from_numpy(v) for k, v in gn.items()}
+    cp = (np.arange(gn["vwgt"].size) * 40503 % 4).astype(np.int32)
+    for U in (7, 60, 1000):
+        want, _ = oracle.cluster(gn, U, 3, 4, 9, constraint_part=cp)
+        got, _ = S.sclap_cluster(dev(g), U, 3, 4, 9, torch.from_numpy(cp).cuda())
+        assert np.array_equal(got.cpu().numpy(), want), U
+        want, _ = oracle.cluster(gn, U, 3, 4, 9)
+        got, _ = S.sclap_cluster(dev(g), U, 3, 4, 9)
+        assert np.array_equal(got.cpu().numpy(), want), U
+
+
 @pytest.mark.parametrize("name", ["chunglu2k", "weighted", "rmat14", "star5k"])
 @pytest.mark.parametrize("k", [2, 16, 64, 100])
 def test_refine_matches_oracle(name, k):

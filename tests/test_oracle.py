@@ -174,6 +174,30 @@ def test_unconstrained_single_subround_is_plain_synchronous_lp():
         assert list(got) == lab
 
 
+def test_isolated_nodes_are_packed_up_to_U():
+    # R6: nodes without neighbours, in id order, join group floor(P(v) / U')
+    # with U' = U - cmax + 1; each group is labelled by its smallest id.
+    # Unit weights, U = 2: U' = 2, P = 0,1,2,3,4 -> groups {0,1} {2,3} {4}.
+    iso5 = {"xadj": np.zeros(6, np.int64), "adjncy": np.zeros(0, np.int32),
+            "adjwgt": np.zeros(0, np.int32), "vwgt": np.ones(5, np.int32)}
+    lab, rd = oracle.cluster(iso5, 2, 3, 4, 1)
+    assert list(lab) == [0, 0, 2, 2, 4] and rd == 1
+    # weights 2,1,2,1 with U = 3: cmax = 2, U' = 2, P = 0,2,3,5 -> groups 0,1,1,2
+    iso4 = {"xadj": np.zeros(5, np.int64), "adjncy": np.zeros(0, np.int32),
+            "adjwgt": np.zeros(0, np.int32), "vwgt": np.array([2, 1, 2, 1], np.int32)}
+    lab, _ = oracle.cluster(iso4, 3, 3, 4, 1)
+    assert list(lab) == [0, 1, 1, 3]
+    # mixed with an edge (1-3): isolated 0, 2, 4 form one group when U = 3;
+    # 1 and 3 keep swapping labels (S = 1) and are not touched by the packing
+    g = mk(5, [(1, 3)])
+    lab, _ = oracle.cluster(g, 3, 2, 1, 1)
+    assert lab[0] == lab[2] == lab[4] == 0 and {lab[1], lab[3]} == {1, 3}
+    # with a constraint partition the packing is per block
+    cp = np.array([0, 1, 1, 0, 1], np.int32)
+    lab, _ = oracle.cluster(iso5, 5, 2, 1, 1, constraint_part=cp)
+    assert list(lab) == [0, 1, 1, 0, 1]
+
+
 def test_vcycle_constraint_keeps_clusters_inside_blocks():
     g = I.to_numpy(I.random_graph(200, 800, seed=9))
     cp = (np.arange(200) * 7919 % 3).astype(np.int32)
