@@ -205,9 +205,11 @@ def test_edge_cases():
     iso = {"xadj": torch.zeros(11, dtype=torch.int64), "adjncy": torch.zeros(0, dtype=torch.int32),
            "adjwgt": torch.zeros(0, dtype=torch.int32), "vwgt": torch.ones(10, dtype=torch.int32)}
     lab, rd = S.sclap_cluster(dev(iso), 3, 3, 4, 1)
-    assert torch.equal(lab.cpu(), torch.arange(10, dtype=torch.int32)) and rd == 1
+    # packed in id order into groups of weight <= U = 3
+    assert lab.cpu().tolist() == [0, 0, 0, 3, 3, 3, 6, 6, 6, 9] and rd == 1
     cg, f2c = S.contract_graph(dev(iso), lab)
-    assert cg["xadj"].numel() == 11 and cg["adjncy"].numel() == 0
+    assert cg["xadj"].numel() == 5 and cg["adjncy"].numel() == 0
+    assert cg["vwgt"].cpu().tolist() == [3, 3, 3, 1]
     # k = 1 refinement never moves
     g = dev(GRAPHS["weighted"]())
     p, cut, bw, rd = S.sclap_refine(g, 1, 0.03, 4, 4, 1, torch.zeros(3000, dtype=torch.int32,
