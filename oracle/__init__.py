@@ -75,7 +75,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            # SCLAP_ORACLE_LIB: a prebuilt variant (the mutation tests plant
+            # deliberate mistakes in a copy of the C source and load it here)
+            L = C.CDLL(os.environ.get("SCLAP_ORACLE_LIB") or build())
             L.or_mix64.restype = C.c_uint64
             L.or_mix64.argtypes = [C.c_uint64]
             L.or_colour.restype = C.c_uint32

@@ -361,6 +361,15 @@ def test_initial_partition_lpt_start_is_balanced():
     assert cuts[best] == brute.cut(g, part) and mx[best] == max(bw)
 
 
+def test_initial_partition_lpt_hand_example():
+    # Path 0-1-2 with weights 5, 3, 3, k = 2, one individual, no refinement:
+    # node 0 (heaviest) goes to block 0 (all empty, lowest id wins), then both
+    # weight-3 nodes go to the lighter block 1, whatever their shuffled order.
+    g = mk(3, [(0, 1), (1, 2)], vw=[5, 3, 3])
+    part, cuts, mx, best = oracle.initial_partition(g, 2, 100, 1, 0, 1, 5)
+    assert list(part) == [0, 1, 1] and list(cuts) == [1] and list(mx) == [6] and best == 0
+
+
 def test_initial_partition_picks_the_best_feasible_individual():
     g = I.to_numpy(I.random_graph(150, 600, seed=5, max_c=9, max_w=5))
     k = 4
