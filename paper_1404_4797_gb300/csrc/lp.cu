@@ -4,49 +4,71 @@
 // refinement form adds the overloaded-block rule (Sec. III.A).
 //
 // Per round r:
-//   k_build_wl    every node with >= 1 neighbour goes to bucket
-//                 2*colour + (deg > kHubDeg), colour = (h(v,r) >> 32) mod S.
-// Per sub-round j:
-//   k_propose     normal nodes: CTA items of kItemNodes worklist nodes, split
-//                 into chunks of <= kChunkEntries entries; a shared-memory
-//                 open-addressing (linear probing) table keyed by (node slot,
-//                 label) accumulates omega(v, L); the best eligible label per
-//                 node comes from a 64-bit atomicMax over (omega, ~tie) and an
-//                 atomicMin over labels on exact ties.  Hub nodes run in a
-//                 second launch on a side stream, one CTA per node, with a
-//                 global-memory table when the row exceeds shared memory.
-//                 The dense variant (k <= 64 blocks) accumulates into a
-//                 per-node k-array instead of a hash table.
+//   k_build_wl    nodes with 1..kMedDeg neighbours go to bucket
+//                 5*colour + class (classes: degree <= 4, 8, 16, 32, and
+//                 33..kMedDeg), colour = (h(v,r) >> 32) mod S.  Nodes of
+//                 larger degree are enumerated once per call.
+// Per sub-round j, one fused, dynamically scheduled propose kernel:
+//   large nodes   rows cut into kChunk-entry pieces spread over CTAs; each
+//                 piece aggregates omega(v, L) in a shared-memory table; a
+//                 single-piece row is finished in place, a longer one is
+//                 merged into its own global table and the CTA completing
+//                 the last piece selects the best label;
+//   medium nodes  CTA items of kMedItem nodes cut into chunks of <= kChunk
+//                 entries; a shared-memory linear-probing table keyed
+//                 (node slot, label) (the paper's Sec. IV.A choice of linear
+//                 probing) with an O(1) bitmap lookup of an entry's node;
+//   small nodes   G lanes per node (G = 4, 8, 16, 32; at most G entries):
+//                 __match_any_sync on (node, label) and __reduce_add_sync
+//                 give omega(v, L) in registers, shuffles pick the best.
+//   The best eligible label maximises (omega << 32 | ~tie); exact ties on
+//   that key go to the smallest label.  The dense variant (k <= 64 blocks)
+//   replaces the hash table by per-node k-arrays.
+// Then arbitration:
 //   k_src         refinement only: departures from overloaded blocks.
 //   k_classify    uncontested targets (sum of proposed weight <= capacity)
 //                 are applied at once; contested targets get a segment.
 //   k_scatter     contested proposals are written to their target's segment.
-//   k_arbitrate   per contested target: weighted radix select of the first
-//                 key (gain desc, id asc) whose inclusive prefix exceeds the
-//                 capacity; admitted moves are applied; per-target counters
-//                 are reset.
+//   k_arbitrate   per contested target: weighted radix select, over the bits
+//                 where the segment's keys differ, of the first key in (gain
+//                 desc, id asc) order whose inclusive prefix exceeds the
+//                 capacity; admitted moves are applied.
+//   k_reset_targets clears the per-target accumulators.
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
 #include <algorithm>
+#include <type_traits>
 
 #include "lp.cuh"
 #include "prims.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sclap {
 
 // ---------------------------------------------------------------- tunables
 
 constexpr int kThreads = 256;
-constexpr int kItemNodes = 256;       // worklist nodes per CTA work item
-constexpr int kHubDeg = 512;          // degree above which a node is a hub
-constexpr int kChunkEntries = 2048;   // entries per shared-memory chunk (max)
-constexpr int kChunkTarget = kChunkEntries - kHubDeg;  // chunking step
-constexpr int kTableSlots = 4096;     // >= 2 * kChunkEntries
-constexpr int kTableBits = 12;
+constexpr int kSmallDeg = 32;            // small nodes: <= 32 entries (one warp pass)
+constexpr int kMedDeg = 512;             // medium nodes: 33..512 entries
+constexpr int kChunk = 1536;             // entries per shared-memory chunk / large piece
+constexpr int kChunkStep = kChunk - kMedDeg;
+constexpr int kSlots = 4096;             // hash table slots (>= 2 * kChunk)
+constexpr int kSlotBits = 12;
+constexpr int kMedItem = 64;             // medium worklist nodes per CTA item
 constexpr int kDenseMaxK = 64;
-constexpr int kDenseItemNodes = 128;
+constexpr int kClasses = 5;              // buckets per colour
+constexpr int kSegSmem = 2048;           // contested segments staged in shared memory
 constexpr uint64_t kEmpty = ~0ull;
 
-static_assert((1 << kTableBits) == kTableSlots, "table size");
-static_assert(kTableSlots >= 2 * kChunkEntries, "load factor");
+static_assert((1 << kSlotBits) == kSlots, "table size");
+static_assert(kSlots >= 2 * kChunk, "load factor <= 1/2");
+static_assert(kChunk >= kMedDeg, "a medium row fits a chunk");
+static_assert(kMedItem <= kThreads, "one thread per item node");
+
+// MODE: 0 clustering (hash), 1 refinement (hash, k > 64), 2 refinement (dense)
+constexpr int kCluster = 0, kRefineHash = 1, kRefineDense = 2;
 
 struct Prop {
     int32_t v, T, own, gain;
@@ -67,8 +89,8 @@ struct Seg {
 struct Ctr {
     int32_t nprop, nseg;
     int64_t segtotal;
-    int32_t item_next, hub_next;
-    int32_t err, pad;
+    int32_t large_next, med_next, small_next;
+    int32_t err;
 };
 
 struct LPArgs {
@@ -78,9 +100,9 @@ struct LPArgs {
     int64_t B, nW;
     const int32_t *cp;
     uint64_t seed;
-    int32_t round;
-    const int32_t *wl;      // this bucket's worklist
-    const int32_t *wl_cnt;  // its length (device)
+    int32_t round, colour, S;
+    const int32_t *wl;      // worklists of this round: bucket b at wl + b * n
+    const int32_t *wl_cnt;  // bucket lengths (device)
     Prop *props;
     Ctr *ctr;
     int64_t *tsum;
@@ -90,13 +112,18 @@ struct LPArgs {
     Seg *segs;
     SegEntry *segbuf;
     int64_t *moves;         // moves of this round
-    // hub tables (global, one region per hub CTA)
+    // large nodes (degree > kMedDeg), enumerated once per call
+    int64_t nL;
+    const int32_t *Lnodes;
+    const int64_t *Lpre;    // piece prefix [nL + 1]
+    const int64_t *Loff;    // global table offset of multi-piece rows (hash) [nL + 1]
+    const int64_t *Ldlo;    // global distinct-list offset [nL + 1]
+    int32_t *Ldone, *Lndl;
     unsigned long long *gkeys;
     int32_t *gvals;
     int32_t *gdl;
-    int64_t gcap;
-    int gbits;
-    unsigned long long *prof;  // [2] entries, nodes (normal items), or null
+    int32_t *gacc;          // dense: [nL * k]
+    unsigned long long *prof;  // [2] entries, nodes, or null
 };
 
 __device__ __forceinline__ uint64_t seg_key(int32_t gain, int32_t v) {
@@ -111,6 +138,14 @@ __device__ __forceinline__ uint32_t tie_of(uint64_t h, int32_t L) {
     return (uint32_t)(mix64(h ^ (uint64_t)(uint32_t)L) >> 32);
 }
 
+__device__ __forceinline__ uint32_t colour_of(uint64_t seed, int32_t round, int32_t v, int S) {
+    return (uint32_t)(node_hash(seed, round, (uint32_t)v) >> 32) % (uint32_t)S;
+}
+
+__device__ __forceinline__ unsigned long long cand_key(int32_t w, uint64_t h, int32_t L) {
+    return ((unsigned long long)(uint32_t)w << 32) | (uint32_t)~tie_of(h, L);
+}
+
 // Applies one admitted move (Sec. III.A: the node joins the target; weights
 // move with it).
 __device__ __forceinline__ void apply_move(const LPArgs &a, int32_t v, int32_t T, int32_t own,
@@ -122,10 +157,14 @@ __device__ __forceinline__ void apply_move(const LPArgs &a, int32_t v, int32_t T
 
 // ---------------------------------------------------------------- worklists
 
+__device__ __forceinline__ int degree_class(int64_t d) {
+    return d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= kSmallDeg ? 3 : 4;
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_build_wl(DGraph g, uint64_t seed, int32_t round, int32_t S, int32_t *wl, int32_t *cnt) {
-    __shared__ int lcnt[64], lbase[64];
-    const int nb = 2 * S;
+    __shared__ int lcnt[32 * kClasses], lbase[32 * kClasses];
+    const int nb = kClasses * S;
     for (int64_t tile = (int64_t)blockIdx.x * kThreads * 4; tile < g.n;
          tile += (int64_t)gridDim.x * kThreads * 4) {
         for (int i = threadIdx.x; i < nb; i += kThreads) lcnt[i] = 0;
@@ -139,9 +178,9 @@ __global__ void __launch_bounds__(kThreads)
             vv[j] = (int32_t)v;
             if (v < g.n) {
                 int64_t d = g.xadj[v + 1] - g.xadj[v];
-                if (d > 0) {
-                    uint32_t col = (uint32_t)(node_hash(seed, round, (uint32_t)v) >> 32) % (uint32_t)S;
-                    bk[j] = 2 * (int)col + (d > kHubDeg ? 1 : 0);
+                if (d > 0 && d <= kMedDeg) {
+                    uint32_t col = colour_of(seed, round, (int32_t)v, S);
+                    bk[j] = kClasses * (int)col + degree_class(d);
                     rk[j] = atomicAdd(&lcnt[bk[j]], 1);
                 }
             }
@@ -157,46 +196,85 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// ---------------------------------------------------------------- propose (hash tables)
+// ---------------------------------------------------------------- emission
 
-struct NodeSm {
-    int32_t v[kItemNodes];
-    int32_t own[kItemNodes];
-    int32_t c[kItemNodes];
-    int32_t cpv[kItemNodes];
-    int32_t ownw[kItemNodes];
-    int32_t bestL[kItemNodes];
-    int32_t epre[kItemNodes + 1];
-    int64_t rs[kItemNodes];
-    uint64_t h[kItemNodes];
-    unsigned long long best[kItemNodes];
-    uint8_t ovl[kItemNodes];
-};
-
-struct HashSm {
-    unsigned long long keys[kTableSlots];
-    int32_t vals[kTableSlots];
-    int32_t dl[kChunkEntries];
-    NodeSm nd;
-    int64_t scan_tmp[kThreads / 32 + 1];
-    int ndl;
-    int item;
-    int ns;
-    int64_t E;
-};
-
-// Index of the node slot owning entry e: largest s in [lo, hi) with epre[s] <= e.
-__device__ __forceinline__ int owner_slot(const int32_t *epre, int lo, int hi, int32_t e) {
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (epre[mid] <= e) lo = mid;
-        else hi = mid;
+// Appends the proposal of the calling thread (called by proposing threads
+// only; appends are aggregated over the coalesced threads).  AGG groups the
+// threads by target for the per-target counters (few targets: refinement).
+template <bool AGG>
+__device__ __forceinline__ void emit(const LPArgs &a, int32_t v, int32_t T, int32_t own,
+                                     int32_t gain, int32_t c, bool ovl, int64_t wT) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    int pos = 0;
+    if (g.thread_rank() == 0) pos = atomicAdd(&a.ctr->nprop, (int)g.size());
+    pos = g.shfl(pos, 0) + (int)g.thread_rank();
+    int slot;
+    if (ovl) {
+        atomicAdd((unsigned long long *)&a.ssum[own], (unsigned long long)(int64_t)c);
+        slot = -2;
+    } else if (AGG) {
+        cg::coalesced_group h = cg::coalesced_threads();
+        cg::coalesced_group t = cg::labeled_partition(h, (unsigned)T);
+        long long sum = cg::reduce(t, (long long)c, cg::plus<long long>());
+        int base = 0;
+        if (t.thread_rank() == 0) {
+            base = atomicAdd(&a.tcnt[T], (int)t.size());
+            atomicAdd((unsigned long long *)&a.tsum[T], (unsigned long long)sum);
+        }
+        slot = t.shfl(base, 0) + (int)t.thread_rank();
+    } else {
+        atomicAdd((unsigned long long *)&a.tsum[T], (unsigned long long)(int64_t)c);
+        slot = atomicAdd(&a.tcnt[T], 1);
     }
-    return lo;
+    Prop p;
+    p.v = v;
+    p.T = T;
+    p.own = own;
+    p.gain = gain;
+    p.c = c;
+    p.slot = slot;
+    p.wT = wT;
+    a.props[pos] = p;
 }
 
-// Inserts (key, w) into a linear-probing table; records first insertions in dl.
-__device__ __forceinline__ bool table_add(unsigned long long *keys, int32_t *vals, int32_t *dl,
+// ---------------------------------------------------------------- shared memory
+
+struct NodeSm {
+    int32_t v[kMedItem], own[kMedItem], c[kMedItem], cpv[kMedItem], ownw[kMedItem],
+        bestL[kMedItem];
+    int32_t epre[kMedItem + 1];
+    int64_t rs[kMedItem];
+    uint64_t h[kMedItem];
+    unsigned long long best[kMedItem];
+    uint8_t ovl[kMedItem];
+};
+
+struct HashTab {
+    unsigned long long keys[kSlots];
+    int32_t vals[kSlots];
+    uint16_t dl[kChunk];
+};
+
+struct DenseTab {
+    int32_t acc[kMedItem * kDenseMaxK];
+};
+
+template <int MODE>
+struct PropSm {
+    typename std::conditional<MODE == kRefineDense, DenseTab, HashTab>::type t;
+    uint32_t bm[kChunk / 32 + 1];
+    int32_t bmpre[kChunk / 32 + 1];
+    NodeSm nd;
+    int64_t W[kDenseMaxK];
+    int64_t scan_tmp[kThreads / 32 + 1];
+    int64_t li;
+    int ndl, item, flag;
+};
+
+// Inserts (key, w) into a linear-probing table; a first insertion appends its
+// slot to dl.  Returns false only if the table is full (never at load <= 1/2).
+template <typename DL>
+__device__ __forceinline__ bool table_add(unsigned long long *keys, int32_t *vals, DL *dl,
                                           int *ndl, uint32_t mask, int bits, uint64_t key,
                                           int32_t w) {
     uint32_t slot = table_hash(key, bits);
@@ -204,465 +282,605 @@ __device__ __forceinline__ bool table_add(unsigned long long *keys, int32_t *val
         unsigned long long prev = atomicCAS(&keys[slot], kEmpty, (unsigned long long)key);
         if (prev == kEmpty || prev == key) {
             atomicAdd(&vals[slot], w);
-            if (prev == kEmpty) dl[atomicAdd(ndl, 1)] = (int32_t)slot;
+            if (prev == kEmpty) dl[atomicAdd(ndl, 1)] = (DL)slot;
             return true;
         }
         slot = (slot + 1) & mask;
     }
-    return false;  // table full: cannot happen at load factor <= 1/2
+    return false;
 }
 
-// Emits the proposal of node slot s if `active` and the node proposes.  Every
-// lane of the warp must call it (warp-aggregated append).
-template <bool REFINE>
-__device__ __forceinline__ void emit_hash(const LPArgs &a, NodeSm &nd, int s, bool active) {
-    unsigned long long b = active ? nd.best[s] : 0ull;
-    bool prop = false;
-    int32_t L = 0, gain = 0;
-    if (b != 0) {
-        L = nd.bestL[s];
-        gain = (int32_t)(b >> 32) - nd.ownw[s];
-        prop = gain > 0 || (REFINE && nd.ovl[s]);
-    }
-    unsigned m = __ballot_sync(0xffffffffu, prop);
-    if (!m) return;
-    int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(&a.ctr->nprop, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (!prop) return;
-    int pos = base + __popc(m & ((1u << lane) - 1));
-    Prop p;
-    p.v = nd.v[s];
-    p.T = L;
-    p.own = nd.own[s];
-    p.gain = gain;
-    p.c = nd.c[s];
-    p.wT = a.W[L];
-    if (REFINE && nd.ovl[s]) {
-        atomicAdd((unsigned long long *)&a.ssum[p.own], (unsigned long long)(int64_t)p.c);
-        p.slot = -2;
-    } else {
-        atomicAdd((unsigned long long *)&a.tsum[L], (unsigned long long)(int64_t)p.c);
-        p.slot = atomicAdd(&a.tcnt[L], 1);
-    }
-    a.props[pos] = p;
+// Loads that bypass L1 (tables merged by other CTAs through L2 atomics).
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld(const T *p) {
+    if constexpr (COHERENT) return __ldcg(p);
+    else return *p;
 }
 
-// Selection over the distinct (slot, label) entries of the current chunk.
-template <bool REFINE>
+// Best eligible label per node slot over the distinct (slot, label) entries.
+template <bool COHERENT = false, typename DL>
 __device__ __forceinline__ void select_best(const LPArgs &a, const unsigned long long *keys,
-                                            const int32_t *vals, const int32_t *dl, int ndl,
+                                            const int32_t *vals, const DL *dl, int ndl,
                                             NodeSm &nd) {
     for (int i = threadIdx.x; i < ndl; i += kThreads) {
-        int32_t slot = dl[i];
-        uint64_t key = keys[slot];
+        int32_t slot = ld<COHERENT>(&dl[i]);
+        uint64_t key = ld<COHERENT>(&keys[slot]);
         int s = (int)(key >> 32);
         int32_t L = (int32_t)(uint32_t)key;
-        int32_t w = vals[slot];
+        int32_t w = ld<COHERENT>(&vals[slot]);
         if (L == nd.own[s]) {
             nd.ownw[s] = w;
         } else if (a.W[L] + nd.c[s] <= a.B) {
-            unsigned long long ck =
-                ((unsigned long long)(uint32_t)w << 32) | (uint32_t)~tie_of(nd.h[s], L);
-            atomicMax(&nd.best[s], ck);
+            atomicMax(&nd.best[s], cand_key(w, nd.h[s], L));
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ndl; i += kThreads) {
-        int32_t slot = dl[i];
-        uint64_t key = keys[slot];
+        int32_t slot = ld<COHERENT>(&dl[i]);
+        uint64_t key = ld<COHERENT>(&keys[slot]);
         int s = (int)(key >> 32);
         int32_t L = (int32_t)(uint32_t)key;
+        int32_t w = ld<COHERENT>(&vals[slot]);
         unsigned long long b = nd.best[s];
-        if (b == 0 || L == nd.own[s] || (uint32_t)vals[slot] != (uint32_t)(b >> 32)) continue;
+        if (b == 0 || L == nd.own[s] || (uint32_t)w != (uint32_t)(b >> 32)) continue;
         if (a.W[L] + nd.c[s] > a.B) continue;
-        unsigned long long ck =
-            ((unsigned long long)(uint32_t)vals[slot] << 32) | (uint32_t)~tie_of(nd.h[s], L);
-        if (ck == b) atomicMin(&nd.bestL[s], L);
+        if (cand_key(w, nd.h[s], L) == b) atomicMin(&nd.bestL[s], L);
     }
     __syncthreads();
 }
 
-template <bool REFINE>
-__device__ void load_nodes(const LPArgs &a, NodeSm &nd, int64_t i0, int ns, int64_t *scan_tmp,
-                           int64_t *E_out) {
-    int32_t deg = 0;
-    int t = threadIdx.x;
-    if (t < ns) {
-        int32_t v = a.wl[i0 + t];
-        nd.v[t] = v;
-        int64_t b = a.g.xadj[v];
-        nd.rs[t] = b;
-        deg = (int32_t)(a.g.xadj[v + 1] - b);
-        int32_t own = a.lab[v];
-        nd.own[t] = own;
-        nd.c[t] = a.g.vwgt[v];
-        nd.cpv[t] = a.cp ? a.cp[v] : 0;
-        nd.h[t] = node_hash(a.seed, a.round, (uint32_t)v);
-        nd.ovl[t] = REFINE ? (a.W[own] > a.B) : 0;
+// Dense variant for node slot s with blocks 0..k-1 in acc[0..k): one warp;
+// clears the k-array; result in nd.best / nd.bestL / nd.ownw.
+__device__ __forceinline__ void select_dense_warp(const LPArgs &a, const int64_t *Wsm,
+                                                  int32_t *acc, int k, NodeSm &nd, int s) {
+    const int lane = threadIdx.x & 31;
+    const int32_t own = nd.own[s], c = nd.c[s];
+    const uint64_t h = nd.h[s];
+    int32_t w0 = lane < k ? acc[lane] : 0;
+    int32_t w1 = lane + 32 < k ? acc[lane + 32] : 0;
+    __syncwarp();
+    if (lane < k) acc[lane] = 0;
+    if (lane + 32 < k) acc[lane + 32] = 0;
+    int32_t ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
+    unsigned long long ck0 = 0, ck1 = 0;
+    if (w0 > 0 && lane != own && Wsm[lane] + c <= a.B) ck0 = cand_key(w0, h, lane);
+    if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= a.B) ck1 = cand_key(w1, h, lane + 32);
+    unsigned long long m = ck0 > ck1 ? ck0 : ck1;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, m, d);
+        m = o > m ? o : m;
     }
-    if (t < kItemNodes) {
-        nd.ownw[t] = 0;
-        nd.best[t] = 0;
-        nd.bestL[t] = 0x7fffffff;
+    int32_t L = 0x7fffffff;
+    if (m != 0 && ck0 == m) L = lane;
+    else if (m != 0 && ck1 == m) L = lane + 32;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) L = min(L, __shfl_xor_sync(0xffffffffu, L, d));
+    if (lane == 0) {
+        nd.best[s] = m;
+        nd.bestL[s] = L;
+        nd.ownw[s] = ownw;
     }
-    int64_t tot;
-    int64_t pre = block_exclusive_scan<kThreads>((int64_t)deg, &tot, scan_tmp);
-    if (t < ns) nd.epre[t] = (int32_t)pre;
-    if (t == 0) nd.epre[ns] = (int32_t)tot;
-    *E_out = tot;
-    __syncthreads();
 }
 
-template <bool REFINE>
-__global__ void __launch_bounds__(kThreads, 3) k_propose_hash(LPArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    HashSm &sm = *reinterpret_cast<HashSm *>(smraw);
-    for (int i = threadIdx.x; i < kTableSlots; i += kThreads) {
-        sm.keys[i] = kEmpty;
-        sm.vals[i] = 0;
-    }
-    const int64_t nwl = *a.wl_cnt;
-    const int items = (int)ceil_div<int64_t>(nwl, kItemNodes);
+// Proposal decision of node slot s after selection (one thread per node).
+template <int MODE>
+__device__ __forceinline__ void decide_and_emit(const LPArgs &a, const int64_t *Wsm, NodeSm &nd,
+                                                int s) {
+    const unsigned long long b = nd.best[s];
+    if (b == 0) return;
+    const int32_t gain = (int32_t)(b >> 32) - nd.ownw[s];
+    const bool ovl = MODE != kCluster && nd.ovl[s];
+    if (!(gain > 0 || ovl)) return;
+    const int32_t L = nd.bestL[s];
+    const int64_t wT = MODE == kRefineDense ? Wsm[L] : a.W[L];
+    emit<MODE == kRefineDense>(a, nd.v[s], L, nd.own[s], gain, nd.c[s], ovl, wT);
+}
+
+// Loads node v into slot t and resets its selection state; returns its degree.
+template <int MODE>
+__device__ __forceinline__ int32_t load_node(const LPArgs &a, const int64_t *Wsm, NodeSm &nd,
+                                             int t, int32_t v) {
+    nd.v[t] = v;
+    const int64_t b = a.g.xadj[v];
+    nd.rs[t] = b;
+    const int32_t deg = (int32_t)(a.g.xadj[v + 1] - b);
+    const int32_t own = a.lab[v];
+    nd.own[t] = own;
+    nd.c[t] = a.g.vwgt[v];
+    nd.cpv[t] = a.cp ? a.cp[v] : 0;
+    nd.h[t] = node_hash(a.seed, a.round, (uint32_t)v);
+    nd.ovl[t] = MODE == kCluster ? 0 : ((MODE == kRefineDense ? Wsm[own] : a.W[own]) > a.B);
+    nd.ownw[t] = 0;
+    nd.best[t] = 0;
+    nd.bestL[t] = 0x7fffffff;
+    return deg;
+}
+
+// ---------------------------------------------------------------- fused propose kernel
+
+template <int MODE>
+__device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
+    constexpr bool DENSE = MODE == kRefineDense;
+    const int64_t npieces = a.Lpre[a.nL];
     while (true) {
         __syncthreads();
-        if (threadIdx.x == 0) sm.item = atomicAdd(&a.ctr->item_next, 1);
+        if (threadIdx.x == 0) {
+            const int p = atomicAdd(&a.ctr->large_next, 1);
+            sm.item = p;
+            if (p < npieces) {
+                int64_t lo = 0, hi = a.nL;  // node of piece p: largest li with Lpre[li] <= p
+                while (hi - lo > 1) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (a.Lpre[mid] <= p) lo = mid;
+                    else hi = mid;
+                }
+                sm.li = lo;
+                sm.flag = colour_of(a.seed, a.round, a.Lnodes[lo], a.S) == (uint32_t)a.colour;
+            }
+        }
+        __syncthreads();
+        const int p = sm.item;
+        if (p >= npieces) break;
+        if (!sm.flag) continue;
+        const int64_t li = sm.li;
+        const int32_t v = a.Lnodes[li];
+        const int64_t pieces = a.Lpre[li + 1] - a.Lpre[li];
+        const int64_t pi = p - a.Lpre[li];
+        if (threadIdx.x == 0) {
+            load_node<MODE>(a, sm.W, sm.nd, 0, v);
+            sm.ndl = 0;
+        }
+        __syncthreads();
+        const int64_t deg = a.g.xadj[v + 1] - a.g.xadj[v];
+        const int64_t e0 = pi * kChunk;
+        const int64_t e1 = min64(deg, e0 + kChunk);
+        if (a.prof && threadIdx.x == 0) {
+            atomicAdd(&a.prof[0], (unsigned long long)(e1 - e0));
+            if (pi == 0) atomicAdd(&a.prof[1], 1ull);
+        }
+        const int64_t rs = sm.nd.rs[0];
+        const int32_t cpv = sm.nd.cpv[0];
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
+            const int32_t u = __ldg(&a.g.adjncy[rs + e]);
+            const int32_t w = __ldg(&a.g.adjwgt[rs + e]);
+            if (MODE == kCluster && a.cp && __ldg(&a.cp[u]) != cpv) continue;
+            const int32_t L = __ldg(&a.lab[u]);
+            if constexpr (DENSE) {
+                atomicAdd(&sm.t.acc[L], w);
+            } else {
+                if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
+                               (uint64_t)(uint32_t)L, w))
+                    a.ctr->err = 1;
+            }
+        }
+        __syncthreads();
+        if (pieces == 1) {
+            // the whole row is in shared memory: select and emit here
+            if constexpr (DENSE) {
+                if (threadIdx.x < 32) select_dense_warp(a, sm.W, sm.t.acc, k, sm.nd, 0);
+            } else {
+                const int ndl = sm.ndl;
+                select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, sm.nd);
+                for (int i = threadIdx.x; i < ndl; i += kThreads) {
+                    const int slot = sm.t.dl[i];
+                    sm.t.keys[slot] = kEmpty;
+                    sm.t.vals[slot] = 0;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) decide_and_emit<MODE>(a, sm.W, sm.nd, 0);
+            continue;
+        }
+        // merge the piece into the node's global table
+        if constexpr (DENSE) {
+            int32_t *gacc = a.gacc + li * k;
+            for (int b = threadIdx.x; b < k; b += kThreads) {
+                const int32_t w = sm.t.acc[b];
+                if (w) {
+                    atomicAdd(&gacc[b], w);
+                    sm.t.acc[b] = 0;
+                }
+            }
+        } else {
+            const int ndl = sm.ndl;
+            const int64_t off = a.Loff[li];
+            const uint32_t cap = (uint32_t)(a.Loff[li + 1] - off);
+            const int bits = 31 - __clz((int)cap);
+            int32_t *gdl = a.gdl + a.Ldlo[li];
+            for (int i = threadIdx.x; i < ndl; i += kThreads) {
+                const int slot = sm.t.dl[i];
+                const uint64_t key = sm.t.keys[slot];
+                const int32_t w = sm.t.vals[slot];
+                sm.t.keys[slot] = kEmpty;
+                sm.t.vals[slot] = 0;
+                if (!table_add(a.gkeys + off, a.gvals + off, gdl, &a.Lndl[li], cap - 1, bits, key, w))
+                    a.ctr->err = 1;
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) sm.flag = atomicAdd(&a.Ldone[li], 1) == (int)pieces - 1;
+        __syncthreads();
+        if (!sm.flag) continue;
+        // the last piece of this row: select over the merged table
+        __threadfence();
+        if constexpr (DENSE) {
+            int32_t *gacc = a.gacc + li * k;
+            if (threadIdx.x < 32) {
+                for (int b = threadIdx.x; b < k; b += 32) sm.t.acc[b] = atomicExch(&gacc[b], 0);
+                __syncwarp();
+                select_dense_warp(a, sm.W, sm.t.acc, k, sm.nd, 0);
+            }
+        } else {
+            const int64_t off = a.Loff[li];
+            int32_t *gdl = a.gdl + a.Ldlo[li];
+            const int ndl = __ldcg(&a.Lndl[li]);
+            select_best<true>(a, a.gkeys + off, a.gvals + off, gdl, ndl, sm.nd);
+            for (int i = threadIdx.x; i < ndl; i += kThreads) {
+                const int slot = __ldcg(&gdl[i]);
+                a.gkeys[off + slot] = kEmpty;
+                a.gvals[off + slot] = 0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            decide_and_emit<MODE>(a, sm.W, sm.nd, 0);
+            a.Ldone[li] = 0;
+            a.Lndl[li] = 0;
+        }
+    }
+}
+
+template <int MODE>
+__device__ void process_medium(const LPArgs &a, PropSm<MODE> &sm, int k) {
+    constexpr bool DENSE = MODE == kRefineDense;
+    const int32_t *wl = a.wl + (int64_t)(kClasses * a.colour + 4) * a.g.n;
+    const int64_t nwl = a.wl_cnt[kClasses * a.colour + 4];
+    const int items = (int)ceil_div<int64_t>(nwl, kMedItem);
+    NodeSm &nd = sm.nd;
+    const int t = threadIdx.x;
+    while (true) {
+        __syncthreads();
+        if (t == 0) sm.item = atomicAdd(&a.ctr->med_next, 1);
         __syncthreads();
         const int item = sm.item;
         if (item >= items) break;
-        const int64_t i0 = (int64_t)item * kItemNodes;
-        const int ns = (int)min64(kItemNodes, nwl - i0);
+        const int64_t i0 = (int64_t)item * kMedItem;
+        const int ns = (int)min64(kMedItem, nwl - i0);
+        int32_t deg = 0;
+        if (t < ns) deg = load_node<MODE>(a, sm.W, nd, t, wl[i0 + t]);
         int64_t E;
-        load_nodes<REFINE>(a, sm.nd, i0, ns, sm.scan_tmp, &E);
-        if (a.prof && threadIdx.x == 0) {
+        const int64_t pre = block_exclusive_scan<kThreads>((int64_t)deg, &E, sm.scan_tmp);
+        if (t < ns) nd.epre[t] = (int32_t)pre;
+        if (t == 0) nd.epre[ns] = (int32_t)E;
+        if (a.prof && t == 0) {
             atomicAdd(&a.prof[0], (unsigned long long)E);
             atomicAdd(&a.prof[1], (unsigned long long)ns);
         }
-        // chunks: node s belongs to chunk epre[s] / kChunkTarget
-        const int nchunks = (int)(sm.nd.epre[ns - 1] / kChunkTarget) + 1;
+        __syncthreads();
+        const int nchunks = nd.epre[ns - 1] / kChunkStep + 1;
         int s0 = 0;
         for (int ch = 0; ch < nchunks; ch++) {
-            // s1 = first slot with epre[s] >= (ch + 1) * kChunkTarget
-            int32_t lim = (ch + 1) * kChunkTarget;
-            int lo = s0, hi = ns;
+            const int32_t lim = (ch + 1) * kChunkStep;
+            int lo = s0, hi = ns;  // s1: first slot with epre >= lim
             while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (sm.nd.epre[mid] >= lim) hi = mid;
+                const int mid = (lo + hi) >> 1;
+                if (nd.epre[mid] >= lim) hi = mid;
                 else lo = mid + 1;
             }
             const int s1 = lo;
             if (s1 == s0) continue;
-            if (threadIdx.x == 0) sm.ndl = 0;
+            const int32_t e0 = nd.epre[s0];
+            const int32_t len = nd.epre[s1] - e0;
+            const int nwords = (len + 31) >> 5;
+            // bitmap of row starts -> O(1) owner lookup of an entry
+            for (int i = t; i < nwords; i += kThreads) sm.bm[i] = 0;
+            if (t == 0) sm.ndl = 0;
             __syncthreads();
-            const int32_t e0 = sm.nd.epre[s0], e1 = sm.nd.epre[s1];
-            for (int32_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
-                int s = owner_slot(sm.nd.epre, s0, s1, e);
-                int64_t idx = sm.nd.rs[s] + (e - sm.nd.epre[s]);
-                int32_t u = __ldg(&a.g.adjncy[idx]);
-                int32_t w = __ldg(&a.g.adjwgt[idx]);
-                if (a.cp && __ldg(&a.cp[u]) != sm.nd.cpv[s]) continue;
-                int32_t L = __ldg(&a.lab[u]);
-                uint64_t key = ((uint64_t)(uint32_t)s << 32) | (uint32_t)L;
-                if (!table_add(sm.keys, sm.vals, sm.dl, &sm.ndl, kTableSlots - 1, kTableBits, key, w))
-                    a.ctr->err = 1;
+            if (t >= s0 && t < s1) {
+                const int32_t le = nd.epre[t] - e0;
+                atomicOr(&sm.bm[le >> 5], 1u << (le & 31));
             }
             __syncthreads();
-            const int ndl = sm.ndl;
-            select_best<REFINE>(a, sm.keys, sm.vals, sm.dl, ndl, sm.nd);
-            // emit: every thread takes part (warp-aggregated appends)
-            for (int base = s0; base < s1; base += kThreads)
-                emit_hash<REFINE>(a, sm.nd, base + threadIdx.x, base + (int)threadIdx.x < s1);
-            for (int i = threadIdx.x; i < ndl; i += kThreads) {
-                int32_t slot = sm.dl[i];
-                sm.keys[slot] = kEmpty;
-                sm.vals[slot] = 0;
+            if (t < 32) {
+                int run = 0;
+                for (int base = 0; base < nwords; base += 32) {
+                    const int i = base + t;
+                    const int c = i < nwords ? __popc(sm.bm[i]) : 0;
+                    int inc = c;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+                        if (t >= d) inc += y;
+                    }
+                    if (i < nwords) sm.bmpre[i] = run + inc - c;
+                    run += __shfl_sync(0xffffffffu, inc, 31);
+                }
             }
+            __syncthreads();
+            for (int32_t le = t; le < len; le += kThreads) {
+                const uint32_t word = sm.bm[le >> 5];
+                const int s = s0 + sm.bmpre[le >> 5] +
+                              __popc(word & (0xffffffffu >> (31 - (le & 31)))) - 1;
+                const int64_t idx = nd.rs[s] + (e0 + le - nd.epre[s]);
+                const int32_t u = __ldg(&a.g.adjncy[idx]);
+                const int32_t w = __ldg(&a.g.adjwgt[idx]);
+                if (MODE == kCluster && a.cp && __ldg(&a.cp[u]) != nd.cpv[s]) continue;
+                const int32_t L = __ldg(&a.lab[u]);
+                if constexpr (DENSE) {
+                    atomicAdd(&sm.t.acc[(s - s0) * k + L], w);
+                } else {
+                    const uint64_t key = ((uint64_t)(uint32_t)s << 32) | (uint32_t)L;
+                    if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
+                                   key, w))
+                        a.ctr->err = 1;
+                }
+            }
+            __syncthreads();
+            if constexpr (DENSE) {
+                for (int s = s0 + (t >> 5); s < s1; s += kThreads / 32)
+                    select_dense_warp(a, sm.W, sm.t.acc + (s - s0) * k, k, nd, s);
+            } else {
+                const int ndl = sm.ndl;
+                select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, nd);
+                for (int i = t; i < ndl; i += kThreads) {
+                    const int slot = sm.t.dl[i];
+                    sm.t.keys[slot] = kEmpty;
+                    sm.t.vals[slot] = 0;
+                }
+            }
+            __syncthreads();
+            if (t >= s0 && t < s1) decide_and_emit<MODE>(a, sm.W, nd, t);
             s0 = s1;
             __syncthreads();
         }
     }
 }
 
-// Hub nodes: one CTA per node; the row's (label, omega) table lives in shared
-// memory when deg <= kChunkEntries, otherwise in this CTA's global region.
-template <bool REFINE>
-__global__ void __launch_bounds__(kThreads) k_propose_hub(LPArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    HashSm &sm = *reinterpret_cast<HashSm *>(smraw);
-    for (int i = threadIdx.x; i < kTableSlots; i += kThreads) {
-        sm.keys[i] = kEmpty;
-        sm.vals[i] = 0;
+// Small nodes: G lanes per node, one pass (deg <= G).
+template <int MODE, int G>
+__device__ __forceinline__ void small_item(const LPArgs &a, const int64_t *Wsm, const int32_t *wl,
+                                           int64_t cnt, int64_t item) {
+    constexpr int NPW = 32 / G;  // nodes per warp
+    const int lane = threadIdx.x & 31;
+    const int q = lane / G, r = lane % G;
+    const int64_t idx = item * NPW + q;
+    const bool has = idx < cnt;
+    int32_t v = 0, own = 0, c = 0, deg = 0, L = 0, w = 0;
+    uint64_t h = 0;
+    bool valid = false;
+    if (has) {
+        v = wl[idx];
+        const int64_t b = a.g.xadj[v];
+        deg = (int32_t)(a.g.xadj[v + 1] - b);
+        own = a.lab[v];
+        c = a.g.vwgt[v];
+        h = node_hash(a.seed, a.round, (uint32_t)v);
+        if (r < deg) {
+            const int32_t u = __ldg(&a.g.adjncy[b + r]);
+            w = __ldg(&a.g.adjwgt[b + r]);
+            if (!(MODE == kCluster && a.cp && __ldg(&a.cp[u]) != a.cp[v])) {
+                L = __ldg(&a.lab[u]);
+                valid = true;
+            }
+        }
     }
-    const int64_t nwl = *a.wl_cnt;
-    unsigned long long *gk = a.gkeys ? a.gkeys + (int64_t)blockIdx.x * a.gcap : nullptr;
-    int32_t *gv = a.gvals ? a.gvals + (int64_t)blockIdx.x * a.gcap : nullptr;
-    int32_t *gdl = a.gdl ? a.gdl + (int64_t)blockIdx.x * (a.gcap / 2) : nullptr;
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) sm.item = atomicAdd(&a.ctr->hub_next, 1);
-        __syncthreads();
-        const int item = sm.item;
-        if (item >= nwl) break;
-        int64_t E;
-        load_nodes<REFINE>(a, sm.nd, item, 1, sm.scan_tmp, &E);
-        const bool global = E > kChunkEntries;
-        unsigned long long *keys = global ? gk : sm.keys;
-        int32_t *vals = global ? gv : sm.vals;
-        int32_t *dl = global ? gdl : sm.dl;
-        const uint32_t mask = global ? (uint32_t)(a.gcap - 1) : (kTableSlots - 1);
-        const int bits = global ? a.gbits : kTableBits;
-        if (threadIdx.x == 0) sm.ndl = 0;
-        __syncthreads();
-        const int64_t rs = sm.nd.rs[0];
-        const int32_t cpv = sm.nd.cpv[0];
-        for (int64_t e = threadIdx.x; e < E; e += kThreads) {
-            int32_t u = __ldg(&a.g.adjncy[rs + e]);
-            int32_t w = __ldg(&a.g.adjwgt[rs + e]);
-            if (a.cp && __ldg(&a.cp[u]) != cpv) continue;
-            int32_t L = __ldg(&a.lab[u]);
-            if (!table_add(keys, vals, dl, &sm.ndl, mask, bits, (uint64_t)(uint32_t)L, w))
-                a.ctr->err = 1;
+    if (a.prof && has && r == 0) {
+        atomicAdd(&a.prof[0], (unsigned long long)deg);
+        atomicAdd(&a.prof[1], 1ull);
+    }
+    const unsigned long long mkey =
+        valid ? (((unsigned long long)q << 32) | (uint32_t)L) : (0xffffffff00000000ull | lane);
+    const unsigned peers = __match_any_sync(0xffffffffu, mkey);
+    const unsigned wsum = __reduce_add_sync(peers, valid ? (unsigned)w : 0u);
+    const bool leader = valid && (peers & ((1u << lane) - 1)) == 0;
+    unsigned long long ck = 0;
+    int32_t ownw = 0;
+    if (leader) {
+        if (L == own) {
+            ownw = (int32_t)wsum;
+        } else {
+            const int64_t WL = MODE == kRefineDense ? Wsm[L] : a.W[L];
+            if (WL + c <= a.B) ck = cand_key((int32_t)wsum, h, L);
         }
-        __syncthreads();
-        const int ndl = sm.ndl;
-        select_best<REFINE>(a, keys, vals, dl, ndl, sm.nd);
-        if (threadIdx.x < 32) emit_hash<REFINE>(a, sm.nd, 0, threadIdx.x == 0);
-        for (int i = threadIdx.x; i < ndl; i += kThreads) {
-            int32_t slot = dl[i];
-            keys[slot] = kEmpty;
-            vals[slot] = 0;
+    }
+    unsigned long long best = ck;  // reduce within the node's G lanes
+#pragma unroll
+    for (int d = G / 2; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+        best = o > best ? o : best;
+        ownw += __shfl_xor_sync(0xffffffffu, ownw, d);
+    }
+    int32_t bl = (best != 0 && ck == best) ? L : 0x7fffffff;
+#pragma unroll
+    for (int d = G / 2; d > 0; d >>= 1) bl = min(bl, __shfl_xor_sync(0xffffffffu, bl, d));
+    if (has && r == 0 && best != 0) {
+        const int32_t gain = (int32_t)(best >> 32) - ownw;
+        const bool ovl = MODE != kCluster && (MODE == kRefineDense ? Wsm[own] : a.W[own]) > a.B;
+        if (gain > 0 || ovl) {
+            const int64_t wT = MODE == kRefineDense ? Wsm[bl] : a.W[bl];
+            emit<MODE == kRefineDense>(a, v, bl, own, gain, c, ovl, wT);
         }
-        __syncthreads();
     }
 }
 
-// ---------------------------------------------------------------- propose (dense k <= 64)
-
-struct DenseSm {
-    int32_t acc[kDenseItemNodes * kDenseMaxK];
-    int64_t W[kDenseMaxK];
-    int32_t v[kDenseItemNodes], own[kDenseItemNodes], c[kDenseItemNodes];
-    int32_t epre[kDenseItemNodes + 1];
-    int64_t rs[kDenseItemNodes];
-    uint64_t h[kDenseItemNodes];
-    // staged proposals of the item
-    int32_t pT[kDenseItemNodes], pgain[kDenseItemNodes], pslot[kDenseItemNodes];
-    uint8_t povl[kDenseItemNodes], pflag[kDenseItemNodes];
-    int32_t lcnt[kDenseMaxK];
-    int64_t lsum[kDenseMaxK];
-    int64_t lssum[kDenseMaxK];
-    int32_t gbase[kDenseMaxK];
-    int64_t scan_tmp[kThreads / 32 + 1];
-    int item, nprop, pbase;
-};
-
-template <bool HUB>
-__global__ void __launch_bounds__(kThreads) k_propose_dense(LPArgs a, int k) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    DenseSm &sm = *reinterpret_cast<DenseSm *>(smraw);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kDenseItemNodes * k; i += kThreads) sm.acc[i] = 0;
-    for (int b = threadIdx.x; b < k; b += kThreads) {
-        sm.W[b] = a.W[b];
-        sm.lcnt[b] = 0;
-        sm.lsum[b] = 0;
-        sm.lssum[b] = 0;
-    }
-    const int64_t nwl = *a.wl_cnt;
-    const int items = HUB ? (int)nwl : (int)ceil_div<int64_t>(nwl, kDenseItemNodes);
+template <int MODE>
+__device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
+    const int b0 = kClasses * a.colour;
+    const int64_t c0 = a.wl_cnt[b0], c1 = a.wl_cnt[b0 + 1], c2 = a.wl_cnt[b0 + 2],
+                  c3 = a.wl_cnt[b0 + 3];
+    // warp items: G = 4, 8, 16, 32 hold 8, 4, 2, 1 nodes
+    const int64_t i1 = ceil_div<int64_t>(c0, 8);
+    const int64_t i2 = i1 + ceil_div<int64_t>(c1, 4);
+    const int64_t i3 = i2 + ceil_div<int64_t>(c2, 2);
+    const int64_t i4 = i3 + c3;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = a.g.n;
     while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            sm.item = atomicAdd(HUB ? &a.ctr->hub_next : &a.ctr->item_next, 1);
-            sm.nprop = 0;
-        }
-        __syncthreads();
-        const int item = sm.item;
-        if (item >= items) break;
-        const int64_t i0 = HUB ? item : (int64_t)item * kDenseItemNodes;
-        const int ns = HUB ? 1 : (int)min64(kDenseItemNodes, nwl - i0);
-        int32_t deg = 0;
-        const int t = threadIdx.x;
-        if (t < ns) {
-            int32_t v = a.wl[i0 + t];
-            sm.v[t] = v;
-            int64_t b = a.g.xadj[v];
-            sm.rs[t] = b;
-            deg = (int32_t)(a.g.xadj[v + 1] - b);
-            sm.own[t] = a.lab[v];
-            sm.c[t] = a.g.vwgt[v];
-            sm.h[t] = node_hash(a.seed, a.round, (uint32_t)v);
-        }
-        int64_t E;
-        int64_t pre = block_exclusive_scan<kThreads>((int64_t)deg, &E, sm.scan_tmp);
-        if (t < ns) sm.epre[t] = (int32_t)pre;
-        if (t == 0) sm.epre[ns] = (int32_t)E;
-        if (!HUB && a.prof && t == 0) {
-            atomicAdd(&a.prof[0], (unsigned long long)E);
-            atomicAdd(&a.prof[1], (unsigned long long)ns);
-        }
-        __syncthreads();
-        // accumulate omega(v, b) for every entry of the item
-        for (int64_t e = t; e < E; e += kThreads) {
-            int s = HUB ? 0 : owner_slot(sm.epre, 0, ns, (int32_t)e);
-            int64_t idx = sm.rs[s] + (e - sm.epre[s]);
-            int32_t u = __ldg(&a.g.adjncy[idx]);
-            int32_t w = __ldg(&a.g.adjwgt[idx]);
-            int32_t L = __ldg(&a.lab[u]);
-            atomicAdd(&sm.acc[s * k + L], w);
-        }
-        __syncthreads();
-        // selection: one warp per node, lanes over blocks b = lane, lane + 32
-        for (int s = warp; s < ns; s += kThreads / 32) {
-            const int32_t own = sm.own[s], c = sm.c[s];
-            const uint64_t h = sm.h[s];
-            int32_t w0 = lane < k ? sm.acc[s * k + lane] : 0;
-            int32_t w1 = lane + 32 < k ? sm.acc[s * k + lane + 32] : 0;
-            __syncwarp();
-            if (lane < k) sm.acc[s * k + lane] = 0;
-            if (lane + 32 < k) sm.acc[s * k + lane + 32] = 0;
-            int32_t ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
-            unsigned long long ck0 = 0, ck1 = 0;
-            if (w0 > 0 && lane != own && sm.W[lane] + c <= a.B)
-                ck0 = ((unsigned long long)(uint32_t)w0 << 32) | (uint32_t)~tie_of(h, lane);
-            if (w1 > 0 && lane + 32 != own && sm.W[lane + 32] + c <= a.B)
-                ck1 = ((unsigned long long)(uint32_t)w1 << 32) | (uint32_t)~tie_of(h, lane + 32);
-            unsigned long long m = ck0 > ck1 ? ck0 : ck1;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                unsigned long long o = __shfl_xor_sync(0xffffffffu, m, d);
-                m = o > m ? o : m;
-            }
-            int32_t L = 0x7fffffff;
-            if (m != 0) {
-                if (ck0 == m) L = lane;
-                else if (ck1 == m) L = lane + 32;
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) L = min(L, __shfl_xor_sync(0xffffffffu, L, d));
-            }
-            if (lane == 0) {
-                bool ovl = sm.W[own] > a.B;
-                int32_t gain = (int32_t)(m >> 32) - ownw;
-                bool prop = m != 0 && (gain > 0 || ovl);
-                sm.pflag[s] = prop;
-                if (prop) {
-                    sm.pT[s] = L;
-                    sm.pgain[s] = gain;
-                    sm.povl[s] = ovl;
-                    atomicAdd(&sm.nprop, 1);
-                    if (ovl) {
-                        atomicAdd((unsigned long long *)&sm.lssum[own], (unsigned long long)c);
-                        sm.pslot[s] = -2;
-                    } else {
-                        atomicAdd((unsigned long long *)&sm.lsum[L], (unsigned long long)c);
-                        sm.pslot[s] = atomicAdd(&sm.lcnt[L], 1);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (sm.nprop == 0) continue;
-        for (int b = threadIdx.x; b < k; b += kThreads) {
-            if (sm.lcnt[b]) {
-                sm.gbase[b] = atomicAdd(&a.tcnt[b], sm.lcnt[b]);
-                atomicAdd((unsigned long long *)&a.tsum[b], (unsigned long long)sm.lsum[b]);
-            }
-            if (sm.lssum[b]) atomicAdd((unsigned long long *)&a.ssum[b], (unsigned long long)sm.lssum[b]);
-            sm.lcnt[b] = 0;
-            sm.lsum[b] = 0;
-            sm.lssum[b] = 0;
-        }
-        if (threadIdx.x == 0) sm.pbase = atomicAdd(&a.ctr->nprop, sm.nprop);
-        if (threadIdx.x == 0) sm.nprop = 0;
-        __syncthreads();
-        // write the staged proposals (positions by a block scan over flags)
-        int flag = (t < ns) ? sm.pflag[t] : 0;
-        int64_t tot;
-        int64_t pos = block_exclusive_scan<kThreads>((int64_t)flag, &tot, sm.scan_tmp);
-        if (flag) {
-            Prop p;
-            p.v = sm.v[t];
-            p.T = sm.pT[t];
-            p.own = sm.own[t];
-            p.gain = sm.pgain[t];
-            p.c = sm.c[t];
-            p.slot = sm.pslot[t] >= 0 ? sm.gbase[p.T] + sm.pslot[t] : -2;
-            p.wT = sm.W[p.T];
-            a.props[sm.pbase + pos] = p;
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&a.ctr->small_next, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= i4) break;
+        if (it < i1) small_item<MODE, 4>(a, Wsm, a.wl + b0 * n, c0, it);
+        else if (it < i2) small_item<MODE, 8>(a, Wsm, a.wl + (b0 + 1) * n, c1, it - i1);
+        else if (it < i3) small_item<MODE, 16>(a, Wsm, a.wl + (b0 + 2) * n, c2, it - i2);
+        else small_item<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, c3, it - i3);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_propose(LPArgs a, int k) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    PropSm<MODE> &sm = *reinterpret_cast<PropSm<MODE> *>(smraw);
+    if constexpr (MODE == kRefineDense) {
+        for (int i = threadIdx.x; i < kMedItem * k; i += kThreads) sm.t.acc[i] = 0;
+        for (int b = threadIdx.x; b < k; b += kThreads) sm.W[b] = a.W[b];
+    } else {
+        for (int i = threadIdx.x; i < kSlots; i += kThreads) {
+            sm.t.keys[i] = kEmpty;
+            sm.t.vals[i] = 0;
         }
     }
+    if (a.nL > 0) process_large<MODE>(a, sm, k);
+    process_medium<MODE>(a, sm, k);
+    __syncthreads();
+    process_small<MODE>(a, sm.W);
 }
 
 // ---------------------------------------------------------------- arbitration
 
-// Weighted radix select: the smallest key K such that the total weight of
-// entries with key <= K is >= thr (entries (key, c) in [0, cnt)); ~0 if the
-// total is < thr.  All threads of the CTA call it.
+// Sum of a non-negative 32-bit value over the lanes of `peers` as int64 (two
+// 16-bit halves, so the warp reduction cannot overflow).
+__device__ __forceinline__ int64_t peer_sum64(unsigned peers, int32_t c) {
+    const unsigned lo = __reduce_add_sync(peers, (unsigned)c & 0xffffu);
+    const unsigned hi = __reduce_add_sync(peers, (unsigned)c >> 16);
+    return ((int64_t)hi << 16) + (int64_t)lo;
+}
+
+// Weighted radix select: the smallest key K such that the total weight of the
+// entries with key <= K is >= thr; ~0 if the total is < thr.  get(i, &key, &c)
+// returns entry i (c = 0 entries carry no weight).  Only the bits where
+// kmin and kmax differ are examined.  All threads of the CTA call it.
 template <typename Get>
-__device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr,
-                                          unsigned long long *hist /* [256] */,
-                                          int64_t *shared_acc, uint64_t *shared_prefix,
-                                          int *shared_done) {
+__device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uint64_t kmin,
+                                          uint64_t kmax, unsigned long long *hist /* [256] */,
+                                          int64_t *s_acc, uint64_t *s_pf, int *s_done) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t diff = kmin ^ kmax;
+    const int top = diff ? 63 - __clzll((long long)diff) : 0;  // highest differing bit
     if (threadIdx.x == 0) {
-        *shared_acc = 0;
-        *shared_prefix = 0;
-        *shared_done = 0;
+        *s_acc = 0;
+        *s_pf = top >= 63 ? 0ull : (kmin & (~0ull << (top + 1)));
+        *s_done = 0;
     }
     __syncthreads();
-    for (int shift = 56; shift >= 0; shift -= 8) {
+    const int64_t cnt_r = ceil_div<int64_t>(cnt, blockDim.x) * blockDim.x;
+    for (int hb = top; hb >= 0; hb -= 8) {
+        const int width = hb + 1 < 8 ? hb + 1 : 8;
+        const int shift = hb - width + 1;
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        const uint64_t hm = (shift == 56) ? 0ull : (~0ull << (shift + 8));
-        const uint64_t pf = *shared_prefix;
-        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-            uint64_t k;
-            int32_t c;
-            get(i, &k, &c);
-            if ((k & hm) == (pf & hm) && c > 0)
-                atomicAdd(&hist[(k >> shift) & 255], (unsigned long long)c);
+        const uint64_t hm = (hb >= 63) ? 0ull : (~0ull << (hb + 1));
+        const uint64_t pf = *s_pf;
+        for (int64_t i = threadIdx.x; i < cnt_r; i += blockDim.x) {
+            uint64_t key = 0;
+            int32_t c = 0;
+            if (i < cnt) get(i, &key, &c);
+            const bool in = i < cnt && c > 0 && (key & hm) == (pf & hm);
+            const unsigned d = in ? (unsigned)((key >> shift) & ((1u << width) - 1)) : 0xffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int64_t s = peer_sum64(peers, in ? c : 0);
+            if (in && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&hist[d], (unsigned long long)s);
         }
         __syncthreads();
         if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
             unsigned long long local = 0;
             for (int j = 0; j < 8; j++) local += hist[lane * 8 + j];
             unsigned long long inc = local;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
                 if (lane >= d) inc += y;
             }
-            const int64_t acc = *shared_acc;
-            bool reach = acc + (int64_t)inc >= thr;
-            unsigned m = __ballot_sync(0xffffffffu, reach);
+            const int64_t acc = *s_acc;
+            const bool reach = acc + (int64_t)inc >= thr;
+            const unsigned m = __ballot_sync(0xffffffffu, reach);
             if (m == 0) {
-                if (lane == 0) *shared_done = 1;  // total below threshold
-            } else {
-                int first = __ffs(m) - 1;
-                if (lane == first) {
-                    int64_t run = acc + (int64_t)(inc - local);
-                    int d = lane * 8;
-                    for (int j = 0; j < 8; j++) {
-                        if (run + (int64_t)hist[lane * 8 + j] >= thr) { d = lane * 8 + j; break; }
-                        run += (int64_t)hist[lane * 8 + j];
-                    }
-                    *shared_acc = run;
-                    *shared_prefix = pf | ((uint64_t)d << shift);
+                if (lane == 0) *s_done = 1;  // total below the threshold
+            } else if (lane == __ffs(m) - 1) {
+                int64_t run = acc + (int64_t)(inc - local);
+                int d = lane * 8;
+                for (int j = 0; j < 8; j++) {
+                    if (run + (int64_t)hist[lane * 8 + j] >= thr) { d = lane * 8 + j; break; }
+                    run += (int64_t)hist[lane * 8 + j];
                 }
+                *s_acc = run;
+                *s_pf = pf | ((uint64_t)d << shift);
             }
         }
         __syncthreads();
-        if (*shared_done) return ~0ull;
+        if (*s_done) return ~0ull;
     }
-    return *shared_prefix;
+    return *s_pf;
 }
+
+// Min and max key over the entries with c > 0 (all threads of the CTA).
+template <typename Get>
+__device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *out_max,
+                             unsigned long long *red /* [64] */) {
+    unsigned long long mn = ~0ull, mx = 0;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        uint64_t key;
+        int32_t c;
+        get(i, &key, &c);
+        if (c <= 0) continue;
+        mn = key < mn ? key : mn;
+        mx = key > mx ? key : mx;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn, d);
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, d);
+        mn = x < mn ? x : mn;
+        mx = y > mx ? y : mx;
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[w] = mn;
+        red[32 + w] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+            mn = red[i] < mn ? red[i] : mn;
+            mx = red[32 + i] > mx ? red[32 + i] : mx;
+        }
+        red[0] = mn;
+        red[32] = mx;
+    }
+    __syncthreads();
+    *out_min = red[0];
+    *out_max = red[32];
+    __syncthreads();
+}
+
+struct ArbSm {
+    unsigned long long hist[256];
+    unsigned long long red[64];
+    uint64_t keys[kSegSmem];
+    int32_t c[kSegSmem];
+    int64_t acc;
+    uint64_t pf;
+    int done;
+};
 
 // Refinement: departures from overloaded blocks (slot == -2).  CTAs with
 // blockIdx < nW handle block b = blockIdx when its departures are contested;
 // the others pass the uncontested sources' proposals through.
 __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
     __shared__ unsigned long long hist[256];
+    __shared__ unsigned long long red[64];
     __shared__ int64_t s_acc;
     __shared__ uint64_t s_pf;
     __shared__ int s_done;
@@ -673,13 +891,16 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
         if (Wb <= a.B) return;
         const int64_t X = Wb - a.B;
         if (a.ssum[b] < X) return;  // uncontested: handled by the pass-through CTAs
-        auto get = [&](int64_t i, uint64_t *k, int32_t *c) {
+        auto get = [&](int64_t i, uint64_t *key, int32_t *c) {
             const Prop &p = a.props[i];
-            bool mine = p.slot == -2 && p.own == b;
-            *k = mine ? seg_key(p.gain, p.v) : 0;
+            const bool mine = p.slot == -2 && p.own == b;
+            *key = mine ? seg_key(p.gain, p.v) : 0;
             *c = mine ? p.c : 0;
         };
-        uint64_t K = select_first_reaching(get, nprop, X, hist, &s_acc, &s_pf, &s_done);
+        uint64_t kmin, kmax;
+        block_minmax(get, nprop, &kmin, &kmax, red);
+        const uint64_t K = select_first_reaching(get, nprop, X, kmin, kmax, hist, &s_acc, &s_pf,
+                                                 &s_done);
         for (int64_t i = threadIdx.x; i < nprop; i += blockDim.x) {
             Prop &p = a.props[i];
             if (p.slot != -2 || p.own != b) continue;
@@ -725,7 +946,8 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) moved += __shfl_down_sync(0xffffffffu, moved, d);
-    if ((threadIdx.x & 31) == 0 && moved) atomicAdd((unsigned long long *)a.moves, (unsigned long long)moved);
+    if ((threadIdx.x & 31) == 0 && moved)
+        atomicAdd((unsigned long long *)a.moves, (unsigned long long)moved);
 }
 
 __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
@@ -741,10 +963,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
-    __shared__ unsigned long long hist[256];
-    __shared__ int64_t s_acc;
-    __shared__ uint64_t s_pf;
-    __shared__ int s_done;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ArbSm &sm = *reinterpret_cast<ArbSm *>(smraw);
     const int nseg = a.ctr->nseg;
     const int lane = threadIdx.x & 31;
     int64_t moved = 0;
@@ -757,15 +977,15 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         uint64_t key = ~0ull;
         int32_t c = 0, own = 0;
         if (lane < sg.cnt) {
-            SegEntry e = a.segbuf[sg.base + lane];
+            const SegEntry e = a.segbuf[sg.base + lane];
             key = e.key;
             c = e.c;
             own = e.own;
         }
         int64_t pre = 0;
         for (int j = 0; j < sg.cnt; j++) {
-            uint64_t kj = __shfl_sync(0xffffffffu, key, j);
-            int32_t cj = __shfl_sync(0xffffffffu, c, j);
+            const uint64_t kj = __shfl_sync(0xffffffffu, key, j);
+            const int32_t cj = __shfl_sync(0xffffffffu, c, j);
             if (kj <= key) pre += cj;
         }
         if (lane < sg.cnt && (c == 0 || pre < sg.thr)) {
@@ -778,14 +998,31 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         const Seg sg = a.segs[si];
         if (sg.cnt <= 32) continue;
         const SegEntry *ent = a.segbuf + sg.base;
-        auto get = [&](int64_t i, uint64_t *k, int32_t *c) {
-            SegEntry e = ent[i];
-            *k = e.key;
-            *c = e.c;
+        const bool staged = sg.cnt <= kSegSmem;
+        if (staged) {
+            for (int i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
+                const SegEntry e = ent[i];
+                sm.keys[i] = e.key;
+                sm.c[i] = e.c;
+            }
+            __syncthreads();
+        }
+        auto get = [&](int64_t i, uint64_t *key, int32_t *c) {
+            if (staged) {
+                *key = sm.keys[i];
+                *c = sm.c[i];
+            } else {
+                const SegEntry e = ent[i];
+                *key = e.key;
+                *c = e.c;
+            }
         };
-        uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, hist, &s_acc, &s_pf, &s_done);
+        uint64_t kmin, kmax;
+        block_minmax(get, sg.cnt, &kmin, &kmax, sm.red);
+        const uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, kmin, kmax, sm.hist, &sm.acc,
+                                                 &sm.pf, &sm.done);
         for (int64_t i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
-            SegEntry e = ent[i];
+            const SegEntry e = ent[i];
             if (e.key < K || e.c == 0) {
                 apply_move(a, (int32_t)(uint32_t)e.key, sg.T, e.own, e.c);
                 moved++;
@@ -809,6 +1046,52 @@ __global__ void __launch_bounds__(kThreads) k_reset_targets(LPArgs a) {
         if (a.ssum) a.ssum[p.own] = 0;
     }
 }
+
+// ---------------------------------------------------------------- large-node lists
+
+struct LargeFlag {
+    const int64_t *xadj;
+    __device__ int64_t operator()(int64_t v) const { return xadj[v + 1] - xadj[v] > kMedDeg ? 1 : 0; }
+};
+
+__global__ void k_large_compact(DGraph g, const int64_t *pos, int32_t *Lnodes) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (g.xadj[v + 1] - g.xadj[v] > kMedDeg) Lnodes[pos[v]] = (int32_t)v;
+}
+
+struct LargePieces {
+    const int64_t *xadj;
+    const int32_t *Lnodes;
+    __device__ int64_t operator()(int64_t i) const {
+        const int32_t v = Lnodes[i];
+        return ceil_div<int64_t>(xadj[v + 1] - xadj[v], kChunk);
+    }
+};
+
+// Global table slots of a multi-piece row, 2^ceil(log2(2 deg)); single-piece rows: 0.
+struct LargeCap {
+    const int64_t *xadj;
+    const int32_t *Lnodes;
+    __device__ int64_t operator()(int64_t i) const {
+        const int32_t v = Lnodes[i];
+        const int64_t d = xadj[v + 1] - xadj[v];
+        if (d <= kChunk) return 0;
+        int64_t c = 1;
+        while (c < 2 * d) c <<= 1;
+        return c;
+    }
+};
+
+struct LargeDl {
+    const int64_t *xadj;
+    const int32_t *Lnodes;
+    __device__ int64_t operator()(int64_t i) const {
+        const int32_t v = Lnodes[i];
+        const int64_t d = xadj[v + 1] - xadj[v];
+        return d <= kChunk ? 0 : d;
+    }
+};
 
 // ---------------------------------------------------------------- weights
 
@@ -957,8 +1240,18 @@ void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, 
 
 // ---------------------------------------------------------------- host driver
 
-static size_t hash_smem() { return sizeof(HashSm); }
-static size_t dense_smem() { return sizeof(DenseSm); }
+template <int MODE>
+static void set_propose_attr(size_t smem) {
+    CK(cudaFuncSetAttribute(k_propose<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
+template <int MODE>
+static int propose_grid(int sms) {
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose<MODE>, kThreads,
+                                                     sizeof(PropSm<MODE>)));
+    return sms * std::max(1, occ);
+}
 
 int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, int64_t *W_out) {
     cudaStream_t s = sc.stream();
@@ -970,7 +1263,9 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         if (W_out && g.n == 0) CK(cudaMemsetAsync(W_out, 0, cfg.nW * sizeof(int64_t), s));
         return 0;
     }
-    const bool dense = cfg.refine && cfg.nW <= kDenseMaxK;
+    if (S < 1 || S > 32) fail(SCLAP_EINVAL, "subrounds");
+    const int mode = !cfg.refine ? kCluster : (cfg.nW <= kDenseMaxK ? kRefineDense : kRefineHash);
+    const int k = (int)cfg.nW;
 
     int64_t *W = W_out ? W_out : sc.get<int64_t>(cfg.nW);
     if (cfg.refine) {
@@ -991,6 +1286,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.nW = cfg.nW;
     a.cp = cfg.refine ? nullptr : cfg.cp;
     a.seed = cfg.seed;
+    a.S = S;
     a.tsum = sc.zeros<int64_t>(cfg.nW);
     a.tcnt = sc.zeros<int32_t>(cfg.nW);
     a.tbase = sc.get<int64_t>(cfg.nW);
@@ -998,115 +1294,113 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.props = sc.get<Prop>(g.n);
     a.segs = sc.get<Seg>(g.n);
     a.segbuf = sc.get<SegEntry>(g.n);
-    int32_t *wl = sc.get<int32_t>((size_t)2 * S * g.n);
-    int32_t *wl_cnt = sc.get<int32_t>(2 * S);
+    int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
+    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S);
     Ctr *ctr = sc.get<Ctr>(S);
     int64_t *d_moves = sc.zeros<int64_t>(cfg.rounds);
+    a.wl = wl;
+    a.wl_cnt = wl_cnt;
     a.prof = prof().on ? prof().d_counts : nullptr;
 
-    // hub tables (hash variant only)
-    const int hub_ctas = std::max(1, std::min(sms, 152));
-    if (!dense && cfg.max_deg > kChunkEntries) {
-        int bits = bit_width_u64((uint64_t)(2 * cfg.max_deg - 1));
-        a.gbits = bits;
-        a.gcap = (int64_t)1 << bits;
-        a.gkeys = sc.get<unsigned long long>((size_t)hub_ctas * a.gcap);
-        a.gvals = sc.zeros<int32_t>((size_t)hub_ctas * a.gcap);
-        a.gdl = sc.get<int32_t>((size_t)hub_ctas * (a.gcap / 2));
-        CK(cudaMemsetAsync(a.gkeys, 0xff, (size_t)hub_ctas * a.gcap * sizeof(uint64_t), s));
-    }
-
+    // nodes of degree > kMedDeg: one list per call, cut into kChunk pieces
     {
-        CK(cudaFuncSetAttribute(k_propose_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_smem()));
-        CK(cudaFuncSetAttribute(k_propose_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_smem()));
-        CK(cudaFuncSetAttribute(k_propose_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_smem()));
-        CK(cudaFuncSetAttribute(k_propose_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_smem()));
-        CK(cudaFuncSetAttribute(k_propose_dense<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem()));
-        CK(cudaFuncSetAttribute(k_propose_dense<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem()));
+        int64_t *pos = sc.get<int64_t>(g.n);
+        int64_t *d_nL = sc.get<int64_t>(1);
+        exclusive_scan(LargeFlag{g.xadj}, g.n, pos, d_nL, sc);
+        int64_t nL = 0;
+        CK(cudaMemcpyAsync(&nL, d_nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        a.nL = nL;
+        if (nL > 0) {
+            int32_t *Lnodes = sc.get<int32_t>(nL);
+            k_large_compact<<<sms * 4, 256, 0, s>>>(g, pos, Lnodes);
+            LAUNCHED();
+            int64_t *Lpre = sc.get<int64_t>(nL + 1);
+            exclusive_scan(LargePieces{g.xadj, Lnodes}, nL, Lpre, Lpre + nL, sc);
+            a.Lnodes = Lnodes;
+            a.Lpre = Lpre;
+            a.Ldone = sc.zeros<int32_t>(nL);
+            a.Lndl = sc.zeros<int32_t>(nL);
+            if (mode == kRefineDense) {
+                a.gacc = sc.zeros<int32_t>((size_t)nL * k);
+            } else {
+                int64_t *Loff = sc.get<int64_t>(nL + 1);
+                int64_t *Ldlo = sc.get<int64_t>(nL + 1);
+                exclusive_scan(LargeCap{g.xadj, Lnodes}, nL, Loff, Loff + nL, sc);
+                exclusive_scan(LargeDl{g.xadj, Lnodes}, nL, Ldlo, Ldlo + nL, sc);
+                int64_t tot[2];
+                CK(cudaMemcpyAsync(&tot[0], Loff + nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(&tot[1], Ldlo + nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                a.Loff = Loff;
+                a.Ldlo = Ldlo;
+                a.gkeys = sc.get<unsigned long long>(tot[0]);
+                a.gvals = sc.zeros<int32_t>(tot[0]);
+                a.gdl = sc.get<int32_t>(tot[1]);
+                if (tot[0]) CK(cudaMemsetAsync(a.gkeys, 0xff, tot[0] * sizeof(uint64_t), s));
+            }
+        }
     }
-    int occ_hash = 0, occ_dense = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_hash, k_propose_hash<false>, kThreads, hash_smem()));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_dense, k_propose_dense<false>, kThreads, dense_smem()));
-    const int grid_main = sms * std::max(1, dense ? occ_dense : occ_hash);
-    const int grid_small = sms * 4;
 
-    cudaStream_t side;
-    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    cudaEvent_t ev_fork, ev_join;
-    CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    size_t psmem = 0;
+    int grid_main = 0;
+    switch (mode) {
+        case kCluster: psmem = sizeof(PropSm<kCluster>); set_propose_attr<kCluster>(psmem);
+                       grid_main = propose_grid<kCluster>(sms); break;
+        case kRefineHash: psmem = sizeof(PropSm<kRefineHash>); set_propose_attr<kRefineHash>(psmem);
+                          grid_main = propose_grid<kRefineHash>(sms); break;
+        default: psmem = sizeof(PropSm<kRefineDense>); set_propose_attr<kRefineDense>(psmem);
+                 grid_main = propose_grid<kRefineDense>(sms); break;
+    }
+    CK(cudaFuncSetAttribute(k_arbitrate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sizeof(ArbSm)));
+    const int grid_small = sms * 4;
 
     int done = 0;
     int64_t hmoves = 0;
-    try {
-        for (int r = 0; r < cfg.rounds; r++) {
-            a.round = r;
-            a.moves = d_moves + r;
-            CK(cudaMemsetAsync(wl_cnt, 0, 2 * S * sizeof(int32_t), s));
-            CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
-            k_build_wl<<<sms * 4, kThreads, 0, s>>>(g, cfg.seed, r, S, wl, wl_cnt);
+    for (int r = 0; r < cfg.rounds; r++) {
+        a.round = r;
+        a.moves = d_moves + r;
+        CK(cudaMemsetAsync(wl_cnt, 0, kClasses * S * sizeof(int32_t), s));
+        CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
+        k_build_wl<<<sms * 4, kThreads, 0, s>>>(g, cfg.seed, r, S, wl, wl_cnt);
+        LAUNCHED();
+        for (int j = 0; j < S; j++) {
+            a.ctr = ctr + j;
+            a.colour = j;
+            cudaEvent_t pb, pe;
+            prof_begin(s, &pb, &pe);
+            switch (mode) {
+                case kCluster: k_propose<kCluster><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+                case kRefineHash: k_propose<kRefineHash><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+                default: k_propose<kRefineDense><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+            }
             LAUNCHED();
-            for (int j = 0; j < S; j++) {
-                a.ctr = ctr + j;
-                // hub nodes on the side stream, concurrently with the normal nodes
-                CK(cudaEventRecord(ev_fork, s));
-                CK(cudaStreamWaitEvent(side, ev_fork, 0));
-                LPArgs ah = a;
-                ah.wl = wl + (int64_t)(2 * j + 1) * g.n;
-                ah.wl_cnt = wl_cnt + 2 * j + 1;
-                ah.prof = nullptr;
-                if (dense) k_propose_dense<true><<<hub_ctas, kThreads, dense_smem(), side>>>(ah, (int)cfg.nW);
-                else if (cfg.refine) k_propose_hub<true><<<hub_ctas, kThreads, hash_smem(), side>>>(ah);
-                else k_propose_hub<false><<<hub_ctas, kThreads, hash_smem(), side>>>(ah);
-                LAUNCHED();
-                CK(cudaEventRecord(ev_join, side));
-
-                a.wl = wl + (int64_t)(2 * j) * g.n;
-                a.wl_cnt = wl_cnt + 2 * j;
-                cudaEvent_t pb, pe;
-                prof_begin(s, &pb, &pe);
-                if (dense) k_propose_dense<false><<<grid_main, kThreads, dense_smem(), s>>>(a, (int)cfg.nW);
-                else if (cfg.refine) k_propose_hash<true><<<grid_main, kThreads, hash_smem(), s>>>(a);
-                else k_propose_hash<false><<<grid_main, kThreads, hash_smem(), s>>>(a);
-                LAUNCHED();
-                prof_end(s, pb, pe);
-                CK(cudaStreamWaitEvent(s, ev_join, 0));
-
-                if (cfg.refine) {
-                    k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, s>>>(a);
-                    LAUNCHED();
-                }
-                k_classify<<<grid_small, kThreads, 0, s>>>(a);
-                LAUNCHED();
-                k_scatter<<<grid_small, kThreads, 0, s>>>(a);
-                LAUNCHED();
-                k_arbitrate<<<grid_small, kThreads, 0, s>>>(a);
-                LAUNCHED();
-                k_reset_targets<<<grid_small, kThreads, 0, s>>>(a);
+            prof_end(s, pb, pe);
+            if (cfg.refine) {
+                k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, s>>>(a);
                 LAUNCHED();
             }
-            CK(cudaMemcpyAsync(&hmoves, d_moves + r, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            done = r + 1;
-            if (moves_out) moves_out->push_back(hmoves);
-            if (hmoves == 0) break;
+            k_classify<<<grid_small, kThreads, 0, s>>>(a);
+            LAUNCHED();
+            k_scatter<<<grid_small, kThreads, 0, s>>>(a);
+            LAUNCHED();
+            k_arbitrate<<<grid_small, kThreads, sizeof(ArbSm), s>>>(a);
+            LAUNCHED();
+            k_reset_targets<<<grid_small, kThreads, 0, s>>>(a);
+            LAUNCHED();
         }
-        Ctr hc[64];
-        CK(cudaMemcpyAsync(hc, ctr, S * sizeof(Ctr), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&hmoves, d_moves + r, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        for (int j = 0; j < S; j++)
-            if (hc[j].err) fail(SCLAP_ECUDA, "hash table overflow");
-    } catch (...) {
-        cudaStreamSynchronize(side);
-        cudaEventDestroy(ev_fork);
-        cudaEventDestroy(ev_join);
-        cudaStreamDestroy(side);
-        throw;
+        done = r + 1;
+        if (moves_out) moves_out->push_back(hmoves);
+        if (hmoves == 0) break;
     }
-    CK(cudaStreamSynchronize(side));
-    CK(cudaEventDestroy(ev_fork));
-    CK(cudaEventDestroy(ev_join));
-    CK(cudaStreamDestroy(side));
+    Ctr hc[32];
+    CK(cudaMemcpyAsync(hc, ctr, S * sizeof(Ctr), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int j = 0; j < S; j++)
+        if (hc[j].err) fail(SCLAP_ECUDA, "hash table overflow");
     return done;
 }
 

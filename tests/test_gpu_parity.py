@@ -36,6 +36,9 @@ GRAPHS = {
     "weighted": lambda: I.random_graph(3000, 12000, seed=5, max_w=20, max_c=9),
     "rmat14": lambda: I.rmat(14, 16, seed=2),
     "star5k": lambda: star(5000),                # hub beyond shared memory
+    "stars": lambda: I.csr_from_edges(                # hubs of 600, 1600 and 3100 leaves
+        5303, torch.cat([torch.zeros(600), torch.ones(1600), torch.full((3100,), 2)]).long(),
+        torch.arange(3, 5303), (torch.arange(5300) % 7 + 1)),
     "sparse": lambda: I.random_graph(4000, 1500, seed=9),  # many isolated nodes
 }
 
@@ -80,7 +83,7 @@ def test_cluster_isolated_packing_with_constraint():
         assert np.array_equal(got.cpu().numpy(), want), U
 
 
-@pytest.mark.parametrize("name", ["chunglu2k", "weighted", "rmat14", "star5k"])
+@pytest.mark.parametrize("name", ["chunglu2k", "weighted", "rmat14", "star5k", "stars"])
 @pytest.mark.parametrize("k", [2, 16, 64, 100])
 def test_refine_matches_oracle(name, k):
     g = GRAPHS[name]()
