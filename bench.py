@@ -184,6 +184,50 @@ def cpu_baseline(cfg, budget_s=20.0):
                       f"{dt:.2f} s each"}
 
 
+def run_phase(args, cfg, S, I, g, n, m, dev):
+    """Times one SCLaP phase on the input graph: `cluster` (l rounds, U as in
+    the multilevel driver) or `refine` (r rounds from a seeded random k-way
+    assignment).  Reports SCLaP edges/s = rounds x m / time."""
+    import torch
+    k = cfg["k"]
+    if args.op == "cluster":
+        U = max(1, n // (10 * k))
+        rounds = cfg["cluster_rounds"]
+        fn = lambda: S.sclap_cluster(g, U, rounds, cfg["subrounds"], cfg["seed"])
+    else:
+        p0 = (I.rand_below(cfg["seed"], 7, torch.arange(n, device=dev), k)).to(torch.int32)
+        rounds = cfg["refine_rounds"]
+        fn = lambda: S.sclap_refine(g, k, cfg["eps"], rounds, cfg["subrounds"], cfg["seed"], p0)
+    S.set_validation(False)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    S.prof_enable(True)
+    S.prof_reset()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    done = 0
+    for _ in range(args.steps):
+        out = fn()
+        done += out[1] if args.op == "cluster" else out[3]
+    t1.record()
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1) / args.steps
+    prof = S.prof_read()
+    S.prof_enable(False)
+    peak, kind = measured_peaks()
+    ach = prof["propose_bytes"] / (prof["propose_ms"] / 1e3) / 1e9 if prof["propose_ms"] else 0
+    line = {"op": args.op, "scale": cfg["scale"], "n": n, "m": m, "ms_per_call": ms,
+            "rounds_per_call": done / args.steps,
+            "sclap_gteps": done / args.steps * m / (ms / 1e3) / 1e9,
+            "propose": {"launches": prof["propose_launches"], "ms": prof["propose_ms"],
+                        "achieved_gbs": ach, "frac": ach / peak, "peak_kind": kind,
+                        "bytes": prof["propose_bytes"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +237,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling)")
     ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
+    ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine"],
+                    help="time one SCLaP phase on the input graph instead (profiling aid)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
     if args.scale:
@@ -226,6 +272,8 @@ def main():
             torch.distributed.barrier()
 
     part = torch.empty(n, dtype=torch.int32, device=dev)
+    if args.op != "multilevel":
+        return run_phase(args, cfg, S, I, g, n, m, dev)
     for _ in range(args.warmup):
         S.partition_multilevel(g, params, part_out=part)
 

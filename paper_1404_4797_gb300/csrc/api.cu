@@ -68,42 +68,50 @@ __global__ void k_validate_nodes(DGraph g, int *bad) {
         if (g.xadj[0] != 0 || g.xadj[g.n] != g.nnz) atomicOr(bad, 1);
 }
 
-__device__ __forceinline__ int64_t ub64(const int64_t *a, int64_t lo, int64_t hi, int64_t x) {
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] <= x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
+// Entry checks (xadj already known to be monotone): ids in range, no
+// self-loops, omega > 0, rows strictly ascending; symmetry (every (v, u, w)
+// has its mirror (u, v, w)) through a fingerprint: the wrapping sums of
+// mix64 over (v, u, w) and over (u, v, w) must agree (a mismatch escapes with
+// probability about 2^-64).
+constexpr int kValTile = 4096;
+
+__device__ __forceinline__ uint64_t entry_fp(uint64_t a, uint64_t b, uint64_t w) {
+    return mix64(mix64((a << 32) | b) ^ (w * 0x9E3779B97F4A7C15ull));
 }
 
-// Entry checks (xadj already known to be monotone): ids in range, no
-// self-loops, omega > 0, rows strictly ascending, mirror entry present with
-// the same weight.
-__global__ void k_validate_entries(DGraph g, int *bad) {
-    const int64_t runs = ceil_div<int64_t>(g.nnz, 16);
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < runs;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t e = r * 16, e1 = min64(g.nnz, e + 16);
-        int64_t v = ub64(g.xadj, 0, g.n + 1, e) - 1;
-        for (; e < e1; e++) {
-            while (e >= g.xadj[v + 1]) v++;
-            int32_t u = g.adjncy[e];
-            int32_t w = g.adjwgt[e];
-            if (u < 0 || u >= g.n || u == v || w <= 0) { atomicOr(bad, 1); return; }
-            if (e > g.xadj[v] && g.adjncy[e - 1] >= u) { atomicOr(bad, 1); return; }
-            // mirror (u, v) by binary search in row u
-            int64_t lo = g.xadj[u], hi = g.xadj[u + 1];
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if (g.adjncy[mid] < v) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo >= g.xadj[u + 1] || g.adjncy[lo] != v || g.adjwgt[lo] != w) {
-                atomicOr(bad, 1);
-                return;
-            }
+__global__ void __launch_bounds__(256) k_validate_entries(DGraph g, int *bad,
+                                                          unsigned long long *fp /* [2] */) {
+    __shared__ int32_t rowof[kValTile];
+    __shared__ int32_t tmp[16];
+    const int64_t tiles = ceil_div<int64_t>(g.nnz, kValTile);
+    unsigned long long f0 = 0, f1 = 0;
+    int err = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kValTile;
+        const int len = (int)min64(kValTile, g.nnz - e0);
+        block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
+        for (int i = threadIdx.x; i < len; i += 256) {
+            const int64_t e = e0 + i;
+            const int32_t v = rowof[i];
+            const int32_t u = g.adjncy[e];
+            const int32_t w = g.adjwgt[e];
+            if (u < 0 || u >= g.n || u == v || w <= 0) err = 1;
+            if (e > g.xadj[v] && g.adjncy[e - 1] >= u) err = 1;
+            f0 += entry_fp((uint32_t)v, (uint32_t)u, (uint32_t)w);
+            f1 += entry_fp((uint32_t)u, (uint32_t)v, (uint32_t)w);
         }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        f0 += __shfl_down_sync(0xffffffffu, f0, d);
+        f1 += __shfl_down_sync(0xffffffffu, f1, d);
+        err |= __shfl_down_sync(0xffffffffu, err, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&fp[0], f0);
+        atomicAdd(&fp[1], f1);
+        if (err) atomicOr(bad, 1);
     }
 }
 
@@ -122,11 +130,15 @@ void validate_graph(const DGraph &g, Scratch &sc) {
     CK(cudaStreamSynchronize(s));
     if (h) fail(SCLAP_EGRAPH, "xadj / vwgt");
     if (g.nnz > 0) {
-        k_validate_entries<<<grid, 256, 0, s>>>(g, bad);
+        unsigned long long *fp = sc.zeros<unsigned long long>(2);
+        const int vgrid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kValTile), grid);
+        k_validate_entries<<<vgrid, 256, 0, s>>>(g, bad, fp);
         LAUNCHED();
+        unsigned long long hf[2];
         CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hf, fp, sizeof(hf), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (h) fail(SCLAP_EGRAPH, "adjacency");
+        if (h || hf[0] != hf[1]) fail(SCLAP_EGRAPH, "adjacency");
     }
 }
 
@@ -188,34 +200,38 @@ __global__ void k_lpt_keys2(int64_t n, int64_t P, const int32_t *idx, const int3
     }
 }
 
-// One block per individual t: nodes in sorted order go to the lightest block
-// (lowest id on ties).  Sequential by nature; one warp does the argmin.
+// One warp per individual t: nodes in sorted order go to the lightest block
+// (lowest id on ties).  Sequential by nature: block weights live in shared
+// memory, 32 upcoming nodes are prefetched per lane, and the argmin is two
+// warp reductions (weights fit 32 bits: c(V) <= INT32_MAX is checked).
 __global__ void k_lpt_assign(int64_t n, int32_t k, const int32_t *order, const int32_t *vwgt,
                              int32_t *upart) {
-    extern __shared__ int64_t bw[];
+    extern __shared__ unsigned bw[];
     const int64_t t = blockIdx.x;
     const int lane = threadIdx.x;
     for (int b = lane; b < k; b += 32) bw[b] = 0;
     __syncwarp();
     const int32_t *ord = order + t * n;
-    for (int64_t i = 0; i < n; i++) {
-        int64_t u = ord[i];
-        int64_t v = u - t * n;
-        int64_t bestw = INT64_MAX;
-        int bestb = 0x7fffffff;
-        for (int b = lane; b < k; b += 32)
-            if (bw[b] < bestw) { bestw = bw[b]; bestb = b; }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            int64_t ow = __shfl_xor_sync(0xffffffffu, bestw, d);
-            int ob = __shfl_xor_sync(0xffffffffu, bestb, d);
-            if (ow < bestw || (ow == bestw && ob < bestb)) { bestw = ow; bestb = ob; }
+    for (int64_t i0 = 0; i0 < n; i0 += 32) {
+        const int64_t i = i0 + lane;
+        int32_t u = 0, c = 0;
+        if (i < n) {
+            u = ord[i];
+            c = vwgt[u - t * n];
         }
-        if (lane == 0) {
-            upart[u] = (int32_t)(t * k + bestb);
-            bw[bestb] += vwgt[v];
+        const int cnt = (int)min64(32, n - i0);
+        for (int j = 0; j < cnt; j++) {
+            const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+            const int32_t cj = __shfl_sync(0xffffffffu, c, j);
+            unsigned wmin = 0xffffffffu, bmin = 0xffffffffu;
+            for (int b = lane; b < k; b += 32)
+                if (bw[b] < wmin) { wmin = bw[b]; bmin = (unsigned)b; }
+            const unsigned gw = __reduce_min_sync(0xffffffffu, wmin);
+            const unsigned gb = __reduce_min_sync(0xffffffffu, wmin == gw ? bmin : 0xffffffffu);
+            if (lane == (int)(gb & 31)) bw[gb] += (unsigned)cj;
+            if (lane == 0) upart[uj] = (int32_t)(t * k + gb);
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -289,7 +305,8 @@ InitResult initial_impl(const DGraph &g, int32_t k, int64_t B, int32_t P, int32_
     k_lpt_keys2<<<grid, 256, 0, s>>>(n, P, idx, g.vwgt, cb, tot.maxc, key);
     LAUNCHED();
     radix_sort_pairs(key, idx, un, cb + tb, sc);
-    k_lpt_assign<<<P, 32, k * sizeof(int64_t), s>>>(n, k, idx, g.vwgt, up);
+    if (tot.cV > INT32_MAX) fail(SCLAP_EOVERFLOW, "c(V)");
+    k_lpt_assign<<<P, 32, k * sizeof(unsigned), s>>>(n, k, idx, g.vwgt, up);
     LAUNCHED();
     // refine all individuals together on the disjoint union
     DGraph ug{un, unnz, ux, ua, uw, uc};
@@ -303,7 +320,6 @@ InitResult initial_impl(const DGraph &g, int32_t k, int64_t B, int32_t P, int32_
     cfg.seed = seed;
     cfg.rounds = rounds;
     cfg.S = S;
-    cfg.max_deg = tot.max_deg;
     lp_run(cfg, sc, nullptr, nullptr);
     int64_t *d_cut = sc.get<int64_t>(P);
     int64_t *d_bw = sc.get<int64_t>((int64_t)k * P);
@@ -400,7 +416,6 @@ int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subr
         cfg.seed = seed;
         cfg.rounds = rounds;
         cfg.S = subrounds;
-        cfg.max_deg = t.max_deg;
         int rd = 0;
         if (rounds > 0 && g.n > 0) rd = lp_run(cfg, sc, nullptr, nullptr);
         else identity_labels(g.n, labels_out, s);
@@ -422,7 +437,7 @@ int sclap_refine_bound(const sclap_graph *gp, int32_t nblocks, int64_t B, int32_
         DGraph g = view(gp);
         validate_graph(g, sc);
         if (!in_range(g.n, part_inout, nblocks, sc)) fail(SCLAP_EINVAL, "part out of range");
-        GraphTotals t = graph_totals(g, sc);
+        GraphTotals t = graph_totals(g, sc, true);
         if (t.max_wdeg > INT32_MAX) fail(SCLAP_EOVERFLOW, "weighted degree");
         CK(cudaMalloc(&backup, (g.n ? g.n : 1) * sizeof(int32_t)));
         CK(cudaMemcpyAsync(backup, part_inout, g.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
@@ -435,7 +450,6 @@ int sclap_refine_bound(const sclap_graph *gp, int32_t nblocks, int64_t B, int32_
         cfg.seed = seed;
         cfg.rounds = rounds;
         cfg.S = subrounds;
-        cfg.max_deg = t.max_deg;
         int rd = lp_run(cfg, sc, nullptr, nullptr);
         CK(cudaStreamSynchronize(s));
         if (rounds_done) *rounds_done = rd;
@@ -561,7 +575,7 @@ int sclap_initial_partition(const sclap_graph *gp, int32_t k, int64_t B, int32_t
         Scratch sc(s);
         DGraph g = view(gp);
         validate_graph(g, sc);
-        GraphTotals t = graph_totals(g, sc);
+        GraphTotals t = graph_totals(g, sc, true);
         if (t.max_wdeg > INT32_MAX) fail(SCLAP_EOVERFLOW, "weighted degree");
         InitResult r = initial_impl(g, k, B, P, rounds, subrounds, seed, part_out, sc);
         if (cuts_out) std::memcpy(cuts_out, r.cuts.data(), P * sizeof(int64_t));
@@ -610,7 +624,6 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
         std::memset(&st, 0, sizeof(st));
         std::vector<DGraph> G{g0};
         std::vector<int32_t *> F;  // f2c per level
-        std::vector<int64_t> maxdeg{t0.max_deg};
         int L = 0;
         while (G[L].n >= p->n_stop && L + 1 < maxl && G[L].n > 0) {
             const DGraph &g = G[L];
@@ -625,7 +638,6 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
             cfg.seed = level_seed(p->seed, L);
             cfg.rounds = p->cluster_rounds;
             cfg.S = p->subrounds;
-            cfg.max_deg = maxdeg[L];
             int rd = 0;
             if (cfg.rounds > 0) rd = lp_run(cfg, tmp, nullptr, nullptr);
             else identity_labels(g.n, lab, s);
@@ -638,7 +650,6 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
             F.push_back(f2c);
             DGraph c{cg.n, cg.nnz, cg.xadj, cg.adjncy, cg.adjwgt, cg.vwgt};
             G.push_back(c);
-            maxdeg.push_back(graph_totals(c, tmp).max_deg);
             L++;
             if (20 * G[L].n > 19 * G[L - 1].n) break;  // stalled (< 5% shrink)
         }
@@ -664,7 +675,6 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
             cfg.seed = level_seed(p->seed, l);
             cfg.rounds = p->refine_rounds;
             cfg.S = p->subrounds;
-            cfg.max_deg = maxdeg[l];
             st.refine_rounds_done[l] = lp_run(cfg, tmp, nullptr, nullptr);
         }
         // final cut and balance

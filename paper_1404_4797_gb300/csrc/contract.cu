@@ -307,37 +307,31 @@ void project_impl(int64_t n, const int32_t *f2c, const int32_t *cp, int32_t *fp,
 
 // ---------------------------------------------------------------- cut / balance
 
-// Each thread scans a run of kCutRun consecutive entries; the row of the
-// first entry comes from a binary search over xadj.
-constexpr int kCutRun = 16;
+// Entries in tiles of kCutTile; block_rows gives each entry's row.
+constexpr int kCutTile = 4096;
 
-__global__ void k_cut(DGraph g, const int32_t *part, int64_t n_group, int64_t groups,
-                      unsigned long long *cut) {
-    const int64_t runs = ceil_div<int64_t>(g.nnz, kCutRun);
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < runs;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t e = r * kCutRun;
-        const int64_t e1 = min64(g.nnz, e + kCutRun);
-        int64_t v = upper_bound_i64(g.xadj, 0, g.n + 1, e) - 1;
-        int64_t vend = g.xadj[v + 1];
-        int32_t pv = part[v];
-        int64_t grp = groups > 1 ? v / n_group : 0;
-        int64_t acc = 0;
-        for (; e < e1; e++) {
-            while (e >= vend) {
-                v++;
-                vend = g.xadj[v + 1];
-                pv = part[v];
-                int64_t ng = groups > 1 ? v / n_group : 0;
-                if (ng != grp) {
-                    if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
-                    acc = 0;
-                    grp = ng;
-                }
+__global__ void __launch_bounds__(256) k_cut(DGraph g, const int32_t *part, int64_t n_group,
+                                             int64_t groups, unsigned long long *cut) {
+    __shared__ int32_t rowof[kCutTile];
+    __shared__ int32_t tmp[16];
+    const int64_t tiles = ceil_div<int64_t>(g.nnz, kCutTile);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kCutTile;
+        const int len = (int)min64(kCutTile, g.nnz - e0);
+        block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
+        int64_t grp = -1, acc = 0;
+        for (int i = threadIdx.x; i < len; i += 256) {
+            const int32_t v = rowof[i];
+            const int64_t gv = groups > 1 ? v / n_group : 0;
+            if (gv != grp) {
+                if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
+                acc = 0;
+                grp = gv;
             }
-            if (part[g.adjncy[e]] != pv) acc += g.adjwgt[e];
+            if (part[g.adjncy[e0 + i]] != part[v]) acc += g.adjwgt[e0 + i];
         }
         if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
+        __syncthreads();
     }
 }
 
@@ -369,7 +363,8 @@ void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t gro
     CK(cudaMemsetAsync(d_cut, 0, groups * sizeof(int64_t), s));
     if (d_bw) CK(cudaMemsetAsync(d_bw, 0, nblocks * sizeof(int64_t), s));
     if (g.nnz > 0) {
-        k_cut<<<grid, 256, 0, s>>>(g, part, n_group, groups, (unsigned long long *)d_cut);
+        const int cgrid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kCutTile), grid);
+        k_cut<<<cgrid, 256, 0, s>>>(g, part, n_group, groups, (unsigned long long *)d_cut);
         LAUNCHED();
         k_halve<<<1, 256, 0, s>>>((unsigned long long *)d_cut, groups);
         LAUNCHED();

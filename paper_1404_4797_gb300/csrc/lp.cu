@@ -123,6 +123,9 @@ struct LPArgs {
     int32_t *gvals;
     int32_t *gdl;
     int32_t *gacc;          // dense: [nL * k]
+    const int64_t *Hfin;    // hash: selection items of multi-piece rows [nL + 1]
+    unsigned long long *hbest;
+    int32_t *hbestL, *hown;
     unsigned long long *prof;  // [2] entries, nodes, or null
 };
 
@@ -472,7 +475,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
             if (threadIdx.x == 0) decide_and_emit<MODE>(a, sm.W, sm.nd, 0);
             continue;
         }
-        // merge the piece into the node's global table
+        // merge the piece into the row's global state
         if constexpr (DENSE) {
             int32_t *gacc = a.gacc + li * k;
             for (int b = threadIdx.x; b < k; b += kThreads) {
@@ -482,52 +485,66 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                     sm.t.acc[b] = 0;
                 }
             }
-        } else {
-            const int ndl = sm.ndl;
-            const int64_t off = a.Loff[li];
-            const uint32_t cap = (uint32_t)(a.Loff[li + 1] - off);
-            const int bits = 31 - __clz((int)cap);
-            int32_t *gdl = a.gdl + a.Ldlo[li];
-            for (int i = threadIdx.x; i < ndl; i += kThreads) {
-                const int slot = sm.t.dl[i];
-                const uint64_t key = sm.t.keys[slot];
-                const int32_t w = sm.t.vals[slot];
-                sm.t.keys[slot] = kEmpty;
-                sm.t.vals[slot] = 0;
-                if (!table_add(a.gkeys + off, a.gvals + off, gdl, &a.Lndl[li], cap - 1, bits, key, w))
-                    a.ctr->err = 1;
-            }
-        }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) sm.flag = atomicAdd(&a.Ldone[li], 1) == (int)pieces - 1;
-        __syncthreads();
-        if (!sm.flag) continue;
-        // the last piece of this row: select over the merged table
-        __threadfence();
-        if constexpr (DENSE) {
-            int32_t *gacc = a.gacc + li * k;
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) sm.flag = atomicAdd(&a.Ldone[li], 1) == (int)pieces - 1;
+            __syncthreads();
+            if (!sm.flag) continue;
+            // the last piece of this row: select over the k merged sums
+            __threadfence();
             if (threadIdx.x < 32) {
                 for (int b = threadIdx.x; b < k; b += 32) sm.t.acc[b] = atomicExch(&gacc[b], 0);
                 __syncwarp();
                 select_dense_warp(a, sm.W, sm.t.acc, k, sm.nd, 0);
             }
-        } else {
-            const int64_t off = a.Loff[li];
-            int32_t *gdl = a.gdl + a.Ldlo[li];
-            const int ndl = __ldcg(&a.Lndl[li]);
-            select_best<true>(a, a.gkeys + off, a.gvals + off, gdl, ndl, sm.nd);
-            for (int i = threadIdx.x; i < ndl; i += kThreads) {
-                const int slot = __ldcg(&gdl[i]);
-                a.gkeys[off + slot] = kEmpty;
-                a.gvals[off + slot] = 0;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                decide_and_emit<MODE>(a, sm.W, sm.nd, 0);
+                a.Ldone[li] = 0;
             }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            decide_and_emit<MODE>(a, sm.W, sm.nd, 0);
-            a.Ldone[li] = 0;
-            a.Lndl[li] = 0;
+        } else {
+            // hash: insert into the row's global table; the best label is
+            // selected afterwards by k_hub_cand / k_hub_tie / k_hub_emit
+            const int ndl = sm.ndl;
+            const int64_t off = a.Loff[li];
+            const uint32_t cap = (uint32_t)(a.Loff[li + 1] - off);
+            const int bits = 31 - __clz((int)cap);
+            int32_t *gdl = a.gdl + a.Ldlo[li];
+            unsigned long long *gk = a.gkeys + off;
+            int32_t *gv = a.gvals + off;
+            const int lane = threadIdx.x & 31;
+            const int ndl_r = (ndl + 31) & ~31;
+            for (int i = threadIdx.x; i < ndl_r; i += kThreads) {
+                int32_t gslot = -1;
+                if (i < ndl) {
+                    const int slot = sm.t.dl[i];
+                    const uint64_t key = sm.t.keys[slot];
+                    const int32_t w = sm.t.vals[slot];
+                    sm.t.keys[slot] = kEmpty;
+                    sm.t.vals[slot] = 0;
+                    uint32_t q = table_hash(key, bits);
+                    bool placed = false;
+                    for (uint32_t probe = 0; probe < cap; probe++) {
+                        const unsigned long long prev = atomicCAS(&gk[q], kEmpty, key);
+                        if (prev == kEmpty || prev == key) {
+                            atomicAdd(&gv[q], w);
+                            if (prev == kEmpty) gslot = (int32_t)q;
+                            placed = true;
+                            break;
+                        }
+                        q = (q + 1) & (cap - 1);
+                    }
+                    if (!placed) a.ctr->err = 1;
+                }
+                // one append per warp for the slots it inserted first
+                const unsigned m = __ballot_sync(0xffffffffu, gslot >= 0);
+                if (m) {
+                    int base = 0;
+                    if (lane == __ffs(m) - 1) base = atomicAdd(&a.Lndl[li], __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+                    if (gslot >= 0) gdl[base + __popc(m & ((1u << lane) - 1))] = gslot;
+                }
+            }
         }
     }
 }
@@ -1047,6 +1064,141 @@ __global__ void __launch_bounds__(kThreads) k_reset_targets(LPArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- multi-piece rows (hash)
+
+// Rows longer than one piece have their (label, omega) sums merged in a
+// global table by the propose kernel; these three kernels select their best
+// label in parallel: items of kFin distinct entries, enumerated over all
+// multi-piece rows (rows of other sub-rounds are skipped).
+constexpr int kFin = 2048;
+
+struct HubItem {
+    int64_t li;
+    int64_t begin, end;  // distinct-list range of this item
+    bool active;
+};
+
+__device__ __forceinline__ HubItem hub_item(const LPArgs &a, int64_t t, int round) {
+    int64_t lo = 0, hi = a.nL;  // largest li with Hfin[li] <= t
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a.Hfin[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    HubItem it;
+    it.li = lo;
+    const int64_t c = t - a.Hfin[lo];
+    const int64_t ndl = __ldcg(&a.Lndl[lo]);
+    it.begin = c * kFin;
+    it.end = min64(ndl, it.begin + kFin);
+    it.active = colour_of(a.seed, round, a.Lnodes[lo], a.S) == (uint32_t)a.colour &&
+                it.begin < it.end;
+    return it;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
+    __shared__ unsigned long long red[kThreads / 32];
+    const int64_t items = a.Hfin[a.nL];
+    for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+        const HubItem it = hub_item(a, t, a.round);
+        if (!it.active) continue;  // uniform over the CTA
+        const int32_t v = a.Lnodes[it.li];
+        const int32_t own = a.lab[v], c = a.g.vwgt[v];
+        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+        const int64_t off = a.Loff[it.li];
+        const int32_t *gdl = a.gdl + a.Ldlo[it.li];
+        unsigned long long best = 0;
+        for (int64_t i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
+            const int32_t slot = __ldcg(&gdl[i]);
+            const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
+            const int32_t w = __ldcg(&a.gvals[off + slot]);
+            if (L == own) a.hown[it.li] = w;
+            else if (a.W[L] + c <= a.B) {
+                const unsigned long long ck = cand_key(w, h, L);
+                best = ck > best ? ck : best;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+            best = o > best ? o : best;
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kThreads / 32; w++) best = red[w] > best ? red[w] : best;
+            if (best) atomicMax(&a.hbest[it.li], best);
+        }
+        __syncthreads();
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
+    const int64_t items = a.Hfin[a.nL];
+    for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
+        const HubItem it = hub_item(a, t, a.round);
+        if (!it.active) continue;
+        const int32_t v = a.Lnodes[it.li];
+        const int32_t own = a.lab[v], c = a.g.vwgt[v];
+        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+        const int64_t off = a.Loff[it.li];
+        const int32_t *gdl = a.gdl + a.Ldlo[it.li];
+        const unsigned long long b = a.hbest[it.li];
+        for (int64_t i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
+            const int32_t slot = __ldcg(&gdl[i]);
+            const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
+            const int32_t w = __ldcg(&a.gvals[off + slot]);
+            if (b != 0 && L != own && (uint32_t)w == (uint32_t)(b >> 32) && a.W[L] + c <= a.B &&
+                cand_key(w, h, L) == b)
+                atomicMin(&a.hbestL[it.li], L);
+            a.gkeys[off + slot] = kEmpty;
+            a.gvals[off + slot] = 0;
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
+    for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < a.nL;
+         li += (int64_t)gridDim.x * blockDim.x) {
+        if (a.Hfin[li + 1] == a.Hfin[li]) continue;  // single-piece row
+        const int32_t v = a.Lnodes[li];
+        if (colour_of(a.seed, a.round, v, a.S) != (uint32_t)a.colour) continue;
+        const unsigned long long b = a.hbest[li];
+        const int32_t own = a.lab[v];
+        if (b != 0) {
+            const int32_t gain = (int32_t)(b >> 32) - a.hown[li];
+            const bool ovl = MODE != kCluster && a.W[own] > a.B;
+            if (gain > 0 || ovl) {
+                const int32_t L = a.hbestL[li];
+                emit<false>(a, v, L, own, gain, a.g.vwgt[v], ovl, a.W[L]);
+            }
+        }
+        a.hbest[li] = 0;
+        a.hbestL[li] = 0x7fffffff;
+        a.hown[li] = 0;
+        a.Lndl[li] = 0;
+    }
+}
+
+struct HubFin {
+    const int64_t *xadj;
+    const int32_t *Lnodes;
+    __device__ int64_t operator()(int64_t i) const {
+        const int32_t v = Lnodes[i];
+        const int64_t d = xadj[v + 1] - xadj[v];
+        return d <= kChunk ? 0 : ceil_div<int64_t>(d, kFin);
+    }
+};
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = val;
+}
+
 // ---------------------------------------------------------------- large-node lists
 
 struct LargeFlag {
@@ -1303,6 +1455,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.prof = prof().on ? prof().d_counts : nullptr;
 
     // nodes of degree > kMedDeg: one list per call, cut into kChunk pieces
+    int64_t hub_items = 0;
     {
         int64_t *pos = sc.get<int64_t>(g.n);
         int64_t *d_nL = sc.get<int64_t>(1);
@@ -1334,10 +1487,20 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 CK(cudaStreamSynchronize(s));
                 a.Loff = Loff;
                 a.Ldlo = Ldlo;
+                int64_t *Hfin = sc.get<int64_t>(nL + 1);
+                exclusive_scan(HubFin{g.xadj, Lnodes}, nL, Hfin, Hfin + nL, sc);
+                CK(cudaMemcpyAsync(&hub_items, Hfin + nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                a.Hfin = Hfin;
+                a.hbest = sc.zeros<unsigned long long>(nL);
+                a.hown = sc.zeros<int32_t>(nL);
+                a.hbestL = sc.get<int32_t>(nL);
+                k_fill_i32<<<sms, 256, 0, s>>>(a.hbestL, nL, 0x7fffffff);
+                LAUNCHED();
                 a.gkeys = sc.get<unsigned long long>(tot[0]);
                 a.gvals = sc.zeros<int32_t>(tot[0]);
                 a.gdl = sc.get<int32_t>(tot[1]);
                 if (tot[0]) CK(cudaMemsetAsync(a.gkeys, 0xff, tot[0] * sizeof(uint64_t), s));
+                CK(cudaStreamSynchronize(s));
             }
         }
     }
@@ -1377,6 +1540,24 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             }
             LAUNCHED();
             prof_end(s, pb, pe);
+            if (hub_items > 0) {
+                const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
+                switch (mode) {
+                    case kCluster:
+                        k_hub_cand<kCluster><<<hg, kThreads, 0, s>>>(a);
+                        k_hub_tie<kCluster><<<hg, kThreads, 0, s>>>(a);
+                        k_hub_emit<kCluster><<<sms, kThreads, 0, s>>>(a);
+                        break;
+                    default:
+                        k_hub_cand<kRefineHash><<<hg, kThreads, 0, s>>>(a);
+                        k_hub_tie<kRefineHash><<<hg, kThreads, 0, s>>>(a);
+                        k_hub_emit<kRefineHash><<<sms, kThreads, 0, s>>>(a);
+                        break;
+                }
+                LAUNCHED();
+                LAUNCHED();
+                LAUNCHED();
+            }
             if (cfg.refine) {
                 k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, s>>>(a);
                 LAUNCHED();

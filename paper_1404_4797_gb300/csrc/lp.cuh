@@ -16,7 +16,6 @@ struct LPConfig {
     const int32_t *cp;     // V-cycle constraint partition (clustering only) or null
     uint64_t seed;
     int32_t rounds, S;
-    int64_t max_deg;       // maximum degree of g (sizes the hub tables)
 };
 
 // Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)

@@ -181,81 +181,99 @@ void radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, Scrat
 // ---------------------------------------------------------------- graph totals
 
 __global__ void k_totals(DGraph g, unsigned long long *acc /* [5] */) {
-    int64_t cV = 0, maxc = 0, sw = 0, maxwd = 0, maxd = 0;
+    int64_t cV = 0, maxc = 0, sw = 0, maxd = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        int64_t c = g.vwgt[v];
+        const int64_t c = g.vwgt[v];
         cV += c;
-        maxc = max(maxc, c);
-        int64_t b = g.xadj[v], e = g.xadj[v + 1];
-        maxd = max(maxd, e - b);
+        maxc = max64(maxc, c);
+        maxd = max64(maxd, g.xadj[v + 1] - g.xadj[v]);
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nnz;
          i += (int64_t)gridDim.x * blockDim.x)
         sw += g.adjwgt[i];
-    // weighted degree: one warp per node would be exact but slow; bound it by
-    // a per-row sum computed with a thread per node (only rows <= 4096 long
-    // are summed here; longer rows are summed by k_row_wsum below).
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = g.xadj[v], e = g.xadj[v + 1];
-        if (e - b > 4096) continue;
-        int64_t s = 0;
-        for (int64_t i = b; i < e; i++) s += g.adjwgt[i];
-        maxwd = max(maxwd, s);
-    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         cV += __shfl_down_sync(0xffffffffu, cV, d);
         sw += __shfl_down_sync(0xffffffffu, sw, d);
-        maxc = max(maxc, __shfl_down_sync(0xffffffffu, maxc, d));
-        maxwd = max(maxwd, __shfl_down_sync(0xffffffffu, maxwd, d));
-        maxd = max(maxd, __shfl_down_sync(0xffffffffu, maxd, d));
+        maxc = max64(maxc, __shfl_down_sync(0xffffffffu, maxc, d));
+        maxd = max64(maxd, __shfl_down_sync(0xffffffffu, maxd, d));
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&acc[0], (unsigned long long)cV);
         atomicMax(&acc[1], (unsigned long long)maxc);
         atomicAdd(&acc[2], (unsigned long long)sw);
-        atomicMax(&acc[3], (unsigned long long)maxwd);
         atomicMax(&acc[4], (unsigned long long)maxd);
     }
 }
 
-// Weighted degree of long rows: one block per such row.
-__global__ void k_row_wsum(DGraph g, unsigned long long *acc) {
-    for (int64_t v = blockIdx.x; v < g.n; v += gridDim.x) {
-        int64_t b = g.xadj[v], e = g.xadj[v + 1];
-        if (e - b <= 4096) continue;
-        int64_t s = 0;
-        for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) s += g.adjwgt[i];
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-        __shared__ int64_t part[32];
-        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t t = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
-            atomicMax(&acc[3], (unsigned long long)t);
+// Exact weighted degrees (only needed when the total edge weight exceeds the
+// 32-bit range): per-entry sums into wdeg[row], aggregated per warp and row.
+constexpr int kWdegTile = 4096;
+
+__global__ void __launch_bounds__(256) k_wdeg(DGraph g, unsigned long long *wdeg) {
+    __shared__ int32_t rowof[kWdegTile];
+    __shared__ int32_t tmp[16];
+    const int64_t tiles = ceil_div<int64_t>(g.nnz, kWdegTile);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kWdegTile;
+        const int len = (int)min64(kWdegTile, g.nnz - e0);
+        block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
+        const int lanes = (len + 31) & ~31;
+        for (int i = threadIdx.x; i < lanes; i += 256) {
+            const bool in = i < len;
+            const int32_t v = in ? rowof[i] : -1 - (int32_t)(threadIdx.x & 31);
+            const unsigned peers = __match_any_sync(0xffffffffu, v);
+            int64_t w = in ? g.adjwgt[e0 + i] : 0;
+            int64_t s = 0;
+            for (unsigned m = peers; m; m &= m - 1) s += __shfl_sync(peers, w, __ffs(m) - 1);
+            if (in && (peers & ((1u << (threadIdx.x & 31)) - 1)) == 0)
+                atomicAdd(&wdeg[v], (unsigned long long)s);
         }
         __syncthreads();
     }
 }
 
-GraphTotals graph_totals(const DGraph &g, Scratch &sc) {
+__global__ void k_max_u64(const unsigned long long *x, int64_t n, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = x[i] > m ? x[i] : m;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, m, d);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+GraphTotals graph_totals(const DGraph &g, Scratch &sc, bool need_wdeg) {
     cudaStream_t s = sc.stream();
     unsigned long long *acc = sc.zeros<unsigned long long>(5);
-    int sms = dev_info().sms;
+    const int sms = dev_info().sms;
     if (g.n > 0) {
         k_totals<<<sms * 4, 256, 0, s>>>(g, acc);
-        LAUNCHED();
-        k_row_wsum<<<sms * 2, 256, 0, s>>>(g, acc);
         LAUNCHED();
     }
     unsigned long long h[5];
     CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return GraphTotals{(int64_t)h[0], (int64_t)h[1], (int64_t)h[2], (int64_t)h[3], (int64_t)h[4]};
+    GraphTotals t{(int64_t)h[0], (int64_t)h[1], (int64_t)h[2], (int64_t)h[2], (int64_t)h[4]};
+    // every weighted degree is at most the total; compute it exactly only when
+    // the total alone does not settle the 32-bit check
+    if (need_wdeg && t.sum_w > INT32_MAX && g.nnz > 0) {
+        unsigned long long *wdeg = sc.zeros<unsigned long long>(g.n);
+        const int grid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kWdegTile), sms * 8);
+        k_wdeg<<<grid, 256, 0, s>>>(g, wdeg);
+        LAUNCHED();
+        k_max_u64<<<sms * 4, 256, 0, s>>>(wdeg, g.n, acc + 3);
+        LAUNCHED();
+        unsigned long long m = 0;
+        CK(cudaMemcpyAsync(&m, acc + 3, sizeof(m), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        t.max_wdeg = (int64_t)m;
+    }
+    return t;
 }
 
 }  // namespace sclap

@@ -133,6 +133,82 @@ inline int bit_width_u64(uint64_t x) {
     return b;
 }
 
+// ---------------------------------------------------------------- entry -> row
+
+// For the entry range [e0, e0 + len) (len <= NT * PER) of a CSR with row
+// offsets xadj[0..n], writes rowof[i] = the row containing entry e0 + i.
+// Rows are found once per range (two binary searches); each row start inside
+// the range marks its position (the largest row id wins, skipping empty
+// rows), and an inclusive max-scan spreads the row ids.  All threads call it.
+template <int NT, int PER>
+__device__ void block_rows(const int64_t *xadj, int64_t n, int64_t e0, int len, int32_t *rowof,
+                           int32_t *scan_tmp /* >= NT/32 + 2 */) {
+    __shared__ int64_t s_rows[2];
+    if (threadIdx.x == 0) {
+        // first row: largest v with xadj[v] <= e0; last: largest v with xadj[v] <= e0+len-1
+        int64_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (xadj[mid] <= e0) lo = mid;
+            else hi = mid;
+        }
+        s_rows[0] = lo;
+        int64_t lo2 = lo, hi2 = n;
+        const int64_t eL = e0 + len - 1;
+        while (hi2 - lo2 > 1) {
+            const int64_t mid = (lo2 + hi2) >> 1;
+            if (xadj[mid] <= eL) lo2 = mid;
+            else hi2 = mid;
+        }
+        s_rows[1] = lo2;
+    }
+    for (int i = threadIdx.x; i < len; i += NT) rowof[i] = -1;
+    __syncthreads();
+    const int64_t v0 = s_rows[0], v1 = s_rows[1];
+    if (threadIdx.x == 0) atomicMax(&rowof[0], (int32_t)v0);
+    for (int64_t v = v0 + 1 + threadIdx.x; v <= v1; v += NT) {
+        const int64_t p = xadj[v] - e0;
+        if (p >= 0 && p < len) atomicMax(&rowof[p], (int32_t)v);
+    }
+    __syncthreads();
+    // inclusive max-scan over rowof (thread t owns [t*PER, (t+1)*PER))
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t run = -1;
+    const int base = threadIdx.x * PER;
+#pragma unroll
+    for (int j = 0; j < PER; j++)
+        if (base + j < len) run = max(run, rowof[base + j]);
+    int32_t inc = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc = max(inc, y);
+    }
+    if (lane == 31) scan_tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < NT / 32 ? scan_tmp[lane] : -1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w = max(w, y);
+        }
+        if (lane < NT / 32) scan_tmp[lane] = w;
+    }
+    __syncthreads();
+    int32_t pre = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) pre = -1;
+    if (warp > 0) pre = max(pre, scan_tmp[warp - 1]);
+    int32_t cur = pre;
+#pragma unroll
+    for (int j = 0; j < PER; j++)
+        if (base + j < len) {
+            cur = max(cur, rowof[base + j]);
+            rowof[base + j] = cur;
+        }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- reductions
 
 // Device-side sums / maxima used for validation and bounds (results to host).
@@ -140,9 +216,11 @@ struct GraphTotals {
     int64_t cV;          // sum of c
     int64_t maxc;        // max c
     int64_t sum_w;       // sum of omega over all directed entries
-    int64_t max_wdeg;    // max weighted degree
+    int64_t max_wdeg;    // max weighted degree (an upper bound unless computed exactly)
     int64_t max_deg;     // max degree
 };
-GraphTotals graph_totals(const DGraph &g, Scratch &sc);
+// need_wdeg: make max_wdeg exact when the total edge weight is above INT32_MAX
+// (otherwise the total is reported as the bound).
+GraphTotals graph_totals(const DGraph &g, Scratch &sc, bool need_wdeg = false);
 
 }  // namespace sclap
