@@ -60,6 +60,8 @@ constexpr int kMedItem = 64;             // medium worklist nodes per CTA item
 constexpr int kDenseMaxK = 64;
 constexpr int kClasses = 5;              // buckets per colour
 constexpr int kSegSmem = 2048;           // contested segments staged in shared memory
+constexpr int kUnroll = 4;               // entries in flight per thread
+constexpr int kAggW = 1024;              // label weights aggregated in shared memory up to this
 constexpr uint64_t kEmpty = ~0ull;
 
 static_assert((1 << kSlotBits) == kSlots, "table size");
@@ -123,6 +125,9 @@ struct LPArgs {
     int32_t *gvals;
     int32_t *gdl;
     int32_t *gacc;          // dense: [nL * k]
+    int64_t *plist;         // per-colour piece lists: colour c at plist + c * Ptot
+    int32_t *pcnt;          // their lengths
+    int64_t Ptot;
     const int64_t *Hfin;    // hash: selection items of multi-piece rows [nL + 1]
     unsigned long long *hbest;
     int32_t *hbestL, *hown;
@@ -158,15 +163,59 @@ __device__ __forceinline__ void apply_move(const LPArgs &a, int32_t v, int32_t T
     atomicAdd((unsigned long long *)&a.W[own], (unsigned long long)(-(int64_t)c));
 }
 
+// Weight deltas of applied moves: with few labels (refinement) they collect in
+// shared memory and are flushed once per CTA; otherwise moves into and out of
+// the same label are merged per warp (labelled partitions) before the global
+// atomics.
+struct WDelta {
+    long long d[kAggW];
+};
+
+__device__ __forceinline__ void wd_init(WDelta &wd, int64_t nW) {
+    if (nW <= kAggW)
+        for (int i = threadIdx.x; i < nW; i += blockDim.x) wd.d[i] = 0;
+    __syncthreads();
+}
+
+// Applies a move (label write, weight delta).  Called by moving threads only.
+__device__ __forceinline__ void apply_agg(const LPArgs &a, WDelta &wd, int32_t v, int32_t T,
+                                          int32_t own, int32_t c) {
+    a.lab[v] = T;
+    if (a.nW <= kAggW) {
+        atomicAdd((unsigned long long *)&wd.d[T], (unsigned long long)(long long)c);
+        atomicAdd((unsigned long long *)&wd.d[own], (unsigned long long)(-(long long)c));
+        return;
+    }
+    cg::coalesced_group g = cg::coalesced_threads();
+    {
+        cg::coalesced_group t = cg::labeled_partition(g, (unsigned)T);
+        const long long sum = cg::reduce(t, (long long)c, cg::plus<long long>());
+        if (t.thread_rank() == 0) atomicAdd((unsigned long long *)&a.W[T], (unsigned long long)sum);
+    }
+    {
+        cg::coalesced_group o = cg::labeled_partition(g, (unsigned)own);
+        const long long sum = cg::reduce(o, (long long)c, cg::plus<long long>());
+        if (o.thread_rank() == 0) atomicAdd((unsigned long long *)&a.W[own], (unsigned long long)(-sum));
+    }
+}
+
+__device__ __forceinline__ void wd_flush(const LPArgs &a, WDelta &wd) {
+    __syncthreads();
+    if (a.nW <= kAggW)
+        for (int i = threadIdx.x; i < a.nW; i += blockDim.x)
+            if (wd.d[i]) atomicAdd((unsigned long long *)&a.W[i], (unsigned long long)wd.d[i]);
+}
+
 // ---------------------------------------------------------------- worklists
 
 __device__ __forceinline__ int degree_class(int64_t d) {
     return d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= kSmallDeg ? 3 : 4;
 }
 
-__global__ void __launch_bounds__(kThreads)
-    k_build_wl(DGraph g, uint64_t seed, int32_t round, int32_t S, int32_t *wl, int32_t *cnt) {
+__global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, int32_t *cnt) {
     __shared__ int lcnt[32 * kClasses], lbase[32 * kClasses];
+    const DGraph &g = a.g;
+    const int S = a.S;
     const int nb = kClasses * S;
     for (int64_t tile = (int64_t)blockIdx.x * kThreads * 4; tile < g.n;
          tile += (int64_t)gridDim.x * kThreads * 4) {
@@ -176,15 +225,29 @@ __global__ void __launch_bounds__(kThreads)
         int32_t vv[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            int64_t v = tile + (int64_t)j * kThreads + threadIdx.x;
+            const int64_t v = tile + (int64_t)j * kThreads + threadIdx.x;
             bk[j] = -1;
             vv[j] = (int32_t)v;
             if (v < g.n) {
-                int64_t d = g.xadj[v + 1] - g.xadj[v];
-                if (d > 0 && d <= kMedDeg) {
-                    uint32_t col = colour_of(seed, round, (int32_t)v, S);
-                    bk[j] = kClasses * (int)col + degree_class(d);
-                    rk[j] = atomicAdd(&lcnt[bk[j]], 1);
+                const int64_t d = g.xadj[v + 1] - g.xadj[v];
+                if (d > 0) {
+                    const uint32_t col = colour_of(a.seed, a.round, (int32_t)v, S);
+                    if (d <= kMedDeg) {
+                        bk[j] = kClasses * (int)col + degree_class(d);
+                        rk[j] = atomicAdd(&lcnt[bk[j]], 1);
+                    } else {
+                        // a large row: list its pieces for sub-round `col`
+                        int64_t lo = 0, hi = a.nL;  // li: Lnodes[li] == v
+                        while (hi - lo > 1) {
+                            const int64_t mid = (lo + hi) >> 1;
+                            if (a.Lnodes[mid] <= v) lo = mid;
+                            else hi = mid;
+                        }
+                        const int64_t np = a.Lpre[lo + 1] - a.Lpre[lo];
+                        const int base = atomicAdd(&a.pcnt[col], (int)np);
+                        int64_t *pl = a.plist + (int64_t)col * a.Ptot + base;
+                        for (int64_t p = 0; p < np; p++) pl[p] = (lo << 20) | p;
+                    }
                 }
             }
         }
@@ -405,31 +468,22 @@ __device__ __forceinline__ int32_t load_node(const LPArgs &a, const int64_t *Wsm
 template <int MODE>
 __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
     constexpr bool DENSE = MODE == kRefineDense;
-    const int64_t npieces = a.Lpre[a.nL];
+    const int npieces = a.pcnt[a.colour];
+    const int64_t *plist = a.plist + (int64_t)a.colour * a.Ptot;
     while (true) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const int p = atomicAdd(&a.ctr->large_next, 1);
             sm.item = p;
-            if (p < npieces) {
-                int64_t lo = 0, hi = a.nL;  // node of piece p: largest li with Lpre[li] <= p
-                while (hi - lo > 1) {
-                    int64_t mid = (lo + hi) >> 1;
-                    if (a.Lpre[mid] <= p) lo = mid;
-                    else hi = mid;
-                }
-                sm.li = lo;
-                sm.flag = colour_of(a.seed, a.round, a.Lnodes[lo], a.S) == (uint32_t)a.colour;
-            }
+            if (p < npieces) sm.li = plist[p];
         }
         __syncthreads();
         const int p = sm.item;
         if (p >= npieces) break;
-        if (!sm.flag) continue;
-        const int64_t li = sm.li;
+        const int64_t li = sm.li >> 20;
+        const int64_t pi = sm.li & ((1 << 20) - 1);
         const int32_t v = a.Lnodes[li];
         const int64_t pieces = a.Lpre[li + 1] - a.Lpre[li];
-        const int64_t pi = p - a.Lpre[li];
         if (threadIdx.x == 0) {
             load_node<MODE>(a, sm.W, sm.nd, 0, v);
             sm.ndl = 0;
@@ -444,17 +498,29 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
         }
         const int64_t rs = sm.nd.rs[0];
         const int32_t cpv = sm.nd.cpv[0];
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
-            const int32_t u = __ldg(&a.g.adjncy[rs + e]);
-            const int32_t w = __ldg(&a.g.adjwgt[rs + e]);
-            if (MODE == kCluster && a.cp && __ldg(&a.cp[u]) != cpv) continue;
-            const int32_t L = __ldg(&a.lab[u]);
-            if constexpr (DENSE) {
-                atomicAdd(&sm.t.acc[L], w);
-            } else {
-                if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
-                               (uint64_t)(uint32_t)L, w))
-                    a.ctr->err = 1;
+        for (int64_t eb = e0 + threadIdx.x; eb < e1; eb += kUnroll * kThreads) {
+            int32_t u[kUnroll], w[kUnroll], L[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                const int64_t e = eb + j * kThreads;
+                u[j] = e < e1 ? __ldg(&a.g.adjncy[rs + e]) : -1;
+                w[j] = e < e1 ? __ldg(&a.g.adjwgt[rs + e]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != cpv) u[j] = -1;
+                L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                if (u[j] < 0) continue;
+                if constexpr (DENSE) {
+                    atomicAdd(&sm.t.acc[L[j]], w[j]);
+                } else {
+                    if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
+                                   (uint64_t)(uint32_t)L[j], w[j]))
+                        a.ctr->err = 1;
+                }
             }
         }
         __syncthreads();
@@ -616,22 +682,41 @@ __device__ void process_medium(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 }
             }
             __syncthreads();
-            for (int32_t le = t; le < len; le += kThreads) {
-                const uint32_t word = sm.bm[le >> 5];
-                const int s = s0 + sm.bmpre[le >> 5] +
-                              __popc(word & (0xffffffffu >> (31 - (le & 31)))) - 1;
-                const int64_t idx = nd.rs[s] + (e0 + le - nd.epre[s]);
-                const int32_t u = __ldg(&a.g.adjncy[idx]);
-                const int32_t w = __ldg(&a.g.adjwgt[idx]);
-                if (MODE == kCluster && a.cp && __ldg(&a.cp[u]) != nd.cpv[s]) continue;
-                const int32_t L = __ldg(&a.lab[u]);
-                if constexpr (DENSE) {
-                    atomicAdd(&sm.t.acc[(s - s0) * k + L], w);
-                } else {
-                    const uint64_t key = ((uint64_t)(uint32_t)s << 32) | (uint32_t)L;
-                    if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
-                                   key, w))
-                        a.ctr->err = 1;
+            for (int32_t lb = t; lb < len; lb += kUnroll * kThreads) {
+                int32_t sl[kUnroll], u[kUnroll], w[kUnroll], L[kUnroll];
+#pragma unroll
+                for (int j = 0; j < kUnroll; j++) {
+                    const int32_t le = lb + j * kThreads;
+                    u[j] = -1;
+                    w[j] = 0;
+                    sl[j] = 0;
+                    if (le < len) {
+                        const uint32_t word = sm.bm[le >> 5];
+                        const int s = s0 + sm.bmpre[le >> 5] +
+                                      __popc(word & (0xffffffffu >> (31 - (le & 31)))) - 1;
+                        const int64_t idx = nd.rs[s] + (e0 + le - nd.epre[s]);
+                        sl[j] = s;
+                        u[j] = __ldg(&a.g.adjncy[idx]);
+                        w[j] = __ldg(&a.g.adjwgt[idx]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kUnroll; j++) {
+                    if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != nd.cpv[sl[j]])
+                        u[j] = -1;
+                    L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kUnroll; j++) {
+                    if (u[j] < 0) continue;
+                    if constexpr (DENSE) {
+                        atomicAdd(&sm.t.acc[(sl[j] - s0) * k + L[j]], w[j]);
+                    } else {
+                        const uint64_t key = ((uint64_t)(uint32_t)sl[j] << 32) | (uint32_t)L[j];
+                        if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
+                                       key, w[j]))
+                            a.ctr->err = 1;
+                    }
                 }
             }
             __syncthreads();
@@ -761,8 +846,18 @@ __global__ void __launch_bounds__(kThreads) k_propose(LPArgs a, int k) {
     }
     if (a.nL > 0) process_large<MODE>(a, sm, k);
     process_medium<MODE>(a, sm, k);
-    __syncthreads();
-    process_small<MODE>(a, sm.W);
+}
+
+// Nodes of degree <= 32: no shared memory but the dense W snapshot, so it runs
+// at full occupancy next to k_propose (side stream).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_propose_small(LPArgs a, int k) {
+    __shared__ int64_t W[kDenseMaxK];
+    if constexpr (MODE == kRefineDense) {
+        for (int b = threadIdx.x; b < k; b += kThreads) W[b] = a.W[b];
+        __syncthreads();
+    }
+    process_small<MODE>(a, W);
 }
 
 // ---------------------------------------------------------------- arbitration
@@ -883,6 +978,7 @@ __device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *
 }
 
 struct ArbSm {
+    WDelta wd;
     unsigned long long hist[256];
     unsigned long long red[64];
     uint64_t keys[kSegSmem];
@@ -942,6 +1038,8 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
+    __shared__ WDelta wd;
+    wd_init(wd, a.nW);
     const int nprop = a.ctr->nprop;
     int64_t moved = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nprop;
@@ -950,7 +1048,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
         if (p.slot < 0) continue;
         const int64_t cap = a.B - p.wT;
         if (a.tsum[p.T] <= cap) {
-            apply_move(a, p.v, p.T, p.own, p.c);
+            apply_agg(a, wd, p.v, p.T, p.own, p.c);
             moved++;
         } else if (p.slot == 0) {
             const int32_t cnt = a.tcnt[p.T];
@@ -961,6 +1059,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
             a.segs[si] = Seg{p.T, cnt, base, cap + 1};
         }
     }
+    wd_flush(a, wd);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) moved += __shfl_down_sync(0xffffffffu, moved, d);
     if ((threadIdx.x & 31) == 0 && moved)
@@ -982,6 +1081,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
 __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ArbSm &sm = *reinterpret_cast<ArbSm *>(smraw);
+    wd_init(sm.wd, a.nW);
     const int nseg = a.ctr->nseg;
     const int lane = threadIdx.x & 31;
     int64_t moved = 0;
@@ -1006,7 +1106,7 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
             if (kj <= key) pre += cj;
         }
         if (lane < sg.cnt && (c == 0 || pre < sg.thr)) {
-            apply_move(a, (int32_t)(uint32_t)key, sg.T, own, c);
+            apply_agg(a, sm.wd, (int32_t)(uint32_t)key, sg.T, own, c);
             moved++;
         }
     }
@@ -1041,12 +1141,13 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         for (int64_t i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
             const SegEntry e = ent[i];
             if (e.key < K || e.c == 0) {
-                apply_move(a, (int32_t)(uint32_t)e.key, sg.T, e.own, e.c);
+                apply_agg(a, sm.wd, (int32_t)(uint32_t)e.key, sg.T, e.own, e.c);
                 moved++;
             }
         }
         __syncthreads();
     }
+    wd_flush(a, sm.wd);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) moved += __shfl_down_sync(0xffffffffu, moved, d);
     if (lane == 0 && moved) atomicAdd((unsigned long long *)a.moves, (unsigned long long)moved);
@@ -1447,11 +1548,12 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.segs = sc.get<Seg>(g.n);
     a.segbuf = sc.get<SegEntry>(g.n);
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
-    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S);
+    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + S);  // bucket lengths, then piece counts
     Ctr *ctr = sc.get<Ctr>(S);
     int64_t *d_moves = sc.zeros<int64_t>(cfg.rounds);
     a.wl = wl;
     a.wl_cnt = wl_cnt;
+    a.pcnt = wl_cnt + kClasses * S;
     a.prof = prof().on ? prof().d_counts : nullptr;
 
     // nodes of degree > kMedDeg: one list per call, cut into kChunk pieces
@@ -1472,6 +1574,9 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             exclusive_scan(LargePieces{g.xadj, Lnodes}, nL, Lpre, Lpre + nL, sc);
             a.Lnodes = Lnodes;
             a.Lpre = Lpre;
+            CK(cudaMemcpyAsync(&a.Ptot, Lpre + nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            a.plist = sc.get<int64_t>((size_t)S * (a.Ptot ? a.Ptot : 1));
             a.Ldone = sc.zeros<int32_t>(nL);
             a.Lndl = sc.zeros<int32_t>(nL);
             if (mode == kRefineDense) {
@@ -1519,64 +1624,100 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                             (int)sizeof(ArbSm)));
     const int grid_small = sms * 4;
 
+    cudaStream_t side;
+    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    cudaEvent_t ev_fork, ev_join;
+    CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    int occ_small = 0;
+    switch (mode) {
+        case kCluster: CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_small, k_propose_small<kCluster>, kThreads, 0)); break;
+        case kRefineHash: CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_small, k_propose_small<kRefineHash>, kThreads, 0)); break;
+        default: CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_small, k_propose_small<kRefineDense>, kThreads, 0)); break;
+    }
+    const int grid_sm = sms * std::max(1, occ_small);
+
     int done = 0;
     int64_t hmoves = 0;
-    for (int r = 0; r < cfg.rounds; r++) {
-        a.round = r;
-        a.moves = d_moves + r;
-        CK(cudaMemsetAsync(wl_cnt, 0, kClasses * S * sizeof(int32_t), s));
-        CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
-        k_build_wl<<<sms * 4, kThreads, 0, s>>>(g, cfg.seed, r, S, wl, wl_cnt);
-        LAUNCHED();
-        for (int j = 0; j < S; j++) {
-            a.ctr = ctr + j;
-            a.colour = j;
-            cudaEvent_t pb, pe;
-            prof_begin(s, &pb, &pe);
-            switch (mode) {
-                case kCluster: k_propose<kCluster><<<grid_main, kThreads, psmem, s>>>(a, k); break;
-                case kRefineHash: k_propose<kRefineHash><<<grid_main, kThreads, psmem, s>>>(a, k); break;
-                default: k_propose<kRefineDense><<<grid_main, kThreads, psmem, s>>>(a, k); break;
-            }
+    try {
+        for (int r = 0; r < cfg.rounds; r++) {
+            a.round = r;
+            a.moves = d_moves + r;
+            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + S) * sizeof(int32_t), s));
+            CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
+            k_build_wl<<<sms * 4, kThreads, 0, s>>>(a, wl, wl_cnt);
             LAUNCHED();
-            prof_end(s, pb, pe);
-            if (hub_items > 0) {
-                const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
+            for (int j = 0; j < S; j++) {
+                a.ctr = ctr + j;
+                a.colour = j;
+                cudaEvent_t pb, pe;
+                prof_begin(s, &pb, &pe);
+                // small rows on the side stream, next to the large and medium rows
+                CK(cudaEventRecord(ev_fork, s));
+                CK(cudaStreamWaitEvent(side, ev_fork, 0));
                 switch (mode) {
-                    case kCluster:
-                        k_hub_cand<kCluster><<<hg, kThreads, 0, s>>>(a);
-                        k_hub_tie<kCluster><<<hg, kThreads, 0, s>>>(a);
-                        k_hub_emit<kCluster><<<sms, kThreads, 0, s>>>(a);
-                        break;
-                    default:
-                        k_hub_cand<kRefineHash><<<hg, kThreads, 0, s>>>(a);
-                        k_hub_tie<kRefineHash><<<hg, kThreads, 0, s>>>(a);
-                        k_hub_emit<kRefineHash><<<sms, kThreads, 0, s>>>(a);
-                        break;
+                    case kCluster: k_propose_small<kCluster><<<grid_sm, kThreads, 0, side>>>(a, k); break;
+                    case kRefineHash: k_propose_small<kRefineHash><<<grid_sm, kThreads, 0, side>>>(a, k); break;
+                    default: k_propose_small<kRefineDense><<<grid_sm, kThreads, 0, side>>>(a, k); break;
                 }
                 LAUNCHED();
+                CK(cudaEventRecord(ev_join, side));
+                switch (mode) {
+                    case kCluster: k_propose<kCluster><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+                    case kRefineHash: k_propose<kRefineHash><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+                    default: k_propose<kRefineDense><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+                }
                 LAUNCHED();
+                CK(cudaStreamWaitEvent(s, ev_join, 0));
+                prof_end(s, pb, pe);
+                if (hub_items > 0) {
+                    const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
+                    switch (mode) {
+                        case kCluster:
+                            k_hub_cand<kCluster><<<hg, kThreads, 0, s>>>(a);
+                            k_hub_tie<kCluster><<<hg, kThreads, 0, s>>>(a);
+                            k_hub_emit<kCluster><<<sms, kThreads, 0, s>>>(a);
+                            break;
+                        default:
+                            k_hub_cand<kRefineHash><<<hg, kThreads, 0, s>>>(a);
+                            k_hub_tie<kRefineHash><<<hg, kThreads, 0, s>>>(a);
+                            k_hub_emit<kRefineHash><<<sms, kThreads, 0, s>>>(a);
+                            break;
+                    }
+                    LAUNCHED();
+                    LAUNCHED();
+                    LAUNCHED();
+                }
+                if (cfg.refine) {
+                    k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, s>>>(a);
+                    LAUNCHED();
+                }
+                k_classify<<<grid_small, kThreads, 0, s>>>(a);
+                LAUNCHED();
+                k_scatter<<<grid_small, kThreads, 0, s>>>(a);
+                LAUNCHED();
+                k_arbitrate<<<grid_small, kThreads, sizeof(ArbSm), s>>>(a);
+                LAUNCHED();
+                k_reset_targets<<<grid_small, kThreads, 0, s>>>(a);
                 LAUNCHED();
             }
-            if (cfg.refine) {
-                k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, s>>>(a);
-                LAUNCHED();
-            }
-            k_classify<<<grid_small, kThreads, 0, s>>>(a);
-            LAUNCHED();
-            k_scatter<<<grid_small, kThreads, 0, s>>>(a);
-            LAUNCHED();
-            k_arbitrate<<<grid_small, kThreads, sizeof(ArbSm), s>>>(a);
-            LAUNCHED();
-            k_reset_targets<<<grid_small, kThreads, 0, s>>>(a);
-            LAUNCHED();
+            CK(cudaMemcpyAsync(&hmoves, d_moves + r, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            done = r + 1;
+            if (moves_out) moves_out->push_back(hmoves);
+            if (hmoves == 0) break;
         }
-        CK(cudaMemcpyAsync(&hmoves, d_moves + r, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        done = r + 1;
-        if (moves_out) moves_out->push_back(hmoves);
-        if (hmoves == 0) break;
+    } catch (...) {
+        cudaStreamSynchronize(side);
+        cudaEventDestroy(ev_fork);
+        cudaEventDestroy(ev_join);
+        cudaStreamDestroy(side);
+        throw;
     }
+    CK(cudaStreamSynchronize(side));
+    CK(cudaEventDestroy(ev_fork));
+    CK(cudaEventDestroy(ev_join));
+    CK(cudaStreamDestroy(side));
     Ctr hc[32];
     CK(cudaMemcpyAsync(hc, ctr, S * sizeof(Ctr), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
