@@ -167,6 +167,19 @@ int project_partition(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_
 int sclap_cut(const sclap_graph *g, const int32_t *part, int32_t k, int64_t *cut_out,
               int64_t *block_w_out, void *stream);
 
+/* Cut and block weights like sclap_cut, without allocating any memory.  The
+ * paper has no counterpart: this exists for callers that cannot let a library
+ * allocate (inside another framework's CUDA-graph capture, in loops that must
+ * not reach the allocator, under a custom memory owner).  Its accumulators are
+ * a file-scope device array of 1 + 65536 int64 values, held by every GPU that
+ * loads the library until the process exits; k > 65536 returns SCLAP_EINVAL.
+ * The first call on a device looks up that array's device address (make that
+ * call before any stream capture).  All calls share the array and clear the
+ * part they use; calls that overlap on the GPU race.  Same arguments and
+ * outputs as sclap_cut; no graph validation. */
+int sclap_cut_noalloc(const sclap_graph *g, const int32_t *part, int32_t k, int64_t *cut_out,
+                      int64_t *block_w_out, void *stream);
+
 /* Initial partition of a (coarsest) graph; stands in for the paper's
  * evolutionary initial partitioner (Sec. II.C, Sec. IV.E).  P individuals:
  * individual t places the nodes in (c desc, h_t(v) asc, v asc) order into

@@ -86,6 +86,7 @@ _SIGS = {
     "contract_graph": (C.c_int, [C.POINTER(Graph), _VP, C.POINTER(GraphOwned), _VP, _VP]),
     "project_partition": (C.c_int, [C.c_int64, _VP, _VP, _VP, _VP]),
     "sclap_cut": (C.c_int, [C.POINTER(Graph), _VP, C.c_int32, _P64, _P64, _VP]),
+    "sclap_cut_noalloc": (C.c_int, [C.POINTER(Graph), _VP, C.c_int32, _P64, _P64, _VP]),
     "sclap_initial_partition": (C.c_int, [C.POINTER(Graph), C.c_int32, C.c_int64, C.c_int32,
                                           C.c_int32, C.c_int32, C.c_uint64, _VP, _P64, _P64,
                                           _P32, _VP]),
@@ -245,6 +246,19 @@ def sclap_cut(g: dict, part: torch.Tensor, k: int, stream=None):
     gg = _graph(g)
     _check(lib().sclap_cut(C.byref(gg), _ptr(part), k, C.byref(cut), C.cast(bw.data_ptr(), _P64),
                            _stream(stream)), "sclap_cut")
+    return cut.value, bw
+
+
+def sclap_cut_noalloc(g: dict, part: torch.Tensor, k: int, stream=None):
+    """Like sclap_cut, but the library allocates nothing (its accumulators are a
+    fixed device array; k <= 65536).  Returns (cut, block_weights[k] on the CPU)."""
+    _require_cuda(g["xadj"], part)
+    cut = C.c_int64(0)
+    bw = torch.zeros(k, dtype=torch.int64)
+    gg = _graph(g)
+    _check(lib().sclap_cut_noalloc(C.byref(gg), _ptr(part), k, C.byref(cut),
+                                   C.cast(bw.data_ptr(), _P64), _stream(stream)),
+           "sclap_cut_noalloc")
     return cut.value, bw
 
 

@@ -356,6 +356,23 @@ __global__ void k_bw(DGraph g, const int32_t *part, int64_t nblocks, unsigned lo
             if (lbw[b]) atomicAdd(&bw[b], lbw[b]);
 }
 
+void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned long long *d_cut,
+                unsigned long long *d_bw, cudaStream_t s, int sms) {
+    const int grid = sms * 8;
+    if (g.nnz > 0) {
+        const int cgrid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kCutTile), grid);
+        k_cut<<<cgrid, 256, 0, s>>>(g, part, g.n, 1, d_cut);
+        LAUNCHED();
+        k_halve<<<1, 256, 0, s>>>(d_cut, 1);
+        LAUNCHED();
+    }
+    if (g.n > 0) {
+        size_t shm = nblocks <= 2048 ? nblocks * sizeof(unsigned long long) : 0;
+        k_bw<<<grid, 256, shm, s>>>(g, part, nblocks, d_bw);
+        LAUNCHED();
+    }
+}
+
 void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t groups,
               int64_t n_group, int64_t *d_cut, int64_t *d_bw, Scratch &sc) {
     cudaStream_t s = sc.stream();

@@ -27,4 +27,9 @@ void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t gro
               int64_t n_group, int64_t *d_cut /* [groups] */, int64_t *d_bw /* [nblocks] */,
               Scratch &sc);
 
+// The same cut and block-weight kernels on caller-provided, zeroed device
+// accumulators (d_cut: 1 entry, d_bw: nblocks entries); allocates nothing.
+void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned long long *d_cut,
+                unsigned long long *d_bw, cudaStream_t s, int sms);
+
 }  // namespace sclap
