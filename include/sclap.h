@@ -196,6 +196,31 @@ int sclap_initial_partition(const sclap_graph *g, int32_t k, int64_t B, int32_t 
                             int32_t *part_out, int64_t *cuts_out, int64_t *maxbw_out,
                             int32_t *best_out, void *stream);
 
+/* A set of graphs for batched runs (host array of graph views). */
+typedef struct {
+    int32_t ngraphs;
+    const sclap_graph *graphs;
+} sclap_batch;
+
+/* Batched SCLaP population: many seeded runs on uneven graphs at once, the
+ * stand-in for the paper's population-based initial partitioning of the
+ * coarsest graph (Sec. II.C, Sec. IV.E).  Run r works on graph run_graph[r]
+ * with k blocks bounded by that graph's L_max = (1+eps) ceil(c(V)/k) (Sec.
+ * II.A): it places the nodes in (c desc, h_r(v) asc, v asc) order into the
+ * currently lightest block (lowest id on ties), h_r(v) = high 32 bits of
+ * mix64(s_r ^ v), s_r = mix64(seed ^ (0xD1B54A32D192ED03 * (r + 1))); then all
+ * runs are refined together for `rounds` rounds as one SCLaP refinement over
+ * the disjoint union of the runs' graphs (run r: nodes off_r + v, blocks
+ * r*k .. r*k+k-1; seed `seed`).
+ *   run_graph  host int32[nruns], graph index per run
+ *   parts_out  device int32[sum of the runs' n], per-run block ids 0..k-1,
+ *              concatenated in run order
+ *   cuts_out, maxbw_out  host int64[nruns] (NULL allowed)
+ * Needs c(V) <= INT32_MAX per graph and every weighted degree <= INT32_MAX. */
+int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t rounds,
+                         int32_t subrounds, uint64_t seed, int32_t nruns, const int32_t *run_graph,
+                         int32_t *parts_out, int64_t *cuts_out, int64_t *maxbw_out, void *stream);
+
 /* The multilevel partitioner, Sec. IV.E: l rounds of clustering and a
  * contraction per level while n >= n_stop (stop also when a level shrinks by
  * less than 5%, when it does not shrink at all, or at max_levels); the

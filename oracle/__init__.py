@@ -104,6 +104,11 @@ def lib():
             L.or_initial_partition.argtypes = g + [C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                                                    C.c_int32, C.c_uint64, _P32, _P64, _P64, _P32]
             L.or_multilevel.argtypes = g + [C.POINTER(MLParams), _P32, C.POINTER(MLStats)]
+            _PP64 = C.POINTER(_P64)
+            _PP32 = C.POINTER(_P32)
+            L.or_refine_batched.argtypes = [C.c_int32, _P64, _PP64, _PP32, _PP32, _PP32,
+                                            C.c_int32, _P64, C.c_int32, C.c_int32, C.c_uint64,
+                                            C.c_int32, _P32, _P32, _P64, _P64]
             _lib = L
     return _lib
 
@@ -249,6 +254,34 @@ def initial_partition(g, k, B, P, rounds, subrounds, seed):
                                     _p64(cuts), _p64(mx), C.byref(best))
     _check(rc, "initial_partition")
     return part, cuts, mx, best.value
+
+
+def refine_batched(graphs, k, eps, rounds, subrounds, seed, run_graph):
+    """Batched runs (see or_refine_batched).  Returns (list of per-run
+    partitions, cuts[nruns], maxbw[nruns])."""
+    keeps = [_graph_args(g) for g in graphs]
+    ng = len(graphs)
+    ns = np.array([a[0] for _, a in keeps], np.int64)
+    xs = (_P64 * ng)(*[a[1] for _, a in keeps])
+    As = (_P32 * ng)(*[a[2] for _, a in keeps])
+    Ws = (_P32 * ng)(*[a[3] for _, a in keeps])
+    Cs = (_P32 * ng)(*[a[4] for _, a in keeps])
+    Bg = np.array([lmax(int(np.asarray(g["vwgt"], np.int64).sum()), k, eps) for g in graphs],
+                  np.int64)
+    rg = np.ascontiguousarray(run_graph, np.int32)
+    nr = len(rg)
+    tot = int(sum(ns[g] for g in rg))
+    parts = np.empty(max(tot, 1), np.int32)
+    cuts = np.zeros(nr, np.int64)
+    mx = np.zeros(nr, np.int64)
+    rc = lib().or_refine_batched(ng, _p64(ns), xs, As, Ws, Cs, k, _p64(Bg), rounds, subrounds,
+                                 seed, nr, _p32(rg), _p32(parts), _p64(cuts), _p64(mx))
+    _check(rc, "refine_batched")
+    out, off = [], 0
+    for g in rg:
+        out.append(parts[off:off + ns[g]].copy())
+        off += ns[g]
+    return out, cuts, mx
 
 
 def default_params(k, eps=0.03, seed=1, **kw):

@@ -172,10 +172,17 @@ typedef struct {
 
 /* One round (R1-R5).  lab: label per node; W: weight per label (nW labels);
  * B: U (clustering) or L_max (refinement).  Returns the moves applied. */
+/* Bound of label L: Bv[L] when per-label bounds are given (batched runs, one
+ * L_max per run), else B. */
+static int64_t bound_of(const int64_t *Bv, int64_t B, int64_t L)
+{
+    return Bv ? Bv[L] : B;
+}
+
 static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                         const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
-                        int64_t *W, int64_t B, int refine, const int32_t *cp,
-                        uint64_t seed, int32_t round, int32_t S, lp_ws *ws)
+                        int64_t *W, int64_t B, const int64_t *Bv, int refine,
+                        const int32_t *cp, uint64_t seed, int32_t round, int32_t S, lp_ws *ws)
 {
     int64_t moves = 0;
     for (int32_t j = 0; j < S; j++) {
@@ -194,13 +201,13 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
             }
             int64_t own = lab[v];
             int64_t w_own = ws->acc[own];
-            int overloaded = refine && W[own] > B;
+            int overloaded = refine && W[own] > bound_of(Bv, B, own);
             int64_t best = -1;
             uint32_t best_tie = 0;
             for (int64_t t = 0; t < nt; t++) {
                 int64_t L = ws->touched[t];
                 if (L == own) continue;
-                if (W[L] + vwgt[v] > B) continue; /* not eligible */
+                if (W[L] + vwgt[v] > bound_of(Bv, B, L)) continue; /* not eligible */
                 uint32_t tl = or_tie(seed, round, v, L);
                 int better;
                 if (best < 0) better = 1;
@@ -226,8 +233,8 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
             while (i < np) {
                 int64_t b = ws->props[i].own, e = i;
                 while (e < np && ws->props[e].own == b) e++;
-                if (W[b] > B) {
-                    int64_t excess = W[b] - B, departed = 0;
+                if (W[b] > bound_of(Bv, B, b)) {
+                    int64_t excess = W[b] - bound_of(Bv, B, b), departed = 0;
                     for (int64_t q = i; q < e; q++) {
                         if (departed < excess) departed += ws->props[q].c;
                         else ws->props[q].keep = 0;
@@ -242,7 +249,7 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         while (i < np) {
             int64_t T = ws->props[i].target, e = i;
             while (e < np && ws->props[e].target == T) e++;
-            int64_t cap = B - W[T], sum = 0;
+            int64_t cap = bound_of(Bv, B, T) - W[T], sum = 0;
             for (int64_t q = i; q < e; q++) {
                 proposal *p = &ws->props[q];
                 if (!p->keep) continue;
@@ -266,9 +273,9 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
 
 static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
-                  int64_t *W, int64_t nW, int64_t B, int refine, const int32_t *cp,
-                  uint64_t seed, int32_t rounds, int32_t S, int32_t *rounds_done,
-                  int64_t *moves_per_round)
+                  int64_t *W, int64_t nW, int64_t B, const int64_t *Bv, int refine,
+                  const int32_t *cp, uint64_t seed, int32_t rounds, int32_t S,
+                  int32_t *rounds_done, int64_t *moves_per_round)
 {
     lp_ws ws;
     ws.acc = (int64_t *)calloc((size_t)(nW ? nW : 1), sizeof(int64_t));
@@ -280,7 +287,7 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     }
     int32_t done = 0;
     for (int32_t r = 0; r < rounds; r++) {
-        int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, refine, cp,
+        int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, Bv, refine, cp,
                              seed, r, S, &ws);
         if (moves_per_round) moves_per_round[r] = m;
         done = r + 1;
@@ -372,18 +379,19 @@ int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     int64_t *W = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
     if (!W) return OR_ENOMEM;
     for (int64_t v = 0; v < n; v++) { labels_out[v] = (int32_t)v; W[v] = vwgt[v]; }
-    int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, labels_out, W, n, U, 0,
+    int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, labels_out, W, n, U, NULL, 0,
                     constraint_part, seed, rounds, S, rounds_done, moves_per_round);
     free(W);
     if (rc) return rc;
     return pack_isolated(n, xadj, vwgt, U, constraint_part, labels_out);
 }
 
-/* Sec. III.A, local-search form with an explicit bound B on every block. */
-int or_refine_bound(int64_t n, const int64_t *xadj, const int32_t *adjncy,
-                    const int32_t *adjwgt, const int32_t *vwgt, int32_t nblocks,
-                    int64_t B, int32_t rounds, int32_t S, uint64_t seed,
-                    int32_t *part, int32_t *rounds_done, int64_t *moves_per_round)
+/* Sec. III.A, local-search form with a bound on every block: Bv[b] when given,
+ * else B. */
+static int refine_bounds(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                         const int32_t *adjwgt, const int32_t *vwgt, int32_t nblocks,
+                         int64_t B, const int64_t *Bv, int32_t rounds, int32_t S, uint64_t seed,
+                         int32_t *part, int32_t *rounds_done, int64_t *moves_per_round)
 {
     if (nblocks < 1 || rounds < 0 || S < 1) return OR_EINVAL;
     for (int64_t v = 0; v < n; v++)
@@ -391,10 +399,19 @@ int or_refine_bound(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     int64_t *W = (int64_t *)calloc((size_t)nblocks, sizeof(int64_t));
     if (!W) return OR_ENOMEM;
     for (int64_t v = 0; v < n; v++) W[part[v]] += vwgt[v];
-    int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, part, W, nblocks, B, 1, NULL,
+    int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, part, W, nblocks, B, Bv, 1, NULL,
                     seed, rounds, S, rounds_done, moves_per_round);
     free(W);
     return rc;
+}
+
+int or_refine_bound(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                    const int32_t *adjwgt, const int32_t *vwgt, int32_t nblocks,
+                    int64_t B, int32_t rounds, int32_t S, uint64_t seed,
+                    int32_t *part, int32_t *rounds_done, int64_t *moves_per_round)
+{
+    return refine_bounds(n, xadj, adjncy, adjwgt, vwgt, nblocks, B, NULL, rounds, S, seed,
+                         part, rounds_done, moves_per_round);
 }
 
 int or_refine(int64_t n, const int64_t *xadj, const int32_t *adjncy,
@@ -536,51 +553,62 @@ static int cmp_lpt(const void *a, const void *b)
     return x->v < y->v ? -1 : (x->v > y->v);
 }
 
-/* Reading (the paper runs an evolutionary algorithm here): P individuals.
- * Individual t: nodes in (c desc, h_t(v) asc, v asc) order, each placed in
- * the currently lightest block (lowest id on ties); h_t(v) = high 32 bits of
- * mix64(s_t ^ v), s_t = mix64(seed ^ (0xD1B54A32D192ED03 * (t+1))).  All P
- * individuals are then refined together, as one SCLaP refinement over the
- * disjoint union of P copies of the graph (copy t: nodes t*n + v, blocks
- * t*k .. t*k+k-1, bound B, seed `seed`).  The best individual has the
- * lowest cut among those with max block weight <= B (lowest t on ties);
- * with none feasible, the smallest max block weight, then cut, then t. */
-int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
-                         const int32_t *adjwgt, const int32_t *vwgt, int32_t k,
-                         int64_t B, int32_t P, int32_t rounds, int32_t S,
-                         uint64_t seed, int32_t *part_out, int64_t *cuts_out,
-                         int64_t *maxbw_out, int32_t *best_out)
+/* Batched runs: run r refines graph run_graph[r] (bound Bg[run_graph[r]] on
+ * each of its k blocks) from its own LPT start.  Reading (the paper's
+ * population lives in an evolutionary algorithm): run r places its graph's
+ * nodes in (c desc, h_r(v) asc, v asc) order into the currently lightest of
+ * its k blocks (lowest id on ties), h_r(v) = high 32 bits of mix64(s_r ^ v),
+ * s_r = mix64(seed ^ (0xD1B54A32D192ED03 * (r+1))); then all runs are refined
+ * together as one SCLaP refinement of the disjoint union of the runs' graphs
+ * (run r: nodes off_r + v with off_r the node count of the runs before it,
+ * blocks r*k .. r*k+k-1), `rounds` rounds, `seed`.  Outputs per run: its
+ * partition (block ids 0..k-1, concatenated in run order), cut and largest
+ * block weight. */
+int or_refine_batched(int32_t ngraphs, const int64_t *ns, const int64_t *const *xadjs,
+                      const int32_t *const *adjncys, const int32_t *const *adjwgts,
+                      const int32_t *const *vwgts, int32_t k, const int64_t *Bg,
+                      int32_t rounds, int32_t S, uint64_t seed, int32_t nruns,
+                      const int32_t *run_graph, int32_t *parts_out, int64_t *cuts_out,
+                      int64_t *maxbw_out)
 {
-    if (k < 1 || P < 1) return OR_EINVAL;
-    int64_t nnz = xadj[n];
-    int64_t un = n * P, unnz = nnz * P;
+    if (k < 1 || nruns < 1 || ngraphs < 1) return OR_EINVAL;
+    int64_t un = 0, unnz = 0, nmax = 0;
+    for (int32_t r = 0; r < nruns; r++) {
+        int32_t g = run_graph[r];
+        if (g < 0 || g >= ngraphs) return OR_EINVAL;
+        un += ns[g];
+        unnz += xadjs[g][ns[g]];
+        if (ns[g] > nmax) nmax = ns[g];
+    }
     int64_t *ux = (int64_t *)malloc(sizeof(int64_t) * (size_t)(un + 1));
     int32_t *ua = (int32_t *)malloc(sizeof(int32_t) * (size_t)(unnz ? unnz : 1));
     int32_t *uw = (int32_t *)malloc(sizeof(int32_t) * (size_t)(unnz ? unnz : 1));
     int32_t *uc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
     int32_t *up = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
-    lpt_item *it = (lpt_item *)malloc(sizeof(lpt_item) * (size_t)(n ? n : 1));
+    int64_t *Bv = (int64_t *)malloc(sizeof(int64_t) * (size_t)nruns * (size_t)k);
+    lpt_item *it = (lpt_item *)malloc(sizeof(lpt_item) * (size_t)(nmax ? nmax : 1));
     int64_t *bw = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
     int rc = OR_OK;
-    if (!ux || !ua || !uw || !uc || !up || !it || !bw) { rc = OR_ENOMEM; goto out; }
+    if (!ux || !ua || !uw || !uc || !up || !Bv || !it || !bw) { rc = OR_ENOMEM; goto out; }
 
-    for (int32_t t = 0; t < P; t++) {           /* the disjoint union */
+    int64_t off = 0, eoff = 0;
+    for (int32_t r = 0; r < nruns; r++) {        /* the disjoint union */
+        int32_t g = run_graph[r];
+        int64_t n = ns[g];
         for (int64_t v = 0; v < n; v++) {
-            ux[t * n + v] = t * nnz + xadj[v];
-            uc[t * n + v] = vwgt[v];
+            ux[off + v] = eoff + xadjs[g][v];
+            uc[off + v] = vwgts[g][v];
         }
-        for (int64_t i = 0; i < nnz; i++) {
-            ua[t * nnz + i] = (int32_t)(adjncy[i] + t * n);
-            uw[t * nnz + i] = adjwgt[i];
+        for (int64_t i = 0; i < xadjs[g][n]; i++) {
+            ua[eoff + i] = (int32_t)(adjncys[g][i] + off);
+            uw[eoff + i] = adjwgts[g][i];
         }
-    }
-    ux[un] = unnz;
-
-    for (int32_t t = 0; t < P; t++) {           /* LPT start per individual */
-        uint64_t st = or_mix64(seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(t + 1)));
+        for (int32_t b = 0; b < k; b++) Bv[(int64_t)r * k + b] = Bg[g];
+        /* LPT start of run r */
+        uint64_t sr = or_mix64(seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(r + 1)));
         for (int64_t v = 0; v < n; v++) {
-            it[v].v = v; it[v].c = vwgt[v];
-            it[v].h = (uint32_t)(or_mix64(st ^ (uint64_t)v) >> 32);
+            it[v].v = v; it[v].c = vwgts[g][v];
+            it[v].h = (uint32_t)(or_mix64(sr ^ (uint64_t)v) >> 32);
         }
         if (n > 0) qsort(it, (size_t)n, sizeof(lpt_item), cmp_lpt);
         for (int32_t b = 0; b < k; b++) bw[b] = 0;
@@ -588,26 +616,65 @@ int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
             int32_t bb = 0;
             for (int32_t b = 1; b < k; b++)
                 if (bw[b] < bw[bb]) bb = b;
-            up[t * n + it[i].v] = t * k + bb;
+            up[off + it[i].v] = r * k + bb;
             bw[bb] += it[i].c;
         }
+        off += n;
+        eoff += xadjs[g][n];
     }
+    ux[un] = unnz;
 
-    rc = or_refine_bound(un, ux, ua, uw, uc, k * P, B, rounds, S, seed, up, NULL, NULL);
+    rc = refine_bounds(un, ux, ua, uw, uc, k * nruns, 0, Bv, rounds, S, seed, up, NULL, NULL);
     if (rc) goto out;
 
+    off = 0;
+    for (int32_t r = 0; r < nruns; r++) {
+        int32_t g = run_graph[r];
+        int64_t n = ns[g];
+        int64_t cut = 0;
+        for (int64_t v = 0; v < n; v++)
+            for (int64_t i = xadjs[g][v]; i < xadjs[g][v + 1]; i++)
+                if (up[off + adjncys[g][i]] != up[off + v]) cut += adjwgts[g][i];
+        for (int32_t b = 0; b < k; b++) bw[b] = 0;
+        for (int64_t v = 0; v < n; v++) bw[up[off + v] - r * k] += vwgts[g][v];
+        int64_t mx = 0;
+        for (int32_t b = 0; b < k; b++) if (bw[b] > mx) mx = bw[b];
+        if (cuts_out) cuts_out[r] = cut / 2;
+        if (maxbw_out) maxbw_out[r] = mx;
+        if (parts_out)
+            for (int64_t v = 0; v < n; v++) parts_out[off + v] = up[off + v] - r * k;
+        off += n;
+    }
+out:
+    free(ux); free(ua); free(uw); free(uc); free(up); free(Bv); free(it); free(bw);
+    return rc;
+}
+
+/* Reading (the paper runs an evolutionary algorithm here): P individuals,
+ * computed as P batched runs on the same graph with bound B (see
+ * or_refine_batched).  The best individual has the lowest cut among those
+ * with max block weight <= B (lowest t on ties); with none feasible, the
+ * smallest max block weight, then cut, then t. */
+int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                         const int32_t *adjwgt, const int32_t *vwgt, int32_t k,
+                         int64_t B, int32_t P, int32_t rounds, int32_t S,
+                         uint64_t seed, int32_t *part_out, int64_t *cuts_out,
+                         int64_t *maxbw_out, int32_t *best_out)
+{
+    if (k < 1 || P < 1) return OR_EINVAL;
+    int32_t *rg = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    int32_t *parts = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * P ? n * P : 1));
+    int64_t *cuts = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
+    int64_t *mxs = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
+    int rc = OR_OK;
+    if (!rg || !parts || !cuts || !mxs) { rc = OR_ENOMEM; goto out; }
+    rc = or_refine_batched(1, &n, &xadj, &adjncy, &adjwgt, &vwgt, k, &B, rounds, S, seed, P, rg,
+                           parts, cuts, mxs);
+    if (rc) goto out;
     int32_t best = -1;
     int64_t best_cut = 0, best_max = 0;
     for (int32_t t = 0; t < P; t++) {
-        int64_t cut = 0;
-        for (int64_t v = 0; v < n; v++)
-            for (int64_t i = xadj[v]; i < xadj[v + 1]; i++)
-                if (up[t * n + adjncy[i]] != up[t * n + v]) cut += adjwgt[i];
-        cut /= 2;
-        for (int32_t b = 0; b < k; b++) bw[b] = 0;
-        for (int64_t v = 0; v < n; v++) bw[up[t * n + v] - t * k] += vwgt[v];
-        int64_t mx = 0;
-        for (int32_t b = 0; b < k; b++) if (bw[b] > mx) mx = bw[b];
+        int64_t cut = cuts[t], mx = mxs[t];
         if (cuts_out) cuts_out[t] = cut;
         if (maxbw_out) maxbw_out[t] = mx;
         int better;
@@ -620,10 +687,10 @@ int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         }
         if (better) { best = t; best_cut = cut; best_max = mx; }
     }
-    for (int64_t v = 0; v < n; v++) part_out[v] = up[(int64_t)best * n + v] - best * k;
+    for (int64_t v = 0; v < n; v++) part_out[v] = parts[(int64_t)best * n + v];
     if (best_out) *best_out = best;
 out:
-    free(ux); free(ua); free(uw); free(uc); free(up); free(it); free(bw);
+    free(rg); free(parts); free(cuts); free(mxs);
     return rc;
 }
 

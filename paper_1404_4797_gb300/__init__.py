@@ -45,6 +45,10 @@ class GraphOwned(C.Structure):
                 ("adjncy", C.c_void_p), ("adjwgt", C.c_void_p), ("vwgt", C.c_void_p)]
 
 
+class Batch(C.Structure):
+    _fields_ = [("ngraphs", C.c_int32), ("graphs", C.POINTER(Graph))]
+
+
 class MLParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("eps", C.c_double), ("U", C.c_int64),
                 ("cluster_rounds", C.c_int32), ("refine_rounds", C.c_int32),
@@ -90,6 +94,9 @@ _SIGS = {
     "sclap_initial_partition": (C.c_int, [C.POINTER(Graph), C.c_int32, C.c_int64, C.c_int32,
                                           C.c_int32, C.c_int32, C.c_uint64, _VP, _P64, _P64,
                                           _P32, _VP]),
+    "sclap_refine_batched": (C.c_int, [C.POINTER(Batch), C.c_int32, C.c_double, C.c_int32,
+                                       C.c_int32, C.c_uint64, C.c_int32, _P32, _VP, _P64, _P64,
+                                       _VP]),
     "partition_multilevel": (C.c_int, [C.POINTER(Graph), C.POINTER(MLParams), _VP,
                                        C.POINTER(MLStats), _VP]),
     "sclap_graph_copy_out": (C.c_int, [C.POINTER(GraphOwned), _VP, _VP, _VP, _VP, _VP]),
@@ -278,6 +285,30 @@ def sclap_initial_partition(g: dict, k: int, B: int, P: int, rounds: int, subrou
                                          C.cast(mx.data_ptr(), _P64), C.byref(best),
                                          _stream(stream)), "sclap_initial_partition")
     return part, cuts, mx, best.value
+
+
+def sclap_refine_batched(graphs: list, k: int, eps: float, rounds: int, subrounds: int,
+                         seed: int, run_graph, stream=None):
+    """Batched SCLaP runs over uneven graphs (the population stand-in).  Returns
+    (list of per-run partitions (CUDA int32), cuts[nruns], maxbw[nruns])."""
+    for g in graphs:
+        _require_cuda(g["xadj"])
+    views = (Graph * len(graphs))(*[_graph(g) for g in graphs])
+    b = Batch(len(graphs), views)
+    rg = torch.as_tensor(list(run_graph), dtype=torch.int32)
+    ns = [graphs[i]["vwgt"].numel() for i in rg.tolist()]
+    parts = torch.empty(max(sum(ns), 1), dtype=torch.int32, device=graphs[0]["xadj"].device)
+    cuts = torch.zeros(len(ns), dtype=torch.int64)
+    mx = torch.zeros(len(ns), dtype=torch.int64)
+    _check(lib().sclap_refine_batched(C.byref(b), k, eps, rounds, subrounds, seed & (2**64 - 1),
+                                      len(ns), C.cast(rg.data_ptr(), _P32), _ptr(parts),
+                                      C.cast(cuts.data_ptr(), _P64), C.cast(mx.data_ptr(), _P64),
+                                      _stream(stream)), "sclap_refine_batched")
+    out, off = [], 0
+    for n in ns:
+        out.append(parts[off:off + n])
+        off += n
+    return out, cuts, mx
 
 
 def default_params(k: int, eps: float = 0.03, seed: int = 1, **kw) -> dict:

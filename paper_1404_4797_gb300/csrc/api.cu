@@ -162,62 +162,88 @@ bool in_range(int64_t n, const int32_t *a, int64_t hi, Scratch &sc) {
 
 // ---------------------------------------------------------------- initial partition
 
-__global__ void k_union(DGraph g, int64_t P, int64_t *ux, int32_t *ua, int32_t *uw, int32_t *uc) {
-    const int64_t un = g.n * P, unnz = g.nnz * P;
+// Batched runs over the disjoint union of their graphs (run r: nodes off_r + v,
+// entries eoff_r + i, blocks r*k .. r*k+k-1).
+struct RunDesc {
+    const int64_t *xadj;
+    const int32_t *adjncy, *adjwgt, *vwgt;
+    int64_t n, off, eoff;
+    int64_t bound;  // the run's L_max
+    uint64_t lpt_seed;
+};
+
+__device__ __forceinline__ int64_t run_of(const RunDesc *rd, int64_t nruns, int64_t x, bool entries) {
+    int64_t lo = 0, hi = nruns;  // largest r with off_r <= x
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((entries ? rd[mid].eoff : rd[mid].off) <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_union_batch(const RunDesc *rd, int64_t nruns, int64_t un, int64_t unnz,
+                              int64_t *ux, int32_t *ua, int32_t *uw, int32_t *uc, int64_t *goff) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t t = i / g.n, v = i % g.n;
-        ux[i] = t * g.nnz + g.xadj[v];
-        uc[i] = g.vwgt[v];
+        const RunDesc &r = rd[run_of(rd, nruns, i, false)];
+        const int64_t v = i - r.off;
+        ux[i] = r.eoff + r.xadj[v];
+        uc[i] = r.vwgt[v];
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < unnz;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t t = i / g.nnz, e = i % g.nnz;
-        ua[i] = (int32_t)(g.adjncy[e] + t * g.n);
-        uw[i] = g.adjwgt[e];
+        const RunDesc &r = rd[run_of(rd, nruns, i, true)];
+        const int64_t e = i - r.eoff;
+        ua[i] = (int32_t)(r.adjncy[e] + r.off);
+        uw[i] = r.adjwgt[e];
     }
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nruns;
+         r += (int64_t)gridDim.x * blockDim.x)
+        goff[r] = r < nruns ? rd[r].off : un;
     if (blockIdx.x == 0 && threadIdx.x == 0) ux[un] = unnz;
 }
 
-// LPT order keys: first pass h_t(v), second pass (t, Cmax - c).
-__global__ void k_lpt_keys1(int64_t n, int64_t P, uint64_t seed, uint64_t *key, int32_t *idx) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * P;
+// LPT order keys: first pass h_r(v) (local v), second pass (r, cmax - c).
+__global__ void k_lpt_keys1(const RunDesc *rd, int64_t nruns, int64_t un, uint64_t *key,
+                            int32_t *idx) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t t = i / n, v = i % n;
-        uint64_t st = mix64(seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(t + 1)));
-        key[i] = mix64(st ^ (uint64_t)v) >> 32;
+        const RunDesc &r = rd[run_of(rd, nruns, i, false)];
+        key[i] = mix64(r.lpt_seed ^ (uint64_t)(i - r.off)) >> 32;
         idx[i] = (int32_t)i;
     }
 }
 
-__global__ void k_lpt_keys2(int64_t n, int64_t P, const int32_t *idx, const int32_t *vwgt, int cb,
-                             int64_t cmax, uint64_t *key) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * P;
+__global__ void k_lpt_keys2(const RunDesc *rd, int64_t nruns, const int32_t *idx,
+                            const int32_t *uc, int cb, int64_t cmax, int64_t un, uint64_t *key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t u = idx[i];
-        int64_t t = u / n, v = u % n;
-        key[i] = ((uint64_t)t << cb) | (uint64_t)(cmax - vwgt[v]);
+        const int64_t u = idx[i];
+        const int64_t r = run_of(rd, nruns, u, false);
+        key[i] = ((uint64_t)r << cb) | (uint64_t)(cmax - uc[u]);
     }
 }
 
-// One warp per individual t: nodes in sorted order go to the lightest block
-// (lowest id on ties).  Sequential by nature: block weights live in shared
-// memory, 32 upcoming nodes are prefetched per lane, and the argmin is two
-// warp reductions (weights fit 32 bits: c(V) <= INT32_MAX is checked).
-__global__ void k_lpt_assign(int64_t n, int32_t k, const int32_t *order, const int32_t *vwgt,
-                             int32_t *upart) {
+// One warp per run: its nodes in sorted order go to the lightest of its k
+// blocks (lowest id on ties).  Sequential by nature: block weights live in
+// shared memory, 32 upcoming nodes are prefetched per lane, and the argmin
+// is two warp reductions (weights fit 32 bits: c(V) <= INT32_MAX is checked).
+__global__ void k_lpt_assign(const RunDesc *rd, int32_t k, const int32_t *order,
+                             const int32_t *uc, int32_t *upart) {
     extern __shared__ unsigned bw[];
-    const int64_t t = blockIdx.x;
+    const int64_t r = blockIdx.x;
     const int lane = threadIdx.x;
     for (int b = lane; b < k; b += 32) bw[b] = 0;
     __syncwarp();
-    const int32_t *ord = order + t * n;
+    const int64_t n = rd[r].n;
+    const int32_t *ord = order + rd[r].off;
     for (int64_t i0 = 0; i0 < n; i0 += 32) {
         const int64_t i = i0 + lane;
         int32_t u = 0, c = 0;
         if (i < n) {
             u = ord[i];
-            c = vwgt[u - t * n];
+            c = uc[u];
         }
         const int cnt = (int)min64(32, n - i0);
         for (int j = 0; j < cnt; j++) {
@@ -229,42 +255,140 @@ __global__ void k_lpt_assign(int64_t n, int32_t k, const int32_t *order, const i
             const unsigned gw = __reduce_min_sync(0xffffffffu, wmin);
             const unsigned gb = __reduce_min_sync(0xffffffffu, wmin == gw ? bmin : 0xffffffffu);
             if (lane == (int)(gb & 31)) bw[gb] += (unsigned)cj;
-            if (lane == 0) upart[uj] = (int32_t)(t * k + gb);
+            if (lane == 0) upart[uj] = (int32_t)(r * k + gb);
             __syncwarp();
         }
     }
 }
 
+__global__ void k_run_bounds(const RunDesc *rd, int64_t nruns, int32_t k, int64_t *Bv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nruns * k;
+         i += (int64_t)gridDim.x * blockDim.x)
+        Bv[i] = rd[i / k].bound;
+}
+
+__global__ void k_run_max(int64_t nruns, int32_t k, const int64_t *bw, int64_t *maxbw) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nruns;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = 0;
+        for (int b = 0; b < k; b++) m = max64(m, bw[r * k + b]);
+        maxbw[r] = m;
+    }
+}
+
+__global__ void k_run_parts(const RunDesc *rd, int64_t nruns, int32_t k, int64_t un,
+                            const int32_t *upart, int32_t *parts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
+         i += (int64_t)gridDim.x * blockDim.x)
+        parts[i] = upart[i] - (int32_t)(run_of(rd, nruns, i, false) * k);
+}
+
+struct BatchResult {
+    std::vector<int64_t> cuts, maxbw;
+    int64_t total_n = 0;
+};
+
+// All runs refined together (see sclap_refine_batched).  parts_out: device,
+// sum of the runs' node counts.
+BatchResult batched_impl(const std::vector<DGraph> &G, const std::vector<int64_t> &bound,
+                         const std::vector<int32_t> &run_graph, int32_t k, int32_t rounds,
+                         int32_t S, uint64_t seed, int32_t *parts_out, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    const int grid = dev_info().sms * 8;
+    const int64_t nruns = (int64_t)run_graph.size();
+    std::vector<RunDesc> rd(nruns);
+    int64_t un = 0, unnz = 0, cmax = 0, cV = 0;
+    std::vector<GraphTotals> tot(G.size());
+    for (size_t gi = 0; gi < G.size(); gi++) tot[gi] = graph_totals(G[gi], sc, true);
+    for (int64_t r = 0; r < nruns; r++) {
+        const DGraph &g = G[run_graph[r]];
+        rd[r] = RunDesc{g.xadj, g.adjncy, g.adjwgt, g.vwgt, g.n, un, unnz, bound[run_graph[r]],
+                        mix64(seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(r + 1)))};
+        un += g.n;
+        unnz += g.nnz;
+        cmax = std::max<int64_t>(cmax, tot[run_graph[r]].maxc);
+        cV = std::max<int64_t>(cV, tot[run_graph[r]].cV);
+        if (tot[run_graph[r]].max_wdeg > INT32_MAX) fail(SCLAP_EOVERFLOW, "weighted degree");
+    }
+    if (cV > INT32_MAX) fail(SCLAP_EOVERFLOW, "c(V) of a run");
+    if (un > INT32_MAX) fail(SCLAP_EINVAL, "batched runs too large");
+    BatchResult res;
+    res.cuts.assign(nruns, 0);
+    res.maxbw.assign(nruns, 0);
+    res.total_n = un;
+    if (un == 0) return res;
+    RunDesc *d_rd = sc.get<RunDesc>(nruns);
+    CK(cudaMemcpyAsync(d_rd, rd.data(), nruns * sizeof(RunDesc), cudaMemcpyHostToDevice, s));
+    int64_t *ux = sc.get<int64_t>(un + 1);
+    int32_t *ua = sc.get<int32_t>(unnz);
+    int32_t *uw = sc.get<int32_t>(unnz);
+    int32_t *uc = sc.get<int32_t>(un);
+    int32_t *up = sc.get<int32_t>(un);
+    int64_t *goff = sc.get<int64_t>(nruns + 1);
+    k_union_batch<<<grid, 256, 0, s>>>(d_rd, nruns, un, unnz, ux, ua, uw, uc, goff);
+    LAUNCHED();
+    // LPT start of every run: order (run, c desc, h_r(v) asc, v asc) by two stable sorts
+    uint64_t *key = sc.get<uint64_t>(un);
+    int32_t *idx = sc.get<int32_t>(un);
+    k_lpt_keys1<<<grid, 256, 0, s>>>(d_rd, nruns, un, key, idx);
+    LAUNCHED();
+    radix_sort_pairs(key, idx, un, 32, sc);
+    const int cb = std::max(1, bit_width_u64((uint64_t)cmax));
+    const int rb = std::max(1, bit_width_u64((uint64_t)(nruns - 1)));
+    k_lpt_keys2<<<grid, 256, 0, s>>>(d_rd, nruns, idx, uc, cb, cmax, un, key);
+    LAUNCHED();
+    radix_sort_pairs(key, idx, un, cb + rb, sc);
+    k_lpt_assign<<<(unsigned)nruns, 32, k * sizeof(unsigned), s>>>(d_rd, k, idx, uc, up);
+    LAUNCHED();
+    int64_t *Bv = sc.get<int64_t>(nruns * k);
+    k_run_bounds<<<grid, 256, 0, s>>>(d_rd, nruns, k, Bv);
+    LAUNCHED();
+    // refine all runs together on the disjoint union
+    DGraph ug{un, unnz, ux, ua, uw, uc};
+    LPConfig cfg{};
+    cfg.g = ug;
+    cfg.lab = up;
+    cfg.nW = (int64_t)k * nruns;
+    cfg.B = 0;
+    cfg.Bv = Bv;
+    cfg.refine = true;
+    cfg.cp = nullptr;
+    cfg.seed = seed;
+    cfg.rounds = rounds;
+    cfg.S = S;
+    lp_run(cfg, sc, nullptr, nullptr);
+    int64_t *d_cut = sc.get<int64_t>(nruns);
+    int64_t *d_bw = sc.get<int64_t>((int64_t)k * nruns);
+    int64_t *d_max = sc.get<int64_t>(nruns);
+    cut_impl(ug, up, (int64_t)k * nruns, nruns, goff, d_cut, d_bw, sc);
+    k_run_max<<<grid, 256, 0, s>>>(nruns, k, d_bw, d_max);
+    LAUNCHED();
+    if (parts_out) {
+        k_run_parts<<<grid, 256, 0, s>>>(d_rd, nruns, k, un, up, parts_out);
+        LAUNCHED();
+    }
+    CK(cudaMemcpyAsync(res.cuts.data(), d_cut, nruns * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(res.maxbw.data(), d_max, nruns * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return res;
+}
+
 // Best individual: lowest cut among those with max block <= B (lowest t on
 // ties); otherwise smallest max block, then cut, then t.
-__global__ void k_pick_best(int64_t P, int32_t k, int64_t B, const int64_t *cut, const int64_t *bw,
-                            int64_t *maxbw_out, int32_t *best_out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+int32_t pick_best(const std::vector<int64_t> &cuts, const std::vector<int64_t> &mx, int64_t B) {
     int32_t best = -1;
-    int64_t bc = 0, bm = 0;
-    for (int64_t t = 0; t < P; t++) {
-        int64_t mx = 0;
-        for (int b = 0; b < k; b++) mx = max(mx, bw[t * k + b]);
-        maxbw_out[t] = mx;
+    for (int32_t t = 0; t < (int32_t)cuts.size(); t++) {
         bool better;
         if (best < 0) better = true;
         else {
-            bool fn = mx <= B, fo = bm <= B;
+            const bool fn = mx[t] <= B, fo = mx[best] <= B;
             if (fn != fo) better = fn;
-            else if (fn) better = cut[t] < bc;
-            else better = mx < bm || (mx == bm && cut[t] < bc);
+            else if (fn) better = cuts[t] < cuts[best];
+            else better = mx[t] < mx[best] || (mx[t] == mx[best] && cuts[t] < cuts[best]);
         }
-        if (better) { best = (int32_t)t; bc = cut[t]; bm = mx; }
+        if (better) best = t;
     }
-    *best_out = best;
-}
-
-__global__ void k_extract(int64_t n, int32_t k, const int32_t *best, const int32_t *upart,
-                          int32_t *part) {
-    const int64_t t = *best;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        part[v] = upart[t * n + v] - (int32_t)(t * k);
+    return best;
 }
 
 struct InitResult {
@@ -272,68 +396,19 @@ struct InitResult {
     std::vector<int64_t> cuts, maxbw;
 };
 
+// P individuals on one graph (batched runs) and the best of them.
 InitResult initial_impl(const DGraph &g, int32_t k, int64_t B, int32_t P, int32_t rounds,
                         int32_t S, uint64_t seed, int32_t *part_out, Scratch &sc) {
     cudaStream_t s = sc.stream();
-    const int grid = dev_info().sms * 8;
-    const int64_t n = g.n;
-    const int64_t un = n * P, unnz = g.nnz * P;
-    if (un > INT32_MAX) fail(SCLAP_EINVAL, "initial partition too large");
-    int64_t *ux = sc.get<int64_t>(un + 1);
-    int32_t *ua = sc.get<int32_t>(unnz);
-    int32_t *uw = sc.get<int32_t>(unnz);
-    int32_t *uc = sc.get<int32_t>(un);
-    int32_t *up = sc.get<int32_t>(un);
     InitResult res;
-    res.cuts.assign(P, 0);
-    res.maxbw.assign(P, 0);
-    if (n == 0) {
-        res.best = 0;
-        return res;
-    }
-    k_union<<<grid, 256, 0, s>>>(g, P, ux, ua, uw, uc);
-    LAUNCHED();
-    // LPT order per individual: (t, c desc, h asc, v asc) by two stable sorts
-    uint64_t *key = sc.get<uint64_t>(un);
-    int32_t *idx = sc.get<int32_t>(un);
-    k_lpt_keys1<<<grid, 256, 0, s>>>(n, P, seed, key, idx);
-    LAUNCHED();
-    radix_sort_pairs(key, idx, un, 32, sc);
-    GraphTotals tot = graph_totals(g, sc);
-    const int cb = std::max(1, bit_width_u64((uint64_t)tot.maxc));
-    const int tb = std::max(1, bit_width_u64((uint64_t)(P - 1)));
-    k_lpt_keys2<<<grid, 256, 0, s>>>(n, P, idx, g.vwgt, cb, tot.maxc, key);
-    LAUNCHED();
-    radix_sort_pairs(key, idx, un, cb + tb, sc);
-    if (tot.cV > INT32_MAX) fail(SCLAP_EOVERFLOW, "c(V)");
-    k_lpt_assign<<<P, 32, k * sizeof(unsigned), s>>>(n, k, idx, g.vwgt, up);
-    LAUNCHED();
-    // refine all individuals together on the disjoint union
-    DGraph ug{un, unnz, ux, ua, uw, uc};
-    LPConfig cfg{};
-    cfg.g = ug;
-    cfg.lab = up;
-    cfg.nW = (int64_t)k * P;
-    cfg.B = B;
-    cfg.refine = true;
-    cfg.cp = nullptr;
-    cfg.seed = seed;
-    cfg.rounds = rounds;
-    cfg.S = S;
-    lp_run(cfg, sc, nullptr, nullptr);
-    int64_t *d_cut = sc.get<int64_t>(P);
-    int64_t *d_bw = sc.get<int64_t>((int64_t)k * P);
-    cut_impl(ug, up, (int64_t)k * P, P, n, d_cut, d_bw, sc);
-    int64_t *d_max = sc.get<int64_t>(P);
-    int32_t *d_best = sc.get<int32_t>(1);
-    k_pick_best<<<1, 32, 0, s>>>(P, k, B, d_cut, d_bw, d_max, d_best);
-    LAUNCHED();
-    k_extract<<<grid, 256, 0, s>>>(n, k, d_best, up, part_out);
-    LAUNCHED();
-    CK(cudaMemcpyAsync(res.cuts.data(), d_cut, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(res.maxbw.data(), d_max, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&res.best, d_best, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    int32_t *parts = sc.get<int32_t>((size_t)g.n * P);
+    BatchResult br = batched_impl({g}, {B}, std::vector<int32_t>(P, 0), k, rounds, S, seed, parts, sc);
+    res.cuts = br.cuts;
+    res.maxbw = br.maxbw;
+    res.best = g.n > 0 ? pick_best(br.cuts, br.maxbw, B) : 0;
+    if (g.n > 0)
+        CK(cudaMemcpyAsync(part_out, parts + (int64_t)res.best * g.n, g.n * sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, s));
     return res;
 }
 
@@ -494,7 +569,7 @@ int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cu
         DGraph g = view(gp);
         int64_t *d_cut = sc.get<int64_t>(1);
         int64_t *d_bw = sc.get<int64_t>(k);
-        cut_impl(g, part, k, 1, g.n, d_cut, d_bw, sc);
+        cut_impl(g, part, k, 1, nullptr, d_cut, d_bw, sc);
         int64_t c = 0;
         CK(cudaMemcpyAsync(&c, d_cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         if (block_w_out)
@@ -581,6 +656,36 @@ int sclap_initial_partition(const sclap_graph *gp, int32_t k, int64_t B, int32_t
         if (cuts_out) std::memcpy(cuts_out, r.cuts.data(), P * sizeof(int64_t));
         if (maxbw_out) std::memcpy(maxbw_out, r.maxbw.data(), P * sizeof(int64_t));
         if (best_out) *best_out = r.best;
+    });
+}
+
+int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t rounds,
+                         int32_t subrounds, uint64_t seed, int32_t nruns, const int32_t *run_graph,
+                         int32_t *parts_out, int64_t *cuts_out, int64_t *maxbw_out, void *stream) {
+    return guarded([&] {
+        if (!b || b->ngraphs < 1 || !b->graphs || k < 1 || !(eps >= 0) || rounds < 0 ||
+            subrounds < 1 || subrounds > 32 || nruns < 1 || !run_graph)
+            fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        std::vector<DGraph> G;
+        std::vector<int64_t> bound;
+        for (int32_t i = 0; i < b->ngraphs; i++) {
+            DGraph g = view(&b->graphs[i]);
+            validate_graph(g, sc);
+            G.push_back(g);
+            bound.push_back(lmax_of(graph_totals(g, sc).cV, k, eps));
+        }
+        std::vector<int32_t> rg(run_graph, run_graph + nruns);
+        int64_t total = 0;
+        for (int32_t r : rg) {
+            if (r < 0 || r >= b->ngraphs) fail(SCLAP_EINVAL, "run_graph");
+            total += G[r].n;
+        }
+        if (total > 0 && !parts_out) fail(SCLAP_EINVAL, "parts_out");
+        BatchResult br = batched_impl(G, bound, rg, k, rounds, subrounds, seed, parts_out, sc);
+        if (cuts_out) std::memcpy(cuts_out, br.cuts.data(), nruns * sizeof(int64_t));
+        if (maxbw_out) std::memcpy(maxbw_out, br.maxbw.data(), nruns * sizeof(int64_t));
     });
 }
 
@@ -680,7 +785,7 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
         // final cut and balance
         int64_t *d_cut = top.get<int64_t>(1);
         int64_t *d_bw = top.get<int64_t>(p->k);
-        cut_impl(g0, cur, p->k, 1, n, d_cut, d_bw, top);
+        cut_impl(g0, cur, p->k, 1, nullptr, d_cut, d_bw, top);
         std::vector<int64_t> bw(p->k);
         CK(cudaMemcpyAsync(&st.cut, d_cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(bw.data(), d_bw, p->k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));

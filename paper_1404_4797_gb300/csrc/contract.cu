@@ -310,28 +310,47 @@ void project_impl(int64_t n, const int32_t *f2c, const int32_t *cp, int32_t *fp,
 // Entries in tiles of kCutTile; block_rows gives each entry's row.
 constexpr int kCutTile = 4096;
 
-__global__ void __launch_bounds__(256) k_cut(DGraph g, const int32_t *part, int64_t n_group,
+__global__ void __launch_bounds__(256) k_cut(DGraph g, const int32_t *part, const int64_t *goff,
                                              int64_t groups, unsigned long long *cut) {
     __shared__ int32_t rowof[kCutTile];
     __shared__ int32_t tmp[16];
     const int64_t tiles = ceil_div<int64_t>(g.nnz, kCutTile);
+    // a thread's rows only grow (tiles and entries in increasing order), so
+    // it keeps one running sum per group and flushes it when the group changes
+    int64_t grp = -1, acc = 0, gend = -1;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t e0 = t * kCutTile;
         const int len = (int)min64(kCutTile, g.nnz - e0);
         block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
-        int64_t grp = -1, acc = 0;
         for (int i = threadIdx.x; i < len; i += 256) {
             const int32_t v = rowof[i];
-            const int64_t gv = groups > 1 ? v / n_group : 0;
-            if (gv != grp) {
+            if (v >= gend) {  // rows only grow along a thread's entries
                 if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
                 acc = 0;
-                grp = gv;
+                if (groups == 1) {
+                    grp = 0;
+                    gend = g.n;
+                } else {
+                    int64_t lo = 0, hi = groups;  // largest grp with goff[grp] <= v
+                    while (hi - lo > 1) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if (goff[mid] <= v) lo = mid;
+                        else hi = mid;
+                    }
+                    grp = lo;
+                    gend = goff[lo + 1];
+                }
             }
             if (part[g.adjncy[e0 + i]] != part[v]) acc += g.adjwgt[e0 + i];
         }
-        if (acc) atomicAdd(&cut[grp], (unsigned long long)acc);
         __syncthreads();
+    }
+    if (groups == 1) {  // one group: reduce per warp before the atomic
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+        if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&cut[0], (unsigned long long)acc);
+    } else if (acc) {
+        atomicAdd(&cut[grp], (unsigned long long)acc);
     }
 }
 
@@ -361,7 +380,7 @@ void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned 
     const int grid = sms * 8;
     if (g.nnz > 0) {
         const int cgrid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kCutTile), grid);
-        k_cut<<<cgrid, 256, 0, s>>>(g, part, g.n, 1, d_cut);
+        k_cut<<<cgrid, 256, 0, s>>>(g, part, nullptr, 1, d_cut);
         LAUNCHED();
         k_halve<<<1, 256, 0, s>>>(d_cut, 1);
         LAUNCHED();
@@ -374,14 +393,14 @@ void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned 
 }
 
 void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t groups,
-              int64_t n_group, int64_t *d_cut, int64_t *d_bw, Scratch &sc) {
+              const int64_t *goff, int64_t *d_cut, int64_t *d_bw, Scratch &sc) {
     cudaStream_t s = sc.stream();
     const int grid = dev_info().sms * 8;
     CK(cudaMemsetAsync(d_cut, 0, groups * sizeof(int64_t), s));
     if (d_bw) CK(cudaMemsetAsync(d_bw, 0, nblocks * sizeof(int64_t), s));
     if (g.nnz > 0) {
         const int cgrid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kCutTile), grid);
-        k_cut<<<cgrid, 256, 0, s>>>(g, part, n_group, groups, (unsigned long long *)d_cut);
+        k_cut<<<cgrid, 256, 0, s>>>(g, part, goff, groups, (unsigned long long *)d_cut);
         LAUNCHED();
         k_halve<<<1, 256, 0, s>>>((unsigned long long *)d_cut, groups);
         LAUNCHED();

@@ -20,11 +20,11 @@ void contract_impl(const DGraph &g, const int32_t *lab, int32_t *f2c, CoarseGrap
 void project_impl(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_part,
                   int32_t *fine_part, cudaStream_t s);
 
-// cut and block weights.  groups > 1: nodes [t*n_group, (t+1)*n_group) form
-// group t (disjoint copies); cut_out[t] and block weights are per group with
-// k blocks each (block ids t*k .. t*k+k-1).  Results are device arrays.
+// Cut and block weights.  groups > 1: nodes [goff[t], goff[t+1]) form group t
+// (disjoint graphs; goff device int64[groups+1]) and d_cut[t] is its cut.
+// Results are device arrays.
 void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t groups,
-              int64_t n_group, int64_t *d_cut /* [groups] */, int64_t *d_bw /* [nblocks] */,
+              const int64_t *goff, int64_t *d_cut /* [groups] */, int64_t *d_bw /* [nblocks] */,
               Scratch &sc);
 
 // The same cut and block-weight kernels on caller-provided, zeroed device

@@ -100,6 +100,7 @@ struct LPArgs {
     int32_t *lab;
     int64_t *W;
     int64_t B, nW;
+    const int64_t *Bv;      // per-label bounds (batched runs) or null: B for every label
     const int32_t *cp;
     uint64_t seed;
     int32_t round, colour, S;
@@ -133,6 +134,11 @@ struct LPArgs {
     int32_t *hbestL, *hown;
     unsigned long long *prof;  // [2] entries, nodes, or null
 };
+
+// Bound of label L (U, L_max, or the run's L_max in batched runs).
+__device__ __forceinline__ int64_t bnd(const LPArgs &a, int64_t L) {
+    return a.Bv ? __ldg(&a.Bv[L]) : a.B;
+}
 
 __device__ __forceinline__ uint64_t seg_key(int32_t gain, int32_t v) {
     return ((uint64_t)(uint32_t)(0x7fffffff - gain) << 32) | (uint32_t)v;
@@ -376,7 +382,7 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const unsigned long
         int32_t w = ld<COHERENT>(&vals[slot]);
         if (L == nd.own[s]) {
             nd.ownw[s] = w;
-        } else if (a.W[L] + nd.c[s] <= a.B) {
+        } else if (a.W[L] + nd.c[s] <= bnd(a, L)) {
             atomicMax(&nd.best[s], cand_key(w, nd.h[s], L));
         }
     }
@@ -389,7 +395,7 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const unsigned long
         int32_t w = ld<COHERENT>(&vals[slot]);
         unsigned long long b = nd.best[s];
         if (b == 0 || L == nd.own[s] || (uint32_t)w != (uint32_t)(b >> 32)) continue;
-        if (a.W[L] + nd.c[s] > a.B) continue;
+        if (a.W[L] + nd.c[s] > bnd(a, L)) continue;
         if (cand_key(w, nd.h[s], L) == b) atomicMin(&nd.bestL[s], L);
     }
     __syncthreads();
@@ -409,8 +415,9 @@ __device__ __forceinline__ void select_dense_warp(const LPArgs &a, const int64_t
     if (lane + 32 < k) acc[lane + 32] = 0;
     int32_t ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
     unsigned long long ck0 = 0, ck1 = 0;
-    if (w0 > 0 && lane != own && Wsm[lane] + c <= a.B) ck0 = cand_key(w0, h, lane);
-    if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= a.B) ck1 = cand_key(w1, h, lane + 32);
+    if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane);
+    if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32))
+        ck1 = cand_key(w1, h, lane + 32);
     unsigned long long m = ck0 > ck1 ? ck0 : ck1;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -456,7 +463,7 @@ __device__ __forceinline__ int32_t load_node(const LPArgs &a, const int64_t *Wsm
     nd.c[t] = a.g.vwgt[v];
     nd.cpv[t] = a.cp ? a.cp[v] : 0;
     nd.h[t] = node_hash(a.seed, a.round, (uint32_t)v);
-    nd.ovl[t] = MODE == kCluster ? 0 : ((MODE == kRefineDense ? Wsm[own] : a.W[own]) > a.B);
+    nd.ovl[t] = MODE == kCluster ? 0 : ((MODE == kRefineDense ? Wsm[own] : a.W[own]) > bnd(a, own));
     nd.ownw[t] = 0;
     nd.best[t] = 0;
     nd.bestL[t] = 0x7fffffff;
@@ -784,7 +791,7 @@ __device__ __forceinline__ void small_item(const LPArgs &a, const int64_t *Wsm, 
             ownw = (int32_t)wsum;
         } else {
             const int64_t WL = MODE == kRefineDense ? Wsm[L] : a.W[L];
-            if (WL + c <= a.B) ck = cand_key((int32_t)wsum, h, L);
+            if (WL + c <= bnd(a, L)) ck = cand_key((int32_t)wsum, h, L);
         }
     }
     unsigned long long best = ck;  // reduce within the node's G lanes
@@ -799,7 +806,8 @@ __device__ __forceinline__ void small_item(const LPArgs &a, const int64_t *Wsm, 
     for (int d = G / 2; d > 0; d >>= 1) bl = min(bl, __shfl_xor_sync(0xffffffffu, bl, d));
     if (has && r == 0 && best != 0) {
         const int32_t gain = (int32_t)(best >> 32) - ownw;
-        const bool ovl = MODE != kCluster && (MODE == kRefineDense ? Wsm[own] : a.W[own]) > a.B;
+        const bool ovl =
+            MODE != kCluster && (MODE == kRefineDense ? Wsm[own] : a.W[own]) > bnd(a, own);
         if (gain > 0 || ovl) {
             const int64_t wT = MODE == kRefineDense ? Wsm[bl] : a.W[bl];
             emit<MODE == kRefineDense>(a, v, bl, own, gain, c, ovl, wT);
@@ -1001,8 +1009,8 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
     if (blockIdx.x < a.nW) {
         const int32_t b = blockIdx.x;
         const int64_t Wb = a.W[b];
-        if (Wb <= a.B) return;
-        const int64_t X = Wb - a.B;
+        if (Wb <= bnd(a, b)) return;
+        const int64_t X = Wb - bnd(a, b);
         if (a.ssum[b] < X) return;  // uncontested: handled by the pass-through CTAs
         auto get = [&](int64_t i, uint64_t *key, int32_t *c) {
             const Prop &p = a.props[i];
@@ -1030,7 +1038,7 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
          i += (int64_t)(gridDim.x - a.nW) * blockDim.x) {
         Prop &p = a.props[i];
         if (p.slot != -2) continue;
-        if (a.ssum[p.own] < a.W[p.own] - a.B) {
+        if (a.ssum[p.own] < a.W[p.own] - bnd(a, p.own)) {
             atomicAdd((unsigned long long *)&a.tsum[p.T], (unsigned long long)(int64_t)p.c);
             p.slot = atomicAdd(&a.tcnt[p.T], 1);
         }
@@ -1046,7 +1054,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
          i += (int64_t)gridDim.x * blockDim.x) {
         const Prop p = a.props[i];
         if (p.slot < 0) continue;
-        const int64_t cap = a.B - p.wT;
+        const int64_t cap = bnd(a, p.T) - p.wT;
         if (a.tsum[p.T] <= cap) {
             apply_agg(a, wd, p.v, p.T, p.own, p.c);
             moved++;
@@ -1073,7 +1081,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
          i += (int64_t)gridDim.x * blockDim.x) {
         const Prop p = a.props[i];
         if (p.slot < 0) continue;
-        if (a.tsum[p.T] <= a.B - p.wT) continue;
+        if (a.tsum[p.T] <= bnd(a, p.T) - p.wT) continue;
         a.segbuf[a.tbase[p.T] + p.slot] = SegEntry{seg_key(p.gain, p.v), p.c, p.own};
     }
 }
@@ -1215,7 +1223,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
             const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
             const int32_t w = __ldcg(&a.gvals[off + slot]);
             if (L == own) a.hown[it.li] = w;
-            else if (a.W[L] + c <= a.B) {
+            else if (a.W[L] + c <= bnd(a, L)) {
                 const unsigned long long ck = cand_key(w, h, L);
                 best = ck > best ? ck : best;
             }
@@ -1251,7 +1259,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
             const int32_t slot = __ldcg(&gdl[i]);
             const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
             const int32_t w = __ldcg(&a.gvals[off + slot]);
-            if (b != 0 && L != own && (uint32_t)w == (uint32_t)(b >> 32) && a.W[L] + c <= a.B &&
+            if (b != 0 && L != own && (uint32_t)w == (uint32_t)(b >> 32) && a.W[L] + c <= bnd(a, L) &&
                 cand_key(w, h, L) == b)
                 atomicMin(&a.hbestL[it.li], L);
             a.gkeys[off + slot] = kEmpty;
@@ -1271,7 +1279,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
         const int32_t own = a.lab[v];
         if (b != 0) {
             const int32_t gain = (int32_t)(b >> 32) - a.hown[li];
-            const bool ovl = MODE != kCluster && a.W[own] > a.B;
+            const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
             if (gain > 0 || ovl) {
                 const int32_t L = a.hbestL[li];
                 emit<false>(a, v, L, own, gain, a.g.vwgt[v], ovl, a.W[L]);
@@ -1536,6 +1544,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.lab = cfg.lab;
     a.W = W;
     a.B = cfg.B;
+    a.Bv = cfg.Bv;
     a.nW = cfg.nW;
     a.cp = cfg.refine ? nullptr : cfg.cp;
     a.seed = cfg.seed;

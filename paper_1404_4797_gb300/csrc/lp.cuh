@@ -12,6 +12,7 @@ struct LPConfig {
     int32_t *lab;          // device labels (cluster ids or blocks), updated in place
     int64_t nW;            // number of labels: n (clustering) or nblocks (refinement)
     int64_t B;             // U or L_max
+    const int64_t *Bv;     // device per-label bounds (batched runs) or null
     bool refine;           // refinement form (overloaded-block rule) vs clustering
     const int32_t *cp;     // V-cycle constraint partition (clustering only) or null
     uint64_t seed;

@@ -239,3 +239,16 @@ def test_errors_are_reported():
     with pytest.raises(S.SclapError) as e:
         S.sclap_cluster(big, 2**31 - 1, 3, 4, 1)
     assert e.value.code == S.EOVERFLOW
+
+
+def test_batched_runs_match_oracle():
+    gens = [I.random_graph(n, 4 * n, seed=n, max_w=30, max_c=20) for n in (700, 2500, 6000, 1200)]
+    gs = [I.to_numpy(g) for g in gens]
+    gd = [dev(g) for g in gens]
+    rg = [3, 0, 2, 2, 1, 0, 3, 2, 1, 1, 0, 2]
+    for k in (4, 16):
+        want, wc, wm = oracle.refine_batched(gs, k, 0.03, 6, 4, 9, rg)
+        got, gc, gm = S.sclap_refine_batched(gd, k, 0.03, 6, 4, 9, rg)
+        assert np.array_equal(gc.numpy(), wc) and np.array_equal(gm.numpy(), wm)
+        for r in range(len(rg)):
+            assert np.array_equal(got[r].cpu().numpy(), want[r]), (k, r)

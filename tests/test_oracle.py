@@ -394,3 +394,53 @@ def test_multilevel_config1_shape_is_deterministic_and_balanced():
     if st["init_maxbw"] <= st["lmax"]:
         assert bw.max() <= st["lmax"]
     assert st["U"] == max(1, 16384 // 40)
+
+
+# ---------------------------------------------------------------- batched runs
+
+def _lpt_by_hand(g, k, seed, r):
+    # the LPT start of run r written out from its definition
+    sr = brute.mix64(seed ^ ((0xD1B54A32D192ED03 * (r + 1)) & brute.M64))
+    n = len(g["vwgt"])
+    order = sorted(range(n), key=lambda v: (-int(g["vwgt"][v]), brute.mix64(sr ^ v) >> 32, v))
+    bw = [0] * k
+    part = [0] * n
+    for v in order:
+        b = min(range(k), key=lambda x: (bw[x], x))
+        part[v] = b
+        bw[b] += int(g["vwgt"][v])
+    return part
+
+
+def test_batched_runs_start_from_their_lpt_placement():
+    gs = [I.to_numpy(I.random_graph(40, 90, seed=s, max_c=7, max_w=3)) for s in (1, 2)]
+    rg = [0, 1, 1, 0]
+    parts, cuts, mx = oracle.refine_batched(gs, 3, 0.1, 0, 2, 77, rg)
+    for r, g in enumerate(rg):
+        assert list(parts[r]) == _lpt_by_hand(gs[g], 3, 77, r)
+        assert cuts[r] == brute.cut(gs[g], parts[r])
+        assert mx[r] == max(brute.block_weights(gs[g], parts[r], 3))
+
+
+def test_batched_runs_respect_their_own_bounds_and_report_consistently():
+    gs = [I.to_numpy(I.random_graph(n, 4 * n, seed=n, max_c=9, max_w=5)) for n in (60, 200, 500)]
+    k = 4
+    rg = [2, 0, 1, 2, 1]
+    parts, cuts, mx = oracle.refine_batched(gs, k, 0.03, 6, 4, 5, rg)
+    for r, g in enumerate(rg):
+        B = oracle.lmax(int(gs[g]["vwgt"].sum()), k, 0.03)
+        bw = brute.block_weights(gs[g], parts[r], k)
+        assert cuts[r] == brute.cut(gs[g], parts[r]) and mx[r] == max(bw)
+        start = _lpt_by_hand(gs[g], k, 5, r)
+        if max(brute.block_weights(gs[g], start, k)) <= B:
+            assert max(bw) <= B   # a feasible start stays feasible
+
+
+def test_initial_partition_is_the_best_of_batched_runs():
+    g = I.to_numpy(I.random_graph(120, 400, seed=6, max_c=5, max_w=4))
+    k, P = 4, 5
+    B = oracle.lmax(int(g["vwgt"].sum()), k, 0.03)
+    part, cuts, mx, best = oracle.initial_partition(g, k, B, P, 4, 4, 21)
+    parts, bc, bm = oracle.refine_batched([g], k, 0.03, 4, 4, 21, [0] * P)
+    assert list(cuts) == list(bc) and list(mx) == list(bm)
+    assert np.array_equal(part, parts[best])
