@@ -59,7 +59,9 @@ constexpr int kSlotBits = 12;
 constexpr int kMedItem = 64;             // medium worklist nodes per CTA item
 constexpr int kDenseMaxK = 64;
 constexpr int kClasses = 5;              // buckets per colour
-constexpr int kSegSmem = 2048;           // contested segments staged in shared memory
+constexpr int kSegSmem = 6144;           // contested segments staged in shared memory
+constexpr int kDigit = 11;               // radix-select digit width
+constexpr int kBins = 1 << kDigit;
 constexpr int kUnroll = 4;               // entries in flight per thread
 constexpr int kAggW = 1024;              // label weights aggregated in shared memory up to this
 constexpr uint64_t kEmpty = ~0ull;
@@ -747,52 +749,69 @@ __device__ void process_medium(const LPArgs &a, PropSm<MODE> &sm, int k) {
     }
 }
 
-// Small nodes: G lanes per node, one pass (deg <= G).
+// Small nodes: G lanes per node, one pass (deg <= G).  Loading and computing
+// are split so a warp keeps kSmallIlp items' load chains in flight.
+constexpr int kSmallIlp = 4;
+
+struct SmallLoad {
+    int32_t v, own, c, L, w;
+    int64_t WL, Wown;
+    uint64_t h;
+    bool has, valid;
+};
+
 template <int MODE, int G>
-__device__ __forceinline__ void small_item(const LPArgs &a, const int64_t *Wsm, const int32_t *wl,
-                                           int64_t cnt, int64_t item) {
-    constexpr int NPW = 32 / G;  // nodes per warp
+__device__ __forceinline__ SmallLoad small_load(const LPArgs &a, const int64_t *Wsm,
+                                                const int32_t *wl, int64_t cnt, int64_t item) {
+    constexpr int NPW = 32 / G;  // nodes per warp item
     const int lane = threadIdx.x & 31;
     const int q = lane / G, r = lane % G;
     const int64_t idx = item * NPW + q;
-    const bool has = idx < cnt;
-    int32_t v = 0, own = 0, c = 0, deg = 0, L = 0, w = 0;
-    uint64_t h = 0;
-    bool valid = false;
-    if (has) {
-        v = wl[idx];
-        const int64_t b = a.g.xadj[v];
-        deg = (int32_t)(a.g.xadj[v + 1] - b);
-        own = a.lab[v];
-        c = a.g.vwgt[v];
-        h = node_hash(a.seed, a.round, (uint32_t)v);
+    SmallLoad x;
+    x.has = item >= 0 && idx < cnt;
+    x.valid = false;
+    x.v = x.own = x.c = x.L = x.w = 0;
+    x.WL = x.Wown = 0;
+    x.h = 0;
+    if (x.has) {
+        x.v = wl[idx];
+        const int64_t b = a.g.xadj[x.v];
+        const int32_t deg = (int32_t)(a.g.xadj[x.v + 1] - b);
+        x.own = a.lab[x.v];
+        x.c = a.g.vwgt[x.v];
         if (r < deg) {
             const int32_t u = __ldg(&a.g.adjncy[b + r]);
-            w = __ldg(&a.g.adjwgt[b + r]);
-            if (!(MODE == kCluster && a.cp && __ldg(&a.cp[u]) != a.cp[v])) {
-                L = __ldg(&a.lab[u]);
-                valid = true;
+            x.w = __ldg(&a.g.adjwgt[b + r]);
+            if (!(MODE == kCluster && a.cp && __ldg(&a.cp[u]) != a.cp[x.v])) {
+                x.L = __ldg(&a.lab[u]);
+                x.valid = true;
+                x.WL = MODE == kRefineDense ? Wsm[x.L] : a.W[x.L];
             }
         }
+        if (MODE != kCluster) x.Wown = MODE == kRefineDense ? Wsm[x.own] : a.W[x.own];
+        if (a.prof && r == 0) {
+            atomicAdd(&a.prof[0], (unsigned long long)deg);
+            atomicAdd(&a.prof[1], 1ull);
+        }
     }
-    if (a.prof && has && r == 0) {
-        atomicAdd(&a.prof[0], (unsigned long long)deg);
-        atomicAdd(&a.prof[1], 1ull);
-    }
+    return x;
+}
+
+template <int MODE, int G>
+__device__ __forceinline__ void small_compute(const LPArgs &a, const int64_t *Wsm, const SmallLoad &x) {
+    const int lane = threadIdx.x & 31;
+    const int q = lane / G, r = lane % G;
+    const uint64_t h = x.has ? node_hash(a.seed, a.round, (uint32_t)x.v) : 0;
     const unsigned long long mkey =
-        valid ? (((unsigned long long)q << 32) | (uint32_t)L) : (0xffffffff00000000ull | lane);
+        x.valid ? (((unsigned long long)q << 32) | (uint32_t)x.L) : (0xffffffff00000000ull | lane);
     const unsigned peers = __match_any_sync(0xffffffffu, mkey);
-    const unsigned wsum = __reduce_add_sync(peers, valid ? (unsigned)w : 0u);
-    const bool leader = valid && (peers & ((1u << lane) - 1)) == 0;
+    const unsigned wsum = __reduce_add_sync(peers, x.valid ? (unsigned)x.w : 0u);
+    const bool leader = x.valid && (peers & ((1u << lane) - 1)) == 0;
     unsigned long long ck = 0;
     int32_t ownw = 0;
     if (leader) {
-        if (L == own) {
-            ownw = (int32_t)wsum;
-        } else {
-            const int64_t WL = MODE == kRefineDense ? Wsm[L] : a.W[L];
-            if (WL + c <= bnd(a, L)) ck = cand_key((int32_t)wsum, h, L);
-        }
+        if (x.L == x.own) ownw = (int32_t)wsum;
+        else if (x.WL + x.c <= bnd(a, x.L)) ck = cand_key((int32_t)wsum, h, x.L);
     }
     unsigned long long best = ck;  // reduce within the node's G lanes
 #pragma unroll
@@ -801,42 +820,47 @@ __device__ __forceinline__ void small_item(const LPArgs &a, const int64_t *Wsm, 
         best = o > best ? o : best;
         ownw += __shfl_xor_sync(0xffffffffu, ownw, d);
     }
-    int32_t bl = (best != 0 && ck == best) ? L : 0x7fffffff;
+    int32_t bl = (best != 0 && ck == best) ? x.L : 0x7fffffff;
 #pragma unroll
     for (int d = G / 2; d > 0; d >>= 1) bl = min(bl, __shfl_xor_sync(0xffffffffu, bl, d));
-    if (has && r == 0 && best != 0) {
+    if (x.has && r == 0 && best != 0) {
         const int32_t gain = (int32_t)(best >> 32) - ownw;
-        const bool ovl =
-            MODE != kCluster && (MODE == kRefineDense ? Wsm[own] : a.W[own]) > bnd(a, own);
+        const bool ovl = MODE != kCluster && x.Wown > bnd(a, x.own);
         if (gain > 0 || ovl) {
             const int64_t wT = MODE == kRefineDense ? Wsm[bl] : a.W[bl];
-            emit<MODE == kRefineDense>(a, v, bl, own, gain, c, ovl, wT);
+            emit<MODE == kRefineDense>(a, x.v, bl, x.own, gain, x.c, ovl, wT);
         }
+    }
+}
+
+template <int MODE, int G>
+__device__ __forceinline__ void small_bin(const LPArgs &a, const int64_t *Wsm, const int32_t *wl,
+                                          int64_t cnt, int64_t gwarp, int64_t nwarps) {
+    constexpr int NPW = 32 / G;
+    const int64_t items = ceil_div<int64_t>(cnt, NPW);
+    for (int64_t it = gwarp; it < items; it += kSmallIlp * nwarps) {
+        SmallLoad x[kSmallIlp];
+#pragma unroll
+        for (int j = 0; j < kSmallIlp; j++) {
+            const int64_t t = it + j * nwarps;
+            x[j] = small_load<MODE, G>(a, Wsm, wl, cnt, t < items ? t : -1);
+        }
+#pragma unroll
+        for (int j = 0; j < kSmallIlp; j++)
+            if (it + j * nwarps < items) small_compute<MODE, G>(a, Wsm, x[j]);  // warp-uniform
     }
 }
 
 template <int MODE>
 __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
     const int b0 = kClasses * a.colour;
-    const int64_t c0 = a.wl_cnt[b0], c1 = a.wl_cnt[b0 + 1], c2 = a.wl_cnt[b0 + 2],
-                  c3 = a.wl_cnt[b0 + 3];
-    // warp items: G = 4, 8, 16, 32 hold 8, 4, 2, 1 nodes
-    const int64_t i1 = ceil_div<int64_t>(c0, 8);
-    const int64_t i2 = i1 + ceil_div<int64_t>(c1, 4);
-    const int64_t i3 = i2 + ceil_div<int64_t>(c2, 2);
-    const int64_t i4 = i3 + c3;
-    const int lane = threadIdx.x & 31;
     const int64_t n = a.g.n;
-    while (true) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(&a.ctr->small_next, 1);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= i4) break;
-        if (it < i1) small_item<MODE, 4>(a, Wsm, a.wl + b0 * n, c0, it);
-        else if (it < i2) small_item<MODE, 8>(a, Wsm, a.wl + (b0 + 1) * n, c1, it - i1);
-        else if (it < i3) small_item<MODE, 16>(a, Wsm, a.wl + (b0 + 2) * n, c2, it - i2);
-        else small_item<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, c3, it - i3);
-    }
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    small_bin<MODE, 4>(a, Wsm, a.wl + b0 * n, a.wl_cnt[b0], gwarp, nwarps);
+    small_bin<MODE, 8>(a, Wsm, a.wl + (b0 + 1) * n, a.wl_cnt[b0 + 1], gwarp, nwarps);
+    small_bin<MODE, 16>(a, Wsm, a.wl + (b0 + 2) * n, a.wl_cnt[b0 + 2], gwarp, nwarps);
+    small_bin<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, a.wl_cnt[b0 + 3], gwarp, nwarps);
 }
 
 template <int MODE>
@@ -881,10 +905,11 @@ __device__ __forceinline__ int64_t peer_sum64(unsigned peers, int32_t c) {
 // Weighted radix select: the smallest key K such that the total weight of the
 // entries with key <= K is >= thr; ~0 if the total is < thr.  get(i, &key, &c)
 // returns entry i (c = 0 entries carry no weight).  Only the bits where
-// kmin and kmax differ are examined.  All threads of the CTA call it.
+// kmin and kmax differ are examined, kDigit bits per pass; each thread keeps
+// four entries in flight.  All threads of the CTA call it.
 template <typename Get>
 __device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uint64_t kmin,
-                                          uint64_t kmax, unsigned long long *hist /* [256] */,
+                                          uint64_t kmax, unsigned long long *hist /* [kBins] */,
                                           int64_t *s_acc, uint64_t *s_pf, int *s_done) {
     const int lane = threadIdx.x & 31;
     const uint64_t diff = kmin ^ kmax;
@@ -895,28 +920,44 @@ __device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uin
         *s_done = 0;
     }
     __syncthreads();
+    const int64_t step = 4 * (int64_t)blockDim.x;
     const int64_t cnt_r = ceil_div<int64_t>(cnt, blockDim.x) * blockDim.x;
-    for (int hb = top; hb >= 0; hb -= 8) {
-        const int width = hb + 1 < 8 ? hb + 1 : 8;
+    for (int hb = top; hb >= 0; hb -= kDigit) {
+        const int width = hb + 1 < kDigit ? hb + 1 : kDigit;
         const int shift = hb - width + 1;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        const unsigned nb = 1u << width;
+        for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         const uint64_t hm = (hb >= 63) ? 0ull : (~0ull << (hb + 1));
         const uint64_t pf = *s_pf;
-        for (int64_t i = threadIdx.x; i < cnt_r; i += blockDim.x) {
-            uint64_t key = 0;
-            int32_t c = 0;
-            if (i < cnt) get(i, &key, &c);
-            const bool in = i < cnt && c > 0 && (key & hm) == (pf & hm);
-            const unsigned d = in ? (unsigned)((key >> shift) & ((1u << width) - 1)) : 0xffffu;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int64_t s = peer_sum64(peers, in ? c : 0);
-            if (in && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&hist[d], (unsigned long long)s);
+        for (int64_t base = threadIdx.x; base < cnt_r; base += step) {
+            uint64_t kk[4];
+            int32_t cc[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t i = base + j * (int64_t)blockDim.x;
+                kk[j] = 0;
+                cc[j] = 0;
+                if (i < cnt) get(i, &kk[j], &cc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (base + j * (int64_t)blockDim.x >= cnt_r) break;  // warp-uniform
+                const bool in = cc[j] > 0 && (kk[j] & hm) == (pf & hm);
+                const unsigned d = in ? (unsigned)((kk[j] >> shift) & (nb - 1)) : 0xffffffffu;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int64_t sw = peer_sum64(peers, in ? cc[j] : 0);
+                if (in && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&hist[d], (unsigned long long)sw);
+            }
         }
         __syncthreads();
         if (threadIdx.x < 32) {
+            const unsigned per = nb / 32 > 0 ? nb / 32 : 1;  // bins per lane
             unsigned long long local = 0;
-            for (int j = 0; j < 8; j++) local += hist[lane * 8 + j];
+            for (unsigned j = 0; j < per; j++) {
+                const unsigned bi = lane * per + j;
+                if (bi < nb) local += hist[bi];
+            }
             unsigned long long inc = local;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -930,10 +971,12 @@ __device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uin
                 if (lane == 0) *s_done = 1;  // total below the threshold
             } else if (lane == __ffs(m) - 1) {
                 int64_t run = acc + (int64_t)(inc - local);
-                int d = lane * 8;
-                for (int j = 0; j < 8; j++) {
-                    if (run + (int64_t)hist[lane * 8 + j] >= thr) { d = lane * 8 + j; break; }
-                    run += (int64_t)hist[lane * 8 + j];
+                unsigned d = lane * per;
+                for (unsigned j = 0; j < per; j++) {
+                    const unsigned bi = lane * per + j;
+                    if (bi >= nb) break;
+                    if (run + (int64_t)hist[bi] >= thr) { d = bi; break; }
+                    run += (int64_t)hist[bi];
                 }
                 *s_acc = run;
                 *s_pf = pf | ((uint64_t)d << shift);
@@ -950,13 +993,22 @@ template <typename Get>
 __device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *out_max,
                              unsigned long long *red /* [64] */) {
     unsigned long long mn = ~0ull, mx = 0;
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        uint64_t key;
-        int32_t c;
-        get(i, &key, &c);
-        if (c <= 0) continue;
-        mn = key < mn ? key : mn;
-        mx = key > mx ? key : mx;
+    for (int64_t base = threadIdx.x; base < cnt; base += 4 * (int64_t)blockDim.x) {
+        uint64_t kk[4];
+        int32_t cc[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t i = base + j * (int64_t)blockDim.x;
+            kk[j] = 0;
+            cc[j] = 0;
+            if (i < cnt) get(i, &kk[j], &cc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (cc[j] <= 0) continue;
+            mn = kk[j] < mn ? kk[j] : mn;
+            mx = kk[j] > mx ? kk[j] : mx;
+        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -987,7 +1039,7 @@ __device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *
 
 struct ArbSm {
     WDelta wd;
-    unsigned long long hist[256];
+    unsigned long long hist[kBins];
     unsigned long long red[64];
     uint64_t keys[kSegSmem];
     int32_t c[kSegSmem];
@@ -1000,7 +1052,7 @@ struct ArbSm {
 // blockIdx < nW handle block b = blockIdx when its departures are contested;
 // the others pass the uncontested sources' proposals through.
 __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
-    __shared__ unsigned long long hist[256];
+    __shared__ unsigned long long hist[kBins];
     __shared__ unsigned long long red[64];
     __shared__ int64_t s_acc;
     __shared__ uint64_t s_pf;
@@ -1147,9 +1199,11 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         const uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, kmin, kmax, sm.hist, &sm.acc,
                                                  &sm.pf, &sm.done);
         for (int64_t i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
-            const SegEntry e = ent[i];
-            if (e.key < K || e.c == 0) {
-                apply_agg(a, sm.wd, (int32_t)(uint32_t)e.key, sg.T, e.own, e.c);
+            uint64_t key;
+            int32_t c;
+            get(i, &key, &c);
+            if (key < K || c == 0) {
+                apply_agg(a, sm.wd, (int32_t)(uint32_t)key, sg.T, ent[i].own, c);
                 moved++;
             }
         }
