@@ -14,10 +14,9 @@
 //                 single-piece row is finished in place, a longer one is
 //                 merged into its own global table and the CTA completing
 //                 the last piece selects the best label;
-//   medium nodes  CTA items of kMedItem nodes cut into chunks of <= kChunk
-//                 entries; a shared-memory linear-probing table keyed
-//                 (node slot, label) (the paper's Sec. IV.A choice of linear
-//                 probing) with an O(1) bitmap lookup of an entry's node;
+//   medium nodes  one warp per row with a warp-private shared-memory
+//                 linear-probing table (the paper's Sec. IV.A choice of
+//                 linear probing), no block-wide barriers;
 //   small nodes   G lanes per node (G = 4, 8, 16, 32; at most G entries):
 //                 __match_any_sync on (node, label) and __reduce_add_sync
 //                 give omega(v, L) in registers, shuffles pick the best.
@@ -51,12 +50,12 @@ namespace sclap {
 
 constexpr int kThreads = 256;
 constexpr int kSmallDeg = 32;            // small nodes: <= 32 entries (one warp pass)
-constexpr int kMedDeg = 512;             // medium nodes: 33..512 entries
-constexpr int kChunk = 1536;             // entries per shared-memory chunk / large piece
-constexpr int kChunkStep = kChunk - kMedDeg;
+constexpr int kMedDeg = 256;             // medium nodes: 33..256 entries (one warp each)
+constexpr int kChunk = 1536;             // entries per large-row piece (one CTA)
+constexpr int kWSlots = 512;             // per-warp table slots for medium rows (>= 2 * kMedDeg)
 constexpr int kSlots = 4096;             // hash table slots (>= 2 * kChunk)
 constexpr int kSlotBits = 12;
-constexpr int kMedItem = 64;             // medium worklist nodes per CTA item
+constexpr int kMedItem = 1;              // node slots of the CTA path (one large row at a time)
 constexpr int kDenseMaxK = 64;
 constexpr int kClasses = 5;              // buckets per colour
 constexpr int kSegSmem = 6144;           // contested segments staged in shared memory
@@ -68,8 +67,7 @@ constexpr uint64_t kEmpty = ~0ull;
 
 static_assert((1 << kSlotBits) == kSlots, "table size");
 static_assert(kSlots >= 2 * kChunk, "load factor <= 1/2");
-static_assert(kChunk >= kMedDeg, "a medium row fits a chunk");
-static_assert(kMedItem <= kThreads, "one thread per item node");
+static_assert(kWSlots >= 2 * kMedDeg, "per-warp table load <= 1/2");
 
 // MODE: 0 clustering (hash), 1 refinement (hash, k > 64), 2 refinement (dense)
 constexpr int kCluster = 0, kRefineHash = 1, kRefineDense = 2;
@@ -330,14 +328,12 @@ struct HashTab {
 };
 
 struct DenseTab {
-    int32_t acc[kMedItem * kDenseMaxK];
+    int32_t acc[kDenseMaxK];
 };
 
 template <int MODE>
 struct PropSm {
     typename std::conditional<MODE == kRefineDense, DenseTab, HashTab>::type t;
-    uint32_t bm[kChunk / 32 + 1];
-    int32_t bmpre[kChunk / 32 + 1];
     NodeSm nd;
     int64_t W[kDenseMaxK];
     int64_t scan_tmp[kThreads / 32 + 1];
@@ -624,131 +620,6 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
     }
 }
 
-template <int MODE>
-__device__ void process_medium(const LPArgs &a, PropSm<MODE> &sm, int k) {
-    constexpr bool DENSE = MODE == kRefineDense;
-    const int32_t *wl = a.wl + (int64_t)(kClasses * a.colour + 4) * a.g.n;
-    const int64_t nwl = a.wl_cnt[kClasses * a.colour + 4];
-    const int items = (int)ceil_div<int64_t>(nwl, kMedItem);
-    NodeSm &nd = sm.nd;
-    const int t = threadIdx.x;
-    while (true) {
-        __syncthreads();
-        if (t == 0) sm.item = atomicAdd(&a.ctr->med_next, 1);
-        __syncthreads();
-        const int item = sm.item;
-        if (item >= items) break;
-        const int64_t i0 = (int64_t)item * kMedItem;
-        const int ns = (int)min64(kMedItem, nwl - i0);
-        int32_t deg = 0;
-        if (t < ns) deg = load_node<MODE>(a, sm.W, nd, t, wl[i0 + t]);
-        int64_t E;
-        const int64_t pre = block_exclusive_scan<kThreads>((int64_t)deg, &E, sm.scan_tmp);
-        if (t < ns) nd.epre[t] = (int32_t)pre;
-        if (t == 0) nd.epre[ns] = (int32_t)E;
-        if (a.prof && t == 0) {
-            atomicAdd(&a.prof[0], (unsigned long long)E);
-            atomicAdd(&a.prof[1], (unsigned long long)ns);
-        }
-        __syncthreads();
-        const int nchunks = nd.epre[ns - 1] / kChunkStep + 1;
-        int s0 = 0;
-        for (int ch = 0; ch < nchunks; ch++) {
-            const int32_t lim = (ch + 1) * kChunkStep;
-            int lo = s0, hi = ns;  // s1: first slot with epre >= lim
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (nd.epre[mid] >= lim) hi = mid;
-                else lo = mid + 1;
-            }
-            const int s1 = lo;
-            if (s1 == s0) continue;
-            const int32_t e0 = nd.epre[s0];
-            const int32_t len = nd.epre[s1] - e0;
-            const int nwords = (len + 31) >> 5;
-            // bitmap of row starts -> O(1) owner lookup of an entry
-            for (int i = t; i < nwords; i += kThreads) sm.bm[i] = 0;
-            if (t == 0) sm.ndl = 0;
-            __syncthreads();
-            if (t >= s0 && t < s1) {
-                const int32_t le = nd.epre[t] - e0;
-                atomicOr(&sm.bm[le >> 5], 1u << (le & 31));
-            }
-            __syncthreads();
-            if (t < 32) {
-                int run = 0;
-                for (int base = 0; base < nwords; base += 32) {
-                    const int i = base + t;
-                    const int c = i < nwords ? __popc(sm.bm[i]) : 0;
-                    int inc = c;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, inc, d);
-                        if (t >= d) inc += y;
-                    }
-                    if (i < nwords) sm.bmpre[i] = run + inc - c;
-                    run += __shfl_sync(0xffffffffu, inc, 31);
-                }
-            }
-            __syncthreads();
-            for (int32_t lb = t; lb < len; lb += kUnroll * kThreads) {
-                int32_t sl[kUnroll], u[kUnroll], w[kUnroll], L[kUnroll];
-#pragma unroll
-                for (int j = 0; j < kUnroll; j++) {
-                    const int32_t le = lb + j * kThreads;
-                    u[j] = -1;
-                    w[j] = 0;
-                    sl[j] = 0;
-                    if (le < len) {
-                        const uint32_t word = sm.bm[le >> 5];
-                        const int s = s0 + sm.bmpre[le >> 5] +
-                                      __popc(word & (0xffffffffu >> (31 - (le & 31)))) - 1;
-                        const int64_t idx = nd.rs[s] + (e0 + le - nd.epre[s]);
-                        sl[j] = s;
-                        u[j] = __ldg(&a.g.adjncy[idx]);
-                        w[j] = __ldg(&a.g.adjwgt[idx]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kUnroll; j++) {
-                    if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != nd.cpv[sl[j]])
-                        u[j] = -1;
-                    L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : 0;
-                }
-#pragma unroll
-                for (int j = 0; j < kUnroll; j++) {
-                    if (u[j] < 0) continue;
-                    if constexpr (DENSE) {
-                        atomicAdd(&sm.t.acc[(sl[j] - s0) * k + L[j]], w[j]);
-                    } else {
-                        const uint64_t key = ((uint64_t)(uint32_t)sl[j] << 32) | (uint32_t)L[j];
-                        if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
-                                       key, w[j]))
-                            a.ctr->err = 1;
-                    }
-                }
-            }
-            __syncthreads();
-            if constexpr (DENSE) {
-                for (int s = s0 + (t >> 5); s < s1; s += kThreads / 32)
-                    select_dense_warp(a, sm.W, sm.t.acc + (s - s0) * k, k, nd, s);
-            } else {
-                const int ndl = sm.ndl;
-                select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, nd);
-                for (int i = t; i < ndl; i += kThreads) {
-                    const int slot = sm.t.dl[i];
-                    sm.t.keys[slot] = kEmpty;
-                    sm.t.vals[slot] = 0;
-                }
-            }
-            __syncthreads();
-            if (t >= s0 && t < s1) decide_and_emit<MODE>(a, sm.W, nd, t);
-            s0 = s1;
-            __syncthreads();
-        }
-    }
-}
-
 // Small nodes: G lanes per node, one pass (deg <= G).  Loading and computing
 // are split so a warp keeps kSmallIlp items' load chains in flight.
 constexpr int kSmallIlp = 4;
@@ -867,8 +738,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_propose(LPArgs a, int k) {
     extern __shared__ __align__(16) unsigned char smraw[];
     PropSm<MODE> &sm = *reinterpret_cast<PropSm<MODE> *>(smraw);
+    if (a.nL == 0) return;
     if constexpr (MODE == kRefineDense) {
-        for (int i = threadIdx.x; i < kMedItem * k; i += kThreads) sm.t.acc[i] = 0;
+        for (int i = threadIdx.x; i < kDenseMaxK; i += kThreads) sm.t.acc[i] = 0;
         for (int b = threadIdx.x; b < k; b += kThreads) sm.W[b] = a.W[b];
     } else {
         for (int i = threadIdx.x; i < kSlots; i += kThreads) {
@@ -876,20 +748,166 @@ __global__ void __launch_bounds__(kThreads) k_propose(LPArgs a, int k) {
             sm.t.vals[i] = 0;
         }
     }
-    if (a.nL > 0) process_large<MODE>(a, sm, k);
-    process_medium<MODE>(a, sm, k);
+    process_large<MODE>(a, sm, k);
 }
 
-// Nodes of degree <= 32: no shared memory but the dense W snapshot, so it runs
-// at full occupancy next to k_propose (side stream).
+// Medium rows (33..kMedDeg entries): one warp per row with a warp-private
+// shared-memory table, no block-wide barriers.
+struct WarpTab {
+    uint32_t keys[kWSlots];   // labels; 0xffffffff = empty
+    int32_t vals[kWSlots];
+    uint16_t dl[kMedDeg];     // slots in insertion order
+    int ndl;
+};
+
+constexpr uint32_t kEmpty32 = 0xffffffffu;
+
+__device__ __forceinline__ void wtab_add(WarpTab &t, uint32_t L, int32_t w) {
+    uint32_t slot = (uint32_t)(((uint64_t)L * 0x9E3779B97F4A7C15ull) >> 55) & (kWSlots - 1);
+    for (int probe = 0; probe < kWSlots; probe++) {
+        const uint32_t prev = atomicCAS(&t.keys[slot], kEmpty32, L);
+        if (prev == kEmpty32 || prev == L) {
+            atomicAdd(&t.vals[slot], w);
+            if (prev == kEmpty32) t.dl[atomicAdd(&t.ndl, 1)] = (uint16_t)slot;
+            return;
+        }
+        slot = (slot + 1) & (kWSlots - 1);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, WarpTab &t,
+                                           int32_t *dacc, int k, int32_t v) {
+    constexpr bool DENSE = MODE == kRefineDense;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = a.g.xadj[v];
+    const int32_t deg = (int32_t)(a.g.xadj[v + 1] - b);
+    const int32_t own = a.lab[v];
+    const int32_t c = a.g.vwgt[v];
+    const int32_t cpv = (MODE == kCluster && a.cp) ? a.cp[v] : 0;
+    const int64_t Wown = MODE == kCluster ? 0 : (DENSE ? Wsm[own] : a.W[own]);
+    const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+    if (a.prof && lane == 0) {
+        atomicAdd(&a.prof[0], (unsigned long long)deg);
+        atomicAdd(&a.prof[1], 1ull);
+    }
+    for (int32_t e0 = 0; e0 < deg; e0 += 32 * kUnroll) {
+        int32_t u[kUnroll], w[kUnroll], L[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            const int32_t e = e0 + j * 32 + lane;
+            u[j] = e < deg ? __ldg(&a.g.adjncy[b + e]) : -1;
+            w[j] = e < deg ? __ldg(&a.g.adjwgt[b + e]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != cpv) u[j] = -1;
+            L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; j++) {
+            if (u[j] < 0) continue;
+            if constexpr (DENSE) atomicAdd(&dacc[L[j]], w[j]);
+            else wtab_add(t, (uint32_t)L[j], w[j]);
+        }
+    }
+    __syncwarp();
+    unsigned long long best = 0;
+    int32_t ownw = 0, bl = 0x7fffffff;
+    if constexpr (DENSE) {
+        const int32_t w0 = lane < k ? dacc[lane] : 0;
+        const int32_t w1 = lane + 32 < k ? dacc[lane + 32] : 0;
+        __syncwarp();
+        if (lane < k) dacc[lane] = 0;
+        if (lane + 32 < k) dacc[lane + 32] = 0;
+        ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
+        unsigned long long ck0 = 0, ck1 = 0;
+        if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane);
+        if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32))
+            ck1 = cand_key(w1, h, lane + 32);
+        best = ck0 > ck1 ? ck0 : ck1;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+            best = o > best ? o : best;
+        }
+        if (best != 0 && ck0 == best) bl = lane;
+        else if (best != 0 && ck1 == best) bl = lane + 32;
+    } else {
+        const int nd = t.ndl;
+        constexpr int PER = kMedDeg / 32;  // distinct labels per lane (<= deg)
+        unsigned long long ck[PER];
+        int32_t lab[PER];
+#pragma unroll
+        for (int j = 0; j < PER; j++) {
+            ck[j] = 0;
+            lab[j] = 0;
+            const int i = lane + 32 * j;
+            if (i < nd) {
+                const int slot = t.dl[i];
+                const int32_t L = (int32_t)t.keys[slot];
+                const int32_t w = t.vals[slot];
+                t.keys[slot] = kEmpty32;
+                t.vals[slot] = 0;
+                lab[j] = L;
+                if (L == own) ownw = w;
+                else if (a.W[L] + c <= bnd(a, L)) ck[j] = cand_key(w, h, L);
+                best = ck[j] > best ? ck[j] : best;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+            best = o > best ? o : best;
+            ownw += __shfl_xor_sync(0xffffffffu, ownw, d);
+        }
+#pragma unroll
+        for (int j = 0; j < PER; j++)
+            if (best != 0 && ck[j] == best) bl = min(bl, lab[j]);
+        __syncwarp();
+        if (lane == 0) t.ndl = 0;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) bl = min(bl, __shfl_xor_sync(0xffffffffu, bl, d));
+    __syncwarp();
+    if (lane == 0 && best != 0) {
+        const int32_t gain = (int32_t)(best >> 32) - ownw;
+        const bool ovl = MODE != kCluster && Wown > bnd(a, own);
+        if (gain > 0 || ovl) {
+            const int64_t wT = DENSE ? Wsm[bl] : a.W[bl];
+            emit<DENSE>(a, v, bl, own, gain, c, ovl, wT);
+        }
+    }
+}
+
+// Rows of <= kMedDeg entries: warps take small-row items (G lanes per row)
+// and then medium rows (a warp per row).  Runs next to k_propose (side stream).
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_propose_small(LPArgs a, int k) {
     __shared__ int64_t W[kDenseMaxK];
+    __shared__ WarpTab tabs[MODE == kRefineDense ? 1 : kThreads / 32];
+    __shared__ int32_t dacc[MODE == kRefineDense ? kThreads / 32 : 1][kDenseMaxK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (MODE == kRefineDense) {
         for (int b = threadIdx.x; b < k; b += kThreads) W[b] = a.W[b];
-        __syncthreads();
+        for (int b = lane; b < kDenseMaxK; b += 32) dacc[warp][b] = 0;
+    } else {
+        for (int i = lane; i < kWSlots; i += 32) {
+            tabs[warp].keys[i] = kEmpty32;
+            tabs[warp].vals[i] = 0;
+        }
+        if (lane == 0) tabs[warp].ndl = 0;
     }
+    __syncthreads();
     process_small<MODE>(a, W);
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int bm = kClasses * a.colour + 4;
+    const int32_t *wl = a.wl + (int64_t)bm * a.g.n;
+    const int64_t nmed = a.wl_cnt[bm];
+    WarpTab &t = tabs[MODE == kRefineDense ? 0 : warp];
+    int32_t *dacc_w = dacc[MODE == kRefineDense ? warp : 0];
+    for (int64_t i = gwarp; i < nmed; i += nwarps) medium_row<MODE>(a, W, t, dacc_w, k, wl[i]);
 }
 
 // ---------------------------------------------------------------- arbitration
