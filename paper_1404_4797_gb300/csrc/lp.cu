@@ -59,6 +59,7 @@ constexpr int kMedItem = 1;              // node slots of the CTA path (one larg
 constexpr int kDenseMaxK = 64;
 constexpr int kClasses = 5;              // buckets per colour
 constexpr int kSegSmem = 6144;           // contested segments staged in shared memory
+constexpr int kBigTile = 4096;           // longer segments: tiles spread over the grid
 constexpr int kDigit = 11;               // radix-select digit width
 constexpr int kBins = 1 << kDigit;
 constexpr int kUnroll = 4;               // entries in flight per thread
@@ -92,7 +93,28 @@ struct Ctr {
     int32_t nprop, nseg;
     int64_t segtotal;
     int32_t large_next, med_next, small_next;
-    int32_t err;
+    int32_t err;              // kErrTable or kErrBarrier
+    int32_t nbig, bigtiles;   // segments above kSegSmem and their tiles
+};
+
+constexpr int32_t kErrTable = 1;
+constexpr int32_t kErrBarrier = 2;
+constexpr int32_t kErrBig = 4;
+
+// A contested segment too long for one CTA: its select is spread over tiles
+// of kBigTile entries handled by all CTAs of the arbitration grid.
+struct BigSeg {
+    int32_t si;                     // index into segs
+    int32_t tiles, t0;              // its tiles: [t0, t0 + tiles)
+    int32_t arrived;                // tiles histogrammed in the current pass
+    unsigned long long kmin, kmax;  // over entries with c > 0
+    unsigned long long pf;          // key bits fixed by the passes so far
+    long long acc;                  // weight of the entries below the prefix
+    int32_t done;                   // 1: total weight below the threshold
+};
+
+struct GridBar {
+    unsigned count, gen;
 };
 
 struct LPArgs {
@@ -133,6 +155,12 @@ struct LPArgs {
     unsigned long long *hbest;
     int32_t *hbestL, *hown;
     unsigned long long *prof;  // [2] entries, nodes, or null
+    // segments above kSegSmem entries (arbitrated by the whole grid)
+    BigSeg *big;
+    int32_t *tileseg;          // tile -> index into big
+    unsigned long long *bhist; // [maxbig * kBins], zero between uses
+    GridBar *bar;
+    int32_t maxbig, maxtiles;
 };
 
 // Bound of label L (U, L_max, or the run's L_max in batched runs).
@@ -524,7 +552,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 } else {
                     if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
                                    (uint64_t)(uint32_t)L[j], w[j]))
-                        a.ctr->err = 1;
+                        a.ctr->err = kErrTable;
                 }
             }
         }
@@ -605,7 +633,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                         }
                         q = (q + 1) & (cap - 1);
                     }
-                    if (!placed) a.ctr->err = 1;
+                    if (!placed) a.ctr->err = kErrTable;
                 }
                 // one append per warp for the slots it inserted first
                 const unsigned m = __ballot_sync(0xffffffffu, gslot >= 0);
@@ -1135,6 +1163,17 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
                                                     (unsigned long long)cnt);
             a.tbase[p.T] = base;
             a.segs[si] = Seg{p.T, cnt, base, cap + 1};
+            if (cnt > kSegSmem) {
+                const int nt = (cnt + kBigTile - 1) / kBigTile;
+                const int bi = atomicAdd(&a.ctr->nbig, 1);
+                const int t0 = atomicAdd(&a.ctr->bigtiles, nt);
+                if (bi >= a.maxbig || t0 + nt > a.maxtiles) {
+                    a.ctr->err = kErrBig;  // cannot happen: capacities bound the totals
+                } else {
+                    a.big[bi] = BigSeg{si, nt, t0, 0, ~0ull, 0ull, 0ull, 0ll, 0};
+                    for (int t = 0; t < nt; t++) a.tileseg[t0 + t] = bi;
+                }
+            }
         }
     }
     wd_flush(a, wd);
@@ -1156,6 +1195,251 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
     }
 }
 
+// Grid-wide barrier of a cooperative launch.  The wait is bounded: a CTA
+// that waits longer than kBarCycles (or sees the error flag raised) sets
+// kErrBarrier and goes on; the host then reports the failure.
+constexpr long long kBarCycles = 4000000000ll;  // about two seconds at 2 GHz
+
+__device__ void grid_barrier(GridBar *bar, int32_t *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &bar->gen;
+        volatile int32_t *verr = err;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned old = atomicAdd(&bar->count, 1u);
+        if (old == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g0) {
+                if (*verr & kErrBarrier) break;
+                if (clock64() - t0 > kBarCycles) {
+                    atomicOr(err, kErrBarrier);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Highest differing key bit of a big segment, or -1 if it has no weighted entry.
+__device__ __forceinline__ int big_top(unsigned long long kmin, unsigned long long kmax) {
+    if (kmin > kmax) return -1;
+    const unsigned long long diff = kmin ^ kmax;
+    return diff ? 63 - __clzll((long long)diff) : 0;
+}
+
+__device__ __forceinline__ int big_passes(int top) { return top < 0 ? 0 : top / kDigit + 1; }
+
+// Control values of big-segment tile t, read by thread 0 and handed to the
+// CTA through shared memory so that every thread takes the same branches.
+struct BigTile {
+    int32_t ok, bi, len, top, done;
+    int64_t i0;
+    Seg sg;
+    unsigned long long kmin, pf;
+};
+
+__device__ __forceinline__ BigTile big_tile(const LPArgs &a, int t, int nbig, BigTile *s_bt) {
+    if (threadIdx.x == 0) {
+        BigTile bt{};
+        const int32_t bi = a.tileseg[t];
+        if (bi >= 0 && bi < nbig) {
+            const BigSeg *b = &a.big[bi];
+            bt.bi = bi;
+            bt.sg = a.segs[b->si];
+            bt.i0 = (int64_t)(t - b->t0) * kBigTile;
+            const int64_t rest = bt.sg.cnt - bt.i0;
+            bt.len = (int)(rest < kBigTile ? rest : kBigTile);
+            bt.kmin = __ldcg(&b->kmin);
+            bt.top = big_top(bt.kmin, __ldcg(&b->kmax));
+            bt.done = __ldcg(&b->done);
+            bt.pf = __ldcg(&b->pf);
+            bt.ok = bt.len > 0 && bt.i0 >= 0;
+        }
+        *s_bt = bt;
+    }
+    __syncthreads();
+    const BigTile bt = *s_bt;
+    __syncthreads();
+    return bt;
+}
+
+// Segments of more than kSegSmem entries: the weighted select of
+// select_first_reaching, with each pass's histogram summed over the tiles of
+// all CTAs.  The CTA that flushes a segment's last tile of a pass picks the
+// digit; a grid barrier separates the passes.  Tile blockIdx.x stays staged in
+// shared memory from the first read to the last.
+__device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, int64_t &moved) {
+    __shared__ int s_flag, s_passes;
+    __shared__ BigTile s_bt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // pass 0: key range of each segment
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BigTile bt = big_tile(a, t, nbig, &s_bt);
+        if (!bt.ok) continue;
+        const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
+        const bool stage = t == (int)blockIdx.x;
+        unsigned long long mn = ~0ull, mx = 0;
+        for (int i = threadIdx.x; i < bt.len; i += blockDim.x) {
+            const SegEntry e = ent[i];
+            if (stage) {
+                sm.keys[i] = e.key;
+                sm.c[i] = e.c;
+            }
+            if (e.c > 0) {
+                mn = e.key < mn ? e.key : mn;
+                mx = e.key > mx ? e.key : mx;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn, d);
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, d);
+            mn = x < mn ? x : mn;
+            mx = y > mx ? y : mx;
+        }
+        if (lane == 0 && mn <= mx) {
+            atomicMin(&a.big[bt.bi].kmin, mn);
+            atomicMax(&a.big[bt.bi].kmax, mx);
+        }
+        __syncthreads();
+    }
+    grid_barrier(a.bar, &a.ctr->err);
+    if (threadIdx.x == 0) s_passes = 0;
+    __syncthreads();
+    {
+        int mp = 0;
+        for (int bi = threadIdx.x; bi < nbig; bi += blockDim.x)
+            mp = max(mp, big_passes(big_top(__ldcg(&a.big[bi].kmin), __ldcg(&a.big[bi].kmax))));
+        atomicMax(&s_passes, mp);
+    }
+    __syncthreads();
+    const int passes = s_passes;
+    for (int p = 0; p < passes; p++) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const BigTile bt = big_tile(a, t, nbig, &s_bt);
+            if (!bt.ok || p >= big_passes(bt.top) || bt.done) continue;
+            BigSeg *b = &a.big[bt.bi];
+            const int hb = bt.top - p * kDigit;
+            const int width = hb + 1 < kDigit ? hb + 1 : kDigit;
+            const int shift = hb - width + 1;
+            const unsigned nb = 1u << width;
+            const unsigned long long hm = hb >= 63 ? 0ull : (~0ull << (hb + 1));
+            const unsigned long long pf =
+                p == 0 ? (bt.top >= 63 ? 0ull : (bt.kmin & (~0ull << (bt.top + 1)))) : bt.pf;
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) sm.hist[i] = 0;
+            __syncthreads();
+            const bool staged = t == (int)blockIdx.x;
+            const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
+            const int len_r = (bt.len + blockDim.x - 1) / blockDim.x * blockDim.x;
+            for (int i = threadIdx.x; i < len_r; i += blockDim.x) {
+                uint64_t key = 0;
+                int32_t c = 0;
+                if (i < bt.len) {
+                    if (staged) {
+                        key = sm.keys[i];
+                        c = sm.c[i];
+                    } else {
+                        const SegEntry e = ent[i];
+                        key = e.key;
+                        c = e.c;
+                    }
+                }
+                const bool in = c > 0 && (key & hm) == (pf & hm);
+                const unsigned d = in ? (unsigned)((key >> shift) & (nb - 1)) : 0xffffffffu;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int64_t sw = peer_sum64(peers, in ? c : 0);
+                if (in && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&sm.hist[d], (unsigned long long)sw);
+            }
+            __syncthreads();
+            unsigned long long *gh = a.bhist + (size_t)bt.bi * kBins;
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x)
+                if (sm.hist[i]) atomicAdd(&gh[i], sm.hist[i]);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_flag = atomicAdd(&b->arrived, 1) == __ldcg(&b->tiles) - 1;
+            __syncthreads();
+            const int last = s_flag;
+            __syncthreads();
+            if (!last) continue;
+            // last tile of this segment in this pass: pick the digit
+            __threadfence();
+            if (warp == 0) {
+                const long long acc = p == 0 ? 0ll : __ldcg(&b->acc);
+                const unsigned per = nb / 32 > 0 ? nb / 32 : 1;
+                unsigned long long local = 0;
+                for (unsigned j = 0; j < per; j++) {
+                    const unsigned bi2 = lane * per + j;
+                    if (bi2 < nb) local += __ldcg(&gh[bi2]);
+                }
+                unsigned long long inc = local;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                const bool reach = acc + (long long)inc >= bt.sg.thr;
+                const unsigned m = __ballot_sync(0xffffffffu, reach);
+                if (m == 0) {
+                    if (lane == 0) b->done = 1;
+                } else if (lane == __ffs(m) - 1) {
+                    long long run = acc + (long long)(inc - local);
+                    unsigned d = lane * per;
+                    for (unsigned j = 0; j < per; j++) {
+                        const unsigned bi2 = lane * per + j;
+                        if (bi2 >= nb) break;
+                        const long long h = (long long)__ldcg(&gh[bi2]);
+                        if (run + h >= bt.sg.thr) { d = bi2; break; }
+                        run += h;
+                    }
+                    b->acc = run;
+                    b->pf = pf | ((unsigned long long)d << shift);
+                }
+            }
+            __syncthreads();
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) gh[i] = 0;
+            if (threadIdx.x == 0) b->arrived = 0;
+            __threadfence();
+            __syncthreads();
+        }
+        grid_barrier(a.bar, &a.ctr->err);
+    }
+    // admissions: keys below K (and entries of weight 0)
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BigTile bt = big_tile(a, t, nbig, &s_bt);
+        if (!bt.ok) continue;
+        const unsigned long long K = (bt.top < 0 || bt.done) ? ~0ull : bt.pf;
+        const bool staged = t == (int)blockIdx.x;
+        const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
+        for (int i = threadIdx.x; i < bt.len; i += blockDim.x) {
+            uint64_t key;
+            int32_t c;
+            if (staged) {
+                key = sm.keys[i];
+                c = sm.c[i];
+            } else {
+                const SegEntry e = ent[i];
+                key = e.key;
+                c = e.c;
+            }
+            if (key < K || c == 0) {
+                apply_agg(a, sm.wd, (int32_t)(uint32_t)key, bt.sg.T, ent[i].own, c);
+                moved++;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Launched cooperatively (all CTAs resident): segments of <= 32 entries take
+// one warp, up to kSegSmem one CTA, longer ones the whole grid.
 __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ArbSm &sm = *reinterpret_cast<ArbSm *>(smraw);
@@ -1188,44 +1472,40 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
             moved++;
         }
     }
-    // larger segments: one CTA each
+    // medium segments: one CTA each, staged in shared memory
     for (int si = blockIdx.x; si < nseg; si += gridDim.x) {
         const Seg sg = a.segs[si];
-        if (sg.cnt <= 32) continue;
+        if (sg.cnt <= 32 || sg.cnt > kSegSmem) continue;
         const SegEntry *ent = a.segbuf + sg.base;
-        const bool staged = sg.cnt <= kSegSmem;
-        if (staged) {
-            for (int i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
-                const SegEntry e = ent[i];
-                sm.keys[i] = e.key;
-                sm.c[i] = e.c;
-            }
-            __syncthreads();
+        for (int i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
+            const SegEntry e = ent[i];
+            sm.keys[i] = e.key;
+            sm.c[i] = e.c;
         }
+        __syncthreads();
         auto get = [&](int64_t i, uint64_t *key, int32_t *c) {
-            if (staged) {
-                *key = sm.keys[i];
-                *c = sm.c[i];
-            } else {
-                const SegEntry e = ent[i];
-                *key = e.key;
-                *c = e.c;
-            }
+            *key = sm.keys[i];
+            *c = sm.c[i];
         };
         uint64_t kmin, kmax;
         block_minmax(get, sg.cnt, &kmin, &kmax, sm.red);
         const uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, kmin, kmax, sm.hist, &sm.acc,
                                                  &sm.pf, &sm.done);
         for (int64_t i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
-            uint64_t key;
-            int32_t c;
-            get(i, &key, &c);
+            const uint64_t key = sm.keys[i];
+            const int32_t c = sm.c[i];
             if (key < K || c == 0) {
                 apply_agg(a, sm.wd, (int32_t)(uint32_t)key, sg.T, ent[i].own, c);
                 moved++;
             }
         }
         __syncthreads();
+    }
+    // long segments: the whole grid (the same branch in every CTA)
+    const int nbig = a.ctr->nbig, ntiles = a.ctr->bigtiles;
+    if (nbig > 0 && !(a.ctr->err & kErrBig) && nbig <= a.maxbig && ntiles <= a.maxtiles) {
+        __syncthreads();
+        arbitrate_big(a, sm, nbig, ntiles, moved);
     }
     wd_flush(a, sm.wd);
 #pragma unroll
@@ -1628,6 +1908,13 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.props = sc.get<Prop>(g.n);
     a.segs = sc.get<Seg>(g.n);
     a.segbuf = sc.get<SegEntry>(g.n);
+    // every big segment holds more than kSegSmem of the <= n proposals
+    a.maxbig = (int32_t)std::min<int64_t>(g.n / (kSegSmem + 1) + 1, cfg.nW);
+    a.maxtiles = (int32_t)(g.n / kBigTile + a.maxbig + 1);
+    a.big = sc.get<BigSeg>(a.maxbig);
+    a.tileseg = sc.get<int32_t>(a.maxtiles);
+    a.bhist = sc.zeros<unsigned long long>((size_t)a.maxbig * kBins);
+    a.bar = sc.zeros<GridBar>(1);
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
     int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + S);  // bucket lengths, then piece counts
     Ctr *ctr = sc.get<Ctr>(S);
@@ -1704,6 +1991,11 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     CK(cudaFuncSetAttribute(k_arbitrate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)sizeof(ArbSm)));
     const int grid_small = sms * 4;
+    int occ_arb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_arb, k_arbitrate, kThreads,
+                                                     sizeof(ArbSm)));
+    if (occ_arb < 1) fail(SCLAP_ECUDA, "arbitration kernel does not fit on an SM");
+    const int grid_arb = sms * std::min(occ_arb, 4);
 
     cudaStream_t side;
     CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
@@ -1777,7 +2069,11 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 LAUNCHED();
                 k_scatter<<<grid_small, kThreads, 0, s>>>(a);
                 LAUNCHED();
-                k_arbitrate<<<grid_small, kThreads, sizeof(ArbSm), s>>>(a);
+                {
+                    void *args[] = {&a};
+                    CK(cudaLaunchCooperativeKernel((const void *)k_arbitrate, dim3(grid_arb),
+                                                   dim3(kThreads), args, sizeof(ArbSm), s));
+                }
                 LAUNCHED();
                 k_reset_targets<<<grid_small, kThreads, 0, s>>>(a);
                 LAUNCHED();
@@ -1802,8 +2098,11 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     Ctr hc[32];
     CK(cudaMemcpyAsync(hc, ctr, S * sizeof(Ctr), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int j = 0; j < S; j++)
-        if (hc[j].err) fail(SCLAP_ECUDA, "hash table overflow");
+    for (int j = 0; j < S; j++) {
+        if (hc[j].err & kErrTable) fail(SCLAP_ECUDA, "hash table overflow");
+        if (hc[j].err & kErrBarrier) fail(SCLAP_ECUDA, "grid barrier timed out in arbitration");
+        if (hc[j].err & kErrBig) fail(SCLAP_ECUDA, "long-segment capacity exceeded");
+    }
     return done;
 }
 

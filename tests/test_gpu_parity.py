@@ -112,6 +112,37 @@ def test_refine_overloaded_start_matches_oracle():
         assert cut_g == cut_w and rd_g == rd_w
 
 
+@pytest.mark.parametrize("k,eps", [(2, 0.03), (5, 0.0), (5, 0.2)])
+def test_refine_long_segments_match_oracle(k, eps):
+    # tens of thousands of proposals per target block and sub-round: the
+    # select runs over tiles spread across the grid
+    g = I.random_graph(120000, 600000, seed=13, max_w=5, max_c=7)
+    gn = I.to_numpy(g)
+    n = gn["vwgt"].size
+    p0 = (np.arange(n, dtype=np.int64) * 2654435761 % k).astype(np.int32)
+    for Sr in (1, 4):
+        want, cut_w, bw_w, rd_w = oracle.refine(gn, k, eps, 5, Sr, 8, p0)
+        got, cut_g, bw_g, rd_g = S.sclap_refine(dev(g), k, eps, 5, Sr, 8,
+                                                torch.from_numpy(p0).cuda())
+        assert rd_g == rd_w, Sr
+        assert np.array_equal(got.cpu().numpy(), want), Sr
+        assert cut_g == cut_w and np.array_equal(bw_g.numpy(), bw_w)
+
+
+@pytest.mark.parametrize("leaves,U", [(20000, 500), (30000, 29000), (30000, 40000)])
+def test_cluster_long_segments_match_oracle(leaves, U):
+    # every leaf proposes the hub's label in the same sub-round
+    g = star(leaves, w=3)
+    gn = I.to_numpy(g)
+    gn["vwgt"] = (np.arange(leaves + 1) % 4 + 1).astype(np.int32)
+    g = {k: torch.from_numpy(v) for k, v in gn.items()}
+    for Sr in (1, 2):
+        want, rd_w = oracle.cluster(gn, U, 4, Sr, 5)
+        got, rd_g = S.sclap_cluster(dev(g), U, 4, Sr, 5)
+        assert rd_g == rd_w
+        assert np.array_equal(got.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 def test_contract_matches_oracle(name):
     g = GRAPHS[name]()

@@ -14,8 +14,9 @@ MUTANTS = {
     "propose on zero gain": ("if (gain > 0 || overloaded)", "if (gain >= 0 || overloaded)"),
     "tie-break reversed": ("else if (tl != best_tie) better = tl < best_tie;",
                            "else if (tl != best_tie) better = tl > best_tie;"),
-    "eligibility off by one": ("if (W[L] + vwgt[v] > B) continue; /* not eligible */",
-                               "if (W[L] + vwgt[v] >= B) continue; /* not eligible */"),
+    "eligibility off by one": (
+        "if (W[L] + vwgt[v] > bound_of(Bv, B, L)) continue; /* not eligible */",
+        "if (W[L] + vwgt[v] >= bound_of(Bv, B, L)) continue; /* not eligible */"),
     "exclusive prefix at target": ("if (!(p->c == 0 || sum <= cap)) p->keep = 0;",
                                    "if (!(p->c == 0 || sum < cap)) p->keep = 0;"),
     "departure cap inclusive": ("if (departed < excess) departed += ws->props[q].c;",
