@@ -99,18 +99,30 @@ __global__ void __launch_bounds__(kSortThreads)
 }
 
 // Stable scatter.  Warp w owns tile items [w*32*R, (w+1)*32*R) and walks them
-// in order (round-major, lane-minor), so ranks respect the input order.
+// in order (round-major, lane-minor), so ranks respect the input order.  The
+// tile is first rearranged in shared memory in digit order; the global writes
+// then go out as one contiguous run per digit.
+struct SortSm {
+    int wc[kSortWarps][kRadix];
+    int64_t goff[kRadix];
+    int dstart[kRadix];
+    int scan_tmp[kSortWarps + 1];
+    uint64_t k[kSortTile];
+    int32_t v[kSortTile];
+};
+
 __global__ void __launch_bounds__(kSortThreads)
     k_sort_scatter(const uint64_t *keys, const int32_t *vals, uint64_t *okeys, int32_t *ovals,
                    int64_t n, int shift, int64_t tiles, const int64_t *offs) {
-    __shared__ int wc[kSortWarps][kRadix];
-    __shared__ int64_t goff[kRadix];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    SortSm &sm = *reinterpret_cast<SortSm *>(smraw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wc[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&sm.wc[0][0])[i] = 0;
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
-        goff[d] = offs[(int64_t)d * tiles + blockIdx.x];
+        sm.goff[d] = offs[(int64_t)d * tiles + blockIdx.x];
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortRounds;
+    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t wbase = tbase + (int64_t)warp * 32 * kSortRounds;
     const unsigned lt = (1u << lane) - 1;
     uint64_t k[kSortRounds];
     int32_t v[kSortRounds];
@@ -121,33 +133,52 @@ __global__ void __launch_bounds__(kSortThreads)
         bool ok = i < n;
         k[r] = ok ? keys[i] : 0;
         v[r] = ok ? vals[i] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortRounds; r++) {
+        const bool ok = wbase + r * 32 + lane < n;
         uint32_t d = ok ? digit_of(k[r], shift) : kRadix;  // kRadix: padding
         unsigned peers = __match_any_sync(0xffffffffu, d);
-        int base = (d < kRadix) ? wc[warp][d] : 0;
+        int base = (d < kRadix) ? sm.wc[warp][d] : 0;
         __syncwarp();
-        if (d < kRadix && (peers & lt) == 0) wc[warp][d] = base + __popc(peers);
+        if (d < kRadix && (peers & lt) == 0) sm.wc[warp][d] = base + __popc(peers);
         __syncwarp();
         rk[r] = base + __popc(peers & lt);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+    // per digit: warp offsets, then the digit's start inside the tile
+    int tot = 0;
+    {
+        const int d = threadIdx.x;  // kSortThreads == kRadix
         int run = 0;
         for (int w = 0; w < kSortWarps; w++) {
-            int t = wc[w][d];
-            wc[w][d] = run;
+            const int t = sm.wc[w][d];
+            sm.wc[w][d] = run;
             run += t;
         }
+        tot = run;
     }
+    int all;
+    const int ds = block_exclusive_scan<kSortThreads>(tot, &all, sm.scan_tmp);
+    sm.dstart[threadIdx.x] = ds;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortRounds; r++) {
-        int64_t i = wbase + r * 32 + lane;
-        if (i < n) {
-            uint32_t d = digit_of(k[r], shift);
-            int64_t dst = goff[d] + wc[warp][d] + rk[r];
-            okeys[dst] = k[r];
-            ovals[dst] = v[r];
+        if (wbase + r * 32 + lane < n) {
+            const uint32_t d = digit_of(k[r], shift);
+            const int loc = sm.dstart[d] + sm.wc[warp][d] + rk[r];
+            sm.k[loc] = k[r];
+            sm.v[loc] = v[r];
         }
+    }
+    __syncthreads();
+    const int len = (int)min64(n - tbase, (int64_t)kSortTile);
+    for (int i = threadIdx.x; i < len; i += kSortThreads) {
+        const uint64_t key = sm.k[i];
+        const uint32_t d = digit_of(key, shift);
+        const int64_t dst = sm.goff[d] + (i - sm.dstart[d]);
+        okeys[dst] = key;
+        ovals[dst] = sm.v[i];
     }
 }
 
@@ -159,6 +190,9 @@ void radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, Scrat
     int32_t *v2 = sc.get<int32_t>(n);
     int64_t *hist = sc.get<int64_t>(tiles * kRadix);
     int64_t *offs = sc.get<int64_t>(tiles * kRadix);
+    static_assert(kSortThreads == kRadix, "one digit per thread in the scatter");
+    CK(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sizeof(SortSm)));
     uint64_t *ka = keys, *kb = k2;
     int32_t *va = vals, *vb = v2;
     int passes = 0;
@@ -166,8 +200,8 @@ void radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, Scrat
         k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, n, shift, tiles, hist);
         LAUNCHED();
         exclusive_scan(ArrayI64{hist}, tiles * kRadix, offs, nullptr, sc);
-        k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, tiles,
-                                                                offs);
+        k_sort_scatter<<<(unsigned)tiles, kSortThreads, sizeof(SortSm), s>>>(ka, va, kb, vb, n,
+                                                                             shift, tiles, offs);
         LAUNCHED();
         std::swap(ka, kb);
         std::swap(va, vb);
