@@ -58,6 +58,9 @@ constexpr int kSlotBits = 12;
 constexpr int kMedItem = 1;              // node slots of the CTA path (one large row at a time)
 constexpr int kDenseMaxK = 64;
 constexpr int kClasses = 5;              // buckets per colour
+constexpr int kHugeCS = 8;               // CTAs per cluster for rows above kChunk (hash modes)
+constexpr int kHugeSlots = 4096;         // table slots per CTA of such a cluster (2^12)
+constexpr int kHugeDeg = kHugeCS * kHugeSlots / 2;  // longest row one cluster takes (16384)
 constexpr int kSegSmem = 6144;           // contested segments staged in shared memory
 constexpr int kBigTile = 4096;           // longer segments: tiles spread over the grid
 constexpr int kDigit = 11;               // radix-select digit width
@@ -95,6 +98,7 @@ struct Ctr {
     int32_t large_next, med_next, small_next;
     int32_t err;              // kErrTable or kErrBarrier
     int32_t nbig, bigtiles;   // segments above kSegSmem and their tiles
+    int32_t huge_next;        // next row of the cluster path
 };
 
 constexpr int32_t kErrTable = 1;
@@ -155,6 +159,11 @@ struct LPArgs {
     unsigned long long *hbest;
     int32_t *hbestL, *hown;
     unsigned long long *prof;  // [2] entries, nodes, or null
+    // rows of kChunk < degree <= kHugeDeg in the hash modes: one CTA cluster
+    // each; hlist + c * nL lists colour c's rows (indices into Lnodes)
+    int32_t huge_on;
+    int32_t *hlist;
+    int32_t *hcnt;
     // segments above kSegSmem entries (arbitrated by the whole grid)
     BigSeg *big;
     int32_t *tileseg;          // tile -> index into big
@@ -277,10 +286,15 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
                             if (a.Lnodes[mid] <= v) lo = mid;
                             else hi = mid;
                         }
-                        const int64_t np = a.Lpre[lo + 1] - a.Lpre[lo];
-                        const int base = atomicAdd(&a.pcnt[col], (int)np);
-                        int64_t *pl = a.plist + (int64_t)col * a.Ptot + base;
-                        for (int64_t p = 0; p < np; p++) pl[p] = (lo << 20) | p;
+                        if (a.huge_on && d > kChunk && d <= kHugeDeg) {
+                            const int pos = atomicAdd(&a.hcnt[col], 1);
+                            a.hlist[(int64_t)col * a.nL + pos] = (int32_t)lo;
+                        } else {
+                            const int64_t np = a.Lpre[lo + 1] - a.Lpre[lo];
+                            const int base = atomicAdd(&a.pcnt[col], (int)np);
+                            int64_t *pl = a.plist + (int64_t)col * a.Ptot + base;
+                            for (int64_t p = 0; p < np; p++) pl[p] = (lo << 20) | p;
+                        }
                     }
                 }
             }
@@ -1644,13 +1658,167 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- rows of one CTA cluster
+
+// Rows with kChunk < degree <= kHugeDeg (hash modes): a cluster of kHugeCS
+// CTAs takes one row at a time.  The row's (label, omega) sums live in one
+// open-addressing table spread over the CTAs' shared memory (slot s sits in
+// CTA s / T); each CTA reads a contiguous share of the row and inserts into
+// the owning CTA's slots through distributed shared memory.  The table has
+// >= 2 * degree slots, so an insert always finds room.  Selection follows
+// k_hub_cand / k_hub_tie / k_hub_emit: the largest eligible cand_key, then
+// the smallest label holding it, then the gain rule of Sec. III.A.
+struct HugeSm {
+    uint32_t keys[kHugeSlots];
+    int32_t vals[kHugeSlots];
+    unsigned long long red[kThreads / 32];
+    unsigned long long best;  // rank 0: cluster-wide best cand_key
+    int32_t bestL, ownw;      // rank 0
+    int32_t item;             // rank 0: index into this colour's row list
+};
+
+__device__ __forceinline__ void huge_insert(cg::cluster_group &cl, HugeSm &sm, uint32_t L,
+                                            int32_t w, int tbits, int lbits) {
+    const uint32_t tmask = (1u << tbits) - 1;
+    uint32_t q = (L * 0x9E3779B1u) >> (32 - tbits);
+    for (uint32_t probe = 0; probe <= tmask; probe++) {
+        const unsigned owner = q >> lbits;
+        const uint32_t loc = q & ((1u << lbits) - 1);
+        uint32_t *kp = cl.map_shared_rank(&sm.keys[loc], owner);
+        const uint32_t prev = atomicCAS(kp, kEmpty32, L);
+        if (prev == kEmpty32 || prev == L) {
+            atomicAdd(cl.map_shared_rank(&sm.vals[loc], owner), w);
+            return;
+        }
+        q = (q + 1) & tmask;
+    }
+}
+
+template <int MODE>
+__global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
+    k_propose_huge(LPArgs a) {
+    __shared__ HugeSm sm;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    HugeSm *r0 = cl.map_shared_rank(&sm, 0u);
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kHugeSlots; i += kThreads) {
+        sm.keys[i] = kEmpty32;
+        sm.vals[i] = 0;
+    }
+    const int nrows = a.hcnt[a.colour];
+    const int32_t *hl = a.hlist + (int64_t)a.colour * a.nL;
+    while (true) {
+        if (rank == 0 && threadIdx.x == 0) {
+            sm.item = atomicAdd(&a.ctr->huge_next, 1);
+            sm.best = 0;
+            sm.bestL = 0x7fffffff;
+            sm.ownw = 0;
+        }
+        cl.sync();
+        const int it = r0->item;
+        if (it >= nrows) break;  // the same value in every CTA of the cluster
+        const int32_t li = hl[it];
+        const int32_t v = a.Lnodes[li];
+        const int64_t rs = a.g.xadj[v];
+        const int64_t deg = a.g.xadj[v + 1] - rs;
+        const int32_t own = a.lab[v], c = a.g.vwgt[v];
+        const int32_t cpv = (MODE == kCluster && a.cp) ? a.cp[v] : 0;
+        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+        int lbits = 6;  // slots per CTA: 2^lbits, total >= 2 * deg
+        while (((int64_t)kHugeCS << lbits) < 2 * deg) lbits++;
+        if (lbits > 12) {  // rows are routed here only up to kHugeDeg
+            lbits = 12;
+            if (rank == 0 && threadIdx.x == 0) a.ctr->err = kErrTable;
+        }
+        const int tbits = lbits + 3;  // kHugeCS == 8
+        const int T = 1 << lbits;
+        if (a.prof && rank == 0 && threadIdx.x == 0) {
+            atomicAdd(&a.prof[0], (unsigned long long)deg);
+            atomicAdd(&a.prof[1], 1ull);
+        }
+        const int64_t e0 = deg * rank / kHugeCS, e1 = deg * (rank + 1) / kHugeCS;
+        const int64_t span = e1 - e0;
+        const int64_t span_r = (span + 31) & ~31ll;  // whole warps for match_any
+        for (int64_t eb = threadIdx.x; eb < span_r; eb += kUnroll * kThreads) {
+            int32_t u[kUnroll], w[kUnroll], L[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                const int64_t e = eb + j * kThreads;
+                u[j] = e < span ? __ldg(&a.g.adjncy[rs + e0 + e]) : -1;
+                w[j] = e < span ? __ldg(&a.g.adjwgt[rs + e0 + e]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != cpv) u[j] = -1;
+                L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < kUnroll; j++) {
+                if (eb + j * kThreads >= span_r) break;  // warp-uniform
+                // merge equal labels within the warp first
+                const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)L[j]);
+                const unsigned sum = __reduce_add_sync(peers, (unsigned)w[j]);
+                if (L[j] >= 0 && (peers & ((1u << lane) - 1)) == 0)
+                    huge_insert(cl, sm, (uint32_t)L[j], (int32_t)sum, tbits, lbits);
+            }
+        }
+        cl.sync();
+        // this CTA's slots: best eligible candidate and the own label's sum
+        unsigned long long best = 0;
+        for (int i = threadIdx.x; i < T; i += kThreads) {
+            const uint32_t L = sm.keys[i];
+            if (L == kEmpty32) continue;
+            const int32_t w = sm.vals[i];
+            if ((int32_t)L == own) r0->ownw = w;
+            else if (a.W[L] + c <= bnd(a, (int32_t)L)) {
+                const unsigned long long ck = cand_key(w, h, (int32_t)L);
+                best = ck > best ? ck : best;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+            best = o > best ? o : best;
+        }
+        if (lane == 0) sm.red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < kThreads / 32; i++) best = sm.red[i] > best ? sm.red[i] : best;
+            if (best) atomicMax(&r0->best, best);
+        }
+        cl.sync();
+        const unsigned long long b = r0->best;
+        for (int i = threadIdx.x; i < T; i += kThreads) {
+            const uint32_t L = sm.keys[i];
+            if (L == kEmpty32) continue;
+            const int32_t w = sm.vals[i];
+            if (b != 0 && (int32_t)L != own && (uint32_t)w == (uint32_t)(b >> 32) &&
+                cand_key(w, h, (int32_t)L) == b && a.W[L] + c <= bnd(a, (int32_t)L))
+                atomicMin(&r0->bestL, (int32_t)L);
+            sm.keys[i] = kEmpty32;
+            sm.vals[i] = 0;
+        }
+        cl.sync();
+        if (rank == 0 && threadIdx.x == 0 && b != 0) {
+            const int32_t gain = (int32_t)(b >> 32) - sm.ownw;
+            const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
+            if (gain > 0 || ovl) {
+                const int32_t L = sm.bestL;
+                emit<false>(a, v, L, own, gain, c, ovl, a.W[L]);
+            }
+        }
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 struct HubFin {
     const int64_t *xadj;
     const int32_t *Lnodes;
     __device__ int64_t operator()(int64_t i) const {
         const int32_t v = Lnodes[i];
         const int64_t d = xadj[v + 1] - xadj[v];
-        return d <= kChunk ? 0 : ceil_div<int64_t>(d, kFin);
+        return d <= kHugeDeg ? 0 : ceil_div<int64_t>(d, kFin);
     }
 };
 
@@ -1689,7 +1857,7 @@ struct LargeCap {
     __device__ int64_t operator()(int64_t i) const {
         const int32_t v = Lnodes[i];
         const int64_t d = xadj[v + 1] - xadj[v];
-        if (d <= kChunk) return 0;
+        if (d <= kHugeDeg) return 0;
         int64_t c = 1;
         while (c < 2 * d) c <<= 1;
         return c;
@@ -1702,7 +1870,7 @@ struct LargeDl {
     __device__ int64_t operator()(int64_t i) const {
         const int32_t v = Lnodes[i];
         const int64_t d = xadj[v + 1] - xadj[v];
-        return d <= kChunk ? 0 : d;
+        return d <= kHugeDeg ? 0 : d;
     }
 };
 
@@ -1916,12 +2084,15 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.bhist = sc.zeros<unsigned long long>((size_t)a.maxbig * kBins);
     a.bar = sc.zeros<GridBar>(1);
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
-    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + S);  // bucket lengths, then piece counts
+    // bucket lengths, then piece counts, then cluster-path row counts (per colour)
+    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + 2 * S);
     Ctr *ctr = sc.get<Ctr>(S);
     int64_t *d_moves = sc.zeros<int64_t>(cfg.rounds);
     a.wl = wl;
     a.wl_cnt = wl_cnt;
     a.pcnt = wl_cnt + kClasses * S;
+    a.hcnt = wl_cnt + kClasses * S + S;
+    a.huge_on = mode != kRefineDense;
     a.prof = prof().on ? prof().d_counts : nullptr;
 
     // nodes of degree > kMedDeg: one list per call, cut into kChunk pieces
@@ -1945,6 +2116,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             CK(cudaMemcpyAsync(&a.Ptot, Lpre + nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             a.plist = sc.get<int64_t>((size_t)S * (a.Ptot ? a.Ptot : 1));
+            a.hlist = sc.get<int32_t>((size_t)S * nL);
             a.Ldone = sc.zeros<int32_t>(nL);
             a.Lndl = sc.zeros<int32_t>(nL);
             if (mode == kRefineDense) {
@@ -1997,11 +2169,15 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     if (occ_arb < 1) fail(SCLAP_ECUDA, "arbitration kernel does not fit on an SM");
     const int grid_arb = sms * std::min(occ_arb, 4);
 
-    cudaStream_t side;
+    cudaStream_t side, side2;
     CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    cudaEvent_t ev_fork, ev_join;
+    CK(cudaStreamCreateWithFlags(&side2, cudaStreamNonBlocking));
+    cudaEvent_t ev_fork, ev_join, ev_join2;
     CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming));
+    const bool huge = a.huge_on && a.nL > 0;
+    const int grid_huge = std::max(kHugeCS, (sms * 2) / kHugeCS * kHugeCS);
     int occ_small = 0;
     switch (mode) {
         case kCluster: CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_small, k_propose_small<kCluster>, kThreads, 0)); break;
@@ -2016,7 +2192,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         for (int r = 0; r < cfg.rounds; r++) {
             a.round = r;
             a.moves = d_moves + r;
-            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + S) * sizeof(int32_t), s));
+            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + 2 * S) * sizeof(int32_t), s));
             CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
             k_build_wl<<<sms * 4, kThreads, 0, s>>>(a, wl, wl_cnt);
             LAUNCHED();
@@ -2035,6 +2211,16 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 }
                 LAUNCHED();
                 CK(cudaEventRecord(ev_join, side));
+                if (huge) {
+                    // rows of one CTA cluster on a second side stream
+                    CK(cudaStreamWaitEvent(side2, ev_fork, 0));
+                    if (mode == kCluster)
+                        k_propose_huge<kCluster><<<grid_huge, kThreads, 0, side2>>>(a);
+                    else
+                        k_propose_huge<kRefineHash><<<grid_huge, kThreads, 0, side2>>>(a);
+                    LAUNCHED();
+                    CK(cudaEventRecord(ev_join2, side2));
+                }
                 switch (mode) {
                     case kCluster: k_propose<kCluster><<<grid_main, kThreads, psmem, s>>>(a, k); break;
                     case kRefineHash: k_propose<kRefineHash><<<grid_main, kThreads, psmem, s>>>(a, k); break;
@@ -2042,6 +2228,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 }
                 LAUNCHED();
                 CK(cudaStreamWaitEvent(s, ev_join, 0));
+                if (huge) CK(cudaStreamWaitEvent(s, ev_join2, 0));
                 prof_end(s, pb, pe);
                 if (hub_items > 0) {
                     const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
@@ -2086,15 +2273,21 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         }
     } catch (...) {
         cudaStreamSynchronize(side);
+        cudaStreamSynchronize(side2);
         cudaEventDestroy(ev_fork);
         cudaEventDestroy(ev_join);
+        cudaEventDestroy(ev_join2);
         cudaStreamDestroy(side);
+        cudaStreamDestroy(side2);
         throw;
     }
     CK(cudaStreamSynchronize(side));
+    CK(cudaStreamSynchronize(side2));
     CK(cudaEventDestroy(ev_fork));
     CK(cudaEventDestroy(ev_join));
+    CK(cudaEventDestroy(ev_join2));
     CK(cudaStreamDestroy(side));
+    CK(cudaStreamDestroy(side2));
     Ctr hc[32];
     CK(cudaMemcpyAsync(hc, ctr, S * sizeof(Ctr), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
