@@ -1668,13 +1668,17 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
 // >= 2 * degree slots, so an insert always finds room.  Selection follows
 // k_hub_cand / k_hub_tie / k_hub_emit: the largest eligible cand_key, then
 // the smallest label holding it, then the gain rule of Sec. III.A.
+// Per-CTA results are written to the CTA's own shared memory and read by the
+// others with plain loads after a cluster barrier: only 32-bit CAS and add
+// go to another CTA's shared memory.
 struct HugeSm {
     uint32_t keys[kHugeSlots];
     int32_t vals[kHugeSlots];
     unsigned long long red[kThreads / 32];
-    unsigned long long best;  // rank 0: cluster-wide best cand_key
-    int32_t bestL, ownw;      // rank 0
-    int32_t item;             // rank 0: index into this colour's row list
+    unsigned long long cbest;  // this CTA's best cand_key
+    unsigned long long b;      // the cluster's best (local copy)
+    int32_t cbestL, cown;      // this CTA's smallest label holding b; own label's sum
+    int32_t item;              // rank 0: index into this colour's row list
 };
 
 __device__ __forceinline__ void huge_insert(cg::cluster_group &cl, HugeSm &sm, uint32_t L,
@@ -1709,15 +1713,14 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
     const int nrows = a.hcnt[a.colour];
     const int32_t *hl = a.hlist + (int64_t)a.colour * a.nL;
     while (true) {
-        if (rank == 0 && threadIdx.x == 0) {
-            sm.item = atomicAdd(&a.ctr->huge_next, 1);
-            sm.best = 0;
-            sm.bestL = 0x7fffffff;
-            sm.ownw = 0;
-        }
+        if (rank == 0 && threadIdx.x == 0) sm.item = atomicAdd(&a.ctr->huge_next, 1);
         cl.sync();
         const int it = r0->item;
         if (it >= nrows) break;  // the same value in every CTA of the cluster
+        if (threadIdx.x == 0) {
+            sm.cbestL = 0x7fffffff;
+            sm.cown = 0;
+        }
         const int32_t li = hl[it];
         const int32_t v = a.Lnodes[li];
         const int64_t rs = a.g.xadj[v];
@@ -1770,7 +1773,7 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
             const uint32_t L = sm.keys[i];
             if (L == kEmpty32) continue;
             const int32_t w = sm.vals[i];
-            if ((int32_t)L == own) r0->ownw = w;
+            if ((int32_t)L == own) sm.cown = w;
             else if (a.W[L] + c <= bnd(a, (int32_t)L)) {
                 const unsigned long long ck = cand_key(w, h, (int32_t)L);
                 best = ck > best ? ck : best;
@@ -1785,28 +1788,40 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int i = 1; i < kThreads / 32; i++) best = sm.red[i] > best ? sm.red[i] : best;
-            if (best) atomicMax(&r0->best, best);
+            sm.cbest = best;
         }
         cl.sync();
-        const unsigned long long b = r0->best;
+        if (threadIdx.x == 0) {
+            unsigned long long b = 0;
+            for (unsigned r = 0; r < kHugeCS; r++) {
+                const unsigned long long x = cl.map_shared_rank(&sm, r)->cbest;
+                b = x > b ? x : b;
+            }
+            sm.b = b;
+        }
+        __syncthreads();
+        const unsigned long long b = sm.b;
         for (int i = threadIdx.x; i < T; i += kThreads) {
             const uint32_t L = sm.keys[i];
             if (L == kEmpty32) continue;
             const int32_t w = sm.vals[i];
             if (b != 0 && (int32_t)L != own && (uint32_t)w == (uint32_t)(b >> 32) &&
                 cand_key(w, h, (int32_t)L) == b && a.W[L] + c <= bnd(a, (int32_t)L))
-                atomicMin(&r0->bestL, (int32_t)L);
+                atomicMin(&sm.cbestL, (int32_t)L);
             sm.keys[i] = kEmpty32;
             sm.vals[i] = 0;
         }
         cl.sync();
         if (rank == 0 && threadIdx.x == 0 && b != 0) {
-            const int32_t gain = (int32_t)(b >> 32) - sm.ownw;
-            const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
-            if (gain > 0 || ovl) {
-                const int32_t L = sm.bestL;
-                emit<false>(a, v, L, own, gain, c, ovl, a.W[L]);
+            int32_t L = 0x7fffffff, ownw = 0;
+            for (unsigned r = 0; r < kHugeCS; r++) {
+                const HugeSm *o = cl.map_shared_rank(&sm, r);
+                L = min(L, o->cbestL);
+                ownw += o->cown;
             }
+            const int32_t gain = (int32_t)(b >> 32) - ownw;
+            const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
+            if (gain > 0 || ovl) emit<false>(a, v, L, own, gain, c, ovl, a.W[L]);
         }
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
