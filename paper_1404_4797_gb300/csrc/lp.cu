@@ -51,10 +51,10 @@ namespace sclap {
 constexpr int kThreads = 256;
 constexpr int kSmallDeg = 32;            // small nodes: <= 32 entries (one warp pass)
 constexpr int kMedDeg = 256;             // medium nodes: 33..256 entries (one warp each)
-constexpr int kChunk = 1536;             // entries per large-row piece (one CTA)
+constexpr int kChunk = 4096;             // entries per large-row piece (one CTA)
 constexpr int kWSlots = 512;             // per-warp table slots for medium rows (>= 2 * kMedDeg)
-constexpr int kSlots = 4096;             // hash table slots (>= 2 * kChunk)
-constexpr int kSlotBits = 12;
+constexpr int kSlots = 8192;             // hash table slots (>= 2 * kChunk)
+constexpr int kSlotBits = 13;
 constexpr int kMedItem = 1;              // node slots of the CTA path (one large row at a time)
 constexpr int kDenseMaxK = 64;
 constexpr int kClasses = 5;              // buckets per colour
@@ -68,6 +68,7 @@ constexpr int kBins = 1 << kDigit;
 constexpr int kUnroll = 4;               // entries in flight per thread
 constexpr int kAggW = 1024;              // label weights aggregated in shared memory up to this
 constexpr uint64_t kEmpty = ~0ull;
+constexpr uint32_t kEmpty32 = 0xffffffffu;
 
 static_assert((1 << kSlotBits) == kSlots, "table size");
 static_assert(kSlots >= 2 * kChunk, "load factor <= 1/2");
@@ -364,7 +365,7 @@ struct NodeSm {
 };
 
 struct HashTab {
-    unsigned long long keys[kSlots];
+    uint32_t keys[kSlots];  // labels; kEmpty32 = empty
     int32_t vals[kSlots];
     uint16_t dl[kChunk];
 };
@@ -383,18 +384,18 @@ struct PropSm {
     int ndl, item, flag;
 };
 
-// Inserts (key, w) into a linear-probing table; a first insertion appends its
-// slot to dl.  Returns false only if the table is full (never at load <= 1/2).
+// Inserts (label L, w) into a linear-probing table of 32-bit labels; a first
+// insertion appends its slot to dl.  Returns false only if the table is full
+// (never at load <= 1/2).
 template <typename DL>
-__device__ __forceinline__ bool table_add(unsigned long long *keys, int32_t *vals, DL *dl,
-                                          int *ndl, uint32_t mask, int bits, uint64_t key,
-                                          int32_t w) {
-    uint32_t slot = table_hash(key, bits);
+__device__ __forceinline__ bool table_add(uint32_t *keys, int32_t *vals, DL *dl, int *ndl,
+                                          uint32_t mask, int bits, uint32_t L, int32_t w) {
+    uint32_t slot = (L * 0x9E3779B1u) >> (32 - bits);
     for (uint32_t probe = 0; probe <= mask; probe++) {
-        unsigned long long prev = atomicCAS(&keys[slot], kEmpty, (unsigned long long)key);
-        if (prev == kEmpty || prev == key) {
+        const uint32_t prev = atomicCAS(&keys[slot], kEmpty32, L);
+        if (prev == kEmpty32 || prev == L) {
             atomicAdd(&vals[slot], w);
-            if (prev == kEmpty) dl[atomicAdd(ndl, 1)] = (DL)slot;
+            if (prev == kEmpty32) dl[atomicAdd(ndl, 1)] = (DL)slot;
             return true;
         }
         slot = (slot + 1) & mask;
@@ -409,34 +410,29 @@ __device__ __forceinline__ T ld(const T *p) {
     else return *p;
 }
 
-// Best eligible label per node slot over the distinct (slot, label) entries.
-template <bool COHERENT = false, typename DL>
-__device__ __forceinline__ void select_best(const LPArgs &a, const unsigned long long *keys,
-                                            const int32_t *vals, const DL *dl, int ndl,
+// Best eligible label of the CTA's row (node slot 0) over the distinct labels.
+__device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *keys,
+                                            const int32_t *vals, const uint16_t *dl, int ndl,
                                             NodeSm &nd) {
     for (int i = threadIdx.x; i < ndl; i += kThreads) {
-        int32_t slot = ld<COHERENT>(&dl[i]);
-        uint64_t key = ld<COHERENT>(&keys[slot]);
-        int s = (int)(key >> 32);
-        int32_t L = (int32_t)(uint32_t)key;
-        int32_t w = ld<COHERENT>(&vals[slot]);
-        if (L == nd.own[s]) {
-            nd.ownw[s] = w;
-        } else if (a.W[L] + nd.c[s] <= bnd(a, L)) {
-            atomicMax(&nd.best[s], cand_key(w, nd.h[s], L));
+        const int slot = dl[i];
+        const int32_t L = (int32_t)keys[slot];
+        const int32_t w = vals[slot];
+        if (L == nd.own[0]) {
+            nd.ownw[0] = w;
+        } else if (a.W[L] + nd.c[0] <= bnd(a, L)) {
+            atomicMax(&nd.best[0], cand_key(w, nd.h[0], L));
         }
     }
     __syncthreads();
+    const unsigned long long b = nd.best[0];
     for (int i = threadIdx.x; i < ndl; i += kThreads) {
-        int32_t slot = ld<COHERENT>(&dl[i]);
-        uint64_t key = ld<COHERENT>(&keys[slot]);
-        int s = (int)(key >> 32);
-        int32_t L = (int32_t)(uint32_t)key;
-        int32_t w = ld<COHERENT>(&vals[slot]);
-        unsigned long long b = nd.best[s];
-        if (b == 0 || L == nd.own[s] || (uint32_t)w != (uint32_t)(b >> 32)) continue;
-        if (a.W[L] + nd.c[s] > bnd(a, L)) continue;
-        if (cand_key(w, nd.h[s], L) == b) atomicMin(&nd.bestL[s], L);
+        const int slot = dl[i];
+        const int32_t L = (int32_t)keys[slot];
+        const int32_t w = vals[slot];
+        if (b == 0 || L == nd.own[0] || (uint32_t)w != (uint32_t)(b >> 32)) continue;
+        if (a.W[L] + nd.c[0] > bnd(a, L)) continue;
+        if (cand_key(w, nd.h[0], L) == b) atomicMin(&nd.bestL[0], L);
     }
     __syncthreads();
 }
@@ -565,7 +561,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                     atomicAdd(&sm.t.acc[L[j]], w[j]);
                 } else {
                     if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
-                                   (uint64_t)(uint32_t)L[j], w[j]))
+                                   (uint32_t)L[j], w[j]))
                         a.ctr->err = kErrTable;
                 }
             }
@@ -580,7 +576,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, sm.nd);
                 for (int i = threadIdx.x; i < ndl; i += kThreads) {
                     const int slot = sm.t.dl[i];
-                    sm.t.keys[slot] = kEmpty;
+                    sm.t.keys[slot] = kEmpty32;
                     sm.t.vals[slot] = 0;
                 }
             }
@@ -631,9 +627,9 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 int32_t gslot = -1;
                 if (i < ndl) {
                     const int slot = sm.t.dl[i];
-                    const uint64_t key = sm.t.keys[slot];
+                    const uint64_t key = sm.t.keys[slot];  // the global table keeps 64-bit keys
                     const int32_t w = sm.t.vals[slot];
-                    sm.t.keys[slot] = kEmpty;
+                    sm.t.keys[slot] = kEmpty32;
                     sm.t.vals[slot] = 0;
                     uint32_t q = table_hash(key, bits);
                     bool placed = false;
@@ -786,7 +782,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(LPArgs a, int k) {
         for (int b = threadIdx.x; b < k; b += kThreads) sm.W[b] = a.W[b];
     } else {
         for (int i = threadIdx.x; i < kSlots; i += kThreads) {
-            sm.t.keys[i] = kEmpty;
+            sm.t.keys[i] = kEmpty32;
             sm.t.vals[i] = 0;
         }
     }
@@ -801,8 +797,6 @@ struct WarpTab {
     uint16_t dl[kMedDeg];     // slots in insertion order
     int ndl;
 };
-
-constexpr uint32_t kEmpty32 = 0xffffffffu;
 
 __device__ __forceinline__ void wtab_add(WarpTab &t, uint32_t L, int32_t w) {
     uint32_t slot = (uint32_t)(((uint64_t)L * 0x9E3779B97F4A7C15ull) >> 55) & (kWSlots - 1);
@@ -2192,7 +2186,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming));
     const bool huge = a.huge_on && a.nL > 0;
-    const int grid_huge = std::max(kHugeCS, (sms * 2) / kHugeCS * kHugeCS);
+    const int grid_huge = std::max(kHugeCS, (sms * 4) / kHugeCS * kHugeCS);
     int occ_small = 0;
     switch (mode) {
         case kCluster: CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_small, k_propose_small<kCluster>, kThreads, 0)); break;
