@@ -59,85 +59,70 @@ struct MemberDeg {
     }
 };
 
+// Slice state.  K32: keys are ((C(u) - C(first member)) << cbits) | C(v) in
+// 32 bits (a slice holds at most kCEntries + 1 members, so the first part
+// needs 12 bits; used when cbits <= 20), else (C(u) << cbits) | C(v).
+template <bool K32>
 struct AggSm {
-    unsigned long long keys[kCSlots];
+    typename std::conditional<K32, uint32_t, unsigned long long>::type keys[kCSlots];
     int32_t vals[kCSlots];
-    int32_t dl[kCEntries];
-    int32_t rel[kCEntries + 2];      // member start relative to the slice, clamped
-    int64_t ebase[kCEntries + 1];    // xadj[v] - mpre[i]: entry index = ebase + e
-    int32_t cid[kCEntries + 1];
-    int64_t m0;
+    uint16_t dl[kCEntries];
+    int32_t rowof[kCEntries];  // member index of each slice entry
+    int32_t scan_tmp[kCThreads / 32 + 2];
     unsigned long long out_base;
-    int ndl, nm;
+    int ndl;
+    int32_t cu0;
 };
 
-__device__ __forceinline__ int64_t upper_bound_i64(const int64_t *a, int64_t lo, int64_t hi,
-                                                    int64_t x) {
-    // first index in [lo, hi) with a[i] > x
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] <= x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // Slice t covers concatenated member entries [t*kCEntries, (t+1)*kCEntries).
+template <bool K32>
 __global__ void __launch_bounds__(kCThreads)
     k_aggregate(DGraph g, const int32_t *members, int64_t nmem, const int64_t *mpre,
                 int64_t total, const int32_t *f2c, int cbits, unsigned long long *out_keys,
                 int32_t *out_w, unsigned long long *out_cnt) {
+    using Key = typename std::conditional<K32, uint32_t, unsigned long long>::type;
+    constexpr Key kEmptyK = (Key)~(Key)0;
     extern __shared__ __align__(16) unsigned char smraw[];
-    AggSm &sm = *reinterpret_cast<AggSm *>(smraw);
+    AggSm<K32> &sm = *reinterpret_cast<AggSm<K32> *>(smraw);
     for (int i = threadIdx.x; i < kCSlots; i += kCThreads) {
-        sm.keys[i] = kCEmpty;
+        sm.keys[i] = kEmptyK;
         sm.vals[i] = 0;
     }
+    const uint64_t cmask = (1ull << cbits) - 1;
     const int64_t slices = ceil_div<int64_t>(total, kCEntries);
     for (int64_t t = blockIdx.x; t < slices; t += gridDim.x) {
         const int64_t e0 = t * kCEntries;
-        const int64_t e1 = min64(total, e0 + kCEntries);
+        const int len = (int)min64(total - e0, (int64_t)kCEntries);
         if (threadIdx.x == 0) {
-            int64_t m0 = upper_bound_i64(mpre, 0, nmem, e0) - 1;
-            int64_t m1 = upper_bound_i64(mpre, m0, nmem, e1 - 1);  // one past the last member
-            sm.m0 = m0;
-            sm.nm = (int)(m1 - m0);
-            sm.out_base = 0;
             sm.ndl = 0;
+            sm.out_base = 0;
         }
+        block_rows<kCThreads, kCEntries / kCThreads>(mpre, nmem, e0, len, sm.rowof, sm.scan_tmp);
+        if (threadIdx.x == 0) sm.cu0 = f2c[members[sm.rowof[0]]];
         __syncthreads();
-        const int64_t m0 = sm.m0;
-        const int nm = sm.nm;
-        for (int i = threadIdx.x; i < nm; i += kCThreads) {
-            int64_t mi = m0 + i;
-            int32_t v = members[mi];
-            int64_t p = mpre[mi];
-            sm.rel[i] = (int32_t)max64(0, p - e0);
-            sm.ebase[i] = g.xadj[v] - p;
-            sm.cid[i] = f2c[v];
-        }
-        __syncthreads();
-        const int32_t len = (int32_t)(e1 - e0);
-        for (int32_t le = threadIdx.x; le < len; le += kCThreads) {
-            // member slot: largest i with rel[i] <= le
-            int lo = 0, hi = nm;
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (sm.rel[mid] <= le) lo = mid;
-                else hi = mid;
-            }
-            int64_t idx = sm.ebase[lo] + e0 + le;
-            int32_t cu = sm.cid[lo];
-            int32_t cv = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
+        const int32_t cu0 = sm.cu0;
+        for (int le = threadIdx.x; le < len; le += kCThreads) {
+            const int32_t mi = sm.rowof[le];
+            const int32_t v = __ldg(&members[mi]);
+            const int64_t idx = __ldg(&g.xadj[v]) + (e0 + le - __ldg(&mpre[mi]));
+            const int32_t cu = __ldg(&f2c[v]);
+            const int32_t cv = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
             if (cu == cv) continue;  // edge inside a cluster
-            int32_t w = __ldg(&g.adjwgt[idx]);
-            uint64_t key = ((uint64_t)(uint32_t)cu << cbits) | (uint32_t)cv;
-            uint32_t slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCBits));
+            const int32_t w = __ldg(&g.adjwgt[idx]);
+            Key key;
+            uint32_t slot;
+            if constexpr (K32) {
+                key = ((uint32_t)(cu - cu0) << cbits) | (uint32_t)cv;
+                slot = (key * 0x9E3779B1u) >> (32 - kCBits);
+            } else {
+                key = ((uint64_t)(uint32_t)cu << cbits) | (uint32_t)cv;
+                slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCBits));
+            }
             for (int probe = 0; probe < kCSlots; probe++) {  // never full: load <= 1/2
-                unsigned long long prev = atomicCAS(&sm.keys[slot], kCEmpty, key);
-                if (prev == kCEmpty || prev == key) {
+                const Key prev = atomicCAS(&sm.keys[slot], kEmptyK, key);
+                if (prev == kEmptyK || prev == key) {
                     atomicAdd(&sm.vals[slot], w);
-                    if (prev == kCEmpty) sm.dl[atomicAdd(&sm.ndl, 1)] = (int32_t)slot;
+                    if (prev == kEmptyK) sm.dl[atomicAdd(&sm.ndl, 1)] = (uint16_t)slot;
                     break;
                 }
                 slot = (slot + 1) & (kCSlots - 1);
@@ -149,10 +134,15 @@ __global__ void __launch_bounds__(kCThreads)
         __syncthreads();
         const int64_t ob = (int64_t)sm.out_base;
         for (int i = threadIdx.x; i < ndl; i += kCThreads) {
-            int32_t slot = sm.dl[i];
-            out_keys[ob + i] = sm.keys[slot];
+            const int slot = sm.dl[i];
+            const Key key = sm.keys[slot];
+            if constexpr (K32)
+                out_keys[ob + i] = ((uint64_t)(uint32_t)(cu0 + (int32_t)(key >> cbits)) << cbits) |
+                                   (key & cmask);
+            else
+                out_keys[ob + i] = key;
             out_w[ob + i] = sm.vals[slot];
-            sm.keys[slot] = kCEmpty;
+            sm.keys[slot] = kEmptyK;
             sm.vals[slot] = 0;
         }
         __syncthreads();
@@ -250,13 +240,16 @@ void contract_impl(const DGraph &g, const int32_t *lab, int32_t *f2c, CoarseGrap
     int32_t *pw = sc.get<int32_t>(total);
     unsigned long long *d_P = sc.zeros<unsigned long long>(1);
     if (total > 0) {
-        CK(cudaFuncSetAttribute(k_aggregate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(AggSm)));
-        int occ = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aggregate, kCThreads, sizeof(AggSm)));
-        k_aggregate<<<sms * std::max(1, occ), kCThreads, sizeof(AggSm), s>>>(
-            g, members, nmem, mpre, total, f2c, cbits, pk, pw, d_P);
-        LAUNCHED();
+        auto launch = [&](auto kern, size_t smem) {
+            CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int occ = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCThreads, smem));
+            kern<<<sms * std::max(1, occ), kCThreads, smem, s>>>(g, members, nmem, mpre, total, f2c,
+                                                                 cbits, pk, pw, d_P);
+            LAUNCHED();
+        };
+        if (cbits <= 20) launch(k_aggregate<true>, sizeof(AggSm<true>));
+        else launch(k_aggregate<false>, sizeof(AggSm<false>));
     }
     unsigned long long P = 0;
     CK(cudaMemcpyAsync(&P, d_P, sizeof(P), cudaMemcpyDeviceToHost, s));

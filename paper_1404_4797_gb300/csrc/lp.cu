@@ -919,7 +919,7 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
 // Rows of <= kMedDeg entries: warps take small-row items (G lanes per row)
 // and then medium rows (a warp per row).  Runs next to k_propose (side stream).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_propose_small(LPArgs a, int k) {
+__global__ void __launch_bounds__(kThreads, 4) k_propose_small(LPArgs a, int k) {
     __shared__ int64_t W[kDenseMaxK];
     __shared__ WarpTab tabs[MODE == kRefineDense ? 1 : kThreads / 32];
     __shared__ int32_t dacc[MODE == kRefineDense ? kThreads / 32 : 1][kDenseMaxK];

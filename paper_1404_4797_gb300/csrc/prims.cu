@@ -147,20 +147,28 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     __syncthreads();
     // per digit: warp offsets, then the digit's start inside the tile
-    int tot = 0;
-    {
-        const int d = threadIdx.x;  // kSortThreads == kRadix
+    // (thread t owns the consecutive digits t * kDigitsPerThread + j)
+    int tot[kDigitsPerThread];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < kDigitsPerThread; j++) {
+        const int d = threadIdx.x * kDigitsPerThread + j;
         int run = 0;
         for (int w = 0; w < kSortWarps; w++) {
             const int t = sm.wc[w][d];
             sm.wc[w][d] = run;
             run += t;
         }
-        tot = run;
+        tot[j] = run;
+        sum += run;
     }
     int all;
-    const int ds = block_exclusive_scan<kSortThreads>(tot, &all, sm.scan_tmp);
-    sm.dstart[threadIdx.x] = ds;
+    int ds = block_exclusive_scan<kSortThreads>(sum, &all, sm.scan_tmp);
+#pragma unroll
+    for (int j = 0; j < kDigitsPerThread; j++) {
+        sm.dstart[threadIdx.x * kDigitsPerThread + j] = ds;
+        ds += tot[j];
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortRounds; r++) {
@@ -190,13 +198,13 @@ void radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, Scrat
     int32_t *v2 = sc.get<int32_t>(n);
     int64_t *hist = sc.get<int64_t>(tiles * kRadix);
     int64_t *offs = sc.get<int64_t>(tiles * kRadix);
-    static_assert(kSortThreads == kRadix, "one digit per thread in the scatter");
+    static_assert(kRadix % kSortThreads == 0, "whole digits per thread in the scatter");
     CK(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)sizeof(SortSm)));
     uint64_t *ka = keys, *kb = k2;
     int32_t *va = vals, *vb = v2;
     int passes = 0;
-    for (int shift = 0; shift < nbits; shift += 8, passes++) {
+    for (int shift = 0; shift < nbits; shift += kRadixBits, passes++) {
         k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(ka, n, shift, tiles, hist);
         LAUNCHED();
         exclusive_scan(ArrayI64{hist}, tiles * kRadix, offs, nullptr, sc);

@@ -120,7 +120,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortRounds = 16;                       // items per lane
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
-constexpr int kRadix = 256;
+constexpr int kRadixBits = 9;                          // digit width of one pass
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kDigitsPerThread = kRadix / kSortThreads;
 
 // Sorts (keys, vals) stably by key bits [0, nbits).  keys/vals are sorted in
 // place (alt buffers are scratch).
