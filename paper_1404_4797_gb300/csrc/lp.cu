@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
     const DGraph &g = a.g;
     const int S = a.S;
     const int nb = kClasses * S;
+    unsigned long long p_entries = 0, p_nodes = 0;  // profiling: rows the round visits
     for (int64_t tile = (int64_t)blockIdx.x * kThreads * 4; tile < g.n;
          tile += (int64_t)gridDim.x * kThreads * 4) {
         for (int i = threadIdx.x; i < nb; i += kThreads) lcnt[i] = 0;
@@ -275,6 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
             if (v < g.n) {
                 const int64_t d = g.xadj[v + 1] - g.xadj[v];
                 if (d > 0) {
+                    p_entries += (unsigned long long)d;
+                    p_nodes++;
                     const uint32_t col = colour_of(a.seed, a.round, (int32_t)v, S);
                     if (d <= kMedDeg) {
                         bk[j] = kClasses * (int)col + degree_class(d);
@@ -308,6 +311,17 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
         for (int j = 0; j < 4; j++)
             if (bk[j] >= 0) wl[(int64_t)bk[j] * g.n + lbase[bk[j]] + rk[j]] = vv[j];
         __syncthreads();
+    }
+    if (a.prof) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            p_entries += __shfl_down_sync(0xffffffffu, p_entries, d);
+            p_nodes += __shfl_down_sync(0xffffffffu, p_nodes, d);
+        }
+        if ((threadIdx.x & 31) == 0 && p_nodes) {
+            atomicAdd(&a.prof[0], p_entries);
+            atomicAdd(&a.prof[1], p_nodes);
+        }
     }
 }
 
@@ -535,10 +549,6 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
         const int64_t deg = a.g.xadj[v + 1] - a.g.xadj[v];
         const int64_t e0 = pi * kChunk;
         const int64_t e1 = min64(deg, e0 + kChunk);
-        if (a.prof && threadIdx.x == 0) {
-            atomicAdd(&a.prof[0], (unsigned long long)(e1 - e0));
-            if (pi == 0) atomicAdd(&a.prof[1], 1ull);
-        }
         const int64_t rs = sm.nd.rs[0];
         const int32_t cpv = sm.nd.cpv[0];
         for (int64_t eb = e0 + threadIdx.x; eb < e1; eb += kUnroll * kThreads) {
@@ -698,10 +708,6 @@ __device__ __forceinline__ SmallLoad small_load(const LPArgs &a, const int64_t *
             }
         }
         if (MODE != kCluster) x.Wown = MODE == kRefineDense ? Wsm[x.own] : a.W[x.own];
-        if (a.prof && r == 0) {
-            atomicAdd(&a.prof[0], (unsigned long long)deg);
-            atomicAdd(&a.prof[1], 1ull);
-        }
     }
     return x;
 }
@@ -823,10 +829,6 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
     const int32_t cpv = (MODE == kCluster && a.cp) ? a.cp[v] : 0;
     const int64_t Wown = MODE == kCluster ? 0 : (DENSE ? Wsm[own] : a.W[own]);
     const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
-    if (a.prof && lane == 0) {
-        atomicAdd(&a.prof[0], (unsigned long long)deg);
-        atomicAdd(&a.prof[1], 1ull);
-    }
     for (int32_t e0 = 0; e0 < deg; e0 += 32 * kUnroll) {
         int32_t u[kUnroll], w[kUnroll], L[kUnroll];
 #pragma unroll
@@ -1730,10 +1732,6 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
         }
         const int tbits = lbits + 3;  // kHugeCS == 8
         const int T = 1 << lbits;
-        if (a.prof && rank == 0 && threadIdx.x == 0) {
-            atomicAdd(&a.prof[0], (unsigned long long)deg);
-            atomicAdd(&a.prof[1], 1ull);
-        }
         const int64_t e0 = deg * rank / kHugeCS, e1 = deg * (rank + 1) / kHugeCS;
         const int64_t span = e1 - e0;
         const int64_t span_r = (span + 31) & ~31ll;  // whole warps for match_any
