@@ -1379,15 +1379,21 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
             const int last = s_flag;
             __syncthreads();
             if (!last) continue;
-            // last tile of this segment in this pass: pick the digit
+            // last tile of this segment in this pass: pick the digit from the
+            // summed histogram, staged in shared memory (and cleared behind)
             __threadfence();
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
+                sm.hist[i] = __ldcg(&gh[i]);
+                gh[i] = 0;
+            }
+            __syncthreads();
             if (warp == 0) {
                 const long long acc = p == 0 ? 0ll : __ldcg(&b->acc);
                 const unsigned per = nb / 32 > 0 ? nb / 32 : 1;
                 unsigned long long local = 0;
                 for (unsigned j = 0; j < per; j++) {
                     const unsigned bi2 = lane * per + j;
-                    if (bi2 < nb) local += __ldcg(&gh[bi2]);
+                    if (bi2 < nb) local += sm.hist[bi2];
                 }
                 unsigned long long inc = local;
 #pragma unroll
@@ -1405,7 +1411,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                     for (unsigned j = 0; j < per; j++) {
                         const unsigned bi2 = lane * per + j;
                         if (bi2 >= nb) break;
-                        const long long h = (long long)__ldcg(&gh[bi2]);
+                        const long long h = (long long)sm.hist[bi2];
                         if (run + h >= bt.sg.thr) { d = bi2; break; }
                         run += h;
                     }
@@ -1414,7 +1420,6 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                 }
             }
             __syncthreads();
-            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) gh[i] = 0;
             if (threadIdx.x == 0) b->arrived = 0;
             __threadfence();
             __syncthreads();
@@ -1428,21 +1433,35 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
         const unsigned long long K = (bt.top < 0 || bt.done) ? ~0ull : bt.pf;
         const bool staged = t == (int)blockIdx.x;
         const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
-        for (int i = threadIdx.x; i < bt.len; i += blockDim.x) {
-            uint64_t key;
-            int32_t c;
-            if (staged) {
-                key = sm.keys[i];
-                c = sm.c[i];
-            } else {
-                const SegEntry e = ent[i];
-                key = e.key;
-                c = e.c;
+        const int len_r = (bt.len + 31) & ~31;
+        for (int i = threadIdx.x; i < len_r; i += blockDim.x) {  // whole warps
+            uint64_t key = ~0ull;
+            int32_t c = 1;
+            if (i < bt.len) {
+                if (staged) {
+                    key = sm.keys[i];
+                    c = sm.c[i];
+                } else {
+                    const SegEntry e = ent[i];
+                    key = e.key;
+                    c = e.c;
+                }
             }
-            if (key < K || c == 0) {
+            const bool adm = i < bt.len && (key < K || c == 0);
+            if (a.nW <= kAggW) {
+                // one target per tile: its weight delta is summed over the warp
+                if (adm) {
+                    a.lab[(int32_t)(uint32_t)key] = bt.sg.T;
+                    atomicAdd((unsigned long long *)&sm.wd.d[ent[i].own],
+                              (unsigned long long)(-(long long)c));
+                }
+                const int64_t sw = peer_sum64(0xffffffffu, adm ? c : 0);
+                if (lane == 0 && sw)
+                    atomicAdd((unsigned long long *)&sm.wd.d[bt.sg.T], (unsigned long long)sw);
+            } else if (adm) {
                 apply_agg(a, sm.wd, (int32_t)(uint32_t)key, bt.sg.T, ent[i].own, c);
-                moved++;
             }
+            moved += adm;
         }
         __syncthreads();
     }
