@@ -222,24 +222,24 @@ __device__ __forceinline__ void wd_init(WDelta &wd, int64_t nW) {
 }
 
 // Applies a move (label write, weight delta).  Called by moving threads only.
+// The deltas are summed over the calling threads of the warp that share a
+// label first, so one atomic per distinct label and warp reaches the
+// CTA-local (nW <= kAggW) or global weight array.
 __device__ __forceinline__ void apply_agg(const LPArgs &a, WDelta &wd, int32_t v, int32_t T,
                                           int32_t own, int32_t c) {
     a.lab[v] = T;
-    if (a.nW <= kAggW) {
-        atomicAdd((unsigned long long *)&wd.d[T], (unsigned long long)(long long)c);
-        atomicAdd((unsigned long long *)&wd.d[own], (unsigned long long)(-(long long)c));
-        return;
-    }
+    unsigned long long *dst = a.nW <= kAggW ? (unsigned long long *)wd.d
+                                             : (unsigned long long *)a.W;
     cg::coalesced_group g = cg::coalesced_threads();
     {
         cg::coalesced_group t = cg::labeled_partition(g, (unsigned)T);
         const long long sum = cg::reduce(t, (long long)c, cg::plus<long long>());
-        if (t.thread_rank() == 0) atomicAdd((unsigned long long *)&a.W[T], (unsigned long long)sum);
+        if (t.thread_rank() == 0) atomicAdd(&dst[T], (unsigned long long)sum);
     }
     {
         cg::coalesced_group o = cg::labeled_partition(g, (unsigned)own);
         const long long sum = cg::reduce(o, (long long)c, cg::plus<long long>());
-        if (o.thread_rank() == 0) atomicAdd((unsigned long long *)&a.W[own], (unsigned long long)(-sum));
+        if (o.thread_rank() == 0) atomicAdd(&dst[own], (unsigned long long)(-sum));
     }
 }
 
@@ -978,11 +978,18 @@ __device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uin
     __syncthreads();
     const int64_t step = 4 * (int64_t)blockDim.x;
     const int64_t cnt_r = ceil_div<int64_t>(cnt, blockDim.x) * blockDim.x;
+    const bool split = cnt <= 65536;
     for (int hb = top; hb >= 0; hb -= kDigit) {
         const int width = hb + 1 < kDigit ? hb + 1 : kDigit;
         const int shift = hb - width + 1;
         const unsigned nb = 1u << width;
-        for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+        // weights are summed in two 32-bit halves per bin (native shared
+        // atomics) while cnt * 65535 fits; else in 64-bit bins
+        uint32_t *hlo = reinterpret_cast<uint32_t *>(hist), *hhi = hlo + kBins;
+        for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
+            if (split) hlo[i] = hhi[i] = 0;
+            else hist[i] = 0;
+        }
         __syncthreads();
         const uint64_t hm = (hb >= 63) ? 0ull : (~0ull << (hb + 1));
         const uint64_t pf = *s_pf;
@@ -1002,11 +1009,31 @@ __device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uin
                 const bool in = cc[j] > 0 && (kk[j] & hm) == (pf & hm);
                 const unsigned d = in ? (unsigned)((kk[j] >> shift) & (nb - 1)) : 0xffffffffu;
                 const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const int64_t sw = peer_sum64(peers, in ? cc[j] : 0);
-                if (in && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&hist[d], (unsigned long long)sw);
+                const unsigned c = in ? (unsigned)cc[j] : 0u;
+                const unsigned lo = __reduce_add_sync(peers, c & 0xffffu);
+                const unsigned hi = __reduce_add_sync(peers, c >> 16);
+                if (in && (peers & ((1u << lane) - 1)) == 0) {
+                    if (split) {
+                        atomicAdd(&hlo[d], lo);
+                        if (hi) atomicAdd(&hhi[d], hi);
+                    } else {
+                        atomicAdd(&hist[d], ((unsigned long long)hi << 16) + lo);
+                    }
+                }
             }
         }
         __syncthreads();
+        if (split) {  // into 64-bit bins for the scan (bin i reads lo/hi before anyone writes i)
+            static_assert(kBins / kThreads == 8, "8 bins per thread at kThreads threads");
+            unsigned long long t[kBins / kThreads];
+            int n_t = 0;
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x)
+                t[n_t++] = (unsigned long long)hlo[i] + ((unsigned long long)hhi[i] << 16);
+            __syncthreads();
+            n_t = 0;
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = t[n_t++];
+            __syncthreads();
+        }
         if (threadIdx.x < 32) {
             const unsigned per = nb / 32 > 0 ? nb / 32 : 1;  // bins per lane
             unsigned long long local = 0;
@@ -1344,7 +1371,8 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
             const unsigned long long hm = hb >= 63 ? 0ull : (~0ull << (hb + 1));
             const unsigned long long pf =
                 p == 0 ? (bt.top >= 63 ? 0ull : (bt.kmin & (~0ull << (bt.top + 1)))) : bt.pf;
-            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) sm.hist[i] = 0;
+            uint32_t *hlo = reinterpret_cast<uint32_t *>(sm.hist), *hhi = hlo + kBins;
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) hlo[i] = hhi[i] = 0;
             __syncthreads();
             const bool staged = t == (int)blockIdx.x;
             const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
@@ -1365,13 +1393,21 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                 const bool in = c > 0 && (key & hm) == (pf & hm);
                 const unsigned d = in ? (unsigned)((key >> shift) & (nb - 1)) : 0xffffffffu;
                 const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const int64_t sw = peer_sum64(peers, in ? c : 0);
-                if (in && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&sm.hist[d], (unsigned long long)sw);
+                const unsigned cw = in ? (unsigned)c : 0u;
+                const unsigned lo = __reduce_add_sync(peers, cw & 0xffffu);
+                const unsigned hi = __reduce_add_sync(peers, cw >> 16);
+                if (in && (peers & ((1u << lane) - 1)) == 0) {
+                    atomicAdd(&hlo[d], lo);  // a tile has <= 4096 entries: no overflow
+                    if (hi) atomicAdd(&hhi[d], hi);
+                }
             }
             __syncthreads();
             unsigned long long *gh = a.bhist + (size_t)bt.bi * kBins;
-            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x)
-                if (sm.hist[i]) atomicAdd(&gh[i], sm.hist[i]);
+            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
+                const unsigned long long tot =
+                    (unsigned long long)hlo[i] + ((unsigned long long)hhi[i] << 16);
+                if (tot) atomicAdd(&gh[i], tot);
+            }
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) s_flag = atomicAdd(&b->arrived, 1) == __ldcg(&b->tiles) - 1;
@@ -1448,19 +1484,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                 }
             }
             const bool adm = i < bt.len && (key < K || c == 0);
-            if (a.nW <= kAggW) {
-                // one target per tile: its weight delta is summed over the warp
-                if (adm) {
-                    a.lab[(int32_t)(uint32_t)key] = bt.sg.T;
-                    atomicAdd((unsigned long long *)&sm.wd.d[ent[i].own],
-                              (unsigned long long)(-(long long)c));
-                }
-                const int64_t sw = peer_sum64(0xffffffffu, adm ? c : 0);
-                if (lane == 0 && sw)
-                    atomicAdd((unsigned long long *)&sm.wd.d[bt.sg.T], (unsigned long long)sw);
-            } else if (adm) {
-                apply_agg(a, sm.wd, (int32_t)(uint32_t)key, bt.sg.T, ent[i].own, c);
-            }
+            if (adm) apply_agg(a, sm.wd, (int32_t)(uint32_t)key, bt.sg.T, ent[i].own, c);
             moved += adm;
         }
         __syncthreads();
