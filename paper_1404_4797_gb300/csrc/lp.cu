@@ -1131,6 +1131,56 @@ struct ArbSm {
     int done;
 };
 
+// Copies entries [0, cnt) of a contested segment into shared memory (key,
+// weight); each thread issues 8 loads before its stores.
+__device__ __forceinline__ void stage_segment(const SegEntry *ent, int cnt, uint64_t *keys,
+                                              int32_t *c) {
+    for (int base = threadIdx.x; base < cnt; base += 8 * blockDim.x) {
+        SegEntry e[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int i = base + j * blockDim.x;
+            if (i < cnt) e[j] = ent[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int i = base + j * blockDim.x;
+            if (i < cnt) {
+                keys[i] = e[j].key;
+                c[i] = e[j].c;
+            }
+        }
+    }
+}
+
+// Admits the staged entries of a segment with key < K (and weight 0): the
+// owners are loaded 8 per thread ahead of the moves.  Whole warps iterate.
+__device__ __forceinline__ int64_t admit_segment(const LPArgs &a, WDelta &wd, const SegEntry *ent,
+                                                 int cnt, const uint64_t *keys, const int32_t *c,
+                                                 uint64_t K, int32_t T) {
+    int64_t moved = 0;
+    const int cnt_r = (cnt + 31) & ~31;
+    for (int base = threadIdx.x; base < cnt_r; base += 8 * blockDim.x) {
+        int32_t own[8];
+        bool adm[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int i = base + j * blockDim.x;
+            adm[j] = i < cnt && (keys[i] < K || c[i] == 0);
+            own[j] = adm[j] ? ent[i].own : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int i = base + j * blockDim.x;
+            if (adm[j]) {
+                apply_agg(a, wd, (int32_t)(uint32_t)keys[i], T, own[j], c[i]);
+                moved++;
+            }
+        }
+    }
+    return moved;
+}
+
 // Refinement: departures from overloaded blocks (slot == -2).  CTAs with
 // blockIdx < nW handle block b = blockIdx when its departures are contested;
 // the others pass the uncontested sources' proposals through.
@@ -1324,15 +1374,26 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
         const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
         const bool stage = t == (int)blockIdx.x;
         unsigned long long mn = ~0ull, mx = 0;
-        for (int i = threadIdx.x; i < bt.len; i += blockDim.x) {
-            const SegEntry e = ent[i];
-            if (stage) {
-                sm.keys[i] = e.key;
-                sm.c[i] = e.c;
+        for (int base = threadIdx.x; base < bt.len; base += 8 * blockDim.x) {
+            SegEntry e[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int i = base + j * blockDim.x;
+                e[j].c = 0;
+                if (i < bt.len) e[j] = ent[i];
             }
-            if (e.c > 0) {
-                mn = e.key < mn ? e.key : mn;
-                mx = e.key > mx ? e.key : mx;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int i = base + j * blockDim.x;
+                if (i >= bt.len) continue;
+                if (stage) {
+                    sm.keys[i] = e[j].key;
+                    sm.c[i] = e[j].c;
+                }
+                if (e[j].c > 0) {
+                    mn = e[j].key < mn ? e[j].key : mn;
+                    mx = e[j].key > mx ? e[j].key : mx;
+                }
             }
         }
 #pragma unroll
@@ -1418,9 +1479,21 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
             // last tile of this segment in this pass: pick the digit from the
             // summed histogram, staged in shared memory (and cleared behind)
             __threadfence();
-            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
-                sm.hist[i] = __ldcg(&gh[i]);
-                gh[i] = 0;
+            {
+                unsigned long long hv[kBins / kThreads];
+#pragma unroll
+                for (int j = 0; j < kBins / kThreads; j++) {
+                    const unsigned i = threadIdx.x + j * kThreads;
+                    hv[j] = i < nb ? __ldcg(&gh[i]) : 0ull;
+                }
+#pragma unroll
+                for (int j = 0; j < kBins / kThreads; j++) {
+                    const unsigned i = threadIdx.x + j * kThreads;
+                    if (i < nb) {
+                        sm.hist[i] = hv[j];
+                        gh[i] = 0;
+                    }
+                }
             }
             __syncthreads();
             if (warp == 0) {
@@ -1467,26 +1540,12 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
         const BigTile bt = big_tile(a, t, nbig, &s_bt);
         if (!bt.ok) continue;
         const unsigned long long K = (bt.top < 0 || bt.done) ? ~0ull : bt.pf;
-        const bool staged = t == (int)blockIdx.x;
         const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
-        const int len_r = (bt.len + 31) & ~31;
-        for (int i = threadIdx.x; i < len_r; i += blockDim.x) {  // whole warps
-            uint64_t key = ~0ull;
-            int32_t c = 1;
-            if (i < bt.len) {
-                if (staged) {
-                    key = sm.keys[i];
-                    c = sm.c[i];
-                } else {
-                    const SegEntry e = ent[i];
-                    key = e.key;
-                    c = e.c;
-                }
-            }
-            const bool adm = i < bt.len && (key < K || c == 0);
-            if (adm) apply_agg(a, sm.wd, (int32_t)(uint32_t)key, bt.sg.T, ent[i].own, c);
-            moved += adm;
+        if (t != (int)blockIdx.x) {  // tiles after the first: stage them now
+            stage_segment(ent, bt.len, sm.keys, sm.c);
+            __syncthreads();
         }
+        moved += admit_segment(a, sm.wd, ent, bt.len, sm.keys, sm.c, K, bt.sg.T);
         __syncthreads();
     }
 }
@@ -1530,11 +1589,7 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         const Seg sg = a.segs[si];
         if (sg.cnt <= 32 || sg.cnt > kSegSmem) continue;
         const SegEntry *ent = a.segbuf + sg.base;
-        for (int i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
-            const SegEntry e = ent[i];
-            sm.keys[i] = e.key;
-            sm.c[i] = e.c;
-        }
+        stage_segment(ent, sg.cnt, sm.keys, sm.c);
         __syncthreads();
         auto get = [&](int64_t i, uint64_t *key, int32_t *c) {
             *key = sm.keys[i];
@@ -1544,14 +1599,7 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         block_minmax(get, sg.cnt, &kmin, &kmax, sm.red);
         const uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, kmin, kmax, sm.hist, &sm.acc,
                                                  &sm.pf, &sm.done);
-        for (int64_t i = threadIdx.x; i < sg.cnt; i += blockDim.x) {
-            const uint64_t key = sm.keys[i];
-            const int32_t c = sm.c[i];
-            if (key < K || c == 0) {
-                apply_agg(a, sm.wd, (int32_t)(uint32_t)key, sg.T, ent[i].own, c);
-                moved++;
-            }
-        }
+        moved += admit_segment(a, sm.wd, ent, sg.cnt, sm.keys, sm.c, K, sg.T);
         __syncthreads();
     }
     // long segments: the whole grid (the same branch in every CTA)
