@@ -14,7 +14,6 @@ constexpr int kCThreads = 256;
 constexpr int kCEntries = 2048;
 constexpr int kCSlots = 4096;
 constexpr int kCBits = 12;
-constexpr uint64_t kCEmpty = ~0ull;
 
 __global__ void k_mark(int64_t n, const int32_t *lab, int32_t *mark) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;

@@ -116,6 +116,7 @@ struct BigSeg {
     unsigned long long pf;          // key bits fixed by the passes so far
     long long acc;                  // weight of the entries below the prefix
     int32_t done;                   // 1: total weight below the threshold
+    unsigned idmax;                 // largest node id among entries with c > 0
 };
 
 struct GridBar {
@@ -958,124 +959,87 @@ __device__ __forceinline__ int64_t peer_sum64(unsigned peers, int32_t c) {
     return ((int64_t)hi << 16) + (int64_t)lo;
 }
 
-// Weighted radix select: the smallest key K such that the total weight of the
-// entries with key <= K is >= thr; ~0 if the total is < thr.  get(i, &key, &c)
-// returns entry i (c = 0 entries carry no weight).  Only the bits where
-// kmin and kmax differ are examined, kDigit bits per pass; each thread keeps
-// four entries in flight.  All threads of the CTA call it.
-template <typename Get>
-__device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uint64_t kmin,
-                                          uint64_t kmax, unsigned long long *hist /* [kBins] */,
-                                          int64_t *s_acc, uint64_t *s_pf, int *s_done) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t diff = kmin ^ kmax;
-    const int top = diff ? 63 - __clzll((long long)diff) : 0;  // highest differing bit
-    if (threadIdx.x == 0) {
-        *s_acc = 0;
-        *s_pf = top >= 63 ? 0ull : (kmin & (~0ull << (top + 1)));
-        *s_done = 0;
+// Digit windows of the weighted radix select.  Keys are (order-flipped gain
+// << 32) | node id.  The first window starts at `top`, the highest bit where
+// the smallest and largest weighted keys differ; windows are at most kDigit
+// bits wide and do not cross bit 32; below bit 32 they start at `idtop`, the
+// highest bit set in any weighted key's node id (the bits in between are zero
+// in every key).  Returns false when no window is left.
+__device__ __forceinline__ bool sel_window(int top, int idtop, int p, int *hb, int *width) {
+    int cur = top;
+    for (int q = 0;; q++) {
+        if (cur >= 32) {
+            const int lo = max(32, cur - kDigit + 1);
+            if (q == p) { *hb = cur; *width = cur - lo + 1; return true; }
+            cur = lo - 1;
+            if (cur == 31) cur = min(31, idtop);
+        } else {
+            if (cur < 0) return false;
+            const int lo = max(0, cur - kDigit + 1);
+            if (q == p) { *hb = cur; *width = cur - lo + 1; return true; }
+            cur = lo - 1;
+        }
     }
-    __syncthreads();
-    const int64_t step = 4 * (int64_t)blockDim.x;
-    const int64_t cnt_r = ceil_div<int64_t>(cnt, blockDim.x) * blockDim.x;
-    const bool split = cnt <= 65536;
-    for (int hb = top; hb >= 0; hb -= kDigit) {
-        const int width = hb + 1 < kDigit ? hb + 1 : kDigit;
-        const int shift = hb - width + 1;
-        const unsigned nb = 1u << width;
-        // weights are summed in two 32-bit halves per bin (native shared
-        // atomics) while cnt * 65535 fits; else in 64-bit bins
-        uint32_t *hlo = reinterpret_cast<uint32_t *>(hist), *hhi = hlo + kBins;
-        for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
-            if (split) hlo[i] = hhi[i] = 0;
-            else hist[i] = 0;
-        }
-        __syncthreads();
-        const uint64_t hm = (hb >= 63) ? 0ull : (~0ull << (hb + 1));
-        const uint64_t pf = *s_pf;
-        for (int64_t base = threadIdx.x; base < cnt_r; base += step) {
-            uint64_t kk[4];
-            int32_t cc[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int64_t i = base + j * (int64_t)blockDim.x;
-                kk[j] = 0;
-                cc[j] = 0;
-                if (i < cnt) get(i, &kk[j], &cc[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (base + j * (int64_t)blockDim.x >= cnt_r) break;  // warp-uniform
-                const bool in = cc[j] > 0 && (kk[j] & hm) == (pf & hm);
-                const unsigned d = in ? (unsigned)((kk[j] >> shift) & (nb - 1)) : 0xffffffffu;
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const unsigned c = in ? (unsigned)cc[j] : 0u;
-                const unsigned lo = __reduce_add_sync(peers, c & 0xffffu);
-                const unsigned hi = __reduce_add_sync(peers, c >> 16);
-                if (in && (peers & ((1u << lane) - 1)) == 0) {
-                    if (split) {
-                        atomicAdd(&hlo[d], lo);
-                        if (hi) atomicAdd(&hhi[d], hi);
-                    } else {
-                        atomicAdd(&hist[d], ((unsigned long long)hi << 16) + lo);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (split) {  // into 64-bit bins for the scan (bin i reads lo/hi before anyone writes i)
-            static_assert(kBins / kThreads == 8, "8 bins per thread at kThreads threads");
-            unsigned long long t[kBins / kThreads];
-            int n_t = 0;
-            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x)
-                t[n_t++] = (unsigned long long)hlo[i] + ((unsigned long long)hhi[i] << 16);
-            __syncthreads();
-            n_t = 0;
-            for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = t[n_t++];
-            __syncthreads();
-        }
-        if (threadIdx.x < 32) {
-            const unsigned per = nb / 32 > 0 ? nb / 32 : 1;  // bins per lane
-            unsigned long long local = 0;
-            for (unsigned j = 0; j < per; j++) {
-                const unsigned bi = lane * per + j;
-                if (bi < nb) local += hist[bi];
-            }
-            unsigned long long inc = local;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
-                if (lane >= d) inc += y;
-            }
-            const int64_t acc = *s_acc;
-            const bool reach = acc + (int64_t)inc >= thr;
-            const unsigned m = __ballot_sync(0xffffffffu, reach);
-            if (m == 0) {
-                if (lane == 0) *s_done = 1;  // total below the threshold
-            } else if (lane == __ffs(m) - 1) {
-                int64_t run = acc + (int64_t)(inc - local);
-                unsigned d = lane * per;
-                for (unsigned j = 0; j < per; j++) {
-                    const unsigned bi = lane * per + j;
-                    if (bi >= nb) break;
-                    if (run + (int64_t)hist[bi] >= thr) { d = bi; break; }
-                    run += (int64_t)hist[bi];
-                }
-                *s_acc = run;
-                *s_pf = pf | ((uint64_t)d << shift);
-            }
-        }
-        __syncthreads();
-        if (*s_done) return ~0ull;
-    }
-    return *s_pf;
 }
 
-// Min and max key over the entries with c > 0 (all threads of the CTA).
+// Highest differing key bit, or -1 if kmin > kmax (no weighted entry).
+__device__ __forceinline__ int key_top(unsigned long long kmin, unsigned long long kmax) {
+    if (kmin > kmax) return -1;
+    const unsigned long long diff = kmin ^ kmax;
+    return diff ? 63 - __clzll((long long)diff) : 0;
+}
+
+__device__ __forceinline__ int id_top(unsigned idmax) {
+    return idmax ? 31 - __clz((int)idmax) : 0;
+}
+
+// Adds weight c (>= 0) to bin d: lo sums the low 16 bits, hi the rest (native
+// 32-bit shared atomics; exact while a histogram takes <= 65536 entries).
+__device__ __forceinline__ void split_add(uint32_t *lo, uint32_t *hi, unsigned d, int32_t c) {
+    atomicAdd(&lo[d], (uint32_t)c & 0xffffu);
+    if ((uint32_t)c >> 16) atomicAdd(&hi[d], (uint32_t)c >> 16);
+}
+
+// Digit choice of one pass over the bins h[0, nb): the first bin d where
+// acc + (weight of bins <= d) >= thr, by a block-wide scan (thread t owns 8
+// consecutive bins).  Writes *s_pf |= d << shift and *s_acc, or *s_done = 1
+// when the total stays below thr.  All threads of the CTA call it.
+__device__ __forceinline__ void sel_decide(const unsigned long long *h, unsigned nb, int shift,
+                                           int64_t thr, int64_t *s_acc, uint64_t *s_pf,
+                                           int *s_done, int64_t *scan_tmp /* kThreads/32+1 */) {
+    static_assert(kBins == 8 * kThreads, "8 bins per thread");
+    const unsigned b0 = threadIdx.x * 8;
+    int64_t v[8], local = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        v[j] = b0 + j < nb ? (int64_t)h[b0 + j] : 0;
+        local += v[j];
+    }
+    const int64_t acc = *s_acc;
+    int64_t total;
+    const int64_t ex = block_exclusive_scan<kThreads>(local, &total, scan_tmp);
+    if (acc + total < thr) {
+        if (threadIdx.x == 0) *s_done = 1;
+    } else if (acc + ex + local >= thr && (threadIdx.x == 0 || acc + ex < thr)) {
+        int64_t run = acc + ex;
+        unsigned d = b0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (run + v[j] >= thr) { d = b0 + j; break; }
+            run += v[j];
+        }
+        *s_acc = run;
+        *s_pf |= (uint64_t)d << shift;
+    }
+    __syncthreads();
+}
+
+// Min and max key and max node id over the entries with c > 0 (all threads).
 template <typename Get>
 __device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *out_max,
-                             unsigned long long *red /* [64] */) {
+                             unsigned *out_idmax, unsigned long long *red /* [96] */) {
     unsigned long long mn = ~0ull, mx = 0;
+    unsigned im = 0;
     for (int64_t base = threadIdx.x; base < cnt; base += 4 * (int64_t)blockDim.x) {
         uint64_t kk[4];
         int32_t cc[4];
@@ -1091,6 +1055,7 @@ __device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *
             if (cc[j] <= 0) continue;
             mn = kk[j] < mn ? kk[j] : mn;
             mx = kk[j] > mx ? kk[j] : mx;
+            im = max(im, (unsigned)kk[j]);
         }
     }
 #pragma unroll
@@ -1099,31 +1064,105 @@ __device__ void block_minmax(Get get, int64_t cnt, uint64_t *out_min, uint64_t *
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, d);
         mn = x < mn ? x : mn;
         mx = y > mx ? y : mx;
+        im = max(im, __shfl_xor_sync(0xffffffffu, im, d));
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         red[w] = mn;
         red[32 + w] = mx;
+        red[64 + w] = im;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
             mn = red[i] < mn ? red[i] : mn;
             mx = red[32 + i] > mx ? red[32 + i] : mx;
+            im = max(im, (unsigned)red[64 + i]);
         }
         red[0] = mn;
         red[32] = mx;
+        red[64] = im;
     }
     __syncthreads();
     *out_min = red[0];
     *out_max = red[32];
+    *out_idmax = (unsigned)red[64];
     __syncthreads();
+}
+
+// Weighted radix select: the smallest key K such that the total weight of the
+// entries with key <= K is >= thr; ~0 if the total is < thr.  get(i, &key, &c)
+// returns entry i (c = 0 entries carry no weight); kmin / kmax / idmax come
+// from block_minmax.  Windows from sel_window; each pass histograms the
+// entries that match the digits fixed so far.  All threads of the CTA call it.
+template <typename Get>
+__device__ uint64_t select_first_reaching(Get get, int64_t cnt, int64_t thr, uint64_t kmin,
+                                          uint64_t kmax, unsigned idmax,
+                                          unsigned long long *hist /* [kBins] */,
+                                          int64_t *s_acc, uint64_t *s_pf, int *s_done,
+                                          int64_t *scan_tmp /* kThreads/32+1 */) {
+    const int top = key_top(kmin, kmax);
+    if (top < 0) return ~0ull;  // no weighted entry: everything is admitted
+    const int itop = id_top(idmax);
+    if (threadIdx.x == 0) {
+        *s_acc = 0;
+        *s_pf = top >= 63 ? 0ull : (kmin & (~0ull << (top + 1)));
+        *s_done = 0;
+    }
+    __syncthreads();
+    const bool split = cnt <= 65536;  // else 64-bit bins
+    uint32_t *hlo = reinterpret_cast<uint32_t *>(hist), *hhi = hlo + kBins;
+    const int64_t step = 4 * (int64_t)blockDim.x;
+    int hb, width;
+    for (int p = 0; sel_window(top, itop, p, &hb, &width); p++) {
+        const int shift = hb - width + 1;
+        const unsigned nb = 1u << width;
+        for (unsigned i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const uint64_t hm = (hb >= 63) ? 0ull : (~0ull << (hb + 1));
+        const uint64_t pf = *s_pf;
+        for (int64_t base = threadIdx.x; base < cnt; base += step) {
+            uint64_t kk[4];
+            int32_t cc[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t i = base + j * (int64_t)blockDim.x;
+                kk[j] = 0;
+                cc[j] = 0;
+                if (i < cnt) get(i, &kk[j], &cc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (cc[j] <= 0 || (kk[j] & hm) != (pf & hm)) continue;
+                const unsigned d = (unsigned)((kk[j] >> shift) & (nb - 1));
+                if (split) split_add(hlo, hhi, d, cc[j]);
+                else atomicAdd(&hist[d], (unsigned long long)cc[j]);
+            }
+        }
+        __syncthreads();
+        if (split) {  // to 64-bit bins: bin i reads its halves before anyone writes it
+            unsigned long long t[kBins / kThreads];
+#pragma unroll
+            for (int j = 0; j < kBins / kThreads; j++) {
+                const unsigned i = threadIdx.x + j * kThreads;
+                t[j] = (unsigned long long)hlo[i] + ((unsigned long long)hhi[i] << 16);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < kBins / kThreads; j++) hist[threadIdx.x + j * kThreads] = t[j];
+            __syncthreads();
+        }
+        sel_decide(hist, nb, shift, thr, s_acc, s_pf, s_done, scan_tmp);
+        if (*s_done) return ~0ull;
+    }
+    return *s_pf;
 }
 
 struct ArbSm {
     WDelta wd;
     unsigned long long hist[kBins];
-    unsigned long long red[64];
+    unsigned long long red[96];
+    int64_t scan_tmp[kThreads / 32 + 1];
     uint64_t keys[kSegSmem];
     int32_t c[kSegSmem];
     int64_t acc;
@@ -1153,12 +1192,18 @@ __device__ __forceinline__ void stage_segment(const SegEntry *ent, int cnt, uint
     }
 }
 
-// Admits the staged entries of a segment with key < K (and weight 0): the
-// owners are loaded 8 per thread ahead of the moves.  Whole warps iterate.
+// Admits the staged entries of a segment with key < K (and weight 0).  The
+// owners are loaded 8 per thread ahead of the moves; the weight leaving each
+// owner is summed over the warp's lanes with that owner, the weight entering
+// T per thread and then per warp.  Whole warps iterate.
 __device__ __forceinline__ int64_t admit_segment(const LPArgs &a, WDelta &wd, const SegEntry *ent,
                                                  int cnt, const uint64_t *keys, const int32_t *c,
                                                  uint64_t K, int32_t T) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long *dst = a.nW <= kAggW ? (unsigned long long *)wd.d
+                                             : (unsigned long long *)a.W;
     int64_t moved = 0;
+    long long tin = 0;
     const int cnt_r = (cnt + 31) & ~31;
     for (int base = threadIdx.x; base < cnt_r; base += 8 * blockDim.x) {
         int32_t own[8];
@@ -1167,17 +1212,28 @@ __device__ __forceinline__ int64_t admit_segment(const LPArgs &a, WDelta &wd, co
         for (int j = 0; j < 8; j++) {
             const int i = base + j * blockDim.x;
             adm[j] = i < cnt && (keys[i] < K || c[i] == 0);
-            own[j] = adm[j] ? ent[i].own : 0;
+            own[j] = adm[j] ? ent[i].own : -1;
         }
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int i = base + j * blockDim.x;
+            if (i - lane >= cnt_r) break;  // warp-uniform
+            const int32_t cj = adm[j] ? c[i] : 0;
             if (adm[j]) {
-                apply_agg(a, wd, (int32_t)(uint32_t)keys[i], T, own[j], c[i]);
+                a.lab[(int32_t)(uint32_t)keys[i]] = T;
+                tin += cj;
                 moved++;
             }
+            const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)own[j]);
+            const unsigned lo = __reduce_add_sync(peers, (unsigned)cj & 0xffffu);
+            const unsigned hi = __reduce_add_sync(peers, (unsigned)cj >> 16);
+            if (adm[j] && (peers & ((1u << lane) - 1)) == 0)
+                atomicAdd(&dst[own[j]], (unsigned long long)(-(((long long)hi << 16) + lo)));
         }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) tin += __shfl_down_sync(0xffffffffu, tin, d);
+    if (lane == 0 && tin) atomicAdd(&dst[T], (unsigned long long)tin);
     return moved;
 }
 
@@ -1186,7 +1242,8 @@ __device__ __forceinline__ int64_t admit_segment(const LPArgs &a, WDelta &wd, co
 // the others pass the uncontested sources' proposals through.
 __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
     __shared__ unsigned long long hist[kBins];
-    __shared__ unsigned long long red[64];
+    __shared__ unsigned long long red[96];
+    __shared__ int64_t scan_tmp[kThreads / 32 + 1];
     __shared__ int64_t s_acc;
     __shared__ uint64_t s_pf;
     __shared__ int s_done;
@@ -1204,9 +1261,10 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
             *c = mine ? p.c : 0;
         };
         uint64_t kmin, kmax;
-        block_minmax(get, nprop, &kmin, &kmax, red);
-        const uint64_t K = select_first_reaching(get, nprop, X, kmin, kmax, hist, &s_acc, &s_pf,
-                                                 &s_done);
+        unsigned idmax;
+        block_minmax(get, nprop, &kmin, &kmax, &idmax, red);
+        const uint64_t K = select_first_reaching(get, nprop, X, kmin, kmax, idmax, hist, &s_acc,
+                                                 &s_pf, &s_done, scan_tmp);
         for (int64_t i = threadIdx.x; i < nprop; i += blockDim.x) {
             Prop &p = a.props[i];
             if (p.slot != -2 || p.own != b) continue;
@@ -1257,7 +1315,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
                 if (bi >= a.maxbig || t0 + nt > a.maxtiles) {
                     a.ctr->err = kErrBig;  // cannot happen: capacities bound the totals
                 } else {
-                    a.big[bi] = BigSeg{si, nt, t0, 0, ~0ull, 0ull, 0ull, 0ll, 0};
+                    a.big[bi] = BigSeg{si, nt, t0, 0, ~0ull, 0ull, 0ull, 0ll, 0, 0u};
                     for (int t = 0; t < nt; t++) a.tileseg[t0 + t] = bi;
                 }
             }
@@ -1315,19 +1373,18 @@ __device__ void grid_barrier(GridBar *bar, int32_t *err) {
     __syncthreads();
 }
 
-// Highest differing key bit of a big segment, or -1 if it has no weighted entry.
-__device__ __forceinline__ int big_top(unsigned long long kmin, unsigned long long kmax) {
-    if (kmin > kmax) return -1;
-    const unsigned long long diff = kmin ^ kmax;
-    return diff ? 63 - __clzll((long long)diff) : 0;
+// Number of select passes of a big segment.
+__device__ __forceinline__ int big_passes(int top, int itop) {
+    if (top < 0) return 0;
+    int hb, width, p = 0;
+    while (sel_window(top, itop, p, &hb, &width)) p++;
+    return p;
 }
-
-__device__ __forceinline__ int big_passes(int top) { return top < 0 ? 0 : top / kDigit + 1; }
 
 // Control values of big-segment tile t, read by thread 0 and handed to the
 // CTA through shared memory so that every thread takes the same branches.
 struct BigTile {
-    int32_t ok, bi, len, top, done;
+    int32_t ok, bi, len, top, itop, done;
     int64_t i0;
     Seg sg;
     unsigned long long kmin, pf;
@@ -1345,7 +1402,8 @@ __device__ __forceinline__ BigTile big_tile(const LPArgs &a, int t, int nbig, Bi
             const int64_t rest = bt.sg.cnt - bt.i0;
             bt.len = (int)(rest < kBigTile ? rest : kBigTile);
             bt.kmin = __ldcg(&b->kmin);
-            bt.top = big_top(bt.kmin, __ldcg(&b->kmax));
+            bt.top = key_top(bt.kmin, __ldcg(&b->kmax));
+            bt.itop = id_top(__ldcg(&b->idmax));
             bt.done = __ldcg(&b->done);
             bt.pf = __ldcg(&b->pf);
             bt.ok = bt.len > 0 && bt.i0 >= 0;
@@ -1364,9 +1422,11 @@ __device__ __forceinline__ BigTile big_tile(const LPArgs &a, int t, int nbig, Bi
 // digit; a grid barrier separates the passes.  Tile blockIdx.x stays staged in
 // shared memory from the first read to the last.
 __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, int64_t &moved) {
-    __shared__ int s_flag, s_passes;
+    __shared__ int s_flag, s_passes, s_done;
+    __shared__ int64_t s_acc;
+    __shared__ uint64_t s_pf;
     __shared__ BigTile s_bt;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     // pass 0: key range of each segment
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BigTile bt = big_tile(a, t, nbig, &s_bt);
@@ -1374,6 +1434,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
         const SegEntry *ent = a.segbuf + bt.sg.base + bt.i0;
         const bool stage = t == (int)blockIdx.x;
         unsigned long long mn = ~0ull, mx = 0;
+        unsigned im = 0;
         for (int base = threadIdx.x; base < bt.len; base += 8 * blockDim.x) {
             SegEntry e[8];
 #pragma unroll
@@ -1393,6 +1454,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                 if (e[j].c > 0) {
                     mn = e[j].key < mn ? e[j].key : mn;
                     mx = e[j].key > mx ? e[j].key : mx;
+                    im = max(im, (unsigned)e[j].key);
                 }
             }
         }
@@ -1402,10 +1464,12 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
             const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, d);
             mn = x < mn ? x : mn;
             mx = y > mx ? y : mx;
+            im = max(im, __shfl_xor_sync(0xffffffffu, im, d));
         }
         if (lane == 0 && mn <= mx) {
             atomicMin(&a.big[bt.bi].kmin, mn);
             atomicMax(&a.big[bt.bi].kmax, mx);
+            atomicMax(&a.big[bt.bi].idmax, im);
         }
         __syncthreads();
     }
@@ -1415,7 +1479,8 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
     {
         int mp = 0;
         for (int bi = threadIdx.x; bi < nbig; bi += blockDim.x)
-            mp = max(mp, big_passes(big_top(__ldcg(&a.big[bi].kmin), __ldcg(&a.big[bi].kmax))));
+            mp = max(mp, big_passes(key_top(__ldcg(&a.big[bi].kmin), __ldcg(&a.big[bi].kmax)),
+                                    id_top(__ldcg(&a.big[bi].idmax))));
         atomicMax(&s_passes, mp);
     }
     __syncthreads();
@@ -1423,10 +1488,10 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
     for (int p = 0; p < passes; p++) {
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const BigTile bt = big_tile(a, t, nbig, &s_bt);
-            if (!bt.ok || p >= big_passes(bt.top) || bt.done) continue;
+            int hb, width;
+            if (!bt.ok || bt.top < 0 || bt.done || !sel_window(bt.top, bt.itop, p, &hb, &width))
+                continue;
             BigSeg *b = &a.big[bt.bi];
-            const int hb = bt.top - p * kDigit;
-            const int width = hb + 1 < kDigit ? hb + 1 : kDigit;
             const int shift = hb - width + 1;
             const unsigned nb = 1u << width;
             const unsigned long long hm = hb >= 63 ? 0ull : (~0ull << (hb + 1));
@@ -1451,16 +1516,8 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                         c = e.c;
                     }
                 }
-                const bool in = c > 0 && (key & hm) == (pf & hm);
-                const unsigned d = in ? (unsigned)((key >> shift) & (nb - 1)) : 0xffffffffu;
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const unsigned cw = in ? (unsigned)c : 0u;
-                const unsigned lo = __reduce_add_sync(peers, cw & 0xffffu);
-                const unsigned hi = __reduce_add_sync(peers, cw >> 16);
-                if (in && (peers & ((1u << lane) - 1)) == 0) {
-                    atomicAdd(&hlo[d], lo);  // a tile has <= 4096 entries: no overflow
-                    if (hi) atomicAdd(&hhi[d], hi);
-                }
+                if (c > 0 && (key & hm) == (pf & hm))  // a tile has <= 4096 entries
+                    split_add(hlo, hhi, (unsigned)((key >> shift) & (nb - 1)), c);
             }
             __syncthreads();
             unsigned long long *gh = a.bhist + (size_t)bt.bi * kBins;
@@ -1495,37 +1552,18 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
                     }
                 }
             }
+            if (threadIdx.x == 0) {
+                s_acc = p == 0 ? 0ll : __ldcg(&b->acc);
+                s_pf = pf;
+                s_done = 0;
+            }
             __syncthreads();
-            if (warp == 0) {
-                const long long acc = p == 0 ? 0ll : __ldcg(&b->acc);
-                const unsigned per = nb / 32 > 0 ? nb / 32 : 1;
-                unsigned long long local = 0;
-                for (unsigned j = 0; j < per; j++) {
-                    const unsigned bi2 = lane * per + j;
-                    if (bi2 < nb) local += sm.hist[bi2];
-                }
-                unsigned long long inc = local;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
-                    if (lane >= d) inc += y;
-                }
-                const bool reach = acc + (long long)inc >= bt.sg.thr;
-                const unsigned m = __ballot_sync(0xffffffffu, reach);
-                if (m == 0) {
-                    if (lane == 0) b->done = 1;
-                } else if (lane == __ffs(m) - 1) {
-                    long long run = acc + (long long)(inc - local);
-                    unsigned d = lane * per;
-                    for (unsigned j = 0; j < per; j++) {
-                        const unsigned bi2 = lane * per + j;
-                        if (bi2 >= nb) break;
-                        const long long h = (long long)sm.hist[bi2];
-                        if (run + h >= bt.sg.thr) { d = bi2; break; }
-                        run += h;
-                    }
-                    b->acc = run;
-                    b->pf = pf | ((unsigned long long)d << shift);
+            sel_decide(sm.hist, nb, shift, bt.sg.thr, &s_acc, &s_pf, &s_done, sm.scan_tmp);
+            if (threadIdx.x == 0) {
+                if (s_done) b->done = 1;
+                else {
+                    b->acc = s_acc;
+                    b->pf = s_pf;
                 }
             }
             __syncthreads();
@@ -1596,9 +1634,10 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
             *c = sm.c[i];
         };
         uint64_t kmin, kmax;
-        block_minmax(get, sg.cnt, &kmin, &kmax, sm.red);
-        const uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, kmin, kmax, sm.hist, &sm.acc,
-                                                 &sm.pf, &sm.done);
+        unsigned idmax;
+        block_minmax(get, sg.cnt, &kmin, &kmax, &idmax, sm.red);
+        const uint64_t K = select_first_reaching(get, sg.cnt, sg.thr, kmin, kmax, idmax, sm.hist,
+                                                 &sm.acc, &sm.pf, &sm.done, sm.scan_tmp);
         moved += admit_segment(a, sm.wd, ent, sg.cnt, sm.keys, sm.c, K, sg.T);
         __syncthreads();
     }
