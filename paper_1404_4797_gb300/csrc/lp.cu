@@ -395,6 +395,7 @@ struct PropSm {
     NodeSm nd;
     int64_t W[kDenseMaxK];
     int64_t scan_tmp[kThreads / 32 + 1];
+    unsigned long long red[kThreads / 32];
     int64_t li;
     int ndl, item, flag;
 };
@@ -425,10 +426,13 @@ __device__ __forceinline__ T ld(const T *p) {
     else return *p;
 }
 
-// Best eligible label of the CTA's row (node slot 0) over the distinct labels.
+// Best eligible label of the CTA's row (node slot 0) over the distinct labels:
+// per-thread maxima, reduced over the warp and then by thread 0 (red holds
+// one value per warp); ties on the best key resolve to the smallest label.
 __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *keys,
                                             const int32_t *vals, const uint16_t *dl, int ndl,
-                                            NodeSm &nd) {
+                                            NodeSm &nd, unsigned long long *red) {
+    unsigned long long best = 0;
     for (int i = threadIdx.x; i < ndl; i += kThreads) {
         const int slot = dl[i];
         const int32_t L = (int32_t)keys[slot];
@@ -436,8 +440,20 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *key
         if (L == nd.own[0]) {
             nd.ownw[0] = w;
         } else if (a.W[L] + nd.c[0] <= bnd(a, L)) {
-            atomicMax(&nd.best[0], cand_key(w, nd.h[0], L));
+            const unsigned long long ck = cand_key(w, nd.h[0], L);
+            best = ck > best ? ck : best;
         }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+        best = o > best ? o : best;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; w++) best = red[w] > best ? red[w] : best;
+        nd.best[0] = best;
     }
     __syncthreads();
     const unsigned long long b = nd.best[0];
@@ -584,7 +600,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 if (threadIdx.x < 32) select_dense_warp(a, sm.W, sm.t.acc, k, sm.nd, 0);
             } else {
                 const int ndl = sm.ndl;
-                select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, sm.nd);
+                select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, sm.nd, sm.red);
                 for (int i = threadIdx.x; i < ndl; i += kThreads) {
                     const int slot = sm.t.dl[i];
                     sm.t.keys[slot] = kEmpty32;
