@@ -52,6 +52,7 @@ constexpr int kThreads = 256;
 constexpr int kSmallDeg = 32;            // small nodes: <= 32 entries (one warp pass)
 constexpr int kMedDeg = 256;             // medium nodes: 33..256 entries (one warp each)
 constexpr int kChunk = 4096;             // entries per large-row piece (one CTA)
+constexpr int kMidDeg = 2048;            // rows up to this size: the 128-thread CTA kernel
 constexpr int kWSlots = 512;             // per-warp table slots for medium rows (>= 2 * kMedDeg)
 constexpr int kSlots = 8192;             // hash table slots (>= 2 * kChunk)
 constexpr int kSlotBits = 13;
@@ -100,6 +101,7 @@ struct Ctr {
     int32_t err;              // kErrTable or kErrBarrier
     int32_t nbig, bigtiles;   // segments above kSegSmem and their tiles
     int32_t huge_next;        // next row of the cluster path
+    int32_t mid_next;         // next row of the 128-thread CTA path
 };
 
 constexpr int32_t kErrTable = 1;
@@ -166,6 +168,10 @@ struct LPArgs {
     int32_t huge_on;
     int32_t *hlist;
     int32_t *hcnt;
+    // rows of kMedDeg < degree <= kMidDeg: mlist + c * nL lists colour c's
+    // rows as (index into Lnodes) << 20
+    int64_t *mlist;
+    int32_t *mcnt;
     // segments above kSegSmem entries (arbitrated by the whole grid)
     BigSeg *big;
     int32_t *tileseg;          // tile -> index into big
@@ -291,7 +297,10 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
                             if (a.Lnodes[mid] <= v) lo = mid;
                             else hi = mid;
                         }
-                        if (a.huge_on && d > kChunk && d <= kHugeDeg) {
+                        if (d <= kMidDeg) {
+                            const int pos = atomicAdd(&a.mcnt[col], 1);
+                            a.mlist[(int64_t)col * a.nL + pos] = lo << 20;
+                        } else if (a.huge_on && d > kChunk && d <= kHugeDeg) {
                             const int pos = atomicAdd(&a.hcnt[col], 1);
                             a.hlist[(int64_t)col * a.nL + pos] = (int32_t)lo;
                         } else {
@@ -379,23 +388,34 @@ struct NodeSm {
     uint8_t ovl[kMedItem];
 };
 
+// Shape of a CTA-row kernel: threads, table slots (2^SBITS) and the longest
+// piece it takes.  BigRows: rows up to kChunk entries (and pieces of longer
+// rows); MidRows: rows of kMedDeg < degree <= kMidDeg, more CTAs per SM.
+template <int NT, int SBITS, int CHUNK>
+struct RowShape {
+    static constexpr int kNT = NT, kSBits = SBITS, kSl = 1 << SBITS, kCh = CHUNK;
+    static_assert((1 << SBITS) >= 2 * CHUNK, "load factor <= 1/2");
+};
+using BigRows = RowShape<kThreads, kSlotBits, kChunk>;
+using MidRows = RowShape<128, 12, kMidDeg>;
+
+template <typename RS>
 struct HashTab {
-    uint32_t keys[kSlots];  // labels; kEmpty32 = empty
-    int32_t vals[kSlots];
-    uint16_t dl[kChunk];
+    uint32_t keys[RS::kSl];  // labels; kEmpty32 = empty
+    int32_t vals[RS::kSl];
+    uint16_t dl[RS::kCh];
 };
 
 struct DenseTab {
     int32_t acc[kDenseMaxK];
 };
 
-template <int MODE>
+template <int MODE, typename RS>
 struct PropSm {
-    typename std::conditional<MODE == kRefineDense, DenseTab, HashTab>::type t;
+    typename std::conditional<MODE == kRefineDense, DenseTab, HashTab<RS>>::type t;
     NodeSm nd;
     int64_t W[kDenseMaxK];
-    int64_t scan_tmp[kThreads / 32 + 1];
-    unsigned long long red[kThreads / 32];
+    unsigned long long red[RS::kNT / 32];
     int64_t li;
     int ndl, item, flag;
 };
@@ -429,11 +449,12 @@ __device__ __forceinline__ T ld(const T *p) {
 // Best eligible label of the CTA's row (node slot 0) over the distinct labels:
 // per-thread maxima, reduced over the warp and then by thread 0 (red holds
 // one value per warp); ties on the best key resolve to the smallest label.
+template <int NT>
 __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *keys,
                                             const int32_t *vals, const uint16_t *dl, int ndl,
                                             NodeSm &nd, unsigned long long *red) {
     unsigned long long best = 0;
-    for (int i = threadIdx.x; i < ndl; i += kThreads) {
+    for (int i = threadIdx.x; i < ndl; i += NT) {
         const int slot = dl[i];
         const int32_t L = (int32_t)keys[slot];
         const int32_t w = vals[slot];
@@ -452,12 +473,12 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *key
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < kThreads / 32; w++) best = red[w] > best ? red[w] : best;
+        for (int w = 1; w < NT / 32; w++) best = red[w] > best ? red[w] : best;
         nd.best[0] = best;
     }
     __syncthreads();
     const unsigned long long b = nd.best[0];
-    for (int i = threadIdx.x; i < ndl; i += kThreads) {
+    for (int i = threadIdx.x; i < ndl; i += NT) {
         const int slot = dl[i];
         const int32_t L = (int32_t)keys[slot];
         const int32_t w = vals[slot];
@@ -539,15 +560,15 @@ __device__ __forceinline__ int32_t load_node(const LPArgs &a, const int64_t *Wsm
 
 // ---------------------------------------------------------------- fused propose kernel
 
-template <int MODE>
-__device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
+template <int MODE, typename RS>
+__device__ void process_large(const LPArgs &a, PropSm<MODE, RS> &sm, int k, const int64_t *plist,
+                              int npieces, int32_t *next) {
     constexpr bool DENSE = MODE == kRefineDense;
-    const int npieces = a.pcnt[a.colour];
-    const int64_t *plist = a.plist + (int64_t)a.colour * a.Ptot;
+    constexpr int NT = RS::kNT;
     while (true) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int p = atomicAdd(&a.ctr->large_next, 1);
+            const int p = atomicAdd(next, 1);
             sm.item = p;
             if (p < npieces) sm.li = plist[p];
         }
@@ -564,15 +585,15 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
         }
         __syncthreads();
         const int64_t deg = a.g.xadj[v + 1] - a.g.xadj[v];
-        const int64_t e0 = pi * kChunk;
+        const int64_t e0 = pi * kChunk;  // pieces are kChunk entries (RS::kCh >= any row given here)
         const int64_t e1 = min64(deg, e0 + kChunk);
         const int64_t rs = sm.nd.rs[0];
         const int32_t cpv = sm.nd.cpv[0];
-        for (int64_t eb = e0 + threadIdx.x; eb < e1; eb += kUnroll * kThreads) {
+        for (int64_t eb = e0 + threadIdx.x; eb < e1; eb += kUnroll * NT) {
             int32_t u[kUnroll], w[kUnroll], L[kUnroll];
 #pragma unroll
             for (int j = 0; j < kUnroll; j++) {
-                const int64_t e = eb + j * kThreads;
+                const int64_t e = eb + j * NT;
                 u[j] = e < e1 ? __ldg(&a.g.adjncy[rs + e]) : -1;
                 w[j] = e < e1 ? __ldg(&a.g.adjwgt[rs + e]) : 0;
             }
@@ -587,7 +608,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 if constexpr (DENSE) {
                     atomicAdd(&sm.t.acc[L[j]], w[j]);
                 } else {
-                    if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, kSlots - 1, kSlotBits,
+                    if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, RS::kSl - 1, RS::kSBits,
                                    (uint32_t)L[j], w[j]))
                         a.ctr->err = kErrTable;
                 }
@@ -600,8 +621,8 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
                 if (threadIdx.x < 32) select_dense_warp(a, sm.W, sm.t.acc, k, sm.nd, 0);
             } else {
                 const int ndl = sm.ndl;
-                select_best(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, sm.nd, sm.red);
-                for (int i = threadIdx.x; i < ndl; i += kThreads) {
+                select_best<NT>(a, sm.t.keys, sm.t.vals, sm.t.dl, ndl, sm.nd, sm.red);
+                for (int i = threadIdx.x; i < ndl; i += NT) {
                     const int slot = sm.t.dl[i];
                     sm.t.keys[slot] = kEmpty32;
                     sm.t.vals[slot] = 0;
@@ -614,7 +635,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
         // merge the piece into the row's global state
         if constexpr (DENSE) {
             int32_t *gacc = a.gacc + li * k;
-            for (int b = threadIdx.x; b < k; b += kThreads) {
+            for (int b = threadIdx.x; b < k; b += NT) {
                 const int32_t w = sm.t.acc[b];
                 if (w) {
                     atomicAdd(&gacc[b], w);
@@ -650,7 +671,7 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE> &sm, int k) {
             int32_t *gv = a.gvals + off;
             const int lane = threadIdx.x & 31;
             const int ndl_r = (ndl + 31) & ~31;
-            for (int i = threadIdx.x; i < ndl_r; i += kThreads) {
+            for (int i = threadIdx.x; i < ndl_r; i += NT) {
                 int32_t gslot = -1;
                 if (i < ndl) {
                     const int slot = sm.t.dl[i];
@@ -795,21 +816,28 @@ __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
     small_bin<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, a.wl_cnt[b0 + 3], gwarp, nwarps);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_propose(LPArgs a, int k) {
+// CTA rows: BigRows takes the pieces listed in plist (rows above kMidDeg),
+// MidRows the rows listed in mlist.
+template <int MODE, typename RS>
+__global__ void __launch_bounds__(RS::kNT) k_propose(LPArgs a, int k) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    PropSm<MODE> &sm = *reinterpret_cast<PropSm<MODE> *>(smraw);
+    PropSm<MODE, RS> &sm = *reinterpret_cast<PropSm<MODE, RS> *>(smraw);
     if (a.nL == 0) return;
     if constexpr (MODE == kRefineDense) {
-        for (int i = threadIdx.x; i < kDenseMaxK; i += kThreads) sm.t.acc[i] = 0;
-        for (int b = threadIdx.x; b < k; b += kThreads) sm.W[b] = a.W[b];
+        for (int i = threadIdx.x; i < kDenseMaxK; i += RS::kNT) sm.t.acc[i] = 0;
+        for (int b = threadIdx.x; b < k; b += RS::kNT) sm.W[b] = a.W[b];
     } else {
-        for (int i = threadIdx.x; i < kSlots; i += kThreads) {
+        for (int i = threadIdx.x; i < RS::kSl; i += RS::kNT) {
             sm.t.keys[i] = kEmpty32;
             sm.t.vals[i] = 0;
         }
     }
-    process_large<MODE>(a, sm, k);
+    if constexpr (std::is_same<RS, MidRows>::value)
+        process_large<MODE, RS>(a, sm, k, a.mlist + (int64_t)a.colour * a.nL, a.mcnt[a.colour],
+                                &a.ctr->mid_next);
+    else
+        process_large<MODE, RS>(a, sm, k, a.plist + (int64_t)a.colour * a.Ptot, a.pcnt[a.colour],
+                                &a.ctr->large_next);
 }
 
 // Medium rows (33..kMedDeg entries): one warp per row with a warp-private
@@ -2174,17 +2202,24 @@ void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, 
 
 // ---------------------------------------------------------------- host driver
 
-template <int MODE>
-static void set_propose_attr(size_t smem) {
-    CK(cudaFuncSetAttribute(k_propose<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+// Grid of a CTA-row kernel: resident CTAs per SM times SMs (sets its
+// dynamic shared memory limit first).
+template <int MODE, typename RS>
+static int row_grid(int sms) {
+    const size_t smem = sizeof(PropSm<MODE, RS>);
+    CK(cudaFuncSetAttribute(k_propose<MODE, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose<MODE, RS>, RS::kNT, smem));
+    return sms * std::max(1, occ);
 }
 
 template <int MODE>
-static int propose_grid(int sms) {
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose<MODE>, kThreads,
-                                                     sizeof(PropSm<MODE>)));
-    return sms * std::max(1, occ);
+static void launch_rows(const LPArgs &a, int k, int grid_mid, int grid_big, cudaStream_t s) {
+    k_propose<MODE, MidRows><<<grid_mid, MidRows::kNT, sizeof(PropSm<MODE, MidRows>), s>>>(a, k);
+    LAUNCHED();
+    k_propose<MODE, BigRows><<<grid_big, BigRows::kNT, sizeof(PropSm<MODE, BigRows>), s>>>(a, k);
+    LAUNCHED();
 }
 
 int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, int64_t *W_out) {
@@ -2238,13 +2273,14 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.bar = sc.zeros<GridBar>(1);
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
     // bucket lengths, then piece counts, then cluster-path row counts (per colour)
-    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + 2 * S);
+    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + 3 * S);
     Ctr *ctr = sc.get<Ctr>(S);
     int64_t *d_moves = sc.zeros<int64_t>(cfg.rounds);
     a.wl = wl;
     a.wl_cnt = wl_cnt;
     a.pcnt = wl_cnt + kClasses * S;
     a.hcnt = wl_cnt + kClasses * S + S;
+    a.mcnt = wl_cnt + kClasses * S + 2 * S;
     a.huge_on = mode != kRefineDense;
     a.prof = prof().on ? prof().d_counts : nullptr;
 
@@ -2270,6 +2306,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             CK(cudaStreamSynchronize(s));
             a.plist = sc.get<int64_t>((size_t)S * (a.Ptot ? a.Ptot : 1));
             a.hlist = sc.get<int32_t>((size_t)S * nL);
+            a.mlist = sc.get<int64_t>((size_t)S * nL);
             a.Ldone = sc.zeros<int32_t>(nL);
             a.Lndl = sc.zeros<int32_t>(nL);
             if (mode == kRefineDense) {
@@ -2303,15 +2340,14 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         }
     }
 
-    size_t psmem = 0;
-    int grid_main = 0;
+    int grid_mid = 0, grid_big = 0;
     switch (mode) {
-        case kCluster: psmem = sizeof(PropSm<kCluster>); set_propose_attr<kCluster>(psmem);
-                       grid_main = propose_grid<kCluster>(sms); break;
-        case kRefineHash: psmem = sizeof(PropSm<kRefineHash>); set_propose_attr<kRefineHash>(psmem);
-                          grid_main = propose_grid<kRefineHash>(sms); break;
-        default: psmem = sizeof(PropSm<kRefineDense>); set_propose_attr<kRefineDense>(psmem);
-                 grid_main = propose_grid<kRefineDense>(sms); break;
+        case kCluster: grid_mid = row_grid<kCluster, MidRows>(sms);
+                       grid_big = row_grid<kCluster, BigRows>(sms); break;
+        case kRefineHash: grid_mid = row_grid<kRefineHash, MidRows>(sms);
+                          grid_big = row_grid<kRefineHash, BigRows>(sms); break;
+        default: grid_mid = row_grid<kRefineDense, MidRows>(sms);
+                 grid_big = row_grid<kRefineDense, BigRows>(sms); break;
     }
     CK(cudaFuncSetAttribute(k_arbitrate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)sizeof(ArbSm)));
@@ -2345,7 +2381,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         for (int r = 0; r < cfg.rounds; r++) {
             a.round = r;
             a.moves = d_moves + r;
-            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + 2 * S) * sizeof(int32_t), s));
+            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + 3 * S) * sizeof(int32_t), s));
             CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
             k_build_wl<<<sms * 4, kThreads, 0, s>>>(a, wl, wl_cnt);
             LAUNCHED();
@@ -2374,12 +2410,13 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                     LAUNCHED();
                     CK(cudaEventRecord(ev_join2, side2));
                 }
-                switch (mode) {
-                    case kCluster: k_propose<kCluster><<<grid_main, kThreads, psmem, s>>>(a, k); break;
-                    case kRefineHash: k_propose<kRefineHash><<<grid_main, kThreads, psmem, s>>>(a, k); break;
-                    default: k_propose<kRefineDense><<<grid_main, kThreads, psmem, s>>>(a, k); break;
+                if (a.nL > 0) {
+                    switch (mode) {
+                        case kCluster: launch_rows<kCluster>(a, k, grid_mid, grid_big, s); break;
+                        case kRefineHash: launch_rows<kRefineHash>(a, k, grid_mid, grid_big, s); break;
+                        default: launch_rows<kRefineDense>(a, k, grid_mid, grid_big, s); break;
+                    }
                 }
-                LAUNCHED();
                 CK(cudaStreamWaitEvent(s, ev_join, 0));
                 if (huge) CK(cudaStreamWaitEvent(s, ev_join2, 0));
                 prof_end(s, pb, pe);
