@@ -153,21 +153,34 @@ struct FlagNew {
     __device__ int64_t operator()(int64_t i) const { return (i == 0 || k[i] != k[i - 1]) ? 1 : 0; }
 };
 
+// Sorted (key, w) pairs -> unique keys: the thread at the start of each run
+// of equal keys sums the run and writes the coarse entry; row degrees are
+// counted with one atomic per distinct row in each warp.
 __global__ void k_reduce_by_key(const unsigned long long *keys, const int32_t *w, int64_t P,
                                 const int64_t *pos, int cbits, int32_t *adjncy, int32_t *adjwgt,
                                 int32_t *cdeg) {
     const uint64_t mask = (cbits >= 64) ? ~0ull : ((1ull << cbits) - 1);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        int64_t p = pos[i] - 1 + ((i == 0 || keys[i - 1] != k) ? 1 : 0);
-        // pos is the exclusive scan of "new key" flags; the unique index of i
-        // is pos[i] if i starts a run, else pos[i] - 1.
-        atomicAdd(&adjwgt[p], w[i]);
-        if (i == 0 || keys[i - 1] != k) {
-            adjncy[p] = (int32_t)(k & mask);
-            atomicAdd(&cdeg[(int64_t)(k >> cbits)], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t P_r = (P + 31) & ~31ll;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P_r; i += stride) {
+        bool start = false;
+        int64_t row = -1;
+        if (i < P) {
+            const uint64_t k = keys[i];
+            start = i == 0 || keys[i - 1] != k;
+            if (start) {
+                int64_t sum = w[i];
+                for (int64_t j = i + 1; j < P && keys[j] == k; j++) sum += w[j];
+                const int64_t p = pos[i];  // exclusive count of run starts before i
+                adjncy[p] = (int32_t)(k & mask);
+                adjwgt[p] = (int32_t)sum;
+                row = (int64_t)(k >> cbits);
+            }
         }
+        const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)row);
+        if (start && (peers & ((1u << lane) - 1)) == 0)
+            atomicAdd(&cdeg[row], __popc(peers));
     }
 }
 
@@ -263,7 +276,6 @@ void contract_impl(const DGraph &g, const int32_t *lab, int32_t *f2c, CoarseGrap
     CK(cudaStreamSynchronize(s));
     int32_t *adjncy = (int32_t *)out_alloc(m2 * sizeof(int32_t));
     int32_t *adjwgt = (int32_t *)out_alloc(m2 * sizeof(int32_t));
-    CK(cudaMemsetAsync(adjwgt, 0, (m2 ? m2 : 1) * sizeof(int32_t), s));
     int32_t *cdeg = sc.zeros<int32_t>(n2);
     if (P > 0) {
         k_reduce_by_key<<<grid, 256, 0, s>>>(pk, pw, (int64_t)P, pos, cbits, adjncy, adjwgt, cdeg);
@@ -314,6 +326,26 @@ __global__ void __launch_bounds__(256) k_cut(DGraph g, const int32_t *part, cons
         const int64_t e0 = t * kCutTile;
         const int len = (int)min64(kCutTile, g.nnz - e0);
         block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
+        if (groups == 1) {  // all loads of the thread's 16 entries first
+            int32_t u[16], w[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int i = threadIdx.x + j * 256;
+                u[j] = i < len ? g.adjncy[e0 + i] : 0;
+                w[j] = i < len ? g.adjwgt[e0 + i] : 0;
+            }
+            int32_t pu[16], pv[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int i = threadIdx.x + j * 256;
+                pu[j] = i < len ? __ldg(&part[u[j]]) : 0;
+                pv[j] = i < len ? __ldg(&part[rowof[i]]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) acc += pu[j] != pv[j] ? w[j] : 0;
+            __syncthreads();
+            continue;
+        }
         for (int i = threadIdx.x; i < len; i += 256) {
             const int32_t v = rowof[i];
             if (v >= gend) {  // rows only grow along a thread's entries
