@@ -109,6 +109,21 @@ def lib():
             L.or_refine_batched.argtypes = [C.c_int32, _P64, _PP64, _PP32, _PP32, _PP32,
                                             C.c_int32, _P64, C.c_int32, C.c_int32, C.c_uint64,
                                             C.c_int32, _P32, _P32, _P64, _P64]
+            _PF = C.POINTER(C.c_float)
+            _PU8 = C.POINTER(C.c_uint8)
+            _PU16 = C.POINTER(C.c_uint16)
+            L.or_bf16.restype = C.c_float
+            L.or_bf16.argtypes = [C.c_float]
+            L.or_log2_feature.restype = C.c_float
+            L.or_log2_feature.argtypes = [C.c_int64]
+            L.or_features.argtypes = [C.c_int64, _P64, _P32, _P32, _P32, _P64, C.c_int64, _PU8,
+                                      _PF]
+            L.or_mlp_score.argtypes = [C.c_int64, _PF, _PU16, _PF]
+            L.or_refine_learned.argtypes = g + [C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                                                C.c_uint64, _PU16, C.c_float, C.c_int32, _P32,
+                                                _P32, _P64, _P64, _PF, _PU8]
+            L.or_mlp_loss_grad.restype = C.c_double
+            L.or_mlp_loss_grad.argtypes = [_PF, _PU8, C.c_int64, _PF, C.POINTER(C.c_double)]
             _lib = L
     return _lib
 
@@ -306,3 +321,86 @@ def multilevel(g, params: dict):
                  init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
                  cut=st.cut, maxbw=st.maxbw)
     return part, stats
+
+
+# ---------------------------------------------------------------- learned gate
+
+MLP_NPARAM = 1313
+MLP_LAYOUT = {"W1": (0, (32, 6)), "b1": (192, (32,)), "W2": (224, (32, 32)),
+              "b2": (1248, (32,)), "W3": (1280, (32,)), "b3": (1312, (1,))}
+
+
+def _pf(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _pu8(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def _pu16(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint16))
+
+
+def bf16(x: float) -> float:
+    """bfloat16 rounding (nearest, ties to even) of a float32."""
+    return float(lib().or_bf16(C.c_float(x)))
+
+
+def log2_feature(x: int) -> float:
+    return float(lib().or_log2_feature(x))
+
+
+def features(g, lab, W, lmax, moved=None):
+    """Six bf16-rounded features per node, float32 [n, 6]."""
+    keep, a = _graph_args(g)
+    n = a[0]
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    W = np.ascontiguousarray(W, dtype=np.int64)
+    mv = None if moved is None else np.ascontiguousarray(moved, dtype=np.uint8)
+    x = np.zeros((n, 6), np.float32)
+    lib().or_features(n, a[1], a[2], a[3], _p32(lab), _p64(W), lmax,
+                      None if mv is None else _pu8(mv), _pf(x))
+    return x
+
+
+def mlp_score(X, net_bf16):
+    """Logits of the bf16 network (uint16 [1313]) on feature rows X [N, 6]."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    net = np.ascontiguousarray(net_bf16, dtype=np.uint16)
+    z = np.zeros(X.shape[0], np.float32)
+    lib().or_mlp_score(X.shape[0], _pf(X), _pu16(net), _pf(z))
+    return z
+
+
+def refine_learned(g, k, eps, rounds, subrounds, seed, part, net_bf16=None, z_min=0.0,
+                   full_every=3, trace=False):
+    """Returns (part, moves per round, visited, trace_x or None, trace_y or None)."""
+    keep, a = _graph_args(g)
+    n = a[0]
+    p = np.array(part, dtype=np.int32, copy=True)
+    rd = C.c_int32(0)
+    moves = np.zeros(max(rounds, 1), np.int64)
+    visited = C.c_int64(0)
+    net = None if net_bf16 is None else np.ascontiguousarray(net_bf16, dtype=np.uint16)
+    tx = np.zeros((rounds, n, 6), np.float32) if trace else None
+    ty = np.zeros((rounds, n), np.uint8) if trace else None
+    rc = lib().or_refine_learned(*a, k, eps, rounds, subrounds, seed,
+                                 None if net is None else _pu16(net), z_min, full_every,
+                                 _p32(p), C.byref(rd), _p64(moves), C.byref(visited),
+                                 None if tx is None else _pf(tx), None if ty is None else _pu8(ty))
+    _check(rc, "refine_learned")
+    r = rd.value
+    return (p, moves[:r].copy(), visited.value, None if tx is None else tx[:r],
+            None if ty is None else ty[:r])
+
+
+def mlp_loss_grad(X, y, params):
+    """Mean logistic loss and its gradient (float64 [1313]) of float32 parameters."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    grad = np.zeros(MLP_NPARAM, np.float64)
+    loss = lib().or_mlp_loss_grad(_pf(X), _pu8(y), X.shape[0], _pf(prm),
+                                  grad.ctypes.data_as(C.POINTER(C.c_double)))
+    return float(loss), grad

@@ -182,7 +182,8 @@ static int64_t bound_of(const int64_t *Bv, int64_t B, int64_t L)
 static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                         const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
                         int64_t *W, int64_t B, const int64_t *Bv, int refine,
-                        const int32_t *cp, uint64_t seed, int32_t round, int32_t S, lp_ws *ws)
+                        const int32_t *cp, uint64_t seed, int32_t round, int32_t S,
+                        const uint8_t *active, lp_ws *ws)
 {
     int64_t moves = 0;
     for (int32_t j = 0; j < S; j++) {
@@ -191,6 +192,7 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         for (int64_t v = 0; v < n; v++) {
             if ((int32_t)or_colour(seed, round, v, S) != j) continue;
             if (xadj[v + 1] == xadj[v]) continue;  /* no neighbours: never moves */
+            if (active && !active[v]) continue;    /* learned form: not visited */
             int64_t nt = 0;
             for (int64_t i = xadj[v]; i < xadj[v + 1]; i++) {
                 int64_t u = adjncy[i];
@@ -288,7 +290,7 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     int32_t done = 0;
     for (int32_t r = 0; r < rounds; r++) {
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, Bv, refine, cp,
-                             seed, r, S, &ws);
+                             seed, r, S, NULL, &ws);
         if (moves_per_round) moves_per_round[r] = m;
         done = r + 1;
         if (m == 0) break;
@@ -812,4 +814,233 @@ out:
         if (lv[l].own) { free(lv[l].xadj); free(lv[l].adjncy); free(lv[l].adjwgt); free(lv[l].vwgt); }
     }
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* learned active set for refinement (not in the paper: a gate that    */
+/* decides which nodes a refinement round visits; full sweeps every    */
+/* full_every rounds and in the last round keep it a heuristic over    */
+/* the plain method)                                                   */
+/* ------------------------------------------------------------------ */
+
+/* bfloat16 rounding of a finite float, round to nearest, ties to even: add
+ * 0x7FFF plus the lowest kept bit to the 32-bit pattern and drop the low 16
+ * bits. */
+float or_bf16(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+static float bf16_bits_to_float(uint16_t b)
+{
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* 2^-e as a float, 0 <= e <= 62 (exact). */
+static float pow2_neg(int e)
+{
+    uint32_t u = (uint32_t)(127 - e) << 23;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* Feature 1: log2 of x >= 1 by its piecewise-linear form e + (x - 2^e)/2^e,
+ * e = floor(log2 x); exact at powers of two, every step IEEE-rounded. */
+float or_log2_feature(int64_t x)
+{
+    int e = 0;
+    while (e < 62 && (x >> (e + 1)) != 0) e++;
+    float frac = (float)(x - ((int64_t)1 << e)) * pow2_neg(e);
+    return (float)e + frac;
+}
+
+/* The six features of every node (row-major [n][6], each rounded to bf16):
+ *   f1 log2-feature(1 + deg), f2 W(own)/L_max, f3 external share of the
+ *   weighted degree, f4 v moved in the previous round, f5 share of v's
+ *   neighbours that moved in the previous round, f6 own block overloaded.
+ * Nodes without neighbours get zeros. */
+void or_features(int64_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                 const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
+                 float *x)
+{
+    for (int64_t v = 0; v < n; v++) {
+        float *f = x + v * 6;
+        int64_t deg = xadj[v + 1] - xadj[v];
+        if (deg == 0) {
+            for (int i = 0; i < 6; i++) f[i] = 0.0f;
+            continue;
+        }
+        int64_t wdeg = 0, wown = 0, nmov = 0;
+        for (int64_t i = xadj[v]; i < xadj[v + 1]; i++) {
+            int32_t u = adjncy[i];
+            wdeg += adjwgt[i];
+            if (lab[u] == lab[v]) wown += adjwgt[i];
+            if (moved && moved[u]) nmov++;
+        }
+        int64_t own = lab[v];
+        f[0] = or_bf16(or_log2_feature(1 + deg));
+        f[1] = or_bf16((float)W[own] / (float)Lmax);
+        f[2] = or_bf16((float)(wdeg - wown) / (float)wdeg);
+        f[3] = (moved && moved[v]) ? 1.0f : 0.0f;
+        f[4] = or_bf16((float)nmov / (float)deg);
+        f[5] = W[own] > Lmax ? 1.0f : 0.0f;
+    }
+}
+
+/* Forward pass of the 6-32-32-1 scorer on one node's (bf16) features; the
+ * parameters are 1313 bf16 values: W1[32][6], b1[32], W2[32][32], b2[32],
+ * W3[32], b3.  Every output starts from its bias and adds w * x with one
+ * fmaf per input in index order (float accumulator); hidden outputs go
+ * through ReLU and are rounded to bf16.  Returns the logit z. */
+float or_mlp_forward(const uint16_t *net, const float *x)
+{
+    float h1[32], h2[32];
+    for (int j = 0; j < 32; j++) {
+        float acc = bf16_bits_to_float(net[OR_MLP_B1 + j]);
+        for (int i = 0; i < 6; i++)
+            acc = fmaf(bf16_bits_to_float(net[OR_MLP_W1 + j * 6 + i]), x[i], acc);
+        h1[j] = or_bf16(acc > 0.0f ? acc : 0.0f);
+    }
+    for (int j = 0; j < 32; j++) {
+        float acc = bf16_bits_to_float(net[OR_MLP_B2 + j]);
+        for (int i = 0; i < 32; i++)
+            acc = fmaf(bf16_bits_to_float(net[OR_MLP_W2 + j * 32 + i]), h1[i], acc);
+        h2[j] = or_bf16(acc > 0.0f ? acc : 0.0f);
+    }
+    float z = bf16_bits_to_float(net[OR_MLP_B3]);
+    for (int i = 0; i < 32; i++) z = fmaf(bf16_bits_to_float(net[OR_MLP_W3 + i]), h2[i], z);
+    return z;
+}
+
+/* Refinement with the learned gate (Sec. III.A local search; the gate is not
+ * in the paper).  Before round r the features are built from the state at
+ * that point (moved flags of round r - 1); in a gated round only nodes with
+ * logit >= z_min are visited, in a full round (r % full_every ==
+ * full_every - 1, the last round, or every round when net is NULL) all are.
+ * The run stops after a full round without moves.  trace_x [rounds][n][6]
+ * and trace_y [rounds][n] (moved in round r) are written when non-NULL;
+ * visited_out counts the visited nodes with neighbours over all rounds. */
+int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                      const int32_t *adjwgt, const int32_t *vwgt, int32_t k, double eps,
+                      int32_t rounds, int32_t S, uint64_t seed, const uint16_t *net,
+                      float z_min, int32_t full_every, int32_t *part, int32_t *rounds_done,
+                      int64_t *moves_per_round, int64_t *visited_out, float *trace_x,
+                      uint8_t *trace_y)
+{
+    if (k < 1 || eps < 0 || rounds < 0 || S < 1 || full_every < 1) return OR_EINVAL;
+    for (int64_t v = 0; v < n; v++)
+        if (part[v] < 0 || part[v] >= k) return OR_EINVAL;
+    int64_t B = or_lmax(total_weight(n, vwgt, NULL), k, eps);
+    int64_t *W = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    uint8_t *moved = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+    uint8_t *active = (uint8_t *)malloc((size_t)(n ? n : 1));
+    int32_t *prev = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    float *x = (float *)malloc(sizeof(float) * 6 * (size_t)(n ? n : 1));
+    lp_ws ws;
+    ws.acc = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    ws.touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    ws.props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
+    int rc = OR_OK;
+    if (!W || !moved || !active || !prev || !x || !ws.acc || !ws.touched || !ws.props) {
+        rc = OR_ENOMEM;
+        goto out;
+    }
+    for (int64_t v = 0; v < n; v++) W[part[v]] += vwgt[v];
+    int64_t visited = 0;
+    int32_t done = 0;
+    for (int32_t r = 0; r < rounds; r++) {
+        int full = !net || r % full_every == full_every - 1 || r == rounds - 1;
+        or_features(n, xadj, adjncy, adjwgt, part, W, B, moved, x);
+        if (trace_x) memcpy(trace_x + (size_t)r * n * 6, x, sizeof(float) * 6 * (size_t)n);
+        for (int64_t v = 0; v < n; v++) {
+            active[v] = full ? 1 : (or_mlp_forward(net, x + v * 6) >= z_min);
+            if (active[v] && xadj[v + 1] > xadj[v]) visited++;
+        }
+        memcpy(prev, part, sizeof(int32_t) * (size_t)n);
+        int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, part, W, B, NULL, 1, NULL, seed, r,
+                             S, active, &ws);
+        for (int64_t v = 0; v < n; v++) moved[v] = part[v] != prev[v];
+        if (trace_y) memcpy(trace_y + (size_t)r * n, moved, (size_t)n);
+        if (moves_per_round) moves_per_round[r] = m;
+        done = r + 1;
+        if (full && m == 0) break;
+    }
+    if (rounds_done) *rounds_done = done;
+    if (visited_out) *visited_out = visited;
+out:
+    free(W); free(moved); free(active); free(prev); free(x);
+    free(ws.acc); free(ws.touched); free(ws.props);
+    return rc;
+}
+
+/* Loss and gradient of the scorer for training, in double: mean over the N
+ * samples of the logistic loss log(1 + e^z) - y z of the float parameters
+ * (same layout as the bf16 network, no rounding), with ReLU'(0) = 0.
+ * grad [OR_MLP_NPARAM] is overwritten.  Returns the loss. */
+double or_mlp_loss_grad(const float *X, const uint8_t *y, int64_t N, const float *prm,
+                        double *grad)
+{
+    for (int i = 0; i < OR_MLP_NPARAM; i++) grad[i] = 0.0;
+    double loss = 0.0;
+    for (int64_t s = 0; s < N; s++) {
+        const float *x = X + s * 6;
+        double a1[32], h1[32], a2[32], h2[32];
+        for (int j = 0; j < 32; j++) {
+            double acc = prm[OR_MLP_B1 + j];
+            for (int i = 0; i < 6; i++) acc += (double)prm[OR_MLP_W1 + j * 6 + i] * x[i];
+            a1[j] = acc;
+            h1[j] = acc > 0 ? acc : 0;
+        }
+        for (int j = 0; j < 32; j++) {
+            double acc = prm[OR_MLP_B2 + j];
+            for (int i = 0; i < 32; i++) acc += (double)prm[OR_MLP_W2 + j * 32 + i] * h1[i];
+            a2[j] = acc;
+            h2[j] = acc > 0 ? acc : 0;
+        }
+        double z = prm[OR_MLP_B3];
+        for (int i = 0; i < 32; i++) z += (double)prm[OR_MLP_W3 + i] * h2[i];
+        double t = y[s] ? 1.0 : 0.0;
+        /* log(1 + e^z) - t z, written to avoid overflow */
+        loss += (z > 0 ? z + log1p(exp(-z)) : log1p(exp(z))) - t * z;
+        double dz = 1.0 / (1.0 + exp(-z)) - t;
+        double d2[32], d1[32];
+        grad[OR_MLP_B3] += dz;
+        for (int i = 0; i < 32; i++) {
+            grad[OR_MLP_W3 + i] += dz * h2[i];
+            d2[i] = a2[i] > 0 ? dz * prm[OR_MLP_W3 + i] : 0.0;
+        }
+        for (int i = 0; i < 32; i++) d1[i] = 0.0;
+        for (int j = 0; j < 32; j++) {
+            grad[OR_MLP_B2 + j] += d2[j];
+            for (int i = 0; i < 32; i++) {
+                grad[OR_MLP_W2 + j * 32 + i] += d2[j] * h1[i];
+                d1[i] += d2[j] * prm[OR_MLP_W2 + j * 32 + i];
+            }
+        }
+        for (int j = 0; j < 32; j++) {
+            double dj = a1[j] > 0 ? d1[j] : 0.0;
+            grad[OR_MLP_B1 + j] += dj;
+            for (int i = 0; i < 6; i++) grad[OR_MLP_W1 + j * 6 + i] += dj * x[i];
+        }
+    }
+    if (N > 0) {
+        for (int i = 0; i < OR_MLP_NPARAM; i++) grad[i] /= (double)N;
+        loss /= (double)N;
+    }
+    return loss;
+}
+
+/* The logit of each of N feature rows (row-major [N][6]). */
+void or_mlp_score(int64_t N, const float *X, const uint16_t *net, float *z)
+{
+    for (int64_t s = 0; s < N; s++) z[s] = or_mlp_forward(net, X + s * 6);
 }

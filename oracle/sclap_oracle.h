@@ -113,6 +113,31 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt,
                   const or_ml_params *p, int32_t *part_out, or_ml_stats *st);
 
+/* learned active set (refinement gate; not in the paper) */
+#define OR_MLP_NPARAM 1313
+#define OR_MLP_W1 0     /* [32][6] */
+#define OR_MLP_B1 192   /* [32] */
+#define OR_MLP_W2 224   /* [32][32] */
+#define OR_MLP_B2 1248  /* [32] */
+#define OR_MLP_W3 1280  /* [32] */
+#define OR_MLP_B3 1312  /* [1] */
+
+float or_bf16(float f);
+float or_log2_feature(int64_t x);
+void or_features(int64_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+                 const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
+                 float *x);
+float or_mlp_forward(const uint16_t *net, const float *x);
+void or_mlp_score(int64_t N, const float *X, const uint16_t *net, float *z);
+int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                      const int32_t *adjwgt, const int32_t *vwgt, int32_t k, double eps,
+                      int32_t rounds, int32_t S, uint64_t seed, const uint16_t *net,
+                      float z_min, int32_t full_every, int32_t *part, int32_t *rounds_done,
+                      int64_t *moves_per_round, int64_t *visited_out, float *trace_x,
+                      uint8_t *trace_y);
+double or_mlp_loss_grad(const float *X, const uint8_t *y, int64_t N, const float *prm,
+                        double *grad);
+
 #ifdef __cplusplus
 }
 #endif
