@@ -196,6 +196,58 @@ int sclap_initial_partition(const sclap_graph *g, int32_t k, int64_t B, int32_t 
                             int32_t *part_out, int64_t *cuts_out, int64_t *maxbw_out,
                             int32_t *best_out, void *stream);
 
+/* ---- learned active set (a gate over refinement rounds; the paper has no
+ * counterpart: its refinement visits every node, Sec. III.A) ----
+ *
+ * The scorer is a 6-32-32-1 network of 1313 parameters in this order:
+ * W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3 (row-major, output index
+ * first).  Inference takes them as bf16 bit patterns; training as float.
+ * Features of node v before a round (each rounded to bf16, nearest even):
+ *   1 e + (x - 2^e) / 2^e for x = 1 + deg(v), e = floor(log2 x)
+ *   2 W(own) / L_max
+ *   3 (weighted degree - weight to own block) / weighted degree
+ *   4 1 if v moved in the previous round
+ *   5 moved neighbours in the previous round / deg(v)
+ *   6 1 if W(own) > L_max
+ * (zeros for nodes without neighbours).  Every output starts from its bias
+ * and adds one fmaf per input in index order (float accumulator); hidden
+ * outputs pass ReLU and are rounded to bf16; the last output is the logit. */
+
+/* Refinement (as sclap_refine) where a gated round visits only the nodes
+ * whose logit is >= z_min; round r is full (every node) when r % full_every
+ * == full_every - 1, when r is the last round, or always when net is NULL
+ * (then the call equals sclap_refine).  A run stops after a full round
+ * without moves.
+ *   net          device uint16[1313] bf16 parameters, or NULL
+ *   visited_out  host: nodes with neighbours visited, summed over rounds (NULL ok)
+ *   trace_x      device float[rounds][n][6]: the features before each round (NULL ok)
+ *   trace_y      device uint8[rounds][n]: 1 if the node moved in that round (NULL ok)
+ * Rows of the traces past *rounds_done are left untouched.  Errors as
+ * sclap_refine (EINVAL also for full_every < 1); part_inout is restored. */
+int sclap_refine_learned(const sclap_graph *g, int32_t k, double eps, int32_t rounds,
+                         int32_t subrounds, uint64_t seed, const uint16_t *net, float z_min,
+                         int32_t full_every, int32_t *part_inout, int64_t *cut_out,
+                         int64_t *block_w_out, int32_t *rounds_done, int64_t *visited_out,
+                         float *trace_x, uint8_t *trace_y, void *stream);
+
+/* Logits of N feature rows x (device float[N][6]) with the bf16 network net
+ * (device uint16[1313]) into z_out (device float[N]). */
+int sclap_mlp_score(const float *x, int64_t N, const uint16_t *net, float *z_out, void *stream);
+
+/* Mean logistic loss log(1 + e^z) - y z over N samples (x device float[N][6],
+ * y device uint8[N]) of the float network params (device float[1313], no bf16
+ * rounding) and its gradient (device float[1313], overwritten); *loss_out on
+ * the host.  Float arithmetic, summation order not fixed. */
+int sclap_mlp_loss_grad(const float *x, const uint8_t *y, int64_t N, const float *params,
+                        float *grad_out, double *loss_out, void *stream);
+
+/* Plain minibatch SGD on the loss above: `epochs` passes over the samples in
+ * an order shuffled per epoch (sort by SplitMix64 of seed, epoch and index),
+ * batches of `batch`, params -= lr * gradient after each.  *loss_out: the
+ * loss over all samples after training.  1 <= N <= INT32_MAX. */
+int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, int32_t epochs,
+                    int32_t batch, float lr, uint64_t seed, double *loss_out, void *stream);
+
 /* A set of graphs for batched runs (host array of graph views). */
 typedef struct {
     int32_t ngraphs;

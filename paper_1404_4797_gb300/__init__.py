@@ -101,6 +101,14 @@ _SIGS = {
                                        C.POINTER(MLStats), _VP]),
     "sclap_graph_copy_out": (C.c_int, [C.POINTER(GraphOwned), _VP, _VP, _VP, _VP, _VP]),
     "sclap_graph_free": (None, [C.POINTER(GraphOwned)]),
+    "sclap_refine_learned": (C.c_int, [C.POINTER(Graph), C.c_int32, C.c_double, C.c_int32,
+                                       C.c_int32, C.c_uint64, _VP, C.c_float, C.c_int32, _VP,
+                                       _P64, _P64, _P32, _P64, _VP, _VP, _VP]),
+    "sclap_mlp_score": (C.c_int, [_VP, C.c_int64, _VP, _VP, _VP]),
+    "sclap_mlp_loss_grad": (C.c_int, [_VP, _VP, C.c_int64, _VP, _VP,
+                                      C.POINTER(C.c_double), _VP]),
+    "sclap_mlp_train": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int32, C.c_int32, C.c_float,
+                                  C.c_uint64, C.POINTER(C.c_double), _VP]),
     "sclap_prof_enable": (None, [C.c_int]),
     "sclap_prof_reset": (None, []),
     "sclap_prof_read": (C.c_int, [C.POINTER(Prof)]),
@@ -196,6 +204,81 @@ def sclap_refine(g: dict, k: int, eps: float, rounds: int, subrounds: int, seed:
                               C.byref(cut), C.cast(bw.data_ptr(), _P64), C.byref(rd),
                               _stream(stream)), "sclap_refine")
     return p, cut.value, bw, rd.value
+
+
+MLP_PARAMS = 1313
+
+
+def sclap_refine_learned(g: dict, k: int, eps: float, rounds: int, subrounds: int, seed: int,
+                         part: torch.Tensor, net: torch.Tensor | None = None, z_min: float = 0.0,
+                         full_every: int = 3, trace: bool = False, stream=None):
+    """Refinement with the learned gate (see include/sclap.h).  `net`: device
+    int16/uint16-bit bf16 parameters [1313] or None.  Returns (part, cut,
+    block_weights, rounds_done, visited, trace_x [r, n, 6] or None,
+    trace_y [r, n] or None)."""
+    _require_cuda(g["xadj"], part)
+    n = g["vwgt"].numel()
+    p = part.to(torch.int32).clone()
+    cut = C.c_int64(0)
+    bw = torch.zeros(k, dtype=torch.int64)
+    rd = C.c_int32(0)
+    vis = C.c_int64(0)
+    if net is not None and (net.numel() != MLP_PARAMS or net.element_size() != 2):
+        raise TypeError("net must hold 1313 bf16 bit patterns (16-bit elements)")
+    tx = torch.zeros((max(rounds, 1), n, 6), dtype=torch.float32, device=p.device) if trace else None
+    ty = torch.zeros((max(rounds, 1), n), dtype=torch.uint8, device=p.device) if trace else None
+    gg = _graph(g)
+    _check(lib().sclap_refine_learned(C.byref(gg), k, eps, rounds, subrounds, seed & (2**64 - 1),
+                                      _ptr(net), z_min, full_every, _ptr(p), C.byref(cut),
+                                      C.cast(bw.data_ptr(), _P64), C.byref(rd), C.byref(vis),
+                                      _ptr(tx), _ptr(ty), _stream(stream)),
+           "sclap_refine_learned")
+    r = rd.value
+    return (p, cut.value, bw, r, vis.value, None if tx is None else tx[:r],
+            None if ty is None else ty[:r])
+
+
+def sclap_mlp_score(x: torch.Tensor, net: torch.Tensor, stream=None) -> torch.Tensor:
+    """Logits of the bf16 network on feature rows x (device float32 [N, 6])."""
+    _require_cuda(x, net)
+    x = x.to(torch.float32).contiguous()
+    z = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().sclap_mlp_score(_ptr(x), x.shape[0], _ptr(net), _ptr(z), _stream(stream)),
+           "sclap_mlp_score")
+    return z
+
+
+def sclap_mlp_loss_grad(x: torch.Tensor, y: torch.Tensor, params: torch.Tensor, stream=None):
+    """Mean logistic loss and gradient (device float32 [1313]) of float params."""
+    _require_cuda(x, y, params)
+    x = x.to(torch.float32).contiguous()
+    y = y.to(torch.uint8).contiguous()
+    params = params.to(torch.float32).contiguous()
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = C.c_double(0)
+    _check(lib().sclap_mlp_loss_grad(_ptr(x), _ptr(y), x.shape[0], _ptr(params), _ptr(grad),
+                                     C.byref(loss), _stream(stream)), "sclap_mlp_loss_grad")
+    return loss.value, grad
+
+
+def sclap_mlp_train(x: torch.Tensor, y: torch.Tensor, params: torch.Tensor, epochs: int,
+                    batch: int, lr: float, seed: int, stream=None):
+    """Minibatch SGD on the scorer; trains a copy of params.  Returns (params, loss)."""
+    _require_cuda(x, y, params)
+    x = x.to(torch.float32).contiguous()
+    y = y.to(torch.uint8).contiguous()
+    prm = params.to(torch.float32).clone().contiguous()
+    loss = C.c_double(0)
+    _check(lib().sclap_mlp_train(_ptr(x), _ptr(y), x.shape[0], _ptr(prm), epochs, batch, lr,
+                                 seed & (2**64 - 1), C.byref(loss), _stream(stream)),
+           "sclap_mlp_train")
+    return prm, loss.value
+
+
+def bf16_bits(params: torch.Tensor) -> torch.Tensor:
+    """bf16 bit patterns (int16 tensor) of float parameters, nearest-even
+    rounding (torch's float32 -> bfloat16 conversion)."""
+    return params.to(torch.float32).to(torch.bfloat16).view(torch.int16).contiguous()
 
 
 def sclap_refine_bound(g: dict, nblocks: int, B: int, rounds: int, subrounds: int, seed: int,

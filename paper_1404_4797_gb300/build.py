@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsclap.so")
-SOURCES = ["prims.cu", "lp.cu", "contract.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["prims.cu", "lp.cu", "contract.cu", "api.cu", "noalloc.cu", "learned.cu"]
 HEADERS = ["common.cuh", "prims.cuh", "lp.cuh", "contract.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

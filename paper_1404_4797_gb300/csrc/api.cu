@@ -5,6 +5,7 @@
 #include <new>
 
 #include "contract.cuh"
+#include "learned.cuh"
 #include "lp.cuh"
 #include "prims.cuh"
 
@@ -431,6 +432,26 @@ void check_totals_cluster(const GraphTotals &t) {
 
 // ---------------------------------------------------------------- C ABI
 
+namespace {
+
+// Keys of the shuffle of epoch e: SplitMix64 of (seed, epoch, sample).
+__global__ void k_shuffle_keys(int64_t N, uint64_t seed, int epoch, uint64_t *keys,
+                               int32_t *vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = mix64(seed ^ ((uint64_t)(epoch + 1) << 40) ^ (uint64_t)i);
+        vals[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_widen(int64_t N, const int32_t *a, int64_t *b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *sclap_strerror(int code) {
@@ -558,6 +579,134 @@ int sclap_refine(const sclap_graph *gp, int32_t k, double eps, int32_t rounds, i
         if (cut_out) *cut_out = cut;
     }
     return rc;
+}
+
+int sclap_refine_learned(const sclap_graph *gp, int32_t k, double eps, int32_t rounds,
+                         int32_t subrounds, uint64_t seed, const uint16_t *net, float z_min,
+                         int32_t full_every, int32_t *part_inout, int64_t *cut_out,
+                         int64_t *block_w_out, int32_t *rounds_done, int64_t *visited_out,
+                         float *trace_x, uint8_t *trace_y, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    int32_t *backup = nullptr;
+    int rc = guarded([&] {
+        if (!gp || (!part_inout && gp->n > 0)) fail(SCLAP_EINVAL, "null");
+        if (k < 1 || !(eps >= 0) || rounds < 0 || subrounds < 1 || subrounds > 32 ||
+            full_every < 1)
+            fail(SCLAP_EINVAL, "args");
+        Scratch sc(s);
+        DGraph g = view(gp);
+        validate_graph(g, sc);
+        if (!in_range(g.n, part_inout, k, sc)) fail(SCLAP_EINVAL, "part out of range");
+        GraphTotals t = graph_totals(g, sc, true);
+        if (t.max_wdeg > INT32_MAX) fail(SCLAP_EOVERFLOW, "weighted degree");
+        CK(cudaMalloc(&backup, (g.n ? g.n : 1) * sizeof(int32_t)));
+        CK(cudaMemcpyAsync(backup, part_inout, g.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        int64_t *W = sc.get<int64_t>(k);
+        Gate gt{};
+        gt.g = g;
+        gt.lab = part_inout;
+        gt.W = W;
+        gt.Lmax = lmax_of(t.cV, k, eps);
+        gt.net = net;
+        gt.z_min = z_min;
+        gt.full_every = full_every;
+        gt.rounds = rounds;
+        gt.trace_x = trace_x;
+        gt.trace_y = trace_y;
+        gate_init(gt, sc);
+        LPConfig cfg{};
+        cfg.g = g;
+        cfg.lab = part_inout;
+        cfg.nW = k;
+        cfg.B = gt.Lmax;
+        cfg.refine = true;
+        cfg.seed = seed;
+        cfg.rounds = rounds;
+        cfg.S = subrounds;
+        cfg.before_round = [&](int r, const uint8_t **active) {
+            return gate_round(gt, r, active, s);
+        };
+        int rd = lp_run(cfg, sc, nullptr, W);
+        gate_finish(gt, rd, s);
+        unsigned long long vis = 0;
+        CK(cudaMemcpyAsync(&vis, gt.visited, sizeof(vis), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (rounds_done) *rounds_done = rd;
+        if (visited_out) *visited_out = (int64_t)vis;
+    });
+    if (rc != SCLAP_OK && backup && gp) {
+        cudaMemcpyAsync(part_inout, backup, gp->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    if (backup) cudaFree(backup);
+    if (rc) return rc;
+    if (cut_out || block_w_out) {
+        int64_t cut = 0;
+        rc = sclap_cut(gp, part_inout, k, &cut, block_w_out, stream);
+        if (cut_out) *cut_out = cut;
+    }
+    return rc;
+}
+
+int sclap_mlp_score(const float *x, int64_t N, const uint16_t *net, float *z_out, void *stream) {
+    return guarded([&] {
+        if (N < 0 || (N > 0 && (!x || !net || !z_out))) fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        mlp_score(x, N, net, z_out, s);
+        CK(cudaStreamSynchronize(s));
+    });
+}
+
+int sclap_mlp_loss_grad(const float *x, const uint8_t *y, int64_t N, const float *params,
+                        float *grad_out, double *loss_out, void *stream) {
+    return guarded([&] {
+        if (N < 0 || !params || !grad_out || (N > 0 && (!x || !y))) fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        double *d_loss = sc.zeros<double>(1);
+        CK(cudaMemsetAsync(grad_out, 0, kMlpParams * sizeof(float), s));
+        mlp_loss_grad(x, y, nullptr, N, params, grad_out, d_loss, s);
+        double l = 0;
+        CK(cudaMemcpyAsync(&l, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (loss_out) *loss_out = l;
+    });
+}
+
+int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, int32_t epochs,
+                    int32_t batch, float lr, uint64_t seed, double *loss_out, void *stream) {
+    return guarded([&] {
+        if (N < 1 || N > INT32_MAX || !x || !y || !params || epochs < 0 || batch < 1 || !(lr > 0))
+            fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        Scratch sc(s);
+        const int sms = dev_info().sms;
+        uint64_t *keys = sc.get<uint64_t>(N);
+        int32_t *perm = sc.get<int32_t>(N);
+        int64_t *idx = sc.get<int64_t>(N);
+        float *grad = sc.get<float>(kMlpParams);
+        double *d_loss = sc.zeros<double>(1);
+        for (int e = 0; e < epochs; e++) {
+            k_shuffle_keys<<<sms * 4, 256, 0, s>>>(N, seed, e, keys, perm);
+            LAUNCHED();
+            radix_sort_pairs(keys, perm, N, 64, sc);
+            k_widen<<<sms * 4, 256, 0, s>>>(N, perm, idx);
+            LAUNCHED();
+            for (int64_t b0 = 0; b0 < N; b0 += batch) {
+                const int64_t nb = std::min<int64_t>(batch, N - b0);
+                CK(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s));
+                mlp_loss_grad(x, y, idx + b0, nb, params, grad, d_loss, s);
+                mlp_sgd(params, grad, lr, s);
+            }
+        }
+        CK(cudaMemsetAsync(d_loss, 0, sizeof(double), s));
+        CK(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s));
+        mlp_loss_grad(x, y, nullptr, N, params, grad, d_loss, s);
+        double l = 0;
+        CK(cudaMemcpyAsync(&l, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (loss_out) *loss_out = l;
+    });
 }
 
 int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cut_out,

@@ -1,0 +1,371 @@
+// learned.cu -- the learned active set of refinement (not in the paper: a
+// scorer gates which nodes a refinement round visits; every full_every-th
+// round and the last one visit all nodes) and the training kernels of its
+// 6-32-32-1 scorer.
+//
+// Inference is bit-reproducible on a CPU: features and hidden outputs are
+// rounded to bf16 (nearest, ties to even), every output starts from its bias
+// and adds one fmaf per input in index order, and the gate compares the
+// logit with z_min (no exponential).
+#include "learned.cuh"
+#include "prims.cuh"
+
+namespace sclap {
+
+// ---------------------------------------------------------------- bf16 and features
+
+__device__ __forceinline__ float bf16_round(float f) {
+    uint32_t u = __float_as_uint(f);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return __uint_as_float(u & 0xFFFF0000u);
+}
+
+__device__ __forceinline__ float bf16_value(uint16_t b) {
+    return __uint_as_float((uint32_t)b << 16);
+}
+
+// log2 of x >= 1 in its piecewise-linear form e + (x - 2^e) / 2^e.
+__device__ __forceinline__ float log2_feature(int64_t x) {
+    const int e = 63 - __clzll((long long)x);
+    const float scale = __uint_as_float((uint32_t)(127 - e) << 23);  // 2^-e, exact
+    const float frac = __fmul_rn(__ll2float_rn(x - ((int64_t)1 << e)), scale);
+    return __fadd_rn((float)e, frac);
+}
+
+// Per-row sums over tiles of 4096 entries: thread t takes 16 consecutive
+// entries and flushes a running sum whenever its row changes.  wdeg (if
+// non-null): total weight; wown / nmov (if lab non-null): weight to
+// neighbours with the row's label, neighbours that moved.
+constexpr int kRowTile = 4096;
+
+__global__ void __launch_bounds__(256)
+    k_row_sums(DGraph g, const int32_t *lab, const uint8_t *moved, unsigned long long *wdeg,
+               unsigned long long *wown, int32_t *nmov) {
+    __shared__ int32_t rowof[kRowTile];
+    __shared__ int32_t tmp[16];
+    const int64_t tiles = ceil_div<int64_t>(g.nnz, kRowTile);
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kRowTile;
+        const int len = (int)min64(kRowTile, g.nnz - e0);
+        block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
+        int32_t row = -1;
+        unsigned long long sw = 0, so = 0;
+        int32_t sm = 0;
+        int32_t lrow = 0;
+        for (int j = 0; j < 16; j++) {
+            const int i = threadIdx.x * 16 + j;
+            if (i >= len) break;
+            const int32_t v = rowof[i];
+            if (v != row) {
+                if (row >= 0) {
+                    if (wdeg) atomicAdd(&wdeg[row], sw);
+                    if (lab) {
+                        if (so) atomicAdd(&wown[row], so);
+                        if (sm) atomicAdd(&nmov[row], sm);
+                    }
+                }
+                row = v;
+                sw = so = 0;
+                sm = 0;
+                if (lab) lrow = lab[v];
+            }
+            const int32_t u = g.adjncy[e0 + i];
+            const int32_t w = g.adjwgt[e0 + i];
+            sw += (unsigned long long)w;
+            if (lab) {
+                if (lab[u] == lrow) so += (unsigned long long)w;
+                sm += moved[u] ? 1 : 0;
+            }
+        }
+        if (row >= 0) {
+            if (wdeg) atomicAdd(&wdeg[row], sw);
+            if (lab) {
+                if (so) atomicAdd(&wown[row], so);
+                if (sm) atomicAdd(&nmov[row], sm);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// moved[v] = label changed since the previous call; prev = labels now.
+__global__ void k_moved(int64_t n, const int32_t *lab, int32_t *prev, uint8_t *moved,
+                        uint8_t *trace_y, bool first) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t l = lab[v];
+        const uint8_t m = first ? 0 : (uint8_t)(l != prev[v]);
+        moved[v] = m;
+        prev[v] = l;
+        if (trace_y) trace_y[v] = m;
+    }
+}
+
+// Scorer forward on one row of six bf16 features; params in shared memory
+// (floats holding bf16 values).
+__device__ __forceinline__ float mlp_forward(const float *P, const float *x) {
+    float h1[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        float acc = P[kMlpB1 + j];
+#pragma unroll
+        for (int i = 0; i < 6; i++) acc = __fmaf_rn(P[kMlpW1 + j * 6 + i], x[i], acc);
+        h1[j] = bf16_round(acc > 0.0f ? acc : 0.0f);
+    }
+    float z = P[kMlpB3];
+    for (int j = 0; j < 32; j++) {
+        float acc = P[kMlpB2 + j];
+#pragma unroll
+        for (int i = 0; i < 32; i++) acc = __fmaf_rn(P[kMlpW2 + j * 32 + i], h1[i], acc);
+        z = __fmaf_rn(P[kMlpW3 + j], bf16_round(acc > 0.0f ? acc : 0.0f), z);
+    }
+    return z;
+}
+
+__device__ __forceinline__ void load_net(const uint16_t *net, float *P) {
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) P[i] = bf16_value(net[i]);
+    __syncthreads();
+}
+
+// Features of every node (written to x when non-null) and, in gated rounds,
+// the active flags (logit >= z_min); counts the visited rows.
+__global__ void __launch_bounds__(256)
+    k_gate(DGraph g, const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
+           const unsigned long long *wdeg, const unsigned long long *wown, const int32_t *nmov,
+           const uint16_t *net, float z_min, bool full, float *x_out, uint8_t *active,
+           unsigned long long *visited) {
+    __shared__ float P[kMlpParams];
+    const bool score = !full && net;
+    if (score) load_net(net, P);
+    const int lane = threadIdx.x & 31;
+    const int64_t n_r = (g.n + 31) & ~31ll;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_r;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        bool vis = false;
+        if (v < g.n) {
+            const int64_t deg = g.xadj[v + 1] - g.xadj[v];
+            float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (deg > 0) {
+                const int32_t own = lab[v];
+                const int64_t wo = (int64_t)wown[v], wd = (int64_t)wdeg[v];
+                f[0] = bf16_round(log2_feature(1 + deg));
+                f[1] = bf16_round(__fdiv_rn(__ll2float_rn(W[own]), __ll2float_rn(Lmax)));
+                f[2] = bf16_round(__fdiv_rn(__ll2float_rn(wd - wo), __ll2float_rn(wd)));
+                f[3] = moved[v] ? 1.0f : 0.0f;
+                f[4] = bf16_round(__fdiv_rn(__int2float_rn(nmov[v]), __ll2float_rn(deg)));
+                f[5] = W[own] > Lmax ? 1.0f : 0.0f;
+            }
+            if (x_out) {
+#pragma unroll
+                for (int i = 0; i < 6; i++) x_out[v * 6 + i] = f[i];
+            }
+            bool act = true;
+            if (score) act = mlp_forward(P, f) >= z_min;
+            active[v] = act ? 1 : 0;
+            vis = act && deg > 0;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0 && b) atomicAdd(visited, (unsigned long long)__popc(b));
+    }
+}
+
+__global__ void k_count_rows(DGraph g, unsigned long long *cnt) {
+    const int64_t n_r = (g.n + 31) & ~31ll;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_r;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const bool r = v < g.n && g.xadj[v + 1] > g.xadj[v];
+        const unsigned b = __ballot_sync(0xffffffffu, r);
+        if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, (unsigned long long)__popc(b));
+    }
+}
+
+void gate_init(Gate &gt, Scratch &sc) {
+    const int64_t n = gt.g.n;
+    cudaStream_t s = sc.stream();
+    const int sms = dev_info().sms;
+    unsigned long long *wd = sc.zeros<unsigned long long>(n ? n : 1);
+    gt.wdeg = (int64_t *)wd;
+    gt.prev = sc.get<int32_t>(n ? n : 1);
+    gt.moved = sc.zeros<uint8_t>(n ? n : 1);
+    gt.active = sc.get<uint8_t>(n ? n : 1);
+    gt.wown = sc.get<unsigned long long>(n ? n : 1);
+    gt.nmov = sc.get<int32_t>(n ? n : 1);
+    gt.visited = sc.zeros<unsigned long long>(1);
+    if (gt.g.nnz > 0) {
+        k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, nullptr, nullptr, wd, nullptr, nullptr);
+        LAUNCHED();
+    }
+}
+
+bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
+    const int64_t n = gt.g.n;
+    const int sms = dev_info().sms;
+    const bool full = !gt.net || r % gt.full_every == gt.full_every - 1 || r == gt.rounds - 1;
+    if (n > 0) {
+        k_moved<<<sms * 4, 256, 0, s>>>(n, gt.lab, gt.prev, gt.moved,
+                                        (gt.trace_y && r > 0) ? gt.trace_y + (size_t)(r - 1) * n
+                                                               : nullptr,
+                                        r == 0);
+        LAUNCHED();
+    }
+    float *x = gt.trace_x ? gt.trace_x + (size_t)r * n * 6 : nullptr;
+    if (full && !x) {  // nothing to compute: every node, count the rows
+        if (n > 0) {
+            k_count_rows<<<sms * 4, 256, 0, s>>>(gt.g, gt.visited);
+            LAUNCHED();
+        }
+        *active = nullptr;
+        return true;
+    }
+    if (n > 0) {
+        CK(cudaMemsetAsync(gt.wown, 0, n * sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(gt.nmov, 0, n * sizeof(int32_t), s));
+        if (gt.g.nnz > 0) {
+            k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, gt.lab, gt.moved, nullptr, gt.wown,
+                                               gt.nmov);
+            LAUNCHED();
+        }
+        k_gate<<<sms * 4, 256, 0, s>>>(gt.g, gt.lab, gt.W, gt.Lmax, gt.moved,
+                                       (const unsigned long long *)gt.wdeg, gt.wown, gt.nmov,
+                                       gt.net, gt.z_min, full, x, gt.active, gt.visited);
+        LAUNCHED();
+    }
+    *active = full ? nullptr : gt.active;
+    return full;
+}
+
+void gate_finish(Gate &gt, int rounds_done, cudaStream_t s) {
+    if (!gt.trace_y || rounds_done < 1 || gt.g.n == 0) return;
+    const int sms = dev_info().sms;
+    k_moved<<<sms * 4, 256, 0, s>>>(gt.g.n, gt.lab, gt.prev, gt.moved,
+                                    gt.trace_y + (size_t)(rounds_done - 1) * gt.g.n, false);
+    LAUNCHED();
+}
+
+// ---------------------------------------------------------------- scoring
+
+__global__ void __launch_bounds__(256)
+    k_score(const float *x, int64_t N, const uint16_t *net, float *z) {
+    __shared__ float P[kMlpParams];
+    load_net(net, P);
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        float f[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) f[i] = x[s * 6 + i];
+        z[s] = mlp_forward(P, f);
+    }
+}
+
+void mlp_score(const float *x, int64_t N, const uint16_t *net, float *z, cudaStream_t s) {
+    if (N <= 0) return;
+    k_score<<<dev_info().sms * 4, 256, 0, s>>>(x, N, net, z);
+    LAUNCHED();
+}
+
+// ---------------------------------------------------------------- training
+
+// Warp sum of a float, added by lane 0 to a shared accumulator.
+__device__ __forceinline__ void warp_add(float v, float *dst) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(dst, v);
+}
+
+// Each lane takes one sample (lanes past the end contribute zeros); every
+// gradient term is summed over the warp before one shared atomic; the CTA's
+// sums go to grad with one global atomic per parameter.
+constexpr int kTrainThreads = 128;
+
+__global__ void __launch_bounds__(kTrainThreads)
+    k_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t N, float inv_n,
+                const float *prm, float *grad, double *loss) {
+    __shared__ float P[kMlpParams];
+    __shared__ float G[kMlpParams];
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+        P[i] = prm[i];
+        G[i] = 0.0f;
+    }
+    __syncthreads();
+    double lsum = 0.0;
+    const int64_t N_r = (N + 31) & ~31ll;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N_r;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = q < N;
+        const int64_t s = ok ? (idx ? idx[q] : q) : 0;
+        float x[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) x[i] = ok ? X[s * 6 + i] : 0.0f;
+        const float t = ok && y[s] ? 1.0f : 0.0f;
+        float a1[32], h1[32], a2[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            float acc = P[kMlpB1 + j];
+#pragma unroll
+            for (int i = 0; i < 6; i++) acc = fmaf(P[kMlpW1 + j * 6 + i], x[i], acc);
+            a1[j] = acc;
+            h1[j] = acc > 0.0f ? acc : 0.0f;
+        }
+        float z = P[kMlpB3];
+#pragma unroll 4
+        for (int j = 0; j < 32; j++) {
+            float acc = P[kMlpB2 + j];
+#pragma unroll
+            for (int i = 0; i < 32; i++) acc = fmaf(P[kMlpW2 + j * 32 + i], h1[i], acc);
+            a2[j] = acc;
+            z = fmaf(P[kMlpW3 + j], acc > 0.0f ? acc : 0.0f, z);
+        }
+        if (ok) lsum += (double)((z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z))) - t * z);
+        const float dz = ok ? (1.0f / (1.0f + expf(-z)) - t) * inv_n : 0.0f;
+        warp_add(dz, &G[kMlpB3]);
+        float d1[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) d1[i] = 0.0f;
+        for (int j = 0; j < 32; j++) {
+            const float h2 = a2[j] > 0.0f ? a2[j] : 0.0f;
+            warp_add(dz * h2, &G[kMlpW3 + j]);
+            const float d2 = a2[j] > 0.0f ? dz * P[kMlpW3 + j] : 0.0f;
+            warp_add(d2, &G[kMlpB2 + j]);
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                warp_add(d2 * h1[i], &G[kMlpW2 + j * 32 + i]);
+                d1[i] = fmaf(d2, P[kMlpW2 + j * 32 + i], d1[i]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const float dj = a1[j] > 0.0f ? d1[j] : 0.0f;
+            warp_add(dj, &G[kMlpB1 + j]);
+#pragma unroll
+            for (int i = 0; i < 6; i++) warp_add(dj * x[i], &G[kMlpW1 + j * 6 + i]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x)
+        if (G[i] != 0.0f) atomicAdd(&grad[i], G[i]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, d);
+    if ((threadIdx.x & 31) == 0 && lsum != 0.0) atomicAdd(loss, lsum * (double)inv_n);
+}
+
+void mlp_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t N,
+                   const float *prm, float *grad, double *d_loss, cudaStream_t s) {
+    if (N <= 0) return;
+    const int64_t blocks = std::min<int64_t>(ceil_div<int64_t>(N, kTrainThreads),
+                                             (int64_t)dev_info().sms * 4);
+    k_loss_grad<<<(unsigned)blocks, kTrainThreads, 0, s>>>(X, y, idx, N, 1.0f / (float)N, prm,
+                                                           grad, d_loss);
+    LAUNCHED();
+}
+
+__global__ void k_sgd(float *prm, const float *grad, float lr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x)
+        prm[i] -= lr * grad[i];
+}
+
+void mlp_sgd(float *prm, const float *grad, float lr, cudaStream_t s) {
+    k_sgd<<<ceil_div(kMlpParams, 256), 256, 0, s>>>(prm, grad, lr);
+    LAUNCHED();
+}
+
+}  // namespace sclap

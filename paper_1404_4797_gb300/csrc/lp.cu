@@ -178,6 +178,7 @@ struct LPArgs {
     unsigned long long *bhist; // [maxbig * kBins], zero between uses
     GridBar *bar;
     int32_t maxbig, maxtiles;
+    const uint8_t *active;     // learned refinement: rows visited this round (null: all)
 };
 
 // Bound of label L (U, L_max, or the run's L_max in batched runs).
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
             vv[j] = (int32_t)v;
             if (v < g.n) {
                 const int64_t d = g.xadj[v + 1] - g.xadj[v];
-                if (d > 0) {
+                if (d > 0 && (!a.active || a.active[v])) {
                     p_entries += (unsigned long long)d;
                     p_nodes++;
                     const uint32_t col = colour_of(a.seed, a.round, (int32_t)v, S);
@@ -2379,6 +2380,10 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     int64_t hmoves = 0;
     try {
         for (int r = 0; r < cfg.rounds; r++) {
+            bool full = true;
+            const uint8_t *act = nullptr;
+            if (cfg.before_round) full = cfg.before_round(r, &act);
+            a.active = act;
             a.round = r;
             a.moves = d_moves + r;
             CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + 3 * S) * sizeof(int32_t), s));
@@ -2459,7 +2464,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             CK(cudaStreamSynchronize(s));
             done = r + 1;
             if (moves_out) moves_out->push_back(hmoves);
-            if (hmoves == 0) break;
+            if (hmoves == 0 && full) break;
         }
     } catch (...) {
         cudaStreamSynchronize(side);

@@ -1,6 +1,7 @@
 // lp.cuh -- size-constrained label propagation on the GPU (both forms).
 #pragma once
 
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -17,6 +18,11 @@ struct LPConfig {
     const int32_t *cp;     // V-cycle constraint partition (clustering only) or null
     uint64_t seed;
     int32_t rounds, S;
+    // Optional, called on the LP stream before every round (learned
+    // refinement): sets *active (device flags per node, null = every node)
+    // and returns whether the round is a full one.  A run stops only after a
+    // full round without moves.
+    std::function<bool(int round, const uint8_t **active)> before_round;
 };
 
 // Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)
