@@ -228,6 +228,85 @@ def run_phase(args, cfg, S, I, g, n, m, dev):
     return 0
 
 
+def run_learned(args, cfg, S, I, g, n, m, dev):
+    """Learned active set (refinement gate): traces of plain refinement on
+    training seeds, SGD on them, the logit threshold at move recall >= 0.99 on
+    the training traces, then gated vs plain refinement on held-out seeds.
+    Start partitions: seeded hash partitions into k blocks."""
+    k = args.k
+    rounds, sub, eps = cfg["refine_rounds"], cfg["subrounds"], cfg["eps"]
+    S.set_validation(False)
+
+    def start(seed):
+        return I.rand_below(seed, 7, torch.arange(n, device=dev), k).to(torch.int32)
+
+    xs, ys = [], []
+    for seed in range(1, args.train_seeds + 1):
+        _, _, _, rd, _, tx, ty = S.sclap_refine_learned(g, k, eps, rounds, sub, seed, start(seed),
+                                                        trace=True)
+        xs.append(tx.reshape(-1, 6))
+        ys.append(ty.reshape(-1))
+    X, Y = torch.cat(xs), torch.cat(ys)
+    del xs, ys
+    if X.shape[0] > args.train_samples:  # uniform sample of the traces (with replacement)
+        sel = I.rand_below(3, 11, torch.arange(args.train_samples, device=dev), X.shape[0])
+        X, Y = X[sel].contiguous(), Y[sel].contiguous()
+    rng = torch.Generator().manual_seed(1)
+    p0 = (torch.randn(S.MLP_PARAMS, generator=rng) * 0.2).to(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    prm, loss = S.sclap_mlp_train(X, Y, p0, args.epochs, 4096, 0.5, 11)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    net = S.bf16_bits(prm)
+    z = S.sclap_mlp_score(X, net)
+    zm = torch.sort(z[Y.bool()]).values
+    z_min = float(zm[int(0.01 * zm.numel())]) if zm.numel() else 0.0
+    samples = int(X.shape[0])
+    del X, Y, z, zm
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()  # warm-up
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        out = fn()
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1), out
+
+    res = {"plain_ms": [], "learned_ms": [], "plain_cut": [], "learned_cut": [],
+           "visited_frac": [], "plain_rounds": [], "learned_rounds": []}
+    rows = None
+    for seed in range(17, 17 + args.eval_seeds):
+        ps = start(seed)
+        ms_p, out_p = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps))
+        ms_l, out_l = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps, net,
+                                                           z_min, 3))
+        if rows is None:
+            rows = out_p[4] / max(1, out_p[3])
+        res["plain_ms"].append(ms_p)
+        res["learned_ms"].append(ms_l)
+        res["plain_cut"].append(out_p[1])
+        res["learned_cut"].append(out_l[1])
+        res["plain_rounds"].append(out_p[3])
+        res["learned_rounds"].append(out_l[3])
+        res["visited_frac"].append(out_l[4] / max(1, out_p[4]))
+    mean = lambda v: sum(v) / len(v)
+    line = {"op": "learned", "scale": cfg["scale"], "n": n, "m": m, "k": k, "eps": eps,
+            "rounds": rounds, "train_seeds": args.train_seeds, "eval_seeds": args.eval_seeds,
+            "train_samples": samples, "train_epochs": args.epochs, "train_s": train_s,
+            "train_loss": loss, "z_min": z_min, "full_every": 3,
+            "plain_ms": mean(res["plain_ms"]), "learned_ms": mean(res["learned_ms"]),
+            "speedup": mean(res["plain_ms"]) / mean(res["learned_ms"]),
+            "visited_frac": mean(res["visited_frac"]),
+            "cut_ratio": mean(res["learned_cut"]) / mean(res["plain_cut"]),
+            "plain_cut": mean(res["plain_cut"]), "learned_cut": mean(res["learned_cut"]),
+            "plain_rounds": mean(res["plain_rounds"]), "learned_rounds": mean(res["learned_rounds"])}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,7 +316,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling)")
     ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
-    ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine"],
+    ap.add_argument("--k", type=int, default=32, help="blocks for --op learned")
+    ap.add_argument("--train-seeds", type=int, default=4, help="--op learned: trace seeds 1..T")
+    ap.add_argument("--eval-seeds", type=int, default=4, help="--op learned: seeds 17..")
+    ap.add_argument("--epochs", type=int, default=2, help="--op learned: SGD epochs")
+    ap.add_argument("--train-samples", type=int, default=4_000_000,
+                    help="--op learned: trace samples used for training")
+    ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine",
+                                                           "learned"],
                     help="time one SCLaP phase on the input graph instead (profiling aid)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
@@ -272,6 +358,8 @@ def main():
             torch.distributed.barrier()
 
     part = torch.empty(n, dtype=torch.int32, device=dev)
+    if args.op == "learned":
+        return run_learned(args, cfg, S, I, g, n, m, dev)
     if args.op != "multilevel":
         return run_phase(args, cfg, S, I, g, n, m, dev)
     for _ in range(args.warmup):
@@ -334,7 +422,8 @@ def main():
     per_launch_bytes = prof["propose_bytes"] / max(1, prof["propose_launches"])
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     tr = stored_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_propose (normal-degree nodes)",
+    roofline = {"bound": "hbm",
+                "kernel": "propose step (k_propose_small, k_propose, k_propose_huge per sub-round)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": tr.get("dram_bytes_per_launch") if tr else None,
