@@ -233,6 +233,7 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
     training seeds, SGD on them, the logit threshold at move recall >= 0.99 on
     the training traces, then gated vs plain refinement on held-out seeds.
     Start partitions: seeded hash partitions into k blocks."""
+    import torch
     k = args.k
     rounds, sub, eps = cfg["refine_rounds"], cfg["subrounds"], cfg["eps"]
     S.set_validation(False)
@@ -277,14 +278,11 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
 
     res = {"plain_ms": [], "learned_ms": [], "plain_cut": [], "learned_cut": [],
            "visited_frac": [], "plain_rounds": [], "learned_rounds": []}
-    rows = None
     for seed in range(17, 17 + args.eval_seeds):
         ps = start(seed)
         ms_p, out_p = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps))
         ms_l, out_l = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps, net,
                                                            z_min, 3))
-        if rows is None:
-            rows = out_p[4] / max(1, out_p[3])
         res["plain_ms"].append(ms_p)
         res["learned_ms"].append(ms_l)
         res["plain_cut"].append(out_p[1])
