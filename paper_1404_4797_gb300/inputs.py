@@ -198,6 +198,33 @@ def rmat(scale: int = 22, edge_factor: int = 16, a: float = 0.57, b: float = 0.1
     return g
 
 
+def population(count: int = 32, nmin: int = 2000, nmax: int = 200000, seed: int = 1,
+               device="cpu") -> list:
+    """Coarse-graph population: `count` Chung-Lu graphs (gamma 2.1, mean degree
+    8) with n log-uniform in [nmin, nmax], node weights uniform in 1..500 and
+    edge weights lognormal(mu = 3, sigma = 1.5) rounded and clamped to 1..1000
+    (Box-Muller from two counter-based uniforms keyed by the edge)."""
+    import math
+    graphs = []
+    for t in range(count):
+        u = float(rand_uniform(seed, 500 + t, torch.zeros(1, dtype=torch.int64))[0])
+        n = int(round(math.exp(math.log(nmin) + u * (math.log(nmax) - math.log(nmin)))))
+        base = chung_lu(n, 2.1, 8.0, seed=seed * 1000 + t, device=device)
+        src = torch.repeat_interleave(torch.arange(n, device=device),
+                                      base["xadj"][1:] - base["xadj"][:-1])
+        dst = base["adjncy"].to(torch.int64)
+        up = src < dst
+        a, b = src[up], dst[up]
+        key = a * n + b
+        u1 = rand_uniform(seed * 1000 + t, 600, key).clamp_min(1e-12)
+        u2 = rand_uniform(seed * 1000 + t, 601, key)
+        z = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+        w = torch.exp(3.0 + 1.5 * z).round().clamp(1, 1000).to(torch.int64)
+        c = 1 + rand_below(seed * 1000 + t, 602, torch.arange(n, device=device), 500)
+        graphs.append(csr_from_edges(n, a, b, w, c.to(torch.int32)))
+    return graphs
+
+
 def path_graph(n: int, weights=None) -> dict:
     u = torch.arange(n - 1)
     v = u + 1

@@ -283,3 +283,18 @@ def test_batched_runs_match_oracle():
         assert np.array_equal(gc.numpy(), wc) and np.array_equal(gm.numpy(), wm)
         for r in range(len(rg)):
             assert np.array_equal(got[r].cpu().numpy(), want[r]), (k, r)
+
+
+def test_population_batched_runs_match_oracle():
+    # the coarse-graph population generator (lognormal edge weights up to
+    # 1000, node weights up to 500), 8 graphs, 32 runs: graph (s - 1) mod 8
+    gens = I.population(8, 2000, 12000, seed=4)
+    gs = [I.to_numpy(g) for g in gens]
+    gd = [dev(g) for g in gens]
+    rg = [s % 8 for s in range(32)]
+    want, wc, wm = oracle.refine_batched(gs, 16, 0.03, 6, 4, 1, rg)
+    got, gc, gm = S.sclap_refine_batched(gd, 16, 0.03, 6, 4, 1, rg)
+    assert np.array_equal(gc.numpy(), wc) and np.array_equal(gm.numpy(), wm)
+    for r in range(len(rg)):
+        assert np.array_equal(got[r].cpu().numpy(), want[r]), r
+
