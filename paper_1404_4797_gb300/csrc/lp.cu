@@ -417,7 +417,7 @@ struct PropSm {
     NodeSm nd;
     int64_t W[kDenseMaxK];
     unsigned long long red[RS::kNT / 32];
-    int64_t li, pieces, deg;
+    int64_t li;
     int ndl, item, flag;
 };
 
@@ -566,35 +566,26 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE, RS> &sm, int k, cons
                               int npieces, int32_t *next) {
     constexpr bool DENSE = MODE == kRefineDense;
     constexpr int NT = RS::kNT;
-    // work items are fetched one row ahead: the fetch of the next item
-    // overlaps the current row's entry loop
-    if (threadIdx.x == 0) {
-        const int p = atomicAdd(next, 1);
-        sm.item = p;
-        if (p < npieces) sm.li = plist[p];
-    }
     while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int p = atomicAdd(next, 1);
+            sm.item = p;
+            if (p < npieces) sm.li = plist[p];
+        }
         __syncthreads();
         const int p = sm.item;
         if (p >= npieces) break;
-        const int64_t liv = sm.li;
-        const int64_t li = liv >> 20;
-        const int64_t pi = liv & ((1 << 20) - 1);
+        const int64_t li = sm.li >> 20;
+        const int64_t pi = sm.li & ((1 << 20) - 1);
+        const int32_t v = a.Lnodes[li];
+        const int64_t pieces = a.Lpre[li + 1] - a.Lpre[li];
         if (threadIdx.x == 0) {
-            const int32_t vv = a.Lnodes[li];
-            sm.pieces = a.Lpre[li + 1] - a.Lpre[li];
-            sm.deg = load_node<MODE>(a, sm.W, sm.nd, 0, vv);
+            load_node<MODE>(a, sm.W, sm.nd, 0, v);
             sm.ndl = 0;
         }
-        __syncthreads();  // every thread has read this row's item
-        if (threadIdx.x == NT - 32) {
-            const int p2 = atomicAdd(next, 1);
-            sm.item = p2;
-            if (p2 < npieces) sm.li = plist[p2];
-        }
-        const int32_t v = sm.nd.v[0];
-        const int64_t pieces = sm.pieces;
-        const int64_t deg = sm.deg;
+        __syncthreads();
+        const int64_t deg = a.g.xadj[v + 1] - a.g.xadj[v];
         const int64_t e0 = pi * kChunk;  // pieces are kChunk entries (RS::kCh >= any row given here)
         const int64_t e1 = min64(deg, e0 + kChunk);
         const int64_t rs = sm.nd.rs[0];
