@@ -4,34 +4,36 @@
 // refinement form adds the overloaded-block rule (Sec. III.A).
 //
 // Per round r:
-//   k_build_wl    nodes with 1..kMedDeg neighbours go to bucket
-//                 5*colour + class (classes: degree <= 4, 8, 16, 32, and
-//                 33..kMedDeg), colour = (h(v,r) >> 32) mod S.  Nodes of
-//                 larger degree are enumerated once per call.
-// Per sub-round j, one fused, dynamically scheduled propose kernel:
-//   large nodes   rows cut into kChunk-entry pieces spread over CTAs; each
-//                 piece aggregates omega(v, L) in a shared-memory table; a
-//                 single-piece row is finished in place, a longer one is
-//                 merged into its own global table and the CTA completing
-//                 the last piece selects the best label;
-//   medium nodes  one warp per row with a warp-private shared-memory
-//                 linear-probing table (the paper's Sec. IV.A choice of
-//                 linear probing), no block-wide barriers;
-//   small nodes   G lanes per node (G = 4, 8, 16, 32; at most G entries):
+//   k_build_wl    colour = (h(v,r) >> 32) mod S.  Nodes with 1..kMedDeg
+//                 neighbours go to bucket 5*colour + class (degree <= 4, 8,
+//                 16, 32, 33..kMedDeg); larger rows go to per-colour lists:
+//                 257..kMidDeg, kMidDeg+1..kChunk (and kChunk-entry pieces of
+//                 longer rows), kChunk+1..kHugeDeg in the hash modes.  The
+//                 learned gate (learned.cu) can leave nodes out of a round.
+// Per sub-round j, the propose step runs on three streams:
+//   k_propose_small  small rows: G lanes per node (G = 4, 8, 16, 32),
 //                 __match_any_sync on (node, label) and __reduce_add_sync
-//                 give omega(v, L) in registers, shuffles pick the best.
+//                 give omega(v, L) in registers; medium rows: one warp per
+//                 row with a warp-private linear-probing table (the paper's
+//                 Sec. IV.A choice of linear probing) or a k-array.
+//   k_propose<MODE, RowShape>  one CTA per row (128 threads for rows up to
+//                 kMidDeg, 256 for the rest) with a shared-memory table of
+//                 32-bit labels; pieces of longer rows merge into a global
+//                 table (hash) or k-array (dense) and are finished by
+//                 k_hub_cand / k_hub_tie / k_hub_emit or the last piece.
+//   k_propose_huge  hash modes, rows up to kHugeDeg: an 8-CTA cluster per
+//                 row, its table spread over the CTAs' shared memory.
 //   The best eligible label maximises (omega << 32 | ~tie); exact ties on
-//   that key go to the smallest label.  The dense variant (k <= 64 blocks)
-//   replaces the hash table by per-node k-arrays.
+//   that key go to the smallest label.
 // Then arbitration:
 //   k_src         refinement only: departures from overloaded blocks.
 //   k_classify    uncontested targets (sum of proposed weight <= capacity)
 //                 are applied at once; contested targets get a segment.
 //   k_scatter     contested proposals are written to their target's segment.
-//   k_arbitrate   per contested target: weighted radix select, over the bits
-//                 where the segment's keys differ, of the first key in (gain
-//                 desc, id asc) order whose inclusive prefix exceeds the
-//                 capacity; admitted moves are applied.
+//   k_arbitrate   cooperative launch; per contested target a weighted radix
+//                 select of the first key in (gain desc, id asc) order whose
+//                 inclusive prefix exceeds the capacity (a warp, a CTA, or
+//                 the whole grid by segment size); admitted moves are applied.
 //   k_reset_targets clears the per-target accumulators.
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
