@@ -208,15 +208,6 @@ __device__ __forceinline__ unsigned long long cand_key(int32_t w, uint64_t h, in
     return ((unsigned long long)(uint32_t)w << 32) | (uint32_t)~tie_of(h, L);
 }
 
-// Applies one admitted move (Sec. III.A: the node joins the target; weights
-// move with it).
-__device__ __forceinline__ void apply_move(const LPArgs &a, int32_t v, int32_t T, int32_t own,
-                                           int32_t c) {
-    a.lab[v] = T;
-    atomicAdd((unsigned long long *)&a.W[T], (unsigned long long)(int64_t)c);
-    atomicAdd((unsigned long long *)&a.W[own], (unsigned long long)(-(int64_t)c));
-}
-
 // Weight deltas of applied moves: with few labels (refinement) they collect in
 // shared memory and are flushed once per CTA; otherwise moves into and out of
 // the same label are merged per warp (labelled partitions) before the global
@@ -997,14 +988,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_propose_small(LPArgs a, int k) 
 }
 
 // ---------------------------------------------------------------- arbitration
-
-// Sum of a non-negative 32-bit value over the lanes of `peers` as int64 (two
-// 16-bit halves, so the warp reduction cannot overflow).
-__device__ __forceinline__ int64_t peer_sum64(unsigned peers, int32_t c) {
-    const unsigned lo = __reduce_add_sync(peers, (unsigned)c & 0xffffu);
-    const unsigned hi = __reduce_add_sync(peers, (unsigned)c >> 16);
-    return ((int64_t)hi << 16) + (int64_t)lo;
-}
 
 // Digit windows of the weighted radix select.  Keys are (order-flipped gain
 // << 32) | node id.  The first window starts at `top`, the highest bit where
