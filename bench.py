@@ -109,6 +109,22 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest value of x over the ranks (x itself on one rank)."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gteps(m: int, ms: float, ws: int) -> float:
+    """Whole-job G edges/s of ws replicas that each partition m edges, timed
+    by the slowest replica."""
+    return ws * m / (ms / 1e3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -421,11 +437,8 @@ def main():
     prof = S.prof_read()
     S.prof_enable(False)
     launches = (prof["kernel_launches"] - launches0) // max(1, args.steps)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * m / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, ws, dev)
+    value = job_gteps(m, ms, ws)
 
     # ---- end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -443,11 +456,8 @@ def main():
             _, st_e = S.partition_multilevel(gh, params, part_out=ph)
         torch.cuda.synchronize(dev)
         e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-        if ws > 1:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": ws * m / (e2e_ms / 1e3) / 1e9, "unit": "GTEPS", "ms_per_step": e2e_ms,
+        e2e_ms = max_over_ranks(e2e_ms, ws, dev)
+        e2e = {"value": job_gteps(m, e2e_ms, ws), "unit": "GTEPS", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- roofline of the dominant kernel (neighbour aggregation / propose)
