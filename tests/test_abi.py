@@ -19,7 +19,9 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("sclap_cluster", "sclap_refine", "contract_graph", "project_partition",
-                 "partition_multilevel", "sclap_graph_free", "sclap_strerror"):
+                 "partition_multilevel", "sclap_graph_free", "sclap_strerror",
+                 "sclap_refine_batched", "sclap_refine_learned", "sclap_mlp_score",
+                 "sclap_mlp_loss_grad", "sclap_mlp_train", "sclap_cut_noalloc"):
         assert must in names
 
 
