@@ -104,6 +104,7 @@ def lib():
             L.or_initial_partition.argtypes = g + [C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                                                    C.c_int32, C.c_uint64, _P32, _P64, _P64, _P32]
             L.or_multilevel.argtypes = g + [C.POINTER(MLParams), _P32, C.POINTER(MLStats)]
+            L.or_vcycle.argtypes = g + [C.POINTER(MLParams), _P32, C.POINTER(MLStats)]
             _PP64 = C.POINTER(_P64)
             _PP32 = C.POINTER(_P32)
             L.or_refine_batched.argtypes = [C.c_int32, _P64, _PP64, _PP32, _PP32, _PP32,
@@ -304,6 +305,26 @@ def default_params(k, eps=0.03, seed=1, **kw):
              max_levels=32, init_seeds=8, init_rounds=6, seed=seed)
     p.update(kw)
     return p
+
+
+def _ml_stats(st):
+    L = st.levels
+    return dict(levels=L, n=list(st.n[:L]), nnz=list(st.nnz[:L]),
+                cluster_rounds_done=list(st.cluster_rounds_done[:L]),
+                refine_rounds_done=list(st.refine_rounds_done[:L]), U=st.U, lmax=st.lmax,
+                init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
+                cut=st.cut, maxbw=st.maxbw)
+
+
+def vcycle(g, params: dict, part):
+    """One V-cycle seeded by `part`.  Returns (part, stats dict)."""
+    keep, a = _graph_args(g)
+    p = np.array(part, dtype=np.int32, copy=True)
+    mp = MLParams(**params)
+    st = MLStats()
+    rc = lib().or_vcycle(*a, C.byref(mp), _p32(p), C.byref(st))
+    _check(rc, "vcycle")
+    return p, _ml_stats(st)
 
 
 def multilevel(g, params: dict):

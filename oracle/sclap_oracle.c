@@ -713,9 +713,41 @@ static uint64_t level_seed(uint64_t seed, int32_t l)
     return or_mix64(seed ^ (0x9E3779B97F4A7C15ULL * (uint64_t)(l + 1)));
 }
 
+static int multilevel_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                           const int32_t *adjwgt, const int32_t *vwgt, const or_ml_params *p,
+                           const int32_t *seed_part, int32_t *part_out, or_ml_stats *st);
+
 int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt,
                   const or_ml_params *p, int32_t *part_out, or_ml_stats *st)
+{
+    return multilevel_impl(n, xadj, adjncy, adjwgt, vwgt, p, NULL, part_out, st);
+}
+
+/* One iterated V-cycle (Sec. IV.E, the cycles of the fast and minimal
+ * presets): the multilevel scheme seeded by the partition part_inout.  Every
+ * clustering is restricted to the blocks of the current partition (the
+ * constraint of Sec. III.A's coarsening), each coarse node inherits its
+ * members' block, and the coarsest graph's inherited partition, refined
+ * like every level, is the initial partition (init_best = -1; init_cut /
+ * init_maxbw describe it after refinement).  part_inout: k blocks in, the
+ * new partition out. */
+int or_vcycle(int64_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+              const int32_t *vwgt, const or_ml_params *p, int32_t *part_inout, or_ml_stats *st)
+{
+    for (int64_t v = 0; v < n; v++)
+        if (part_inout[v] < 0 || part_inout[v] >= p->k) return OR_EINVAL;
+    int32_t *seed = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    if (!seed) return OR_ENOMEM;
+    memcpy(seed, part_inout, sizeof(int32_t) * (size_t)n);
+    int rc = multilevel_impl(n, xadj, adjncy, adjwgt, vwgt, p, seed, part_inout, st);
+    free(seed);
+    return rc;
+}
+
+static int multilevel_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                           const int32_t *adjwgt, const int32_t *vwgt, const or_ml_params *p,
+                           const int32_t *seed_part, int32_t *part_out, or_ml_stats *st)
 {
     if (p->k < 1 || p->eps < 0 || p->cluster_rounds < 0 || p->refine_rounds < 0 ||
         p->subrounds < 1 || p->init_seeds < 1 || p->init_rounds < 0)
@@ -729,11 +761,18 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (maxl > OR_MAX_LEVELS) maxl = OR_MAX_LEVELS;
 
     level lv[OR_MAX_LEVELS];
+    int32_t *cpl[OR_MAX_LEVELS];  /* V-cycle: the seed partition on every level */
     memset(lv, 0, sizeof(lv));
+    memset(cpl, 0, sizeof(cpl));
     lv[0].n = n; lv[0].xadj = (int64_t *)xadj; lv[0].adjncy = (int32_t *)adjncy;
     lv[0].adjwgt = (int32_t *)adjwgt; lv[0].vwgt = (int32_t *)vwgt;
     int32_t L = 0, rc = OR_OK;
     memset(st, 0, sizeof(*st));
+    if (seed_part) {
+        cpl[0] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+        if (!cpl[0]) return OR_ENOMEM;
+        memcpy(cpl[0], seed_part, sizeof(int32_t) * (size_t)n);
+    }
 
     /* coarsening: l rounds of clustering, then contraction, recursively */
     while (lv[L].n >= p->n_stop && L + 1 < maxl) {
@@ -743,7 +782,7 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         if (!lab || !g->f2c) { free(lab); rc = OR_ENOMEM; goto out; }
         int32_t rd = 0;
         rc = or_cluster(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, U, p->cluster_rounds,
-                        p->subrounds, level_seed(p->seed, L), NULL, lab, &rd, NULL);
+                        p->subrounds, level_seed(p->seed, L), cpl[L], lab, &rd, NULL);
         if (rc) { free(lab); goto out; }
         st->cluster_rounds_done[L] = rd;
         level *c = &lv[L + 1];
@@ -759,6 +798,11 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
             free(g->f2c); g->f2c = NULL;
             break;
         }
+        if (seed_part) {  /* a cluster lies in one block: the coarse node inherits it */
+            cpl[L + 1] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(c->n ? c->n : 1));
+            if (!cpl[L + 1]) { rc = OR_ENOMEM; goto out; }
+            for (int64_t v = 0; v < g->n; v++) cpl[L + 1][g->f2c[v]] = cpl[L][v];
+        }
         L++;
         if (20 * c->n > 19 * g->n) break;          /* stalled (< 5% shrink) */
     }
@@ -771,11 +815,28 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         int64_t *mx = (int64_t *)malloc(sizeof(int64_t) * (size_t)p->init_seeds);
         if (!cp || !cuts || !mx) { free(cp); free(cuts); free(mx); rc = OR_ENOMEM; goto out; }
         int32_t best = 0;
-        rc = or_initial_partition(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, p->k, lmax,
-                                  p->init_seeds, p->init_rounds, p->subrounds,
-                                  level_seed(p->seed, L), cp, cuts, mx, &best);
-        if (rc) { free(cp); free(cuts); free(mx); goto out; }
-        st->init_best = best; st->init_cut = cuts[best]; st->init_maxbw = mx[best];
+        if (seed_part) {
+            memcpy(cp, cpl[L], sizeof(int32_t) * (size_t)g->n);
+            int32_t rd = 0;
+            rc = or_refine_bound(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, p->k, lmax,
+                                 p->init_rounds, p->subrounds, level_seed(p->seed, L), cp, &rd,
+                                 NULL);
+            if (rc) { free(cp); free(cuts); free(mx); goto out; }
+            int64_t *bw = (int64_t *)calloc((size_t)p->k, sizeof(int64_t));
+            if (!bw) { free(cp); free(cuts); free(mx); rc = OR_ENOMEM; goto out; }
+            or_block_weights(g->n, g->vwgt, cp, p->k, bw);
+            st->init_best = -1;
+            st->init_cut = or_cut(g->n, g->xadj, g->adjncy, g->adjwgt, cp);
+            st->init_maxbw = 0;
+            for (int32_t b = 0; b < p->k; b++) if (bw[b] > st->init_maxbw) st->init_maxbw = bw[b];
+            free(bw);
+        } else {
+            rc = or_initial_partition(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, p->k, lmax,
+                                      p->init_seeds, p->init_rounds, p->subrounds,
+                                      level_seed(p->seed, L), cp, cuts, mx, &best);
+            if (rc) { free(cp); free(cuts); free(mx); goto out; }
+            st->init_best = best; st->init_cut = cuts[best]; st->init_maxbw = mx[best];
+        }
         free(cuts); free(mx);
         /* uncoarsening: project, then r rounds of refinement per level */
         int32_t *cur = cp;
@@ -810,6 +871,7 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     }
 out:
     for (int32_t l = 0; l < OR_MAX_LEVELS; l++) {
+        free(cpl[l]);
         free(lv[l].f2c);
         if (lv[l].own) { free(lv[l].xadj); free(lv[l].adjncy); free(lv[l].adjwgt); free(lv[l].vwgt); }
     }

@@ -113,6 +113,10 @@ int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt,
                   const or_ml_params *p, int32_t *part_out, or_ml_stats *st);
 
+int or_vcycle(int64_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
+              const int32_t *vwgt, const or_ml_params *p, int32_t *part_inout,
+              or_ml_stats *st);
+
 /* learned active set (refinement gate; not in the paper) */
 #define OR_MLP_NPARAM 1313
 #define OR_MLP_W1 0     /* [32][6] */
