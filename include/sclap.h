@@ -286,6 +286,22 @@ int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t ro
 int partition_multilevel(const sclap_graph *g, const sclap_ml_params *p, int32_t *part_out,
                          sclap_ml_stats *stats_out, void *stream);
 
+/* One iterated V-cycle (Sec. IV.E: the fast preset runs two cycles, the
+ * minimal one a single cycle): the multilevel scheme above seeded by the
+ * partition part_inout (k blocks).  Every clustering is restricted to the
+ * blocks of that partition (Sec. III.A's constraint; nodes without
+ * neighbours are packed per block), each coarse node inherits its members'
+ * block, and the coarsest graph's inherited partition, refined with
+ * init_rounds rounds, is the initial partition (stats: init_best = -1,
+ * init_cut / init_maxbw of that partition after refinement).  With zero
+ * refinement rounds the call returns its input.
+ *   part_inout  int32[n], host or device (detected): in, the seed partition;
+ *               out, the new one
+ * EINVAL when a block id is outside 0..k-1; other errors as
+ * partition_multilevel. */
+int sclap_vcycle(const sclap_graph *g, const sclap_ml_params *p, int32_t *part_inout,
+                 sclap_ml_stats *stats_out, void *stream);
+
 void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed);
 
 /* Copies a library-owned graph into caller-allocated device arrays of sizes

@@ -99,6 +99,8 @@ _SIGS = {
                                        _VP]),
     "partition_multilevel": (C.c_int, [C.POINTER(Graph), C.POINTER(MLParams), _VP,
                                        C.POINTER(MLStats), _VP]),
+    "sclap_vcycle": (C.c_int, [C.POINTER(Graph), C.POINTER(MLParams), _VP, C.POINTER(MLStats),
+                               _VP]),
     "sclap_graph_copy_out": (C.c_int, [C.POINTER(GraphOwned), _VP, _VP, _VP, _VP, _VP]),
     "sclap_graph_free": (None, [C.POINTER(GraphOwned)]),
     "sclap_refine_learned": (C.c_int, [C.POINTER(Graph), C.c_int32, C.c_double, C.c_int32,
@@ -422,6 +424,24 @@ def partition_multilevel(g: dict, params: dict, part_out: torch.Tensor | None = 
                  init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
                  cut=st.cut, maxbw=st.maxbw)
     return part_out, stats
+
+
+def sclap_vcycle(g: dict, params: dict, part: torch.Tensor, stream=None):
+    """One iterated V-cycle seeded by `part` (Sec. IV.E); works on a copy.
+    Returns (part, stats dict)."""
+    p = part.to(torch.int32).clone()
+    mp = MLParams(**params)
+    st = MLStats()
+    gg = _graph(g)
+    _check(lib().sclap_vcycle(C.byref(gg), C.byref(mp), _ptr(p), C.byref(st), _stream(stream)),
+           "sclap_vcycle")
+    L = st.levels
+    stats = dict(levels=L, n=list(st.n[:L]), nnz=list(st.nnz[:L]),
+                 cluster_rounds_done=list(st.cluster_rounds_done[:L]),
+                 refine_rounds_done=list(st.refine_rounds_done[:L]), U=st.U, lmax=st.lmax,
+                 init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
+                 cut=st.cut, maxbw=st.maxbw)
+    return p, stats
 
 
 def prof_enable(on: bool = True):

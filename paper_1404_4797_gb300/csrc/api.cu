@@ -838,8 +838,23 @@ int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t ro
     });
 }
 
-int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_t *part_out,
-                         sclap_ml_stats *st_out, void *stream) {
+namespace {
+
+// Coarse node c inherits the block of its members (all members of a
+// constrained cluster share one block).
+__global__ void k_inherit(int64_t n, const int32_t *f2c, const int32_t *fine, int32_t *coarse) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        coarse[f2c[v]] = fine[v];
+}
+
+}  // namespace
+
+// The multilevel scheme; with seed_part (host or device int32[n], k blocks)
+// one V-cycle seeded by it.
+static int multilevel_call(const sclap_graph *gp, const sclap_ml_params *p,
+                           const int32_t *seed_part, int32_t *part_out, sclap_ml_stats *st_out,
+                           void *stream) {
     return guarded([&] {
         if (!gp || !p || (!part_out && gp->n > 0)) fail(SCLAP_EINVAL, "null");
         if (p->k < 1 || !(p->eps >= 0) || p->cluster_rounds < 0 || p->refine_rounds < 0 ||
@@ -877,7 +892,16 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
         sclap_ml_stats st;
         std::memset(&st, 0, sizeof(st));
         std::vector<DGraph> G{g0};
-        std::vector<int32_t *> F;  // f2c per level
+        std::vector<int32_t *> F;   // f2c per level
+        std::vector<int32_t *> CP;  // V-cycle: the seed partition on every level
+        if (seed_part) {
+            int32_t *cp0 = top.get<int32_t>(n ? n : 1);
+            CK(cudaMemcpyAsync(cp0, seed_part, n * sizeof(int32_t),
+                               is_device_ptr(seed_part) ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyHostToDevice, s));
+            if (!in_range(n, cp0, p->k, top)) fail(SCLAP_EINVAL, "part out of range");
+            CP.push_back(cp0);
+        }
         int L = 0;
         while (G[L].n >= p->n_stop && L + 1 < maxl && G[L].n > 0) {
             const DGraph &g = G[L];
@@ -892,15 +916,22 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
             cfg.seed = level_seed(p->seed, L);
             cfg.rounds = p->cluster_rounds;
             cfg.S = p->subrounds;
+            cfg.cp = seed_part ? CP[L] : nullptr;
             int rd = 0;
             if (cfg.rounds > 0) rd = lp_run(cfg, tmp, nullptr, nullptr);
             else identity_labels(g.n, lab, s);
-            pack_isolated(g, nullptr, U, lab, tmp);
+            pack_isolated(g, cfg.cp, U, lab, tmp);
             st.cluster_rounds_done[L] = rd;
             int32_t *f2c = top.get<int32_t>(g.n);
             CoarseGraph cg;
             contract_impl(g, lab, f2c, &cg, &top, tmp);
             if (cg.n == g.n) break;  // no shrink: the level is dropped
+            if (seed_part) {
+                int32_t *cpc = top.get<int32_t>(cg.n ? cg.n : 1);
+                k_inherit<<<dev_info().sms * 4, 256, 0, s>>>(g.n, f2c, CP[L], cpc);
+                LAUNCHED();
+                CP.push_back(cpc);
+            }
             F.push_back(f2c);
             DGraph c{cg.n, cg.nnz, cg.xadj, cg.adjncy, cg.adjwgt, cg.vwgt};
             G.push_back(c);
@@ -908,12 +939,37 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
             if (20 * G[L].n > 19 * G[L - 1].n) break;  // stalled (< 5% shrink)
         }
         // initial partition of the coarsest graph
-        int32_t *cur = top.get<int32_t>(G[L].n);
-        InitResult ir = initial_impl(G[L], p->k, lmax, p->init_seeds, p->init_rounds, p->subrounds,
-                                     level_seed(p->seed, L), cur, top);
-        st.init_best = ir.best;
-        st.init_cut = ir.cuts.empty() ? 0 : ir.cuts[ir.best];
-        st.init_maxbw = ir.maxbw.empty() ? 0 : ir.maxbw[ir.best];
+        int32_t *cur = top.get<int32_t>(G[L].n ? G[L].n : 1);
+        if (seed_part) {  // the inherited partition, refined like every level
+            CK(cudaMemcpyAsync(cur, CP[L], G[L].n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            Scratch tmp(s);
+            LPConfig cfg{};
+            cfg.g = G[L];
+            cfg.lab = cur;
+            cfg.nW = p->k;
+            cfg.B = lmax;
+            cfg.refine = true;
+            cfg.seed = level_seed(p->seed, L);
+            cfg.rounds = p->init_rounds;
+            cfg.S = p->subrounds;
+            if (cfg.rounds > 0) lp_run(cfg, tmp, nullptr, nullptr);
+            int64_t *d_c = tmp.get<int64_t>(1);
+            int64_t *d_b = tmp.get<int64_t>(p->k);
+            cut_impl(G[L], cur, p->k, 1, nullptr, d_c, d_b, tmp);
+            std::vector<int64_t> cbw(p->k);
+            CK(cudaMemcpyAsync(&st.init_cut, d_c, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(cbw.data(), d_b, p->k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            st.init_best = -1;
+            st.init_maxbw = 0;
+            for (int64_t x : cbw) st.init_maxbw = std::max(st.init_maxbw, x);
+        } else {
+            InitResult ir = initial_impl(G[L], p->k, lmax, p->init_seeds, p->init_rounds,
+                                         p->subrounds, level_seed(p->seed, L), cur, top);
+            st.init_best = ir.best;
+            st.init_cut = ir.cuts.empty() ? 0 : ir.cuts[ir.best];
+            st.init_maxbw = ir.maxbw.empty() ? 0 : ir.maxbw[ir.best];
+        }
         // uncoarsening: projection and r rounds of refinement per level
         for (int l = L - 1; l >= 0; l--) {
             int32_t *fp = top.get<int32_t>(G[l].n);
@@ -951,6 +1007,17 @@ int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_
         st.lmax = lmax;
         if (st_out) *st_out = st;
     });
+}
+
+int partition_multilevel(const sclap_graph *gp, const sclap_ml_params *p, int32_t *part_out,
+                         sclap_ml_stats *st_out, void *stream) {
+    return multilevel_call(gp, p, nullptr, part_out, st_out, stream);
+}
+
+int sclap_vcycle(const sclap_graph *gp, const sclap_ml_params *p, int32_t *part_inout,
+                 sclap_ml_stats *st_out, void *stream) {
+    if (!gp || !p || (!part_inout && gp->n > 0)) return SCLAP_EINVAL;
+    return multilevel_call(gp, p, part_inout, part_inout, st_out, stream);
 }
 
 // ---------------------------------------------------------------- profiling

@@ -298,3 +298,22 @@ def test_population_batched_runs_match_oracle():
     for r in range(len(rg)):
         assert np.array_equal(got[r].cpu().numpy(), want[r]), r
 
+
+@pytest.mark.parametrize("name", ["chunglu2k", "weighted", "sparse", "rmat14"])
+def test_vcycle_matches_oracle(name):
+    g = GRAPHS[name]()
+    gn = I.to_numpy(g)
+    k = 8
+    params = oracle.default_params(k, 0.03, 7)
+    params.update(n_stop=200)
+    p0, _ = oracle.multilevel(gn, params)
+    vparams = dict(params, seed=8)
+    want, ws = oracle.vcycle(gn, vparams, p0)
+    got, st = S.sclap_vcycle(dev(g), vparams, torch.from_numpy(p0).cuda())
+    assert st == ws
+    assert np.array_equal(got.cpu().numpy(), want)
+    # no refinement anywhere: the cycle returns its input
+    still, st0 = S.sclap_vcycle(dev(g), dict(vparams, refine_rounds=0, init_rounds=0),
+                                torch.from_numpy(p0).cuda())
+    assert np.array_equal(still.cpu().numpy(), p0) and st0["init_best"] == -1
+
