@@ -321,6 +321,34 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
     return 0
 
 
+def run_vcycle(args, cfg, S, I, g, n, m, dev):
+    """Iterated V-cycles (Sec. IV.E): the multilevel partition, then one
+    V-cycle seeded by it; time of each and the cut after each."""
+    import torch
+    params = params_for(cfg)
+    S.set_validation(False)
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        out = fn()
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1), out
+
+    for _ in range(args.warmup):
+        p0, _ = S.partition_multilevel(g, params)
+        S.sclap_vcycle(g, dict(params, seed=cfg["seed"] + 1), p0)
+    ms0, (p0, st0) = timed(lambda: S.partition_multilevel(g, params))
+    ms1, (p1, st1) = timed(lambda: S.sclap_vcycle(g, dict(params, seed=cfg["seed"] + 1), p0))
+    line = {"op": "vcycle", "scale": cfg["scale"], "n": n, "m": m, "k": cfg["k"],
+            "multilevel_ms": ms0, "vcycle_ms": ms1, "cut_multilevel": st0["cut"],
+            "cut_after_vcycle": st1["cut"], "maxbw_after_vcycle": st1["maxbw"],
+            "lmax": st1["lmax"], "vcycle_levels": st1["n"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args, S, I, dev):
     """Batched population (the stand-in for the paper's evolutionary initial
     partitioner): 32 coarse graphs, 256 seeded runs (graph (s - 1) mod 32), LPT
@@ -371,7 +399,7 @@ def main():
     ap.add_argument("--train-samples", type=int, default=4_000_000,
                     help="--op learned: trace samples used for training")
     ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine",
-                                                           "learned", "batched"],
+                                                           "learned", "batched", "vcycle"],
                     help="time one SCLaP phase on the input graph instead (profiling aid)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
@@ -410,6 +438,8 @@ def main():
     part = torch.empty(n, dtype=torch.int32, device=dev)
     if args.op == "learned":
         return run_learned(args, cfg, S, I, g, n, m, dev)
+    if args.op == "vcycle":
+        return run_vcycle(args, cfg, S, I, g, n, m, dev)
     if args.op != "multilevel":
         return run_phase(args, cfg, S, I, g, n, m, dev)
     for _ in range(args.warmup):
