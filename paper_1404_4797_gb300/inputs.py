@@ -112,12 +112,13 @@ def csr_from_edges(n: int, u: torch.Tensor, v: torch.Tensor, w: torch.Tensor | N
             "adjwgt": ww.to(torch.int32).contiguous(), "vwgt": vwgt.to(torch.int32).contiguous()}
 
 
-def _chung_lu_pairs(n, gamma, mean_deg, seed, stream0, m_target, device, w=None):
+def _chung_lu_pairs(n, gamma, mean_deg, seed, stream0, m_target, device, w=None, dmax=None):
     """Sample endpoint pairs with P(endpoint = i) proportional to the expected
     degree w_i ~ (i + i0)^(-1/(gamma-1)); i0 is chosen so that the largest expected
-    degree is about sqrt(n * mean_deg)."""
+    degree is about dmax (default sqrt(n * mean_deg))."""
     beta = 1.0 / (gamma - 1.0)
-    dmax = math.sqrt(n * mean_deg)
+    if dmax is None:
+        dmax = math.sqrt(n * mean_deg)
     idx = torch.arange(n, dtype=torch.float64, device=device)
     # choose i0 with (i0)^-beta / mean((i+i0)^-beta) ~= dmax / mean_deg
     lo, hi = 0.0, float(n)
@@ -196,6 +197,28 @@ def rmat(scale: int = 22, edge_factor: int = 16, a: float = 0.57, b: float = 0.1
     del key
     g = csr_from_edges(n, u, v)
     return g
+
+
+def web_graph(n: int = 1 << 26, gamma: float = 2.0, mean_deg: float = 32.0,
+              dmax: float = float(1 << 20), long_frac: float = 0.05, seed: int = 1,
+              device="cpu") -> dict:
+    """Web-like graph: Chung-Lu edges (exponent gamma, largest expected degree
+    about dmax) for (1 - long_frac) of n * mean_deg / 2 undirected edges plus
+    long_frac of them between uniform random endpoints; ids permuted, unit
+    weights, duplicates merged."""
+    m = int(n * mean_deg / 2)
+    m_long = int(m * long_frac)
+    key = _chung_lu_pairs(n, gamma, mean_deg, seed, 30, m - m_long, device, dmax=dmax)
+    s = torch.arange(m_long, dtype=torch.int64, device=device)
+    la = rand_below(seed, 40, s, n)
+    lb = rand_below(seed, 41, s, n)
+    keep = la != lb
+    la, lb = la[keep], lb[keep]
+    key = torch.unique(torch.cat([key, torch.minimum(la, lb) * n + torch.maximum(la, lb)]))
+    a, b = key // n, key % n
+    del key, la, lb, s
+    perm = permutation(n, seed, 42, device)
+    return csr_from_edges(n, perm[a], perm[b])
 
 
 def population(count: int = 32, nmin: int = 2000, nmax: int = 200000, seed: int = 1,

@@ -444,3 +444,18 @@ def test_initial_partition_is_the_best_of_batched_runs():
     parts, bc, bm = oracle.refine_batched([g], k, 0.03, 4, 4, 21, [0] * P)
     assert list(cuts) == list(bc) and list(mx) == list(bm)
     assert np.array_equal(part, parts[best])
+
+
+def test_input_generators_web_graph_and_population_shapes():
+    # seeded input generators: symmetric CSR, weight ranges, long-range share
+    g = I.to_numpy(I.web_graph(1 << 12, 2.0, 16.0, dmax=800.0, long_frac=0.05, seed=2))
+    n = g["vwgt"].size
+    assert n == 4096 and oracle.validate(g) == oracle.OK
+    deg = np.diff(g["xadj"])
+    assert deg.max() > 8 * deg.mean()               # power-law hubs
+    assert abs(g["adjncy"].size / 2 / (n * 16 / 2) - 1) < 0.1
+    pop = [I.to_numpy(x) for x in I.population(3, 2000, 4000, seed=5)]
+    for gp in pop:
+        assert 2000 <= gp["vwgt"].size <= 4000 and oracle.validate(gp) == oracle.OK
+        assert gp["vwgt"].min() >= 1 and gp["vwgt"].max() <= 500
+        assert gp["adjwgt"].min() >= 1 and gp["adjwgt"].max() <= 1000
