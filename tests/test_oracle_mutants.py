@@ -40,6 +40,55 @@ MUTANTS = {
 }
 
 
+# mistakes in the learned gate and the V-cycle, caught by their own pin files
+MUTANTS_ELSEWHERE = {
+    "bf16 ties rounded up": ("u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0x8000u;",
+                             "test_oracle_learned.py"),
+    "feature 3 takes the own share": ("f[2] = or_bf16((float)(wdeg - wown) / (float)wdeg);",
+                                      "f[2] = or_bf16((float)wown / (float)wdeg);",
+                                      "test_oracle_learned.py"),
+    "hidden bias dropped": ("float acc = bf16_bits_to_float(net[OR_MLP_B1 + j]);",
+                            "float acc = 0.0f;", "test_oracle_learned.py"),
+    "second ReLU dropped": ("h2[j] = or_bf16(acc > 0.0f ? acc : 0.0f);", "h2[j] = or_bf16(acc);",
+                            "test_oracle_learned.py"),
+    "ReLU gate missing in backprop": ("d2[i] = a2[i] > 0 ? dz * prm[OR_MLP_W3 + i] : 0.0;",
+                                      "d2[i] = dz * prm[OR_MLP_W3 + i];",
+                                      "test_oracle_learned.py"),
+    "full rounds shifted": ("int full = !net || r % full_every == full_every - 1 || r == rounds - 1;",
+                            "int full = !net || r % full_every == 0 || r == rounds - 1;",
+                            "test_oracle_learned.py"),
+    "gated round ends the run": ("if (full && m == 0) break;", "if (m == 0) break;",
+                                 "test_oracle_learned.py"),
+    "V-cycle clustering unconstrained": (
+        "p->subrounds, level_seed(p->seed, L), cpl[L], lab, &rd, NULL);",
+        "p->subrounds, level_seed(p->seed, L), NULL, lab, &rd, NULL);", "test_oracle_vcycle.py"),
+    "V-cycle coarse blocks not inherited": ("cpl[L + 1][g->f2c[v]] = cpl[L][v];",
+                                            "cpl[L + 1][g->f2c[v]] = 0;", "test_oracle_vcycle.py"),
+}
+
+
+@pytest.mark.parametrize("name", list(MUTANTS_ELSEWHERE))
+def test_other_pins_reject_mutant(name, tmp_path):
+    old, new, pins = MUTANTS_ELSEWHERE[name]
+    _check_mutant(name, old, new, pins, tmp_path)
+
+
+def _check_mutant(name, old, new, pins, tmp_path):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {name}"
+    mutated = tmp_path / "sclap_oracle.c"
+    mutated.write_text(src.replace(old, new))
+    (tmp_path / "sclap_oracle.h").write_text(open(SRC.replace(".c", ".h")).read())
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", str(so),
+                           str(mutated), "-lm"])
+    env = dict(os.environ, SCLAP_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", pins)],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant '{name}'\n{r.stdout[-2000:]}"
+
+
 @pytest.mark.parametrize("name", list(MUTANTS))
 def test_pins_reject_mutant(name, tmp_path):
     old, new = MUTANTS[name]
