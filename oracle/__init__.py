@@ -90,6 +90,9 @@ def lib():
             L.or_validate.argtypes = g
             L.or_cluster.argtypes = g + [C.c_int64, C.c_int32, C.c_int32, C.c_uint64, _P32,
                                          _P32, _P32, _P64]
+            L.or_cluster_degree_ordered.argtypes = L.or_cluster.argtypes
+            L.or_degree_colours.argtypes = [C.c_int64, _P64, C.c_uint64, C.c_int32, C.c_int32,
+                                            _P32]
             L.or_refine_bound.argtypes = g + [C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                                               C.c_uint64, _P32, _P32, _P64]
             L.or_refine.argtypes = g + [C.c_int32, C.c_double, C.c_int32, C.c_int32,
@@ -173,19 +176,30 @@ def validate(g) -> int:
     return int(lib().or_validate(*a))
 
 
-def cluster(g, U, rounds, subrounds, seed, constraint_part=None, return_moves=False):
+def cluster(g, U, rounds, subrounds, seed, constraint_part=None, return_moves=False,
+            degree_ordered=False):
     keep, a = _graph_args(g)
     n = a[0]
     lab = np.empty(n, np.int32)
     rd = C.c_int32(0)
     mv = np.zeros(max(rounds, 1), np.int64)
     cp = None if constraint_part is None else np.ascontiguousarray(constraint_part, np.int32)
-    rc = lib().or_cluster(*a, U, rounds, subrounds, seed, None if cp is None else _p32(cp),
-                          _p32(lab), C.byref(rd), _p64(mv))
+    fn = lib().or_cluster_degree_ordered if degree_ordered else lib().or_cluster
+    rc = fn(*a, U, rounds, subrounds, seed, None if cp is None else _p32(cp),
+            _p32(lab), C.byref(rd), _p64(mv))
     _check(rc, "cluster")
     if return_moves:
         return lab, rd.value, mv[:rd.value].copy()
     return lab, rd.value
+
+
+def degree_colours(g, seed, rnd, S):
+    """Sub-round of every node in round rnd under degree-ordered colours."""
+    xadj = np.ascontiguousarray(g["xadj"], dtype=np.int64)
+    n = xadj.size - 1
+    out = np.empty(n, np.int32)
+    _check(lib().or_degree_colours(n, _p64(xadj), seed, rnd, S, _p32(out)), "degree_colours")
+    return out
 
 
 def refine_bound(g, nblocks, B, rounds, subrounds, seed, part, return_moves=False):

@@ -179,18 +179,52 @@ static int64_t bound_of(const int64_t *Bv, int64_t B, int64_t L)
     return Bv ? Bv[L] : B;
 }
 
+typedef struct {
+    int64_t deg;
+    uint32_t h;
+    int64_t v;
+} deg_key;
+
+static int cmp_deg_key(const void *a, const void *b)
+{
+    const deg_key *x = (const deg_key *)a, *y = (const deg_key *)b;
+    if (x->deg != y->deg) return x->deg < y->deg ? -1 : 1;
+    if (x->h != y->h) return x->h < y->h ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+/* Degree-ordered sub-rounds of round r: the nodes in (degree asc, high 32
+ * bits of h(v,r) asc, v asc) order; the node at position p acts in sub-round
+ * floor(p * S / n), so low-degree nodes act first (Sec. III.A visits nodes
+ * in increasing degree) and the S groups differ in size by at most one. */
+int or_degree_colours(int64_t n, const int64_t *xadj, uint64_t seed, int32_t round, int32_t S,
+                      int32_t *colour_out)
+{
+    deg_key *k = (deg_key *)malloc(sizeof(deg_key) * (size_t)(n ? n : 1));
+    if (!k) return OR_ENOMEM;
+    for (int64_t v = 0; v < n; v++) {
+        k[v].deg = xadj[v + 1] - xadj[v];
+        k[v].h = (uint32_t)(node_hash(seed, round, v) >> 32);
+        k[v].v = v;
+    }
+    qsort(k, (size_t)n, sizeof(deg_key), cmp_deg_key);
+    for (int64_t p = 0; p < n; p++) colour_out[k[p].v] = (int32_t)(p * S / n);
+    free(k);
+    return OR_OK;
+}
+
 static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                         const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
                         int64_t *W, int64_t B, const int64_t *Bv, int refine,
                         const int32_t *cp, uint64_t seed, int32_t round, int32_t S,
-                        const uint8_t *active, lp_ws *ws)
+                        const uint8_t *active, const int32_t *colour, lp_ws *ws)
 {
     int64_t moves = 0;
     for (int32_t j = 0; j < S; j++) {
         int64_t np = 0;
         /* --- every node of colour j proposes against the current state --- */
         for (int64_t v = 0; v < n; v++) {
-            if ((int32_t)or_colour(seed, round, v, S) != j) continue;
+            if ((colour ? colour[v] : (int32_t)or_colour(seed, round, v, S)) != j) continue;
             if (xadj[v + 1] == xadj[v]) continue;  /* no neighbours: never moves */
             if (active && !active[v]) continue;    /* learned form: not visited */
             int64_t nt = 0;
@@ -277,26 +311,32 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
                   int64_t *W, int64_t nW, int64_t B, const int64_t *Bv, int refine,
                   const int32_t *cp, uint64_t seed, int32_t rounds, int32_t S,
-                  int32_t *rounds_done, int64_t *moves_per_round)
+                  int32_t degree_order, int32_t *rounds_done, int64_t *moves_per_round)
 {
+    int32_t *colour = NULL;
+    if (degree_order) {
+        colour = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+        if (!colour) return OR_ENOMEM;
+    }
     lp_ws ws;
     ws.acc = (int64_t *)calloc((size_t)(nW ? nW : 1), sizeof(int64_t));
     ws.touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nW ? nW : 1));
     ws.props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
     if (!ws.acc || !ws.touched || !ws.props) {
-        free(ws.acc); free(ws.touched); free(ws.props);
+        free(ws.acc); free(ws.touched); free(ws.props); free(colour);
         return OR_ENOMEM;
     }
     int32_t done = 0;
     for (int32_t r = 0; r < rounds; r++) {
+        if (colour) or_degree_colours(n, xadj, seed, r, S, colour);
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, Bv, refine, cp,
-                             seed, r, S, NULL, &ws);
+                             seed, r, S, NULL, colour, &ws);
         if (moves_per_round) moves_per_round[r] = m;
         done = r + 1;
         if (m == 0) break;
     }
     if (rounds_done) *rounds_done = done;
-    free(ws.acc); free(ws.touched); free(ws.props);
+    free(ws.acc); free(ws.touched); free(ws.props); free(colour);
     return OR_OK;
 }
 
@@ -368,11 +408,40 @@ static int pack_isolated(int64_t n, const int64_t *xadj, const int32_t *vwgt, in
 
 /* Sec. III.A, clustering form: every node starts in its own cluster (label
  * = node id); cluster weights stay <= U. */
+static int cluster_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                        const int32_t *adjwgt, const int32_t *vwgt, int64_t U,
+                        int32_t rounds, int32_t S, uint64_t seed,
+                        const int32_t *constraint_part, int32_t degree_order,
+                        int32_t *labels_out, int32_t *rounds_done, int64_t *moves_per_round);
+
 int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                const int32_t *adjwgt, const int32_t *vwgt, int64_t U,
                int32_t rounds, int32_t S, uint64_t seed,
                const int32_t *constraint_part, int32_t *labels_out,
                int32_t *rounds_done, int64_t *moves_per_round)
+{
+    return cluster_impl(n, xadj, adjncy, adjwgt, vwgt, U, rounds, S, seed, constraint_part, 0,
+                        labels_out, rounds_done, moves_per_round);
+}
+
+/* Clustering with degree-ordered sub-rounds: the closest synchronous
+ * analogue of the paper's traversal in increasing degree (Sec. III.A); see
+ * or_degree_colours.  Otherwise as or_cluster. */
+int or_cluster_degree_ordered(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                              const int32_t *adjwgt, const int32_t *vwgt, int64_t U,
+                              int32_t rounds, int32_t S, uint64_t seed,
+                              const int32_t *constraint_part, int32_t *labels_out,
+                              int32_t *rounds_done, int64_t *moves_per_round)
+{
+    return cluster_impl(n, xadj, adjncy, adjwgt, vwgt, U, rounds, S, seed, constraint_part, 1,
+                        labels_out, rounds_done, moves_per_round);
+}
+
+static int cluster_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                        const int32_t *adjwgt, const int32_t *vwgt, int64_t U,
+                        int32_t rounds, int32_t S, uint64_t seed,
+                        const int32_t *constraint_part, int32_t degree_order,
+                        int32_t *labels_out, int32_t *rounds_done, int64_t *moves_per_round)
 {
     int32_t maxc;
     if (rounds < 0 || S < 1) return OR_EINVAL;
@@ -382,7 +451,8 @@ int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (!W) return OR_ENOMEM;
     for (int64_t v = 0; v < n; v++) { labels_out[v] = (int32_t)v; W[v] = vwgt[v]; }
     int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, labels_out, W, n, U, NULL, 0,
-                    constraint_part, seed, rounds, S, rounds_done, moves_per_round);
+                    constraint_part, seed, rounds, S, degree_order, rounds_done,
+                    moves_per_round);
     free(W);
     if (rc) return rc;
     return pack_isolated(n, xadj, vwgt, U, constraint_part, labels_out);
@@ -402,7 +472,7 @@ static int refine_bounds(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (!W) return OR_ENOMEM;
     for (int64_t v = 0; v < n; v++) W[part[v]] += vwgt[v];
     int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, part, W, nblocks, B, Bv, 1, NULL,
-                    seed, rounds, S, rounds_done, moves_per_round);
+                    seed, rounds, S, 0, rounds_done, moves_per_round);
     free(W);
     return rc;
 }
@@ -1029,7 +1099,7 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         }
         memcpy(prev, part, sizeof(int32_t) * (size_t)n);
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, part, W, B, NULL, 1, NULL, seed, r,
-                             S, active, &ws);
+                             S, active, NULL, &ws);
         for (int64_t v = 0; v < n; v++) moved[v] = part[v] != prev[v];
         if (trace_y) memcpy(trace_y + (size_t)r * n, moved, (size_t)n);
         if (moves_per_round) moves_per_round[r] = m;

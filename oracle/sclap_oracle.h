@@ -68,6 +68,14 @@ int or_cluster(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                const int32_t *constraint_part, int32_t *labels_out,
                int32_t *rounds_done, int64_t *moves_per_round);
 
+int or_cluster_degree_ordered(int64_t n, const int64_t *xadj, const int32_t *adjncy,
+                              const int32_t *adjwgt, const int32_t *vwgt, int64_t U,
+                              int32_t rounds, int32_t S, uint64_t seed,
+                              const int32_t *constraint_part, int32_t *labels_out,
+                              int32_t *rounds_done, int64_t *moves_per_round);
+int or_degree_colours(int64_t n, const int64_t *xadj, uint64_t seed, int32_t round, int32_t S,
+                      int32_t *colour_out);
+
 int or_refine_bound(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                     const int32_t *adjwgt, const int32_t *vwgt, int32_t nblocks,
                     int64_t B, int32_t rounds, int32_t S, uint64_t seed,

@@ -64,6 +64,12 @@ MUTANTS_ELSEWHERE = {
         "p->subrounds, level_seed(p->seed, L), NULL, lab, &rd, NULL);", "test_oracle_vcycle.py"),
     "V-cycle coarse blocks not inherited": ("cpl[L + 1][g->f2c[v]] = cpl[L][v];",
                                             "cpl[L + 1][g->f2c[v]] = 0;", "test_oracle_vcycle.py"),
+    "high degree first": ("if (x->deg != y->deg) return x->deg < y->deg ? -1 : 1;",
+                          "if (x->deg != y->deg) return x->deg < y->deg ? 1 : -1;",
+                          "test_oracle_degree_order.py"),
+    "round-robin groups": ("colour_out[k[p].v] = (int32_t)(p * S / n);",
+                           "colour_out[k[p].v] = (int32_t)(p % S);",
+                           "test_oracle_degree_order.py"),
 }
 
 
