@@ -2473,7 +2473,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     CK(cudaStreamSynchronize(s));
     for (int j = 0; j < S; j++) {
         if (hc[j].err & kErrTable) fail(SCLAP_ECUDA, "hash table overflow");
-        if (hc[j].err & kErrBarrier) fail(SCLAP_ECUDA, "grid barrier timed out in arbitration");
+        if (hc[j].err & kErrBarrier) fail(SCLAP_ETIMEOUT, "grid barrier timed out in arbitration");
         if (hc[j].err & kErrBig) fail(SCLAP_ECUDA, "long-segment capacity exceeded");
     }
     return done;
