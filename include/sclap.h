@@ -162,21 +162,23 @@ int project_partition(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_
                       int32_t *fine_part_out, void *stream);
 
 /* Cut (Sec. II.A) and block weights of a partition.
- *   part        device int32[n] in [0, k)
+ *   part        device int32[n] in [0, k); any other id returns SCLAP_EINVAL
  *   cut_out     host int64;  block_w_out host int64[k] (NULL allowed) */
 int sclap_cut(const sclap_graph *g, const int32_t *part, int32_t k, int64_t *cut_out,
               int64_t *block_w_out, void *stream);
 
 /* Cut and block weights like sclap_cut, without allocating any memory.  The
  * paper has no counterpart: this exists for callers that cannot let a library
- * allocate (inside another framework's CUDA-graph capture, in loops that must
- * not reach the allocator, under a custom memory owner).  Its accumulators are
- * a file-scope device array of 1 + 65536 int64 values, held by every GPU that
+ * allocate device memory, such as loops with a latency budget (cudaMalloc and
+ * cudaFree can synchronise the whole device) and programs whose device memory
+ * is handed out by their own pool or allocator.  Its accumulators are a
+ * file-scope device array of 2 + 65536 int64 values, held by every GPU that
  * loads the library until the process exits; k > 65536 returns SCLAP_EINVAL.
- * The first call on a device looks up that array's device address (make that
- * call before any stream capture).  All calls share the array and clear the
- * part they use; calls that overlap on the GPU race.  Same arguments and
- * outputs as sclap_cut; no graph validation. */
+ * The first call on a device looks up that array's device address.  All calls
+ * share the array and clear the part they use; calls that overlap on the GPU
+ * race.  Same arguments and outputs as sclap_cut; a block id outside [0, k)
+ * returns SCLAP_EINVAL (such ids are skipped on the device, never written);
+ * no other graph validation. */
 int sclap_cut_noalloc(const sclap_graph *g, const int32_t *part, int32_t k, int64_t *cut_out,
                       int64_t *block_w_out, void *stream);
 
@@ -248,6 +250,12 @@ int sclap_mlp_loss_grad(const float *x, const uint8_t *y, int64_t N, const float
 int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, int32_t epochs,
                     int32_t batch, float lr, uint64_t seed, double *loss_out, void *stream);
 
+/* The bf16 network of trained float parameters: net_out[i] = the bf16 bit
+ * pattern of params[i] rounded to nearest, ties to even (the same rounding as
+ * the features and hidden outputs).  params device float[1313], net_out
+ * device uint16[1313]. */
+int sclap_mlp_pack_bf16(const float *params, uint16_t *net_out, void *stream);
+
 /* A set of graphs for batched runs (host array of graph views). */
 typedef struct {
     int32_t ngraphs;
@@ -303,6 +311,16 @@ int sclap_vcycle(const sclap_graph *g, const sclap_ml_params *p, int32_t *part_i
                  sclap_ml_stats *stats_out, void *stream);
 
 void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed);
+
+/* Failure detection of the library's only in-kernel wait (the paper has no
+ * counterpart): the grid barrier of the arbitration kernel gives up after a
+ * bounded number of SM clock cycles, sets an error flag and returns, and the
+ * calling entry point reports SCLAP_ETIMEOUT.  This runs that barrier in a
+ * two-CTA launch where one CTA never arrives, with the bound limit_cycles
+ * (>= 0): the wait must run out.  Returns SCLAP_ETIMEOUT when it did and was
+ * reported (the expected result), SCLAP_OK if the barrier did not time out,
+ * other codes on CUDA errors.  Uses the legacy default stream. */
+int sclap_wait_selftest(int64_t limit_cycles);
 
 /* Copies a library-owned graph into caller-allocated device arrays of sizes
  * n+1, nnz, nnz and n (enqueued on `stream`, synchronised before return). */

@@ -111,6 +111,8 @@ _SIGS = {
                                       C.POINTER(C.c_double), _VP]),
     "sclap_mlp_train": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int32, C.c_int32, C.c_float,
                                   C.c_uint64, C.POINTER(C.c_double), _VP]),
+    "sclap_mlp_pack_bf16": (C.c_int, [_VP, _VP, _VP]),
+    "sclap_wait_selftest": (C.c_int, [C.c_int64]),
     "sclap_prof_enable": (None, [C.c_int]),
     "sclap_prof_reset": (None, []),
     "sclap_prof_read": (C.c_int, [C.POINTER(Prof)]),
@@ -277,10 +279,16 @@ def sclap_mlp_train(x: torch.Tensor, y: torch.Tensor, params: torch.Tensor, epoc
     return prm, loss.value
 
 
-def bf16_bits(params: torch.Tensor) -> torch.Tensor:
-    """bf16 bit patterns (int16 tensor) of float parameters, nearest-even
-    rounding (torch's float32 -> bfloat16 conversion)."""
-    return params.to(torch.float32).to(torch.bfloat16).view(torch.int16).contiguous()
+def bf16_bits(params: torch.Tensor, stream=None) -> torch.Tensor:
+    """The bf16 network (int16 bit patterns, nearest-even rounding) of float
+    scorer parameters, computed by the library (sclap_mlp_pack_bf16)."""
+    _require_cuda(params)
+    prm = params.to(torch.float32).contiguous()
+    if prm.numel() != MLP_PARAMS:
+        raise TypeError("params must hold 1313 floats")
+    net = torch.empty(MLP_PARAMS, dtype=torch.int16, device=prm.device)
+    _check(lib().sclap_mlp_pack_bf16(_ptr(prm), _ptr(net), _stream(stream)), "sclap_mlp_pack_bf16")
+    return net
 
 
 def sclap_refine_bound(g: dict, nblocks: int, B: int, rounds: int, subrounds: int, seed: int,
@@ -442,6 +450,12 @@ def sclap_vcycle(g: dict, params: dict, part: torch.Tensor, stream=None):
                  init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
                  cut=st.cut, maxbw=st.maxbw)
     return p, stats
+
+
+def wait_selftest(limit_cycles: int) -> int:
+    """Runs the arbitration barrier with one CTA absent (see sclap_wait_selftest);
+    returns the status code (ETIMEOUT is the expected one)."""
+    return int(lib().sclap_wait_selftest(int(limit_cycles)))
 
 
 def prof_enable(on: bool = True):

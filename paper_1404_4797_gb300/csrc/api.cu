@@ -709,6 +709,25 @@ int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, 
     });
 }
 
+int sclap_wait_selftest(int64_t limit_cycles) {
+    int got = SCLAP_OK;
+    const int rc = guarded([&] {
+        if (limit_cycles < 0) fail(SCLAP_EINVAL, "limit");
+        Scratch sc(nullptr);
+        got = barrier_selftest((long long)limit_cycles, sc);
+    });
+    return rc != SCLAP_OK ? rc : got;
+}
+
+int sclap_mlp_pack_bf16(const float *params, uint16_t *net_out, void *stream) {
+    return guarded([&] {
+        if (!params || !net_out) fail(SCLAP_EINVAL, "args");
+        cudaStream_t s = as_stream(stream);
+        mlp_pack_bf16(params, net_out, s);
+        CK(cudaStreamSynchronize(s));
+    });
+}
+
 int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cut_out,
               int64_t *block_w_out, void *stream) {
     return guarded([&] {
@@ -716,6 +735,7 @@ int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cu
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
         DGraph g = view(gp);
+        if (!in_range(g.n, part, k, sc)) fail(SCLAP_EINVAL, "part out of range");
         int64_t *d_cut = sc.get<int64_t>(1);
         int64_t *d_bw = sc.get<int64_t>(k);
         cut_impl(g, part, k, 1, nullptr, d_cut, d_bw, sc);

@@ -382,17 +382,27 @@ __global__ void k_halve(unsigned long long *cut, int64_t groups) {
     for (int64_t t = threadIdx.x; t < groups; t += blockDim.x) cut[t] /= 2;
 }
 
-__global__ void k_bw(DGraph g, const int32_t *part, int64_t nblocks, unsigned long long *bw) {
+// Block weights.  Ids outside [0, nblocks) are skipped, so every write stays
+// inside bw[0, nblocks); they are counted in *bad when bad is given.
+__global__ void k_bw(DGraph g, const int32_t *part, int64_t nblocks, unsigned long long *bw,
+                     unsigned long long *bad) {
     extern __shared__ unsigned long long lbw[];
     const bool local = nblocks <= 2048;
     if (local)
         for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) lbw[b] = 0;
     __syncthreads();
+    unsigned long long nbad = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        if (local) atomicAdd(&lbw[part[v]], (unsigned long long)g.vwgt[v]);
-        else atomicAdd(&bw[part[v]], (unsigned long long)g.vwgt[v]);
+        const int32_t p = part[v];
+        if (p < 0 || p >= nblocks) {
+            nbad++;
+            continue;
+        }
+        if (local) atomicAdd(&lbw[p], (unsigned long long)g.vwgt[v]);
+        else atomicAdd(&bw[p], (unsigned long long)g.vwgt[v]);
     }
+    if (bad && nbad) atomicAdd(bad, nbad);
     __syncthreads();
     if (local)
         for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x)
@@ -400,7 +410,7 @@ __global__ void k_bw(DGraph g, const int32_t *part, int64_t nblocks, unsigned lo
 }
 
 void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned long long *d_cut,
-                unsigned long long *d_bw, cudaStream_t s, int sms) {
+                unsigned long long *d_bw, unsigned long long *d_bad, cudaStream_t s, int sms) {
     const int grid = sms * 8;
     if (g.nnz > 0) {
         const int cgrid = (int)std::min<int64_t>(ceil_div<int64_t>(g.nnz, kCutTile), grid);
@@ -411,7 +421,7 @@ void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned 
     }
     if (g.n > 0) {
         size_t shm = nblocks <= 2048 ? nblocks * sizeof(unsigned long long) : 0;
-        k_bw<<<grid, 256, shm, s>>>(g, part, nblocks, d_bw);
+        k_bw<<<grid, 256, shm, s>>>(g, part, nblocks, d_bw, d_bad);
         LAUNCHED();
     }
 }
@@ -431,7 +441,7 @@ void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t gro
     }
     if (d_bw && g.n > 0) {
         size_t shm = nblocks <= 2048 ? nblocks * sizeof(unsigned long long) : 0;
-        k_bw<<<grid, 256, shm, s>>>(g, part, nblocks, (unsigned long long *)d_bw);
+        k_bw<<<grid, 256, shm, s>>>(g, part, nblocks, (unsigned long long *)d_bw, nullptr);
         LAUNCHED();
     }
 }

@@ -28,8 +28,9 @@ void cut_impl(const DGraph &g, const int32_t *part, int64_t nblocks, int64_t gro
               Scratch &sc);
 
 // The same cut and block-weight kernels on caller-provided, zeroed device
-// accumulators (d_cut: 1 entry, d_bw: nblocks entries); allocates nothing.
+// accumulators (d_cut: 1 entry, d_bw: nblocks entries, d_bad: 1 entry that
+// counts block ids outside [0, nblocks), which are skipped); allocates nothing.
 void cut_launch(const DGraph &g, const int32_t *part, int64_t nblocks, unsigned long long *d_cut,
-                unsigned long long *d_bw, cudaStream_t s, int sms);
+                unsigned long long *d_bw, unsigned long long *d_bad, cudaStream_t s, int sms);
 
 }  // namespace sclap

@@ -358,6 +358,18 @@ void mlp_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t
     LAUNCHED();
 }
 
+// bf16 bit patterns of float parameters, nearest even (the rounding of the
+// scorer's features and hidden outputs).
+__global__ void k_pack_bf16(const float *prm, uint16_t *net) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x)
+        net[i] = (uint16_t)(__float_as_uint(bf16_round(prm[i])) >> 16);
+}
+
+void mlp_pack_bf16(const float *prm, uint16_t *net, cudaStream_t s) {
+    k_pack_bf16<<<ceil_div(kMlpParams, 256), 256, 0, s>>>(prm, net);
+    LAUNCHED();
+}
+
 __global__ void k_sgd(float *prm, const float *grad, float lr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x)
         prm[i] -= lr * grad[i];

@@ -47,6 +47,8 @@ void mlp_score(const float *x, int64_t N, const uint16_t *net, float *z, cudaStr
 // are accumulated into (zero them first).
 void mlp_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t N,
                    const float *prm, float *grad, double *d_loss, cudaStream_t s);
+// bf16 bit patterns (nearest even) of the kMlpParams float parameters
+void mlp_pack_bf16(const float *prm, uint16_t *net, cudaStream_t s);
 // prm -= lr * grad
 void mlp_sgd(float *prm, const float *grad, float lr, cudaStream_t s);
 

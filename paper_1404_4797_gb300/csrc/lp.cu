@@ -179,6 +179,7 @@ struct LPArgs {
     int32_t *tileseg;          // tile -> index into big
     unsigned long long *bhist; // [maxbig * kBins], zero between uses
     GridBar *bar;
+    long long bar_cycles;      // bound of every grid-barrier wait (SM clock cycles)
     int32_t maxbig, maxtiles;
     const uint8_t *active;     // learned refinement: rows visited this round (null: all)
 };
@@ -1371,11 +1372,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
 }
 
 // Grid-wide barrier of a cooperative launch.  The wait is bounded: a CTA
-// that waits longer than kBarCycles (or sees the error flag raised) sets
-// kErrBarrier and goes on; the host then reports the failure.
+// that waits longer than `limit` SM clock cycles (or sees the error flag
+// raised) sets kErrBarrier and goes on; the host then reports the failure.
 constexpr long long kBarCycles = 4000000000ll;  // about two seconds at 2 GHz
 
-__device__ void grid_barrier(GridBar *bar, int32_t *err) {
+__device__ void grid_barrier(GridBar *bar, int32_t *err, long long limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = &bar->gen;
@@ -1391,7 +1392,7 @@ __device__ void grid_barrier(GridBar *bar, int32_t *err) {
             const long long t0 = clock64();
             while (*vgen == g0) {
                 if (*verr & kErrBarrier) break;
-                if (clock64() - t0 > kBarCycles) {
+                if (clock64() - t0 > limit) {
                     atomicOr(err, kErrBarrier);
                     break;
                 }
@@ -1401,6 +1402,13 @@ __device__ void grid_barrier(GridBar *bar, int32_t *err) {
         __threadfence();
     }
     __syncthreads();
+}
+
+// Self-test of the bounded wait: CTA 0 never arrives, so CTA 1 must give up
+// after `limit` cycles, raise kErrBarrier and return.
+__global__ void k_barrier_selftest(GridBar *bar, int32_t *err, long long limit) {
+    if (blockIdx.x == 0) return;
+    grid_barrier(bar, err, limit);
 }
 
 // Number of select passes of a big segment.
@@ -1503,7 +1511,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
         }
         __syncthreads();
     }
-    grid_barrier(a.bar, &a.ctr->err);
+    grid_barrier(a.bar, &a.ctr->err, a.bar_cycles);
     if (threadIdx.x == 0) s_passes = 0;
     __syncthreads();
     {
@@ -1601,7 +1609,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
             __threadfence();
             __syncthreads();
         }
-        grid_barrier(a.bar, &a.ctr->err);
+        grid_barrier(a.bar, &a.ctr->err, a.bar_cycles);
     }
     // admissions: keys below K (and entries of weight 0)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -2257,6 +2265,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.tileseg = sc.get<int32_t>(a.maxtiles);
     a.bhist = sc.zeros<unsigned long long>((size_t)a.maxbig * kBins);
     a.bar = sc.zeros<GridBar>(1);
+    a.bar_cycles = kBarCycles;
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
     // bucket lengths, then piece counts, then cluster-path row counts (per colour)
     int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + 3 * S);
@@ -2477,6 +2486,18 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         if (hc[j].err & kErrBig) fail(SCLAP_ECUDA, "long-segment capacity exceeded");
     }
     return done;
+}
+
+int barrier_selftest(long long limit_cycles, Scratch &sc) {
+    cudaStream_t s = sc.stream();
+    GridBar *bar = sc.zeros<GridBar>(1);
+    int32_t *err = sc.zeros<int32_t>(1);
+    k_barrier_selftest<<<2, 32, 0, s>>>(bar, err, limit_cycles);
+    LAUNCHED();
+    int32_t h = 0;
+    CK(cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return (h & kErrBarrier) ? SCLAP_ETIMEOUT : SCLAP_OK;
 }
 
 }  // namespace sclap

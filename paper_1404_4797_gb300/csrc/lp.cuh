@@ -34,4 +34,9 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves, int64_
 // <= U in id order (per block of cp when given); see pack_isolated in lp.cu.
 void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, Scratch &sc);
 
+// Runs the arbitration kernel's bounded grid barrier with one of two CTAs
+// absent, so the wait must give up after limit_cycles; returns SCLAP_ETIMEOUT
+// when it did (the expected result) and SCLAP_OK if it did not.
+int barrier_selftest(long long limit_cycles, Scratch &sc);
+
 }  // namespace sclap

@@ -1,10 +1,10 @@
 // noalloc.cu -- cut and block weights of a partition without any device
-// allocation.  Some callers cannot let a library allocate: code that runs
-// while another framework captures a CUDA graph (cudaMalloc is not allowed
-// inside a capture), real-time loops that must not hit the allocator's
-// device-wide synchronisation, and programs whose memory is owned by a
-// custom allocator.  This entry point keeps its accumulators in a file-scope
-// device array instead of taking memory per call.
+// allocation.  Some callers cannot let a library allocate: loops with a
+// latency budget (cudaMalloc and cudaFree can synchronise the whole device),
+// and programs whose device memory is handed out by their own pool or
+// allocator, which would not see or account for memory a library takes on
+// its own.  This entry point keeps its accumulators in a file-scope device
+// array instead of taking memory per call.
 #include <cstring>
 #include <mutex>
 
@@ -14,10 +14,11 @@ namespace {
 
 constexpr int kNoAllocMaxK = 65536;
 
-// [0] cut accumulator, [1 .. 1 + kNoAllocMaxK) block weights.  Every GPU that
-// loads the library holds this array until the process exits; all calls share
-// it, so calls that overlap on the GPU race.
-static __device__ __align__(256) unsigned long long g_cut_scratch[1 + kNoAllocMaxK];
+// [0] cut accumulator, [1] count of block ids outside [0, k), [2 .. 2 + k)
+// block weights (k <= kNoAllocMaxK).  Every GPU that loads the library holds
+// this array until the process exits; all calls share it, so calls that
+// overlap on the GPU race.
+static __device__ __align__(256) unsigned long long g_cut_scratch[2 + kNoAllocMaxK];
 
 std::mutex g_mu;
 unsigned long long *g_ptr[64];
@@ -58,17 +59,21 @@ extern "C" int sclap_cut_noalloc(const sclap_graph *gp, const int32_t *part, int
     if (rc != SCLAP_OK) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     try {
-        // the array keeps the previous call's sums: clear what this call uses
-        CK(cudaMemsetAsync(acc, 0, (1 + (size_t)k) * sizeof(unsigned long long), s));
+        // The array keeps the previous call's sums: clear what this call uses.
+        // Clearing 2 + k slots is enough because the block-weight kernel skips
+        // (and counts in slot 1) every id outside [0, k), so its writes stay
+        // inside slots [2, 2 + k).
+        CK(cudaMemsetAsync(acc, 0, (2 + (size_t)k) * sizeof(unsigned long long), s));
         sclap::DGraph g{gp->n, gp->nnz, gp->xadj, gp->adjncy, gp->adjwgt, gp->vwgt};
-        sclap::cut_launch(g, part, k, acc, acc + 1, s, sms);
-        unsigned long long c = 0;
-        CK(cudaMemcpyAsync(&c, acc, sizeof(c), cudaMemcpyDeviceToHost, s));
+        sclap::cut_launch(g, part, k, acc, acc + 2, acc + 1, s, sms);
+        unsigned long long c[2] = {0, 0};
+        CK(cudaMemcpyAsync(c, acc, sizeof(c), cudaMemcpyDeviceToHost, s));
         if (block_w_out)
-            CK(cudaMemcpyAsync(block_w_out, acc + 1, (size_t)k * sizeof(int64_t),
-                                      cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(block_w_out, acc + 2, (size_t)k * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (cut_out) *cut_out = (int64_t)c;
+        if (c[1]) return SCLAP_EINVAL;  // a block id outside [0, k)
+        if (cut_out) *cut_out = (int64_t)c[0];
     } catch (const sclap::Error &e) {
         return e.code;
     }

@@ -150,3 +150,13 @@ def test_trace_train_threshold_gate_pipeline():
         assert np.array_equal(got.cpu().numpy(), want) and vis == vis_w and rd == len(mv)
         lmax = oracle.lmax(int(gn["vwgt"].sum()), k, 0.03)
         assert int(bw.max()) <= lmax
+
+
+def test_pack_bf16_matches_oracle_rounding():
+    rng = np.random.default_rng(5)
+    p = (rng.standard_normal(oracle.MLP_NPARAM) * 3).astype(np.float32)
+    # exact ties at both parities, values just above a tie, signed zero
+    p[:6] = np.array([1.0 + 2**-8, 1.0 + 3 * 2**-8, 1.0 + 2**-8 + 2**-12, -(1.0 + 2**-8),
+                      -0.0, 3.0e38], np.float32)
+    got = S.bf16_bits(torch.from_numpy(p).cuda()).cpu().numpy().view(np.uint16)
+    assert np.array_equal(got, bits_of(p))

@@ -55,3 +55,40 @@ def test_cycle_rejects_out_of_range_blocks():
     part[3] = 5
     with pytest.raises(oracle.OracleError):
         oracle.vcycle(g, params(4), part)
+
+
+def _level_seed(seed, l):
+    return oracle.mix64(seed ^ ((0x9E3779B97F4A7C15 * (l + 1)) & (2**64 - 1)))
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_every_level_of_the_cycle_carries_the_seed_partition(name):
+    """Rebuilds the cycle's hierarchy from the constrained clustering and the
+    contraction, one level at a time, and checks at every level what holds by
+    construction (Sec. IV.E): each coarse node's members share one block, so
+    the inherited partition has the input's block weights and cut.  The level
+    sizes must be those the oracle's V-cycle reports."""
+    g = GRAPHS[name]()
+    k = 4
+    n = g["vwgt"].size
+    part = ((np.arange(n, dtype=np.int64) * 2654435761) % k).astype(np.int32)
+    prm = params(k, refine_rounds=0, init_rounds=0)
+    _, st = oracle.vcycle(g, prm, part)
+    cV = int(g["vwgt"].sum())
+    U = max(int(g["vwgt"].max()), cV // (10 * k))
+    want_cut = oracle.cut(g, part)
+    want_bw = oracle.block_weights(g, part, k)
+    cur, cp, sizes = g, part, [n]
+    for lvl in range(st["levels"] - 1):
+        lab, _ = oracle.cluster(cur, U, prm["cluster_rounds"], prm["subrounds"],
+                                _level_seed(prm["seed"], lvl), constraint_part=cp)
+        assert np.array_equal(cp[lab], cp), "a cluster crosses a block"
+        coarse, f2c = oracle.contract(cur, lab)
+        ccp = np.full(coarse["vwgt"].size, -1, np.int32)
+        ccp[f2c] = cp
+        assert np.array_equal(ccp[f2c], cp) and (ccp >= 0).all()
+        assert oracle.cut(coarse, ccp) == want_cut
+        assert np.array_equal(oracle.block_weights(coarse, ccp, k), want_bw)
+        cur, cp = coarse, ccp
+        sizes.append(coarse["vwgt"].size)
+    assert sizes == st["n"]
