@@ -16,11 +16,15 @@
 //                 give omega(v, L) in registers; medium rows: one warp per
 //                 row with a warp-private linear-probing table (the paper's
 //                 Sec. IV.A choice of linear probing) or a k-array.
-//   k_propose<MODE, RowShape>  one CTA per row (128 threads for rows up to
-//                 kMidDeg, 256 for the rest) with a shared-memory table of
-//                 32-bit labels; pieces of longer rows merge into a global
-//                 table (hash) or k-array (dense) and are finished by
-//                 k_hub_cand / k_hub_tie / k_hub_emit or the last piece.
+//   k_propose_pipe<MODE, PipeShape>  rows of kMedDeg+1..kMidDeg entries in
+//                 three length classes: one CTA per row, software-pipelined
+//                 over the CTA's rows, with a shared table of packed
+//                 (label, omega) words sized to the row.
+//   k_propose<MODE, BigRows>  longer rows up to kChunk entries, one CTA per
+//                 row with a table of 32-bit labels; pieces of longer rows
+//                 merge into a global table (hash) or k-array (dense) and
+//                 are finished by k_hub_cand / k_hub_tie / k_hub_emit or the
+//                 last piece.
 //   k_propose_huge  hash modes, rows up to kHugeDeg: an 8-CTA cluster per
 //                 row, its table spread over the CTAs' shared memory.
 //   The best eligible label maximises (omega << 32 | ~tie); exact ties on
@@ -54,7 +58,8 @@ constexpr int kThreads = 256;
 constexpr int kSmallDeg = 32;            // small nodes: <= 32 entries (one warp pass)
 constexpr int kMedDeg = 256;             // medium nodes: 33..256 entries (one warp each)
 constexpr int kChunk = 4096;             // entries per large-row piece (one CTA)
-constexpr int kMidDeg = 2048;            // rows up to this size: the 128-thread CTA kernel
+constexpr int kMidDeg = 2048;            // rows up to this size: the pipelined CTA kernels
+constexpr int kPipeClasses = 3;          // ... in three length classes (bounds below)
 constexpr int kWSlots = 512;             // per-warp table slots for medium rows (>= 2 * kMedDeg)
 constexpr int kSlots = 8192;             // hash table slots (>= 2 * kChunk)
 constexpr int kSlotBits = 13;
@@ -103,7 +108,6 @@ struct Ctr {
     int32_t err;              // kErrTable or kErrBarrier
     int32_t nbig, bigtiles;   // segments above kSegSmem and their tiles
     int32_t huge_next;        // next row of the cluster path
-    int32_t mid_next;         // next row of the 128-thread CTA path
 };
 
 constexpr int32_t kErrTable = 1;
@@ -170,10 +174,11 @@ struct LPArgs {
     int32_t huge_on;
     int32_t *hlist;
     int32_t *hcnt;
-    // rows of kMedDeg < degree <= kMidDeg: mlist + c * nL lists colour c's
-    // rows as (index into Lnodes) << 20
-    int64_t *mlist;
-    int32_t *mcnt;
+    // rows of kMedDeg < degree <= kMidDeg for the pipelined kernels: colour
+    // c's rows of length class q at pl[q] + c * nL (node ids), their number
+    // in pc[q][c]
+    int32_t *pl[kPipeClasses];
+    int32_t *pc[kPipeClasses];
     // segments above kSegSmem entries (arbitrated by the whole grid)
     BigSeg *big;
     int32_t *tileseg;          // tile -> index into big
@@ -258,6 +263,9 @@ __device__ __forceinline__ int degree_class(int64_t d) {
     return d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= kSmallDeg ? 3 : 4;
 }
 
+// Length class of a row of kMedDeg < d <= kMidDeg entries (pipelined kernels).
+__device__ __forceinline__ int pipe_class(int64_t d) { return d <= 512 ? 0 : d <= 1024 ? 1 : 2; }
+
 __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, int32_t *cnt) {
     __shared__ int lcnt[32 * kClasses], lbase[32 * kClasses];
     const DGraph &g = a.g;
@@ -284,6 +292,11 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
                     if (d <= kMedDeg) {
                         bk[j] = kClasses * (int)col + degree_class(d);
                         rk[j] = atomicAdd(&lcnt[bk[j]], 1);
+                    } else if (d <= kMidDeg) {
+                        // a mid row: the pipelined kernel of its length class
+                        const int q = pipe_class(d);
+                        const int pos = atomicAdd(&a.pc[q][col], 1);
+                        a.pl[q][(int64_t)col * a.nL + pos] = (int32_t)v;
                     } else {
                         // a large row: list its pieces for sub-round `col`
                         int64_t lo = 0, hi = a.nL;  // li: Lnodes[li] == v
@@ -292,10 +305,7 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
                             if (a.Lnodes[mid] <= v) lo = mid;
                             else hi = mid;
                         }
-                        if (d <= kMidDeg) {
-                            const int pos = atomicAdd(&a.mcnt[col], 1);
-                            a.mlist[(int64_t)col * a.nL + pos] = lo << 20;
-                        } else if (a.huge_on && d > kChunk && d <= kHugeDeg) {
+                        if (a.huge_on && d > kChunk && d <= kHugeDeg) {
                             const int pos = atomicAdd(&a.hcnt[col], 1);
                             a.hlist[(int64_t)col * a.nL + pos] = (int32_t)lo;
                         } else {
@@ -384,15 +394,14 @@ struct NodeSm {
 };
 
 // Shape of a CTA-row kernel: threads, table slots (2^SBITS) and the longest
-// piece it takes.  BigRows: rows up to kChunk entries (and pieces of longer
-// rows); MidRows: rows of kMedDeg < degree <= kMidDeg, more CTAs per SM.
+// piece it takes.  BigRows: rows of kMidDeg < degree <= kChunk entries and
+// kChunk-entry pieces of longer rows.
 template <int NT, int SBITS, int CHUNK>
 struct RowShape {
     static constexpr int kNT = NT, kSBits = SBITS, kSl = 1 << SBITS, kCh = CHUNK;
     static_assert((1 << SBITS) >= 2 * CHUNK, "load factor <= 1/2");
 };
 using BigRows = RowShape<kThreads, kSlotBits, kChunk>;
-using MidRows = RowShape<128, 12, kMidDeg>;
 
 template <typename RS>
 struct HashTab {
@@ -811,8 +820,7 @@ __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
     small_bin<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, a.wl_cnt[b0 + 3], gwarp, nwarps);
 }
 
-// CTA rows: BigRows takes the pieces listed in plist (rows above kMidDeg),
-// MidRows the rows listed in mlist.
+// CTA rows: the pieces listed in plist (rows above kMidDeg).
 template <int MODE, typename RS>
 __global__ void __launch_bounds__(RS::kNT) k_propose(LPArgs a, int k) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -827,12 +835,301 @@ __global__ void __launch_bounds__(RS::kNT) k_propose(LPArgs a, int k) {
             sm.t.vals[i] = 0;
         }
     }
-    if constexpr (std::is_same<RS, MidRows>::value)
-        process_large<MODE, RS>(a, sm, k, a.mlist + (int64_t)a.colour * a.nL, a.mcnt[a.colour],
-                                &a.ctr->mid_next);
-    else
-        process_large<MODE, RS>(a, sm, k, a.plist + (int64_t)a.colour * a.Ptot, a.pcnt[a.colour],
-                                &a.ctr->large_next);
+    process_large<MODE, RS>(a, sm, k, a.plist + (int64_t)a.colour * a.Ptot, a.pcnt[a.colour],
+                            &a.ctr->large_next);
+}
+
+// ---------------------------------------------------------------- pipelined CTA rows
+
+// Rows of kMedDeg < degree <= kMidDeg.  One CTA per row; CTA b takes rows b,
+// b + grid, b + 2 grid, ... of its colour's list of one length class,
+// software-pipelined: while the current row is aggregated, the neighbour
+// labels of the next row are being gathered, the entries (adjncy, adjwgt; E
+// per thread, in registers) of the row after it and the scalars of the third
+// are in flight, and the node id of the fourth.  The table packs the label in
+// the high and omega in the low 32 bits of one word (weighted degrees fit 31
+// bits, so adding omega never carries into the label) and has
+// 2^ceil(log2(2 deg)) slots for a row of deg entries.  The thread whose CAS
+// creates a slot owns it: it gathers W(L) at once, and after the barrier
+// reads the slot's total, rates the label, and empties the slot, so a row
+// costs work in proportion to its length.  Proposals are buffered in shared
+// memory and emitted 32 at a time by warp 0 (one reservation of proposal
+// slots per batch instead of one contended atomic per row).  Two barriers
+// per row.
+template <int NT, int E, int TBITS, int MINB>
+struct PipeShape {
+    static constexpr int kNT = NT, kE = E, kMaxD = NT * E, kTBits = TBITS, kTS = 1 << TBITS;
+    static constexpr int kMinBlocks = MINB;  // CTAs per SM the register budget must allow
+    static_assert(kTS >= 2 * kMaxD, "load factor <= 1/2");
+    static_assert(NT >= kDenseMaxK, "dense selection: one thread per block");
+};
+using PipeA = PipeShape<128, 4, 10, 8>;   // rows of kMedDeg + 1 .. 512 entries
+using PipeB = PipeShape<128, 8, 11, 5>;   // rows of 513 .. 1024 entries
+using PipeC = PipeShape<512, 4, 12, 2>;   // rows of 1025 .. kMidDeg entries
+static_assert(PipeA::kMaxD == 512 && PipeB::kMaxD == 1024 && PipeC::kMaxD == kMidDeg,
+              "pipelined row classes (pipe_class)");
+
+template <int MODE, typename PS>
+struct PipeSm {
+    unsigned long long tab[MODE == kRefineDense ? 1 : PS::kTS];
+    int32_t dacc[MODE == kRefineDense ? PS::kNT / 32 : 1][kDenseMaxK];
+    int64_t W[kDenseMaxK];
+    unsigned long long wk[PS::kNT / 32];  // per warp: best candidate key
+    int32_t wl[PS::kNT / 32];             //           its label
+    int32_t wo[PS::kNT / 32];             //           omega(v, own) seen
+    int32_t bv[32], bT[32], bown[32], bgain[32], bc[32];  // decided proposals,
+    uint8_t bovl[32];                                    // emitted 32 at a time
+    int nbuf;
+};
+
+struct PipeRow {  // scalars of one row (the same in every thread)
+    int64_t rs, re;
+    int32_t v, own, c, cpv;
+};
+
+template <int MODE>
+__device__ __forceinline__ PipeRow pipe_row(const LPArgs &a, int32_t v) {
+    PipeRow r;
+    r.v = v;
+    r.rs = r.re = 0;
+    r.own = r.c = r.cpv = 0;
+    if (v >= 0) {
+        r.rs = a.g.xadj[v];
+        r.re = a.g.xadj[v + 1];
+        r.own = a.lab[v];
+        r.c = a.g.vwgt[v];
+        if (MODE == kCluster && a.cp) r.cpv = a.cp[v];
+    }
+    return r;
+}
+
+// Entries j*NT + t of row r (t = thread), E per thread.  Whole unrolled steps
+// past the row's end are skipped (the test is the same in every thread).
+template <int NT, int E>
+__device__ __forceinline__ void pipe_entries(const LPArgs &a, const PipeRow &r, int32_t *u,
+                                             int32_t *w) {
+    const int64_t deg = r.re - r.rs;
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const int e = (int)threadIdx.x + j * NT;
+        u[j] = 0;
+        w[j] = 0;
+        if (j * NT < deg && e < deg) {
+            u[j] = __ldcs(&a.g.adjncy[r.rs + e]);
+            w[j] = __ldcs(&a.g.adjwgt[r.rs + e]);
+        }
+    }
+}
+
+// Warp 0 emits the buffered proposals (one reservation per batch, weights
+// per target summed over the batch in dense mode) once 32 have collected, or
+// all of them when `all`.
+template <int MODE, typename PS>
+__device__ __forceinline__ void pipe_flush(const LPArgs &a, PipeSm<MODE, PS> &sm, bool all) {
+    if (threadIdx.x >= 32) return;
+    __syncwarp();
+    const int nb = sm.nbuf;
+    if (nb == 0 || (!all && nb < 32)) return;
+    const int lane = threadIdx.x;
+    if (lane < nb) {
+        const int32_t T = sm.bT[lane];
+        const int64_t wT = MODE == kRefineDense ? sm.W[T] : a.W[T];
+        emit<MODE == kRefineDense>(a, sm.bv[lane], T, sm.bown[lane], sm.bgain[lane], sm.bc[lane],
+                                   sm.bovl[lane] != 0, wT);
+    }
+    __syncwarp();
+    if (lane == 0) sm.nbuf = 0;
+    __syncwarp();
+}
+
+// (key, label) order of candidates: larger key first, then smaller label.
+__device__ __forceinline__ bool cand_better(unsigned long long k1, int32_t l1,
+                                            unsigned long long k2, int32_t l2) {
+    return k1 > k2 || (k1 == k2 && l1 < l2);
+}
+
+template <int MODE, typename PS>
+__global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs a, int k, int cls) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    PipeSm<MODE, PS> &sm = *reinterpret_cast<PipeSm<MODE, PS> *>(smraw);
+    constexpr int NT = PS::kNT, E = PS::kE, NW = NT / 32;
+    constexpr bool DENSE = MODE == kRefineDense;
+    const int32_t *list = a.pl[cls] + (int64_t)a.colour * a.nL;
+    const int cnt = a.pc[cls][a.colour];
+    const int G = gridDim.x;
+    int idx = blockIdx.x;
+    if (idx >= cnt) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (DENSE) {
+        for (int i = threadIdx.x; i < NW * kDenseMaxK; i += NT) (&sm.dacc[0][0])[i] = 0;
+        for (int b = threadIdx.x; b < k; b += NT) sm.W[b] = a.W[b];
+    } else {
+        for (int i = threadIdx.x; i < PS::kTS; i += NT) sm.tab[i] = kEmpty;
+    }
+    if (threadIdx.x == 0) sm.nbuf = 0;
+    // prologue: labels of row 0, entries of row 1, scalars of row 2, id of row 3
+    PipeRow cur = pipe_row<MODE>(a, list[idx]);
+    int32_t u[E], w[E], L[E], cpu[E];
+    pipe_entries<NT, E>(a, cur, u, w);
+    PipeRow nxt = pipe_row<MODE>(a, idx + G < cnt ? list[idx + G] : -1);
+    int32_t v3 = idx + 2 * G < cnt ? list[idx + 2 * G] : -1;
+    {
+        const int64_t deg = cur.re - cur.rs;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const bool in = (int)threadIdx.x + j * NT < deg;
+            L[j] = in ? __ldg(&a.lab[u[j]]) : 0;
+            cpu[j] = (MODE == kCluster && a.cp && in) ? __ldg(&a.cp[u[j]]) : cur.cpv;
+        }
+    }
+    int32_t w0[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) w0[j] = w[j];
+    pipe_entries<NT, E>(a, nxt, u, w);
+    PipeRow nn = pipe_row<MODE>(a, v3);
+    v3 = idx + 3 * G < cnt ? list[idx + 3 * G] : -1;
+    __syncthreads();
+    for (; idx < cnt; idx += G) {
+        // labels of the next row (its entries arrived during the last row)
+        const int64_t deg1 = nxt.re - nxt.rs;
+        int32_t L1[E], cpu1[E], w1[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const bool in = (int)threadIdx.x + j * NT < deg1;
+            L1[j] = in ? __ldg(&a.lab[u[j]]) : 0;
+            cpu1[j] = (MODE == kCluster && a.cp && in) ? __ldg(&a.cp[u[j]]) : nxt.cpv;
+            w1[j] = w[j];
+        }
+        // entries of the row after it, scalars of the third, id of the fourth
+        pipe_entries<NT, E>(a, nn, u, w);
+        const PipeRow n3 = pipe_row<MODE>(a, v3);
+        v3 = idx + 4 * G < cnt ? list[idx + 4 * G] : -1;
+        const int64_t deg = cur.re - cur.rs;
+        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)cur.v);
+        int64_t wown = 0;
+        if (MODE == kRefineHash && threadIdx.x == 0) wown = a.W[cur.own];
+        pipe_flush<MODE, PS>(a, sm, false);
+        // aggregation of the current row; a slot's creator gathers W(L)
+        const uint32_t tbits = deg <= 32 ? 6u : 33u - (uint32_t)__clz((int)(deg - 1));
+        const uint32_t tmask = (1u << tbits) - 1;
+        int32_t myslot[E];
+        int64_t WL[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            myslot[j] = -1;
+            WL[j] = 0;
+            const bool in = (int)threadIdx.x + j * NT < deg && cpu[j] == cur.cpv;
+            if (!in) continue;
+            if constexpr (DENSE) {
+                atomicAdd(&sm.dacc[warp][L[j]], w0[j]);
+            } else {
+                const unsigned long long key = (unsigned long long)(uint32_t)L[j] << 32;
+                uint32_t slot = ((uint32_t)L[j] * 0x9E3779B1u) >> (32 - tbits);
+                for (uint32_t probe = 0; probe <= tmask; probe++) {
+                    const unsigned long long prev =
+                        atomicCAS(&sm.tab[slot], kEmpty, key | (uint32_t)w0[j]);
+                    if (prev == kEmpty) {
+                        myslot[j] = (int32_t)slot;
+                        WL[j] = __ldg(&a.W[L[j]]);
+                        break;
+                    }
+                    if ((prev & 0xffffffff00000000ull) == key) {
+                        atomicAdd(&sm.tab[slot], (unsigned long long)(uint32_t)w0[j]);
+                        break;
+                    }
+                    slot = (slot + 1) & tmask;
+                }
+            }
+        }
+        __syncthreads();
+        // selection: the owners rate their slots (and empty them), or the k
+        // block sums
+        unsigned long long bk = 0;
+        int32_t bl = 0x7fffffff, ow = 0;
+        if constexpr (DENSE) {
+            if ((int)threadIdx.x < k) {
+                const int b = threadIdx.x;
+                int32_t tot = 0;
+#pragma unroll
+                for (int q = 0; q < NW; q++) {
+                    tot += sm.dacc[q][b];
+                    sm.dacc[q][b] = 0;
+                }
+                if (b == cur.own) ow = tot;
+                else if (tot > 0 && sm.W[b] + cur.c <= bnd(a, b)) {
+                    bk = cand_key(tot, h, b);
+                    bl = b;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; j++) {
+                if (myslot[j] < 0) continue;
+                const unsigned long long x = sm.tab[myslot[j]];
+                sm.tab[myslot[j]] = kEmpty;
+                const int32_t wx = (int32_t)(uint32_t)x;
+                if (L[j] == cur.own) {
+                    ow = wx;
+                } else if (WL[j] + cur.c <= bnd(a, L[j])) {
+                    const unsigned long long ck = cand_key(wx, h, L[j]);
+                    if (cand_better(ck, L[j], bk, bl)) {
+                        bk = ck;
+                        bl = L[j];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, d);
+            const int32_t ol = __shfl_xor_sync(0xffffffffu, bl, d);
+            if (cand_better(ok, ol, bk, bl)) {
+                bk = ok;
+                bl = ol;
+            }
+            ow += __shfl_xor_sync(0xffffffffu, ow, d);
+        }
+        if (lane == 0) {
+            sm.wk[warp] = bk;
+            sm.wl[warp] = bl;
+            sm.wo[warp] = ow;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < NW; q++) {
+                if (cand_better(sm.wk[q], sm.wl[q], bk, bl)) {
+                    bk = sm.wk[q];
+                    bl = sm.wl[q];
+                }
+                ow += sm.wo[q];
+            }
+            if (bk != 0) {
+                const int32_t gain = (int32_t)(bk >> 32) - ow;
+                bool ovl = false;
+                if (MODE == kRefineDense) ovl = sm.W[cur.own] > bnd(a, cur.own);
+                if (MODE == kRefineHash) ovl = wown > bnd(a, cur.own);
+                if (gain > 0 || ovl) {
+                    const int i = sm.nbuf++;
+                    sm.bv[i] = cur.v;
+                    sm.bT[i] = bl;
+                    sm.bown[i] = cur.own;
+                    sm.bgain[i] = gain;
+                    sm.bc[i] = cur.c;
+                    sm.bovl[i] = ovl ? 1 : 0;
+                }
+            }
+        }
+        cur = nxt;
+        nxt = nn;
+        nn = n3;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            L[j] = L1[j];
+            cpu[j] = cpu1[j];
+            w0[j] = w1[j];
+        }
+    }
+    pipe_flush<MODE, PS>(a, sm, true);
 }
 
 // Medium rows (33..kMedDeg entries): one warp per row with a warp-private
@@ -2208,11 +2505,40 @@ static int row_grid(int sms) {
     return sms * std::max(1, occ);
 }
 
+template <int MODE, typename PS>
+static int pipe_grid(int sms) {
+    const size_t smem = sizeof(PipeSm<MODE, PS>);
+    CK(cudaFuncSetAttribute(k_propose_pipe<MODE, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose_pipe<MODE, PS>, PS::kNT,
+                                                     smem));
+    return sms * std::max(1, occ);
+}
+
+struct RowGrids {
+    int big, p[kPipeClasses];
+};
+
 template <int MODE>
-static void launch_rows(const LPArgs &a, int k, int grid_mid, int grid_big, cudaStream_t s) {
-    k_propose<MODE, MidRows><<<grid_mid, MidRows::kNT, sizeof(PropSm<MODE, MidRows>), s>>>(a, k);
+static RowGrids row_grids(int sms) {
+    return RowGrids{row_grid<MODE, BigRows>(sms),
+                    {pipe_grid<MODE, PipeA>(sms), pipe_grid<MODE, PipeB>(sms),
+                     pipe_grid<MODE, PipeC>(sms)}};
+}
+
+// Rows above kMedDeg: the pipelined kernels of the two shorter classes and
+// then the pieces on stream s, the longest pipelined class on s2.
+template <int MODE>
+static void launch_rows(const LPArgs &a, int k, const RowGrids &rg, cudaStream_t s,
+                        cudaStream_t s2) {
+    k_propose_pipe<MODE, PipeC><<<rg.p[2], PipeC::kNT, sizeof(PipeSm<MODE, PipeC>), s2>>>(a, k, 2);
     LAUNCHED();
-    k_propose<MODE, BigRows><<<grid_big, BigRows::kNT, sizeof(PropSm<MODE, BigRows>), s>>>(a, k);
+    k_propose_pipe<MODE, PipeA><<<rg.p[0], PipeA::kNT, sizeof(PipeSm<MODE, PipeA>), s>>>(a, k, 0);
+    LAUNCHED();
+    k_propose_pipe<MODE, PipeB><<<rg.p[1], PipeB::kNT, sizeof(PipeSm<MODE, PipeB>), s>>>(a, k, 1);
+    LAUNCHED();
+    k_propose<MODE, BigRows><<<rg.big, BigRows::kNT, sizeof(PropSm<MODE, BigRows>), s>>>(a, k);
     LAUNCHED();
 }
 
@@ -2268,14 +2594,14 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.bar_cycles = kBarCycles;
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
     // bucket lengths, then piece counts, then cluster-path row counts (per colour)
-    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + 3 * S);
+    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + (2 + kPipeClasses) * S);
     Ctr *ctr = sc.get<Ctr>(S);
     int64_t *d_moves = sc.zeros<int64_t>(cfg.rounds);
     a.wl = wl;
     a.wl_cnt = wl_cnt;
     a.pcnt = wl_cnt + kClasses * S;
     a.hcnt = wl_cnt + kClasses * S + S;
-    a.mcnt = wl_cnt + kClasses * S + 2 * S;
+    for (int q = 0; q < kPipeClasses; q++) a.pc[q] = wl_cnt + kClasses * S + (2 + q) * S;
     a.huge_on = mode != kRefineDense;
     a.prof = prof().on ? prof().d_counts : nullptr;
 
@@ -2301,7 +2627,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             CK(cudaStreamSynchronize(s));
             a.plist = sc.get<int64_t>((size_t)S * (a.Ptot ? a.Ptot : 1));
             a.hlist = sc.get<int32_t>((size_t)S * nL);
-            a.mlist = sc.get<int64_t>((size_t)S * nL);
+            for (int q = 0; q < kPipeClasses; q++) a.pl[q] = sc.get<int32_t>((size_t)S * nL);
             a.Ldone = sc.zeros<int32_t>(nL);
             a.Lndl = sc.zeros<int32_t>(nL);
             if (mode == kRefineDense) {
@@ -2335,14 +2661,11 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         }
     }
 
-    int grid_mid = 0, grid_big = 0;
+    RowGrids rgrids{};
     switch (mode) {
-        case kCluster: grid_mid = row_grid<kCluster, MidRows>(sms);
-                       grid_big = row_grid<kCluster, BigRows>(sms); break;
-        case kRefineHash: grid_mid = row_grid<kRefineHash, MidRows>(sms);
-                          grid_big = row_grid<kRefineHash, BigRows>(sms); break;
-        default: grid_mid = row_grid<kRefineDense, MidRows>(sms);
-                 grid_big = row_grid<kRefineDense, BigRows>(sms); break;
+        case kCluster: rgrids = row_grids<kCluster>(sms); break;
+        case kRefineHash: rgrids = row_grids<kRefineHash>(sms); break;
+        default: rgrids = row_grids<kRefineDense>(sms); break;
     }
     CK(cudaFuncSetAttribute(k_arbitrate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)sizeof(ArbSm)));
@@ -2380,7 +2703,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             a.active = act;
             a.round = r;
             a.moves = d_moves + r;
-            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + 3 * S) * sizeof(int32_t), s));
+            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + (2 + kPipeClasses) * S) * sizeof(int32_t), s));
             CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
             k_build_wl<<<sms * 4, kThreads, 0, s>>>(a, wl, wl_cnt);
             LAUNCHED();
@@ -2399,25 +2722,26 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 }
                 LAUNCHED();
                 CK(cudaEventRecord(ev_join, side));
-                if (huge) {
-                    // rows of one CTA cluster on a second side stream
+                if (a.nL > 0) {
+                    // rows of one CTA cluster and the 256-thread pipelined
+                    // rows on a second side stream
                     CK(cudaStreamWaitEvent(side2, ev_fork, 0));
-                    if (mode == kCluster)
-                        k_propose_huge<kCluster><<<grid_huge, kThreads, 0, side2>>>(a);
-                    else
-                        k_propose_huge<kRefineHash><<<grid_huge, kThreads, 0, side2>>>(a);
-                    LAUNCHED();
+                    if (huge) {
+                        if (mode == kCluster)
+                            k_propose_huge<kCluster><<<grid_huge, kThreads, 0, side2>>>(a);
+                        else
+                            k_propose_huge<kRefineHash><<<grid_huge, kThreads, 0, side2>>>(a);
+                        LAUNCHED();
+                    }
+                    switch (mode) {
+                        case kCluster: launch_rows<kCluster>(a, k, rgrids, s, side2); break;
+                        case kRefineHash: launch_rows<kRefineHash>(a, k, rgrids, s, side2); break;
+                        default: launch_rows<kRefineDense>(a, k, rgrids, s, side2); break;
+                    }
                     CK(cudaEventRecord(ev_join2, side2));
                 }
-                if (a.nL > 0) {
-                    switch (mode) {
-                        case kCluster: launch_rows<kCluster>(a, k, grid_mid, grid_big, s); break;
-                        case kRefineHash: launch_rows<kRefineHash>(a, k, grid_mid, grid_big, s); break;
-                        default: launch_rows<kRefineDense>(a, k, grid_mid, grid_big, s); break;
-                    }
-                }
                 CK(cudaStreamWaitEvent(s, ev_join, 0));
-                if (huge) CK(cudaStreamWaitEvent(s, ev_join2, 0));
+                if (a.nL > 0) CK(cudaStreamWaitEvent(s, ev_join2, 0));
                 prof_end(s, pb, pe);
                 if (hub_items > 0) {
                     const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
