@@ -337,6 +337,18 @@ const char *sclap_strerror(int code);
  * weights, omega > 0, c >= 0.  Returns the previous setting. */
 int sclap_set_validation(int on);
 
+/* How the SCLaP rounds of a call are launched (no effect on results):
+ *   0  one round at a time; the host reads the round's move count and stops
+ *      the run after a full round without moves
+ *   1  every round enqueued ahead; that test runs on the device and sets a
+ *      flag after which the kernels of later rounds return at once
+ *   2  (default) as 1, the rounds captured in one CUDA graph on a private
+ *      stream that joins `stream`; while instrumentation is on, or if the
+ *      runtime refuses the capture, the rounds are launched as in 1
+ * Learned refinement always runs as 0.  Values outside 0..2 are clamped.
+ * Returns the previous mode. */
+int sclap_set_launch_mode(int mode);
+
 /* Instrumentation.  When enabled, the library brackets every launch of the
  * neighbour-aggregation (propose) kernel with CUDA events on its stream and
  * counts the algorithmic bytes it must move (12 B per scanned entry: adjncy,
@@ -350,6 +362,7 @@ typedef struct {
     int64_t entries_scanned;      /* directed entries aggregated                  */
     int64_t nodes_visited;
     int64_t kernel_launches;      /* every kernel this library launched           */
+    int64_t graph_launches;       /* CUDA graphs launched (captured rounds)       */
 } sclap_prof;
 void sclap_prof_enable(int on);
 void sclap_prof_reset(void);

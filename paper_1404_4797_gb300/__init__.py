@@ -69,7 +69,8 @@ class MLStats(C.Structure):
 class Prof(C.Structure):
     _fields_ = [("propose_launches", C.c_int64), ("propose_ms", C.c_double),
                 ("propose_bytes", C.c_double), ("entries_scanned", C.c_int64),
-                ("nodes_visited", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("nodes_visited", C.c_int64), ("kernel_launches", C.c_int64),
+                ("graph_launches", C.c_int64)]
 
 
 _P64 = C.POINTER(C.c_int64)
@@ -80,6 +81,7 @@ _VP = C.c_void_p
 _SIGS = {
     "sclap_strerror": (C.c_char_p, [C.c_int]),
     "sclap_set_validation": (C.c_int, [C.c_int]),
+    "sclap_set_launch_mode": (C.c_int, [C.c_int]),
     "sclap_ml_defaults": (None, [C.POINTER(MLParams), C.c_int32, C.c_double, C.c_uint64]),
     "sclap_cluster": (C.c_int, [C.POINTER(Graph), C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
                                 _VP, _VP, _P32, _VP]),
@@ -178,6 +180,13 @@ def _require_cuda(*ts):
 
 def set_validation(on: bool) -> bool:
     return bool(lib().sclap_set_validation(1 if on else 0))
+
+
+def set_launch_mode(mode: int) -> int:
+    """How a call's SCLaP rounds are launched (0 one round at a time, 1 all
+    enqueued ahead, 2 captured in a CUDA graph; results do not depend on it).
+    Returns the previous mode."""
+    return int(lib().sclap_set_launch_mode(int(mode)))
 
 
 def sclap_cluster(g: dict, U: int, rounds: int, subrounds: int = 4, seed: int = 1,

@@ -468,6 +468,8 @@ const char *sclap_strerror(int code) {
     }
 }
 
+int sclap_set_launch_mode(int mode) { return set_launch_mode(mode); }
+
 int sclap_set_validation(int on) {
     int old = g_validate ? 1 : 0;
     g_validate = on != 0;
@@ -1084,6 +1086,7 @@ int sclap_prof_read(sclap_prof *out) {
         out->nodes_visited = (int64_t)c[1];
         out->propose_bytes = 12.0 * (double)c[0] + 24.0 * (double)c[1];
         out->kernel_launches = P.kernel_launches;
+        out->graph_launches = P.graph_launches;
     });
 }
 

@@ -32,6 +32,7 @@ inline void cuda_check(cudaError_t e, const char *what) {
 // ---------------------------------------------------------------- launch accounting
 
 void count_launch();
+void count_graph_launch();
 // After every kernel launch: record it and surface launch-configuration errors.
 #define LAUNCHED() do { ::sclap::count_launch(); CK(cudaGetLastError()); } while (0)
 
@@ -116,6 +117,7 @@ struct ProfState {
     bool on = false;
     int64_t propose_launches = 0;
     int64_t kernel_launches = 0;
+    int64_t graph_launches = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // recorded, not yet read
     double propose_ms = 0;
     // device-side counters of entries / nodes processed by the timed kernel

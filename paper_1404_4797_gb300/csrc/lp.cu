@@ -43,6 +43,7 @@
 #include <cooperative_groups/reduce.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "lp.cuh"
@@ -187,7 +188,12 @@ struct LPArgs {
     long long bar_cycles;      // bound of every grid-barrier wait (SM clock cycles)
     int32_t maxbig, maxtiles;
     const uint8_t *active;     // learned refinement: rows visited this round (null: all)
+    const int32_t *stop;       // device flag: the run has ended (every round kernel returns)
 };
+
+// Every kernel of a round returns at once after the run has ended (the rounds
+// of a call are enqueued, or captured in a CUDA graph, ahead of time).
+__device__ __forceinline__ bool stopped(const LPArgs &a) { return a.stop && *(volatile const int32_t *)a.stop; }
 
 // Bound of label L (U, L_max, or the run's L_max in batched runs).
 __device__ __forceinline__ int64_t bnd(const LPArgs &a, int64_t L) {
@@ -267,6 +273,7 @@ __device__ __forceinline__ int degree_class(int64_t d) {
 __device__ __forceinline__ int pipe_class(int64_t d) { return d <= 512 ? 0 : d <= 1024 ? 1 : 2; }
 
 __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, int32_t *cnt) {
+    if (stopped(a)) return;
     __shared__ int lcnt[32 * kClasses], lbase[32 * kClasses];
     const DGraph &g = a.g;
     const int S = a.S;
@@ -823,6 +830,7 @@ __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
 // CTA rows: the pieces listed in plist (rows above kMidDeg).
 template <int MODE, typename RS>
 __global__ void __launch_bounds__(RS::kNT) k_propose(LPArgs a, int k) {
+    if (stopped(a)) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     PropSm<MODE, RS> &sm = *reinterpret_cast<PropSm<MODE, RS> *>(smraw);
     if (a.nL == 0) return;
@@ -950,6 +958,7 @@ __device__ __forceinline__ bool cand_better(unsigned long long k1, int32_t l1,
 
 template <int MODE, typename PS>
 __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs a, int k, int cls) {
+    if (stopped(a)) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     PipeSm<MODE, PS> &sm = *reinterpret_cast<PipeSm<MODE, PS> *>(smraw);
     constexpr int NT = PS::kNT, E = PS::kE, NW = NT / 32;
@@ -1259,6 +1268,7 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
 // and then medium rows (a warp per row).  Runs next to k_propose (side stream).
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 4) k_propose_small(LPArgs a, int k) {
+    if (stopped(a)) return;
     __shared__ int64_t W[kDenseMaxK];
     __shared__ WarpTab tabs[MODE == kRefineDense ? 1 : kThreads / 32];
     __shared__ int32_t dacc[MODE == kRefineDense ? kThreads / 32 : 1][kDenseMaxK];
@@ -1569,6 +1579,7 @@ __device__ __forceinline__ int64_t admit_segment(const LPArgs &a, WDelta &wd, co
 // blockIdx < nW handle block b = blockIdx when its departures are contested;
 // the others pass the uncontested sources' proposals through.
 __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
+    if (stopped(a)) return;
     __shared__ unsigned long long hist[kBins];
     __shared__ unsigned long long red[96];
     __shared__ int64_t scan_tmp[kThreads / 32 + 1];
@@ -1617,6 +1628,7 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
+    if (stopped(a)) return;
     __shared__ WDelta wd;
     wd_init(wd, a.nW);
     const int nprop = a.ctr->nprop;
@@ -1657,6 +1669,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
+    if (stopped(a)) return;
     const int nprop = a.ctr->nprop;
     if (a.ctr->nseg == 0) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nprop;
@@ -1926,6 +1939,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
 // Launched cooperatively (all CTAs resident): segments of <= 32 entries take
 // one warp, up to kSegSmem one CTA, longer ones the whole grid.
 __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
+    if (stopped(a)) return;  // the same in every CTA, before any grid barrier
     extern __shared__ __align__(16) unsigned char smraw[];
     ArbSm &sm = *reinterpret_cast<ArbSm *>(smraw);
     wd_init(sm.wd, a.nW);
@@ -1990,6 +2004,7 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
 
 // Clears the per-target (and per-source) accumulators touched this sub-round.
 __global__ void __launch_bounds__(kThreads) k_reset_targets(LPArgs a) {
+    if (stopped(a)) return;
     const int nprop = a.ctr->nprop;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nprop;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -2034,6 +2049,7 @@ __device__ __forceinline__ HubItem hub_item(const LPArgs &a, int64_t t, int roun
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
+    if (stopped(a)) return;
     __shared__ unsigned long long red[kThreads / 32];
     const int64_t items = a.Hfin[a.nL];
     for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
@@ -2072,6 +2088,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
+    if (stopped(a)) return;
     const int64_t items = a.Hfin[a.nL];
     for (int64_t t = blockIdx.x; t < items; t += gridDim.x) {
         const HubItem it = hub_item(a, t, a.round);
@@ -2097,6 +2114,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
+    if (stopped(a)) return;
     for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < a.nL;
          li += (int64_t)gridDim.x * blockDim.x) {
         if (a.Hfin[li + 1] == a.Hfin[li]) continue;  // single-piece row
@@ -2162,6 +2180,7 @@ __device__ __forceinline__ void huge_insert(cg::cluster_group &cl, HugeSm &sm, u
 template <int MODE>
 __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
     k_propose_huge(LPArgs a) {
+    if (stopped(a)) return;  // the same in every CTA of the cluster
     __shared__ HugeSm sm;
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
@@ -2542,6 +2561,66 @@ static void launch_rows(const LPArgs &a, int k, const RowGrids &rg, cudaStream_t
     LAUNCHED();
 }
 
+// End of round r: the errors of its sub-rounds are kept, the rounds done
+// counted, and the run stops after a full round without moves.
+__global__ void k_round_end(const int64_t *moves_r, const Ctr *ctr, int S, int32_t *st, int r,
+                            int full) {
+    if (st[0]) return;
+    int32_t err = 0;
+    for (int j = 0; j < S; j++) err |= ctr[j].err;
+    st[2] |= err;
+    st[1] = r + 1;
+    if (*moves_r == 0 && full) st[0] = 1;
+}
+
+static std::atomic<int> g_launch_mode{2};
+int launch_mode() { return g_launch_mode.load(); }
+int set_launch_mode(int mode) { return g_launch_mode.exchange(mode < 0 ? 0 : mode > 2 ? 2 : mode); }
+
+// Captures what enqueue(cs) puts on a private stream cs (and on the streams
+// it forks from cs) into one CUDA graph and launches it after the work already
+// on s; s then waits for the graph.  Returns false, with nothing launched, if
+// capture or instantiation is refused (the caller then enqueues directly).
+template <class F>
+static bool run_captured(cudaStream_t s, F &&enqueue) {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        try {
+            enqueue(cs);
+        } catch (...) {
+            ok = false;
+        }
+        const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        ok = ok && e == cudaSuccess && graph != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    cudaGetLastError();  // a refused capture leaves no sticky error
+    bool launched = false;
+    if (ok) {
+        CK(cudaEventRecord(e0, s));
+        CK(cudaStreamWaitEvent(cs, e0, 0));
+        CK(cudaGraphLaunch(exec, cs));
+        count_graph_launch();
+        CK(cudaEventRecord(e1, cs));
+        CK(cudaStreamWaitEvent(s, e1, 0));
+        CK(cudaStreamSynchronize(cs));
+        launched = true;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(cs);
+    return launched;
+}
+
 int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, int64_t *W_out) {
     cudaStream_t s = sc.stream();
     const DGraph &g = cfg.g;
@@ -2669,6 +2748,9 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     }
     CK(cudaFuncSetAttribute(k_arbitrate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)sizeof(ArbSm)));
+    // the occupancy below assumes the largest shared-memory carveout
+    CK(cudaFuncSetAttribute(k_arbitrate, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            (int)cudaSharedmemCarveoutMaxShared));
     const int grid_small = sms * 4;
     int occ_arb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_arb, k_arbitrate, kThreads,
@@ -2693,96 +2775,145 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     }
     const int grid_sm = sms * std::max(1, occ_small);
 
-    int done = 0;
-    int64_t hmoves = 0;
-    try {
-        for (int r = 0; r < cfg.rounds; r++) {
-            bool full = true;
-            const uint8_t *act = nullptr;
-            if (cfg.before_round) full = cfg.before_round(r, &act);
-            a.active = act;
-            a.round = r;
-            a.moves = d_moves + r;
-            CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + (2 + kPipeClasses) * S) * sizeof(int32_t), s));
-            CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), s));
-            k_build_wl<<<sms * 4, kThreads, 0, s>>>(a, wl, wl_cnt);
+    // Round r: worklists, then S sub-rounds of propose (fork-join over three
+    // streams) and arbitration, then the end-of-round test on the device.
+    int32_t *d_state = sc.zeros<int32_t>(3);  // [0] stop flag, [1] rounds done, [2] errors
+    auto enqueue_round = [&](int r, bool full, cudaStream_t ms) {
+        a.round = r;
+        a.moves = d_moves + r;
+        CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + (2 + kPipeClasses) * S) * sizeof(int32_t), ms));
+        CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), ms));
+        k_build_wl<<<sms * 4, kThreads, 0, ms>>>(a, wl, wl_cnt);
+        LAUNCHED();
+        for (int j = 0; j < S; j++) {
+            a.ctr = ctr + j;
+            a.colour = j;
+            cudaEvent_t pb, pe;
+            prof_begin(ms, &pb, &pe);
+            // small rows on the side stream, next to the large and medium rows
+            CK(cudaEventRecord(ev_fork, ms));
+            CK(cudaStreamWaitEvent(side, ev_fork, 0));
+            switch (mode) {
+                case kCluster: k_propose_small<kCluster><<<grid_sm, kThreads, 0, side>>>(a, k); break;
+                case kRefineHash: k_propose_small<kRefineHash><<<grid_sm, kThreads, 0, side>>>(a, k); break;
+                default: k_propose_small<kRefineDense><<<grid_sm, kThreads, 0, side>>>(a, k); break;
+            }
             LAUNCHED();
-            for (int j = 0; j < S; j++) {
-                a.ctr = ctr + j;
-                a.colour = j;
-                cudaEvent_t pb, pe;
-                prof_begin(s, &pb, &pe);
-                // small rows on the side stream, next to the large and medium rows
-                CK(cudaEventRecord(ev_fork, s));
-                CK(cudaStreamWaitEvent(side, ev_fork, 0));
+            CK(cudaEventRecord(ev_join, side));
+            if (a.nL > 0) {
+                // rows of one CTA cluster and the 256-thread pipelined
+                // rows on a second side stream
+                CK(cudaStreamWaitEvent(side2, ev_fork, 0));
+                if (huge) {
+                    if (mode == kCluster)
+                        k_propose_huge<kCluster><<<grid_huge, kThreads, 0, side2>>>(a);
+                    else
+                        k_propose_huge<kRefineHash><<<grid_huge, kThreads, 0, side2>>>(a);
+                    LAUNCHED();
+                }
                 switch (mode) {
-                    case kCluster: k_propose_small<kCluster><<<grid_sm, kThreads, 0, side>>>(a, k); break;
-                    case kRefineHash: k_propose_small<kRefineHash><<<grid_sm, kThreads, 0, side>>>(a, k); break;
-                    default: k_propose_small<kRefineDense><<<grid_sm, kThreads, 0, side>>>(a, k); break;
+                    case kCluster: launch_rows<kCluster>(a, k, rgrids, ms, side2); break;
+                    case kRefineHash: launch_rows<kRefineHash>(a, k, rgrids, ms, side2); break;
+                    default: launch_rows<kRefineDense>(a, k, rgrids, ms, side2); break;
+                }
+                CK(cudaEventRecord(ev_join2, side2));
+            }
+            CK(cudaStreamWaitEvent(ms, ev_join, 0));
+            if (a.nL > 0) CK(cudaStreamWaitEvent(ms, ev_join2, 0));
+            prof_end(ms, pb, pe);
+            if (hub_items > 0) {
+                const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
+                switch (mode) {
+                    case kCluster:
+                        k_hub_cand<kCluster><<<hg, kThreads, 0, ms>>>(a);
+                        k_hub_tie<kCluster><<<hg, kThreads, 0, ms>>>(a);
+                        k_hub_emit<kCluster><<<sms, kThreads, 0, ms>>>(a);
+                        break;
+                    default:
+                        k_hub_cand<kRefineHash><<<hg, kThreads, 0, ms>>>(a);
+                        k_hub_tie<kRefineHash><<<hg, kThreads, 0, ms>>>(a);
+                        k_hub_emit<kRefineHash><<<sms, kThreads, 0, ms>>>(a);
+                        break;
                 }
                 LAUNCHED();
-                CK(cudaEventRecord(ev_join, side));
-                if (a.nL > 0) {
-                    // rows of one CTA cluster and the 256-thread pipelined
-                    // rows on a second side stream
-                    CK(cudaStreamWaitEvent(side2, ev_fork, 0));
-                    if (huge) {
-                        if (mode == kCluster)
-                            k_propose_huge<kCluster><<<grid_huge, kThreads, 0, side2>>>(a);
-                        else
-                            k_propose_huge<kRefineHash><<<grid_huge, kThreads, 0, side2>>>(a);
-                        LAUNCHED();
-                    }
-                    switch (mode) {
-                        case kCluster: launch_rows<kCluster>(a, k, rgrids, s, side2); break;
-                        case kRefineHash: launch_rows<kRefineHash>(a, k, rgrids, s, side2); break;
-                        default: launch_rows<kRefineDense>(a, k, rgrids, s, side2); break;
-                    }
-                    CK(cudaEventRecord(ev_join2, side2));
-                }
-                CK(cudaStreamWaitEvent(s, ev_join, 0));
-                if (a.nL > 0) CK(cudaStreamWaitEvent(s, ev_join2, 0));
-                prof_end(s, pb, pe);
-                if (hub_items > 0) {
-                    const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);
-                    switch (mode) {
-                        case kCluster:
-                            k_hub_cand<kCluster><<<hg, kThreads, 0, s>>>(a);
-                            k_hub_tie<kCluster><<<hg, kThreads, 0, s>>>(a);
-                            k_hub_emit<kCluster><<<sms, kThreads, 0, s>>>(a);
-                            break;
-                        default:
-                            k_hub_cand<kRefineHash><<<hg, kThreads, 0, s>>>(a);
-                            k_hub_tie<kRefineHash><<<hg, kThreads, 0, s>>>(a);
-                            k_hub_emit<kRefineHash><<<sms, kThreads, 0, s>>>(a);
-                            break;
-                    }
-                    LAUNCHED();
-                    LAUNCHED();
-                    LAUNCHED();
-                }
-                if (cfg.refine) {
-                    k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, s>>>(a);
-                    LAUNCHED();
-                }
-                k_classify<<<grid_small, kThreads, 0, s>>>(a);
                 LAUNCHED();
-                k_scatter<<<grid_small, kThreads, 0, s>>>(a);
-                LAUNCHED();
-                {
-                    void *args[] = {&a};
-                    CK(cudaLaunchCooperativeKernel((const void *)k_arbitrate, dim3(grid_arb),
-                                                   dim3(kThreads), args, sizeof(ArbSm), s));
-                }
-                LAUNCHED();
-                k_reset_targets<<<grid_small, kThreads, 0, s>>>(a);
                 LAUNCHED();
             }
-            CK(cudaMemcpyAsync(&hmoves, d_moves + r, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            if (cfg.refine) {
+                k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, ms>>>(a);
+                LAUNCHED();
+            }
+            k_classify<<<grid_small, kThreads, 0, ms>>>(a);
+            LAUNCHED();
+            k_scatter<<<grid_small, kThreads, 0, ms>>>(a);
+            LAUNCHED();
+            {
+                // cooperative: every CTA resident (the grid barrier needs it),
+                // also as a node of a captured graph
+                cudaLaunchConfig_t lc = {};
+                lc.gridDim = dim3(grid_arb);
+                lc.blockDim = dim3(kThreads);
+                lc.dynamicSmemBytes = sizeof(ArbSm);
+                lc.stream = ms;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                lc.attrs = at;
+                lc.numAttrs = 1;
+                CK(cudaLaunchKernelEx(&lc, k_arbitrate, a));
+            }
+            LAUNCHED();
+            k_reset_targets<<<grid_small, kThreads, 0, ms>>>(a);
+            LAUNCHED();
+        }
+        k_round_end<<<1, 1, 0, ms>>>(d_moves + r, ctr, S, d_state, r, full ? 1 : 0);
+        LAUNCHED();
+    };
+
+    int done = 0;
+    try {
+        const int lm = launch_mode();
+        if (cfg.before_round || lm == 0) {
+            // one round at a time, the host testing the stop rule after each
+            // (always for learned refinement: the host prepares every round's
+            // features and gate)
+            for (int r = 0; r < cfg.rounds; r++) {
+                const uint8_t *act = nullptr;
+                const bool full = cfg.before_round ? cfg.before_round(r, &act) : true;
+                a.active = act;
+                enqueue_round(r, full, s);
+                int64_t hmoves = 0;
+                CK(cudaMemcpyAsync(&hmoves, d_moves + r, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                done = r + 1;
+                if (hmoves == 0 && full) break;
+            }
+        } else {
+            // every round is enqueued ahead: a round without moves sets the
+            // stop flag and the kernels of later rounds return at once.  The
+            // rounds are captured in one CUDA graph when capture is on (and
+            // profiling, which times propose steps with events, is off).
+            a.stop = d_state;
+            bool ran = false;
+            if (lm == 2 && !prof().on)
+                ran = run_captured(s, [&](cudaStream_t cs) {
+                    for (int r = 0; r < cfg.rounds; r++) enqueue_round(r, true, cs);
+                });
+            if (!ran)
+                for (int r = 0; r < cfg.rounds; r++) enqueue_round(r, true, s);
+        }
+        int32_t hs[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync(hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!cfg.before_round && lm != 0) done = hs[1];
+        if (hs[2] & kErrTable) fail(SCLAP_ECUDA, "hash table overflow");
+        if (hs[2] & kErrBarrier) fail(SCLAP_ETIMEOUT, "grid barrier timed out in arbitration");
+        if (hs[2] & kErrBig) fail(SCLAP_ECUDA, "long-segment capacity exceeded");
+        if (moves_out && done > 0) {
+            moves_out->resize(done);
+            CK(cudaMemcpyAsync(moves_out->data(), d_moves, done * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            done = r + 1;
-            if (moves_out) moves_out->push_back(hmoves);
-            if (hmoves == 0 && full) break;
         }
     } catch (...) {
         cudaStreamSynchronize(side);
@@ -2801,14 +2932,6 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     CK(cudaEventDestroy(ev_join2));
     CK(cudaStreamDestroy(side));
     CK(cudaStreamDestroy(side2));
-    Ctr hc[32];
-    CK(cudaMemcpyAsync(hc, ctr, S * sizeof(Ctr), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (int j = 0; j < S; j++) {
-        if (hc[j].err & kErrTable) fail(SCLAP_ECUDA, "hash table overflow");
-        if (hc[j].err & kErrBarrier) fail(SCLAP_ETIMEOUT, "grid barrier timed out in arbitration");
-        if (hc[j].err & kErrBig) fail(SCLAP_ECUDA, "long-segment capacity exceeded");
-    }
     return done;
 }
 

@@ -34,6 +34,13 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves, int64_
 // <= U in id order (per block of cp when given); see pack_isolated in lp.cu.
 void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, Scratch &sc);
 
+// How a call's LP rounds are launched (results do not depend on it): 0 one
+// round at a time, the host testing the stop rule; 1 all rounds enqueued
+// ahead, a device flag ending them; 2 (default) as 1, captured in one CUDA
+// graph.  set_launch_mode returns the previous mode.
+int launch_mode();
+int set_launch_mode(int mode);
+
 // Runs the arbitration kernel's bounded grid barrier with one of two CTAs
 // absent, so the wait must give up after limit_cycles; returns SCLAP_ETIMEOUT
 // when it did (the expected result) and SCLAP_OK if it did not.

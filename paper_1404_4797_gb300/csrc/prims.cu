@@ -8,12 +8,14 @@ namespace sclap {
 
 // ---------------------------------------------------------------- accounting
 
-static std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_launches{0}, g_graph_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_graph_launch() { g_graph_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static ProfState g_prof;
 ProfState &prof() {
     g_prof.kernel_launches = g_launches.load();
+    g_prof.graph_launches = g_graph_launches.load();
     return g_prof;
 }
 

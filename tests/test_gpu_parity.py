@@ -317,3 +317,37 @@ def test_vcycle_matches_oracle(name):
                                 torch.from_numpy(p0).cuda())
     assert np.array_equal(still.cpu().numpy(), p0) and st0["init_best"] == -1
 
+
+
+def test_rounds_identical_in_every_launch_mode():
+    """The rounds of a call run one at a time, enqueued ahead with a device
+    stop flag, or from one captured CUDA graph; all must end after the same
+    round with the same result."""
+    import paper_1404_4797_gb300 as S
+    g = I.rmat(13, 16, seed=4)
+    gd = I.to_device(g, "cuda")
+    n = g["vwgt"].numel()
+    p0 = I.rand_below(9, 7, torch.arange(n), 8).to(torch.int32).cuda()
+    prm = S.default_params(8, 0.03, seed=3, n_stop=300)
+    out = {}
+    old = S.set_launch_mode(2)
+    try:
+        for mode in (0, 1, 2):
+            S.set_launch_mode(mode)
+            lab, rd = S.sclap_cluster(gd, 40, 8, 4, 11)
+            part, cut, bw, rdr = S.sclap_refine(gd, 8, 0.03, 40, 4, 5, p0)
+            mp, st = S.partition_multilevel(gd, prm)
+            out[mode] = (lab.cpu().numpy(), rd, part.cpu().numpy(), cut, rdr, mp.cpu().numpy(),
+                         st["cut"], st["refine_rounds_done"], st["cluster_rounds_done"])
+    finally:
+        S.set_launch_mode(old)
+    for mode in (1, 2):
+        for x, y in zip(out[0], out[mode]):
+            if isinstance(x, np.ndarray):
+                assert np.array_equal(x, y)
+            else:
+                assert x == y
+    # the refinement converged after 18 of its 40 rounds (the oracle's count):
+    # the stop rule ended it
+    gn = I.to_numpy(g)
+    assert out[2][4] == oracle.refine(gn, 8, 0.03, 40, 4, 5, p0.cpu().numpy())[3] < 40
