@@ -352,51 +352,61 @@ def run_vcycle(args, cfg, S, I, g, n, m, dev):
 
 def run_batched(args, S, I, dev):
     """Batched population (the stand-in for the paper's evolutionary initial
-    partitioner): 32 coarse graphs, 256 seeded runs (graph (s - 1) mod 32), LPT
-    starts and r refinement rounds as one batched call; best run per graph."""
+    partitioner): 32 coarse graphs, 256 seeded runs (seed s = 1..256 on graph
+    (s - 1) mod 32), LPT starts and r refinement rounds as one batched call
+    (its rounds captured in one CUDA graph); best run per graph.  The plain
+    form runs the same 256 (graph, seed) runs as 256 separate calls; every run
+    is independent of its batch, so both forms compute the same partitions."""
     import torch
     graphs = I.population(32, 2000, 200000, seed=1, device=dev)
     nodes = sum(int(g["vwgt"].numel()) for g in graphs)
     entries = sum(int(g["adjncy"].numel()) for g in graphs)
-    rg = [s % 32 for s in range(256)]
+    seeds = list(range(1, 257))
+    rg = [(s - 1) % 32 for s in seeds]
     k, eps, rounds, sub = 16, 0.03, 6, 4
     S.set_validation(False)
+
+    def timed(fn, reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            out = fn()
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1) / reps, out
+
+    batched = lambda: S.sclap_refine_batched(graphs, k, eps, rounds, sub, seeds, rg)
+    plain = lambda: [S.sclap_refine_batched([graphs[g]], k, eps, rounds, sub, [sd], [0])
+                     for sd, g in zip(seeds, rg)]
     for _ in range(args.warmup):
-        S.sclap_refine_batched(graphs, k, eps, rounds, sub, 1, rg)
+        batched()
     torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.steps):
-        parts, cuts, mx = S.sclap_refine_batched(graphs, k, eps, rounds, sub, 1, rg)
-    ev1.record()
+    S.prof_enable(False)
+    g0 = S.prof_read()["graph_launches"]
+    ms, (parts, cuts, mx) = timed(batched, args.steps)
+    graphs_per_call = (S.prof_read()["graph_launches"] - g0) / args.steps
+    plain()
     torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    run_entries = sum(int(graphs[g]["adjncy"].numel()) for g in rg)
-    best = {}
+    plain_ms, outs = timed(plain, 1)
+    pcuts = [int(o[1][0]) for o in outs]
+    same = all(int(cuts[r]) == pcuts[r] and torch.equal(parts[r], outs[r][0][0])
+               for r in range(len(rg)))
+    best, pbest = {}, {}
     for r, gi in enumerate(rg):
         best.setdefault(gi, []).append(int(cuts[r]))
-    # the plain form: the same 256 runs as separate single-individual calls
-    # (LPT start + r rounds each), one graph at a time
-    bound = []
-    for gg in graphs:
-        cv = int(gg["vwgt"].sum())
-        bound.append(int(math.floor((1.0 + eps) * float(-(-cv // k)))))
-    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev2.record()
-    pbest = {}
-    for r, gi in enumerate(rg):
-        _, pc, _, _ = S.sclap_initial_partition(graphs[gi], k, bound[gi], 1, rounds, sub, r + 1)
-        pbest.setdefault(gi, []).append(int(pc[0]))
-    ev3.record()
-    torch.cuda.synchronize(dev)
-    plain_ms = ev2.elapsed_time(ev3)
+        pbest.setdefault(gi, []).append(pcuts[r])
+    bound = [int(math.floor((1.0 + eps) * float(-(-int(g["vwgt"].sum()) // k)))) for g in graphs]
+    feasible = sum(1 for r, gi in enumerate(rg) if int(mx[r]) <= bound[gi])
+    run_entries = sum(int(graphs[g]["adjncy"].numel()) for g in rg)
     mean_best = sum(min(v) for v in best.values()) / len(best)
     mean_plain = sum(min(v) for v in pbest.values()) / len(pbest)
     line = {"op": "batched", "graphs": 32, "runs": 256, "nodes": nodes, "entries": entries,
             "k": k, "eps": eps, "rounds": rounds, "ms_per_call": ms,
+            "graph_launches_per_call": graphs_per_call,
             "runs_per_s": 256 / (ms / 1e3),
             "run_entries_per_s": run_entries * rounds / (ms / 1e3),
             "plain_ms": plain_ms, "speedup_vs_plain": plain_ms / ms,
+            "identical_to_plain": same, "runs_within_lmax": feasible,
             "mean_best_cut": mean_best, "mean_best_cut_plain": mean_plain,
             "cut_ratio_vs_plain": mean_best / mean_plain if mean_plain else None}
     print(json.dumps(line), flush=True)

@@ -183,12 +183,10 @@ int sclap_cut_noalloc(const sclap_graph *g, const int32_t *part, int32_t k, int6
                       int64_t *block_w_out, void *stream);
 
 /* Initial partition of a (coarsest) graph; stands in for the paper's
- * evolutionary initial partitioner (Sec. II.C, Sec. IV.E).  P individuals:
- * individual t places the nodes in (c desc, h_t(v) asc, v asc) order into
- * the lightest block, h_t(v) = high 32 bits of mix64(s_t ^ v), s_t =
- * mix64(seed ^ (0xD1B54A32D192ED03 * (t + 1))); all individuals are then
- * refined for `rounds` rounds as one SCLaP refinement over the disjoint union
- * of P copies (copy t: nodes t*n+v, blocks t*k..t*k+k-1, bound B, `seed`).
+ * evolutionary initial partitioner (Sec. II.C, Sec. IV.E).  P independent
+ * individuals: the batched runs of sclap_refine_batched on this graph (bound
+ * B on every block) with seeds s_t = mix64(seed ^ (0xD1B54A32D192ED03 *
+ * (t + 1))), t = 0..P-1.
  * Best = lowest cut with max block <= B (lowest t on ties), else smallest
  * max block, then cut, then t.
  *   part_out  device int32[n];  cuts_out, maxbw_out host int64[P] (NULL ok);
@@ -264,22 +262,28 @@ typedef struct {
 
 /* Batched SCLaP population: many seeded runs on uneven graphs at once, the
  * stand-in for the paper's population-based initial partitioning of the
- * coarsest graph (Sec. II.C, Sec. IV.E).  Run r works on graph run_graph[r]
- * with k blocks bounded by that graph's L_max = (1+eps) ceil(c(V)/k) (Sec.
- * II.A): it places the nodes in (c desc, h_r(v) asc, v asc) order into the
- * currently lightest block (lowest id on ties), h_r(v) = high 32 bits of
- * mix64(s_r ^ v), s_r = mix64(seed ^ (0xD1B54A32D192ED03 * (r + 1))); then all
- * runs are refined together for `rounds` rounds as one SCLaP refinement over
- * the disjoint union of the runs' graphs (run r: nodes off_r + v, blocks
- * r*k .. r*k+k-1; seed `seed`).
+ * coarsest graph (Sec. II.C, Sec. IV.E), whose individuals are independent.
+ * Run r works on graph run_graph[r] with seed s_r = seeds[r] and k blocks
+ * bounded by that graph's L_max = (1+eps) ceil(c(V)/k) (Sec. II.A): it places
+ * the nodes in (c desc, h_r(v) asc, v asc) order into the currently lightest
+ * block (lowest id on ties), h_r(v) = high 32 bits of mix64(s_r ^ v); then
+ * all runs are refined together for `rounds` rounds as one SCLaP refinement
+ * over the disjoint union of the runs' graphs, each run's sub-rounds and
+ * tie-breaks keyed by s_r with its own node and block ids.  A run's result is
+ * therefore the same in any batch and at any position: that start refined by
+ * sclap_refine_bound on its graph alone with seed s_r.
  *   run_graph  host int32[nruns], graph index per run
+ *   seeds      host uint64[nruns], seed per run
  *   parts_out  device int32[sum of the runs' n], per-run block ids 0..k-1,
  *              concatenated in run order
  *   cuts_out, maxbw_out  host int64[nruns] (NULL allowed)
- * Needs c(V) <= INT32_MAX per graph and every weighted degree <= INT32_MAX. */
+ * The rounds run as sclap_set_launch_mode says (by default all of them from
+ * one captured CUDA graph).  Needs c(V) <= INT32_MAX per graph and every
+ * weighted degree <= INT32_MAX. */
 int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t rounds,
-                         int32_t subrounds, uint64_t seed, int32_t nruns, const int32_t *run_graph,
-                         int32_t *parts_out, int64_t *cuts_out, int64_t *maxbw_out, void *stream);
+                         int32_t subrounds, int32_t nruns, const int32_t *run_graph,
+                         const uint64_t *seeds, int32_t *parts_out, int64_t *cuts_out,
+                         int64_t *maxbw_out, void *stream);
 
 /* The multilevel partitioner, Sec. IV.E: l rounds of clustering and a
  * contraction per level while n >= n_stop (stop also when a level shrinks by

@@ -110,9 +110,11 @@ def lib():
             L.or_vcycle.argtypes = g + [C.POINTER(MLParams), _P32, C.POINTER(MLStats)]
             _PP64 = C.POINTER(_P64)
             _PP32 = C.POINTER(_P32)
+            _PU64 = C.POINTER(C.c_uint64)
             L.or_refine_batched.argtypes = [C.c_int32, _P64, _PP64, _PP32, _PP32, _PP32,
-                                            C.c_int32, _P64, C.c_int32, C.c_int32, C.c_uint64,
+                                            C.c_int32, _P64, C.c_int32, C.c_int32, _PU64,
                                             C.c_int32, _P32, _P32, _P64, _P64]
+            L.or_lpt_start.argtypes = [C.c_int64, _P32, C.c_int32, C.c_uint64, _P32]
             _PF = C.POINTER(C.c_float)
             _PU8 = C.POINTER(C.c_uint8)
             _PU16 = C.POINTER(C.c_uint16)
@@ -286,9 +288,18 @@ def initial_partition(g, k, B, P, rounds, subrounds, seed):
     return part, cuts, mx, best.value
 
 
-def refine_batched(graphs, k, eps, rounds, subrounds, seed, run_graph):
-    """Batched runs (see or_refine_batched).  Returns (list of per-run
-    partitions, cuts[nruns], maxbw[nruns])."""
+def lpt_start(g, k, seed):
+    """The LPT start of one run (see or_lpt_start): block per node."""
+    vw = np.ascontiguousarray(g["vwgt"], np.int32)
+    part = np.empty(len(vw), np.int32)
+    _check(lib().or_lpt_start(len(vw), _p32(vw), k, seed & (2**64 - 1), _p32(part)), "lpt_start")
+    return part
+
+
+def refine_batched(graphs, k, eps, rounds, subrounds, seeds, run_graph):
+    """Batched runs, run r on graph run_graph[r] with seed seeds[r] (see
+    or_refine_batched).  Returns (list of per-run partitions, cuts[nruns],
+    maxbw[nruns])."""
     keeps = [_graph_args(g) for g in graphs]
     ng = len(graphs)
     ns = np.array([a[0] for _, a in keeps], np.int64)
@@ -300,12 +311,16 @@ def refine_batched(graphs, k, eps, rounds, subrounds, seed, run_graph):
                   np.int64)
     rg = np.ascontiguousarray(run_graph, np.int32)
     nr = len(rg)
+    sd = np.ascontiguousarray([int(x) & (2**64 - 1) for x in seeds], np.uint64)
+    if len(sd) != nr:
+        raise ValueError("one seed per run")
     tot = int(sum(ns[g] for g in rg))
     parts = np.empty(max(tot, 1), np.int32)
     cuts = np.zeros(nr, np.int64)
     mx = np.zeros(nr, np.int64)
     rc = lib().or_refine_batched(ng, _p64(ns), xs, As, Ws, Cs, k, _p64(Bg), rounds, subrounds,
-                                 seed, nr, _p32(rg), _p32(parts), _p64(cuts), _p64(mx))
+                                 sd.ctypes.data_as(C.POINTER(C.c_uint64)), nr, _p32(rg),
+                                 _p32(parts), _p64(cuts), _p64(mx))
     _check(rc, "refine_batched")
     out, off = [], 0
     for g in rg:

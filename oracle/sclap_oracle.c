@@ -164,6 +164,20 @@ static int cmp_by_target(const void *a, const void *b)
     return x->v < y->v ? -1 : (x->v > y->v);
 }
 
+/* Runs of a batch refined together over the disjoint union of their graphs
+ * (Sec. II.C / IV.E: the individuals of a population are independent).  Node
+ * v of the union belongs to run run_of[v]; that run's nodes are off[r] ..
+ * off[r] + n_r - 1 and its blocks r*k .. r*k + k - 1.  Its sub-rounds and
+ * tie-breaks use its own seed seed[r] with its local node id v - off[r] and
+ * local block id L - r*k, so a run's result does not depend on the other runs
+ * of the batch or on its position in it.  NULL: one graph, one seed. */
+typedef struct {
+    const int32_t *run_of;
+    const uint64_t *seed;
+    const int64_t *off;
+    int32_t k;
+} run_map;
+
 typedef struct {
     int64_t *acc;       /* omega(v, L) for the node being visited, size nW */
     int64_t *touched;   /* labels with acc != 0                             */
@@ -217,14 +231,24 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                         const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
                         int64_t *W, int64_t B, const int64_t *Bv, int refine,
                         const int32_t *cp, uint64_t seed, int32_t round, int32_t S,
-                        const uint8_t *active, const int32_t *colour, lp_ws *ws)
+                        const uint8_t *active, const int32_t *colour, const run_map *rm,
+                        lp_ws *ws)
 {
     int64_t moves = 0;
     for (int32_t j = 0; j < S; j++) {
         int64_t np = 0;
         /* --- every node of colour j proposes against the current state --- */
         for (int64_t v = 0; v < n; v++) {
-            if ((colour ? colour[v] : (int32_t)or_colour(seed, round, v, S)) != j) continue;
+            /* the seed, node id and block-id base that key v's hashes */
+            uint64_t sv = seed;
+            int64_t lv = v, lb = 0;
+            if (rm) {
+                int32_t r = rm->run_of[v];
+                sv = rm->seed[r];
+                lv = v - rm->off[r];
+                lb = (int64_t)r * rm->k;
+            }
+            if ((colour ? colour[v] : (int32_t)or_colour(sv, round, lv, S)) != j) continue;
             if (xadj[v + 1] == xadj[v]) continue;  /* no neighbours: never moves */
             if (active && !active[v]) continue;    /* learned form: not visited */
             int64_t nt = 0;
@@ -244,7 +268,7 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                 int64_t L = ws->touched[t];
                 if (L == own) continue;
                 if (W[L] + vwgt[v] > bound_of(Bv, B, L)) continue; /* not eligible */
-                uint32_t tl = or_tie(seed, round, v, L);
+                uint32_t tl = or_tie(sv, round, lv, L - lb);
                 int better;
                 if (best < 0) better = 1;
                 else if (ws->acc[L] != ws->acc[best]) better = ws->acc[L] > ws->acc[best];
@@ -311,7 +335,8 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt, int32_t *lab,
                   int64_t *W, int64_t nW, int64_t B, const int64_t *Bv, int refine,
                   const int32_t *cp, uint64_t seed, int32_t rounds, int32_t S,
-                  int32_t degree_order, int32_t *rounds_done, int64_t *moves_per_round)
+                  int32_t degree_order, const run_map *rm, int32_t *rounds_done,
+                  int64_t *moves_per_round)
 {
     int32_t *colour = NULL;
     if (degree_order) {
@@ -330,7 +355,7 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     for (int32_t r = 0; r < rounds; r++) {
         if (colour) or_degree_colours(n, xadj, seed, r, S, colour);
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, Bv, refine, cp,
-                             seed, r, S, NULL, colour, &ws);
+                             seed, r, S, NULL, colour, rm, &ws);
         if (moves_per_round) moves_per_round[r] = m;
         done = r + 1;
         if (m == 0) break;
@@ -451,7 +476,7 @@ static int cluster_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (!W) return OR_ENOMEM;
     for (int64_t v = 0; v < n; v++) { labels_out[v] = (int32_t)v; W[v] = vwgt[v]; }
     int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, labels_out, W, n, U, NULL, 0,
-                    constraint_part, seed, rounds, S, degree_order, rounds_done,
+                    constraint_part, seed, rounds, S, degree_order, NULL, rounds_done,
                     moves_per_round);
     free(W);
     if (rc) return rc;
@@ -463,7 +488,8 @@ static int cluster_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy,
 static int refine_bounds(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                          const int32_t *adjwgt, const int32_t *vwgt, int32_t nblocks,
                          int64_t B, const int64_t *Bv, int32_t rounds, int32_t S, uint64_t seed,
-                         int32_t *part, int32_t *rounds_done, int64_t *moves_per_round)
+                         const run_map *rm, int32_t *part, int32_t *rounds_done,
+                         int64_t *moves_per_round)
 {
     if (nblocks < 1 || rounds < 0 || S < 1) return OR_EINVAL;
     for (int64_t v = 0; v < n; v++)
@@ -472,7 +498,7 @@ static int refine_bounds(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (!W) return OR_ENOMEM;
     for (int64_t v = 0; v < n; v++) W[part[v]] += vwgt[v];
     int rc = lp_run(n, xadj, adjncy, adjwgt, vwgt, part, W, nblocks, B, Bv, 1, NULL,
-                    seed, rounds, S, 0, rounds_done, moves_per_round);
+                    seed, rounds, S, 0, rm, rounds_done, moves_per_round);
     free(W);
     return rc;
 }
@@ -483,7 +509,7 @@ int or_refine_bound(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                     int32_t *part, int32_t *rounds_done, int64_t *moves_per_round)
 {
     return refine_bounds(n, xadj, adjncy, adjwgt, vwgt, nblocks, B, NULL, rounds, S, seed,
-                         part, rounds_done, moves_per_round);
+                         NULL, part, rounds_done, moves_per_round);
 }
 
 int or_refine(int64_t n, const int64_t *xadj, const int32_t *adjncy,
@@ -625,21 +651,51 @@ static int cmp_lpt(const void *a, const void *b)
     return x->v < y->v ? -1 : (x->v > y->v);
 }
 
-/* Batched runs: run r refines graph run_graph[r] (bound Bg[run_graph[r]] on
- * each of its k blocks) from its own LPT start.  Reading (the paper's
- * population lives in an evolutionary algorithm): run r places its graph's
- * nodes in (c desc, h_r(v) asc, v asc) order into the currently lightest of
- * its k blocks (lowest id on ties), h_r(v) = high 32 bits of mix64(s_r ^ v),
- * s_r = mix64(seed ^ (0xD1B54A32D192ED03 * (r+1))); then all runs are refined
- * together as one SCLaP refinement of the disjoint union of the runs' graphs
- * (run r: nodes off_r + v with off_r the node count of the runs before it,
- * blocks r*k .. r*k+k-1), `rounds` rounds, `seed`.  Outputs per run: its
- * partition (block ids 0..k-1, concatenated in run order), cut and largest
- * block weight. */
+/* LPT start (the stand-in for an individual's initial assignment): the nodes
+ * in (c desc, h(v) asc, v asc) order, h(v) = high 32 bits of mix64(seed ^ v),
+ * each into the currently lightest of the k blocks (lowest id on ties). */
+int or_lpt_start(int64_t n, const int32_t *vwgt, int32_t k, uint64_t seed, int32_t *part_out)
+{
+    if (k < 1) return OR_EINVAL;
+    lpt_item *it = (lpt_item *)malloc(sizeof(lpt_item) * (size_t)(n ? n : 1));
+    int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    if (!it || !bw) { free(it); free(bw); return OR_ENOMEM; }
+    for (int64_t v = 0; v < n; v++) {
+        it[v].v = v;
+        it[v].c = vwgt[v];
+        it[v].h = (uint32_t)(or_mix64(seed ^ (uint64_t)v) >> 32);
+    }
+    if (n > 0) qsort(it, (size_t)n, sizeof(lpt_item), cmp_lpt);
+    for (int64_t i = 0; i < n; i++) {
+        int32_t bb = 0;
+        for (int32_t b = 1; b < k; b++)
+            if (bw[b] < bw[bb]) bb = b;
+        part_out[it[i].v] = bb;
+        bw[bb] += it[i].c;
+    }
+    free(it);
+    free(bw);
+    return OR_OK;
+}
+
+/* Batched runs (the stand-in for the population of Sec. II.C / IV.E, whose
+ * individuals are independent): run r refines graph run_graph[r] (bound
+ * Bg[run_graph[r]] on each of its k blocks) from its own LPT start with its
+ * own seed s_r = seeds[r].  It places its graph's nodes in (c desc, h_r(v)
+ * asc, v asc) order into the currently lightest of its k blocks (lowest id
+ * on ties), h_r(v) = high 32 bits of mix64(s_r ^ v) (or_lpt_start); then all
+ * runs are refined together for `rounds` rounds as one SCLaP refinement of
+ * the disjoint union of their graphs (run r: nodes off_r + v, blocks r*k ..
+ * r*k+k-1), each run's sub-rounds and tie-breaks keyed by s_r, its local node
+ * ids and its local block ids (run_map).  A run's result therefore equals
+ * or_lpt_start followed by or_refine_bound on its graph alone with seed s_r
+ * (a run that has converged stays unchanged while others go on).  Outputs per
+ * run: its partition (block ids 0..k-1, concatenated in run order), cut and
+ * largest block weight. */
 int or_refine_batched(int32_t ngraphs, const int64_t *ns, const int64_t *const *xadjs,
                       const int32_t *const *adjncys, const int32_t *const *adjwgts,
                       const int32_t *const *vwgts, int32_t k, const int64_t *Bg,
-                      int32_t rounds, int32_t S, uint64_t seed, int32_t nruns,
+                      int32_t rounds, int32_t S, const uint64_t *seeds, int32_t nruns,
                       const int32_t *run_graph, int32_t *parts_out, int64_t *cuts_out,
                       int64_t *maxbw_out)
 {
@@ -658,10 +714,14 @@ int or_refine_batched(int32_t ngraphs, const int64_t *ns, const int64_t *const *
     int32_t *uc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
     int32_t *up = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
     int64_t *Bv = (int64_t *)malloc(sizeof(int64_t) * (size_t)nruns * (size_t)k);
-    lpt_item *it = (lpt_item *)malloc(sizeof(lpt_item) * (size_t)(nmax ? nmax : 1));
     int64_t *bw = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int32_t *run_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(un ? un : 1));
+    int64_t *roff = (int64_t *)malloc(sizeof(int64_t) * (size_t)nruns);
     int rc = OR_OK;
-    if (!ux || !ua || !uw || !uc || !up || !Bv || !it || !bw) { rc = OR_ENOMEM; goto out; }
+    if (!ux || !ua || !uw || !uc || !up || !Bv || !bw || !run_of || !roff) {
+        rc = OR_ENOMEM;
+        goto out;
+    }
 
     int64_t off = 0, eoff = 0;
     for (int32_t r = 0; r < nruns; r++) {        /* the disjoint union */
@@ -676,27 +736,23 @@ int or_refine_batched(int32_t ngraphs, const int64_t *ns, const int64_t *const *
             uw[eoff + i] = adjwgts[g][i];
         }
         for (int32_t b = 0; b < k; b++) Bv[(int64_t)r * k + b] = Bg[g];
-        /* LPT start of run r */
-        uint64_t sr = or_mix64(seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(r + 1)));
-        for (int64_t v = 0; v < n; v++) {
-            it[v].v = v; it[v].c = vwgts[g][v];
-            it[v].h = (uint32_t)(or_mix64(sr ^ (uint64_t)v) >> 32);
-        }
-        if (n > 0) qsort(it, (size_t)n, sizeof(lpt_item), cmp_lpt);
-        for (int32_t b = 0; b < k; b++) bw[b] = 0;
-        for (int64_t i = 0; i < n; i++) {
-            int32_t bb = 0;
-            for (int32_t b = 1; b < k; b++)
-                if (bw[b] < bw[bb]) bb = b;
-            up[off + it[i].v] = r * k + bb;
-            bw[bb] += it[i].c;
-        }
+        for (int64_t v = 0; v < n; v++) run_of[off + v] = r;
+        roff[r] = off;
+        /* LPT start of run r, its blocks shifted to r*k .. r*k+k-1 */
+        rc = or_lpt_start(n, vwgts[g], k, seeds[r], up + off);
+        if (rc) goto out;
+        for (int64_t v = 0; v < n; v++) up[off + v] += r * k;
         off += n;
         eoff += xadjs[g][n];
     }
     ux[un] = unnz;
 
-    rc = refine_bounds(un, ux, ua, uw, uc, k * nruns, 0, Bv, rounds, S, seed, up, NULL, NULL);
+    run_map rm;
+    rm.run_of = run_of;
+    rm.seed = seeds;
+    rm.off = roff;
+    rm.k = k;
+    rc = refine_bounds(un, ux, ua, uw, uc, k * nruns, 0, Bv, rounds, S, 0, &rm, up, NULL, NULL);
     if (rc) goto out;
 
     off = 0;
@@ -718,13 +774,15 @@ int or_refine_batched(int32_t ngraphs, const int64_t *ns, const int64_t *const *
         off += n;
     }
 out:
-    free(ux); free(ua); free(uw); free(uc); free(up); free(Bv); free(it); free(bw);
+    free(ux); free(ua); free(uw); free(uc); free(up); free(Bv); free(bw); free(run_of);
+    free(roff);
     return rc;
 }
 
-/* Reading (the paper runs an evolutionary algorithm here): P individuals,
- * computed as P batched runs on the same graph with bound B (see
- * or_refine_batched).  The best individual has the lowest cut among those
+/* Reading (the paper runs an evolutionary algorithm here): P independent
+ * individuals, computed as P batched runs on the same graph with bound B (see
+ * or_refine_batched), individual t with seed s_t = mix64(seed ^
+ * (0xD1B54A32D192ED03 * (t + 1))).  The best individual has the lowest cut among those
  * with max block weight <= B (lowest t on ties); with none feasible, the
  * smallest max block weight, then cut, then t. */
 int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
@@ -735,13 +793,16 @@ int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
 {
     if (k < 1 || P < 1) return OR_EINVAL;
     int32_t *rg = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    uint64_t *seeds = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)P);
     int32_t *parts = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * P ? n * P : 1));
     int64_t *cuts = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
     int64_t *mxs = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
     int rc = OR_OK;
-    if (!rg || !parts || !cuts || !mxs) { rc = OR_ENOMEM; goto out; }
-    rc = or_refine_batched(1, &n, &xadj, &adjncy, &adjwgt, &vwgt, k, &B, rounds, S, seed, P, rg,
-                           parts, cuts, mxs);
+    if (!rg || !seeds || !parts || !cuts || !mxs) { rc = OR_ENOMEM; goto out; }
+    for (int32_t t = 0; t < P; t++)
+        seeds[t] = or_mix64(seed ^ (0xD1B54A32D192ED03ULL * (uint64_t)(t + 1)));
+    rc = or_refine_batched(1, &n, &xadj, &adjncy, &adjwgt, &vwgt, k, &B, rounds, S, seeds, P,
+                           rg, parts, cuts, mxs);
     if (rc) goto out;
     int32_t best = -1;
     int64_t best_cut = 0, best_max = 0;
@@ -762,7 +823,7 @@ int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     for (int64_t v = 0; v < n; v++) part_out[v] = parts[(int64_t)best * n + v];
     if (best_out) *best_out = best;
 out:
-    free(rg); free(parts); free(cuts); free(mxs);
+    free(rg); free(seeds); free(parts); free(cuts); free(mxs);
     return rc;
 }
 
@@ -1099,7 +1160,7 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         }
         memcpy(prev, part, sizeof(int32_t) * (size_t)n);
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, part, W, B, NULL, 1, NULL, seed, r,
-                             S, active, NULL, &ws);
+                             S, active, NULL, NULL, &ws);
         for (int64_t v = 0; v < n; v++) moved[v] = part[v] != prev[v];
         if (trace_y) memcpy(trace_y + (size_t)r * n, moved, (size_t)n);
         if (moves_per_round) moves_per_round[r] = m;

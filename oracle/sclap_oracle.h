@@ -113,9 +113,11 @@ int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
 int or_refine_batched(int32_t ngraphs, const int64_t *ns, const int64_t *const *xadjs,
                       const int32_t *const *adjncys, const int32_t *const *adjwgts,
                       const int32_t *const *vwgts, int32_t k, const int64_t *Bg,
-                      int32_t rounds, int32_t S, uint64_t seed, int32_t nruns,
+                      int32_t rounds, int32_t S, const uint64_t *seeds, int32_t nruns,
                       const int32_t *run_graph, int32_t *parts_out, int64_t *cuts_out,
                       int64_t *maxbw_out);
+
+int or_lpt_start(int64_t n, const int32_t *vwgt, int32_t k, uint64_t seed, int32_t *part_out);
 
 int or_multilevel(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                   const int32_t *adjwgt, const int32_t *vwgt,

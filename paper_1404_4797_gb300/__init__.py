@@ -97,8 +97,8 @@ _SIGS = {
                                           C.c_int32, C.c_int32, C.c_uint64, _VP, _P64, _P64,
                                           _P32, _VP]),
     "sclap_refine_batched": (C.c_int, [C.POINTER(Batch), C.c_int32, C.c_double, C.c_int32,
-                                       C.c_int32, C.c_uint64, C.c_int32, _P32, _VP, _P64, _P64,
-                                       _VP]),
+                                       C.c_int32, C.c_int32, _P32, C.POINTER(C.c_uint64), _VP,
+                                       _P64, _P64, _VP]),
     "partition_multilevel": (C.c_int, [C.POINTER(Graph), C.POINTER(MLParams), _VP,
                                        C.POINTER(MLStats), _VP]),
     "sclap_vcycle": (C.c_int, [C.POINTER(Graph), C.POINTER(MLParams), _VP, C.POINTER(MLStats),
@@ -390,20 +390,24 @@ def sclap_initial_partition(g: dict, k: int, B: int, P: int, rounds: int, subrou
 
 
 def sclap_refine_batched(graphs: list, k: int, eps: float, rounds: int, subrounds: int,
-                         seed: int, run_graph, stream=None):
-    """Batched SCLaP runs over uneven graphs (the population stand-in).  Returns
-    (list of per-run partitions (CUDA int32), cuts[nruns], maxbw[nruns])."""
+                         seeds, run_graph, stream=None):
+    """Batched SCLaP runs over uneven graphs (the population stand-in): run r
+    on graph run_graph[r] with seed seeds[r].  Returns (list of per-run
+    partitions (CUDA int32), cuts[nruns], maxbw[nruns])."""
     for g in graphs:
         _require_cuda(g["xadj"])
     views = (Graph * len(graphs))(*[_graph(g) for g in graphs])
     b = Batch(len(graphs), views)
     rg = torch.as_tensor(list(run_graph), dtype=torch.int32)
+    sd = (C.c_uint64 * len(rg))(*[int(x) & (2**64 - 1) for x in seeds])
+    if len(sd) != len(rg):
+        raise ValueError("one seed per run")
     ns = [graphs[i]["vwgt"].numel() for i in rg.tolist()]
     parts = torch.empty(max(sum(ns), 1), dtype=torch.int32, device=graphs[0]["xadj"].device)
     cuts = torch.zeros(len(ns), dtype=torch.int64)
     mx = torch.zeros(len(ns), dtype=torch.int64)
-    _check(lib().sclap_refine_batched(C.byref(b), k, eps, rounds, subrounds, seed & (2**64 - 1),
-                                      len(ns), C.cast(rg.data_ptr(), _P32), _ptr(parts),
+    _check(lib().sclap_refine_batched(C.byref(b), k, eps, rounds, subrounds, len(ns),
+                                      C.cast(rg.data_ptr(), _P32), sd, _ptr(parts),
                                       C.cast(cuts.data_ptr(), _P64), C.cast(mx.data_ptr(), _P64),
                                       _stream(stream)), "sclap_refine_batched")
     out, off = [], 0

@@ -170,7 +170,7 @@ struct RunDesc {
     const int32_t *adjncy, *adjwgt, *vwgt;
     int64_t n, off, eoff;
     int64_t bound;  // the run's L_max
-    uint64_t lpt_seed;
+    uint64_t seed;  // the run's seed (LPT order and SCLaP hashes)
 };
 
 __device__ __forceinline__ int64_t run_of(const RunDesc *rd, int64_t nruns, int64_t x, bool entries) {
@@ -181,6 +181,10 @@ __device__ __forceinline__ int64_t run_of(const RunDesc *rd, int64_t nruns, int6
         else hi = mid;
     }
     return lo;
+}
+
+__device__ __forceinline__ int64_t run_of_node(const RunDesc *rd, int64_t nruns, int64_t i) {
+    return run_of(rd, nruns, i, false);
 }
 
 __global__ void k_union_batch(const RunDesc *rd, int64_t nruns, int64_t un, int64_t unnz,
@@ -211,7 +215,7 @@ __global__ void k_lpt_keys1(const RunDesc *rd, int64_t nruns, int64_t un, uint64
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
          i += (int64_t)gridDim.x * blockDim.x) {
         const RunDesc &r = rd[run_of(rd, nruns, i, false)];
-        key[i] = mix64(r.lpt_seed ^ (uint64_t)(i - r.off)) >> 32;
+        key[i] = mix64(r.seed ^ (uint64_t)(i - r.off)) >> 32;
         idx[i] = (int32_t)i;
     }
 }
@@ -268,6 +272,19 @@ __global__ void k_run_bounds(const RunDesc *rd, int64_t nruns, int32_t k, int64_
         Bv[i] = rd[i / k].bound;
 }
 
+// Run id of every union node, and each run's seed and first node.
+__global__ void k_run_map(const RunDesc *rd, int64_t nruns, int64_t un, int32_t *run_of,
+                          uint64_t *run_seed, int64_t *run_off) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < un;
+         i += (int64_t)gridDim.x * blockDim.x)
+        run_of[i] = (int32_t)run_of_node(rd, nruns, i);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nruns;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        run_seed[r] = rd[r].seed;
+        run_off[r] = rd[r].off;
+    }
+}
+
 __global__ void k_run_max(int64_t nruns, int32_t k, const int64_t *bw, int64_t *maxbw) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nruns;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -292,8 +309,8 @@ struct BatchResult {
 // All runs refined together (see sclap_refine_batched).  parts_out: device,
 // sum of the runs' node counts.
 BatchResult batched_impl(const std::vector<DGraph> &G, const std::vector<int64_t> &bound,
-                         const std::vector<int32_t> &run_graph, int32_t k, int32_t rounds,
-                         int32_t S, uint64_t seed, int32_t *parts_out, Scratch &sc) {
+                         const std::vector<int32_t> &run_graph, const std::vector<uint64_t> &seeds,
+                         int32_t k, int32_t rounds, int32_t S, int32_t *parts_out, Scratch &sc) {
     cudaStream_t s = sc.stream();
     const int grid = dev_info().sms * 8;
     const int64_t nruns = (int64_t)run_graph.size();
@@ -304,7 +321,7 @@ BatchResult batched_impl(const std::vector<DGraph> &G, const std::vector<int64_t
     for (int64_t r = 0; r < nruns; r++) {
         const DGraph &g = G[run_graph[r]];
         rd[r] = RunDesc{g.xadj, g.adjncy, g.adjwgt, g.vwgt, g.n, un, unnz, bound[run_graph[r]],
-                        mix64(seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(r + 1)))};
+                        seeds[r]};
         un += g.n;
         unnz += g.nnz;
         cmax = std::max<int64_t>(cmax, tot[run_graph[r]].maxc);
@@ -344,6 +361,11 @@ BatchResult batched_impl(const std::vector<DGraph> &G, const std::vector<int64_t
     int64_t *Bv = sc.get<int64_t>(nruns * k);
     k_run_bounds<<<grid, 256, 0, s>>>(d_rd, nruns, k, Bv);
     LAUNCHED();
+    int32_t *run_of = sc.get<int32_t>(un);
+    uint64_t *run_seed = sc.get<uint64_t>(nruns);
+    int64_t *run_off = sc.get<int64_t>(nruns);
+    k_run_map<<<grid, 256, 0, s>>>(d_rd, nruns, un, run_of, run_seed, run_off);
+    LAUNCHED();
     // refine all runs together on the disjoint union
     DGraph ug{un, unnz, ux, ua, uw, uc};
     LPConfig cfg{};
@@ -354,9 +376,13 @@ BatchResult batched_impl(const std::vector<DGraph> &G, const std::vector<int64_t
     cfg.Bv = Bv;
     cfg.refine = true;
     cfg.cp = nullptr;
-    cfg.seed = seed;
+    cfg.seed = 0;  // every run uses its own seed
     cfg.rounds = rounds;
     cfg.S = S;
+    cfg.run_of = run_of;
+    cfg.run_seed = run_seed;
+    cfg.run_off = run_off;
+    cfg.run_k = k;
     lp_run(cfg, sc, nullptr, nullptr);
     int64_t *d_cut = sc.get<int64_t>(nruns);
     int64_t *d_bw = sc.get<int64_t>((int64_t)k * nruns);
@@ -403,7 +429,9 @@ InitResult initial_impl(const DGraph &g, int32_t k, int64_t B, int32_t P, int32_
     cudaStream_t s = sc.stream();
     InitResult res;
     int32_t *parts = sc.get<int32_t>((size_t)g.n * P);
-    BatchResult br = batched_impl({g}, {B}, std::vector<int32_t>(P, 0), k, rounds, S, seed, parts, sc);
+    std::vector<uint64_t> seeds(P);
+    for (int32_t t = 0; t < P; t++) seeds[t] = mix64(seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(t + 1)));
+    BatchResult br = batched_impl({g}, {B}, std::vector<int32_t>(P, 0), seeds, k, rounds, S, parts, sc);
     res.cuts = br.cuts;
     res.maxbw = br.maxbw;
     res.best = g.n > 0 ? pick_best(br.cuts, br.maxbw, B) : 0;
@@ -831,11 +859,12 @@ int sclap_initial_partition(const sclap_graph *gp, int32_t k, int64_t B, int32_t
 }
 
 int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t rounds,
-                         int32_t subrounds, uint64_t seed, int32_t nruns, const int32_t *run_graph,
-                         int32_t *parts_out, int64_t *cuts_out, int64_t *maxbw_out, void *stream) {
+                         int32_t subrounds, int32_t nruns, const int32_t *run_graph,
+                         const uint64_t *seeds, int32_t *parts_out, int64_t *cuts_out,
+                         int64_t *maxbw_out, void *stream) {
     return guarded([&] {
         if (!b || b->ngraphs < 1 || !b->graphs || k < 1 || !(eps >= 0) || rounds < 0 ||
-            subrounds < 1 || subrounds > 32 || nruns < 1 || !run_graph)
+            subrounds < 1 || subrounds > 32 || nruns < 1 || !run_graph || !seeds)
             fail(SCLAP_EINVAL, "args");
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
@@ -854,7 +883,8 @@ int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t ro
             total += G[r].n;
         }
         if (total > 0 && !parts_out) fail(SCLAP_EINVAL, "parts_out");
-        BatchResult br = batched_impl(G, bound, rg, k, rounds, subrounds, seed, parts_out, sc);
+        BatchResult br = batched_impl(G, bound, rg, std::vector<uint64_t>(seeds, seeds + nruns), k,
+                                      rounds, subrounds, parts_out, sc);
         if (cuts_out) std::memcpy(cuts_out, br.cuts.data(), nruns * sizeof(int64_t));
         if (maxbw_out) std::memcpy(maxbw_out, br.maxbw.data(), nruns * sizeof(int64_t));
     });

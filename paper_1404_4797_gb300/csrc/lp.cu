@@ -189,6 +189,14 @@ struct LPArgs {
     int32_t maxbig, maxtiles;
     const uint8_t *active;     // learned refinement: rows visited this round (null: all)
     const int32_t *stop;       // device flag: the run has ended (every round kernel returns)
+    // batched runs over a disjoint union (null run_of: one graph, one seed):
+    // node v belongs to run run_of[v], whose nodes start at run_off[r] and
+    // whose blocks are r * run_k .. r * run_k + run_k - 1; its hashes use
+    // run_seed[r] with local node and block ids
+    const int32_t *run_of;
+    const uint64_t *run_seed;
+    const int64_t *run_off;
+    int32_t run_k;
 };
 
 // Every kernel of a round returns at once after the run has ended (the rounds
@@ -198,6 +206,18 @@ __device__ __forceinline__ bool stopped(const LPArgs &a) { return a.stop && *(vo
 // Bound of label L (U, L_max, or the run's L_max in batched runs).
 __device__ __forceinline__ int64_t bnd(const LPArgs &a, int64_t L) {
     return a.Bv ? __ldg(&a.Bv[L]) : a.B;
+}
+
+// h(v, round) of node v: its run's seed and its local id in batched runs.
+__device__ __forceinline__ uint64_t nhash(const LPArgs &a, int32_t v) {
+    if (!a.run_of) return node_hash(a.seed, a.round, (uint32_t)v);
+    const int32_t r = __ldg(&a.run_of[v]);
+    return node_hash(__ldg(&a.run_seed[r]), a.round, (uint32_t)(v - __ldg(&a.run_off[r])));
+}
+
+// First label of v's run (0 unless batched): ties hash local block ids.
+__device__ __forceinline__ int32_t lbase(const LPArgs &a, int32_t v) {
+    return a.run_of ? __ldg(&a.run_of[v]) * a.run_k : 0;
 }
 
 __device__ __forceinline__ uint64_t seg_key(int32_t gain, int32_t v) {
@@ -212,8 +232,8 @@ __device__ __forceinline__ uint32_t tie_of(uint64_t h, int32_t L) {
     return (uint32_t)(mix64(h ^ (uint64_t)(uint32_t)L) >> 32);
 }
 
-__device__ __forceinline__ uint32_t colour_of(uint64_t seed, int32_t round, int32_t v, int S) {
-    return (uint32_t)(node_hash(seed, round, (uint32_t)v) >> 32) % (uint32_t)S;
+__device__ __forceinline__ uint32_t colour_of(const LPArgs &a, int32_t v) {
+    return (uint32_t)(nhash(a, v) >> 32) % (uint32_t)a.S;
 }
 
 __device__ __forceinline__ unsigned long long cand_key(int32_t w, uint64_t h, int32_t L) {
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
                 if (d > 0 && (!a.active || a.active[v])) {
                     p_entries += (unsigned long long)d;
                     p_nodes++;
-                    const uint32_t col = colour_of(a.seed, a.round, (int32_t)v, S);
+                    const uint32_t col = colour_of(a, (int32_t)v);
                     if (d <= kMedDeg) {
                         bk[j] = kClasses * (int)col + degree_class(d);
                         rk[j] = atomicAdd(&lcnt[bk[j]], 1);
@@ -396,6 +416,7 @@ struct NodeSm {
     int32_t epre[kMedItem + 1];
     int64_t rs[kMedItem];
     uint64_t h[kMedItem];
+    int32_t lb[kMedItem];
     unsigned long long best[kMedItem];
     uint8_t ovl[kMedItem];
 };
@@ -472,7 +493,7 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *key
         if (L == nd.own[0]) {
             nd.ownw[0] = w;
         } else if (a.W[L] + nd.c[0] <= bnd(a, L)) {
-            const unsigned long long ck = cand_key(w, nd.h[0], L);
+            const unsigned long long ck = cand_key(w, nd.h[0], L - nd.lb[0]);
             best = ck > best ? ck : best;
         }
     }
@@ -495,7 +516,7 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *key
         const int32_t w = vals[slot];
         if (b == 0 || L == nd.own[0] || (uint32_t)w != (uint32_t)(b >> 32)) continue;
         if (a.W[L] + nd.c[0] > bnd(a, L)) continue;
-        if (cand_key(w, nd.h[0], L) == b) atomicMin(&nd.bestL[0], L);
+        if (cand_key(w, nd.h[0], L - nd.lb[0]) == b) atomicMin(&nd.bestL[0], L);
     }
     __syncthreads();
 }
@@ -507,6 +528,7 @@ __device__ __forceinline__ void select_dense_warp(const LPArgs &a, const int64_t
     const int lane = threadIdx.x & 31;
     const int32_t own = nd.own[s], c = nd.c[s];
     const uint64_t h = nd.h[s];
+    const int32_t lb = nd.lb[s];
     int32_t w0 = lane < k ? acc[lane] : 0;
     int32_t w1 = lane + 32 < k ? acc[lane + 32] : 0;
     __syncwarp();
@@ -514,9 +536,9 @@ __device__ __forceinline__ void select_dense_warp(const LPArgs &a, const int64_t
     if (lane + 32 < k) acc[lane + 32] = 0;
     int32_t ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
     unsigned long long ck0 = 0, ck1 = 0;
-    if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane);
+    if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane - lb);
     if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32))
-        ck1 = cand_key(w1, h, lane + 32);
+        ck1 = cand_key(w1, h, lane + 32 - lb);
     unsigned long long m = ck0 > ck1 ? ck0 : ck1;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -561,7 +583,8 @@ __device__ __forceinline__ int32_t load_node(const LPArgs &a, const int64_t *Wsm
     nd.own[t] = own;
     nd.c[t] = a.g.vwgt[v];
     nd.cpv[t] = a.cp ? a.cp[v] : 0;
-    nd.h[t] = node_hash(a.seed, a.round, (uint32_t)v);
+    nd.h[t] = nhash(a, v);
+    nd.lb[t] = lbase(a, v);
     nd.ovl[t] = MODE == kCluster ? 0 : ((MODE == kRefineDense ? Wsm[own] : a.W[own]) > bnd(a, own));
     nd.ownw[t] = 0;
     nd.best[t] = 0;
@@ -765,7 +788,8 @@ template <int MODE, int G>
 __device__ __forceinline__ void small_compute(const LPArgs &a, const int64_t *Wsm, const SmallLoad &x) {
     const int lane = threadIdx.x & 31;
     const int q = lane / G, r = lane % G;
-    const uint64_t h = x.has ? node_hash(a.seed, a.round, (uint32_t)x.v) : 0;
+    const uint64_t h = x.has ? nhash(a, x.v) : 0;
+    const int32_t lb = x.has ? lbase(a, x.v) : 0;
     const unsigned long long mkey =
         x.valid ? (((unsigned long long)q << 32) | (uint32_t)x.L) : (0xffffffff00000000ull | lane);
     const unsigned peers = __match_any_sync(0xffffffffu, mkey);
@@ -775,7 +799,7 @@ __device__ __forceinline__ void small_compute(const LPArgs &a, const int64_t *Ws
     int32_t ownw = 0;
     if (leader) {
         if (x.L == x.own) ownw = (int32_t)wsum;
-        else if (x.WL + x.c <= bnd(a, x.L)) ck = cand_key((int32_t)wsum, h, x.L);
+        else if (x.WL + x.c <= bnd(a, x.L)) ck = cand_key((int32_t)wsum, h, x.L - lb);
     }
     unsigned long long best = ck;  // reduce within the node's G lanes
 #pragma unroll
@@ -1014,7 +1038,8 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
         const PipeRow n3 = pipe_row<MODE>(a, v3);
         v3 = idx + 4 * G < cnt ? list[idx + 4 * G] : -1;
         const int64_t deg = cur.re - cur.rs;
-        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)cur.v);
+        const uint64_t h = nhash(a, cur.v);
+        const int32_t lb = lbase(a, cur.v);
         int64_t wown = 0;
         if (MODE == kRefineHash && threadIdx.x == 0) wown = a.W[cur.own];
         pipe_flush<MODE, PS>(a, sm, false);
@@ -1066,7 +1091,7 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
                 }
                 if (b == cur.own) ow = tot;
                 else if (tot > 0 && sm.W[b] + cur.c <= bnd(a, b)) {
-                    bk = cand_key(tot, h, b);
+                    bk = cand_key(tot, h, b - lb);
                     bl = b;
                 }
             }
@@ -1080,7 +1105,7 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
                 if (L[j] == cur.own) {
                     ow = wx;
                 } else if (WL[j] + cur.c <= bnd(a, L[j])) {
-                    const unsigned long long ck = cand_key(wx, h, L[j]);
+                    const unsigned long long ck = cand_key(wx, h, L[j] - lb);
                     if (cand_better(ck, L[j], bk, bl)) {
                         bk = ck;
                         bl = L[j];
@@ -1174,7 +1199,8 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
     const int32_t c = a.g.vwgt[v];
     const int32_t cpv = (MODE == kCluster && a.cp) ? a.cp[v] : 0;
     const int64_t Wown = MODE == kCluster ? 0 : (DENSE ? Wsm[own] : a.W[own]);
-    const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+    const uint64_t h = nhash(a, v);
+    const int32_t lb = lbase(a, v);
     for (int32_t e0 = 0; e0 < deg; e0 += 32 * kUnroll) {
         int32_t u[kUnroll], w[kUnroll], L[kUnroll];
 #pragma unroll
@@ -1206,9 +1232,9 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
         if (lane + 32 < k) dacc[lane + 32] = 0;
         ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
         unsigned long long ck0 = 0, ck1 = 0;
-        if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane);
+        if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane - lb);
         if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32))
-            ck1 = cand_key(w1, h, lane + 32);
+            ck1 = cand_key(w1, h, lane + 32 - lb);
         best = ck0 > ck1 ? ck0 : ck1;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
@@ -1235,7 +1261,7 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
                 t.vals[slot] = 0;
                 lab[j] = L;
                 if (L == own) ownw = w;
-                else if (a.W[L] + c <= bnd(a, L)) ck[j] = cand_key(w, h, L);
+                else if (a.W[L] + c <= bnd(a, L)) ck[j] = cand_key(w, h, L - lb);
                 best = ck[j] > best ? ck[j] : best;
             }
         }
@@ -2042,7 +2068,7 @@ __device__ __forceinline__ HubItem hub_item(const LPArgs &a, int64_t t, int roun
     const int64_t ndl = __ldcg(&a.Lndl[lo]);
     it.begin = c * kFin;
     it.end = min64(ndl, it.begin + kFin);
-    it.active = colour_of(a.seed, round, a.Lnodes[lo], a.S) == (uint32_t)a.colour &&
+    it.active = colour_of(a, a.Lnodes[lo]) == (uint32_t)a.colour &&
                 it.begin < it.end;
     return it;
 }
@@ -2057,7 +2083,8 @@ __global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
         if (!it.active) continue;  // uniform over the CTA
         const int32_t v = a.Lnodes[it.li];
         const int32_t own = a.lab[v], c = a.g.vwgt[v];
-        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+        const uint64_t h = nhash(a, v);
+        const int32_t lb = lbase(a, v);
         const int64_t off = a.Loff[it.li];
         const int32_t *gdl = a.gdl + a.Ldlo[it.li];
         unsigned long long best = 0;
@@ -2067,7 +2094,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
             const int32_t w = __ldcg(&a.gvals[off + slot]);
             if (L == own) a.hown[it.li] = w;
             else if (a.W[L] + c <= bnd(a, L)) {
-                const unsigned long long ck = cand_key(w, h, L);
+                const unsigned long long ck = cand_key(w, h, L - lb);
                 best = ck > best ? ck : best;
             }
         }
@@ -2095,7 +2122,8 @@ __global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
         if (!it.active) continue;
         const int32_t v = a.Lnodes[it.li];
         const int32_t own = a.lab[v], c = a.g.vwgt[v];
-        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+        const uint64_t h = nhash(a, v);
+        const int32_t lb = lbase(a, v);
         const int64_t off = a.Loff[it.li];
         const int32_t *gdl = a.gdl + a.Ldlo[it.li];
         const unsigned long long b = a.hbest[it.li];
@@ -2104,7 +2132,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
             const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
             const int32_t w = __ldcg(&a.gvals[off + slot]);
             if (b != 0 && L != own && (uint32_t)w == (uint32_t)(b >> 32) && a.W[L] + c <= bnd(a, L) &&
-                cand_key(w, h, L) == b)
+                cand_key(w, h, L - lb) == b)
                 atomicMin(&a.hbestL[it.li], L);
             a.gkeys[off + slot] = kEmpty;
             a.gvals[off + slot] = 0;
@@ -2119,7 +2147,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
          li += (int64_t)gridDim.x * blockDim.x) {
         if (a.Hfin[li + 1] == a.Hfin[li]) continue;  // single-piece row
         const int32_t v = a.Lnodes[li];
-        if (colour_of(a.seed, a.round, v, a.S) != (uint32_t)a.colour) continue;
+        if (colour_of(a, v) != (uint32_t)a.colour) continue;
         const unsigned long long b = a.hbest[li];
         const int32_t own = a.lab[v];
         if (b != 0) {
@@ -2207,7 +2235,8 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
         const int64_t deg = a.g.xadj[v + 1] - rs;
         const int32_t own = a.lab[v], c = a.g.vwgt[v];
         const int32_t cpv = (MODE == kCluster && a.cp) ? a.cp[v] : 0;
-        const uint64_t h = node_hash(a.seed, a.round, (uint32_t)v);
+        const uint64_t h = nhash(a, v);
+        const int32_t lb = lbase(a, v);
         int lbits = 6;  // slots per CTA: 2^lbits, total >= 2 * deg
         while (((int64_t)kHugeCS << lbits) < 2 * deg) lbits++;
         if (lbits > 12) {  // rows are routed here only up to kHugeDeg
@@ -2251,7 +2280,7 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
             const int32_t w = sm.vals[i];
             if ((int32_t)L == own) sm.cown = w;
             else if (a.W[L] + c <= bnd(a, (int32_t)L)) {
-                const unsigned long long ck = cand_key(w, h, (int32_t)L);
+                const unsigned long long ck = cand_key(w, h, (int32_t)L - lb);
                 best = ck > best ? ck : best;
             }
         }
@@ -2282,7 +2311,7 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
             if (L == kEmpty32) continue;
             const int32_t w = sm.vals[i];
             if (b != 0 && (int32_t)L != own && (uint32_t)w == (uint32_t)(b >> 32) &&
-                cand_key(w, h, (int32_t)L) == b && a.W[L] + c <= bnd(a, (int32_t)L))
+                cand_key(w, h, (int32_t)L - lb) == b && a.W[L] + c <= bnd(a, (int32_t)L))
                 atomicMin(&sm.cbestL, (int32_t)L);
             sm.keys[i] = kEmpty32;
             sm.vals[i] = 0;
@@ -2656,6 +2685,10 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.cp = cfg.refine ? nullptr : cfg.cp;
     a.seed = cfg.seed;
     a.S = S;
+    a.run_of = cfg.run_of;
+    a.run_seed = cfg.run_seed;
+    a.run_off = cfg.run_off;
+    a.run_k = cfg.run_k;
     a.tsum = sc.zeros<int64_t>(cfg.nW);
     a.tcnt = sc.zeros<int32_t>(cfg.nW);
     a.tbase = sc.get<int64_t>(cfg.nW);

@@ -23,6 +23,14 @@ struct LPConfig {
     // and returns whether the round is a full one.  A run stops only after a
     // full round without moves.
     std::function<bool(int round, const uint8_t **active)> before_round;
+    // Batched runs over a disjoint union (all null / 0 for one graph): run of
+    // every node, seed and first node of every run, blocks per run.  A run's
+    // sub-rounds and tie-breaks use its seed with its local node and block
+    // ids, so it evolves exactly as it would alone.
+    const int32_t *run_of = nullptr;
+    const uint64_t *run_seed = nullptr;
+    const int64_t *run_off = nullptr;
+    int32_t run_k = 0;
 };
 
 // Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)

@@ -277,12 +277,18 @@ def test_batched_runs_match_oracle():
     gs = [I.to_numpy(g) for g in gens]
     gd = [dev(g) for g in gens]
     rg = [3, 0, 2, 2, 1, 0, 3, 2, 1, 1, 0, 2]
+    seeds = [9 + 7 * r for r in range(len(rg))]
+    seeds[5] = 2**64 - 1
     for k in (4, 16):
-        want, wc, wm = oracle.refine_batched(gs, k, 0.03, 6, 4, 9, rg)
-        got, gc, gm = S.sclap_refine_batched(gd, k, 0.03, 6, 4, 9, rg)
+        want, wc, wm = oracle.refine_batched(gs, k, 0.03, 6, 4, seeds, rg)
+        got, gc, gm = S.sclap_refine_batched(gd, k, 0.03, 6, 4, seeds, rg)
         assert np.array_equal(gc.numpy(), wc) and np.array_equal(gm.numpy(), wm)
         for r in range(len(rg)):
             assert np.array_equal(got[r].cpu().numpy(), want[r]), (k, r)
+    # a run alone (batch of one) on the GPU equals the same run in the batch
+    for r in (0, 5, 11):
+        alone, ca, ma = S.sclap_refine_batched([gd[rg[r]]], 16, 0.03, 6, 4, [seeds[r]], [0])
+        assert np.array_equal(alone[0].cpu().numpy(), want[r]) and int(ca[0]) == int(wc[r])
 
 
 def test_population_batched_runs_match_oracle():
@@ -292,8 +298,9 @@ def test_population_batched_runs_match_oracle():
     gs = [I.to_numpy(g) for g in gens]
     gd = [dev(g) for g in gens]
     rg = [s % 8 for s in range(32)]
-    want, wc, wm = oracle.refine_batched(gs, 16, 0.03, 6, 4, 1, rg)
-    got, gc, gm = S.sclap_refine_batched(gd, 16, 0.03, 6, 4, 1, rg)
+    seeds = list(range(1, 33))
+    want, wc, wm = oracle.refine_batched(gs, 16, 0.03, 6, 4, seeds, rg)
+    got, gc, gm = S.sclap_refine_batched(gd, 16, 0.03, 6, 4, seeds, rg)
     assert np.array_equal(gc.numpy(), wc) and np.array_equal(gm.numpy(), wm)
     for r in range(len(rg)):
         assert np.array_equal(got[r].cpu().numpy(), want[r]), r

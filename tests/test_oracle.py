@@ -398,9 +398,8 @@ def test_multilevel_config1_shape_is_deterministic_and_balanced():
 
 # ---------------------------------------------------------------- batched runs
 
-def _lpt_by_hand(g, k, seed, r):
-    # the LPT start of run r written out from its definition
-    sr = brute.mix64(seed ^ ((0xD1B54A32D192ED03 * (r + 1)) & brute.M64))
+def _lpt_by_hand(g, k, sr):
+    # the LPT start of a run with seed sr written out from its definition
     n = len(g["vwgt"])
     order = sorted(range(n), key=lambda v: (-int(g["vwgt"][v]), brute.mix64(sr ^ v) >> 32, v))
     bw = [0] * k
@@ -415,9 +414,11 @@ def _lpt_by_hand(g, k, seed, r):
 def test_batched_runs_start_from_their_lpt_placement():
     gs = [I.to_numpy(I.random_graph(40, 90, seed=s, max_c=7, max_w=3)) for s in (1, 2)]
     rg = [0, 1, 1, 0]
-    parts, cuts, mx = oracle.refine_batched(gs, 3, 0.1, 0, 2, 77, rg)
+    seeds = [77, 78, 2**63 + 5, 77]
+    parts, cuts, mx = oracle.refine_batched(gs, 3, 0.1, 0, 2, seeds, rg)
     for r, g in enumerate(rg):
-        assert list(parts[r]) == _lpt_by_hand(gs[g], 3, 77, r)
+        assert list(parts[r]) == _lpt_by_hand(gs[g], 3, seeds[r])
+        assert list(oracle.lpt_start(gs[g], 3, seeds[r])) == list(parts[r])
         assert cuts[r] == brute.cut(gs[g], parts[r])
         assert mx[r] == max(brute.block_weights(gs[g], parts[r], 3))
 
@@ -426,14 +427,41 @@ def test_batched_runs_respect_their_own_bounds_and_report_consistently():
     gs = [I.to_numpy(I.random_graph(n, 4 * n, seed=n, max_c=9, max_w=5)) for n in (60, 200, 500)]
     k = 4
     rg = [2, 0, 1, 2, 1]
-    parts, cuts, mx = oracle.refine_batched(gs, k, 0.03, 6, 4, 5, rg)
+    seeds = [5, 6, 7, 8, 9]
+    parts, cuts, mx = oracle.refine_batched(gs, k, 0.03, 6, 4, seeds, rg)
     for r, g in enumerate(rg):
         B = oracle.lmax(int(gs[g]["vwgt"].sum()), k, 0.03)
         bw = brute.block_weights(gs[g], parts[r], k)
         assert cuts[r] == brute.cut(gs[g], parts[r]) and mx[r] == max(bw)
-        start = _lpt_by_hand(gs[g], k, 5, r)
+        start = _lpt_by_hand(gs[g], k, seeds[r])
         if max(brute.block_weights(gs[g], start, k)) <= B:
             assert max(bw) <= B   # a feasible start stays feasible
+
+
+def test_a_run_in_a_batch_equals_the_same_run_alone():
+    """Sec. II.C / IV.E: the individuals of a population are independent.  A
+    run's result must not depend on the other runs of its batch or on its
+    position: it equals the batch holding only that run, and that equals the
+    run's LPT start refined on its graph alone with its seed (the single-run
+    code path)."""
+    gs = [I.to_numpy(I.random_graph(n, 5 * n, seed=n + 1, max_c=6, max_w=7))
+          for n in (90, 300, 160)]
+    k, rounds, S = 4, 8, 3
+    rg = [1, 0, 2, 1, 1, 2, 0]
+    seeds = [11, 12, 13, 14, 11, 2**64 - 3, 17]
+    parts, cuts, mx = oracle.refine_batched(gs, k, 0.03, rounds, S, seeds, rg)
+    for r, g in enumerate(rg):
+        alone, ca, ma = oracle.refine_batched([gs[g]], k, 0.03, rounds, S, [seeds[r]], [0])
+        assert np.array_equal(parts[r], alone[0]) and cuts[r] == ca[0] and mx[r] == ma[0]
+        B = oracle.lmax(int(gs[g]["vwgt"].sum()), k, 0.03)
+        single, _ = oracle.refine_bound(gs[g], k, B, rounds, S, seeds[r],
+                                        oracle.lpt_start(gs[g], k, seeds[r]))
+        assert np.array_equal(parts[r], single)
+    # runs 1 and 4 share graph and seed: identical results at different positions
+    assert np.array_equal(parts[0], parts[4])
+    # the runs really moved nodes (the equalities above are not about starts)
+    assert any(not np.array_equal(parts[r], oracle.lpt_start(gs[g], k, seeds[r]))
+               for r, g in enumerate(rg))
 
 
 def test_initial_partition_is_the_best_of_batched_runs():
@@ -441,7 +469,8 @@ def test_initial_partition_is_the_best_of_batched_runs():
     k, P = 4, 5
     B = oracle.lmax(int(g["vwgt"].sum()), k, 0.03)
     part, cuts, mx, best = oracle.initial_partition(g, k, B, P, 4, 4, 21)
-    parts, bc, bm = oracle.refine_batched([g], k, 0.03, 4, 4, 21, [0] * P)
+    seeds = [brute.mix64(21 ^ ((0xD1B54A32D192ED03 * (t + 1)) & brute.M64)) for t in range(P)]
+    parts, bc, bm = oracle.refine_batched([g], k, 0.03, 4, 4, seeds, [0] * P)
     assert list(cuts) == list(bc) and list(mx) == list(bm)
     assert np.array_equal(part, parts[best])
 

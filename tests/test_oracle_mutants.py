@@ -35,6 +35,10 @@ MUTANTS = {
     "LPT ties to last block": ("if (bw[b] < bw[bb]) bb = b;", "if (bw[b] <= bw[bb]) bb = b;"),
     "mix64 constant": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
                        "z = (z ^ (z >> 27)) * 0x94D049BB133111EFULL;"),
+    "batched run keyed by its union node id": ("lv = v - rm->off[r];", "lv = v;"),
+    "batched ties on union block ids": ("uint32_t tl = or_tie(sv, round, lv, L - lb);",
+                                        "uint32_t tl = or_tie(sv, round, lv, L);"),
+    "batched runs share one seed": ("sv = rm->seed[r];", "sv = rm->seed[0];"),
     "coarse weight overwritten": ("for (int64_t v = 0; v < n; v++) cvwgt[f2c[v]] += vwgt[v];",
                                   "for (int64_t v = 0; v < n; v++) cvwgt[f2c[v]] = vwgt[v];"),
 }
