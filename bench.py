@@ -40,8 +40,12 @@ WORKLOAD = dict(workload="R-MAT scale 22, edge factor 16, a=0.57 b=0.19 c=0.19, 
                          "k=16, eps=0.03, l=3, r=6, S=4, n_stop=2000, 8 initial individuals",
                 scale=22, edge_factor=16, k=16, eps=0.03, cluster_rounds=3, refine_rounds=6,
                 subrounds=4, n_stop=2000, init_seeds=8, seed=1)
-# bounded sample for the CPU oracle: same generator and parameters, 1/16 of the nodes
-SAMPLE_SCALE = 18
+# the reference arm (the CPU oracle) times a bounded sample of the workload:
+# the same generator and parameters at the largest scale whose steps fit the
+# time budget (the oracle takes about 37 s per step at scale 22, halving per
+# scale step)
+ORACLE_S_SCALE22 = 37.0
+REFERENCE_BUDGET_S = 150.0
 
 
 def params_for(cfg, seed=None):
@@ -135,28 +139,50 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """SHA-256 (first 16 hex digits) of the propose kernels' source file."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1404_4797_gb300", "csrc", "lp.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def stored_traffic():
-    """Per-launch DRAM bytes of the propose kernel from the committed ncu summary
-    (profiles/propose_traffic.json), if one matches the current kernel build."""
+    """DRAM bytes per algorithmic byte of the propose step from the committed ncu
+    summary (profiles/propose_traffic.json), or None when the summary was taken
+    on another version of the kernels (its source hash differs)."""
     p = os.path.join(ROOT, "profiles", "propose_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         with open(p) as f:
             d = json.load(f)
-        return d
     except (OSError, ValueError):
         return None
+    if d.get("lp_cu_sha16") != kernel_source_hash() or "dram_per_algorithmic_byte" not in d:
+        return None
+    return d
+
+
+def reference_scale(steps, warmup, cap=22):
+    """Largest R-MAT scale <= cap whose (steps + warmup) oracle steps fit the
+    reference arm's time budget."""
+    total = max(1, steps + warmup)
+    s = cap
+    while s > 14 and total * ORACLE_S_SCALE22 / 2 ** (22 - s) > REFERENCE_BUDGET_S:
+        s -= 1
+    return s
 
 
 def run_reference(args, cfg):
-    """The oracle (plain single-threaded C) on a bounded sample of the workload."""
+    """The oracle (plain single-threaded C) on a bounded sample of the workload:
+    the same generator and parameters at the scale reference_scale picks."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     from paper_1404_4797_gb300 import inputs as I
-    g = I.to_numpy(I.rmat(SAMPLE_SCALE, cfg["edge_factor"], seed=cfg["seed"]))
+    scale = reference_scale(args.steps, args.warmup, cfg["scale"])
+    g = I.to_numpy(I.rmat(scale, cfg["edge_factor"], seed=cfg["seed"]))
     m = int(g["adjncy"].size) // 2
     params = params_for(cfg)
     for _ in range(args.warmup):
@@ -166,12 +192,15 @@ def run_reference(args, cfg):
         part, st = oracle.multilevel(g, params)
     dt = (time.perf_counter() - t0) / max(1, args.steps)
     value = m / dt / 1e9
-    sample = (f"R-MAT scale {SAMPLE_SCALE} (same generator and parameters as the workload, "
-              f"n={len(g['vwgt'])}, m={m}), full multilevel partition per step")
+    sample = (f"R-MAT scale {scale} (same generator and parameters as the workload, "
+              f"n={len(g['vwgt'])}, m={m}), full multilevel partition per step, one thread")
+    config = dict(cfg, scale=scale, n=len(g["vwgt"]), m=m,
+                  workload=cfg["workload"].replace(f"scale {cfg['scale']}", f"scale {scale}"),
+                  sample_of=f"R-MAT scale {cfg['scale']}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {k: cfg[k] for k in cfg},
+            "data": "synthetic", "config": config, "same_config": scale == cfg["scale"],
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
@@ -181,24 +210,58 @@ def run_reference(args, cfg):
     return 0
 
 
-def cpu_baseline(cfg, budget_s=20.0):
-    """Times the oracle's multilevel partition on the bounded sample (rank 0, N=1)."""
+def cpu_baseline(cfg, gn, m):
+    """Times the oracle's multilevel partition on the benchmark's own workload
+    (the same graph the GPU partitions), once, on one host core (rank 0, N=1)."""
     import oracle
-    from paper_1404_4797_gb300 import inputs as I
-    g = I.to_numpy(I.rmat(SAMPLE_SCALE, cfg["edge_factor"], seed=cfg["seed"]))
-    m = int(g["adjncy"].size) // 2
     params = params_for(cfg)
-    reps, total = 0, 0.0
-    while total < budget_s and reps < 5:
-        t0 = time.perf_counter()
-        oracle.multilevel(g, params)
-        total += time.perf_counter() - t0
-        reps += 1
-    dt = total / reps
+    t0 = time.perf_counter()
+    _, st = oracle.multilevel(gn, params)
+    dt = time.perf_counter() - t0
     return {"value": m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"R-MAT scale {SAMPLE_SCALE} (same generator/parameters, n={len(g['vwgt'])}, "
-                      f"m={m}); {reps} full multilevel partitions, single thread, "
-                      f"{dt:.2f} s each"}
+            "sample": f"the full workload (R-MAT scale {cfg['scale']}, n={len(gn['vwgt'])}, "
+                      f"m={m}): one multilevel partition, single thread, {dt:.1f} s",
+            "cut": st["cut"]}
+
+
+def sweep_gteps(S, I, cfg, g, n, m, dev, reps=3):
+    """SCLaP GTEPS of the level-0 sweeps: rounds x m / time of sclap_cluster
+    (l rounds, the multilevel driver's U and level-0 seed) and of sclap_refine
+    (r rounds from a seeded random k-way start), with the propose step's
+    algorithmic bandwidth in each."""
+    import torch
+    k = cfg["k"]
+    U = max(1, n // (10 * k))
+    p0 = I.rand_below(cfg["seed"], 7, torch.arange(n, device=dev), k).to(torch.int32)
+    calls = {
+        "cluster": (lambda: S.sclap_cluster(g, U, cfg["cluster_rounds"], cfg["subrounds"],
+                                            cfg["seed"]), lambda out: out[1]),
+        "refine": (lambda: S.sclap_refine(g, k, cfg["eps"], cfg["refine_rounds"],
+                                          cfg["subrounds"], cfg["seed"], p0),
+                   lambda out: out[3]),
+    }
+    res = {}
+    peak, _ = measured_peaks()
+    for name, (fn, rounds_of) in calls.items():
+        fn()
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        rd = 0
+        for _ in range(reps):
+            rd += rounds_of(fn())
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / reps
+        S.prof_enable(True)
+        S.prof_reset()
+        fn()
+        pr = S.prof_read()
+        S.prof_enable(False)
+        ach = pr["propose_bytes"] / (pr["propose_ms"] / 1e3) / 1e9 if pr["propose_ms"] else 0.0
+        res[name] = {"gteps": rd / reps * m / (ms / 1e3) / 1e9, "ms_per_call": ms,
+                     "rounds": rd / reps, "propose_gbs": ach, "propose_frac": ach / peak}
+    return res
 
 
 def run_phase(args, cfg, S, I, g, n, m, dev):
@@ -413,6 +476,33 @@ def run_batched(args, S, I, dev):
     return 0
 
 
+def run_config1(args, S, I, dev):
+    """Config 1: Chung-Lu n = 16,384 (exponent 2.1, mean degree 16, ~131k
+    edges), k = 4, eps = 0.03, 10 rounds per level, coarsening below 2000
+    nodes.  The graph fits in L2, so this line reports time and GTEPS only."""
+    import torch
+    g = I.to_device(I.chung_lu(16384, 2.1, 16.0, seed=1), dev)
+    m = I.num_edges(g)
+    params = S.default_params(4, 0.03, seed=1, cluster_rounds=10, refine_rounds=10,
+                              n_stop=2000)
+    S.set_validation(False)
+    for _ in range(args.warmup):
+        S.partition_multilevel(g, params)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        _, st = S.partition_multilevel(g, params)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    line = {"op": "config1", "n": int(g["vwgt"].numel()), "m": m, "k": 4, "ms_per_step": ms,
+            "gteps": m / (ms / 1e3) / 1e9, "cut": st["cut"], "cut_frac": st["cut"] / m,
+            "maxbw": st["maxbw"], "lmax": st["lmax"], "levels": st["n"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,7 +519,8 @@ def main():
     ap.add_argument("--train-samples", type=int, default=4_000_000,
                     help="--op learned: trace samples used for training")
     ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine",
-                                                           "learned", "batched", "vcycle"],
+                                                           "learned", "batched", "vcycle",
+                                                           "config1"],
                     help="time one SCLaP phase on the input graph instead (profiling aid)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
@@ -454,6 +545,8 @@ def main():
     S.lib()
     if args.op == "batched":
         return run_batched(args, S, I, dev)
+    if args.op == "config1":
+        return run_config1(args, S, I, dev)
     g = I.rmat(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"], device=dev)
     n = g["vwgt"].numel()
     m = I.num_edges(g)
@@ -475,9 +568,8 @@ def main():
     for _ in range(args.warmup):
         S.partition_multilevel(g, params, part_out=part)
 
-    # ---- device-resident timed region
-    S.prof_enable(True)
-    S.prof_reset()
+    # ---- device-resident timed region (instrumentation off)
+    S.prof_enable(False)
     launches0 = S.prof_read()["kernel_launches"]
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
                           else local)
@@ -494,10 +586,16 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (S.prof_read()["kernel_launches"] - launches0) // max(1, args.steps)
+    ms = max_over_ranks(ms, ws, dev)
+    # ---- one instrumented step: CUDA events around every propose step
+    S.prof_enable(True)
+    S.prof_reset()
+    prof_steps = 2
+    for _ in range(prof_steps):
+        S.partition_multilevel(g, params, part_out=part)
     prof = S.prof_read()
     S.prof_enable(False)
-    launches = (prof["kernel_launches"] - launches0) // max(1, args.steps)
-    ms = max_over_ranks(ms, ws, dev)
     value = job_gteps(m, ms, ws)
 
     # ---- end to end through the C ABI with host (pinned) buffers
@@ -520,6 +618,9 @@ def main():
         e2e = {"value": job_gteps(m, e2e_ms, ws), "unit": "GTEPS", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- level-0 SCLaP sweeps (GTEPS), outside the timed region
+    sweeps = sweep_gteps(S, I, cfg, g, n, m, dev)
+
     # ---- roofline of the dominant kernel (neighbour aggregation / propose)
     peak, peak_kind = measured_peaks()
     per_launch_ms = prof["propose_ms"] / max(1, prof["propose_launches"])
@@ -530,10 +631,11 @@ def main():
                 "kernel": "propose step (k_propose_small, k_propose, k_propose_huge per sub-round)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": tr.get("dram_bytes_per_launch") if tr else None,
+                "traffic": (tr["dram_per_algorithmic_byte"] * per_launch_bytes) if tr else None,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "launches": prof["propose_launches"], "ms_per_launch": per_launch_ms,
-                "share_of_step": prof["propose_ms"] / (ms * args.steps) if ms > 0 else None}
+                "share_of_step": prof["propose_ms"] / (ms * prof_steps) if ms > 0 else None,
+                "measured_in": f"{prof_steps} instrumented steps after the timed region"}
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -543,10 +645,13 @@ def main():
                        (h2d / 1e9), "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "cut": st["cut"], "maxbw": st["maxbw"], "lmax": st["lmax"], "levels": st["n"],
+            "cut_frac": st["cut"] / m, "random_split_cut_frac": 1.0 - 1.0 / cfg["k"],
+            "sclap_gteps": {k_: round(v["gteps"], 3) for k_, v in sweeps.items()},
+            "level0_sweeps": sweeps,
             "sclap_entries_per_s": prof["entries_scanned"] / (prof["propose_ms"] / 1e3)
             if prof["propose_ms"] > 0 else None}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg)
+        line["cpu_baseline"] = cpu_baseline(cfg, I.to_numpy(g), m)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

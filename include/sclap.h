@@ -278,7 +278,7 @@ typedef struct {
  *              concatenated in run order
  *   cuts_out, maxbw_out  host int64[nruns] (NULL allowed)
  * The rounds run as sclap_set_launch_mode says (by default all of them from
- * one captured CUDA graph).  Needs c(V) <= INT32_MAX per graph and every
+ * one captured CUDA graph, launched once).  Needs c(V) <= INT32_MAX per graph and every
  * weighted degree <= INT32_MAX. */
 int sclap_refine_batched(const sclap_batch *b, int32_t k, double eps, int32_t rounds,
                          int32_t subrounds, int32_t nruns, const int32_t *run_graph,
@@ -346,10 +346,12 @@ int sclap_set_validation(int on);
  *      the run after a full round without moves
  *   1  every round enqueued ahead; that test runs on the device and sets a
  *      flag after which the kernels of later rounds return at once
- *   2  (default) as 1, the rounds captured in one CUDA graph on a private
- *      stream that joins `stream`; while instrumentation is on, or if the
- *      runtime refuses the capture, the rounds are launched as in 1
- * Learned refinement always runs as 0.  Values outside 0..2 are clamped.
+ *   2  as 1, the rounds captured in one CUDA graph on a private stream that
+ *      joins `stream`; while instrumentation is on, or if the runtime
+ *      refuses the capture, the rounds are launched as in 1
+ *  -1  (default) 2 for the batched runs (sclap_refine_batched and the
+ *      initial partition's individuals), 0 for every other call
+ * Learned refinement always runs as 0.  Other values are clamped to -1..2.
  * Returns the previous mode. */
 int sclap_set_launch_mode(int mode);
 

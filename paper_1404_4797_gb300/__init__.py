@@ -184,8 +184,9 @@ def set_validation(on: bool) -> bool:
 
 def set_launch_mode(mode: int) -> int:
     """How a call's SCLaP rounds are launched (0 one round at a time, 1 all
-    enqueued ahead, 2 captured in a CUDA graph; results do not depend on it).
-    Returns the previous mode."""
+    enqueued ahead, 2 captured in a CUDA graph, -1 the default: 2 for batched
+    runs, 0 otherwise; results do not depend on it).  Returns the previous
+    mode."""
     return int(lib().sclap_set_launch_mode(int(mode)))
 
 

@@ -383,6 +383,7 @@ BatchResult batched_impl(const std::vector<DGraph> &G, const std::vector<int64_t
     cfg.run_seed = run_seed;
     cfg.run_off = run_off;
     cfg.run_k = k;
+    cfg.prefer_capture = true;
     lp_run(cfg, sc, nullptr, nullptr);
     int64_t *d_cut = sc.get<int64_t>(nruns);
     int64_t *d_bw = sc.get<int64_t>((int64_t)k * nruns);

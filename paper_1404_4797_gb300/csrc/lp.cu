@@ -2602,9 +2602,9 @@ __global__ void k_round_end(const int64_t *moves_r, const Ctr *ctr, int S, int32
     if (*moves_r == 0 && full) st[0] = 1;
 }
 
-static std::atomic<int> g_launch_mode{2};
+static std::atomic<int> g_launch_mode{-1};
 int launch_mode() { return g_launch_mode.load(); }
-int set_launch_mode(int mode) { return g_launch_mode.exchange(mode < 0 ? 0 : mode > 2 ? 2 : mode); }
+int set_launch_mode(int mode) { return g_launch_mode.exchange(mode < -1 ? -1 : mode > 2 ? 2 : mode); }
 
 // Captures what enqueue(cs) puts on a private stream cs (and on the streams
 // it forks from cs) into one CUDA graph and launches it after the work already
@@ -2905,7 +2905,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
 
     int done = 0;
     try {
-        const int lm = launch_mode();
+        const int lm = launch_mode() >= 0 ? launch_mode() : (cfg.prefer_capture ? 2 : 0);
         if (cfg.before_round || lm == 0) {
             // one round at a time, the host testing the stop rule after each
             // (always for learned refinement: the host prepares every round's

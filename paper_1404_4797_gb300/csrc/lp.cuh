@@ -31,6 +31,7 @@ struct LPConfig {
     const uint64_t *run_seed = nullptr;
     const int64_t *run_off = nullptr;
     int32_t run_k = 0;
+    bool prefer_capture = false;  // launch mode -1: capture this call's rounds
 };
 
 // Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)
@@ -44,8 +45,9 @@ void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, 
 
 // How a call's LP rounds are launched (results do not depend on it): 0 one
 // round at a time, the host testing the stop rule; 1 all rounds enqueued
-// ahead, a device flag ending them; 2 (default) as 1, captured in one CUDA
-// graph.  set_launch_mode returns the previous mode.
+// ahead, a device flag ending them; 2 as 1, captured in one CUDA graph; -1
+// (default) 2 for calls that prefer capture (batched runs), else 0.
+// set_launch_mode returns the previous mode.
 int launch_mode();
 int set_launch_mode(int mode);
 

@@ -337,9 +337,9 @@ def test_rounds_identical_in_every_launch_mode():
     p0 = I.rand_below(9, 7, torch.arange(n), 8).to(torch.int32).cuda()
     prm = S.default_params(8, 0.03, seed=3, n_stop=300)
     out = {}
-    old = S.set_launch_mode(2)
+    old = S.set_launch_mode(-1)
     try:
-        for mode in (0, 1, 2):
+        for mode in (0, 1, 2, -1):
             S.set_launch_mode(mode)
             lab, rd = S.sclap_cluster(gd, 40, 8, 4, 11)
             part, cut, bw, rdr = S.sclap_refine(gd, 8, 0.03, 40, 4, 5, p0)
@@ -348,7 +348,7 @@ def test_rounds_identical_in_every_launch_mode():
                          st["cut"], st["refine_rounds_done"], st["cluster_rounds_done"])
     finally:
         S.set_launch_mode(old)
-    for mode in (1, 2):
+    for mode in (1, 2, -1):
         for x, y in zip(out[0], out[mode]):
             if isinstance(x, np.ndarray):
                 assert np.array_equal(x, y)
