@@ -503,6 +503,43 @@ def run_config1(args, S, I, dev):
     return 0
 
 
+def run_coarsening(args, S, I, dev):
+    """Coarsening on a social-type graph (R-MAT) and a mesh-type graph (rgg,
+    Sec. V.A) of the same scale, with hash-coloured and degree-ordered
+    sub-rounds (Sec. III.A): level sizes, shrink per level, cut and time of
+    the multilevel partition (k = 16, the benchmark's parameters)."""
+    import torch
+    scale = args.scale or 22
+    out = {"op": "coarsening", "scale": scale}
+    for name, make in (("rmat", lambda: I.rmat(scale, 16, seed=1, device=dev)),
+                       ("rgg", lambda: I.rgg(scale, seed=1, device=dev))):
+        g = make()
+        m = I.num_edges(g)
+        S.set_validation(False)
+        for order in (0, 1):
+            prm = dict(params_for(WORKLOAD), degree_order=order)
+            S.partition_multilevel(g, prm)
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(args.steps):
+                _, st = S.partition_multilevel(g, prm)
+            ev1.record()
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            ns = st["n"]
+            out[f"{name}_{'degree' if order else 'hash'}"] = {
+                "n": int(g["vwgt"].numel()), "m": m, "ms": ms, "gteps": m / (ms / 1e3) / 1e9,
+                "levels": ns, "nnz": st["nnz"],
+                "shrink": [round(ns[i + 1] / ns[i], 4) for i in range(len(ns) - 1)],
+                "cut": st["cut"], "cut_frac": st["cut"] / m, "maxbw": st["maxbw"],
+                "lmax": st["lmax"]}
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -520,7 +557,7 @@ def main():
                     help="--op learned: trace samples used for training")
     ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine",
                                                            "learned", "batched", "vcycle",
-                                                           "config1"],
+                                                           "config1", "coarsening"],
                     help="time one SCLaP phase on the input graph instead (profiling aid)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
@@ -547,6 +584,8 @@ def main():
         return run_batched(args, S, I, dev)
     if args.op == "config1":
         return run_config1(args, S, I, dev)
+    if args.op == "coarsening":
+        return run_coarsening(args, S, I, dev)
     g = I.rmat(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"], device=dev)
     n = g["vwgt"].numel()
     m = I.num_edges(g)

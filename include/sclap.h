@@ -95,6 +95,8 @@ typedef struct {
     int32_t init_seeds;     /* P individuals in the initial partition           */
     int32_t init_rounds;    /* refinement rounds inside the initial partition   */
     uint64_t seed;
+    int32_t degree_order;   /* 1: coarsening in degree-ordered sub-rounds (see
+                               sclap_cluster_degree_ordered); 0: by hash       */
 } sclap_ml_params;
 
 #define SCLAP_MAX_LEVELS 64
@@ -127,6 +129,18 @@ typedef struct {
 int sclap_cluster(const sclap_graph *g, int64_t U, int32_t rounds, int32_t subrounds,
                   uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
                   int32_t *rounds_done, void *stream);
+
+/* sclap_cluster with degree-ordered sub-rounds, the synchronous counterpart
+ * of the paper's traversal in increasing degree while coarsening (Sec.
+ * III.A): in round r the nodes are ordered by (degree asc, high 32 bits of
+ * h(v, r) asc, v asc) and the node at position p acts in sub-round
+ * floor(p S / n) (S groups whose sizes differ by at most one, low degrees
+ * first).  Tie-breaks still use h(v, r).  With S = 1 it equals
+ * sclap_cluster.  Same arguments and errors as sclap_cluster. */
+int sclap_cluster_degree_ordered(const sclap_graph *g, int64_t U, int32_t rounds,
+                                 int32_t subrounds, uint64_t seed,
+                                 const int32_t *constraint_part, int32_t *labels_out,
+                                 int32_t *rounds_done, void *stream);
 
 /* SCLaP as local search on a k-partition, Sec. III.A (bound L_max, the
  * overloaded-block rule) and Sec. IV.B (exact block weights).

@@ -54,7 +54,7 @@ class MLParams(C.Structure):
                 ("cluster_rounds", C.c_int32), ("refine_rounds", C.c_int32),
                 ("subrounds", C.c_int32), ("n_stop", C.c_int64),
                 ("max_levels", C.c_int32), ("init_seeds", C.c_int32),
-                ("init_rounds", C.c_int32), ("seed", C.c_uint64)]
+                ("init_rounds", C.c_int32), ("seed", C.c_uint64), ("degree_order", C.c_int32)]
 
 
 class MLStats(C.Structure):
@@ -331,7 +331,7 @@ def refine_batched(graphs, k, eps, rounds, subrounds, seeds, run_graph):
 
 def default_params(k, eps=0.03, seed=1, **kw):
     p = dict(k=k, eps=eps, U=0, cluster_rounds=3, refine_rounds=6, subrounds=4, n_stop=2000,
-             max_levels=32, init_seeds=8, init_rounds=6, seed=seed)
+             max_levels=32, init_seeds=8, init_rounds=6, seed=seed, degree_order=0)
     p.update(kw)
     return p
 

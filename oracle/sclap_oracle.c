@@ -912,8 +912,9 @@ static int multilevel_impl(int64_t n, const int64_t *xadj, const int32_t *adjncy
         g->f2c = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n ? g->n : 1));
         if (!lab || !g->f2c) { free(lab); rc = OR_ENOMEM; goto out; }
         int32_t rd = 0;
-        rc = or_cluster(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, U, p->cluster_rounds,
-                        p->subrounds, level_seed(p->seed, L), cpl[L], lab, &rd, NULL);
+        rc = cluster_impl(g->n, g->xadj, g->adjncy, g->adjwgt, g->vwgt, U, p->cluster_rounds,
+                          p->subrounds, level_seed(p->seed, L), cpl[L], p->degree_order != 0,
+                          lab, &rd, NULL);
         if (rc) { free(lab); goto out; }
         st->cluster_rounds_done[L] = rd;
         level *c = &lv[L + 1];

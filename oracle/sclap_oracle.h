@@ -39,6 +39,7 @@ typedef struct {
     int32_t init_seeds;     /* P: initial-partition population size        */
     int32_t init_rounds;    /* refinement rounds inside initial partition   */
     uint64_t seed;
+    int32_t degree_order;   /* 1: degree-ordered clustering sub-rounds      */
 } or_ml_params;
 
 #define OR_MAX_LEVELS 64

@@ -53,7 +53,8 @@ class MLParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("eps", C.c_double), ("U", C.c_int64),
                 ("cluster_rounds", C.c_int32), ("refine_rounds", C.c_int32),
                 ("subrounds", C.c_int32), ("n_stop", C.c_int64), ("max_levels", C.c_int32),
-                ("init_seeds", C.c_int32), ("init_rounds", C.c_int32), ("seed", C.c_uint64)]
+                ("init_seeds", C.c_int32), ("init_rounds", C.c_int32), ("seed", C.c_uint64),
+                ("degree_order", C.c_int32)]
 
 
 class MLStats(C.Structure):
@@ -85,6 +86,8 @@ _SIGS = {
     "sclap_ml_defaults": (None, [C.POINTER(MLParams), C.c_int32, C.c_double, C.c_uint64]),
     "sclap_cluster": (C.c_int, [C.POINTER(Graph), C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
                                 _VP, _VP, _P32, _VP]),
+    "sclap_cluster_degree_ordered": (C.c_int, [C.POINTER(Graph), C.c_int64, C.c_int32, C.c_int32,
+                                               C.c_uint64, _VP, _VP, _P32, _VP]),
     "sclap_refine": (C.c_int, [C.POINTER(Graph), C.c_int32, C.c_double, C.c_int32, C.c_int32,
                                C.c_uint64, _VP, _P64, _P64, _P32, _VP]),
     "sclap_refine_bound": (C.c_int, [C.POINTER(Graph), C.c_int32, C.c_int64, C.c_int32, C.c_int32,
@@ -191,16 +194,18 @@ def set_launch_mode(mode: int) -> int:
 
 
 def sclap_cluster(g: dict, U: int, rounds: int, subrounds: int = 4, seed: int = 1,
-                  constraint_part: torch.Tensor | None = None, stream=None):
-    """Size-constrained clustering (Sec. III.A).  Returns (labels, rounds_done)."""
+                  constraint_part: torch.Tensor | None = None, stream=None,
+                  degree_ordered: bool = False):
+    """Size-constrained clustering (Sec. III.A), by hash-coloured or (with
+    degree_ordered) degree-ordered sub-rounds.  Returns (labels, rounds_done)."""
     _require_cuda(g["xadj"], constraint_part)
     n = g["vwgt"].numel()
     labels = torch.empty(n, dtype=torch.int32, device=g["xadj"].device)
     rd = C.c_int32(0)
     gg = _graph(g)
-    _check(lib().sclap_cluster(C.byref(gg), U, rounds, subrounds, seed & (2**64 - 1),
-                               _ptr(constraint_part), _ptr(labels), C.byref(rd), _stream(stream)),
-           "sclap_cluster")
+    fn = lib().sclap_cluster_degree_ordered if degree_ordered else lib().sclap_cluster
+    _check(fn(C.byref(gg), U, rounds, subrounds, seed & (2**64 - 1), _ptr(constraint_part),
+              _ptr(labels), C.byref(rd), _stream(stream)), "sclap_cluster")
     return labels, rd.value
 
 

@@ -520,9 +520,9 @@ void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed)
     p->seed = seed;
 }
 
-int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subrounds,
-                  uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
-                  int32_t *rounds_done, void *stream) {
+static int cluster_call(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subrounds,
+                        uint64_t seed, const int32_t *constraint_part, bool degree_order,
+                        int32_t *labels_out, int32_t *rounds_done, void *stream) {
     return guarded([&] {
         if (!gp || (!labels_out && gp->n > 0)) fail(SCLAP_EINVAL, "null");
         if (rounds < 0 || subrounds < 1 || subrounds > 32) fail(SCLAP_EINVAL, "rounds");
@@ -543,6 +543,7 @@ int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subr
         cfg.seed = seed;
         cfg.rounds = rounds;
         cfg.S = subrounds;
+        cfg.degree_order = degree_order;
         int rd = 0;
         if (rounds > 0 && g.n > 0) rd = lp_run(cfg, sc, nullptr, nullptr);
         else identity_labels(g.n, labels_out, s);
@@ -550,6 +551,21 @@ int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subr
         CK(cudaStreamSynchronize(s));
         if (rounds_done) *rounds_done = rd;
     });
+}
+
+int sclap_cluster(const sclap_graph *gp, int64_t U, int32_t rounds, int32_t subrounds,
+                  uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
+                  int32_t *rounds_done, void *stream) {
+    return cluster_call(gp, U, rounds, subrounds, seed, constraint_part, false, labels_out,
+                        rounds_done, stream);
+}
+
+int sclap_cluster_degree_ordered(const sclap_graph *gp, int64_t U, int32_t rounds,
+                                 int32_t subrounds, uint64_t seed,
+                                 const int32_t *constraint_part, int32_t *labels_out,
+                                 int32_t *rounds_done, void *stream) {
+    return cluster_call(gp, U, rounds, subrounds, seed, constraint_part, true, labels_out,
+                        rounds_done, stream);
 }
 
 int sclap_refine_bound(const sclap_graph *gp, int32_t nblocks, int64_t B, int32_t rounds,
@@ -970,6 +986,7 @@ static int multilevel_call(const sclap_graph *gp, const sclap_ml_params *p,
             cfg.rounds = p->cluster_rounds;
             cfg.S = p->subrounds;
             cfg.cp = seed_part ? CP[L] : nullptr;
+            cfg.degree_order = p->degree_order != 0;
             int rd = 0;
             if (cfg.rounds > 0) rd = lp_run(cfg, tmp, nullptr, nullptr);
             else identity_labels(g.n, lab, s);

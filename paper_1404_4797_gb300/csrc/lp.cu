@@ -197,6 +197,7 @@ struct LPArgs {
     const uint64_t *run_seed;
     const int64_t *run_off;
     int32_t run_k;
+    const int32_t *col;        // degree-ordered sub-rounds: sub-round per node (null: hash)
 };
 
 // Every kernel of a round returns at once after the run has ended (the rounds
@@ -233,6 +234,7 @@ __device__ __forceinline__ uint32_t tie_of(uint64_t h, int32_t L) {
 }
 
 __device__ __forceinline__ uint32_t colour_of(const LPArgs &a, int32_t v) {
+    if (a.col) return (uint32_t)__ldg(&a.col[v]);
     return (uint32_t)(nhash(a, v) >> 32) % (uint32_t)a.S;
 }
 
@@ -2590,6 +2592,26 @@ static void launch_rows(const LPArgs &a, int k, const RowGrids &rg, cudaStream_t
     LAUNCHED();
 }
 
+// Degree-ordered sub-rounds (Sec. III.A visits nodes in increasing degree
+// when coarsening): in round r the nodes in (degree asc, high 32 bits of
+// h(v, r) asc, v asc) order, the node at position p acting in sub-round
+// floor(p S / n).  Keys for the stable sort (v order breaks the last ties):
+__global__ void k_degree_keys(DGraph g, uint64_t seed, int32_t round, uint64_t *key,
+                              int32_t *val) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = (uint64_t)(g.xadj[v + 1] - g.xadj[v]);
+        key[v] = (d << 32) | (node_hash(seed, round, (uint32_t)v) >> 32);
+        val[v] = (int32_t)v;
+    }
+}
+
+__global__ void k_degree_colours(int64_t n, int S, const int32_t *order, int32_t *col) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        col[order[p]] = (int32_t)(p * S / n);
+}
+
 // End of round r: the errors of its sub-rounds are kept, the rounds done
 // counted, and the run stops after a full round without moves.
 __global__ void k_round_end(const int64_t *moves_r, const Ctr *ctr, int S, int32_t *st, int r,
@@ -2689,6 +2711,17 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.run_seed = cfg.run_seed;
     a.run_off = cfg.run_off;
     a.run_k = cfg.run_k;
+    // degree-ordered sub-rounds: sort keys, order and colour per node
+    uint64_t *dkey = nullptr;
+    int32_t *dord = nullptr, *dcol = nullptr;
+    int dbits = 0;
+    if (cfg.degree_order) {
+        if (cfg.run_of) fail(SCLAP_EINVAL, "degree order with batched runs");
+        dkey = sc.get<uint64_t>(g.n);
+        dord = sc.get<int32_t>(g.n);
+        dcol = sc.get<int32_t>(g.n);
+        dbits = 32 + std::max(1, bit_width_u64((uint64_t)graph_totals(g, sc).max_deg));
+    }
     a.tsum = sc.zeros<int64_t>(cfg.nW);
     a.tcnt = sc.zeros<int32_t>(cfg.nW);
     a.tbase = sc.get<int64_t>(cfg.nW);
@@ -2814,6 +2847,14 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     auto enqueue_round = [&](int r, bool full, cudaStream_t ms) {
         a.round = r;
         a.moves = d_moves + r;
+        if (cfg.degree_order) {  // this round's sub-round of every node (stream ms == s)
+            k_degree_keys<<<sms * 4, 256, 0, ms>>>(g, cfg.seed, r, dkey, dord);
+            LAUNCHED();
+            radix_sort_pairs(dkey, dord, g.n, dbits, sc);
+            k_degree_colours<<<sms * 4, 256, 0, ms>>>(g.n, S, dord, dcol);
+            LAUNCHED();
+            a.col = dcol;
+        }
         CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + (2 + kPipeClasses) * S) * sizeof(int32_t), ms));
         CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), ms));
         k_build_wl<<<sms * 4, kThreads, 0, ms>>>(a, wl, wl_cnt);
@@ -2905,7 +2946,9 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
 
     int done = 0;
     try {
-        const int lm = launch_mode() >= 0 ? launch_mode() : (cfg.prefer_capture ? 2 : 0);
+        // degree-ordered rounds sort on the call's stream: one round at a time
+        const int lm = cfg.degree_order ? 0
+                       : launch_mode() >= 0 ? launch_mode() : (cfg.prefer_capture ? 2 : 0);
         if (cfg.before_round || lm == 0) {
             // one round at a time, the host testing the stop rule after each
             // (always for learned refinement: the host prepares every round's

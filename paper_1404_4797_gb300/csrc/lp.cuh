@@ -32,6 +32,9 @@ struct LPConfig {
     const int64_t *run_off = nullptr;
     int32_t run_k = 0;
     bool prefer_capture = false;  // launch mode -1: capture this call's rounds
+    // Clustering: sub-rounds by degree quantile (low degrees first) instead
+    // of by hash (Sec. III.A's increasing-degree order while coarsening).
+    bool degree_order = false;
 };
 
 // Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)

@@ -221,6 +221,53 @@ def web_graph(n: int = 1 << 26, gamma: float = 2.0, mean_deg: float = 32.0,
     return csr_from_edges(n, perm[a], perm[b])
 
 
+def rgg(scale: int, seed: int = 1, device="cpu", radius_factor: float = 0.55) -> dict:
+    """Random geometric graph rggX (the paper's mesh-type family, Sec. V.A):
+    n = 2^scale points uniform in the unit square, an edge between two points
+    whose Euclidean distance is below radius_factor * sqrt(ln n / n); unit
+    weights.  Node ids follow the points' grid-cell order (row-major cells of
+    side >= the radius), so neighbours have nearby ids as in mesh orderings.
+    Pairs are found cell by cell: each point against its own cell (higher ids)
+    and four of its eight neighbouring cells, which covers every pair once."""
+    n = 1 << scale
+    r = radius_factor * math.sqrt(math.log(n) / n)
+    idx = torch.arange(n, dtype=torch.int64, device=device)
+    x = rand_uniform(seed, 700, idx)
+    y = rand_uniform(seed, 701, idx)
+    G = max(1, int(1.0 / r))                   # G x G cells of side 1/G >= r
+    cx = torch.clamp((x * G).to(torch.int64), max=G - 1)
+    cy = torch.clamp((y * G).to(torch.int64), max=G - 1)
+    order = torch.argsort(cy * G + cx, stable=True)
+    x, y, cx, cy = x[order], y[order], cx[order], cy[order]
+    cell = cy * G + cx
+    counts = torch.bincount(cell, minlength=G * G)
+    start = torch.cumsum(counts, 0) - counts
+    us, vs = [], []
+    r2 = r * r
+    for dx, dy in ((0, 0), (1, 0), (-1, 1), (0, 1), (1, 1)):
+        nx, ny = cx + dx, cy + dy
+        ok = (nx >= 0) & (nx < G) & (ny < G)
+        p = idx[ok]
+        nc = (ny * G + nx)[ok]
+        cnt = counts[nc]
+        tot = int(cnt.sum())
+        if tot == 0:
+            continue
+        rep_p = torch.repeat_interleave(p, cnt)
+        base = torch.repeat_interleave(start[nc] - (torch.cumsum(cnt, 0) - cnt), cnt)
+        q = base + torch.arange(tot, dtype=torch.int64, device=device)
+        d2 = (x[rep_p] - x[q]) ** 2 + (y[rep_p] - y[q]) ** 2
+        keep = d2 < r2
+        if dx == 0 and dy == 0:
+            keep &= q > rep_p
+        us.append(rep_p[keep])
+        vs.append(q[keep])
+        del rep_p, base, q, d2, keep
+    u = torch.cat(us) if us else idx[:0]
+    v = torch.cat(vs) if vs else idx[:0]
+    return csr_from_edges(n, u, v)
+
+
 def population(count: int = 32, nmin: int = 2000, nmax: int = 200000, seed: int = 1,
                device="cpu") -> list:
     """Coarse-graph population: `count` Chung-Lu graphs (gamma 2.1, mean degree

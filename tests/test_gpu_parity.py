@@ -358,3 +358,38 @@ def test_rounds_identical_in_every_launch_mode():
     # the stop rule ended it
     gn = I.to_numpy(g)
     assert out[2][4] == oracle.refine(gn, 8, 0.03, 40, 4, 5, p0.cpu().numpy())[3] < 40
+
+
+@pytest.mark.parametrize("S_", [1, 3, 4])
+def test_degree_ordered_cluster_matches_oracle(S_):
+    """Degree-ordered sub-rounds (Sec. III.A's increasing-degree traversal): a
+    per-round sort on the GPU against the oracle's order, bit for bit."""
+    for g in (I.chung_lu(4096, 2.1, 8.0, seed=3), I.random_graph(5000, 20000, seed=5, max_w=20,
+                                                                  max_c=9), I.rmat(13, 16, seed=2)):
+        gn = I.to_numpy(g)
+        cV = int(gn["vwgt"].sum())
+        U = max(int(gn["vwgt"].max()), cV // 40)
+        want, wr = oracle.cluster(gn, U, 6, S_, 7, degree_ordered=True)
+        got, gr = S.sclap_cluster(dev(g), U, 6, S_, 7, degree_ordered=True)
+        assert gr == wr and np.array_equal(got.cpu().numpy(), want)
+
+
+def test_multilevel_and_vcycle_degree_ordered_match_oracle():
+    g = I.chung_lu(8192, 2.1, 12.0, seed=9)
+    gn = I.to_numpy(g)
+    prm = S.default_params(8, 0.03, seed=5, n_stop=400, degree_order=1)
+    got, st = S.partition_multilevel(dev(g), prm)
+    want, ws = oracle.multilevel(gn, dict(prm))
+    assert st == ws and np.array_equal(got.cpu().numpy(), want)
+    got2, st2 = S.sclap_vcycle(dev(g), dict(prm, seed=6), got)
+    want2, ws2 = oracle.vcycle(gn, dict(prm, seed=6), want)
+    assert st2 == ws2 and np.array_equal(got2.cpu().numpy(), want2)
+
+
+def test_rgg_multilevel_matches_oracle():
+    g = I.rgg(14, seed=4)
+    gn = I.to_numpy(g)
+    prm = S.default_params(16, 0.03, seed=2, n_stop=500)
+    got, st = S.partition_multilevel(dev(g), prm)
+    want, ws = oracle.multilevel(gn, dict(prm))
+    assert st == ws and np.array_equal(got.cpu().numpy(), want)

@@ -64,8 +64,9 @@ MUTANTS_ELSEWHERE = {
     "gated round ends the run": ("if (full && m == 0) break;", "if (m == 0) break;",
                                  "test_oracle_learned.py"),
     "V-cycle clustering unconstrained": (
-        "p->subrounds, level_seed(p->seed, L), cpl[L], lab, &rd, NULL);",
-        "p->subrounds, level_seed(p->seed, L), NULL, lab, &rd, NULL);", "test_oracle_vcycle.py"),
+        "p->subrounds, level_seed(p->seed, L), cpl[L], p->degree_order != 0,",
+        "p->subrounds, level_seed(p->seed, L), NULL, p->degree_order != 0,",
+        "test_oracle_vcycle.py"),
     "V-cycle coarse blocks not inherited": ("cpl[L + 1][g->f2c[v]] = cpl[L][v];",
                                             "cpl[L + 1][g->f2c[v]] = 0;", "test_oracle_vcycle.py"),
     "high degree first": ("if (x->deg != y->deg) return x->deg < y->deg ? -1 : 1;",
