@@ -598,6 +598,12 @@ def main():
             torch.distributed.barrier()
 
     part = torch.empty(n, dtype=torch.int32, device=dev)
+    # degree-bin and segment thresholds: the autotuner's choice for this device
+    # and workload (cached per device and graph signature; results do not
+    # depend on it)
+    from paper_1404_4797_gb300 import autotune
+    tune = autotune.load_or_tune(g, cfg["k"], cfg["eps"], cfg["cluster_rounds"],
+                                 cfg["refine_rounds"], cfg["subrounds"], cfg["seed"])
     if args.op == "learned":
         return run_learned(args, cfg, S, I, g, n, m, dev)
     if args.op == "vcycle":
@@ -683,6 +689,7 @@ def main():
             "config": {**cfg, "n": n, "m": m, "l2": "inputs larger than L2 (CSR %.2f GB)" %
                        (h2d / 1e9), "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "tuning": dict(tune["best"], cached=tune["cached"]),
             "cut": st["cut"], "maxbw": st["maxbw"], "lmax": st["lmax"], "levels": st["n"],
             "cut_frac": st["cut"] / m, "random_split_cut_frac": 1.0 - 1.0 / cfg["k"],
             "sclap_gteps": {k_: round(v["gteps"], 3) for k_, v in sweeps.items()},

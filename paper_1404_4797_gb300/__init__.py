@@ -67,6 +67,11 @@ class MLStats(C.Structure):
                 ("maxbw", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("small_max", C.c_int32), ("med_max", C.c_int32), ("mid_max", C.c_int32),
+                ("seg_smem", C.c_int32)]
+
+
 class Prof(C.Structure):
     _fields_ = [("propose_launches", C.c_int64), ("propose_ms", C.c_double),
                 ("propose_bytes", C.c_double), ("entries_scanned", C.c_int64),
@@ -83,6 +88,8 @@ _SIGS = {
     "sclap_strerror": (C.c_char_p, [C.c_int]),
     "sclap_set_validation": (C.c_int, [C.c_int]),
     "sclap_set_launch_mode": (C.c_int, [C.c_int]),
+    "sclap_set_tuning": (C.c_int, [C.POINTER(Tuning)]),
+    "sclap_get_tuning": (None, [C.POINTER(Tuning)]),
     "sclap_ml_defaults": (None, [C.POINTER(MLParams), C.c_int32, C.c_double, C.c_uint64]),
     "sclap_cluster": (C.c_int, [C.POINTER(Graph), C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
                                 _VP, _VP, _P32, _VP]),
@@ -191,6 +198,19 @@ def set_launch_mode(mode: int) -> int:
     runs, 0 otherwise; results do not depend on it).  Returns the previous
     mode."""
     return int(lib().sclap_set_launch_mode(int(mode)))
+
+
+def get_tuning() -> dict:
+    """The degree-bin and segment thresholds later calls use."""
+    t = Tuning()
+    lib().sclap_get_tuning(C.byref(t))
+    return {name: getattr(t, name) for name, _ in Tuning._fields_}
+
+
+def set_tuning(small_max: int, med_max: int, mid_max: int, seg_smem: int):
+    """Sets the thresholds (results do not depend on them; see sclap.h)."""
+    _check(lib().sclap_set_tuning(C.byref(Tuning(small_max, med_max, mid_max, seg_smem))),
+           "sclap_set_tuning")
 
 
 def sclap_cluster(g: dict, U: int, rounds: int, subrounds: int = 4, seed: int = 1,

@@ -499,6 +499,21 @@ const char *sclap_strerror(int code) {
 
 int sclap_set_launch_mode(int mode) { return set_launch_mode(mode); }
 
+int sclap_set_tuning(const sclap_tuning *t) {
+    if (!t) return SCLAP_EINVAL;
+    return set_tuning(Tuning{t->small_max, t->med_max, t->mid_max, t->seg_smem}) ? SCLAP_OK
+                                                                                : SCLAP_EINVAL;
+}
+
+void sclap_get_tuning(sclap_tuning *t) {
+    if (!t) return;
+    const Tuning x = tuning();
+    t->small_max = x.small_max;
+    t->med_max = x.med_max;
+    t->mid_max = x.mid_max;
+    t->seg_smem = x.seg_smem;
+}
+
 int sclap_set_validation(int on) {
     int old = g_validate ? 1 : 0;
     g_validate = on != 0;

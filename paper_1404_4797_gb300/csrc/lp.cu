@@ -44,6 +44,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "lp.cuh"
@@ -180,6 +181,7 @@ struct LPArgs {
     // in pc[q][c]
     int32_t *pl[kPipeClasses];
     int32_t *pc[kPipeClasses];
+    int64_t nP;                // capacity of each colour's pipelined list
     // segments above kSegSmem entries (arbitrated by the whole grid)
     BigSeg *big;
     int32_t *tileseg;          // tile -> index into big
@@ -198,6 +200,7 @@ struct LPArgs {
     const int64_t *run_off;
     int32_t run_k;
     const int32_t *col;        // degree-ordered sub-rounds: sub-round per node (null: hash)
+    Tuning t;                  // degree-bin and segment thresholds of this call
 };
 
 // Every kernel of a round returns at once after the run has ended (the rounds
@@ -287,8 +290,9 @@ __device__ __forceinline__ void wd_flush(const LPArgs &a, WDelta &wd) {
 
 // ---------------------------------------------------------------- worklists
 
-__device__ __forceinline__ int degree_class(int64_t d) {
-    return d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= kSmallDeg ? 3 : 4;
+__device__ __forceinline__ int degree_class(int64_t d, int small_max) {
+    if (d > small_max) return 4;
+    return d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : 3;
 }
 
 // Length class of a row of kMedDeg < d <= kMidDeg entries (pipelined kernels).
@@ -318,14 +322,14 @@ __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, in
                     p_entries += (unsigned long long)d;
                     p_nodes++;
                     const uint32_t col = colour_of(a, (int32_t)v);
-                    if (d <= kMedDeg) {
-                        bk[j] = kClasses * (int)col + degree_class(d);
+                    if (d <= a.t.med_max) {
+                        bk[j] = kClasses * (int)col + degree_class(d, a.t.small_max);
                         rk[j] = atomicAdd(&lcnt[bk[j]], 1);
-                    } else if (d <= kMidDeg) {
+                    } else if (d <= a.t.mid_max) {
                         // a mid row: the pipelined kernel of its length class
                         const int q = pipe_class(d);
                         const int pos = atomicAdd(&a.pc[q][col], 1);
-                        a.pl[q][(int64_t)col * a.nL + pos] = (int32_t)v;
+                        a.pl[q][(int64_t)col * a.nP + pos] = (int32_t)v;
                     } else {
                         // a large row: list its pieces for sub-round `col`
                         int64_t lo = 0, hi = a.nL;  // li: Lnodes[li] == v
@@ -989,7 +993,7 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
     PipeSm<MODE, PS> &sm = *reinterpret_cast<PipeSm<MODE, PS> *>(smraw);
     constexpr int NT = PS::kNT, E = PS::kE, NW = NT / 32;
     constexpr bool DENSE = MODE == kRefineDense;
-    const int32_t *list = a.pl[cls] + (int64_t)a.colour * a.nL;
+    const int32_t *list = a.pl[cls] + (int64_t)a.colour * a.nP;
     const int cnt = a.pc[cls][a.colour];
     const int G = gridDim.x;
     int idx = blockIdx.x;
@@ -1676,7 +1680,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
                                                     (unsigned long long)cnt);
             a.tbase[p.T] = base;
             a.segs[si] = Seg{p.T, cnt, base, cap + 1};
-            if (cnt > kSegSmem) {
+            if (cnt > a.t.seg_smem) {
                 const int nt = (cnt + kBigTile - 1) / kBigTile;
                 const int bi = atomicAdd(&a.ctr->nbig, 1);
                 const int t0 = atomicAdd(&a.ctr->bigtiles, nt);
@@ -2002,7 +2006,7 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
     // medium segments: one CTA each, staged in shared memory
     for (int si = blockIdx.x; si < nseg; si += gridDim.x) {
         const Seg sg = a.segs[si];
-        if (sg.cnt <= 32 || sg.cnt > kSegSmem) continue;
+        if (sg.cnt <= 32 || sg.cnt > a.t.seg_smem) continue;
         const SegEntry *ent = a.segbuf + sg.base;
         stage_segment(ent, sg.cnt, sm.keys, sm.c);
         __syncthreads();
@@ -2357,6 +2361,13 @@ struct LargeFlag {
     __device__ int64_t operator()(int64_t v) const { return xadj[v + 1] - xadj[v] > kMedDeg ? 1 : 0; }
 };
 
+// Rows longer than the warp path takes (the pipelined lists' capacity).
+struct PipeFlag {
+    const int64_t *xadj;
+    int64_t med_max;
+    __device__ int64_t operator()(int64_t v) const { return xadj[v + 1] - xadj[v] > med_max ? 1 : 0; }
+};
+
 __global__ void k_large_compact(DGraph g, const int64_t *pos, int32_t *Lnodes) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n;
          v += (int64_t)gridDim.x * blockDim.x)
@@ -2624,6 +2635,24 @@ __global__ void k_round_end(const int64_t *moves_r, const Ctr *ctr, int S, int32
     if (*moves_r == 0 && full) st[0] = 1;
 }
 
+static std::mutex g_tune_mu;
+static Tuning g_tune{kSmallDeg, kMedDeg, kMidDeg, kSegSmem};
+Tuning tuning() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
+bool set_tuning(const Tuning &t) {
+    const bool ok = (t.small_max == 4 || t.small_max == 8 || t.small_max == 16 ||
+                     t.small_max == 32) &&
+                    t.med_max >= t.small_max && t.med_max <= kMedDeg &&
+                    (t.mid_max == 512 || t.mid_max == 1024 || t.mid_max == kMidDeg) &&
+                    t.seg_smem >= 64 && t.seg_smem <= kSegSmem;
+    if (!ok) return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = t;
+    return true;
+}
+
 static std::atomic<int> g_launch_mode{-1};
 int launch_mode() { return g_launch_mode.load(); }
 int set_launch_mode(int mode) { return g_launch_mode.exchange(mode < -1 ? -1 : mode > 2 ? 2 : mode); }
@@ -2729,8 +2758,9 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.props = sc.get<Prop>(g.n);
     a.segs = sc.get<Seg>(g.n);
     a.segbuf = sc.get<SegEntry>(g.n);
-    // every big segment holds more than kSegSmem of the <= n proposals
-    a.maxbig = (int32_t)std::min<int64_t>(g.n / (kSegSmem + 1) + 1, cfg.nW);
+    // every big segment holds more than seg_smem of the <= n proposals
+    a.t = tuning();
+    a.maxbig = (int32_t)std::min<int64_t>(g.n / (a.t.seg_smem + 1) + 1, cfg.nW);
     a.maxtiles = (int32_t)(g.n / kBigTile + a.maxbig + 1);
     a.big = sc.get<BigSeg>(a.maxbig);
     a.tileseg = sc.get<int32_t>(a.maxtiles);
@@ -2760,6 +2790,19 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
         CK(cudaMemcpyAsync(&nL, d_nL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         a.nL = nL;
+        // pipelined lists: room for every row above med_max (the large rows
+        // when med_max is kMedDeg)
+        int64_t nP = nL;
+        if (a.t.med_max < kMedDeg) {
+            int64_t *ppos = sc.get<int64_t>(g.n);
+            int64_t *d_nP = sc.get<int64_t>(1);
+            exclusive_scan(PipeFlag{g.xadj, a.t.med_max}, g.n, ppos, d_nP, sc);
+            CK(cudaMemcpyAsync(&nP, d_nP, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        a.nP = nP;
+        if (nP > 0)
+            for (int q = 0; q < kPipeClasses; q++) a.pl[q] = sc.get<int32_t>((size_t)S * nP);
         if (nL > 0) {
             int32_t *Lnodes = sc.get<int32_t>(nL);
             k_large_compact<<<sms * 4, 256, 0, s>>>(g, pos, Lnodes);
@@ -2772,7 +2815,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             CK(cudaStreamSynchronize(s));
             a.plist = sc.get<int64_t>((size_t)S * (a.Ptot ? a.Ptot : 1));
             a.hlist = sc.get<int32_t>((size_t)S * nL);
-            for (int q = 0; q < kPipeClasses; q++) a.pl[q] = sc.get<int32_t>((size_t)S * nL);
+
             a.Ldone = sc.zeros<int32_t>(nL);
             a.Lndl = sc.zeros<int32_t>(nL);
             if (mode == kRefineDense) {
@@ -2874,7 +2917,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             }
             LAUNCHED();
             CK(cudaEventRecord(ev_join, side));
-            if (a.nL > 0) {
+            if (a.nP > 0) {
                 // rows of one CTA cluster and the 256-thread pipelined
                 // rows on a second side stream
                 CK(cudaStreamWaitEvent(side2, ev_fork, 0));
@@ -2893,7 +2936,7 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 CK(cudaEventRecord(ev_join2, side2));
             }
             CK(cudaStreamWaitEvent(ms, ev_join, 0));
-            if (a.nL > 0) CK(cudaStreamWaitEvent(ms, ev_join2, 0));
+            if (a.nP > 0) CK(cudaStreamWaitEvent(ms, ev_join2, 0));
             prof_end(ms, pb, pe);
             if (hub_items > 0) {
                 const int hg = (int)std::min<int64_t>(hub_items, (int64_t)sms * 8);

@@ -46,6 +46,20 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves, int64_
 // <= U in id order (per block of cp when given); see pack_isolated in lp.cu.
 void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, Scratch &sc);
 
+// Degree-bin and segment thresholds that route rows and contested segments
+// to kernel paths.  Every setting gives the same results (each path computes
+// the same selection and arbitration); only the speed differs.  tuning()
+// returns the values later calls use; set_tuning returns false (and changes
+// nothing) outside the supported ranges.
+struct Tuning {
+    int32_t small_max;  // rows of <= small_max entries: G-lane groups (4, 8, 16, 32)
+    int32_t med_max;    // rows of <= med_max entries: one warp each (small_max..256)
+    int32_t mid_max;    // rows of <= mid_max entries: pipelined CTA rows (512, 1024, 2048)
+    int32_t seg_smem;   // contested segments of <= seg_smem entries: one CTA (64..6144)
+};
+Tuning tuning();
+bool set_tuning(const Tuning &t);
+
 // How a call's LP rounds are launched (results do not depend on it): 0 one
 // round at a time, the host testing the stop rule; 1 all rounds enqueued
 // ahead, a device flag ending them; 2 as 1, captured in one CUDA graph; -1
