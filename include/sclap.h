@@ -249,16 +249,21 @@ int sclap_refine_learned(const sclap_graph *g, int32_t k, double eps, int32_t ro
 int sclap_mlp_score(const float *x, int64_t N, const uint16_t *net, float *z_out, void *stream);
 
 /* Mean logistic loss log(1 + e^z) - y z over N samples (x device float[N][6],
- * y device uint8[N]) of the float network params (device float[1313], no bf16
- * rounding) and its gradient (device float[1313], overwritten); *loss_out on
- * the host.  Float arithmetic, summation order not fixed. */
+ * y device uint8[N]) and its gradient (device float[1313], overwritten) with
+ * respect to the float parameters params (device float[1313]); *loss_out on
+ * the host.  bf16_in = 0: z is the float network's logit.  bf16_in = 1
+ * (BF16-in / FP32-accumulate, what training uses): z is the logit inference
+ * computes (parameters rounded to bf16, hidden outputs ReLU then bf16, fp32
+ * fmaf accumulation in index order), and the gradient is the straight-through
+ * one (each rounding passed as the identity).  Summation order not fixed. */
 int sclap_mlp_loss_grad(const float *x, const uint8_t *y, int64_t N, const float *params,
-                        float *grad_out, double *loss_out, void *stream);
+                        int32_t bf16_in, float *grad_out, double *loss_out, void *stream);
 
-/* Plain minibatch SGD on the loss above: `epochs` passes over the samples in
- * an order shuffled per epoch (sort by SplitMix64 of seed, epoch and index),
- * batches of `batch`, params -= lr * gradient after each.  *loss_out: the
- * loss over all samples after training.  1 <= N <= INT32_MAX. */
+/* Plain minibatch SGD on the BF16-in loss above (bf16_in = 1; float master
+ * parameters): `epochs` passes over the samples in an order shuffled per
+ * epoch (sort by SplitMix64 of seed, epoch and index), batches of `batch`,
+ * params -= lr * gradient after each.  *loss_out: the BF16-in loss over all
+ * samples after training.  1 <= N <= INT32_MAX. */
 int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, int32_t epochs,
                     int32_t batch, float lr, uint64_t seed, double *loss_out, void *stream);
 

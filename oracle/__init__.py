@@ -130,6 +130,9 @@ def lib():
                                                 _P32, _P64, _P64, _PF, _PU8]
             L.or_mlp_loss_grad.restype = C.c_double
             L.or_mlp_loss_grad.argtypes = [_PF, _PU8, C.c_int64, _PF, C.POINTER(C.c_double)]
+            L.or_mlp_loss_grad_bf16.restype = C.c_double
+            L.or_mlp_loss_grad_bf16.argtypes = [_PF, _PU8, C.c_int64, _PF,
+                                                C.POINTER(C.c_double)]
             _lib = L
     return _lib
 
@@ -445,12 +448,14 @@ def refine_learned(g, k, eps, rounds, subrounds, seed, part, net_bf16=None, z_mi
             None if ty is None else ty[:r])
 
 
-def mlp_loss_grad(X, y, params):
-    """Mean logistic loss and its gradient (float64 [1313]) of float32 parameters."""
+def mlp_loss_grad(X, y, params, bf16_in=False):
+    """Mean logistic loss and its gradient (float64 [1313]) of float32
+    parameters: of the float network, or with bf16_in of the network inference
+    runs (bf16 parameters and hidden outputs, straight-through gradient)."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     y = np.ascontiguousarray(y, dtype=np.uint8)
     prm = np.ascontiguousarray(params, dtype=np.float32)
     grad = np.zeros(MLP_NPARAM, np.float64)
-    loss = lib().or_mlp_loss_grad(_pf(X), _pu8(y), X.shape[0], _pf(prm),
-                                  grad.ctypes.data_as(C.POINTER(C.c_double)))
+    fn = lib().or_mlp_loss_grad_bf16 if bf16_in else lib().or_mlp_loss_grad
+    loss = fn(_pf(X), _pu8(y), X.shape[0], _pf(prm), grad.ctypes.data_as(C.POINTER(C.c_double)))
     return float(loss), grad

@@ -1115,6 +1115,69 @@ float or_mlp_forward(const uint16_t *net, const float *x)
     return z;
 }
 
+/* BF16-in / FP32-accumulate training loss: the mean logistic loss of the
+ * network inference runs (or_mlp_forward's arithmetic: parameters rounded to
+ * bf16, one fmaf per input in index order from the bias, hidden outputs
+ * ReLU then bf16) on the float master parameters prm, and its straight-through
+ * gradient: the derivative of that loss with respect to the rounded
+ * parameters, each rounding (of a parameter or a hidden output) passed as the
+ * identity.  The loss and the backward sums are kept in double. */
+double or_mlp_loss_grad_bf16(const float *X, const uint8_t *y, int64_t N, const float *prm,
+                             double *grad)
+{
+    float q[OR_MLP_NPARAM];
+    for (int i = 0; i < OR_MLP_NPARAM; i++) {
+        q[i] = or_bf16(prm[i]);
+        grad[i] = 0.0;
+    }
+    double loss = 0.0;
+    for (int64_t s = 0; s < N; s++) {
+        const float *x = X + s * 6;
+        float a1[32], h1[32], a2[32], h2[32];
+        for (int j = 0; j < 32; j++) {
+            float acc = q[OR_MLP_B1 + j];
+            for (int i = 0; i < 6; i++) acc = fmaf(q[OR_MLP_W1 + j * 6 + i], x[i], acc);
+            a1[j] = acc;
+            h1[j] = or_bf16(acc > 0.0f ? acc : 0.0f);
+        }
+        for (int j = 0; j < 32; j++) {
+            float acc = q[OR_MLP_B2 + j];
+            for (int i = 0; i < 32; i++) acc = fmaf(q[OR_MLP_W2 + j * 32 + i], h1[i], acc);
+            a2[j] = acc;
+            h2[j] = or_bf16(acc > 0.0f ? acc : 0.0f);
+        }
+        float zf = q[OR_MLP_B3];
+        for (int i = 0; i < 32; i++) zf = fmaf(q[OR_MLP_W3 + i], h2[i], zf);
+        double z = zf, t = y[s] ? 1.0 : 0.0;
+        loss += (z > 0 ? z + log1p(exp(-z)) : log1p(exp(z))) - t * z;
+        double dz = 1.0 / (1.0 + exp(-z)) - t;
+        double d2[32], d1[32];
+        grad[OR_MLP_B3] += dz;
+        for (int i = 0; i < 32; i++) {
+            grad[OR_MLP_W3 + i] += dz * h2[i];
+            d2[i] = a2[i] > 0.0f ? dz * q[OR_MLP_W3 + i] : 0.0;
+        }
+        for (int i = 0; i < 32; i++) d1[i] = 0.0;
+        for (int j = 0; j < 32; j++) {
+            grad[OR_MLP_B2 + j] += d2[j];
+            for (int i = 0; i < 32; i++) {
+                grad[OR_MLP_W2 + j * 32 + i] += d2[j] * h1[i];
+                d1[i] += d2[j] * q[OR_MLP_W2 + j * 32 + i];
+            }
+        }
+        for (int j = 0; j < 32; j++) {
+            double dj = a1[j] > 0.0f ? d1[j] : 0.0;
+            grad[OR_MLP_B1 + j] += dj;
+            for (int i = 0; i < 6; i++) grad[OR_MLP_W1 + j * 6 + i] += dj * x[i];
+        }
+    }
+    if (N > 0) {
+        for (int i = 0; i < OR_MLP_NPARAM; i++) grad[i] /= (double)N;
+        loss /= (double)N;
+    }
+    return loss;
+}
+
 /* Refinement with the learned gate (Sec. III.A local search; the gate is not
  * in the paper).  Before round r the features are built from the state at
  * that point (moved flags of round r - 1); in a gated round only nodes with

@@ -150,6 +150,8 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                       float z_min, int32_t full_every, int32_t *part, int32_t *rounds_done,
                       int64_t *moves_per_round, int64_t *visited_out, float *trace_x,
                       uint8_t *trace_y);
+double or_mlp_loss_grad_bf16(const float *X, const uint8_t *y, int64_t N, const float *prm,
+                             double *grad);
 double or_mlp_loss_grad(const float *X, const uint8_t *y, int64_t N, const float *prm,
                         double *grad);
 

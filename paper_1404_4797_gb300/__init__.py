@@ -119,7 +119,7 @@ _SIGS = {
                                        C.c_int32, C.c_uint64, _VP, C.c_float, C.c_int32, _VP,
                                        _P64, _P64, _P32, _P64, _VP, _VP, _VP]),
     "sclap_mlp_score": (C.c_int, [_VP, C.c_int64, _VP, _VP, _VP]),
-    "sclap_mlp_loss_grad": (C.c_int, [_VP, _VP, C.c_int64, _VP, _VP,
+    "sclap_mlp_loss_grad": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int32, _VP,
                                       C.POINTER(C.c_double), _VP]),
     "sclap_mlp_train": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int32, C.c_int32, C.c_float,
                                   C.c_uint64, C.POINTER(C.c_double), _VP]),
@@ -287,16 +287,19 @@ def sclap_mlp_score(x: torch.Tensor, net: torch.Tensor, stream=None) -> torch.Te
     return z
 
 
-def sclap_mlp_loss_grad(x: torch.Tensor, y: torch.Tensor, params: torch.Tensor, stream=None):
-    """Mean logistic loss and gradient (device float32 [1313]) of float params."""
+def sclap_mlp_loss_grad(x: torch.Tensor, y: torch.Tensor, params: torch.Tensor,
+                        bf16_in: bool = False, stream=None):
+    """Mean logistic loss and gradient (device float32 [1313]) of float params
+    (bf16_in: of the bf16 network inference runs, straight-through gradient)."""
     _require_cuda(x, y, params)
     x = x.to(torch.float32).contiguous()
     y = y.to(torch.uint8).contiguous()
     params = params.to(torch.float32).contiguous()
     grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
     loss = C.c_double(0)
-    _check(lib().sclap_mlp_loss_grad(_ptr(x), _ptr(y), x.shape[0], _ptr(params), _ptr(grad),
-                                     C.byref(loss), _stream(stream)), "sclap_mlp_loss_grad")
+    _check(lib().sclap_mlp_loss_grad(_ptr(x), _ptr(y), x.shape[0], _ptr(params),
+                                     1 if bf16_in else 0, _ptr(grad), C.byref(loss),
+                                     _stream(stream)), "sclap_mlp_loss_grad")
     return loss.value, grad
 
 

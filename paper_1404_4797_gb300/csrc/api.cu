@@ -720,14 +720,14 @@ int sclap_mlp_score(const float *x, int64_t N, const uint16_t *net, float *z_out
 }
 
 int sclap_mlp_loss_grad(const float *x, const uint8_t *y, int64_t N, const float *params,
-                        float *grad_out, double *loss_out, void *stream) {
+                        int32_t bf16_in, float *grad_out, double *loss_out, void *stream) {
     return guarded([&] {
         if (N < 0 || !params || !grad_out || (N > 0 && (!x || !y))) fail(SCLAP_EINVAL, "args");
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
         double *d_loss = sc.zeros<double>(1);
         CK(cudaMemsetAsync(grad_out, 0, kMlpParams * sizeof(float), s));
-        mlp_loss_grad(x, y, nullptr, N, params, grad_out, d_loss, s);
+        mlp_loss_grad(x, y, nullptr, N, params, grad_out, d_loss, bf16_in != 0, s);
         double l = 0;
         CK(cudaMemcpyAsync(&l, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -757,13 +757,13 @@ int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, 
             for (int64_t b0 = 0; b0 < N; b0 += batch) {
                 const int64_t nb = std::min<int64_t>(batch, N - b0);
                 CK(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s));
-                mlp_loss_grad(x, y, idx + b0, nb, params, grad, d_loss, s);
+                mlp_loss_grad(x, y, idx + b0, nb, params, grad, d_loss, true, s);
                 mlp_sgd(params, grad, lr, s);
             }
         }
         CK(cudaMemsetAsync(d_loss, 0, sizeof(double), s));
         CK(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s));
-        mlp_loss_grad(x, y, nullptr, N, params, grad, d_loss, s);
+        mlp_loss_grad(x, y, nullptr, N, params, grad, d_loss, true, s);
         double l = 0;
         CK(cudaMemcpyAsync(&l, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

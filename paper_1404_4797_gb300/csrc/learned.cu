@@ -277,13 +277,18 @@ __device__ __forceinline__ void warp_add(float v, float *dst) {
 // sums go to grad with one global atomic per parameter.
 constexpr int kTrainThreads = 128;
 
+// BF16: the forward of inference (parameters rounded to bf16, hidden outputs
+// ReLU then bf16, fp32 fmaf accumulation in index order) and the
+// straight-through gradient (each rounding passed as the identity) with
+// respect to the float master parameters; else the float network.
+template <bool BF16>
 __global__ void __launch_bounds__(kTrainThreads)
     k_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t N, float inv_n,
                 const float *prm, float *grad, double *loss) {
     __shared__ float P[kMlpParams];
     __shared__ float G[kMlpParams];
     for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
-        P[i] = prm[i];
+        P[i] = BF16 ? bf16_round(prm[i]) : prm[i];
         G[i] = 0.0f;
     }
     __syncthreads();
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kTrainThreads)
 #pragma unroll
             for (int i = 0; i < 6; i++) acc = fmaf(P[kMlpW1 + j * 6 + i], x[i], acc);
             a1[j] = acc;
-            h1[j] = acc > 0.0f ? acc : 0.0f;
+            h1[j] = BF16 ? bf16_round(acc > 0.0f ? acc : 0.0f) : (acc > 0.0f ? acc : 0.0f);
         }
         float z = P[kMlpB3];
 #pragma unroll 4
@@ -313,7 +318,8 @@ __global__ void __launch_bounds__(kTrainThreads)
 #pragma unroll
             for (int i = 0; i < 32; i++) acc = fmaf(P[kMlpW2 + j * 32 + i], h1[i], acc);
             a2[j] = acc;
-            z = fmaf(P[kMlpW3 + j], acc > 0.0f ? acc : 0.0f, z);
+            const float r = acc > 0.0f ? acc : 0.0f;
+            z = fmaf(P[kMlpW3 + j], BF16 ? bf16_round(r) : r, z);
         }
         if (ok) lsum += (double)((z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z))) - t * z);
         const float dz = ok ? (1.0f / (1.0f + expf(-z)) - t) * inv_n : 0.0f;
@@ -322,7 +328,8 @@ __global__ void __launch_bounds__(kTrainThreads)
 #pragma unroll
         for (int i = 0; i < 32; i++) d1[i] = 0.0f;
         for (int j = 0; j < 32; j++) {
-            const float h2 = a2[j] > 0.0f ? a2[j] : 0.0f;
+            const float h2 = BF16 ? bf16_round(a2[j] > 0.0f ? a2[j] : 0.0f)
+                                  : (a2[j] > 0.0f ? a2[j] : 0.0f);
             warp_add(dz * h2, &G[kMlpW3 + j]);
             const float d2 = a2[j] > 0.0f ? dz * P[kMlpW3 + j] : 0.0f;
             warp_add(d2, &G[kMlpB2 + j]);
@@ -349,12 +356,16 @@ __global__ void __launch_bounds__(kTrainThreads)
 }
 
 void mlp_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t N,
-                   const float *prm, float *grad, double *d_loss, cudaStream_t s) {
+                   const float *prm, float *grad, double *d_loss, bool bf16_in, cudaStream_t s) {
     if (N <= 0) return;
     const int64_t blocks = std::min<int64_t>(ceil_div<int64_t>(N, kTrainThreads),
                                              (int64_t)dev_info().sms * 4);
-    k_loss_grad<<<(unsigned)blocks, kTrainThreads, 0, s>>>(X, y, idx, N, 1.0f / (float)N, prm,
-                                                           grad, d_loss);
+    if (bf16_in)
+        k_loss_grad<true><<<(unsigned)blocks, kTrainThreads, 0, s>>>(X, y, idx, N, 1.0f / (float)N,
+                                                                     prm, grad, d_loss);
+    else
+        k_loss_grad<false><<<(unsigned)blocks, kTrainThreads, 0, s>>>(
+            X, y, idx, N, 1.0f / (float)N, prm, grad, d_loss);
     LAUNCHED();
 }
 

@@ -43,10 +43,11 @@ void gate_finish(Gate &gt, int rounds_done, cudaStream_t s);
 // Logits of N feature rows with the bf16 scorer.
 void mlp_score(const float *x, int64_t N, const uint16_t *net, float *z, cudaStream_t s);
 // Mean logistic loss and gradient over samples idx[0, N) (idx null: 0..N-1)
-// of float parameters; grad (device, kMlpParams) and *d_loss (device double)
-// are accumulated into (zero them first).
+// of float parameters (bf16_in: of the bf16 network inference runs, with the
+// straight-through gradient); grad (device, kMlpParams) and *d_loss (device
+// double) are accumulated into (zero them first).
 void mlp_loss_grad(const float *X, const uint8_t *y, const int64_t *idx, int64_t N,
-                   const float *prm, float *grad, double *d_loss, cudaStream_t s);
+                   const float *prm, float *grad, double *d_loss, bool bf16_in, cudaStream_t s);
 // bf16 bit patterns (nearest even) of the kMlpParams float parameters
 void mlp_pack_bf16(const float *prm, uint16_t *net, cudaStream_t s);
 // prm -= lr * grad

@@ -94,18 +94,23 @@ def test_gated_refinement_matches_oracle(name, k):
     assert cut == oracle.cut(gn, want)
 
 
-def test_loss_gradient_matches_oracle():
+@pytest.mark.parametrize("bf16_in", [False, True])
+def test_loss_gradient_matches_oracle(bf16_in):
     rng = np.random.default_rng(4)
     X = (rng.random((20000, 6)) * 3).astype(np.float32)
+    if bf16_in:  # trace features are bf16 values
+        X = np.array([[oracle.bf16(float(v)) for v in row] for row in X], np.float32)
     y = (rng.random(20000) < 0.2).astype(np.uint8)
     p = random_net(9, 0.3)
-    loss_w, g_w = oracle.mlp_loss_grad(X, y, p)
+    loss_w, g_w = oracle.mlp_loss_grad(X, y, p, bf16_in=bf16_in)
     loss_g, g_g = S.sclap_mlp_loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
-                                        torch.from_numpy(p).cuda())
+                                        torch.from_numpy(p).cuda(), bf16_in=bf16_in)
     g_g = g_g.cpu().numpy().astype(np.float64)
     assert loss_g == pytest.approx(loss_w, rel=1e-3)
     assert np.max(np.abs(g_g - g_w)) <= 1e-3 * np.max(np.abs(g_w))
     assert np.linalg.norm(g_g - g_w) <= 1e-3 * np.linalg.norm(g_w)
+    if bf16_in:  # the rounding matters for this network
+        assert not np.allclose(g_w, oracle.mlp_loss_grad(X, y, p)[1], rtol=1e-4)
 
 
 def test_training_lowers_the_loss():
@@ -114,10 +119,11 @@ def test_training_lowers_the_loss():
     y = ((X[:, 0] + 0.5 * X[:, 3]) > 0.9).astype(np.uint8)
     p0 = random_net(3, 0.2)
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
-    l0, _ = S.sclap_mlp_loss_grad(Xd, yd, torch.from_numpy(p0).cuda())
+    l0, _ = S.sclap_mlp_loss_grad(Xd, yd, torch.from_numpy(p0).cuda(), bf16_in=True)
     p1, l1 = S.sclap_mlp_train(Xd, yd, torch.from_numpy(p0).cuda(), 8, 256, 0.5, 5)
     assert l1 < 0.6 * l0 and l1 < 0.4
-    lw, _ = oracle.mlp_loss_grad(X, y, p1.cpu().numpy())
+    # training reports the BF16-in loss of the network inference will run
+    lw, _ = oracle.mlp_loss_grad(X, y, p1.cpu().numpy(), bf16_in=True)
     assert l1 == pytest.approx(lw, rel=1e-3)
 
 

@@ -134,6 +134,63 @@ def test_loss_by_hand_for_constant_logit():
     assert oracle.mlp_loss_grad(X, y, p)[1][1312] == pytest.approx(-0.5)
 
 
+def _exact_net(rng):
+    """A network on which bf16 rounding changes nothing: weights in {-1, 0, 1}
+    (second layer mostly zero), small integer biases, inputs in {0, 0.5, 1, 2},
+    so every parameter and every hidden output is a small dyadic number that
+    bf16 represents exactly."""
+    p = np.zeros(oracle.MLP_NPARAM, np.float32)
+    p[0:192] = rng.integers(-1, 2, 192)
+    p[192:224] = rng.integers(-2, 3, 32)
+    p[224:1248] = rng.integers(-1, 2, 1024) * (rng.random(1024) < 0.1)
+    p[1248:1280] = rng.integers(-1, 2, 32)
+    p[1280:1312] = rng.integers(-1, 2, 32) * 0.5
+    p[1312] = 0.25
+    X = rng.choice(np.array([0.0, 0.5, 1.0, 2.0], np.float32), (30, 6))
+    y = (rng.random(30) < 0.4).astype(np.uint8)
+    return p, X, y
+
+
+def test_bf16_training_equals_float_training_where_rounding_is_exact():
+    # where nothing rounds, the BF16-in loss and straight-through gradient are
+    # the float network's loss and gradient (pinned by finite differences above)
+    rng = np.random.default_rng(8)
+    p, X, y = _exact_net(rng)
+    lb, gb = oracle.mlp_loss_grad(X, y, p, bf16_in=True)
+    lf, gf = oracle.mlp_loss_grad(X, y, p)
+    assert lb == pytest.approx(lf, rel=1e-12) and lb > 0
+    assert np.allclose(gb, gf, rtol=1e-9, atol=1e-12)
+    assert np.count_nonzero(gf) > 100
+
+
+def test_bf16_training_rounds_parameters_and_hidden_outputs():
+    X = np.array([[1, 0, 0, 0, 0, 0]], np.float32)
+    y = np.array([1], np.uint8)
+    # parameter rounding: W3[0] = 1 + 2^-10 is not a bf16 value and rounds to 1
+    p = np.zeros(oracle.MLP_NPARAM, np.float32)
+    p[0] = 1.0                     # W1[0][0]
+    p[224] = 1.0                   # W2[0][0]
+    p[1280] = 1.0 + 2.0 ** -10     # W3[0]
+    q = p.copy()
+    q[1280] = 1.0
+    lb, gb = oracle.mlp_loss_grad(X, y, p, bf16_in=True)
+    lq, gq = oracle.mlp_loss_grad(X, y, q)
+    assert lb == lq and np.array_equal(gb, gq)
+    # z = 1 by hand: loss log(1 + e^-1), dL/db3 = sigmoid(1) - 1, dL/dW3[0] = dz * h2 = dz
+    dz = 1.0 / (1.0 + np.exp(-1.0)) - 1.0
+    assert lb == pytest.approx(np.log1p(np.exp(-1.0)), rel=1e-12)
+    assert gb[1312] == pytest.approx(dz, rel=1e-12) and gb[1280] == pytest.approx(dz, rel=1e-12)
+    # hidden-output rounding: b1[0] = 2^-9 makes a1 = 1 + 2^-9, which the
+    # forward rounds to 1 (a quarter of a bf16 step), so z stays exactly 1
+    p2 = np.zeros(oracle.MLP_NPARAM, np.float32)
+    p2[0], p2[192], p2[224], p2[1280] = 1.0, 2.0 ** -9, 1.0, 1.0
+    l2, g2 = oracle.mlp_loss_grad(X, y, p2, bf16_in=True)
+    assert l2 == lb and g2[1280] == gb[1280] and g2[1312] == gb[1312]
+    # dL/dW2[0][0] = d2 * h1 = dz * W3[0] * h1 takes the rounded h1 = 1
+    assert g2[224] == pytest.approx(dz, rel=1e-12)
+    assert oracle.mlp_loss_grad(X, y, p2)[0] != l2   # the float network sees 1 + 2^-9
+
+
 GRAPHS = {
     "chunglu": lambda: I.to_numpy(I.chung_lu(2048, 2.1, 8.0, seed=3)),
     "weighted": lambda: I.to_numpy(I.random_graph(3000, 12000, seed=5, max_w=20, max_c=9)),

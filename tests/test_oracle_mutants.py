@@ -53,11 +53,19 @@ MUTANTS_ELSEWHERE = {
                                       "test_oracle_learned.py"),
     "hidden bias dropped": ("float acc = bf16_bits_to_float(net[OR_MLP_B1 + j]);",
                             "float acc = 0.0f;", "test_oracle_learned.py"),
-    "second ReLU dropped": ("h2[j] = or_bf16(acc > 0.0f ? acc : 0.0f);", "h2[j] = or_bf16(acc);",
-                            "test_oracle_learned.py"),
+    "second ReLU dropped": (
+        "h1[i], acc);\n        h2[j] = or_bf16(acc > 0.0f ? acc : 0.0f);\n    }\n    float z = bf16",
+        "h1[i], acc);\n        h2[j] = or_bf16(acc);\n    }\n    float z = bf16",
+        "test_oracle_learned.py"),
     "ReLU gate missing in backprop": ("d2[i] = a2[i] > 0 ? dz * prm[OR_MLP_W3 + i] : 0.0;",
                                       "d2[i] = dz * prm[OR_MLP_W3 + i];",
                                       "test_oracle_learned.py"),
+    "bf16 training skips parameter rounding": ("        q[i] = or_bf16(prm[i]);\n        grad[i] = 0.0;",
+                                               "        q[i] = prm[i];\n        grad[i] = 0.0;",
+                                               "test_oracle_learned.py"),
+    "bf16 training skips hidden rounding": ("            h1[j] = or_bf16(acc > 0.0f ? acc : 0.0f);\n        }\n        for (int j = 0; j < 32; j++) {\n            float acc = q[OR_MLP_B2 + j];",
+                                            "            h1[j] = acc > 0.0f ? acc : 0.0f;\n        }\n        for (int j = 0; j < 32; j++) {\n            float acc = q[OR_MLP_B2 + j];",
+                                            "test_oracle_learned.py"),
     "full rounds shifted": ("int full = !net || r % full_every == full_every - 1 || r == rounds - 1;",
                             "int full = !net || r % full_every == 0 || r == rounds - 1;",
                             "test_oracle_learned.py"),
