@@ -322,16 +322,18 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
         return I.rand_below(seed, 7, torch.arange(n, device=dev), k).to(torch.int32)
 
     xs, ys = [], []
+    per_seed = max(1, args.train_samples // args.train_seeds)
     for seed in range(1, args.train_seeds + 1):
         _, _, _, rd, _, tx, ty = S.sclap_refine_learned(g, k, eps, rounds, sub, seed, start(seed),
                                                         trace=True)
-        xs.append(tx.reshape(-1, 6))
-        ys.append(ty.reshape(-1))
+        tx, ty = tx.reshape(-1, 6), ty.reshape(-1)
+        # a uniform sample (with replacement) of this seed's trace rows
+        sel = I.rand_below(3 + seed, 11, torch.arange(per_seed, device=dev), tx.shape[0])
+        xs.append(tx[sel].contiguous())
+        ys.append(ty[sel].contiguous())
+        del tx, ty
     X, Y = torch.cat(xs), torch.cat(ys)
     del xs, ys
-    if X.shape[0] > args.train_samples:  # uniform sample of the traces (with replacement)
-        sel = I.rand_below(3, 11, torch.arange(args.train_samples, device=dev), X.shape[0])
-        X, Y = X[sel].contiguous(), Y[sel].contiguous()
     rng = torch.Generator().manual_seed(1)
     p0 = (torch.randn(S.MLP_PARAMS, generator=rng) * 0.2).to(dev)
     torch.cuda.synchronize(dev)
@@ -342,8 +344,11 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
     net = S.bf16_bits(prm)
     z = S.sclap_mlp_score(X, net)
     zm = torch.sort(z[Y.bool()]).values
+    # logit thresholds at move recall 0.99 and 0.9 on the training traces
     z_min = float(zm[int(0.01 * zm.numel())]) if zm.numel() else 0.0
+    z_min90 = float(zm[int(0.10 * zm.numel())]) if zm.numel() else 0.0
     samples = int(X.shape[0])
+    moved_frac = float(Y.float().mean())
     del X, Y, z, zm
 
     def timed(fn):
@@ -356,30 +361,47 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
         torch.cuda.synchronize(dev)
         return ev0.elapsed_time(ev1), out
 
-    res = {"plain_ms": [], "learned_ms": [], "plain_cut": [], "learned_cut": [],
-           "visited_frac": [], "plain_rounds": [], "learned_rounds": []}
+    lmax = int(math.floor((1.0 + eps) * float(-(-int(g["vwgt"].sum()) // k))))
+    rows = int((g["xadj"][1:] > g["xadj"][:-1]).sum())
+    res = {key: [] for key in ("plain_ms", "learned_ms", "learned90_ms", "plain_cut",
+                               "learned_cut", "learned90_cut", "visited_frac", "visited90_frac",
+                               "plain_rounds", "learned_rounds", "plain_bal", "learned_bal")}
     for seed in range(17, 17 + args.eval_seeds):
         ps = start(seed)
-        ms_p, out_p = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps))
+        ms_p, out_p = timed(lambda: S.sclap_refine(g, k, eps, rounds, sub, seed, ps))
         ms_l, out_l = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps, net,
                                                            z_min, 3))
+        ms_9, out_9 = timed(lambda: S.sclap_refine_learned(g, k, eps, rounds, sub, seed, ps, net,
+                                                           z_min90, 3))
         res["plain_ms"].append(ms_p)
         res["learned_ms"].append(ms_l)
+        res["learned90_ms"].append(ms_9)
         res["plain_cut"].append(out_p[1])
         res["learned_cut"].append(out_l[1])
+        res["learned90_cut"].append(out_9[1])
         res["plain_rounds"].append(out_p[3])
         res["learned_rounds"].append(out_l[3])
-        res["visited_frac"].append(out_l[4] / max(1, out_p[4]))
+        res["visited_frac"].append(out_l[4] / max(1, rows * out_p[3]))
+        res["visited90_frac"].append(out_9[4] / max(1, rows * out_p[3]))
+        res["plain_bal"].append(int(out_p[2].max()) / lmax)
+        res["learned_bal"].append(max(int(out_l[2].max()), int(out_9[2].max())) / lmax)
     mean = lambda v: sum(v) / len(v)
     line = {"op": "learned", "scale": cfg["scale"], "n": n, "m": m, "k": k, "eps": eps,
             "rounds": rounds, "train_seeds": args.train_seeds, "eval_seeds": args.eval_seeds,
             "train_samples": samples, "train_epochs": args.epochs, "train_s": train_s,
             "train_loss": loss, "z_min": z_min, "full_every": 3,
+            "moved_frac_in_traces": moved_frac, "z_min90": z_min90,
             "plain_ms": mean(res["plain_ms"]), "learned_ms": mean(res["learned_ms"]),
             "speedup": mean(res["plain_ms"]) / mean(res["learned_ms"]),
             "visited_frac": mean(res["visited_frac"]),
             "cut_ratio": mean(res["learned_cut"]) / mean(res["plain_cut"]),
             "plain_cut": mean(res["plain_cut"]), "learned_cut": mean(res["learned_cut"]),
+            "recall90": {"ms": mean(res["learned90_ms"]),
+                         "speedup": mean(res["plain_ms"]) / mean(res["learned90_ms"]),
+                         "visited_frac": mean(res["visited90_frac"]),
+                         "cut_ratio": mean(res["learned90_cut"]) / mean(res["plain_cut"])},
+            "max_block_over_lmax": {"plain": max(res["plain_bal"]),
+                                    "learned": max(res["learned_bal"])},
             "plain_rounds": mean(res["plain_rounds"]), "learned_rounds": mean(res["learned_rounds"])}
     print(json.dumps(line), flush=True)
     return 0
@@ -550,8 +572,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling)")
     ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
     ap.add_argument("--k", type=int, default=32, help="blocks for --op learned")
-    ap.add_argument("--train-seeds", type=int, default=4, help="--op learned: trace seeds 1..T")
-    ap.add_argument("--eval-seeds", type=int, default=4, help="--op learned: seeds 17..")
+    ap.add_argument("--train-seeds", type=int, default=16, help="--op learned: trace seeds 1..T")
+    ap.add_argument("--eval-seeds", type=int, default=16, help="--op learned: seeds 17..")
     ap.add_argument("--epochs", type=int, default=2, help="--op learned: SGD epochs")
     ap.add_argument("--train-samples", type=int, default=4_000_000,
                     help="--op learned: trace samples used for training")

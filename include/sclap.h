@@ -216,22 +216,26 @@ int sclap_initial_partition(const sclap_graph *g, int32_t k, int64_t B, int32_t 
  * The scorer is a 6-32-32-1 network of 1313 parameters in this order:
  * W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3 (row-major, output index
  * first).  Inference takes them as bf16 bit patterns; training as float.
- * Features of node v before a round (each rounded to bf16, nearest even):
+ * Features of node v before a round (each rounded to bf16, nearest even),
+ * with wdeg its weighted degree and wb / wo the weight to the best eligible
+ * other block / to its own block that v's latest visit in this call saw
+ * (recorded by the propose step; 0 before the first visit):
  *   1 e + (x - 2^e) / 2^e for x = 1 + deg(v), e = floor(log2 x)
  *   2 W(own) / L_max
- *   3 (weighted degree - weight to own block) / weighted degree
+ *   3 (wb - wo) / wdeg, the best external gain
  *   4 1 if v moved in the previous round
  *   5 moved neighbours in the previous round / deg(v)
- *   6 1 if W(own) > L_max
+ *   6 wo / wdeg
  * (zeros for nodes without neighbours).  Every output starts from its bias
  * and adds one fmaf per input in index order (float accumulator); hidden
  * outputs pass ReLU and are rounded to bf16; the last output is the logit. */
 
 /* Refinement (as sclap_refine) where a gated round visits only the nodes
- * whose logit is >= z_min; round r is full (every node) when r % full_every
- * == full_every - 1, when r is the last round, or always when net is NULL
- * (then the call equals sclap_refine).  A run stops after a full round
- * without moves.
+ * whose logit is >= z_min; round r is full (every node) when r == 0, when
+ * r % full_every == full_every - 1, when r is the last round, or always when
+ * net is NULL (then the call equals sclap_refine).  A run stops after a full
+ * round without moves.  A gated round reads no edges beyond the rows it
+ * visits and those of the nodes that moved in the round before.
  *   net          device uint16[1313] bf16 parameters, or NULL
  *   visited_out  host: nodes with neighbours visited, summed over rounds (NULL ok)
  *   trace_x      device float[rounds][n][6]: the features before each round (NULL ok)

@@ -123,7 +123,7 @@ def lib():
             L.or_log2_feature.restype = C.c_float
             L.or_log2_feature.argtypes = [C.c_int64]
             L.or_features.argtypes = [C.c_int64, _P64, _P32, _P32, _P32, _P64, C.c_int64, _PU8,
-                                      _PF]
+                                      _P64, _P64, _PF]
             L.or_mlp_score.argtypes = [C.c_int64, _PF, _PU16, _PF]
             L.or_refine_learned.argtypes = g + [C.c_int32, C.c_double, C.c_int32, C.c_int32,
                                                 C.c_uint64, _PU16, C.c_float, C.c_int32, _P32,
@@ -404,16 +404,19 @@ def log2_feature(x: int) -> float:
     return float(lib().or_log2_feature(x))
 
 
-def features(g, lab, W, lmax, moved=None):
-    """Six bf16-rounded features per node, float32 [n, 6]."""
+def features(g, lab, W, lmax, moved=None, vis_best=None, vis_own=None):
+    """Six bf16-rounded features per node, float32 [n, 6] (see or_features)."""
     keep, a = _graph_args(g)
     n = a[0]
     lab = np.ascontiguousarray(lab, dtype=np.int32)
     W = np.ascontiguousarray(W, dtype=np.int64)
     mv = None if moved is None else np.ascontiguousarray(moved, dtype=np.uint8)
+    vb = None if vis_best is None else np.ascontiguousarray(vis_best, dtype=np.int64)
+    vo = None if vis_own is None else np.ascontiguousarray(vis_own, dtype=np.int64)
     x = np.zeros((n, 6), np.float32)
     lib().or_features(n, a[1], a[2], a[3], _p32(lab), _p64(W), lmax,
-                      None if mv is None else _pu8(mv), _pf(x))
+                      None if mv is None else _pu8(mv), None if vb is None else _p64(vb),
+                      None if vo is None else _p64(vo), _pf(x))
     return x
 
 

@@ -232,7 +232,7 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                         int64_t *W, int64_t B, const int64_t *Bv, int refine,
                         const int32_t *cp, uint64_t seed, int32_t round, int32_t S,
                         const uint8_t *active, const int32_t *colour, const run_map *rm,
-                        lp_ws *ws)
+                        int64_t *vis_best, int64_t *vis_own, lp_ws *ws)
 {
     int64_t moves = 0;
     for (int32_t j = 0; j < S; j++) {
@@ -275,6 +275,10 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                 else if (tl != best_tie) better = tl < best_tie;
                 else better = L < best;
                 if (better) { best = L; best_tie = tl; }
+            }
+            if (vis_best) {  /* learned form: what this visit saw (R12) */
+                vis_best[v] = best >= 0 ? ws->acc[best] : 0;
+                vis_own[v] = w_own;
             }
             if (best >= 0) {
                 int64_t gain = ws->acc[best] - w_own;
@@ -355,7 +359,7 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     for (int32_t r = 0; r < rounds; r++) {
         if (colour) or_degree_colours(n, xadj, seed, r, S, colour);
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, lab, W, B, Bv, refine, cp,
-                             seed, r, S, NULL, colour, rm, &ws);
+                             seed, r, S, NULL, colour, rm, NULL, NULL, &ws);
         if (moves_per_round) moves_per_round[r] = m;
         done = r + 1;
         if (m == 0) break;
@@ -1057,14 +1061,17 @@ float or_log2_feature(int64_t x)
     return (float)e + frac;
 }
 
-/* The six features of every node (row-major [n][6], each rounded to bf16):
- *   f1 log2-feature(1 + deg), f2 W(own)/L_max, f3 external share of the
- *   weighted degree, f4 v moved in the previous round, f5 share of v's
- *   neighbours that moved in the previous round, f6 own block overloaded.
+/* The six features of every node (row-major [n][6], each rounded to bf16),
+ * wdeg = v's weighted degree, wb / wo = the weight to the best eligible
+ * other block / to its own block that v's most recent visit saw (vis_best,
+ * vis_own; 0 before any visit or when NULL):
+ *   f1 log2-feature(1 + deg), f2 W(own)/L_max, f3 (wb - wo)/wdeg (the best
+ *   external gain), f4 v moved in the previous round, f5 share of v's
+ *   neighbours that moved in the previous round, f6 wo/wdeg.
  * Nodes without neighbours get zeros. */
 void or_features(int64_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                  const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
-                 float *x)
+                 const int64_t *vis_best, const int64_t *vis_own, float *x)
 {
     for (int64_t v = 0; v < n; v++) {
         float *f = x + v * 6;
@@ -1073,20 +1080,19 @@ void or_features(int64_t n, const int64_t *xadj, const int32_t *adjncy, const in
             for (int i = 0; i < 6; i++) f[i] = 0.0f;
             continue;
         }
-        int64_t wdeg = 0, wown = 0, nmov = 0;
+        int64_t wdeg = 0, nmov = 0;
         for (int64_t i = xadj[v]; i < xadj[v + 1]; i++) {
-            int32_t u = adjncy[i];
             wdeg += adjwgt[i];
-            if (lab[u] == lab[v]) wown += adjwgt[i];
-            if (moved && moved[u]) nmov++;
+            if (moved && moved[adjncy[i]]) nmov++;
         }
         int64_t own = lab[v];
+        int64_t wb = vis_best ? vis_best[v] : 0, wo = vis_own ? vis_own[v] : 0;
         f[0] = or_bf16(or_log2_feature(1 + deg));
         f[1] = or_bf16((float)W[own] / (float)Lmax);
-        f[2] = or_bf16((float)(wdeg - wown) / (float)wdeg);
+        f[2] = or_bf16((float)(wb - wo) / (float)wdeg);
         f[3] = (moved && moved[v]) ? 1.0f : 0.0f;
         f[4] = or_bf16((float)nmov / (float)deg);
-        f[5] = W[own] > Lmax ? 1.0f : 0.0f;
+        f[5] = or_bf16((float)wo / (float)wdeg);
     }
 }
 
@@ -1180,11 +1186,14 @@ double or_mlp_loss_grad_bf16(const float *X, const uint8_t *y, int64_t N, const 
 
 /* Refinement with the learned gate (Sec. III.A local search; the gate is not
  * in the paper).  Before round r the features are built from the state at
- * that point (moved flags of round r - 1); in a gated round only nodes with
- * logit >= z_min are visited, in a full round (r % full_every ==
- * full_every - 1, the last round, or every round when net is NULL) all are.
- * The run stops after a full round without moves.  trace_x [rounds][n][6]
- * and trace_y [rounds][n] (moved in round r) are written when non-NULL;
+ * that point (or_features): block weights and labels now, moved flags of
+ * round r - 1, and what each node's most recent visit saw (the weight to the
+ * best eligible other block and to its own block, recorded by lp_round).  In
+ * a gated round only nodes with logit >= z_min are visited; a round is full
+ * (every node) when r == 0 (no visit has been recorded yet), r % full_every
+ * == full_every - 1, r is the last round, or always when net is NULL.  The
+ * run stops after a full round without moves.  trace_x [rounds][n][6] and
+ * trace_y [rounds][n] (moved in round r) are written when non-NULL;
  * visited_out counts the visited nodes with neighbours over all rounds. */
 int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                       const int32_t *adjwgt, const int32_t *vwgt, int32_t k, double eps,
@@ -1202,12 +1211,15 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     uint8_t *active = (uint8_t *)malloc((size_t)(n ? n : 1));
     int32_t *prev = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
     float *x = (float *)malloc(sizeof(float) * 6 * (size_t)(n ? n : 1));
+    int64_t *vb = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    int64_t *vo = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
     lp_ws ws;
     ws.acc = (int64_t *)calloc((size_t)k, sizeof(int64_t));
     ws.touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
     ws.props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
     int rc = OR_OK;
-    if (!W || !moved || !active || !prev || !x || !ws.acc || !ws.touched || !ws.props) {
+    if (!W || !moved || !active || !prev || !x || !vb || !vo || !ws.acc || !ws.touched ||
+        !ws.props) {
         rc = OR_ENOMEM;
         goto out;
     }
@@ -1215,8 +1227,8 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     int64_t visited = 0;
     int32_t done = 0;
     for (int32_t r = 0; r < rounds; r++) {
-        int full = !net || r % full_every == full_every - 1 || r == rounds - 1;
-        or_features(n, xadj, adjncy, adjwgt, part, W, B, moved, x);
+        int full = !net || r == 0 || r % full_every == full_every - 1 || r == rounds - 1;
+        or_features(n, xadj, adjncy, adjwgt, part, W, B, moved, vb, vo, x);
         if (trace_x) memcpy(trace_x + (size_t)r * n * 6, x, sizeof(float) * 6 * (size_t)n);
         for (int64_t v = 0; v < n; v++) {
             active[v] = full ? 1 : (or_mlp_forward(net, x + v * 6) >= z_min);
@@ -1224,7 +1236,7 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         }
         memcpy(prev, part, sizeof(int32_t) * (size_t)n);
         int64_t m = lp_round(n, xadj, adjncy, adjwgt, vwgt, part, W, B, NULL, 1, NULL, seed, r,
-                             S, active, NULL, NULL, &ws);
+                             S, active, NULL, NULL, vb, vo, &ws);
         for (int64_t v = 0; v < n; v++) moved[v] = part[v] != prev[v];
         if (trace_y) memcpy(trace_y + (size_t)r * n, moved, (size_t)n);
         if (moves_per_round) moves_per_round[r] = m;
@@ -1234,7 +1246,7 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (rounds_done) *rounds_done = done;
     if (visited_out) *visited_out = visited;
 out:
-    free(W); free(moved); free(active); free(prev); free(x);
+    free(W); free(moved); free(active); free(prev); free(x); free(vb); free(vo);
     free(ws.acc); free(ws.touched); free(ws.props);
     return rc;
 }

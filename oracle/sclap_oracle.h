@@ -141,7 +141,7 @@ float or_bf16(float f);
 float or_log2_feature(int64_t x);
 void or_features(int64_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt,
                  const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
-                 float *x);
+                 const int64_t *vis_best, const int64_t *vis_own, float *x);
 float or_mlp_forward(const uint16_t *net, const float *x);
 void or_mlp_score(int64_t N, const float *X, const uint16_t *net, float *z);
 int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,

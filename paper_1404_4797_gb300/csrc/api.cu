@@ -688,6 +688,8 @@ int sclap_refine_learned(const sclap_graph *gp, int32_t k, double eps, int32_t r
         cfg.before_round = [&](int r, const uint8_t **active) {
             return gate_round(gt, r, active, s);
         };
+        cfg.visit_best = gt.vb;
+        cfg.visit_own = gt.vo;
         int rd = lp_run(cfg, sc, nullptr, W);
         gate_finish(gt, rd, s);
         unsigned long long vis = 0;

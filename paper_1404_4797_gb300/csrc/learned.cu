@@ -32,15 +32,11 @@ __device__ __forceinline__ float log2_feature(int64_t x) {
     return __fadd_rn((float)e, frac);
 }
 
-// Per-row sums over tiles of 4096 entries: thread t takes 16 consecutive
-// entries and flushes a running sum whenever its row changes.  wdeg (if
-// non-null): total weight; wown / nmov (if lab non-null): weight to
-// neighbours with the row's label, neighbours that moved.
+// Weighted degree of every row over tiles of 4096 entries: thread t takes 16
+// consecutive entries and flushes a running sum whenever its row changes.
 constexpr int kRowTile = 4096;
 
-__global__ void __launch_bounds__(256)
-    k_row_sums(DGraph g, const int32_t *lab, const uint8_t *moved, unsigned long long *wdeg,
-               unsigned long long *wown, int32_t *nmov) {
+__global__ void __launch_bounds__(256) k_row_sums(DGraph g, unsigned long long *wdeg) {
     __shared__ int32_t rowof[kRowTile];
     __shared__ int32_t tmp[16];
     const int64_t tiles = ceil_div<int64_t>(g.nnz, kRowTile);
@@ -49,55 +45,60 @@ __global__ void __launch_bounds__(256)
         const int len = (int)min64(kRowTile, g.nnz - e0);
         block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
         int32_t row = -1;
-        unsigned long long sw = 0, so = 0;
-        int32_t sm = 0;
-        int32_t lrow = 0;
+        unsigned long long sw = 0;
         for (int j = 0; j < 16; j++) {
             const int i = threadIdx.x * 16 + j;
             if (i >= len) break;
             const int32_t v = rowof[i];
             if (v != row) {
-                if (row >= 0) {
-                    if (wdeg) atomicAdd(&wdeg[row], sw);
-                    if (lab) {
-                        if (so) atomicAdd(&wown[row], so);
-                        if (sm) atomicAdd(&nmov[row], sm);
-                    }
-                }
+                if (row >= 0) atomicAdd(&wdeg[row], sw);
                 row = v;
-                sw = so = 0;
-                sm = 0;
-                if (lab) lrow = lab[v];
+                sw = 0;
             }
-            const int32_t u = g.adjncy[e0 + i];
-            const int32_t w = g.adjwgt[e0 + i];
-            sw += (unsigned long long)w;
-            if (lab) {
-                if (lab[u] == lrow) so += (unsigned long long)w;
-                sm += moved[u] ? 1 : 0;
-            }
+            sw += (unsigned long long)g.adjwgt[e0 + i];
         }
-        if (row >= 0) {
-            if (wdeg) atomicAdd(&wdeg[row], sw);
-            if (lab) {
-                if (so) atomicAdd(&wown[row], so);
-                if (sm) atomicAdd(&nmov[row], sm);
-            }
-        }
+        if (row >= 0) atomicAdd(&wdeg[row], sw);
         __syncthreads();
     }
 }
 
-// moved[v] = label changed since the previous call; prev = labels now.
+// moved[v] = label changed since the previous call; prev = labels now.  The
+// moved nodes are appended to movers (count in *nmovers) when movers is given.
 __global__ void k_moved(int64_t n, const int32_t *lab, int32_t *prev, uint8_t *moved,
-                        uint8_t *trace_y, bool first) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+                        uint8_t *trace_y, bool first, int32_t *movers, int32_t *nmovers) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_r = (n + 31) & ~31ll;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_r;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t l = lab[v];
-        const uint8_t m = first ? 0 : (uint8_t)(l != prev[v]);
-        moved[v] = m;
-        prev[v] = l;
-        if (trace_y) trace_y[v] = m;
+        uint8_t m = 0;
+        if (v < n) {
+            const int32_t l = lab[v];
+            m = first ? 0 : (uint8_t)(l != prev[v]);
+            moved[v] = m;
+            prev[v] = l;
+            if (trace_y) trace_y[v] = m;
+        }
+        if (movers) {
+            const unsigned b = __ballot_sync(0xffffffffu, m != 0);
+            int base = 0;
+            if (lane == 0 && b) base = atomicAdd(nmovers, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (m) movers[base + __popc(b & ((1u << lane) - 1))] = (int32_t)v;
+        }
+    }
+}
+
+// Moved-neighbour counts: every mover adds 1 to each of its neighbours (one
+// warp per mover), so the cost follows the movers' rows, not the graph.
+__global__ void k_scatter_moved(DGraph g, const int32_t *movers, const int32_t *nmovers,
+                                int32_t *nmov) {
+    const int cnt = *nmovers;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t v = movers[i];
+        for (int64_t e = g.xadj[v] + lane; e < g.xadj[v + 1]; e += 32)
+            atomicAdd(&nmov[g.adjncy[e]], 1);
     }
 }
 
@@ -128,12 +129,14 @@ __device__ __forceinline__ void load_net(const uint16_t *net, float *P) {
 }
 
 // Features of every node (written to x when non-null) and, in gated rounds,
-// the active flags (logit >= z_min); counts the visited rows.
+// the active flags (logit >= z_min); counts the visited rows.  vb / vo: the
+// weight to the best eligible other block / own block that the node's latest
+// visit saw (recorded by the propose kernels).
 __global__ void __launch_bounds__(256)
     k_gate(DGraph g, const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
-           const unsigned long long *wdeg, const unsigned long long *wown, const int32_t *nmov,
-           const uint16_t *net, float z_min, bool full, float *x_out, uint8_t *active,
-           unsigned long long *visited) {
+           const unsigned long long *wdeg, const int32_t *vb, const int32_t *vo,
+           const int32_t *nmov, const uint16_t *net, float z_min, bool full, float *x_out,
+           uint8_t *active, unsigned long long *visited) {
     __shared__ float P[kMlpParams];
     const bool score = !full && net;
     if (score) load_net(net, P);
@@ -147,13 +150,13 @@ __global__ void __launch_bounds__(256)
             float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (deg > 0) {
                 const int32_t own = lab[v];
-                const int64_t wo = (int64_t)wown[v], wd = (int64_t)wdeg[v];
+                const int64_t wb = vb[v], wo = vo[v], wd = (int64_t)wdeg[v];
                 f[0] = bf16_round(log2_feature(1 + deg));
                 f[1] = bf16_round(__fdiv_rn(__ll2float_rn(W[own]), __ll2float_rn(Lmax)));
-                f[2] = bf16_round(__fdiv_rn(__ll2float_rn(wd - wo), __ll2float_rn(wd)));
+                f[2] = bf16_round(__fdiv_rn(__ll2float_rn(wb - wo), __ll2float_rn(wd)));
                 f[3] = moved[v] ? 1.0f : 0.0f;
                 f[4] = bf16_round(__fdiv_rn(__int2float_rn(nmov[v]), __ll2float_rn(deg)));
-                f[5] = W[own] > Lmax ? 1.0f : 0.0f;
+                f[5] = bf16_round(__fdiv_rn(__ll2float_rn(wo), __ll2float_rn(wd)));
             }
             if (x_out) {
 #pragma unroll
@@ -188,11 +191,14 @@ void gate_init(Gate &gt, Scratch &sc) {
     gt.prev = sc.get<int32_t>(n ? n : 1);
     gt.moved = sc.zeros<uint8_t>(n ? n : 1);
     gt.active = sc.get<uint8_t>(n ? n : 1);
-    gt.wown = sc.get<unsigned long long>(n ? n : 1);
+    gt.vb = sc.zeros<int32_t>(n ? n : 1);
+    gt.vo = sc.zeros<int32_t>(n ? n : 1);
     gt.nmov = sc.get<int32_t>(n ? n : 1);
+    gt.movers = sc.get<int32_t>(n ? n : 1);
+    gt.nmovers = sc.get<int32_t>(1);
     gt.visited = sc.zeros<unsigned long long>(1);
     if (gt.g.nnz > 0) {
-        k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, nullptr, nullptr, wd, nullptr, nullptr);
+        k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, wd);
         LAUNCHED();
     }
 }
@@ -200,12 +206,14 @@ void gate_init(Gate &gt, Scratch &sc) {
 bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
     const int64_t n = gt.g.n;
     const int sms = dev_info().sms;
-    const bool full = !gt.net || r % gt.full_every == gt.full_every - 1 || r == gt.rounds - 1;
+    const bool full =
+        !gt.net || r == 0 || r % gt.full_every == gt.full_every - 1 || r == gt.rounds - 1;
     if (n > 0) {
+        CK(cudaMemsetAsync(gt.nmovers, 0, sizeof(int32_t), s));
         k_moved<<<sms * 4, 256, 0, s>>>(n, gt.lab, gt.prev, gt.moved,
                                         (gt.trace_y && r > 0) ? gt.trace_y + (size_t)(r - 1) * n
                                                                : nullptr,
-                                        r == 0);
+                                        r == 0, gt.movers, gt.nmovers);
         LAUNCHED();
     }
     float *x = gt.trace_x ? gt.trace_x + (size_t)r * n * 6 : nullptr;
@@ -218,16 +226,16 @@ bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
         return true;
     }
     if (n > 0) {
-        CK(cudaMemsetAsync(gt.wown, 0, n * sizeof(unsigned long long), s));
+        // neighbours that moved in round r - 1, scattered from its movers
         CK(cudaMemsetAsync(gt.nmov, 0, n * sizeof(int32_t), s));
-        if (gt.g.nnz > 0) {
-            k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, gt.lab, gt.moved, nullptr, gt.wown,
-                                               gt.nmov);
+        if (gt.g.nnz > 0 && r > 0) {
+            k_scatter_moved<<<sms * 8, 256, 0, s>>>(gt.g, gt.movers, gt.nmovers, gt.nmov);
             LAUNCHED();
         }
         k_gate<<<sms * 4, 256, 0, s>>>(gt.g, gt.lab, gt.W, gt.Lmax, gt.moved,
-                                       (const unsigned long long *)gt.wdeg, gt.wown, gt.nmov,
-                                       gt.net, gt.z_min, full, x, gt.active, gt.visited);
+                                       (const unsigned long long *)gt.wdeg, gt.vb, gt.vo,
+                                       gt.nmov, gt.net, gt.z_min, full, x, gt.active,
+                                       gt.visited);
         LAUNCHED();
     }
     *active = full ? nullptr : gt.active;
@@ -238,7 +246,8 @@ void gate_finish(Gate &gt, int rounds_done, cudaStream_t s) {
     if (!gt.trace_y || rounds_done < 1 || gt.g.n == 0) return;
     const int sms = dev_info().sms;
     k_moved<<<sms * 4, 256, 0, s>>>(gt.g.n, gt.lab, gt.prev, gt.moved,
-                                    gt.trace_y + (size_t)(rounds_done - 1) * gt.g.n, false);
+                                    gt.trace_y + (size_t)(rounds_done - 1) * gt.g.n, false,
+                                    nullptr, nullptr);
     LAUNCHED();
 }
 

@@ -27,15 +27,17 @@ struct Gate {
     int32_t *prev;          // labels at the start of the previous round
     uint8_t *moved;         // moved in the previous round
     uint8_t *active;
-    unsigned long long *wown;   // per round: weight to the own block
+    int32_t *vb, *vo;           // latest visit: weight to the best eligible other / own block
     int32_t *nmov;              // per round: moved neighbours
+    int32_t *movers, *nmovers;  // nodes that moved in the previous round
     unsigned long long *visited;  // device counter
 };
 
 // Allocates the gate's arrays and computes the weighted degrees.
 void gate_init(Gate &gt, Scratch &sc);
 // Before round r: moved flags of round r - 1 (into trace_y[r - 1]), features
-// (into trace_x[r]), scores and active flags.  Returns whether r is full.
+// (into trace_x[r]), scores and active flags.  Returns whether r is full
+// (r == 0, r % full_every == full_every - 1, the last round, or no network).
 bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s);
 // After the last executed round: its moved flags into trace_y[rounds_done - 1].
 void gate_finish(Gate &gt, int rounds_done, cudaStream_t s);

@@ -201,7 +201,19 @@ struct LPArgs {
     int32_t run_k;
     const int32_t *col;        // degree-ordered sub-rounds: sub-round per node (null: hash)
     Tuning t;                  // degree-bin and segment thresholds of this call
+    // learned refinement (null otherwise): per visited node, the weight to the
+    // best eligible other label and to its own label that the visit saw
+    int32_t *vb, *vo;
 };
+
+// Records what the visit of v saw (learned refinement): best = the best
+// eligible candidate key (0: none), ownw = omega(v, own).
+__device__ __forceinline__ void record_visit(const LPArgs &a, int32_t v, unsigned long long best,
+                                             int32_t ownw) {
+    if (!a.vb) return;
+    a.vb[v] = best ? (int32_t)(best >> 32) : 0;
+    a.vo[v] = ownw;
+}
 
 // Every kernel of a round returns at once after the run has ended (the rounds
 // of a call are enqueued, or captured in a CUDA graph, ahead of time).
@@ -568,6 +580,7 @@ template <int MODE>
 __device__ __forceinline__ void decide_and_emit(const LPArgs &a, const int64_t *Wsm, NodeSm &nd,
                                                 int s) {
     const unsigned long long b = nd.best[s];
+    record_visit(a, nd.v[s], b, nd.ownw[s]);
     if (b == 0) return;
     const int32_t gain = (int32_t)(b >> 32) - nd.ownw[s];
     const bool ovl = MODE != kCluster && nd.ovl[s];
@@ -817,6 +830,7 @@ __device__ __forceinline__ void small_compute(const LPArgs &a, const int64_t *Ws
     int32_t bl = (best != 0 && ck == best) ? x.L : 0x7fffffff;
 #pragma unroll
     for (int d = G / 2; d > 0; d >>= 1) bl = min(bl, __shfl_xor_sync(0xffffffffu, bl, d));
+    if (x.has && r == 0) record_visit(a, x.v, best, ownw);
     if (x.has && r == 0 && best != 0) {
         const int32_t gain = (int32_t)(best >> 32) - ownw;
         const bool ovl = MODE != kCluster && x.Wown > bnd(a, x.own);
@@ -1143,6 +1157,7 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
                 }
                 ow += sm.wo[q];
             }
+            record_visit(a, cur.v, bk, ow);
             if (bk != 0) {
                 const int32_t gain = (int32_t)(bk >> 32) - ow;
                 bool ovl = false;
@@ -1286,6 +1301,7 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) bl = min(bl, __shfl_xor_sync(0xffffffffu, bl, d));
     __syncwarp();
+    if (lane == 0) record_visit(a, v, best, ownw);
     if (lane == 0 && best != 0) {
         const int32_t gain = (int32_t)(best >> 32) - ownw;
         const bool ovl = MODE != kCluster && Wown > bnd(a, own);
@@ -2156,6 +2172,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
         if (colour_of(a, v) != (uint32_t)a.colour) continue;
         const unsigned long long b = a.hbest[li];
         const int32_t own = a.lab[v];
+        record_visit(a, v, b, a.hown[li]);
         if (b != 0) {
             const int32_t gain = (int32_t)(b >> 32) - a.hown[li];
             const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
@@ -2323,6 +2340,15 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
             sm.vals[i] = 0;
         }
         cl.sync();
+        if (rank == 0 && threadIdx.x == 0) {
+            int32_t L = 0x7fffffff, ownw = 0;
+            for (unsigned r = 0; r < kHugeCS; r++) {
+                const HugeSm *o = cl.map_shared_rank(&sm, r);
+                L = min(L, o->cbestL);
+                ownw += o->cown;
+            }
+            record_visit(a, v, b, ownw);
+        }
         if (rank == 0 && threadIdx.x == 0 && b != 0) {
             int32_t L = 0x7fffffff, ownw = 0;
             for (unsigned r = 0; r < kHugeCS; r++) {
@@ -2740,6 +2766,8 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.run_seed = cfg.run_seed;
     a.run_off = cfg.run_off;
     a.run_k = cfg.run_k;
+    a.vb = cfg.visit_best;
+    a.vo = cfg.visit_own;
     // degree-ordered sub-rounds: sort keys, order and colour per node
     uint64_t *dkey = nullptr;
     int32_t *dord = nullptr, *dcol = nullptr;

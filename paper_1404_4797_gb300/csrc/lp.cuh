@@ -35,6 +35,9 @@ struct LPConfig {
     // Clustering: sub-rounds by degree quantile (low degrees first) instead
     // of by hash (Sec. III.A's increasing-degree order while coarsening).
     bool degree_order = false;
+    // Learned refinement: per node, the weight to the best eligible other
+    // label (0 if none) and to its own label that its latest visit saw.
+    int32_t *visit_best = nullptr, *visit_own = nullptr;
 };
 
 // Runs up to cfg.rounds rounds; returns rounds executed.  moves (optional)

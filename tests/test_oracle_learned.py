@@ -52,19 +52,50 @@ def test_features_by_hand():
     lab = np.array([0, 0, 1, 1], np.int32)
     W = np.array([2, 2], np.int64)
     moved = np.array([0, 1, 0, 0], np.uint8)
-    x = oracle.features(g, lab, W, 2, moved)
-    # node 1: deg 2 -> log2-feature(3) = 1.5; W/Lmax = 1; external 2 of 3 -> 2/3 in bf16;
-    # moved; neighbours 0 and 2 moved? none -> 0; not overloaded
+    vb = np.array([0, 2, 2, 0], np.int64)   # best external weight seen at the last visit
+    vo = np.array([1, 1, 3, 3], np.int64)   # own-block weight seen at the last visit
+    x = oracle.features(g, lab, W, 2, moved, vb, vo)
+    # node 1: deg 2 -> log2-feature(3) = 1.5; W/Lmax = 1; weighted degree 3:
+    # (2 - 1)/3 and 1/3 in bf16; moved; neighbours 0 and 2 did not move
     assert x[1, 0] == 1.5 and x[1, 1] == 1.0
-    assert x[1, 2] == oracle.bf16(2.0 / 3.0)
-    assert x[1, 3] == 1.0 and x[1, 4] == 0.0 and x[1, 5] == 0.0
-    # node 0: one neighbour (1, moved, same block) -> f3 0, f5 1
-    assert list(x[0]) == [1.0, 1.0, 0.0, 0.0, 1.0, 0.0]
-    # node 3: neighbour 2 same block, weight 3
-    assert x[3, 2] == 0.0 and x[3, 4] == 0.0
-    # overloaded block
+    assert x[1, 2] == oracle.bf16(1.0 / 3.0) and x[1, 5] == oracle.bf16(1.0 / 3.0)
+    assert x[1, 3] == 1.0 and x[1, 4] == 0.0
+    # node 0: one neighbour (1, which moved), weighted degree 1: gain -1, own share 1
+    assert list(x[0]) == [1.0, 1.0, -1.0, 0.0, 1.0, 1.0]
+    # node 3: weighted degree 3, gain (0 - 3)/3, own share 1, neighbour 2 did not move
+    assert x[3, 2] == -1.0 and x[3, 4] == 0.0 and x[3, 5] == 1.0
+    # before any visit the visit features are 0; W / L_max of an overloaded block
     x2 = oracle.features(g, lab, np.array([3, 1], np.int64), 2, None)
-    assert x2[0, 5] == 1.0 and x2[0, 1] == 1.5 and x2[2, 5] == 0.0
+    assert x2[0, 1] == 1.5 and x2[2, 1] == 0.5
+    assert np.all(x2[:, 2] == 0) and np.all(x2[:, 5] == 0)
+
+
+def test_visit_features_record_what_the_visit_saw():
+    # With one sub-round every node of round 0 is visited against the start
+    # state, so the features before round 1 carry, per node, the weight to its
+    # start block and to the best eligible other block at the start (brute
+    # force here), divided by its weighted degree.
+    g = I.to_numpy(I.random_graph(300, 1200, seed=4, max_w=7, max_c=3))
+    n, k, eps = 300, 6, 0.03
+    p0 = (np.arange(n, dtype=np.int64) * 2654435761 % k).astype(np.int32)
+    _, moves, _, tx, _ = oracle.refine_learned(g, k, eps, 2, 1, 13, p0, net_const(8.0), 0.0,
+                                               3, trace=True)
+    assert len(moves) == 2
+    lmax = oracle.lmax(int(g["vwgt"].sum()), k, eps)
+    W0 = np.bincount(p0, weights=g["vwgt"], minlength=k).astype(np.int64)
+    for v in range(n):
+        row = range(g["xadj"][v], g["xadj"][v + 1])
+        if len(row) == 0:
+            continue
+        acc = np.zeros(k, np.int64)
+        for i in row:
+            acc[p0[g["adjncy"][i]]] += g["adjwgt"][i]
+        own = p0[v]
+        wd = int(acc.sum())
+        elig = [b for b in range(k) if b != own and acc[b] > 0 and W0[b] + g["vwgt"][v] <= lmax]
+        wb = max((int(acc[b]) for b in elig), default=0)
+        assert tx[1][v, 5] == oracle.bf16(float(np.float32(acc[own]) / np.float32(wd)))
+        assert tx[1][v, 2] == oracle.bf16(float(np.float32(wb - acc[own]) / np.float32(wd)))
 
 
 def test_mlp_forward_exact_small_values():
@@ -224,7 +255,7 @@ def test_gate_that_admits_nobody_visits_full_rounds_only(name):
     deg = np.diff(g["xadj"])
     r = len(moves)
     assert r >= 3  # gated rounds without moves do not end the run
-    full = [i for i in range(r) if i % 3 == 2 or i == 6]
+    full = [i for i in range(r) if i == 0 or i % 3 == 2 or i == 6]
     assert visited == len(full) * int(np.sum(deg > 0))
     for i in range(r):
         if i not in full:

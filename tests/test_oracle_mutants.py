@@ -48,9 +48,11 @@ MUTANTS = {
 MUTANTS_ELSEWHERE = {
     "bf16 ties rounded up": ("u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0x8000u;",
                              "test_oracle_learned.py"),
-    "feature 3 takes the own share": ("f[2] = or_bf16((float)(wdeg - wown) / (float)wdeg);",
-                                      "f[2] = or_bf16((float)wown / (float)wdeg);",
-                                      "test_oracle_learned.py"),
+    "feature 3 drops the own weight": ("f[2] = or_bf16((float)(wb - wo) / (float)wdeg);",
+                                       "f[2] = or_bf16((float)wb / (float)wdeg);",
+                                       "test_oracle_learned.py"),
+    "visit records the own weight as best": ("vis_best[v] = best >= 0 ? ws->acc[best] : 0;",
+                                             "vis_best[v] = w_own;", "test_oracle_learned.py"),
     "hidden bias dropped": ("float acc = bf16_bits_to_float(net[OR_MLP_B1 + j]);",
                             "float acc = 0.0f;", "test_oracle_learned.py"),
     "second ReLU dropped": (
@@ -66,9 +68,10 @@ MUTANTS_ELSEWHERE = {
     "bf16 training skips hidden rounding": ("            h1[j] = or_bf16(acc > 0.0f ? acc : 0.0f);\n        }\n        for (int j = 0; j < 32; j++) {\n            float acc = q[OR_MLP_B2 + j];",
                                             "            h1[j] = acc > 0.0f ? acc : 0.0f;\n        }\n        for (int j = 0; j < 32; j++) {\n            float acc = q[OR_MLP_B2 + j];",
                                             "test_oracle_learned.py"),
-    "full rounds shifted": ("int full = !net || r % full_every == full_every - 1 || r == rounds - 1;",
-                            "int full = !net || r % full_every == 0 || r == rounds - 1;",
-                            "test_oracle_learned.py"),
+    "full rounds shifted": (
+        "int full = !net || r == 0 || r % full_every == full_every - 1 || r == rounds - 1;",
+        "int full = !net || r == 0 || r % full_every == 0 || r == rounds - 1;",
+        "test_oracle_learned.py"),
     "gated round ends the run": ("if (full && m == 0) break;", "if (m == 0) break;",
                                  "test_oracle_learned.py"),
     "V-cycle clustering unconstrained": (
