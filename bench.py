@@ -562,6 +562,40 @@ def run_coarsening(args, S, I, dev):
     return 0
 
 
+def run_web(args, S, I, dev):
+    """Config 3: web-like Chung-Lu graph, n = 2^26 (exponent 2.0, mean degree
+    32, largest expected degree 2^20) plus 5% uniform long-range edges, int64
+    row offsets beyond 2^31 entries, k = 64, eps = 0.03, the paper's fast
+    round counts.  Reports the multilevel partition time, the level-0 SCLaP
+    sweeps and their propose-step bandwidth."""
+    import torch
+    scale = args.scale or 26
+    g = I.web_graph(1 << scale, 2.0, 32.0, dmax=float(1 << min(20, scale - 6)),
+                    long_frac=0.05, seed=1, device=dev)
+    torch.cuda.empty_cache()
+    n, m = int(g["vwgt"].numel()), I.num_edges(g)
+    cfg = dict(WORKLOAD, scale=scale, k=64, workload=f"web-like Chung-Lu n=2^{scale}")
+    params = params_for(cfg)
+    S.set_validation(False)
+    for _ in range(args.warmup):
+        S.partition_multilevel(g, params)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        _, st = S.partition_multilevel(g, params)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    sweeps = sweep_gteps(S, I, cfg, g, n, m, dev, reps=1)
+    line = {"op": "web", "n": n, "m": m, "nnz": 2 * m, "k": 64, "ms_per_step": ms,
+            "gteps": m / (ms / 1e3) / 1e9, "cut": st["cut"], "cut_frac": st["cut"] / m,
+            "random_split_cut_frac": 1 - 1 / 64, "maxbw": st["maxbw"], "lmax": st["lmax"],
+            "levels": st["n"], "nnz_levels": st["nnz"], "sclap_gteps": sweeps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,7 +613,7 @@ def main():
                     help="--op learned: trace samples used for training")
     ap.add_argument("--op", default="multilevel", choices=["multilevel", "cluster", "refine",
                                                            "learned", "batched", "vcycle",
-                                                           "config1", "coarsening"],
+                                                           "config1", "coarsening", "web"],
                     help="time one SCLaP phase on the input graph instead (profiling aid)")
     args = ap.parse_args()
     cfg = dict(WORKLOAD)
@@ -608,6 +642,8 @@ def main():
         return run_config1(args, S, I, dev)
     if args.op == "coarsening":
         return run_coarsening(args, S, I, dev)
+    if args.op == "web":
+        return run_web(args, S, I, dev)
     g = I.rmat(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"], device=dev)
     n = g["vwgt"].numel()
     m = I.num_edges(g)

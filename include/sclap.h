@@ -58,7 +58,7 @@ enum sclap_status {
     SCLAP_OK = 0,
     SCLAP_EINVAL = 1,     /* bad scalar argument (k < 1, eps < 0, U < max c, ...)   */
     SCLAP_EGRAPH = 2,     /* graph fails validation                                  */
-    SCLAP_EOVERFLOW = 3,  /* c(V) or the sum of omega exceeds INT32_MAX              */
+    SCLAP_EOVERFLOW = 3,  /* c(V) or the undirected sum of omega exceeds INT32_MAX   */
     SCLAP_ENOMEM = 4,     /* device allocation failed                                */
     SCLAP_ECUDA = 5,      /* CUDA runtime error                                      */
     SCLAP_ETIMEOUT = 6,   /* a bounded device wait gave up                           */
@@ -125,7 +125,8 @@ typedef struct {
  * (cmax: their largest weight) and P(v) the weight of the earlier ones, v
  * joins group floor(P(v) / U') labelled by its smallest id (weight <= U).
  *   rounds_done     host, rounds executed (the last one may have 0 moves)
- * Needs c(V) <= INT32_MAX and sum(adjwgt) <= INT32_MAX (SCLAP_EOVERFLOW). */
+ * Needs c(V) <= INT32_MAX and sum(adjwgt) / 2 (the undirected total) <=
+ * INT32_MAX (SCLAP_EOVERFLOW). */
 int sclap_cluster(const sclap_graph *g, int64_t U, int32_t rounds, int32_t subrounds,
                   uint64_t seed, const int32_t *constraint_part, int32_t *labels_out,
                   int32_t *rounds_done, void *stream);

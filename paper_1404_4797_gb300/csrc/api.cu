@@ -453,8 +453,11 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Every cluster weight is at most c(V); every coarse edge weight and every
+// omega(v, L) is a sum over distinct undirected edges, so at most the
+// undirected total (half the sum over the directed entries).
 void check_totals_cluster(const GraphTotals &t) {
-    if (t.cV > INT32_MAX || t.sum_w > INT32_MAX) fail(SCLAP_EOVERFLOW, "c(V) or sum(omega)");
+    if (t.cV > INT32_MAX || t.sum_w / 2 > INT32_MAX) fail(SCLAP_EOVERFLOW, "c(V) or sum(omega)");
 }
 
 }  // namespace

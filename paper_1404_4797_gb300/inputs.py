@@ -112,6 +112,42 @@ def csr_from_edges(n: int, u: torch.Tensor, v: torch.Tensor, w: torch.Tensor | N
             "adjwgt": ww.to(torch.int32).contiguous(), "vwgt": vwgt.to(torch.int32).contiguous()}
 
 
+def csr_from_unique_keys(n: int, key: torch.Tensor, vwgt: torch.Tensor | None = None) -> dict:
+    """Symmetric unit-weight CSR from sorted, distinct keys a * n + b with a < b
+    (undirected edges).  The same arrays csr_from_edges returns, built without
+    sorting all 2m entries: row v holds its smaller neighbours (from the edges
+    (b, v), ordered by a stable sort on b) followed by its larger ones (the
+    edges (v, b), already in order)."""
+    device = key.device
+    a = key // n
+    b = key % n
+    deg_fwd = torch.bincount(a, minlength=n)
+    deg_rev = torch.bincount(b, minlength=n)
+    xadj = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    xadj[1:] = torch.cumsum(deg_fwd + deg_rev, 0)
+    nnz = int(xadj[-1])
+    adjncy = torch.empty(nnz, dtype=torch.int32, device=device)
+    # larger neighbours: edge i (a_i, b_i) is entry i - fwd_start[a_i] of a_i's upper part
+    fwd_start = torch.cumsum(deg_fwd, 0) - deg_fwd
+    i = torch.arange(key.numel(), dtype=torch.int64, device=device)
+    pos = xadj[:-1][a] + deg_rev[a] + (i - fwd_start[a])
+    adjncy[pos] = b.to(torch.int32)
+    del pos
+    # smaller neighbours: the edges in (b, a) order
+    order = torch.sort(b, stable=True).indices
+    bs, as_ = b[order], a[order]
+    del order, a, b
+    rev_start = torch.cumsum(deg_rev, 0) - deg_rev
+    pos = xadj[:-1][bs] + (i - rev_start[bs])
+    adjncy[pos] = as_.to(torch.int32)
+    del pos, bs, as_, i
+    if vwgt is None:
+        vwgt = torch.ones(n, dtype=torch.int32, device=device)
+    return {"xadj": xadj, "adjncy": adjncy,
+            "adjwgt": torch.ones(nnz, dtype=torch.int32, device=device),
+            "vwgt": vwgt.to(torch.int32).contiguous()}
+
+
 def _chung_lu_pairs(n, gamma, mean_deg, seed, stream0, m_target, device, w=None, dmax=None):
     """Sample endpoint pairs with P(endpoint = i) proportional to the expected
     degree w_i ~ (i + i0)^(-1/(gamma-1)); i0 is chosen so that the largest expected
@@ -202,23 +238,26 @@ def rmat(scale: int = 22, edge_factor: int = 16, a: float = 0.57, b: float = 0.1
 def web_graph(n: int = 1 << 26, gamma: float = 2.0, mean_deg: float = 32.0,
               dmax: float = float(1 << 20), long_frac: float = 0.05, seed: int = 1,
               device="cpu") -> dict:
-    """Web-like graph: Chung-Lu edges (exponent gamma, largest expected degree
-    about dmax) for (1 - long_frac) of n * mean_deg / 2 undirected edges plus
-    long_frac of them between uniform random endpoints; ids permuted, unit
-    weights, duplicates merged."""
+    """Web-like graph: n * mean_deg / 2 Chung-Lu edges (exponent gamma, largest
+    expected degree about dmax) plus long_frac as many again between uniform
+    random endpoints; ids permuted, unit weights, duplicates merged."""
     m = int(n * mean_deg / 2)
     m_long = int(m * long_frac)
-    key = _chung_lu_pairs(n, gamma, mean_deg, seed, 30, m - m_long, device, dmax=dmax)
+    key = _chung_lu_pairs(n, gamma, mean_deg, seed, 30, m, device, dmax=dmax)
     s = torch.arange(m_long, dtype=torch.int64, device=device)
     la = rand_below(seed, 40, s, n)
     lb = rand_below(seed, 41, s, n)
+    del s
     keep = la != lb
     la, lb = la[keep], lb[keep]
     key = torch.unique(torch.cat([key, torch.minimum(la, lb) * n + torch.maximum(la, lb)]))
-    a, b = key // n, key % n
-    del key, la, lb, s
+    del la, lb, keep
     perm = permutation(n, seed, 42, device)
-    return csr_from_edges(n, perm[a], perm[b])
+    a, b = perm[key // n], perm[key % n]
+    del key, perm
+    key = torch.sort(torch.minimum(a, b) * n + torch.maximum(a, b)).values
+    del a, b
+    return csr_from_unique_keys(n, key)
 
 
 def rgg(scale: int, seed: int = 1, device="cpu", radius_factor: float = 0.55) -> dict:

@@ -270,6 +270,16 @@ def test_errors_are_reported():
     with pytest.raises(S.SclapError) as e:
         S.sclap_cluster(big, 2**31 - 1, 3, 4, 1)
     assert e.value.code == S.EOVERFLOW
+    # edge weights: the undirected total decides (coarse edge weights and
+    # omega(v, L) never exceed it); the directed sum may pass INT32_MAX
+    heavy = I.to_device(I.path_graph(3, [10**9, 10**9]), "cuda")   # 2e9 undirected
+    lab, _ = S.sclap_cluster(heavy, 3, 2, 1, 1)
+    assert lab.cpu().tolist() == oracle.cluster(I.to_numpy(I.path_graph(3, [10**9, 10**9])),
+                                                3, 2, 1, 1)[0].tolist()
+    over = I.to_device(I.path_graph(4, [10**9, 10**9, 10**9]), "cuda")  # 3e9 undirected
+    with pytest.raises(S.SclapError) as e:
+        S.sclap_cluster(over, 4, 2, 1, 1)
+    assert e.value.code == S.EOVERFLOW
 
 
 def test_batched_runs_match_oracle():

@@ -49,3 +49,26 @@ def test_rgg_edge_count_matches_the_papers_rgg26_density():
     m = I.num_edges(g)
     expect = math.pi * 0.55 ** 2 * math.log(n) / 2 * n
     assert 0.93 < m / expect < 1.0
+
+
+def test_csr_from_unique_keys_equals_csr_from_edges():
+    for n, m, seed in ((50, 200, 1), (1000, 6000, 2), (7, 0, 3)):
+        s = torch.arange(m, dtype=torch.int64)
+        u = I.rand_below(seed, 1, s, n)
+        v = I.rand_below(seed, 2, s, n)
+        keep = u != v
+        key = torch.unique(torch.minimum(u[keep], v[keep]) * n + torch.maximum(u[keep], v[keep]))
+        want = I.csr_from_edges(n, key // n, key % n)
+        got = I.csr_from_unique_keys(n, key)
+        for k in ("xadj", "adjncy", "adjwgt", "vwgt"):
+            assert torch.equal(got[k], want[k]), k
+
+
+def test_web_graph_adds_the_long_range_edges():
+    n = 1 << 12
+    g = I.web_graph(n, 2.0, 16.0, dmax=800.0, long_frac=0.05, seed=2)
+    m = I.num_edges(g)
+    assert oracle.validate(I.to_numpy(g)) == oracle.OK
+    # n * mean / 2 Chung-Lu edges plus 5% more, minus the few long-range pairs
+    # that repeat a Chung-Lu edge
+    assert 1.04 < m / (n * 16 / 2) <= 1.05
