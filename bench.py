@@ -183,6 +183,8 @@ def run_reference(args, cfg):
     from paper_1404_4797_gb300 import inputs as I
     scale = reference_scale(args.steps, args.warmup, cfg["scale"])
     g = I.to_numpy(I.rmat(scale, cfg["edge_factor"], seed=cfg["seed"]))
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     m = int(g["adjncy"].size) // 2
     params = params_for(cfg)
     for _ in range(args.warmup):
@@ -193,7 +195,8 @@ def run_reference(args, cfg):
     dt = (time.perf_counter() - t0) / max(1, args.steps)
     value = m / dt / 1e9
     sample = (f"R-MAT scale {scale} (same generator and parameters as the workload, "
-              f"n={len(g['vwgt'])}, m={m}), full multilevel partition per step, one thread")
+              f"n={len(g['vwgt'])}, m={m}), full multilevel partition per step, "
+              f"{cores} host cores")
     config = dict(cfg, scale=scale, n=len(g["vwgt"]), m=m,
                   workload=cfg["workload"].replace(f"scale {cfg['scale']}", f"scale {scale}"),
                   sample_of=f"R-MAT scale {cfg['scale']}")
@@ -201,7 +204,7 @@ def run_reference(args, cfg):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": config, "same_config": scale == cfg["scale"],
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -210,18 +213,36 @@ def run_reference(args, cfg):
     return 0
 
 
-def cpu_baseline(cfg, gn, m):
-    """Times the oracle's multilevel partition on the benchmark's own workload
-    (the same graph the GPU partitions), once, on one host core (rank 0, N=1)."""
+CPU_SAMPLE_SCALE = 20
+
+
+def cpu_baseline(cfg):
+    """Times the oracle's multilevel partition on a bounded sample of the
+    workload (the same generator and parameters at R-MAT scale 20, about 15 s
+    of CPU work per run): once on one host core and once on all of them (its
+    OpenMP build splits each sub-round's propose loop; results are identical).
+    Rank 0, N = 1 only."""
     import oracle
+    from paper_1404_4797_gb300 import inputs as I
+    g = I.to_numpy(I.rmat(CPU_SAMPLE_SCALE, cfg["edge_factor"], seed=cfg["seed"]))
+    m = int(g["adjncy"].size) // 2
     params = params_for(cfg)
-    t0 = time.perf_counter()
-    _, st = oracle.multilevel(gn, params)
-    dt = time.perf_counter() - t0
-    return {"value": m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"the full workload (R-MAT scale {cfg['scale']}, n={len(gn['vwgt'])}, "
-                      f"m={m}): one multilevel partition, single thread, {dt:.1f} s",
-            "cut": st["cut"]}
+    cores = os.cpu_count() or 1
+    res = {}
+    for t in (1, cores):
+        oracle.set_threads(t)
+        t0 = time.perf_counter()
+        _, st = oracle.multilevel(g, params)
+        res[t] = (time.perf_counter() - t0, st["cut"])
+    oracle.set_threads(1)
+    dt, cut = res[cores]
+    return {"value": m / dt / 1e9, "unit": "GTEPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"R-MAT scale {CPU_SAMPLE_SCALE} (same generator and parameters as the "
+                      f"workload, n={len(g['vwgt'])}, m={m}): one multilevel partition on "
+                      f"{cores} host cores, {dt:.1f} s",
+            "single_thread": {"value": m / res[1][0] / 1e9, "s": res[1][0]},
+            "same_cut_as_single_thread": cut == res[1][1]}
 
 
 def sweep_gteps(S, I, cfg, g, n, m, dev, reps=3):
@@ -755,7 +776,7 @@ def main():
             "sclap_entries_per_s": prof["entries_scanned"] / (prof["propose_ms"] / 1e3)
             if prof["propose_ms"] > 0 else None}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, I.to_numpy(g), m)
+        line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

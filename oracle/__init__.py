@@ -43,8 +43,8 @@ def build(force: bool = False) -> str:
         os.path.getmtime(p) > os.path.getmtime(_SO) for p in (_SRC, _HDR))
     if stale:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp,
-                               _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o",
+                               tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -118,6 +118,8 @@ def lib():
             _PF = C.POINTER(C.c_float)
             _PU8 = C.POINTER(C.c_uint8)
             _PU16 = C.POINTER(C.c_uint16)
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_get_threads.restype = C.c_int
             L.or_bf16.restype = C.c_float
             L.or_bf16.argtypes = [C.c_float]
             L.or_log2_feature.restype = C.c_float
@@ -158,6 +160,15 @@ def _graph_args(g):
 def _check(rc, what):
     if rc != OK:
         raise OracleError(rc, what)
+
+
+def set_threads(t: int) -> None:
+    """Threads of the oracle's per-node propose loop (results do not depend on it)."""
+    lib().or_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def mix64(z: int) -> int:

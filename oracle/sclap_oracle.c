@@ -1,5 +1,7 @@
 /*
- * sclap_oracle.c -- plain, slow, single-threaded CPU oracle.
+ * sclap_oracle.c -- plain, slow CPU oracle (one thread by default; built
+ * with OpenMP, or_set_threads splits each sub-round's independent per-node
+ * propose loop over threads, which cannot change any result).
  *
  * TEST INFRASTRUCTURE ONLY: loaded by the tests, by the smoke check and by
  * the CPU-baseline leg of the benchmark; never by the product path.
@@ -46,6 +48,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------ */
 /* hashing (R1, R2)                                                     */
@@ -178,11 +183,64 @@ typedef struct {
     int32_t k;
 } run_map;
 
+/* Workspace of the rounds.  The proposals of one sub-round are computed
+ * node by node against the same state, so nodes are independent: with
+ * OpenMP (or_set_threads) each of nthr threads takes a contiguous range of
+ * nodes with its own acc / touched / proposal list, and the lists are joined
+ * before arbitration, which orders proposals totally, so the result does not
+ * depend on the number of threads. */
 typedef struct {
-    int64_t *acc;       /* omega(v, L) for the node being visited, size nW */
-    int64_t *touched;   /* labels with acc != 0                             */
-    proposal *props;
+    int nthr;
+    int64_t **acc;      /* per thread: omega(v, L) for the node being visited, size nW */
+    int64_t **touched;  /* per thread: labels with acc != 0                             */
+    proposal **tp;      /* per thread: its proposals of the current sub-round           */
+    int64_t *tnp;
+    proposal *props;    /* all proposals of the sub-round                               */
 } lp_ws;
+
+static int g_threads = 1;
+
+void or_set_threads(int t) { g_threads = t < 1 ? 1 : t; }
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads;
+#else
+    return 1;
+#endif
+}
+
+static void ws_free(lp_ws *ws)
+{
+    for (int t = 0; t < ws->nthr; t++) {
+        if (ws->acc) free(ws->acc[t]);
+        if (ws->touched) free(ws->touched[t]);
+        if (ws->tp) free(ws->tp[t]);
+    }
+    free(ws->acc); free(ws->touched); free(ws->tp); free(ws->tnp); free(ws->props);
+    memset(ws, 0, sizeof(*ws));
+}
+
+static int ws_alloc(lp_ws *ws, int64_t n, int64_t nW)
+{
+    memset(ws, 0, sizeof(*ws));
+    ws->nthr = or_get_threads();
+    ws->acc = (int64_t **)calloc((size_t)ws->nthr, sizeof(int64_t *));
+    ws->touched = (int64_t **)calloc((size_t)ws->nthr, sizeof(int64_t *));
+    ws->tp = (proposal **)calloc((size_t)ws->nthr, sizeof(proposal *));
+    ws->tnp = (int64_t *)calloc((size_t)ws->nthr, sizeof(int64_t));
+    ws->props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
+    if (!ws->acc || !ws->touched || !ws->tp || !ws->tnp || !ws->props) { ws_free(ws); return OR_ENOMEM; }
+    int64_t per = n / ws->nthr + 2;
+    for (int t = 0; t < ws->nthr; t++) {
+        ws->acc[t] = (int64_t *)calloc((size_t)(nW ? nW : 1), sizeof(int64_t));
+        ws->touched[t] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nW ? nW : 1));
+        ws->tp[t] = (proposal *)malloc(sizeof(proposal) * (size_t)per);
+        if (!ws->acc[t] || !ws->touched[t] || !ws->tp[t]) { ws_free(ws); return OR_ENOMEM; }
+    }
+    return OR_OK;
+}
 
 /* One round (R1-R5).  lab: label per node; W: weight per label (nW labels);
  * B: U (clustering) or L_max (refinement).  Returns the moves applied. */
@@ -236,9 +294,22 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
 {
     int64_t moves = 0;
     for (int32_t j = 0; j < S; j++) {
-        int64_t np = 0;
         /* --- every node of colour j proposes against the current state --- */
-        for (int64_t v = 0; v < n; v++) {
+        for (int t = 0; t < ws->nthr; t++) ws->tnp[t] = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(ws->nthr)
+#endif
+        {
+#ifdef _OPENMP
+        const int t = omp_get_thread_num(), T = omp_get_num_threads();
+#else
+        const int t = 0, T = 1;
+#endif
+        int64_t *acc = ws->acc[t], *touched = ws->touched[t];
+        /* chunk c: nodes [n c / nthr, n (c + 1) / nthr), proposals into tp[c] */
+        for (int c = t; c < ws->nthr; c += T) {
+        int64_t tn = 0;
+        for (int64_t v = n * c / ws->nthr; v < n * (c + 1) / ws->nthr; v++) {
             /* the seed, node id and block-id base that key v's hashes */
             uint64_t sv = seed;
             int64_t lv = v, lb = 0;
@@ -256,39 +327,47 @@ static int64_t lp_round(int64_t n, const int64_t *xadj, const int32_t *adjncy,
                 int64_t u = adjncy[i];
                 if (cp && cp[u] != cp[v]) continue;  /* V-cycle restriction */
                 int64_t L = lab[u];
-                if (ws->acc[L] == 0) ws->touched[nt++] = L;
-                ws->acc[L] += adjwgt[i];
+                if (acc[L] == 0) touched[nt++] = L;
+                acc[L] += adjwgt[i];
             }
             int64_t own = lab[v];
-            int64_t w_own = ws->acc[own];
+            int64_t w_own = acc[own];
             int overloaded = refine && W[own] > bound_of(Bv, B, own);
             int64_t best = -1;
             uint32_t best_tie = 0;
-            for (int64_t t = 0; t < nt; t++) {
-                int64_t L = ws->touched[t];
+            for (int64_t q = 0; q < nt; q++) {
+                int64_t L = touched[q];
                 if (L == own) continue;
                 if (W[L] + vwgt[v] > bound_of(Bv, B, L)) continue; /* not eligible */
                 uint32_t tl = or_tie(sv, round, lv, L - lb);
                 int better;
                 if (best < 0) better = 1;
-                else if (ws->acc[L] != ws->acc[best]) better = ws->acc[L] > ws->acc[best];
+                else if (acc[L] != acc[best]) better = acc[L] > acc[best];
                 else if (tl != best_tie) better = tl < best_tie;
                 else better = L < best;
                 if (better) { best = L; best_tie = tl; }
             }
             if (vis_best) {  /* learned form: what this visit saw (R12) */
-                vis_best[v] = best >= 0 ? ws->acc[best] : 0;
+                vis_best[v] = best >= 0 ? acc[best] : 0;
                 vis_own[v] = w_own;
             }
             if (best >= 0) {
-                int64_t gain = ws->acc[best] - w_own;
+                int64_t gain = acc[best] - w_own;
                 if (gain > 0 || overloaded) {
-                    proposal *p = &ws->props[np++];
+                    proposal *p = &ws->tp[c][tn++];
                     p->v = v; p->target = best; p->own = own; p->gain = gain;
                     p->c = vwgt[v]; p->keep = 1;
                 }
             }
-            for (int64_t t = 0; t < nt; t++) ws->acc[ws->touched[t]] = 0;
+            for (int64_t q = 0; q < nt; q++) acc[touched[q]] = 0;
+        }
+        ws->tnp[c] = tn;
+        }
+        }
+        int64_t np = 0;
+        for (int t = 0; t < ws->nthr; t++) {
+            memcpy(ws->props + np, ws->tp[t], sizeof(proposal) * (size_t)ws->tnp[t]);
+            np += ws->tnp[t];
         }
         /* --- R3: departures from overloaded blocks (refinement only) --- */
         if (refine && np > 0) {
@@ -348,11 +427,8 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         if (!colour) return OR_ENOMEM;
     }
     lp_ws ws;
-    ws.acc = (int64_t *)calloc((size_t)(nW ? nW : 1), sizeof(int64_t));
-    ws.touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nW ? nW : 1));
-    ws.props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
-    if (!ws.acc || !ws.touched || !ws.props) {
-        free(ws.acc); free(ws.touched); free(ws.props); free(colour);
+    if (ws_alloc(&ws, n, nW) != OR_OK) {
+        free(colour);
         return OR_ENOMEM;
     }
     int32_t done = 0;
@@ -365,7 +441,8 @@ static int lp_run(int64_t n, const int64_t *xadj, const int32_t *adjncy,
         if (m == 0) break;
     }
     if (rounds_done) *rounds_done = done;
-    free(ws.acc); free(ws.touched); free(ws.props); free(colour);
+    ws_free(&ws);
+    free(colour);
     return OR_OK;
 }
 
@@ -1214,12 +1291,9 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     int64_t *vb = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
     int64_t *vo = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
     lp_ws ws;
-    ws.acc = (int64_t *)calloc((size_t)k, sizeof(int64_t));
-    ws.touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
-    ws.props = (proposal *)malloc(sizeof(proposal) * (size_t)(n ? n : 1));
+    const int ws_rc = ws_alloc(&ws, n, k);
     int rc = OR_OK;
-    if (!W || !moved || !active || !prev || !x || !vb || !vo || !ws.acc || !ws.touched ||
-        !ws.props) {
+    if (!W || !moved || !active || !prev || !x || !vb || !vo || ws_rc != OR_OK) {
         rc = OR_ENOMEM;
         goto out;
     }
@@ -1247,7 +1321,7 @@ int or_refine_learned(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (visited_out) *visited_out = visited;
 out:
     free(W); free(moved); free(active); free(prev); free(x); free(vb); free(vo);
-    free(ws.acc); free(ws.touched); free(ws.props);
+    if (ws_rc == OR_OK) ws_free(&ws);
     return rc;
 }
 

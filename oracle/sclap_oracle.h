@@ -55,6 +55,11 @@ typedef struct {
     int64_t cut, maxbw;
 } or_ml_stats;
 
+/* Threads of the per-node propose loop (OpenMP builds; default 1).  The
+ * results do not depend on it. */
+void or_set_threads(int t);
+int or_get_threads(void);
+
 uint64_t or_mix64(uint64_t z);
 uint32_t or_colour(uint64_t seed, int32_t round, int64_t v, int32_t S);
 uint32_t or_tie(uint64_t seed, int32_t round, int64_t v, int64_t L);

@@ -488,3 +488,26 @@ def test_input_generators_web_graph_and_population_shapes():
         assert 2000 <= gp["vwgt"].size <= 4000 and oracle.validate(gp) == oracle.OK
         assert gp["vwgt"].min() >= 1 and gp["vwgt"].max() <= 500
         assert gp["adjwgt"].min() >= 1 and gp["adjwgt"].max() <= 1000
+
+
+def test_threads_do_not_change_results():
+    """The OpenMP build splits each sub-round's propose loop over threads;
+    arbitration orders proposals totally, so results equal the one-thread ones."""
+    g = I.to_numpy(I.chung_lu(4096, 2.1, 8.0, seed=11))
+    n = g["vwgt"].size
+    prm = oracle.default_params(8, 0.03, seed=4, n_stop=300)
+    p0 = (np.arange(n, dtype=np.int64) * 2654435761 % 8).astype(np.int32)
+    old = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        want = oracle.multilevel(g, prm)
+        want_r = oracle.refine(g, 8, 0.03, 6, 4, 3, p0)
+        for t in (2, 5, 8):
+            oracle.set_threads(t)
+            got = oracle.multilevel(g, prm)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1]
+            got_r = oracle.refine(g, 8, 0.03, 6, 4, 3, p0)
+            assert np.array_equal(got_r[0], want_r[0]) and got_r[1] == want_r[1]
+            assert np.array_equal(got_r[2], want_r[2]) and got_r[3] == want_r[3]
+    finally:
+        oracle.set_threads(old)

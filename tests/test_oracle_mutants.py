@@ -51,7 +51,7 @@ MUTANTS_ELSEWHERE = {
     "feature 3 drops the own weight": ("f[2] = or_bf16((float)(wb - wo) / (float)wdeg);",
                                        "f[2] = or_bf16((float)wb / (float)wdeg);",
                                        "test_oracle_learned.py"),
-    "visit records the own weight as best": ("vis_best[v] = best >= 0 ? ws->acc[best] : 0;",
+    "visit records the own weight as best": ("vis_best[v] = best >= 0 ? acc[best] : 0;",
                                              "vis_best[v] = w_own;", "test_oracle_learned.py"),
     "hidden bias dropped": ("float acc = bf16_bits_to_float(net[OR_MLP_B1 + j]);",
                             "float acc = 0.0f;", "test_oracle_learned.py"),
