@@ -174,8 +174,9 @@ def reference_scale(steps, warmup, cap=22):
 
 
 def run_reference(args, cfg):
-    """The oracle (plain single-threaded C) on a bounded sample of the workload:
-    the same generator and parameters at the scale reference_scale picks."""
+    """The oracle (plain C; its OpenMP build on all host cores, results identical
+    to one thread) on a bounded sample of the workload: the same generator and
+    parameters at the scale reference_scale picks."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
