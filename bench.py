@@ -683,7 +683,8 @@ def main():
     # depend on it)
     from paper_1404_4797_gb300 import autotune
     tune = autotune.load_or_tune(g, cfg["k"], cfg["eps"], cfg["cluster_rounds"],
-                                 cfg["refine_rounds"], cfg["subrounds"], cfg["seed"])
+                                 cfg["refine_rounds"], cfg["subrounds"], cfg["seed"],
+                                 ml_params=params if args.op == "multilevel" else None)
     if args.op == "learned":
         return run_learned(args, cfg, S, I, g, n, m, dev)
     if args.op == "vcycle":
@@ -769,7 +770,7 @@ def main():
             "config": {**cfg, "n": n, "m": m, "l2": "inputs larger than L2 (CSR %.2f GB)" %
                        (h2d / 1e9), "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "tuning": dict(tune["best"], cached=tune["cached"]),
+            "tuning": dict(tune["best"], cached=tune["cached"], tuned_on=tune.get("workload")),
             "cut": st["cut"], "maxbw": st["maxbw"], "lmax": st["lmax"], "levels": st["n"],
             "cut_frac": st["cut"] / m, "random_split_cut_frac": 1.0 - 1.0 / cfg["k"],
             "sclap_gteps": {k_: round(v["gteps"], 3) for k_, v in sweeps.items()},

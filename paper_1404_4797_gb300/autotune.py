@@ -36,13 +36,14 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 
 
 def signature(g: dict, k: int, eps: float, cluster_rounds: int, refine_rounds: int,
-              subrounds: int) -> str:
+              subrounds: int, ml_params: dict | None = None) -> str:
     """Graph size, degree profile and run parameters, hashed."""
     deg = (g["xadj"][1:] - g["xadj"][:-1]).to(torch.int64)
     hist = torch.bincount(torch.clamp(torch.log2(deg.clamp(min=1).double()).to(torch.int64),
                                       max=40), minlength=41)
     key = (int(g["vwgt"].numel()), int(g["adjncy"].numel()), hist.cpu().tolist(), k, eps,
-           cluster_rounds, refine_rounds, subrounds)
+           cluster_rounds, refine_rounds, subrounds,
+           sorted(ml_params.items()) if ml_params else None)
     return hashlib.sha256(repr(key).encode()).hexdigest()[:16]
 
 
@@ -58,11 +59,19 @@ def _sweeps(g, k, eps, cluster_rounds, refine_rounds, subrounds, seed, p0):
     return lab, part
 
 
+def _multilevel(g, ml_params):
+    from . import partition_multilevel
+    return (partition_multilevel(g, ml_params)[0],)
+
+
 def autotune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
              refine_rounds: int = 6, subrounds: int = 4, seed: int = 1, candidates=None,
-             reps: int = 2, cache: str | None = DEFAULT_CACHE) -> dict:
+             reps: int = 2, cache: str | None = DEFAULT_CACHE,
+             ml_params: dict | None = None) -> dict:
     """Times every candidate, applies the fastest and returns {"best", "ms",
-    "identical", "signature", "device"}; with `cache`, stores the result."""
+    "identical", "signature", "device"}; with `cache`, stores the result.
+    The timed work is the level-0 sweeps, or with `ml_params` one multilevel
+    partition of g with those parameters (the whole call a user makes)."""
     from . import inputs as I
     candidates = list(candidates or CANDIDATES)
     dev = g["xadj"].device
@@ -74,7 +83,8 @@ def autotune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
     try:
         for cand in candidates:
             set_tuning(*cand)
-            out = _sweeps(g, k, eps, cluster_rounds, refine_rounds, subrounds, seed, p0)
+            out = (_multilevel(g, ml_params) if ml_params else
+                   _sweeps(g, k, eps, cluster_rounds, refine_rounds, subrounds, seed, p0))
             if ref is None:
                 ref = out
             else:
@@ -84,7 +94,10 @@ def autotune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record()
             for _ in range(reps):
-                _sweeps(g, k, eps, cluster_rounds, refine_rounds, subrounds, seed, p0)
+                if ml_params:
+                    _multilevel(g, ml_params)
+                else:
+                    _sweeps(g, k, eps, cluster_rounds, refine_rounds, subrounds, seed, p0)
             ev1.record()
             torch.cuda.synchronize(dev)
             times[cand] = ev0.elapsed_time(ev1) / reps
@@ -98,7 +111,8 @@ def autotune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
     res = {"best": dict(zip(("small_max", "med_max", "mid_max", "seg_smem"), best)),
            "ms": {"/".join(map(str, c)): round(t, 3) for c, t in times.items()},
            "identical": identical, "device": _device_name(),
-           "signature": signature(g, k, eps, cluster_rounds, refine_rounds, subrounds)}
+           "signature": signature(g, k, eps, cluster_rounds, refine_rounds, subrounds, ml_params),
+           "workload": "multilevel" if ml_params else "level-0 sweeps"}
     if cache and identical:
         data = {}
         if os.path.exists(cache):
@@ -118,10 +132,10 @@ def autotune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
 
 def load_or_tune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
                  refine_rounds: int = 6, subrounds: int = 4, seed: int = 1,
-                 cache: str = DEFAULT_CACHE) -> dict:
+                 cache: str = DEFAULT_CACHE, ml_params: dict | None = None) -> dict:
     """Applies the cached setting for this device and graph, or tunes (and
     caches) one.  Returns the entry with "cached" set accordingly."""
-    sig = signature(g, k, eps, cluster_rounds, refine_rounds, subrounds)
+    sig = signature(g, k, eps, cluster_rounds, refine_rounds, subrounds, ml_params)
     key = f"{_device_name()}|{sig}"
     if os.path.exists(cache):
         try:
@@ -133,4 +147,4 @@ def load_or_tune(g: dict, k: int, eps: float = 0.03, cluster_rounds: int = 3,
             set_tuning(**entry["best"])
             return dict(entry, cached=True)
     return dict(autotune(g, k, eps, cluster_rounds, refine_rounds, subrounds, seed,
-                         cache=cache), cached=False)
+                         cache=cache, ml_params=ml_params), cached=False)

@@ -496,45 +496,60 @@ __device__ __forceinline__ T ld(const T *p) {
     else return *p;
 }
 
-// Best eligible label of the CTA's row (node slot 0) over the distinct labels:
-// per-thread maxima, reduced over the warp and then by thread 0 (red holds
-// one value per warp); ties on the best key resolve to the smallest label.
+// Best eligible label of the CTA's row (node slot 0) over the distinct labels,
+// in two steps: the largest eligible omega and the own label's omega first
+// (per-thread maxima, warp reductions, red holds one value per warp), then,
+// only when the row proposes (that omega beats the own one, or the block is
+// overloaded), the smallest (tie, label) over the labels reaching it.  The
+// result is the label of the largest (omega, ~tie) key, ties on the key to
+// the smallest label; nd.best gets omega << 32 alone when the row does not
+// propose.
 template <int NT>
 __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *keys,
                                             const int32_t *vals, const uint16_t *dl, int ndl,
                                             NodeSm &nd, unsigned long long *red) {
-    unsigned long long best = 0;
+    uint32_t mw = 0;
     for (int i = threadIdx.x; i < ndl; i += NT) {
         const int slot = dl[i];
         const int32_t L = (int32_t)keys[slot];
-        const int32_t w = vals[slot];
-        if (L == nd.own[0]) {
-            nd.ownw[0] = w;
-        } else if (a.W[L] + nd.c[0] <= bnd(a, L)) {
-            const unsigned long long ck = cand_key(w, nd.h[0], L - nd.lb[0]);
-            best = ck > best ? ck : best;
-        }
+        const uint32_t w = (uint32_t)vals[slot];
+        if (L == nd.own[0]) nd.ownw[0] = (int32_t)w;
+        else if (w > mw && a.W[L] + nd.c[0] <= bnd(a, L)) mw = w;
+    }
+    mw = __reduce_max_sync(0xffffffffu, mw);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mw;
+    __syncthreads();
+    uint32_t M = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) M = max(M, (uint32_t)red[w]);
+    const bool prop = M > 0 && ((int32_t)M > nd.ownw[0] || nd.ovl[0]);
+    __syncthreads();  // red is reused below
+    if (!prop) {
+        if (threadIdx.x == 0) nd.best[0] = (unsigned long long)M << 32;
+        __syncthreads();
+        return;
+    }
+    unsigned long long tl = ~0ull;  // (tie << 32) | label, smallest wins
+    for (int i = threadIdx.x; i < ndl; i += NT) {
+        const int slot = dl[i];
+        const int32_t L = (int32_t)keys[slot];
+        if ((uint32_t)vals[slot] != M || L == nd.own[0]) continue;
+        if (a.W[L] + nd.c[0] > bnd(a, L)) continue;
+        const unsigned long long x =
+            ((unsigned long long)tie_of(nd.h[0], L - nd.lb[0]) << 32) | (uint32_t)L;
+        tl = x < tl ? x : tl;
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
-        best = o > best ? o : best;
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, tl, d);
+        tl = o < tl ? o : tl;
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tl;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < NT / 32; w++) best = red[w] > best ? red[w] : best;
-        nd.best[0] = best;
-    }
-    __syncthreads();
-    const unsigned long long b = nd.best[0];
-    for (int i = threadIdx.x; i < ndl; i += NT) {
-        const int slot = dl[i];
-        const int32_t L = (int32_t)keys[slot];
-        const int32_t w = vals[slot];
-        if (b == 0 || L == nd.own[0] || (uint32_t)w != (uint32_t)(b >> 32)) continue;
-        if (a.W[L] + nd.c[0] > bnd(a, L)) continue;
-        if (cand_key(w, nd.h[0], L - nd.lb[0]) == b) atomicMin(&nd.bestL[0], L);
+        for (int w = 1; w < NT / 32; w++) tl = red[w] < tl ? red[w] : tl;
+        nd.best[0] = ((unsigned long long)M << 32) | (uint32_t)~(uint32_t)(tl >> 32);
+        nd.bestL[0] = (int32_t)(uint32_t)tl;
     }
     __syncthreads();
 }
@@ -907,7 +922,7 @@ __global__ void __launch_bounds__(RS::kNT) k_propose(LPArgs a, int k) {
 // costs work in proportion to its length.  Proposals are buffered in shared
 // memory and emitted 32 at a time by warp 0 (one reservation of proposal
 // slots per batch instead of one contended atomic per row).  Two barriers
-// per row.
+// per row, three when the row proposes (tie hashes only then, see below).
 template <int NT, int E, int TBITS, int MINB>
 struct PipeShape {
     static constexpr int kNT = NT, kE = E, kMaxD = NT * E, kTBits = TBITS, kTS = 1 << TBITS;
@@ -926,7 +941,9 @@ struct PipeSm {
     unsigned long long tab[MODE == kRefineDense ? 1 : PS::kTS];
     int32_t dacc[MODE == kRefineDense ? PS::kNT / 32 : 1][kDenseMaxK];
     int64_t W[kDenseMaxK];
-    unsigned long long wk[PS::kNT / 32];  // per warp: best candidate key
+    unsigned long long wk[PS::kNT / 32];  // per warp: best candidate key (dense)
+    uint32_t wm[PS::kNT / 32];            //           largest eligible omega
+    uint32_t wt[PS::kNT / 32];            //           smallest tie at that omega
     int32_t wl[PS::kNT / 32];             //           its label
     int32_t wo[PS::kNT / 32];             //           omega(v, own) seen
     int32_t bv[32], bT[32], bown[32], bgain[32], bc[32];  // decided proposals,
@@ -1000,6 +1017,19 @@ __device__ __forceinline__ bool cand_better(unsigned long long k1, int32_t l1,
     return k1 > k2 || (k1 == k2 && l1 < l2);
 }
 
+// Thread 0 buffers the current row's proposal (target T).
+template <int MODE, typename PS>
+__device__ __forceinline__ void pipe_buffer(PipeSm<MODE, PS> &sm, const PipeRow &r, int32_t T,
+                                            int32_t gain, bool ovl) {
+    const int i = sm.nbuf++;
+    sm.bv[i] = r.v;
+    sm.bT[i] = T;
+    sm.bown[i] = r.own;
+    sm.bgain[i] = gain;
+    sm.bc[i] = r.c;
+    sm.bovl[i] = ovl ? 1 : 0;
+}
+
 template <int MODE, typename PS>
 __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs a, int k, int cls) {
     if (stopped(a)) return;
@@ -1060,8 +1090,7 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
         const int64_t deg = cur.re - cur.rs;
         const uint64_t h = nhash(a, cur.v);
         const int32_t lb = lbase(a, cur.v);
-        int64_t wown = 0;
-        if (MODE == kRefineHash && threadIdx.x == 0) wown = a.W[cur.own];
+        const int64_t wown = MODE == kRefineHash ? a.W[cur.own] : 0;
         pipe_flush<MODE, PS>(a, sm, false);
         // aggregation of the current row; a slot's creator gathers W(L)
         const uint32_t tbits = deg <= 32 ? 6u : 33u - (uint32_t)__clz((int)(deg - 1));
@@ -1096,11 +1125,10 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
             }
         }
         __syncthreads();
-        // selection: the owners rate their slots (and empty them), or the k
-        // block sums
-        unsigned long long bk = 0;
-        int32_t bl = 0x7fffffff, ow = 0;
         if constexpr (DENSE) {
+            // selection: the first k threads rate the k block sums
+            unsigned long long bk = 0;
+            int32_t bl = 0x7fffffff, ow = 0;
             if ((int)threadIdx.x < k) {
                 const int b = threadIdx.x;
                 int32_t tot = 0;
@@ -1115,62 +1143,104 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
                     bl = b;
                 }
             }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, d);
+                const int32_t ol = __shfl_xor_sync(0xffffffffu, bl, d);
+                if (cand_better(ok, ol, bk, bl)) {
+                    bk = ok;
+                    bl = ol;
+                }
+                ow += __shfl_xor_sync(0xffffffffu, ow, d);
+            }
+            if (lane == 0) {
+                sm.wk[warp] = bk;
+                sm.wl[warp] = bl;
+                sm.wo[warp] = ow;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int q = 1; q < NW; q++) {
+                    if (cand_better(sm.wk[q], sm.wl[q], bk, bl)) {
+                        bk = sm.wk[q];
+                        bl = sm.wl[q];
+                    }
+                    ow += sm.wo[q];
+                }
+                record_visit(a, cur.v, bk, ow);
+                if (bk != 0) {
+                    const int32_t gain = (int32_t)(bk >> 32) - ow;
+                    const bool ovl = sm.W[cur.own] > bnd(a, cur.own);
+                    if (gain > 0 || ovl) pipe_buffer(sm, cur, bl, gain, ovl);
+                }
+            }
         } else {
+            // selection in two steps.  The slot owners empty their slots and
+            // find the largest omega over the eligible labels and the own
+            // label's omega, with no tie hashes.  Only when the row proposes
+            // (that omega beats the own one, or the block is overloaded) do
+            // the labels reaching it hash their ties, and the smallest (tie,
+            // label) wins.  This is the label of the largest (omega, ~tie)
+            // key, ties on the key to the smallest label.
+            uint32_t mw = 0, xw[E];
+            int32_t ow = 0;
 #pragma unroll
             for (int j = 0; j < E; j++) {
+                xw[j] = 0;
                 if (myslot[j] < 0) continue;
-                const unsigned long long x = sm.tab[myslot[j]];
+                const uint32_t wx = (uint32_t)sm.tab[myslot[j]];
                 sm.tab[myslot[j]] = kEmpty;
-                const int32_t wx = (int32_t)(uint32_t)x;
                 if (L[j] == cur.own) {
-                    ow = wx;
+                    ow = (int32_t)wx;
                 } else if (WL[j] + cur.c <= bnd(a, L[j])) {
-                    const unsigned long long ck = cand_key(wx, h, L[j] - lb);
-                    if (cand_better(ck, L[j], bk, bl)) {
-                        bk = ck;
-                        bl = L[j];
+                    xw[j] = wx;
+                    mw = max(mw, wx);
+                }
+            }
+            mw = __reduce_max_sync(0xffffffffu, mw);
+            ow = (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)ow);
+            if (lane == 0) {
+                sm.wm[warp] = mw;
+                sm.wo[warp] = ow;
+            }
+            __syncthreads();
+            uint32_t M = 0;
+            int32_t OW = 0;
+#pragma unroll
+            for (int q = 0; q < NW; q++) {
+                M = max(M, sm.wm[q]);
+                OW += sm.wo[q];
+            }
+            const bool ovl = MODE == kRefineHash && wown > bnd(a, cur.own);
+            if (threadIdx.x == 0) record_visit(a, cur.v, (unsigned long long)M << 32, OW);
+            if (M > 0 && ((int32_t)M > OW || ovl)) {  // the same in every thread
+                uint32_t bt = 0xffffffffu, bl = 0x7fffffffu;
+#pragma unroll
+                for (int j = 0; j < E; j++) {
+                    if (xw[j] != M) continue;
+                    const uint32_t t = tie_of(h, L[j] - lb);
+                    if (t < bt || (t == bt && (uint32_t)L[j] < bl)) {
+                        bt = t;
+                        bl = (uint32_t)L[j];
                     }
                 }
-            }
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, d);
-            const int32_t ol = __shfl_xor_sync(0xffffffffu, bl, d);
-            if (cand_better(ok, ol, bk, bl)) {
-                bk = ok;
-                bl = ol;
-            }
-            ow += __shfl_xor_sync(0xffffffffu, ow, d);
-        }
-        if (lane == 0) {
-            sm.wk[warp] = bk;
-            sm.wl[warp] = bl;
-            sm.wo[warp] = ow;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int q = 1; q < NW; q++) {
-                if (cand_better(sm.wk[q], sm.wl[q], bk, bl)) {
-                    bk = sm.wk[q];
-                    bl = sm.wl[q];
+                const uint32_t wt = __reduce_min_sync(0xffffffffu, bt);
+                bl = __reduce_min_sync(0xffffffffu, bt == wt ? bl : 0x7fffffffu);
+                if (lane == 0) {
+                    sm.wt[warp] = wt;
+                    sm.wl[warp] = (int32_t)bl;
                 }
-                ow += sm.wo[q];
-            }
-            record_visit(a, cur.v, bk, ow);
-            if (bk != 0) {
-                const int32_t gain = (int32_t)(bk >> 32) - ow;
-                bool ovl = false;
-                if (MODE == kRefineDense) ovl = sm.W[cur.own] > bnd(a, cur.own);
-                if (MODE == kRefineHash) ovl = wown > bnd(a, cur.own);
-                if (gain > 0 || ovl) {
-                    const int i = sm.nbuf++;
-                    sm.bv[i] = cur.v;
-                    sm.bT[i] = bl;
-                    sm.bown[i] = cur.own;
-                    sm.bgain[i] = gain;
-                    sm.bc[i] = cur.c;
-                    sm.bovl[i] = ovl ? 1 : 0;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint32_t tb = sm.wt[0];
+                    int32_t lbest = sm.wl[0];
+                    for (int q = 1; q < NW; q++) {
+                        if (sm.wt[q] < tb || (sm.wt[q] == tb && sm.wl[q] < lbest)) {
+                            tb = sm.wt[q];
+                            lbest = sm.wl[q];
+                        }
+                    }
+                    pipe_buffer(sm, cur, lbest, (int32_t)M - OW, ovl);
                 }
             }
         }
@@ -1265,13 +1335,17 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
         if (best != 0 && ck0 == best) bl = lane;
         else if (best != 0 && ck1 == best) bl = lane + 32;
     } else {
+        // the largest eligible omega and the own omega first; tie hashes
+        // only when the row proposes, and only for the labels reaching that
+        // omega (the label of the largest (omega, ~tie) key, then the
+        // smallest label)
         const int nd = t.ndl;
         constexpr int PER = kMedDeg / 32;  // distinct labels per lane (<= deg)
-        unsigned long long ck[PER];
+        uint32_t xw[PER], mw = 0;
         int32_t lab[PER];
 #pragma unroll
         for (int j = 0; j < PER; j++) {
-            ck[j] = 0;
+            xw[j] = 0;
             lab[j] = 0;
             const int i = lane + 32 * j;
             if (i < nd) {
@@ -1281,20 +1355,33 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
                 t.keys[slot] = kEmpty32;
                 t.vals[slot] = 0;
                 lab[j] = L;
-                if (L == own) ownw = w;
-                else if (a.W[L] + c <= bnd(a, L)) ck[j] = cand_key(w, h, L - lb);
-                best = ck[j] > best ? ck[j] : best;
+                if (L == own) {
+                    ownw = w;
+                } else if (a.W[L] + c <= bnd(a, L)) {
+                    xw[j] = (uint32_t)w;
+                    mw = max(mw, (uint32_t)w);
+                }
             }
         }
+        mw = __reduce_max_sync(0xffffffffu, mw);
+        ownw = (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)ownw);
+        best = (unsigned long long)mw << 32;
+        const bool ovl = MODE != kCluster && Wown > bnd(a, own);
+        if (mw > 0 && ((int32_t)mw > ownw || ovl)) {
+            uint32_t bt = 0xffffffffu, lb2 = 0x7fffffffu;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
-            best = o > best ? o : best;
-            ownw += __shfl_xor_sync(0xffffffffu, ownw, d);
+            for (int j = 0; j < PER; j++) {
+                if (xw[j] != mw) continue;
+                const uint32_t tj = tie_of(h, lab[j] - lb);
+                if (tj < bt || (tj == bt && (uint32_t)lab[j] < lb2)) {
+                    bt = tj;
+                    lb2 = (uint32_t)lab[j];
+                }
+            }
+            const uint32_t wt = __reduce_min_sync(0xffffffffu, bt);
+            bl = (int32_t)__reduce_min_sync(0xffffffffu, bt == wt ? lb2 : 0x7fffffffu);
+            best |= (uint32_t)~wt;
         }
-#pragma unroll
-        for (int j = 0; j < PER; j++)
-            if (best != 0 && ck[j] == best) bl = min(bl, lab[j]);
         __syncwarp();
         if (lane == 0) t.ndl = 0;
     }
@@ -2195,9 +2282,11 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
 // open-addressing table spread over the CTAs' shared memory (slot s sits in
 // CTA s / T); each CTA reads a contiguous share of the row and inserts into
 // the owning CTA's slots through distributed shared memory.  The table has
-// >= 2 * degree slots, so an insert always finds room.  Selection follows
-// k_hub_cand / k_hub_tie / k_hub_emit: the largest eligible cand_key, then
-// the smallest label holding it, then the gain rule of Sec. III.A.
+// >= 2 * degree slots, so an insert always finds room.  Selection: the
+// largest eligible omega M and the own label's omega over the cluster, the
+// gain rule of Sec. III.A, and, only for a row that proposes, the smallest
+// (tie, label) over the labels at omega M (the label of the largest
+// cand_key, ties on the key to the smallest label).
 // Per-CTA results are written to the CTA's own shared memory and read by the
 // others with plain loads after a cluster barrier: only 32-bit CAS and add
 // go to another CTA's shared memory.
@@ -2205,9 +2294,10 @@ struct HugeSm {
     uint32_t keys[kHugeSlots];
     int32_t vals[kHugeSlots];
     unsigned long long red[kThreads / 32];
-    unsigned long long cbest;  // this CTA's best cand_key
-    unsigned long long b;      // the cluster's best (local copy)
-    int32_t cbestL, cown;      // this CTA's smallest label holding b; own label's sum
+    unsigned long long cbest;  // this CTA's largest eligible omega
+    unsigned long long b;      // the cluster's (local copy)
+    unsigned long long ctl;    // this CTA's smallest (tie << 32 | label) at omega b
+    int32_t cown, bown;        // own label's sum: this CTA's, the cluster's
     int32_t item;              // rank 0: index into this colour's row list
 };
 
@@ -2249,7 +2339,7 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
         const int it = r0->item;
         if (it >= nrows) break;  // the same value in every CTA of the cluster
         if (threadIdx.x == 0) {
-            sm.cbestL = 0x7fffffff;
+            sm.ctl = ~0ull;
             sm.cown = 0;
         }
         const int32_t li = hl[it];
@@ -2295,70 +2385,62 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
             }
         }
         cl.sync();
-        // this CTA's slots: best eligible candidate and the own label's sum
-        unsigned long long best = 0;
+        // this CTA's slots: the largest eligible omega and the own label's sum
+        uint32_t mw = 0;
         for (int i = threadIdx.x; i < T; i += kThreads) {
             const uint32_t L = sm.keys[i];
             if (L == kEmpty32) continue;
-            const int32_t w = sm.vals[i];
-            if ((int32_t)L == own) sm.cown = w;
-            else if (a.W[L] + c <= bnd(a, (int32_t)L)) {
-                const unsigned long long ck = cand_key(w, h, (int32_t)L - lb);
-                best = ck > best ? ck : best;
-            }
+            const uint32_t w = (uint32_t)sm.vals[i];
+            if ((int32_t)L == own) sm.cown = (int32_t)w;
+            else if (w > mw && a.W[L] + c <= bnd(a, (int32_t)L)) mw = w;
         }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
-            best = o > best ? o : best;
-        }
-        if (lane == 0) sm.red[threadIdx.x >> 5] = best;
+        mw = __reduce_max_sync(0xffffffffu, mw);
+        if (lane == 0) sm.red[threadIdx.x >> 5] = mw;
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int i = 1; i < kThreads / 32; i++) best = sm.red[i] > best ? sm.red[i] : best;
-            sm.cbest = best;
+            for (int i = 1; i < kThreads / 32; i++) mw = max(mw, (uint32_t)sm.red[i]);
+            sm.cbest = mw;
         }
         cl.sync();
         if (threadIdx.x == 0) {
-            unsigned long long b = 0;
+            uint32_t M = 0;
+            int32_t ownw = 0;
             for (unsigned r = 0; r < kHugeCS; r++) {
-                const unsigned long long x = cl.map_shared_rank(&sm, r)->cbest;
-                b = x > b ? x : b;
+                const HugeSm *o = cl.map_shared_rank(&sm, r);
+                M = max(M, (uint32_t)o->cbest);
+                ownw += o->cown;
             }
-            sm.b = b;
+            sm.b = M;
+            sm.bown = ownw;
         }
         __syncthreads();
-        const unsigned long long b = sm.b;
+        const uint32_t M = (uint32_t)sm.b;
+        const int32_t ownw = sm.bown;
+        const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
+        const bool prop = M > 0 && ((int32_t)M > ownw || ovl);
+        // tie hashes only when the row proposes, only for labels at omega M:
+        // the smallest (tie, label) over the cluster wins
         for (int i = threadIdx.x; i < T; i += kThreads) {
             const uint32_t L = sm.keys[i];
             if (L == kEmpty32) continue;
-            const int32_t w = sm.vals[i];
-            if (b != 0 && (int32_t)L != own && (uint32_t)w == (uint32_t)(b >> 32) &&
-                cand_key(w, h, (int32_t)L - lb) == b && a.W[L] + c <= bnd(a, (int32_t)L))
-                atomicMin(&sm.cbestL, (int32_t)L);
+            if (prop && (uint32_t)sm.vals[i] == M && (int32_t)L != own &&
+                a.W[L] + c <= bnd(a, (int32_t)L))
+                atomicMin(&sm.ctl, ((unsigned long long)tie_of(h, (int32_t)L - lb) << 32) | L);
             sm.keys[i] = kEmpty32;
             sm.vals[i] = 0;
         }
         cl.sync();
         if (rank == 0 && threadIdx.x == 0) {
-            int32_t L = 0x7fffffff, ownw = 0;
-            for (unsigned r = 0; r < kHugeCS; r++) {
-                const HugeSm *o = cl.map_shared_rank(&sm, r);
-                L = min(L, o->cbestL);
-                ownw += o->cown;
+            record_visit(a, v, (unsigned long long)M << 32, ownw);
+            if (prop) {
+                unsigned long long tl = ~0ull;
+                for (unsigned r = 0; r < kHugeCS; r++) {
+                    const unsigned long long x = cl.map_shared_rank(&sm, r)->ctl;
+                    tl = x < tl ? x : tl;
+                }
+                const int32_t L = (int32_t)(uint32_t)tl;
+                emit<false>(a, v, L, own, (int32_t)M - ownw, c, ovl, a.W[L]);
             }
-            record_visit(a, v, b, ownw);
-        }
-        if (rank == 0 && threadIdx.x == 0 && b != 0) {
-            int32_t L = 0x7fffffff, ownw = 0;
-            for (unsigned r = 0; r < kHugeCS; r++) {
-                const HugeSm *o = cl.map_shared_rank(&sm, r);
-                L = min(L, o->cbestL);
-                ownw += o->cown;
-            }
-            const int32_t gain = (int32_t)(b >> 32) - ownw;
-            const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
-            if (gain > 0 || ovl) emit<false>(a, v, L, own, gain, c, ovl, a.W[L]);
         }
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory

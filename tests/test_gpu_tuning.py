@@ -91,3 +91,25 @@ def test_autotuner_finds_candidates_identical_and_applies_the_fastest(tmp_path):
         assert again["cached"] and again["best"] == res["best"]
     finally:
         S.set_tuning(**old)
+
+
+def test_autotuner_on_the_multilevel_call(tmp_path):
+    """Tuning on the whole multilevel partition: every candidate returns the
+    same partition, and the cache entry is keyed apart from the sweep one."""
+    import paper_1404_4797_gb300 as S
+    from paper_1404_4797_gb300 import autotune
+    g = I.to_device(_graph(), "cuda")
+    params = S.default_params(8, 0.03, 3)
+    old = S.get_tuning()
+    try:
+        cache = str(tmp_path / "t.json")
+        res = autotune.autotune(g, 8, cache=cache, reps=1, ml_params=params,
+                                candidates=autotune.CANDIDATES[:3])
+        assert res["identical"] and res["workload"] == "multilevel"
+        assert S.get_tuning() == res["best"]
+        sweeps = autotune.load_or_tune(g, 8, cache=cache)
+        assert not sweeps["cached"]  # a different entry
+        again = autotune.load_or_tune(g, 8, cache=cache, ml_params=params)
+        assert again["cached"] and again["best"] == res["best"]
+    finally:
+        S.set_tuning(**old)
