@@ -383,7 +383,7 @@ int sclap_set_launch_mode(int mode);
  * They route rows and contested target segments to kernel paths and change
  * only the speed: every setting gives the same results (each path computes
  * the same selection and arbitration).  The paper has no counterpart.
- * Defaults 32 / 256 / 2048 / 6144; `autotune.py` of the Python package picks
+ * Defaults 32 / 256 / 4096 / 6144; `autotune.py` of the Python package picks
  * them per device and workload by timing candidate sets. */
 typedef struct {
     int32_t small_max;  /* rows of <= small_max entries: groups of lanes of one
@@ -391,7 +391,7 @@ typedef struct {
     int32_t med_max;    /* rows of <= med_max entries: one warp each
                            (small_max .. 256)                                  */
     int32_t mid_max;    /* rows of <= mid_max entries: software-pipelined CTA
-                           rows (512, 1024 or 2048); longer: CTA tables,
+                           rows (512, 1024, 2048 or 4096); longer: CTA tables,
                            thread-block clusters and pieces                    */
     int32_t seg_smem;   /* contested segments of <= seg_smem proposals: one CTA
                            (64 .. 6144); longer: the whole grid               */

@@ -7,8 +7,9 @@
 //   k_build_wl    colour = (h(v,r) >> 32) mod S.  Nodes with 1..kMedDeg
 //                 neighbours go to bucket 5*colour + class (degree <= 4, 8,
 //                 16, 32, 33..kMedDeg); larger rows go to per-colour lists:
-//                 257..kMidDeg, kMidDeg+1..kChunk (and kChunk-entry pieces of
-//                 longer rows), kChunk+1..kHugeDeg in the hash modes.  The
+//                 257..kMidDeg in four length classes, kChunk-entry pieces of
+//                 longer rows (and rows up to kChunk when the tuning lowers
+//                 the pipelined bound), kChunk+1..kHugeDeg in the hash modes.  The
 //                 learned gate (learned.cu) can leave nodes out of a round.
 // Per sub-round j, the propose step runs on three streams:
 //   k_propose_small  small rows: G lanes per node (G = 4, 8, 16, 32),
@@ -17,11 +18,12 @@
 //                 row with a warp-private linear-probing table (the paper's
 //                 Sec. IV.A choice of linear probing) or a k-array.
 //   k_propose_pipe<MODE, PipeShape>  rows of kMedDeg+1..kMidDeg entries in
-//                 three length classes: one CTA per row, software-pipelined
+//                 four length classes: one CTA per row, software-pipelined
 //                 over the CTA's rows, with a shared table of packed
 //                 (label, omega) words sized to the row.
-//   k_propose<MODE, BigRows>  longer rows up to kChunk entries, one CTA per
-//                 row with a table of 32-bit labels; pieces of longer rows
+//   k_propose<MODE, BigRows>  rows above the pipelined bound up to kChunk
+//                 entries, one CTA per row with a table of 32-bit labels;
+//                 pieces of longer rows
 //                 merge into a global table (hash) or k-array (dense) and
 //                 are finished by k_hub_cand / k_hub_tie / k_hub_emit or the
 //                 last piece.
@@ -60,8 +62,8 @@ constexpr int kThreads = 256;
 constexpr int kSmallDeg = 32;            // small nodes: <= 32 entries (one warp pass)
 constexpr int kMedDeg = 256;             // medium nodes: 33..256 entries (one warp each)
 constexpr int kChunk = 4096;             // entries per large-row piece (one CTA)
-constexpr int kMidDeg = 2048;            // rows up to this size: the pipelined CTA kernels
-constexpr int kPipeClasses = 3;          // ... in three length classes (bounds below)
+constexpr int kMidDeg = 4096;            // rows up to this size: the pipelined CTA kernels
+constexpr int kPipeClasses = 4;          // ... in four length classes (bounds below)
 constexpr int kWSlots = 512;             // per-warp table slots for medium rows (>= 2 * kMedDeg)
 constexpr int kSlots = 8192;             // hash table slots (>= 2 * kChunk)
 constexpr int kSlotBits = 13;
@@ -308,7 +310,9 @@ __device__ __forceinline__ int degree_class(int64_t d, int small_max) {
 }
 
 // Length class of a row of kMedDeg < d <= kMidDeg entries (pipelined kernels).
-__device__ __forceinline__ int pipe_class(int64_t d) { return d <= 512 ? 0 : d <= 1024 ? 1 : 2; }
+__device__ __forceinline__ int pipe_class(int64_t d) {
+    return d <= 512 ? 0 : d <= 1024 ? 1 : d <= 2048 ? 2 : 3;
+}
 
 __global__ void __launch_bounds__(kThreads) k_build_wl(LPArgs a, int32_t *wl, int32_t *cnt) {
     if (stopped(a)) return;
@@ -440,8 +444,8 @@ struct NodeSm {
 };
 
 // Shape of a CTA-row kernel: threads, table slots (2^SBITS) and the longest
-// piece it takes.  BigRows: rows of kMidDeg < degree <= kChunk entries and
-// kChunk-entry pieces of longer rows.
+// piece it takes.  BigRows: rows above the pipelined bound (the tuning's
+// mid_max) up to kChunk entries and kChunk-entry pieces of longer rows.
 template <int NT, int SBITS, int CHUNK>
 struct RowShape {
     static constexpr int kNT = NT, kSBits = SBITS, kSl = 1 << SBITS, kCh = CHUNK;
@@ -778,16 +782,18 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE, RS> &sm, int k, cons
 // are split so a warp keeps kSmallIlp items' load chains in flight.
 constexpr int kSmallIlp = 4;
 
+// One item's loads: node, own label, weight, one entry's label and omega, and
+// (hash modes) the gathered weight of that label, kept in 32 bits (every
+// label weight is <= c(V) <= INT32_MAX); dense refinement reads the k block
+// weights from shared memory when it rates.
 struct SmallLoad {
-    int32_t v, own, c, L, w;
-    int64_t WL, Wown;
-    uint64_t h;
+    int32_t v, own, c, L, w, WL, Wown;
     bool has, valid;
 };
 
 template <int MODE, int G>
-__device__ __forceinline__ SmallLoad small_load(const LPArgs &a, const int64_t *Wsm,
-                                                const int32_t *wl, int64_t cnt, int64_t item) {
+__device__ __forceinline__ SmallLoad small_load(const LPArgs &a, const int32_t *wl, int64_t cnt,
+                                                int64_t item) {
     constexpr int NPW = 32 / G;  // nodes per warp item
     const int lane = threadIdx.x & 31;
     const int q = lane / G, r = lane % G;
@@ -795,9 +801,7 @@ __device__ __forceinline__ SmallLoad small_load(const LPArgs &a, const int64_t *
     SmallLoad x;
     x.has = item >= 0 && idx < cnt;
     x.valid = false;
-    x.v = x.own = x.c = x.L = x.w = 0;
-    x.WL = x.Wown = 0;
-    x.h = 0;
+    x.v = x.own = x.c = x.L = x.w = x.WL = x.Wown = 0;
     if (x.has) {
         x.v = wl[idx];
         const int64_t b = a.g.xadj[x.v];
@@ -810,10 +814,10 @@ __device__ __forceinline__ SmallLoad small_load(const LPArgs &a, const int64_t *
             if (!(MODE == kCluster && a.cp && __ldg(&a.cp[u]) != a.cp[x.v])) {
                 x.L = __ldg(&a.lab[u]);
                 x.valid = true;
-                x.WL = MODE == kRefineDense ? Wsm[x.L] : a.W[x.L];
+                if (MODE != kRefineDense) x.WL = (int32_t)a.W[x.L];
             }
         }
-        if (MODE != kCluster) x.Wown = MODE == kRefineDense ? Wsm[x.own] : a.W[x.own];
+        if (MODE == kRefineHash) x.Wown = (int32_t)a.W[x.own];
     }
     return x;
 }
@@ -832,8 +836,9 @@ __device__ __forceinline__ void small_compute(const LPArgs &a, const int64_t *Ws
     unsigned long long ck = 0;
     int32_t ownw = 0;
     if (leader) {
+        const int64_t WL = MODE == kRefineDense ? Wsm[x.L] : (int64_t)x.WL;
         if (x.L == x.own) ownw = (int32_t)wsum;
-        else if (x.WL + x.c <= bnd(a, x.L)) ck = cand_key((int32_t)wsum, h, x.L - lb);
+        else if (WL + x.c <= bnd(a, x.L)) ck = cand_key((int32_t)wsum, h, x.L - lb);
     }
     unsigned long long best = ck;  // reduce within the node's G lanes
 #pragma unroll
@@ -848,7 +853,8 @@ __device__ __forceinline__ void small_compute(const LPArgs &a, const int64_t *Ws
     if (x.has && r == 0) record_visit(a, x.v, best, ownw);
     if (x.has && r == 0 && best != 0) {
         const int32_t gain = (int32_t)(best >> 32) - ownw;
-        const bool ovl = MODE != kCluster && x.Wown > bnd(a, x.own);
+        const int64_t Wown = MODE == kRefineDense ? Wsm[x.own] : (int64_t)x.Wown;
+        const bool ovl = MODE != kCluster && Wown > bnd(a, x.own);
         if (gain > 0 || ovl) {
             const int64_t wT = MODE == kRefineDense ? Wsm[bl] : a.W[bl];
             emit<MODE == kRefineDense>(a, x.v, bl, x.own, gain, x.c, ovl, wT);
@@ -866,7 +872,7 @@ __device__ __forceinline__ void small_bin(const LPArgs &a, const int64_t *Wsm, c
 #pragma unroll
         for (int j = 0; j < kSmallIlp; j++) {
             const int64_t t = it + j * nwarps;
-            x[j] = small_load<MODE, G>(a, Wsm, wl, cnt, t < items ? t : -1);
+            x[j] = small_load<MODE, G>(a, wl, cnt, t < items ? t : -1);
         }
 #pragma unroll
         for (int j = 0; j < kSmallIlp; j++)
@@ -886,7 +892,7 @@ __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
     small_bin<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, a.wl_cnt[b0 + 3], gwarp, nwarps);
 }
 
-// CTA rows: the pieces listed in plist (rows above kMidDeg).
+// CTA rows: the pieces listed in plist (rows above the pipelined bound).
 template <int MODE, typename RS>
 __global__ void __launch_bounds__(RS::kNT) k_propose(LPArgs a, int k) {
     if (stopped(a)) return;
@@ -932,8 +938,10 @@ struct PipeShape {
 };
 using PipeA = PipeShape<128, 4, 10, 8>;   // rows of kMedDeg + 1 .. 512 entries
 using PipeB = PipeShape<128, 8, 11, 5>;   // rows of 513 .. 1024 entries
-using PipeC = PipeShape<512, 4, 12, 2>;   // rows of 1025 .. kMidDeg entries
-static_assert(PipeA::kMaxD == 512 && PipeB::kMaxD == 1024 && PipeC::kMaxD == kMidDeg,
+using PipeC = PipeShape<512, 4, 12, 2>;   // rows of 1025 .. 2048 entries
+using PipeD = PipeShape<1024, 4, 13, 1>;  // rows of 2049 .. kMidDeg entries
+static_assert(PipeA::kMaxD == 512 && PipeB::kMaxD == 1024 && PipeC::kMaxD == 2048 &&
+                  PipeD::kMaxD == kMidDeg && kMidDeg <= kChunk,
               "pipelined row classes (pipe_class)");
 
 template <int MODE, typename PS>
@@ -1402,7 +1410,7 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
 // Rows of <= kMedDeg entries: warps take small-row items (G lanes per row)
 // and then medium rows (a warp per row).  Runs next to k_propose (side stream).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 4) k_propose_small(LPArgs a, int k) {
+__global__ void __launch_bounds__(kThreads, 5) k_propose_small(LPArgs a, int k) {
     if (stopped(a)) return;
     __shared__ int64_t W[kDenseMaxK];
     __shared__ WarpTab tabs[MODE == kRefineDense ? 1 : kThreads / 32];
@@ -2693,14 +2701,16 @@ template <int MODE>
 static RowGrids row_grids(int sms) {
     return RowGrids{row_grid<MODE, BigRows>(sms),
                     {pipe_grid<MODE, PipeA>(sms), pipe_grid<MODE, PipeB>(sms),
-                     pipe_grid<MODE, PipeC>(sms)}};
+                     pipe_grid<MODE, PipeC>(sms), pipe_grid<MODE, PipeD>(sms)}};
 }
 
 // Rows above kMedDeg: the pipelined kernels of the two shorter classes and
-// then the pieces on stream s, the longest pipelined class on s2.
+// then the pieces on stream s, the two longer pipelined classes on s2.
 template <int MODE>
 static void launch_rows(const LPArgs &a, int k, const RowGrids &rg, cudaStream_t s,
                         cudaStream_t s2) {
+    k_propose_pipe<MODE, PipeD><<<rg.p[3], PipeD::kNT, sizeof(PipeSm<MODE, PipeD>), s2>>>(a, k, 3);
+    LAUNCHED();
     k_propose_pipe<MODE, PipeC><<<rg.p[2], PipeC::kNT, sizeof(PipeSm<MODE, PipeC>), s2>>>(a, k, 2);
     LAUNCHED();
     k_propose_pipe<MODE, PipeA><<<rg.p[0], PipeA::kNT, sizeof(PipeSm<MODE, PipeA>), s>>>(a, k, 0);
@@ -2753,7 +2763,8 @@ bool set_tuning(const Tuning &t) {
     const bool ok = (t.small_max == 4 || t.small_max == 8 || t.small_max == 16 ||
                      t.small_max == 32) &&
                     t.med_max >= t.small_max && t.med_max <= kMedDeg &&
-                    (t.mid_max == 512 || t.mid_max == 1024 || t.mid_max == kMidDeg) &&
+                    (t.mid_max == 512 || t.mid_max == 1024 || t.mid_max == 2048 ||
+                     t.mid_max == kMidDeg) &&
                     t.seg_smem >= 64 && t.seg_smem <= kSegSmem;
     if (!ok) return false;
     std::lock_guard<std::mutex> lk(g_tune_mu);

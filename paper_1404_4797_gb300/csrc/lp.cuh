@@ -57,7 +57,7 @@ void pack_isolated(const DGraph &g, const int32_t *cp, int64_t U, int32_t *lab, 
 struct Tuning {
     int32_t small_max;  // rows of <= small_max entries: G-lane groups (4, 8, 16, 32)
     int32_t med_max;    // rows of <= med_max entries: one warp each (small_max..256)
-    int32_t mid_max;    // rows of <= mid_max entries: pipelined CTA rows (512, 1024, 2048)
+    int32_t mid_max;    // rows of <= mid_max entries: pipelined CTA rows (512 .. 4096)
     int32_t seg_smem;   // contested segments of <= seg_smem entries: one CTA (64..6144)
 };
 Tuning tuning();

@@ -12,7 +12,8 @@ from paper_1404_4797_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-SETTINGS = [(32, 256, 2048, 6144), (4, 16, 512, 64), (8, 64, 1024, 2048), (16, 200, 512, 300)]
+SETTINGS = [(32, 256, 4096, 6144), (32, 256, 2048, 6144), (4, 16, 512, 64), (8, 64, 1024, 2048),
+            (16, 200, 512, 300)]
 
 
 def _graph():
