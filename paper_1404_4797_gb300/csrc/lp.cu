@@ -880,14 +880,92 @@ __device__ __forceinline__ void small_bin(const LPArgs &a, const int64_t *Wsm, c
     }
 }
 
+// Rows of <= D entries (D = 4, 8): one thread per node.  The node's (label, omega)
+// pairs are merged in registers (the first occurrence of a label keeps the
+// sum), then rated like every other path: the largest omega over the
+// eligible labels first, tie hashes only when the node proposes and only at
+// that omega.  A warp thus rates 32 nodes with one instruction stream instead
+// of 32 / G nodes in groups of G lanes.
+template <int MODE, int D>
+__device__ __forceinline__ void tiny_node(const LPArgs &a, const int64_t *Wsm, int32_t v) {
+    constexpr bool DENSE = MODE == kRefineDense;
+    const int64_t b = a.g.xadj[v];
+    const int32_t deg = (int32_t)(a.g.xadj[v + 1] - b);
+    const int32_t own = a.lab[v];
+    const int32_t c = a.g.vwgt[v];
+    const int32_t cpv = (MODE == kCluster && a.cp) ? a.cp[v] : 0;
+    int32_t L[D], w[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        L[j] = -1;
+        w[j] = 0;
+        if (j < deg) {
+            const int32_t u = __ldg(&a.g.adjncy[b + j]);
+            w[j] = __ldg(&a.g.adjwgt[b + j]);
+            if (!(MODE == kCluster && a.cp && __ldg(&a.cp[u]) != cpv)) L[j] = __ldg(&a.lab[u]);
+        }
+    }
+#pragma unroll
+    for (int j = 1; j < D; j++)
+#pragma unroll
+        for (int i = 0; i < j; i++)
+            if (L[j] >= 0 && L[i] == L[j]) {
+                w[i] += w[j];
+                L[j] = -1;
+            }
+    int32_t ownw = 0;
+    uint32_t M = 0, ew[D];  // ew: omega of an eligible label, else 0
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        ew[j] = 0;
+        if (L[j] < 0) continue;
+        if (L[j] == own) {
+            ownw = w[j];
+        } else {
+            const int64_t WL = DENSE ? Wsm[L[j]] : a.W[L[j]];
+            if (WL + c <= bnd(a, L[j])) {
+                ew[j] = (uint32_t)w[j];
+                M = max(M, ew[j]);
+            }
+        }
+    }
+    record_visit(a, v, (unsigned long long)M << 32, ownw);
+    const bool ovl = MODE != kCluster && (DENSE ? Wsm[own] : a.W[own]) > bnd(a, own);
+    if (M > 0 && ((int32_t)M > ownw || ovl)) {
+        const uint64_t h = nhash(a, v);
+        const int32_t lb = lbase(a, v);
+        uint32_t bt = 0xffffffffu;
+        int32_t bl = 0x7fffffff;
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            if (ew[j] != M) continue;
+            const uint32_t t = tie_of(h, L[j] - lb);
+            if (t < bt || (t == bt && L[j] < bl)) {
+                bt = t;
+                bl = L[j];
+            }
+        }
+        const int64_t wT = DENSE ? Wsm[bl] : a.W[bl];
+        emit<DENSE>(a, v, bl, own, (int32_t)M - ownw, c, ovl, wT);
+    }
+}
+
+template <int MODE, int D>
+__device__ __forceinline__ void tiny_bin(const LPArgs &a, const int64_t *Wsm, const int32_t *wl,
+                                         int64_t cnt) {
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += nth)
+        tiny_node<MODE, D>(a, Wsm, wl[i]);
+}
+
 template <int MODE>
 __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
     const int b0 = kClasses * a.colour;
     const int64_t n = a.g.n;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    small_bin<MODE, 4>(a, Wsm, a.wl + b0 * n, a.wl_cnt[b0], gwarp, nwarps);
-    small_bin<MODE, 8>(a, Wsm, a.wl + (b0 + 1) * n, a.wl_cnt[b0 + 1], gwarp, nwarps);
+    tiny_bin<MODE, 4>(a, Wsm, a.wl + b0 * n, a.wl_cnt[b0]);
+    tiny_bin<MODE, 8>(a, Wsm, a.wl + (b0 + 1) * n, a.wl_cnt[b0 + 1]);
     small_bin<MODE, 16>(a, Wsm, a.wl + (b0 + 2) * n, a.wl_cnt[b0 + 2], gwarp, nwarps);
     small_bin<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, a.wl_cnt[b0 + 3], gwarp, nwarps);
 }
