@@ -3,8 +3,8 @@
 // coarse node weights, and the quotient edges.  Quotient edges are reduced
 // in two stages: a shared-memory hash table merges equal (C(u), C(v)) pairs
 // inside fixed 2048-entry slices of the fine rows (rows grouped by coarse
-// node), then a radix sort by (C(u), C(v)) and a reduce-by-key produce the
-// canonical sorted CSR.  Also projection (uncoarsening) and cut/balance.
+// node), then a radix sort by (C(u), C(v)) and a tiled reduce of equal keys
+// produce the canonical sorted CSR.  Also projection (uncoarsening) and cut/balance.
 #include "contract.cuh"
 #include "prims.cuh"
 
@@ -148,40 +148,94 @@ __global__ void __launch_bounds__(kCThreads)
     }
 }
 
-struct FlagNew {
-    const unsigned long long *k;
-    __device__ int64_t operator()(int64_t i) const { return (i == 0 || k[i] != k[i - 1]) ? 1 : 0; }
+// Sorted (key, w) pairs -> unique keys, in tiles of kRTile pairs.  Pass 1
+// counts the run starts (first pair of each distinct key) per tile; an
+// exclusive scan of the counts gives each tile its first output position.
+// Pass 2 stages the tile in shared memory, gives each thread kRItems
+// consecutive pairs, ranks its run starts by a block scan, sums each run
+// (reading past the tile when a run continues into the next one) and writes
+// the coarse entry; row degrees get one atomic per row and thread.
+constexpr int kRThreads = 256;
+constexpr int kRItems = 16;
+constexpr int kRTile = kRThreads * kRItems;
+
+__global__ void __launch_bounds__(kRThreads) k_run_count(const unsigned long long *keys, int64_t P,
+                                                         int64_t *tile_cnt) {
+    __shared__ int64_t sm[kRThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kRTile;
+    int64_t cnt = 0;
+#pragma unroll 4
+    for (int j = 0; j < kRItems; j++) {
+        const int64_t i = base + (int64_t)j * kRThreads + threadIdx.x;
+        if (i < P) cnt += (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+    }
+    int64_t tot;
+    block_exclusive_scan<kRThreads>(cnt, &tot, sm);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+}
+
+// Shared tile, one pad slot after every kRItems pairs so that the threads'
+// blocked reads (kRItems apart) fall into different banks.
+constexpr int kRPad = kRTile + kRTile / kRItems;
+__device__ __forceinline__ int rpad(int l) { return l + l / kRItems; }
+
+struct RunSm {
+    unsigned long long k[kRPad];
+    int32_t w[kRPad];
+    int64_t scan[kRThreads / 32 + 1];
 };
 
-// Sorted (key, w) pairs -> unique keys: the thread at the start of each run
-// of equal keys sums the run and writes the coarse entry; row degrees are
-// counted with one atomic per distinct row in each warp.
-__global__ void k_reduce_by_key(const unsigned long long *keys, const int32_t *w, int64_t P,
-                                const int64_t *pos, int cbits, int32_t *adjncy, int32_t *adjwgt,
-                                int32_t *cdeg) {
+__global__ void __launch_bounds__(kRThreads) k_run_emit(const unsigned long long *keys,
+                                                        const int32_t *w, int64_t P,
+                                                        const int64_t *tile_off, int cbits,
+                                                        int32_t *adjncy, int32_t *adjwgt,
+                                                        int32_t *cdeg) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    RunSm &sm = *reinterpret_cast<RunSm *>(smraw);
     const uint64_t mask = (cbits >= 64) ? ~0ull : ((1ull << cbits) - 1);
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t P_r = (P + 31) & ~31ll;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P_r; i += stride) {
-        bool start = false;
-        int64_t row = -1;
-        if (i < P) {
-            const uint64_t k = keys[i];
-            start = i == 0 || keys[i - 1] != k;
-            if (start) {
-                int64_t sum = w[i];
-                for (int64_t j = i + 1; j < P && keys[j] == k; j++) sum += w[j];
-                const int64_t p = pos[i];  // exclusive count of run starts before i
-                adjncy[p] = (int32_t)(k & mask);
-                adjwgt[p] = (int32_t)sum;
-                row = (int64_t)(k >> cbits);
-            }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)row);
-        if (start && (peers & ((1u << lane) - 1)) == 0)
-            atomicAdd(&cdeg[row], __popc(peers));
+    const int64_t base = (int64_t)blockIdx.x * kRTile;
+    const int len = (int)min64(P - base, (int64_t)kRTile);
+    for (int i = threadIdx.x; i < len; i += kRThreads) {
+        sm.k[rpad(i)] = keys[base + i];
+        sm.w[rpad(i)] = w[base + i];
     }
+    __syncthreads();
+    const int l0 = threadIdx.x * kRItems;
+    const unsigned long long before = base > 0 ? keys[base - 1] : 0;
+    int64_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kRItems; j++) {
+        const int l = l0 + j;
+        if (l < len)
+            cnt += (l == 0 ? (base == 0 || sm.k[0] != before) : sm.k[rpad(l)] != sm.k[rpad(l - 1)])
+                       ? 1 : 0;
+    }
+    int64_t tot;
+    int64_t p = tile_off[blockIdx.x] + block_exclusive_scan<kRThreads>(cnt, &tot, sm.scan);
+    int64_t row = -1;
+    int32_t rcnt = 0;
+    for (int j = 0; j < kRItems; j++) {
+        const int l = l0 + j;
+        if (l >= len) break;
+        const unsigned long long k = sm.k[rpad(l)];
+        if (!(l == 0 ? (base == 0 || k != before) : k != sm.k[rpad(l - 1)])) continue;
+        int64_t sum = sm.w[rpad(l)];
+        int m = l + 1;
+        for (; m < len && sm.k[rpad(m)] == k; m++) sum += sm.w[rpad(m)];
+        if (m == len)
+            for (int64_t i = base + len; i < P && keys[i] == k; i++) sum += w[i];
+        adjncy[p] = (int32_t)(k & mask);
+        adjwgt[p] = (int32_t)sum;
+        p++;
+        const int64_t r = (int64_t)(k >> cbits);
+        if (r != row) {
+            if (rcnt) atomicAdd(&cdeg[row], rcnt);
+            row = r;
+            rcnt = 0;
+        }
+        rcnt++;
+    }
+    if (rcnt) atomicAdd(&cdeg[row], rcnt);
 }
 
 struct ArrayI32to64 {
@@ -269,16 +323,25 @@ void contract_impl(const DGraph &g, const int32_t *lab, int32_t *f2c, CoarseGrap
 
     // stage 2: sort by (C(u), C(v)) and reduce equal keys
     radix_sort_pairs((uint64_t *)pk, pw, (int64_t)P, 2 * cbits, sc);
-    int64_t *pos = sc.get<int64_t>((int64_t)P + 1);
-    exclusive_scan(FlagNew{pk}, (int64_t)P, pos, pos + P, sc);
+    const int64_t rtiles = ceil_div<int64_t>((int64_t)P, kRTile);
+    int64_t *tcnt = sc.get<int64_t>(rtiles + 1);
+    int64_t *toff = sc.get<int64_t>(rtiles + 1);
     int64_t m2 = 0;
-    CK(cudaMemcpyAsync(&m2, pos + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    if (P > 0) {
+        k_run_count<<<(unsigned)rtiles, kRThreads, 0, s>>>(pk, (int64_t)P, tcnt);
+        LAUNCHED();
+        exclusive_scan(ArrayI64{tcnt}, rtiles, toff, toff + rtiles, sc);
+        CK(cudaMemcpyAsync(&m2, toff + rtiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
     int32_t *adjncy = (int32_t *)out_alloc(m2 * sizeof(int32_t));
     int32_t *adjwgt = (int32_t *)out_alloc(m2 * sizeof(int32_t));
     int32_t *cdeg = sc.zeros<int32_t>(n2);
     if (P > 0) {
-        k_reduce_by_key<<<grid, 256, 0, s>>>(pk, pw, (int64_t)P, pos, cbits, adjncy, adjwgt, cdeg);
+        CK(cudaFuncSetAttribute(k_run_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(RunSm)));
+        k_run_emit<<<(unsigned)rtiles, kRThreads, sizeof(RunSm), s>>>(
+            pk, pw, (int64_t)P, toff, cbits, adjncy, adjwgt, cdeg);
         LAUNCHED();
     }
     int64_t *cpre = sc.get<int64_t>(n2);

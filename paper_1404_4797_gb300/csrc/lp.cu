@@ -12,9 +12,10 @@
 //                 the pipelined bound), kChunk+1..kHugeDeg in the hash modes.  The
 //                 learned gate (learned.cu) can leave nodes out of a round.
 // Per sub-round j, the propose step runs on three streams:
-//   k_propose_small  small rows: G lanes per node (G = 4, 8, 16, 32),
-//                 __match_any_sync on (node, label) and __reduce_add_sync
-//                 give omega(v, L) in registers; medium rows: one warp per
+//   k_propose_small  small rows: one thread per node for rows of <= 4, 8
+//                 and 16 entries (labels merged in registers); rows of
+//                 17..32 entries on one warp, __match_any_sync on the label
+//                 and __reduce_add_sync give omega(v, L); medium rows: one warp per
 //                 row with a warp-private linear-probing table (the paper's
 //                 Sec. IV.A choice of linear probing) or a k-array.
 //   k_propose_pipe<MODE, PipeShape>  rows of kMedDeg+1..kMidDeg entries in
@@ -880,12 +881,12 @@ __device__ __forceinline__ void small_bin(const LPArgs &a, const int64_t *Wsm, c
     }
 }
 
-// Rows of <= D entries (D = 4, 8): one thread per node.  The node's (label, omega)
-// pairs are merged in registers (the first occurrence of a label keeps the
-// sum), then rated like every other path: the largest omega over the
-// eligible labels first, tie hashes only when the node proposes and only at
-// that omega.  A warp thus rates 32 nodes with one instruction stream instead
-// of 32 / G nodes in groups of G lanes.
+// Rows of <= D entries (D = 4, 8, 16): one thread per node.  The node's
+// (label, omega) pairs are merged in registers (the first occurrence of a
+// label keeps the sum), then rated like every other path: the largest omega
+// over the eligible labels first, tie hashes only when the node proposes and
+// only at that omega.  A warp thus rates 32 nodes with one instruction stream
+// instead of 32 / G nodes in groups of G lanes.
 template <int MODE, int D>
 __device__ __forceinline__ void tiny_node(const LPArgs &a, const int64_t *Wsm, int32_t v) {
     constexpr bool DENSE = MODE == kRefineDense;
@@ -966,7 +967,7 @@ __device__ void process_small(const LPArgs &a, const int64_t *Wsm) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     tiny_bin<MODE, 4>(a, Wsm, a.wl + b0 * n, a.wl_cnt[b0]);
     tiny_bin<MODE, 8>(a, Wsm, a.wl + (b0 + 1) * n, a.wl_cnt[b0 + 1]);
-    small_bin<MODE, 16>(a, Wsm, a.wl + (b0 + 2) * n, a.wl_cnt[b0 + 2], gwarp, nwarps);
+    tiny_bin<MODE, 16>(a, Wsm, a.wl + (b0 + 2) * n, a.wl_cnt[b0 + 2]);
     small_bin<MODE, 32>(a, Wsm, a.wl + (b0 + 3) * n, a.wl_cnt[b0 + 3], gwarp, nwarps);
 }
 
