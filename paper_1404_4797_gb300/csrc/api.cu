@@ -695,11 +695,11 @@ int sclap_refine_learned(const sclap_graph *gp, int32_t k, double eps, int32_t r
         cfg.visit_own = gt.vo;
         int rd = lp_run(cfg, sc, nullptr, W);
         gate_finish(gt, rd, s);
-        unsigned long long vis = 0;
-        CK(cudaMemcpyAsync(&vis, gt.visited, sizeof(vis), cudaMemcpyDeviceToHost, s));
+        unsigned long long vis[2] = {0, 0};
+        CK(cudaMemcpyAsync(vis, gt.visited, sizeof(vis), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (rounds_done) *rounds_done = rd;
-        if (visited_out) *visited_out = (int64_t)vis;
+        if (visited_out) *visited_out = (int64_t)(vis[0] + (unsigned long long)gt.nfull * vis[1]);
     });
     if (rc != SCLAP_OK && backup && gp) {
         cudaMemcpyAsync(part_inout, backup, gp->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);

@@ -32,33 +32,26 @@ __device__ __forceinline__ float log2_feature(int64_t x) {
     return __fadd_rn((float)e, frac);
 }
 
-// Weighted degree of every row over tiles of 4096 entries: thread t takes 16
-// consecutive entries and flushes a running sum whenever its row changes.
-constexpr int kRowTile = 4096;
-
+// Weighted degree of every row: a warp takes 32 consecutive rows and sums
+// each one with its lanes striding over the row's entries (coalesced), then
+// one warp reduction per row.  The callers have checked that every weighted
+// degree fits 31 bits, so 32-bit lane sums and the reduction cannot wrap.
 __global__ void __launch_bounds__(256) k_row_sums(DGraph g, unsigned long long *wdeg) {
-    __shared__ int32_t rowof[kRowTile];
-    __shared__ int32_t tmp[16];
-    const int64_t tiles = ceil_div<int64_t>(g.nnz, kRowTile);
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int64_t e0 = t * kRowTile;
-        const int len = (int)min64(kRowTile, g.nnz - e0);
-        block_rows<256, 16>(g.xadj, g.n, e0, len, rowof, tmp);
-        int32_t row = -1;
-        unsigned long long sw = 0;
-        for (int j = 0; j < 16; j++) {
-            const int i = threadIdx.x * 16 + j;
-            if (i >= len) break;
-            const int32_t v = rowof[i];
-            if (v != row) {
-                if (row >= 0) atomicAdd(&wdeg[row], sw);
-                row = v;
-                sw = 0;
-            }
-            sw += (unsigned long long)g.adjwgt[e0 + i];
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < g.n;
+         base += nw * 32) {
+        const int64_t v = base + lane;
+        const int64_t rs = v < g.n ? g.xadj[v] : 0, re = v < g.n ? g.xadj[v + 1] : 0;
+        uint32_t mine = 0;
+        for (int r = 0; r < 32; r++) {
+            const int64_t s = __shfl_sync(0xffffffffu, rs, r), e = __shfl_sync(0xffffffffu, re, r);
+            uint32_t sum = 0;
+            for (int64_t i = s + lane; i < e; i += 32) sum += (uint32_t)__ldg(&g.adjwgt[i]);
+            sum = __reduce_add_sync(0xffffffffu, sum);
+            if (lane == r) mine = sum;
         }
-        if (row >= 0) atomicAdd(&wdeg[row], sw);
-        __syncthreads();
+        if (v < g.n) wdeg[v] = mine;
     }
 }
 
@@ -123,52 +116,130 @@ __device__ __forceinline__ float mlp_forward(const float *P, const float *x) {
     return z;
 }
 
+// The same forward for two rows at once: every parameter read from shared
+// memory (float4 / float2 vectors) feeds both rows, and each row keeps its
+// own fmaf chain in index order, so each result equals mlp_forward's.
+__device__ __forceinline__ void mlp_forward2(const float *P, const float *xa, const float *xb,
+                                             float *za, float *zb) {
+    float ha[32], hb[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        float aa = P[kMlpB1 + j], ab = aa;
+#pragma unroll
+        for (int i = 0; i < 6; i += 2) {
+            const float2 w = *reinterpret_cast<const float2 *>(&P[kMlpW1 + j * 6 + i]);
+            aa = __fmaf_rn(w.x, xa[i], aa);
+            ab = __fmaf_rn(w.x, xb[i], ab);
+            aa = __fmaf_rn(w.y, xa[i + 1], aa);
+            ab = __fmaf_rn(w.y, xb[i + 1], ab);
+        }
+        ha[j] = bf16_round(aa > 0.0f ? aa : 0.0f);
+        hb[j] = bf16_round(ab > 0.0f ? ab : 0.0f);
+    }
+    float ya = P[kMlpB3], yb = ya;
+#pragma unroll 2
+    for (int j = 0; j < 32; j++) {
+        float aa = P[kMlpB2 + j], ab = aa;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) {
+            const float4 w = *reinterpret_cast<const float4 *>(&P[kMlpW2 + j * 32 + i]);
+            aa = __fmaf_rn(w.x, ha[i], aa);
+            ab = __fmaf_rn(w.x, hb[i], ab);
+            aa = __fmaf_rn(w.y, ha[i + 1], aa);
+            ab = __fmaf_rn(w.y, hb[i + 1], ab);
+            aa = __fmaf_rn(w.z, ha[i + 2], aa);
+            ab = __fmaf_rn(w.z, hb[i + 2], ab);
+            aa = __fmaf_rn(w.w, ha[i + 3], aa);
+            ab = __fmaf_rn(w.w, hb[i + 3], ab);
+        }
+        const float w3 = P[kMlpW3 + j];
+        ya = __fmaf_rn(w3, bf16_round(aa > 0.0f ? aa : 0.0f), ya);
+        yb = __fmaf_rn(w3, bf16_round(ab > 0.0f ? ab : 0.0f), yb);
+    }
+    *za = ya;
+    *zb = yb;
+}
+static_assert(kMlpW2 % 4 == 0 && kMlpW1 % 2 == 0, "vector reads of the parameters");
+
 __device__ __forceinline__ void load_net(const uint16_t *net, float *P) {
     for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) P[i] = bf16_value(net[i]);
     __syncthreads();
 }
 
+// The six features of node v (zeros for a node without neighbours); returns
+// its degree.
+__device__ __forceinline__ int64_t node_features(const DGraph &g, const int32_t *lab,
+                                                 const int64_t *W, int64_t Lmax,
+                                                 const uint8_t *moved,
+                                                 const unsigned long long *wdeg,
+                                                 const int32_t *vb, const int32_t *vo,
+                                                 const int32_t *nmov, int64_t v, float *f) {
+    const int64_t deg = g.xadj[v + 1] - g.xadj[v];
+#pragma unroll
+    for (int i = 0; i < 6; i++) f[i] = 0.f;
+    if (deg > 0) {
+        const int32_t own = lab[v];
+        const int64_t wb = vb[v], wo = vo[v], wd = (int64_t)wdeg[v];
+        f[0] = bf16_round(log2_feature(1 + deg));
+        f[1] = bf16_round(__fdiv_rn(__ll2float_rn(W[own]), __ll2float_rn(Lmax)));
+        f[2] = bf16_round(__fdiv_rn(__ll2float_rn(wb - wo), __ll2float_rn(wd)));
+        f[3] = moved[v] ? 1.0f : 0.0f;
+        f[4] = bf16_round(__fdiv_rn(__int2float_rn(nmov[v]), __ll2float_rn(deg)));
+        f[5] = bf16_round(__fdiv_rn(__ll2float_rn(wo), __ll2float_rn(wd)));
+    }
+    return deg;
+}
+
 // Features of every node (written to x when non-null) and, in gated rounds,
 // the active flags (logit >= z_min); counts the visited rows.  vb / vo: the
 // weight to the best eligible other block / own block that the node's latest
-// visit saw (recorded by the propose kernels).
-__global__ void __launch_bounds__(256)
+// visit saw (recorded by the propose kernels).  A CTA takes 2 * blockDim
+// consecutive nodes per step, each thread two of them (v and v + blockDim).
+__global__ void __launch_bounds__(256, 2)
     k_gate(DGraph g, const int32_t *lab, const int64_t *W, int64_t Lmax, const uint8_t *moved,
            const unsigned long long *wdeg, const int32_t *vb, const int32_t *vo,
            const int32_t *nmov, const uint16_t *net, float z_min, bool full, float *x_out,
            uint8_t *active, unsigned long long *visited) {
-    __shared__ float P[kMlpParams];
+    __shared__ __align__(16) float P[kMlpParams];
     const bool score = !full && net;
     if (score) load_net(net, P);
     const int lane = threadIdx.x & 31;
-    const int64_t n_r = (g.n + 31) & ~31ll;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_r;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        bool vis = false;
-        if (v < g.n) {
-            const int64_t deg = g.xadj[v + 1] - g.xadj[v];
-            float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (deg > 0) {
-                const int32_t own = lab[v];
-                const int64_t wb = vb[v], wo = vo[v], wd = (int64_t)wdeg[v];
-                f[0] = bf16_round(log2_feature(1 + deg));
-                f[1] = bf16_round(__fdiv_rn(__ll2float_rn(W[own]), __ll2float_rn(Lmax)));
-                f[2] = bf16_round(__fdiv_rn(__ll2float_rn(wb - wo), __ll2float_rn(wd)));
-                f[3] = moved[v] ? 1.0f : 0.0f;
-                f[4] = bf16_round(__fdiv_rn(__int2float_rn(nmov[v]), __ll2float_rn(deg)));
-                f[5] = bf16_round(__fdiv_rn(__ll2float_rn(wo), __ll2float_rn(wd)));
-            }
-            if (x_out) {
+    const int64_t chunk = 2 * (int64_t)blockDim.x;
+    const int64_t nchunks = ceil_div<int64_t>(g.n, chunk);
+    for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+        const int64_t v[2] = {ci * chunk + threadIdx.x, ci * chunk + threadIdx.x + blockDim.x};
+        float f[2][6];
+        int64_t deg[2] = {0, 0};
 #pragma unroll
-                for (int i = 0; i < 6; i++) x_out[v * 6 + i] = f[i];
+        for (int q = 0; q < 2; q++) {
+            if (v[q] < g.n) {
+                deg[q] = node_features(g, lab, W, Lmax, moved, wdeg, vb, vo, nmov, v[q], f[q]);
+                if (x_out) {
+#pragma unroll
+                    for (int i = 0; i < 6; i++) x_out[v[q] * 6 + i] = f[q][i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 6; i++) f[q][i] = 0.f;
             }
-            bool act = true;
-            if (score) act = mlp_forward(P, f) >= z_min;
-            active[v] = act ? 1 : 0;
-            vis = act && deg > 0;
         }
-        const unsigned b = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0 && b) atomicAdd(visited, (unsigned long long)__popc(b));
+        bool act[2] = {true, true};
+        if (score) {
+            float z[2];
+            mlp_forward2(P, f[0], f[1], &z[0], &z[1]);
+            act[0] = z[0] >= z_min;
+            act[1] = z[1] >= z_min;
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            if (v[q] < g.n) {
+                active[v[q]] = act[q] ? 1 : 0;
+                if (act[q] && deg[q] > 0) cnt++;
+            }
+        }
+        cnt = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        if (lane == 0 && cnt) atomicAdd(visited, (unsigned long long)cnt);
     }
 }
 
@@ -196,9 +267,14 @@ void gate_init(Gate &gt, Scratch &sc) {
     gt.nmov = sc.get<int32_t>(n ? n : 1);
     gt.movers = sc.get<int32_t>(n ? n : 1);
     gt.nmovers = sc.get<int32_t>(1);
-    gt.visited = sc.zeros<unsigned long long>(1);
+    gt.visited = sc.zeros<unsigned long long>(2);
+    gt.nfull = 0;
     if (gt.g.nnz > 0) {
         k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, wd);
+        LAUNCHED();
+    }
+    if (n > 0) {
+        k_count_rows<<<sms * 4, 256, 0, s>>>(gt.g, gt.visited + 1);
         LAUNCHED();
     }
 }
@@ -217,11 +293,8 @@ bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
         LAUNCHED();
     }
     float *x = gt.trace_x ? gt.trace_x + (size_t)r * n * 6 : nullptr;
-    if (full && !x) {  // nothing to compute: every node, count the rows
-        if (n > 0) {
-            k_count_rows<<<sms * 4, 256, 0, s>>>(gt.g, gt.visited);
-            LAUNCHED();
-        }
+    if (full && !x) {  // nothing to compute: every row is visited
+        gt.nfull++;
         *active = nullptr;
         return true;
     }

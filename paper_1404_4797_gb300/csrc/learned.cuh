@@ -30,7 +30,10 @@ struct Gate {
     int32_t *vb, *vo;           // latest visit: weight to the best eligible other / own block
     int32_t *nmov;              // per round: moved neighbours
     int32_t *movers, *nmovers;  // nodes that moved in the previous round
-    unsigned long long *visited;  // device counter
+    unsigned long long *visited;  // device counters: rows visited by gated or traced
+                                  // rounds; [1] rows with neighbours
+    int nfull = 0;                // full rounds without traces (host count): each
+                                  // visits visited[1] rows
 };
 
 // Allocates the gate's arrays and computes the weighted degrees.

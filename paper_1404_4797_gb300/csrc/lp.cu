@@ -171,8 +171,8 @@ struct LPArgs {
     int32_t *pcnt;          // their lengths
     int64_t Ptot;
     const int64_t *Hfin;    // hash: selection items of multi-piece rows [nL + 1]
-    unsigned long long *hbest;
-    int32_t *hbestL, *hown;
+    unsigned long long *hbest, *htl;  // per multi-piece row: omega M << 32; (tie << 32) | label
+    int32_t *hown;
     unsigned long long *prof;  // [2] entries, nodes, or null
     // rows of kChunk < degree <= kHugeDeg in the hash modes: one CTA cluster
     // each; hlist + c * nL lists colour c's rows (indices into Lnodes)
@@ -1344,26 +1344,31 @@ __global__ void __launch_bounds__(PS::kNT, PS::kMinBlocks) k_propose_pipe(LPArgs
     pipe_flush<MODE, PS>(a, sm, true);
 }
 
-// Medium rows (33..kMedDeg entries): one warp per row with a warp-private
-// shared-memory table, no block-wide barriers.
+// Medium rows (up to kMedDeg entries): one warp per row with a warp-private
+// shared-memory table, no block-wide barriers.  A slot packs the label in the
+// high and omega in the low 32 bits (a row's weighted degree fits 31 bits, so
+// adding omega never carries into the label): a new label is one CAS, a
+// repeated one one add.
 struct WarpTab {
-    uint32_t keys[kWSlots];   // labels; 0xffffffff = empty
-    int32_t vals[kWSlots];
-    uint16_t dl[kMedDeg];     // slots in insertion order
+    unsigned long long s[kWSlots];  // kEmpty = empty
+    uint16_t dl[kMedDeg];           // slots in insertion order
     int ndl;
 };
 
-__device__ __forceinline__ void wtab_add(WarpTab &t, uint32_t L, int32_t w) {
+// Adds (L, w); returns the slot when this call created it, else -1.
+__device__ __forceinline__ int wtab_insert(WarpTab &t, uint32_t L, int32_t w) {
+    const unsigned long long key = (unsigned long long)L << 32;
     uint32_t slot = (uint32_t)(((uint64_t)L * 0x9E3779B97F4A7C15ull) >> 55) & (kWSlots - 1);
     for (int probe = 0; probe < kWSlots; probe++) {
-        const uint32_t prev = atomicCAS(&t.keys[slot], kEmpty32, L);
-        if (prev == kEmpty32 || prev == L) {
-            atomicAdd(&t.vals[slot], w);
-            if (prev == kEmpty32) t.dl[atomicAdd(&t.ndl, 1)] = (uint16_t)slot;
-            return;
+        const unsigned long long prev = atomicCAS(&t.s[slot], kEmpty, key | (uint32_t)w);
+        if (prev == kEmpty) return (int)slot;
+        if ((prev & 0xffffffff00000000ull) == key) {
+            atomicAdd(&t.s[slot], (unsigned long long)(uint32_t)w);
+            return -1;
         }
         slot = (slot + 1) & (kWSlots - 1);
     }
+    return -1;
 }
 
 template <int MODE>
@@ -1394,9 +1399,20 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
         }
 #pragma unroll
         for (int j = 0; j < kUnroll; j++) {
-            if (u[j] < 0) continue;
-            if constexpr (DENSE) atomicAdd(&dacc[L[j]], w[j]);
-            else wtab_add(t, (uint32_t)L[j], w[j]);
+            if constexpr (DENSE) {
+                if (u[j] >= 0) atomicAdd(&dacc[L[j]], w[j]);
+            } else {
+                const int cs = u[j] >= 0 ? wtab_insert(t, (uint32_t)L[j], w[j]) : -1;
+                // the warp appends its new slots to the insertion-order list
+                const unsigned m = __ballot_sync(0xffffffffu, cs >= 0);
+                if (m) {
+                    const int base = t.ndl;
+                    if (cs >= 0) t.dl[base + __popc(m & ((1u << lane) - 1))] = (uint16_t)cs;
+                    __syncwarp();
+                    if (lane == 0) t.ndl = base + __popc(m);
+                    __syncwarp();
+                }
+            }
         }
     }
     __syncwarp();
@@ -1437,10 +1453,10 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
             const int i = lane + 32 * j;
             if (i < nd) {
                 const int slot = t.dl[i];
-                const int32_t L = (int32_t)t.keys[slot];
-                const int32_t w = t.vals[slot];
-                t.keys[slot] = kEmpty32;
-                t.vals[slot] = 0;
+                const unsigned long long x = t.s[slot];
+                const int32_t L = (int32_t)(x >> 32);
+                const int32_t w = (int32_t)(uint32_t)x;
+                t.s[slot] = kEmpty;
                 lab[j] = L;
                 if (L == own) {
                     ownw = w;
@@ -1500,8 +1516,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_propose_small(LPArgs a, int k) 
         for (int b = lane; b < kDenseMaxK; b += 32) dacc[warp][b] = 0;
     } else {
         for (int i = lane; i < kWSlots; i += 32) {
-            tabs[warp].keys[i] = kEmpty32;
-            tabs[warp].vals[i] = 0;
+            tabs[warp].s[i] = kEmpty;
         }
         if (lane == 0) tabs[warp].ndl = 0;
     }
@@ -2283,27 +2298,20 @@ __global__ void __launch_bounds__(kThreads) k_hub_cand(LPArgs a) {
         const int32_t lb = lbase(a, v);
         const int64_t off = a.Loff[it.li];
         const int32_t *gdl = a.gdl + a.Ldlo[it.li];
-        unsigned long long best = 0;
+        uint32_t mw = 0;
         for (int64_t i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
             const int32_t slot = __ldcg(&gdl[i]);
             const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
-            const int32_t w = __ldcg(&a.gvals[off + slot]);
-            if (L == own) a.hown[it.li] = w;
-            else if (a.W[L] + c <= bnd(a, L)) {
-                const unsigned long long ck = cand_key(w, h, L - lb);
-                best = ck > best ? ck : best;
-            }
+            const uint32_t w = (uint32_t)__ldcg(&a.gvals[off + slot]);
+            if (L == own) a.hown[it.li] = (int32_t)w;
+            else if (w > mw && a.W[L] + c <= bnd(a, L)) mw = w;
         }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
-            best = o > best ? o : best;
-        }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+        mw = __reduce_max_sync(0xffffffffu, mw);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mw;
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 1; w < kThreads / 32; w++) best = red[w] > best ? red[w] : best;
-            if (best) atomicMax(&a.hbest[it.li], best);
+            for (int w = 1; w < kThreads / 32; w++) mw = max(mw, (uint32_t)red[w]);
+            if (mw) atomicMax(&a.hbest[it.li], (unsigned long long)mw << 32);
         }
         __syncthreads();
     }
@@ -2322,16 +2330,29 @@ __global__ void __launch_bounds__(kThreads) k_hub_tie(LPArgs a) {
         const int32_t lb = lbase(a, v);
         const int64_t off = a.Loff[it.li];
         const int32_t *gdl = a.gdl + a.Ldlo[it.li];
-        const unsigned long long b = a.hbest[it.li];
+        // tie hashes only for a row that proposes, only at omega M
+        const uint32_t M = (uint32_t)(a.hbest[it.li] >> 32);
+        const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
+        const bool prop = M > 0 && ((int32_t)M > __ldcg(&a.hown[it.li]) || ovl);
+        unsigned long long tl = ~0ull;
         for (int64_t i = it.begin + threadIdx.x; i < it.end; i += kThreads) {
             const int32_t slot = __ldcg(&gdl[i]);
             const int32_t L = (int32_t)(uint32_t)__ldcg(&a.gkeys[off + slot]);
-            const int32_t w = __ldcg(&a.gvals[off + slot]);
-            if (b != 0 && L != own && (uint32_t)w == (uint32_t)(b >> 32) && a.W[L] + c <= bnd(a, L) &&
-                cand_key(w, h, L - lb) == b)
-                atomicMin(&a.hbestL[it.li], L);
+            const uint32_t w = (uint32_t)__ldcg(&a.gvals[off + slot]);
+            if (prop && L != own && w == M && a.W[L] + c <= bnd(a, L)) {
+                const unsigned long long x = ((unsigned long long)tie_of(h, L - lb) << 32) | (uint32_t)L;
+                tl = x < tl ? x : tl;
+            }
             a.gkeys[off + slot] = kEmpty;
             a.gvals[off + slot] = 0;
+        }
+        if (__any_sync(0xffffffffu, tl != ~0ull)) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, tl, d);
+                tl = o < tl ? o : tl;
+            }
+            if ((threadIdx.x & 31) == 0) atomicMin(&a.htl[it.li], tl);
         }
     }
 }
@@ -2344,19 +2365,19 @@ __global__ void __launch_bounds__(kThreads) k_hub_emit(LPArgs a) {
         if (a.Hfin[li + 1] == a.Hfin[li]) continue;  // single-piece row
         const int32_t v = a.Lnodes[li];
         if (colour_of(a, v) != (uint32_t)a.colour) continue;
-        const unsigned long long b = a.hbest[li];
+        const unsigned long long b = a.hbest[li];  // omega M << 32
         const int32_t own = a.lab[v];
         record_visit(a, v, b, a.hown[li]);
         if (b != 0) {
             const int32_t gain = (int32_t)(b >> 32) - a.hown[li];
             const bool ovl = MODE != kCluster && a.W[own] > bnd(a, own);
             if (gain > 0 || ovl) {
-                const int32_t L = a.hbestL[li];
+                const int32_t L = (int32_t)(uint32_t)a.htl[li];
                 emit<false>(a, v, L, own, gain, a.g.vwgt[v], ovl, a.W[L]);
             }
         }
         a.hbest[li] = 0;
-        a.hbestL[li] = 0x7fffffff;
+        a.htl[li] = ~0ull;
         a.hown[li] = 0;
         a.Lndl[li] = 0;
     }
@@ -2542,12 +2563,6 @@ struct HubFin {
         return d <= kHugeDeg ? 0 : ceil_div<int64_t>(d, kFin);
     }
 };
-
-__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t val) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = val;
-}
 
 // ---------------------------------------------------------------- large-node lists
 
@@ -3037,8 +3052,8 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 a.Hfin = Hfin;
                 a.hbest = sc.zeros<unsigned long long>(nL);
                 a.hown = sc.zeros<int32_t>(nL);
-                a.hbestL = sc.get<int32_t>(nL);
-                k_fill_i32<<<sms, 256, 0, s>>>(a.hbestL, nL, 0x7fffffff);
+                a.htl = sc.get<unsigned long long>(nL);
+                CK(cudaMemsetAsync(a.htl, 0xff, nL * sizeof(unsigned long long), s));
                 LAUNCHED();
                 a.gkeys = sc.get<unsigned long long>(tot[0]);
                 a.gvals = sc.zeros<int32_t>(tot[0]);
