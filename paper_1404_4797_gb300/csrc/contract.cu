@@ -100,32 +100,39 @@ __global__ void __launch_bounds__(kCThreads)
         if (threadIdx.x == 0) sm.cu0 = f2c[members[sm.rowof[0]]];
         __syncthreads();
         const int32_t cu0 = sm.cu0;
-        for (int le = threadIdx.x; le < len; le += kCThreads) {
-            const int32_t mi = sm.rowof[le];
-            const int32_t v = __ldg(&members[mi]);
-            const int64_t idx = __ldg(&g.xadj[v]) + (e0 + le - __ldg(&mpre[mi]));
-            const int32_t cu = __ldg(&f2c[v]);
-            const int32_t cv = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
-            if (cu == cv) continue;  // edge inside a cluster
-            const int32_t w = __ldg(&g.adjwgt[idx]);
-            Key key;
-            uint32_t slot;
-            if constexpr (K32) {
-                key = ((uint32_t)(cu - cu0) << cbits) | (uint32_t)cv;
-                slot = (key * 0x9E3779B1u) >> (32 - kCBits);
-            } else {
-                key = ((uint64_t)(uint32_t)cu << cbits) | (uint32_t)cv;
-                slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCBits));
-            }
-            for (int probe = 0; probe < kCSlots; probe++) {  // never full: load <= 1/2
-                const Key prev = atomicCAS(&sm.keys[slot], kEmptyK, key);
-                if (prev == kEmptyK || prev == key) {
-                    atomicAdd(&sm.vals[slot], w);
-                    if (prev == kEmptyK) sm.dl[atomicAdd(&sm.ndl, 1)] = (uint16_t)slot;
-                    break;
+        // the same number of steps in every thread (warp-wide appends of new slots)
+        for (int lb = 0; lb < len; lb += kCThreads) {
+            const int le = lb + threadIdx.x;
+            int created = -1;
+            if (le < len) {
+                const int32_t mi = sm.rowof[le];
+                const int32_t v = __ldg(&members[mi]);
+                const int64_t idx = __ldg(&g.xadj[v]) + (e0 + le - __ldg(&mpre[mi]));
+                const int32_t cu = __ldg(&f2c[v]);
+                const int32_t cv = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
+                if (cu != cv) {  // else an edge inside a cluster
+                    const int32_t w = __ldg(&g.adjwgt[idx]);
+                    Key key;
+                    uint32_t slot;
+                    if constexpr (K32) {
+                        key = ((uint32_t)(cu - cu0) << cbits) | (uint32_t)cv;
+                        slot = (key * 0x9E3779B1u) >> (32 - kCBits);
+                    } else {
+                        key = ((uint64_t)(uint32_t)cu << cbits) | (uint32_t)cv;
+                        slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCBits));
+                    }
+                    for (int probe = 0; probe < kCSlots; probe++) {  // never full: load <= 1/2
+                        const Key prev = atomicCAS(&sm.keys[slot], kEmptyK, key);
+                        if (prev == kEmptyK || prev == key) {
+                            atomicAdd(&sm.vals[slot], w);
+                            if (prev == kEmptyK) created = (int)slot;
+                            break;
+                        }
+                        slot = (slot + 1) & (kCSlots - 1);
+                    }
                 }
-                slot = (slot + 1) & (kCSlots - 1);
             }
+            warp_append(sm.dl, &sm.ndl, created);
         }
         __syncthreads();
         const int ndl = sm.ndl;

@@ -475,23 +475,22 @@ struct PropSm {
     int ndl, item, flag;
 };
 
-// Inserts (label L, w) into a linear-probing table of 32-bit labels; a first
-// insertion appends its slot to dl.  Returns false only if the table is full
-// (never at load <= 1/2).
-template <typename DL>
-__device__ __forceinline__ bool table_add(uint32_t *keys, int32_t *vals, DL *dl, int *ndl,
-                                          uint32_t mask, int bits, uint32_t L, int32_t w) {
+// Inserts (label L, w) into a linear-probing table of 32-bit labels.  Returns
+// the slot when this call created it (the caller appends it to the distinct
+// list, one reservation per warp), -1 when the label was there, -2 only if
+// the table is full (never at load <= 1/2).
+__device__ __forceinline__ int table_insert(uint32_t *keys, int32_t *vals, uint32_t mask, int bits,
+                                            uint32_t L, int32_t w) {
     uint32_t slot = (L * 0x9E3779B1u) >> (32 - bits);
     for (uint32_t probe = 0; probe <= mask; probe++) {
         const uint32_t prev = atomicCAS(&keys[slot], kEmpty32, L);
         if (prev == kEmpty32 || prev == L) {
             atomicAdd(&vals[slot], w);
-            if (prev == kEmpty32) dl[atomicAdd(ndl, 1)] = (DL)slot;
-            return true;
+            return prev == kEmpty32 ? (int)slot : -1;
         }
         slot = (slot + 1) & mask;
     }
-    return false;
+    return -2;
 }
 
 // Loads that bypass L1 (tables merged by other CTAs through L2 atomics).
@@ -662,7 +661,9 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE, RS> &sm, int k, cons
         const int64_t e1 = min64(deg, e0 + kChunk);
         const int64_t rs = sm.nd.rs[0];
         const int32_t cpv = sm.nd.cpv[0];
-        for (int64_t eb = e0 + threadIdx.x; eb < e1; eb += kUnroll * NT) {
+        // every thread runs the same number of steps (warp-wide appends)
+        for (int64_t ebase = e0; ebase < e1; ebase += kUnroll * NT) {
+            const int64_t eb = ebase + threadIdx.x;
             int32_t u[kUnroll], w[kUnroll], L[kUnroll];
 #pragma unroll
             for (int j = 0; j < kUnroll; j++) {
@@ -677,13 +678,14 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE, RS> &sm, int k, cons
             }
 #pragma unroll
             for (int j = 0; j < kUnroll; j++) {
-                if (u[j] < 0) continue;
                 if constexpr (DENSE) {
-                    atomicAdd(&sm.t.acc[L[j]], w[j]);
+                    if (u[j] >= 0) atomicAdd(&sm.t.acc[L[j]], w[j]);
                 } else {
-                    if (!table_add(sm.t.keys, sm.t.vals, sm.t.dl, &sm.ndl, RS::kSl - 1, RS::kSBits,
-                                   (uint32_t)L[j], w[j]))
-                        a.ctr->err = kErrTable;
+                    const int cs = u[j] >= 0 ? table_insert(sm.t.keys, sm.t.vals, RS::kSl - 1,
+                                                            RS::kSBits, (uint32_t)L[j], w[j])
+                                             : -1;
+                    if (cs == -2) a.ctr->err = kErrTable;
+                    warp_append(sm.t.dl, &sm.ndl, cs);
                 }
             }
         }

@@ -44,6 +44,21 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T *total, T *smem /* >= N
     return res;
 }
 
+// Appends the non-negative values x of the calling warp's lanes to list
+// (count in *cnt), lane order within the warp: one atomic per warp.  Every
+// lane of the warp must call it.
+template <typename T>
+__device__ __forceinline__ void warp_append(T *list, int *cnt, int x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, x >= 0);
+    if (!m) return;
+    const int first = __ffs(m) - 1;
+    int base = 0;
+    if (lane == first) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, first);
+    if (x >= 0) list[base + __popc(m & ((1u << lane) - 1))] = (T)x;
+}
+
 // ---------------------------------------------------------------- device-wide exclusive scan
 
 template <typename F>
