@@ -412,6 +412,7 @@ def run_learned(args, cfg, S, I, g, n, m, dev):
             "rounds": rounds, "train_seeds": args.train_seeds, "eval_seeds": args.eval_seeds,
             "train_samples": samples, "train_epochs": args.epochs, "train_s": train_s,
             "train_loss": loss, "z_min": z_min, "full_every": 3,
+            "tuning": getattr(args, "tuning", None),
             "moved_frac_in_traces": moved_frac, "z_min90": z_min90,
             "plain_ms": mean(res["plain_ms"]), "learned_ms": mean(res["learned_ms"]),
             "speedup": mean(res["plain_ms"]) / mean(res["learned_ms"]),
@@ -685,6 +686,7 @@ def main():
     tune = autotune.load_or_tune(g, cfg["k"], cfg["eps"], cfg["cluster_rounds"],
                                  cfg["refine_rounds"], cfg["subrounds"], cfg["seed"],
                                  ml_params=params if args.op == "multilevel" else None)
+    args.tuning = dict(tune["best"], tuned_on=tune.get("workload"))
     if args.op == "learned":
         return run_learned(args, cfg, S, I, g, n, m, dev)
     if args.op == "vcycle":

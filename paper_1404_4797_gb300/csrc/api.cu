@@ -678,6 +678,7 @@ int sclap_refine_learned(const sclap_graph *gp, int32_t k, double eps, int32_t r
         gt.rounds = rounds;
         gt.trace_x = trace_x;
         gt.trace_y = trace_y;
+        gt.unit = t.sum_w == g.nnz;  // weights are >= 1, so a sum of nnz means all are 1
         gate_init(gt, sc);
         LPConfig cfg{};
         cfg.g = g;

@@ -55,43 +55,66 @@ __global__ void __launch_bounds__(256) k_row_sums(DGraph g, unsigned long long *
     }
 }
 
-// moved[v] = label changed since the previous call; prev = labels now.  The
-// moved nodes are appended to movers (count in *nmovers) when movers is given.
-__global__ void k_moved(int64_t n, const int32_t *lab, int32_t *prev, uint8_t *moved,
-                        uint8_t *trace_y, bool first, int32_t *movers, int32_t *nmovers) {
+// Movers with longer rows than this are scattered in pieces of this many
+// entries, one CTA per piece, so one long row does not hold up the launch.
+constexpr int kScatChunk = 2048;
+
+// moved[v] = label changed since the previous call; prev = labels now.  When
+// movers is given, the moved nodes with rows of <= kScatChunk entries are
+// appended to movers (count in cnt[0]) and the pieces of longer rows to
+// pieces as (v << 20) | piece (count in cnt[1]).
+__global__ void k_moved(int64_t n, const int64_t *xadj, const int32_t *lab, int32_t *prev,
+                        uint8_t *moved, uint8_t *trace_y, bool first, int32_t *movers,
+                        int64_t *pieces, int32_t *cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t n_r = (n + 31) & ~31ll;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_r;
          v += (int64_t)gridDim.x * blockDim.x) {
         uint8_t m = 0;
+        int64_t deg = 0;
         if (v < n) {
             const int32_t l = lab[v];
             m = first ? 0 : (uint8_t)(l != prev[v]);
             moved[v] = m;
             prev[v] = l;
             if (trace_y) trace_y[v] = m;
+            if (m && movers) deg = xadj[v + 1] - xadj[v];
         }
         if (movers) {
-            const unsigned b = __ballot_sync(0xffffffffu, m != 0);
+            const bool shortrow = m && deg <= kScatChunk;
+            const unsigned b = __ballot_sync(0xffffffffu, shortrow);
             int base = 0;
-            if (lane == 0 && b) base = atomicAdd(nmovers, __popc(b));
+            if (lane == 0 && b) base = atomicAdd(&cnt[0], __popc(b));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (m) movers[base + __popc(b & ((1u << lane) - 1))] = (int32_t)v;
+            if (shortrow) movers[base + __popc(b & ((1u << lane) - 1))] = (int32_t)v;
+            if (m && deg > kScatChunk) {  // rare: one reservation per long row
+                const int np = (int)((deg + kScatChunk - 1) / kScatChunk);
+                const int pb = atomicAdd(&cnt[1], np);
+                for (int q = 0; q < np; q++) pieces[pb + q] = (v << 20) | q;
+            }
         }
     }
 }
 
-// Moved-neighbour counts: every mover adds 1 to each of its neighbours (one
-// warp per mover), so the cost follows the movers' rows, not the graph.
-__global__ void k_scatter_moved(DGraph g, const int32_t *movers, const int32_t *nmovers,
-                                int32_t *nmov) {
-    const int cnt = *nmovers;
+// Moved-neighbour counts: every mover adds 1 to each of its neighbours, so
+// the cost follows the movers' rows, not the graph.  Short rows: one warp
+// each; pieces of long rows: one CTA each.
+__global__ void k_scatter_moved(DGraph g, const int32_t *movers, const int64_t *pieces,
+                                const int32_t *cnt, int32_t *nmov) {
+    const int nm = cnt[0], np = cnt[1];
     const int lane = threadIdx.x & 31;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nm;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t v = movers[i];
         for (int64_t e = g.xadj[v] + lane; e < g.xadj[v + 1]; e += 32)
             atomicAdd(&nmov[g.adjncy[e]], 1);
+    }
+    for (int64_t i = blockIdx.x; i < np; i += gridDim.x) {
+        const int64_t it = pieces[i];
+        const int64_t v = it >> 20;
+        const int64_t e0 = g.xadj[v] + (it & ((1 << 20) - 1)) * kScatChunk;
+        const int64_t e1 = min64(g.xadj[v + 1], e0 + kScatChunk);
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&nmov[g.adjncy[e]], 1);
     }
 }
 
@@ -179,7 +202,8 @@ __device__ __forceinline__ int64_t node_features(const DGraph &g, const int32_t 
     for (int i = 0; i < 6; i++) f[i] = 0.f;
     if (deg > 0) {
         const int32_t own = lab[v];
-        const int64_t wb = vb[v], wo = vo[v], wd = (int64_t)wdeg[v];
+        // unit edge weights (wdeg null): the weighted degree is the degree
+        const int64_t wb = vb[v], wo = vo[v], wd = wdeg ? (int64_t)wdeg[v] : deg;
         f[0] = bf16_round(log2_feature(1 + deg));
         f[1] = bf16_round(__fdiv_rn(__ll2float_rn(W[own]), __ll2float_rn(Lmax)));
         f[2] = bf16_round(__fdiv_rn(__ll2float_rn(wb - wo), __ll2float_rn(wd)));
@@ -257,7 +281,7 @@ void gate_init(Gate &gt, Scratch &sc) {
     const int64_t n = gt.g.n;
     cudaStream_t s = sc.stream();
     const int sms = dev_info().sms;
-    unsigned long long *wd = sc.zeros<unsigned long long>(n ? n : 1);
+    unsigned long long *wd = gt.unit ? nullptr : sc.zeros<unsigned long long>(n ? n : 1);
     gt.wdeg = (int64_t *)wd;
     gt.prev = sc.get<int32_t>(n ? n : 1);
     gt.moved = sc.zeros<uint8_t>(n ? n : 1);
@@ -266,10 +290,11 @@ void gate_init(Gate &gt, Scratch &sc) {
     gt.vo = sc.zeros<int32_t>(n ? n : 1);
     gt.nmov = sc.get<int32_t>(n ? n : 1);
     gt.movers = sc.get<int32_t>(n ? n : 1);
-    gt.nmovers = sc.get<int32_t>(1);
+    gt.pieces = sc.get<int64_t>(2 * (gt.g.nnz / kScatChunk) + 1);
+    gt.nmovers = sc.get<int32_t>(2);
     gt.visited = sc.zeros<unsigned long long>(2);
     gt.nfull = 0;
-    if (gt.g.nnz > 0) {
+    if (gt.g.nnz > 0 && !gt.unit) {
         k_row_sums<<<sms * 4, 256, 0, s>>>(gt.g, wd);
         LAUNCHED();
     }
@@ -285,11 +310,11 @@ bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
     const bool full =
         !gt.net || r == 0 || r % gt.full_every == gt.full_every - 1 || r == gt.rounds - 1;
     if (n > 0) {
-        CK(cudaMemsetAsync(gt.nmovers, 0, sizeof(int32_t), s));
-        k_moved<<<sms * 4, 256, 0, s>>>(n, gt.lab, gt.prev, gt.moved,
+        CK(cudaMemsetAsync(gt.nmovers, 0, 2 * sizeof(int32_t), s));
+        k_moved<<<sms * 4, 256, 0, s>>>(n, gt.g.xadj, gt.lab, gt.prev, gt.moved,
                                         (gt.trace_y && r > 0) ? gt.trace_y + (size_t)(r - 1) * n
                                                                : nullptr,
-                                        r == 0, gt.movers, gt.nmovers);
+                                        r == 0, gt.movers, gt.pieces, gt.nmovers);
         LAUNCHED();
     }
     float *x = gt.trace_x ? gt.trace_x + (size_t)r * n * 6 : nullptr;
@@ -302,7 +327,8 @@ bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
         // neighbours that moved in round r - 1, scattered from its movers
         CK(cudaMemsetAsync(gt.nmov, 0, n * sizeof(int32_t), s));
         if (gt.g.nnz > 0 && r > 0) {
-            k_scatter_moved<<<sms * 8, 256, 0, s>>>(gt.g, gt.movers, gt.nmovers, gt.nmov);
+            k_scatter_moved<<<sms * 8, 256, 0, s>>>(gt.g, gt.movers, gt.pieces, gt.nmovers,
+                                                    gt.nmov);
             LAUNCHED();
         }
         k_gate<<<sms * 4, 256, 0, s>>>(gt.g, gt.lab, gt.W, gt.Lmax, gt.moved,
@@ -318,9 +344,9 @@ bool gate_round(Gate &gt, int r, const uint8_t **active, cudaStream_t s) {
 void gate_finish(Gate &gt, int rounds_done, cudaStream_t s) {
     if (!gt.trace_y || rounds_done < 1 || gt.g.n == 0) return;
     const int sms = dev_info().sms;
-    k_moved<<<sms * 4, 256, 0, s>>>(gt.g.n, gt.lab, gt.prev, gt.moved,
+    k_moved<<<sms * 4, 256, 0, s>>>(gt.g.n, gt.g.xadj, gt.lab, gt.prev, gt.moved,
                                     gt.trace_y + (size_t)(rounds_done - 1) * gt.g.n, false,
-                                    nullptr, nullptr);
+                                    nullptr, nullptr, nullptr);
     LAUNCHED();
 }
 

@@ -23,13 +23,16 @@ struct Gate {
     int full_every, rounds;
     float *trace_x;         // [rounds][n][6] or null
     uint8_t *trace_y;       // [rounds][n] or null
+    bool unit;              // every edge weight is 1 (then wdeg stays null)
     int64_t *wdeg;          // static weighted degrees
     int32_t *prev;          // labels at the start of the previous round
     uint8_t *moved;         // moved in the previous round
     uint8_t *active;
     int32_t *vb, *vo;           // latest visit: weight to the best eligible other / own block
     int32_t *nmov;              // per round: moved neighbours
-    int32_t *movers, *nmovers;  // nodes that moved in the previous round
+    int32_t *movers, *nmovers;  // nodes that moved in the previous round (short rows;
+                                // nmovers[0]) and the pieces of long ones (nmovers[1])
+    int64_t *pieces;
     unsigned long long *visited;  // device counters: rows visited by gated or traced
                                   // rounds; [1] rows with neighbours
     int nfull = 0;                // full rounds without traces (host count): each
