@@ -232,8 +232,9 @@ __global__ void k_lpt_keys2(const RunDesc *rd, int64_t nruns, const int32_t *idx
 
 // One warp per run: its nodes in sorted order go to the lightest of its k
 // blocks (lowest id on ties).  Sequential by nature: block weights live in
-// shared memory, 32 upcoming nodes are prefetched per lane, and the argmin
-// is two warp reductions (weights fit 32 bits: c(V) <= INT32_MAX is checked).
+// registers (k <= 32, lane b holds block b) or shared memory, 32 upcoming
+// nodes are prefetched per lane, and the argmin is two warp reductions
+// (weights fit 32 bits: c(V) <= INT32_MAX is checked).
 __global__ void k_lpt_assign(const RunDesc *rd, int32_t k, const int32_t *order,
                              const int32_t *uc, int32_t *upart) {
     extern __shared__ unsigned bw[];
@@ -251,6 +252,21 @@ __global__ void k_lpt_assign(const RunDesc *rd, int32_t k, const int32_t *order,
             c = uc[u];
         }
         const int cnt = (int)min64(32, n - i0);
+        if (k <= 32) {
+            // k <= 32: lane b keeps block b's weight in a register
+            unsigned wb = lane < k ? bw[lane] : 0xffffffffu;
+            for (int j = 0; j < cnt; j++) {
+                const int32_t uj = __shfl_sync(0xffffffffu, u, j);
+                const int32_t cj = __shfl_sync(0xffffffffu, c, j);
+                const unsigned gw = __reduce_min_sync(0xffffffffu, wb);
+                const unsigned gb = __reduce_min_sync(0xffffffffu, wb == gw ? (unsigned)lane : 32u);
+                if (lane == (int)gb) wb += (unsigned)cj;
+                if (lane == 0) upart[uj] = (int32_t)(r * k + gb);
+            }
+            if (lane < k) bw[lane] = wb;
+            __syncwarp();
+            continue;
+        }
         for (int j = 0; j < cnt; j++) {
             const int32_t uj = __shfl_sync(0xffffffffu, u, j);
             const int32_t cj = __shfl_sync(0xffffffffu, c, j);

@@ -78,7 +78,9 @@ constexpr int kSegSmem = 6144;           // contested segments staged in shared 
 constexpr int kBigTile = 4096;           // longer segments: tiles spread over the grid
 constexpr int kDigit = 11;               // radix-select digit width
 constexpr int kBins = 1 << kDigit;
-constexpr int kUnroll = 4;               // entries in flight per thread
+constexpr int kBigUnroll = 4;            // entries in flight per thread: CTA-table rows,
+constexpr int kMedUnroll = 4;            //   warp rows,
+constexpr int kHugeUnroll = 4;           //   cluster rows
 constexpr int kAggW = 1024;              // label weights aggregated in shared memory up to this
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kEmpty32 = 0xffffffffu;
@@ -662,22 +664,22 @@ __device__ void process_large(const LPArgs &a, PropSm<MODE, RS> &sm, int k, cons
         const int64_t rs = sm.nd.rs[0];
         const int32_t cpv = sm.nd.cpv[0];
         // every thread runs the same number of steps (warp-wide appends)
-        for (int64_t ebase = e0; ebase < e1; ebase += kUnroll * NT) {
+        for (int64_t ebase = e0; ebase < e1; ebase += kBigUnroll * NT) {
             const int64_t eb = ebase + threadIdx.x;
-            int32_t u[kUnroll], w[kUnroll], L[kUnroll];
+            int32_t u[kBigUnroll], w[kBigUnroll], L[kBigUnroll];
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kBigUnroll; j++) {
                 const int64_t e = eb + j * NT;
                 u[j] = e < e1 ? __ldg(&a.g.adjncy[rs + e]) : -1;
                 w[j] = e < e1 ? __ldg(&a.g.adjwgt[rs + e]) : 0;
             }
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kBigUnroll; j++) {
                 if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != cpv) u[j] = -1;
                 L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : 0;
             }
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kBigUnroll; j++) {
                 if constexpr (DENSE) {
                     if (u[j] >= 0) atomicAdd(&sm.t.acc[L[j]], w[j]);
                 } else {
@@ -1386,21 +1388,21 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
     const int64_t Wown = MODE == kCluster ? 0 : (DENSE ? Wsm[own] : a.W[own]);
     const uint64_t h = nhash(a, v);
     const int32_t lb = lbase(a, v);
-    for (int32_t e0 = 0; e0 < deg; e0 += 32 * kUnroll) {
-        int32_t u[kUnroll], w[kUnroll], L[kUnroll];
+    for (int32_t e0 = 0; e0 < deg; e0 += 32 * kMedUnroll) {
+        int32_t u[kMedUnroll], w[kMedUnroll], L[kMedUnroll];
 #pragma unroll
-        for (int j = 0; j < kUnroll; j++) {
+        for (int j = 0; j < kMedUnroll; j++) {
             const int32_t e = e0 + j * 32 + lane;
             u[j] = e < deg ? __ldg(&a.g.adjncy[b + e]) : -1;
             w[j] = e < deg ? __ldg(&a.g.adjwgt[b + e]) : 0;
         }
 #pragma unroll
-        for (int j = 0; j < kUnroll; j++) {
+        for (int j = 0; j < kMedUnroll; j++) {
             if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != cpv) u[j] = -1;
             L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : 0;
         }
 #pragma unroll
-        for (int j = 0; j < kUnroll; j++) {
+        for (int j = 0; j < kMedUnroll; j++) {
             if constexpr (DENSE) {
                 if (u[j] >= 0) atomicAdd(&dacc[L[j]], w[j]);
             } else {
@@ -2471,21 +2473,21 @@ __global__ void __cluster_dims__(kHugeCS, 1, 1) __launch_bounds__(kThreads)
         const int64_t e0 = deg * rank / kHugeCS, e1 = deg * (rank + 1) / kHugeCS;
         const int64_t span = e1 - e0;
         const int64_t span_r = (span + 31) & ~31ll;  // whole warps for match_any
-        for (int64_t eb = threadIdx.x; eb < span_r; eb += kUnroll * kThreads) {
-            int32_t u[kUnroll], w[kUnroll], L[kUnroll];
+        for (int64_t eb = threadIdx.x; eb < span_r; eb += kHugeUnroll * kThreads) {
+            int32_t u[kHugeUnroll], w[kHugeUnroll], L[kHugeUnroll];
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kHugeUnroll; j++) {
                 const int64_t e = eb + j * kThreads;
                 u[j] = e < span ? __ldg(&a.g.adjncy[rs + e0 + e]) : -1;
                 w[j] = e < span ? __ldg(&a.g.adjwgt[rs + e0 + e]) : 0;
             }
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kHugeUnroll; j++) {
                 if (u[j] >= 0 && MODE == kCluster && a.cp && __ldg(&a.cp[u[j]]) != cpv) u[j] = -1;
                 L[j] = u[j] >= 0 ? __ldg(&a.lab[u[j]]) : -1;
             }
 #pragma unroll
-            for (int j = 0; j < kUnroll; j++) {
+            for (int j = 0; j < kHugeUnroll; j++) {
                 if (eb + j * kThreads >= span_r) break;  // warp-uniform
                 // merge equal labels within the warp first
                 const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)L[j]);
