@@ -560,35 +560,54 @@ __device__ __forceinline__ void select_best(const LPArgs &a, const uint32_t *key
     __syncthreads();
 }
 
+// Dense selection on one warp over k <= 64 block sums (lane b holds w0 for
+// block b and w1 for block b + 32): the largest eligible omega M first;
+// only for a row that proposes (M beats the own omega, or the block is
+// overloaded) the tie hashes of the blocks at M, the smallest (tie, block)
+// winning.  *best = M << 32 | ~tie, or M << 32 alone for a row that does not
+// propose; *bl the block (0x7fffffff if none).
+__device__ __forceinline__ void dense_pick(const LPArgs &a, const int64_t *Wsm, int32_t w0,
+                                           int32_t w1, int32_t own, int32_t c, uint64_t h,
+                                           int32_t lb, int32_t ownw, bool ovl,
+                                           unsigned long long *best, int32_t *bl) {
+    const int lane = threadIdx.x & 31;
+    const bool e0 = w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane);
+    const bool e1 = w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32);
+    const uint32_t M =
+        __reduce_max_sync(0xffffffffu, max(e0 ? (uint32_t)w0 : 0u, e1 ? (uint32_t)w1 : 0u));
+    *best = (unsigned long long)M << 32;
+    *bl = 0x7fffffff;
+    if (M > 0 && ((int32_t)M > ownw || ovl)) {  // the same in every lane
+        const unsigned long long x0 =
+            e0 && (uint32_t)w0 == M ? ((unsigned long long)tie_of(h, lane - lb) << 32) | lane : ~0ull;
+        const unsigned long long x1 =
+            e1 && (uint32_t)w1 == M
+                ? ((unsigned long long)tie_of(h, lane + 32 - lb) << 32) | (lane + 32)
+                : ~0ull;
+        const unsigned long long x = x0 < x1 ? x0 : x1;
+        const uint32_t tmin = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32));
+        const uint32_t b = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32) == tmin ? (uint32_t)x
+                                                                                     : 0xffffffffu);
+        *best |= (uint32_t)~tmin;
+        *bl = (int32_t)b;
+    }
+}
+
 // Dense variant for node slot s with blocks 0..k-1 in acc[0..k): one warp;
 // clears the k-array; result in nd.best / nd.bestL / nd.ownw.
 __device__ __forceinline__ void select_dense_warp(const LPArgs &a, const int64_t *Wsm,
                                                   int32_t *acc, int k, NodeSm &nd, int s) {
     const int lane = threadIdx.x & 31;
-    const int32_t own = nd.own[s], c = nd.c[s];
-    const uint64_t h = nd.h[s];
-    const int32_t lb = nd.lb[s];
+    const int32_t own = nd.own[s];
     int32_t w0 = lane < k ? acc[lane] : 0;
     int32_t w1 = lane + 32 < k ? acc[lane + 32] : 0;
     __syncwarp();
     if (lane < k) acc[lane] = 0;
     if (lane + 32 < k) acc[lane + 32] = 0;
-    int32_t ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
-    unsigned long long ck0 = 0, ck1 = 0;
-    if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane - lb);
-    if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32))
-        ck1 = cand_key(w1, h, lane + 32 - lb);
-    unsigned long long m = ck0 > ck1 ? ck0 : ck1;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        unsigned long long o = __shfl_xor_sync(0xffffffffu, m, d);
-        m = o > m ? o : m;
-    }
-    int32_t L = 0x7fffffff;
-    if (m != 0 && ck0 == m) L = lane;
-    else if (m != 0 && ck1 == m) L = lane + 32;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) L = min(L, __shfl_xor_sync(0xffffffffu, L, d));
+    const int32_t ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
+    unsigned long long m;
+    int32_t L;
+    dense_pick(a, Wsm, w0, w1, own, nd.c[s], nd.h[s], nd.lb[s], ownw, nd.ovl[s] != 0, &m, &L);
     if (lane == 0) {
         nd.best[s] = m;
         nd.bestL[s] = L;
@@ -1429,18 +1448,7 @@ __device__ __forceinline__ void medium_row(const LPArgs &a, const int64_t *Wsm, 
         if (lane < k) dacc[lane] = 0;
         if (lane + 32 < k) dacc[lane + 32] = 0;
         ownw = __shfl_sync(0xffffffffu, (own < 32) ? w0 : w1, own & 31);
-        unsigned long long ck0 = 0, ck1 = 0;
-        if (w0 > 0 && lane != own && Wsm[lane] + c <= bnd(a, lane)) ck0 = cand_key(w0, h, lane - lb);
-        if (w1 > 0 && lane + 32 != own && Wsm[lane + 32] + c <= bnd(a, lane + 32))
-            ck1 = cand_key(w1, h, lane + 32 - lb);
-        best = ck0 > ck1 ? ck0 : ck1;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
-            best = o > best ? o : best;
-        }
-        if (best != 0 && ck0 == best) bl = lane;
-        else if (best != 0 && ck1 == best) bl = lane + 32;
+        dense_pick(a, Wsm, w0, w1, own, c, h, lb, ownw, Wown > bnd(a, own), &best, &bl);
     } else {
         // the largest eligible omega and the own omega first; tie hashes
         // only when the row proposes, and only for the labels reaching that
