@@ -756,7 +756,7 @@ def main():
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     tr = stored_traffic()
     roofline = {"bound": "hbm",
-                "kernel": "propose step (k_propose_small, k_propose, k_propose_huge per sub-round)",
+                "kernel": "propose step (k_propose_small, k_propose_pipe, k_propose, k_propose_huge, hub kernels per sub-round)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": (tr["dram_per_algorithmic_byte"] * per_launch_bytes) if tr else None,
