@@ -383,7 +383,7 @@ int sclap_set_launch_mode(int mode);
  * They route rows and contested target segments to kernel paths and change
  * only the speed: every setting gives the same results (each path computes
  * the same selection and arbitration).  The paper has no counterpart.
- * Defaults 32 / 256 / 4096 / 6144; `autotune.py` of the Python package picks
+ * Defaults 32 / 256 / 2048 / 6144; `autotune.py` of the Python package picks
  * them per device and workload by timing candidate sets. */
 typedef struct {
     int32_t small_max;  /* rows of <= small_max entries: groups of lanes of one

@@ -21,14 +21,14 @@ from . import get_tuning, set_tuning, set_validation, sclap_cluster, sclap_refin
 
 # (small_max, med_max, mid_max, seg_smem); the first is the built-in default
 CANDIDATES = [
-    (32, 256, 4096, 6144),
-    (16, 256, 4096, 6144),
-    (8, 256, 4096, 6144),
-    (32, 128, 4096, 6144),
     (32, 256, 2048, 6144),
     (16, 256, 2048, 6144),
+    (8, 256, 2048, 6144),
+    (32, 128, 2048, 6144),
     (32, 256, 1024, 6144),
-    (32, 256, 4096, 2048),
+    (32, 256, 4096, 6144),
+    (16, 256, 4096, 6144),
+    (32, 256, 2048, 2048),
     (16, 128, 1024, 4096),
 ]
 
