@@ -733,7 +733,10 @@ def main():
     h2d = sum(v.numel() * v.element_size() for v in gh.values())
     d2h = ph.numel() * ph.element_size()
     if not args.no_e2e:
-        S.partition_multilevel(gh, params, part_out=ph)
+        # warm-up calls on the host buffers: the first two calls after the
+        # pinned buffers are made carry one-time costs (about 10 ms)
+        for _ in range(max(2, min(args.warmup, 3))):
+            S.partition_multilevel(gh, params, part_out=ph)
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
