@@ -4,34 +4,37 @@
 // refinement form adds the overloaded-block rule (Sec. III.A).
 //
 // Per round r:
-//   k_build_wl    colour = (h(v,r) >> 32) mod S.  Nodes with 1..kMedDeg
-//                 neighbours go to bucket 5*colour + class (degree <= 4, 8,
-//                 16, 32, 33..kMedDeg); larger rows go to per-colour lists:
-//                 257..kMidDeg in four length classes, kChunk-entry pieces of
-//                 longer rows (and rows up to kChunk when the tuning lowers
-//                 the pipelined bound), kChunk+1..kHugeDeg in the hash modes.  The
-//                 learned gate (learned.cu) can leave nodes out of a round.
+//   k_build_wl    colour = (h(v,r) >> 32) mod S (or the degree-ordered
+//                 colours).  Nodes with 1..med_max neighbours go to bucket
+//                 5*colour + class (degree <= 4, 8, 16, small_max, med_max);
+//                 rows up to the pipelined bound (mid_max) to per-colour
+//                 lists of four length classes; longer rows as kChunk-entry
+//                 pieces (a single piece up to kChunk), kChunk+1..kHugeDeg in
+//                 the hash modes to the cluster list.  The learned gate
+//                 (learned.cu) can leave nodes out of a round.
 // Per sub-round j, the propose step runs on three streams:
 //   k_propose_small  small rows: one thread per node for rows of <= 4, 8
-//                 and 16 entries (labels merged in registers); rows of
-//                 17..32 entries on one warp, __match_any_sync on the label
-//                 and __reduce_add_sync give omega(v, L); medium rows: one warp per
-//                 row with a warp-private linear-probing table (the paper's
-//                 Sec. IV.A choice of linear probing) or a k-array.
-//   k_propose_pipe<MODE, PipeShape>  rows of kMedDeg+1..kMidDeg entries in
-//                 four length classes: one CTA per row, software-pipelined
+//                 and 16 entries (labels merged in registers); rows up to
+//                 small_max on lane groups (__match_any_sync on the label,
+//                 __reduce_add_sync gives omega(v, L)); rows up to med_max
+//                 one warp each with a warp-private linear-probing table (the
+//                 paper's Sec. IV.A choice of linear probing) or a k-array.
+//   k_propose_pipe<MODE, PipeShape>  rows of med_max+1..2048 entries in
+//                 three length classes: one CTA per row, software-pipelined
 //                 over the CTA's rows, with a shared table of packed
 //                 (label, omega) words sized to the row.
+//   k_propose_stage  rows of 2049..4096 entries when the pipelined bound is
+//                 4096: rows staged in shared memory three deep by cp.async.
 //   k_propose<MODE, BigRows>  rows above the pipelined bound up to kChunk
 //                 entries, one CTA per row with a table of 32-bit labels;
-//                 pieces of longer rows
-//                 merge into a global table (hash) or k-array (dense) and
-//                 are finished by k_hub_cand / k_hub_tie / k_hub_emit or the
-//                 last piece.
+//                 pieces of longer rows merge into a global table (hash) or
+//                 k-array (dense) and are finished by k_hub_cand / k_hub_tie
+//                 / k_hub_emit or the last piece.
 //   k_propose_huge  hash modes, rows up to kHugeDeg: an 8-CTA cluster per
 //                 row, its table spread over the CTAs' shared memory.
 //   The best eligible label maximises (omega << 32 | ~tie); exact ties on
-//   that key go to the smallest label.
+//   that key go to the smallest label.  Every path finds the largest
+//   eligible omega first and hashes ties only for a row that proposes.
 // Then arbitration:
 //   k_src         refinement only: departures from overloaded blocks.
 //   k_classify    uncontested targets (sum of proposed weight <= capacity)
