@@ -403,3 +403,44 @@ def test_rgg_multilevel_matches_oracle():
     got, st = S.partition_multilevel(dev(g), prm)
     want, ws = oracle.multilevel(gn, dict(prm))
     assert st == ws and np.array_equal(got.cpu().numpy(), want)
+
+
+def _hub_graph():
+    # hubs whose rows take each long-row path of the hash modes: one CTA table
+    # (3,000), the thread-block cluster (9,000) and the pieces merged in
+    # global tables (40,000 and 80,000), over a weighted random graph
+    n = 100_000
+    base = I.random_graph(n, 300_000, seed=21, max_w=7, max_c=4)
+    src = torch.repeat_interleave(torch.arange(n), base["xadj"][1:] - base["xadj"][:-1])
+    dst = base["adjncy"].to(torch.int64)
+    up = src < dst
+    us, vs = [src[up]], [dst[up]]
+    for h, cnt in ((11, 3000), (22, 9000), (33, 40000), (44, 80000)):
+        leaves = (torch.arange(cnt) * 7919 + 101 + h) % n
+        leaves = leaves[leaves != h]
+        us.append(torch.full((leaves.numel(),), h, dtype=torch.int64))
+        vs.append(leaves)
+    u, v = torch.cat(us), torch.cat(vs)
+    w = I.rand_below(9, 3, u * n + v, 6) + 1
+    c = I.rand_below(9, 4, torch.arange(n), 3) + 1
+    return I.csr_from_edges(n, u, v, w, c.to(torch.int32))
+
+
+def test_long_rows_of_every_class_match_oracle():
+    g = _hub_graph()
+    gn = I.to_numpy(g)
+    deg = np.diff(gn["xadj"])
+    assert deg.max() > 65536 and ((deg > 16384) & (deg <= 65536)).any()
+    cV = int(gn["vwgt"].sum())
+    U = max(int(gn["vwgt"].max()), cV // 400)
+    want, rd_w = oracle.cluster(gn, U, 3, 4, 7)
+    got, rd_g = S.sclap_cluster(dev(g), U, 3, 4, 7)
+    assert rd_g == rd_w
+    assert np.array_equal(got.cpu().numpy(), want)
+    k = 100  # above the dense bound: the hash refinement path
+    p0 = I.rand_below(3, 8, torch.arange(gn["vwgt"].size), k).to(torch.int32)
+    want_p, cut_w, bw_w, rd_w = oracle.refine(gn, k, 0.03, 4, 4, 7, p0.numpy())
+    got_p, cut_g, bw_g, rd_g = S.sclap_refine(dev(g), k, 0.03, 4, 4, 7, p0.cuda())
+    assert rd_g == rd_w
+    assert np.array_equal(got_p.cpu().numpy(), want_p)
+    assert cut_g == cut_w and np.array_equal(bw_g.numpy(), bw_w)
