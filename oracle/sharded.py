@@ -3,10 +3,10 @@ run as torch.distributed ranks on CPU (gloo), one process per rank.
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: it shows that the
 sharded design computes exactly what the single-rank oracle computes, and it is
-run by ``tests/test_sharded.py`` with 2 and 4 ranks.  Every box of this build
-has one GPU, so the product runs replicas only; this module is the host-side
-protocol a multi-GPU product would follow, with each rank's local arithmetic
-written here in numpy.
+run by ``tests/test_sharded.py`` with 2 and 4 ranks.  The product is
+single-GPU (several GPUs run independent replicas); this module is the
+host-side protocol a multi-GPU product would follow, with each rank's local
+arithmetic written here in numpy.
 
 Layout (Sec. IV.A): rank r owns the contiguous node range [lo_r, hi_r) (1-D
 partition, n/P nodes each), the rows of its nodes, and halo copies of the

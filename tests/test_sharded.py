@@ -2,7 +2,7 @@
 target owners, owner arbitration, exscan contraction; Sec. IV.A-C) on 2 and 4
 simulated ranks (gloo, CPU processes) gives bit for bit what the single-rank
 oracle gives: clustering labels, refinement partitions, coarse graphs and
-projections.  Unmeasured on hardware: every box has one GPU."""
+projections.  Not measured on GPUs: the product runs one GPU per process."""
 import os
 import socket
 
