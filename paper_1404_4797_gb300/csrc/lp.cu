@@ -37,14 +37,15 @@
 //   eligible omega first and hashes ties only for a row that proposes.
 // Then arbitration:
 //   k_src         refinement only: departures from overloaded blocks.
-//   k_classify    uncontested targets (sum of proposed weight <= capacity)
-//                 are applied at once; contested targets get a segment.
-//   k_scatter     contested proposals are written to their target's segment.
-//   k_arbitrate   cooperative launch; per contested target a weighted radix
+//   k_arbitrate   one cooperative launch (every CTA resident) with grid
+//                 barriers between its phases: classify (uncontested targets,
+//                 whose proposed weight fits the capacity, are applied at
+//                 once; contested targets get a segment), scatter contested
+//                 proposals into their segments and clear the per-target
+//                 accumulators, then per contested target a weighted radix
 //                 select of the first key in (gain desc, id asc) order whose
 //                 inclusive prefix exceeds the capacity (a warp, a CTA, or
 //                 the whole grid by segment size); admitted moves are applied.
-//   k_reset_targets clears the per-target accumulators.
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
 
@@ -110,6 +111,25 @@ struct Seg {
     int32_t T, cnt;
     int64_t base, thr;  // thr = capacity + 1
 };
+
+// L2-coherent loads of segment state written by other CTAs of the same launch.
+__device__ __forceinline__ SegEntry ldcg_entry(const SegEntry *p) {
+    const int4 v = __ldcg(reinterpret_cast<const int4 *>(p));
+    SegEntry e;
+    e.key = ((uint64_t)(uint32_t)v.y << 32) | (uint32_t)v.x;
+    e.c = v.z;
+    e.own = v.w;
+    return e;
+}
+__device__ __forceinline__ Seg ldcg_seg(const Seg *p) {
+    Seg sg;
+    sg.T = __ldcg(&p->T);
+    sg.cnt = __ldcg(&p->cnt);
+    sg.base = __ldcg(&p->base);
+    sg.thr = __ldcg(&p->thr);
+    return sg;
+}
+static_assert(sizeof(SegEntry) == 16 && alignof(SegEntry) == 8, "SegEntry as one 16-byte load");
 
 struct Ctr {
     int32_t nprop, nseg;
@@ -2027,7 +2047,7 @@ __device__ __forceinline__ void stage_segment(const SegEntry *ent, int cnt, uint
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int i = base + j * blockDim.x;
-            if (i < cnt) e[j] = ent[i];
+            if (i < cnt) e[j] = ldcg_entry(&ent[i]);
         }
 #pragma unroll
         for (int j = 0; j < 8; j++) {
@@ -2060,7 +2080,7 @@ __device__ __forceinline__ int64_t admit_segment(const LPArgs &a, WDelta &wd, co
         for (int j = 0; j < 8; j++) {
             const int i = base + j * blockDim.x;
             adm[j] = i < cnt && (keys[i] < K || c[i] == 0);
-            own[j] = adm[j] ? ent[i].own : -1;
+            own[j] = adm[j] ? __ldcg(&ent[i].own) : -1;
         }
 #pragma unroll
         for (int j = 0; j < 8; j++) {
@@ -2137,60 +2157,6 @@ __global__ void __launch_bounds__(kThreads) k_src(LPArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_classify(LPArgs a) {
-    if (stopped(a)) return;
-    __shared__ WDelta wd;
-    wd_init(wd, a.nW);
-    const int nprop = a.ctr->nprop;
-    int64_t moved = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nprop;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const Prop p = a.props[i];
-        if (p.slot < 0) continue;
-        const int64_t cap = bnd(a, p.T) - p.wT;
-        if (a.tsum[p.T] <= cap) {
-            apply_agg(a, wd, p.v, p.T, p.own, p.c);
-            moved++;
-        } else if (p.slot == 0) {
-            const int32_t cnt = a.tcnt[p.T];
-            const int si = atomicAdd(&a.ctr->nseg, 1);
-            const int64_t base = (int64_t)atomicAdd((unsigned long long *)&a.ctr->segtotal,
-                                                    (unsigned long long)cnt);
-            a.tbase[p.T] = base;
-            a.segs[si] = Seg{p.T, cnt, base, cap + 1};
-            if (cnt > a.t.seg_smem) {
-                const int nt = (cnt + kBigTile - 1) / kBigTile;
-                const int bi = atomicAdd(&a.ctr->nbig, 1);
-                const int t0 = atomicAdd(&a.ctr->bigtiles, nt);
-                if (bi >= a.maxbig || t0 + nt > a.maxtiles) {
-                    a.ctr->err = kErrBig;  // cannot happen: capacities bound the totals
-                } else {
-                    a.big[bi] = BigSeg{si, nt, t0, 0, ~0ull, 0ull, 0ull, 0ll, 0, 0u};
-                    for (int t = 0; t < nt; t++) a.tileseg[t0 + t] = bi;
-                }
-            }
-        }
-    }
-    wd_flush(a, wd);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) moved += __shfl_down_sync(0xffffffffu, moved, d);
-    if ((threadIdx.x & 31) == 0 && moved)
-        atomicAdd((unsigned long long *)a.moves, (unsigned long long)moved);
-}
-
-__global__ void __launch_bounds__(kThreads) k_scatter(LPArgs a) {
-    if (stopped(a)) return;
-    const int nprop = a.ctr->nprop;
-    if (a.ctr->nseg == 0) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nprop;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const Prop p = a.props[i];
-        if (p.slot < 0) continue;
-        if (a.tsum[p.T] <= bnd(a, p.T) - p.wT) continue;
-        a.segbuf[a.tbase[p.T] + p.slot] = SegEntry{seg_key(p.gain, p.v), p.c, p.own};
-    }
-}
-
 // Grid-wide barrier of a cooperative launch.  The wait is bounded: a CTA
 // that waits longer than `limit` SM clock cycles (or sees the error flag
 // raised) sets kErrBarrier and goes on; the host then reports the failure.
@@ -2251,12 +2217,12 @@ struct BigTile {
 __device__ __forceinline__ BigTile big_tile(const LPArgs &a, int t, int nbig, BigTile *s_bt) {
     if (threadIdx.x == 0) {
         BigTile bt{};
-        const int32_t bi = a.tileseg[t];
+        const int32_t bi = __ldcg(&a.tileseg[t]);
         if (bi >= 0 && bi < nbig) {
             const BigSeg *b = &a.big[bi];
             bt.bi = bi;
-            bt.sg = a.segs[b->si];
-            bt.i0 = (int64_t)(t - b->t0) * kBigTile;
+            bt.sg = ldcg_seg(&a.segs[__ldcg(&b->si)]);
+            bt.i0 = (int64_t)(t - __ldcg(&b->t0)) * kBigTile;
             const int64_t rest = bt.sg.cnt - bt.i0;
             bt.len = (int)(rest < kBigTile ? rest : kBigTile);
             bt.kmin = __ldcg(&b->kmin);
@@ -2299,7 +2265,7 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
             for (int j = 0; j < 8; j++) {
                 const int i = base + j * blockDim.x;
                 e[j].c = 0;
-                if (i < bt.len) e[j] = ent[i];
+                if (i < bt.len) e[j] = ldcg_entry(&ent[i]);
             }
 #pragma unroll
             for (int j = 0; j < 8; j++) {
@@ -2448,24 +2414,78 @@ __device__ void arbitrate_big(const LPArgs &a, ArbSm &sm, int nbig, int ntiles, 
 
 // Launched cooperatively (all CTAs resident): segments of <= 32 entries take
 // one warp, up to kSegSmem one CTA, longer ones the whole grid.
+// The whole settle step of a sub-round in one cooperative launch (every CTA
+// resident): classify the proposals (uncontested targets applied, contested
+// ones get a segment), grid barrier, scatter contested proposals into their
+// segments and clear the per-target accumulators, grid barrier, then admit
+// per segment.  State that other CTAs wrote in this launch is read with
+// L2-coherent loads.
 __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
     if (stopped(a)) return;  // the same in every CTA, before any grid barrier
     extern __shared__ __align__(16) unsigned char smraw[];
     ArbSm &sm = *reinterpret_cast<ArbSm *>(smraw);
     wd_init(sm.wd, a.nW);
-    const int nseg = a.ctr->nseg;
     const int lane = threadIdx.x & 31;
     int64_t moved = 0;
+    const int nprop = __ldcg(&a.ctr->nprop);
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    // classify
+    for (int64_t i = gtid; i < nprop; i += gthreads) {
+        const Prop p = a.props[i];
+        if (p.slot < 0) continue;
+        const int64_t cap = bnd(a, p.T) - p.wT;
+        if (a.tsum[p.T] <= cap) {
+            apply_agg(a, sm.wd, p.v, p.T, p.own, p.c);
+            moved++;
+        } else if (p.slot == 0) {
+            const int32_t cnt = a.tcnt[p.T];
+            const int si = atomicAdd(&a.ctr->nseg, 1);
+            const int64_t base = (int64_t)atomicAdd((unsigned long long *)&a.ctr->segtotal,
+                                                    (unsigned long long)cnt);
+            a.tbase[p.T] = base;
+            a.segs[si] = Seg{p.T, cnt, base, cap + 1};
+            if (cnt > a.t.seg_smem) {
+                const int nt = (cnt + kBigTile - 1) / kBigTile;
+                const int bi = atomicAdd(&a.ctr->nbig, 1);
+                const int t0 = atomicAdd(&a.ctr->bigtiles, nt);
+                if (bi >= a.maxbig || t0 + nt > a.maxtiles) {
+                    atomicOr(&a.ctr->err, kErrBig);  // cannot happen: capacities bound the totals
+                } else {
+                    a.big[bi] = BigSeg{si, nt, t0, 0, ~0ull, 0ull, 0ull, 0ll, 0, 0u};
+                    for (int t = 0; t < nt; t++) a.tileseg[t0 + t] = bi;
+                }
+            }
+        }
+    }
+    grid_barrier(a.bar, &a.ctr->err, a.bar_cycles);
+    const int nseg = __ldcg(&a.ctr->nseg);
+    // scatter contested proposals; then nothing reads the per-target sums
+    if (nseg > 0) {
+        for (int64_t i = gtid; i < nprop; i += gthreads) {
+            const Prop p = a.props[i];
+            if (p.slot < 0) continue;
+            if (a.tsum[p.T] <= bnd(a, p.T) - p.wT) continue;
+            a.segbuf[__ldcg(&a.tbase[p.T]) + p.slot] = SegEntry{seg_key(p.gain, p.v), p.c, p.own};
+        }
+    }
+    grid_barrier(a.bar, &a.ctr->err, a.bar_cycles);
+    for (int64_t i = gtid; i < nprop; i += gthreads) {
+        const Prop p = a.props[i];
+        a.tsum[p.T] = 0;
+        a.tcnt[p.T] = 0;
+        if (a.ssum) a.ssum[p.own] = 0;
+    }
     // small segments: one warp each, exact prefix by brute force over <= 32 lanes
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int si = gwarp; si < nseg; si += nwarps) {
-        const Seg sg = a.segs[si];
+        const Seg sg = ldcg_seg(&a.segs[si]);
         if (sg.cnt > 32) continue;
         uint64_t key = ~0ull;
         int32_t c = 0, own = 0;
         if (lane < sg.cnt) {
-            const SegEntry e = a.segbuf[sg.base + lane];
+            const SegEntry e = ldcg_entry(&a.segbuf[sg.base + lane]);
             key = e.key;
             c = e.c;
             own = e.own;
@@ -2483,7 +2503,7 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
     }
     // medium segments: one CTA each, staged in shared memory
     for (int si = blockIdx.x; si < nseg; si += gridDim.x) {
-        const Seg sg = a.segs[si];
+        const Seg sg = ldcg_seg(&a.segs[si]);
         if (sg.cnt <= 32 || sg.cnt > a.t.seg_smem) continue;
         const SegEntry *ent = a.segbuf + sg.base;
         stage_segment(ent, sg.cnt, sm.keys, sm.c);
@@ -2501,8 +2521,8 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
         __syncthreads();
     }
     // long segments: the whole grid (the same branch in every CTA)
-    const int nbig = a.ctr->nbig, ntiles = a.ctr->bigtiles;
-    if (nbig > 0 && !(a.ctr->err & kErrBig) && nbig <= a.maxbig && ntiles <= a.maxtiles) {
+    const int nbig = __ldcg(&a.ctr->nbig), ntiles = __ldcg(&a.ctr->bigtiles);
+    if (nbig > 0 && !(__ldcg(&a.ctr->err) & kErrBig) && nbig <= a.maxbig && ntiles <= a.maxtiles) {
         __syncthreads();
         arbitrate_big(a, sm, nbig, ntiles, moved);
     }
@@ -2510,19 +2530,6 @@ __global__ void __launch_bounds__(kThreads) k_arbitrate(LPArgs a) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) moved += __shfl_down_sync(0xffffffffu, moved, d);
     if (lane == 0 && moved) atomicAdd((unsigned long long *)a.moves, (unsigned long long)moved);
-}
-
-// Clears the per-target (and per-source) accumulators touched this sub-round.
-__global__ void __launch_bounds__(kThreads) k_reset_targets(LPArgs a) {
-    if (stopped(a)) return;
-    const int nprop = a.ctr->nprop;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nprop;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const Prop p = a.props[i];
-        a.tsum[p.T] = 0;
-        a.tcnt[p.T] = 0;
-        if (a.ssum) a.ssum[p.own] = 0;
-    }
 }
 
 // ---------------------------------------------------------------- multi-piece rows (hash)
@@ -3460,10 +3467,6 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 k_src<<<(unsigned)(cfg.nW + grid_small), kThreads, 0, ms>>>(a);
                 LAUNCHED();
             }
-            k_classify<<<grid_small, kThreads, 0, ms>>>(a);
-            LAUNCHED();
-            k_scatter<<<grid_small, kThreads, 0, ms>>>(a);
-            LAUNCHED();
             {
                 // cooperative: every CTA resident (the grid barrier needs it),
                 // also as a node of a captured graph
@@ -3479,8 +3482,6 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
                 lc.numAttrs = 1;
                 CK(cudaLaunchKernelEx(&lc, k_arbitrate, a));
             }
-            LAUNCHED();
-            k_reset_targets<<<grid_small, kThreads, 0, ms>>>(a);
             LAUNCHED();
         }
         k_round_end<<<1, 1, 0, ms>>>(d_moves + r, ctr, S, d_state, r, full ? 1 : 0);
