@@ -140,6 +140,8 @@ struct Ctr {
     int32_t huge_next;        // next row of the cluster path
 };
 
+static_assert(sizeof(Ctr) % sizeof(int32_t) == 0, "Ctr cleared as int32 words");
+
 constexpr int32_t kErrTable = 1;
 constexpr int32_t kErrBarrier = 2;
 constexpr int32_t kErrBig = 4;
@@ -3090,17 +3092,27 @@ static RowGrids row_grids(int sms) {
 
 // Rows above kMedDeg: the pipelined kernels of the two shorter classes and
 // then the pieces on stream s, the two longer pipelined classes on s2.
+// Classes that the tuning's pipelined bound leaves empty are not launched.
 template <int MODE>
 static void launch_rows(const LPArgs &a, int k, const RowGrids &rg, cudaStream_t s,
                         cudaStream_t s2) {
-    k_propose_stage<MODE><<<rg.p[3], kStNT, sizeof(StageSm<MODE>), s2>>>(a, k);
-    LAUNCHED();
-    k_propose_pipe<MODE, PipeC><<<rg.p[2], PipeC::kNT, sizeof(PipeSm<MODE, PipeC>), s2>>>(a, k, 2);
-    LAUNCHED();
+    const int mid = a.t.mid_max;
+    if (mid > 2048) {
+        k_propose_stage<MODE><<<rg.p[3], kStNT, sizeof(StageSm<MODE>), s2>>>(a, k);
+        LAUNCHED();
+    }
+    if (mid > 1024) {
+        k_propose_pipe<MODE, PipeC>
+            <<<rg.p[2], PipeC::kNT, sizeof(PipeSm<MODE, PipeC>), s2>>>(a, k, 2);
+        LAUNCHED();
+    }
     k_propose_pipe<MODE, PipeA><<<rg.p[0], PipeA::kNT, sizeof(PipeSm<MODE, PipeA>), s>>>(a, k, 0);
     LAUNCHED();
-    k_propose_pipe<MODE, PipeB><<<rg.p[1], PipeB::kNT, sizeof(PipeSm<MODE, PipeB>), s>>>(a, k, 1);
-    LAUNCHED();
+    if (mid > 512) {
+        k_propose_pipe<MODE, PipeB>
+            <<<rg.p[1], PipeB::kNT, sizeof(PipeSm<MODE, PipeB>), s>>>(a, k, 1);
+        LAUNCHED();
+    }
     k_propose<MODE, BigRows><<<rg.big, BigRows::kNT, sizeof(PropSm<MODE, BigRows>), s>>>(a, k);
     LAUNCHED();
 }
@@ -3127,14 +3139,24 @@ __global__ void k_degree_colours(int64_t n, int S, const int32_t *order, int32_t
 
 // End of round r: the errors of its sub-rounds are kept, the rounds done
 // counted, and the run stops after a full round without moves.
-__global__ void k_round_end(const int64_t *moves_r, const Ctr *ctr, int S, int32_t *st, int r,
-                            int full) {
+// The counters of the next round (worklist lengths, sub-round counters) are
+// cleared here, after this round's error flags are read.
+__global__ void k_round_end(const int64_t *moves_r, Ctr *ctr, int S, int32_t *st, int r,
+                            int full, int32_t *wl_cnt, int n_wl) {
     if (st[0]) return;
-    int32_t err = 0;
-    for (int j = 0; j < S; j++) err |= ctr[j].err;
-    st[2] |= err;
-    st[1] = r + 1;
-    if (*moves_r == 0 && full) st[0] = 1;
+    __shared__ int32_t err;
+    if (threadIdx.x == 0) err = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < S; j += blockDim.x) atomicOr(&err, ctr[j].err);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st[2] |= err;
+        st[1] = r + 1;
+        if (*moves_r == 0 && full) st[0] = 1;
+    }
+    int32_t *cw = reinterpret_cast<int32_t *>(ctr);
+    for (int i = threadIdx.x; i < (int)(S * sizeof(Ctr) / sizeof(int32_t)); i += blockDim.x) cw[i] = 0;
+    for (int i = threadIdx.x; i < n_wl; i += blockDim.x) wl_cnt[i] = 0;
 }
 
 static std::mutex g_tune_mu;
@@ -3276,7 +3298,8 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
     a.bar_cycles = kBarCycles;
     int32_t *wl = sc.get<int32_t>((size_t)kClasses * S * g.n);
     // bucket lengths, then piece counts, then cluster-path row counts (per colour)
-    int32_t *wl_cnt = sc.get<int32_t>(kClasses * S + (2 + kPipeClasses) * S);
+    const int n_wl = kClasses * S + (2 + kPipeClasses) * S;
+    int32_t *wl_cnt = sc.get<int32_t>(n_wl);
     Ctr *ctr = sc.get<Ctr>(S);
     int64_t *d_moves = sc.zeros<int64_t>(cfg.rounds);
     a.wl = wl;
@@ -3405,8 +3428,10 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             LAUNCHED();
             a.col = dcol;
         }
-        CK(cudaMemsetAsync(wl_cnt, 0, (kClasses * S + (2 + kPipeClasses) * S) * sizeof(int32_t), ms));
-        CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), ms));
+        if (r == 0) {  // later rounds: cleared by the previous round's k_round_end
+            CK(cudaMemsetAsync(wl_cnt, 0, n_wl * sizeof(int32_t), ms));
+            CK(cudaMemsetAsync(ctr, 0, S * sizeof(Ctr), ms));
+        }
         k_build_wl<<<sms * 4, kThreads, 0, ms>>>(a, wl, wl_cnt);
         LAUNCHED();
         for (int j = 0; j < S; j++) {
@@ -3484,7 +3509,8 @@ int lp_run(const LPConfig &cfg, Scratch &sc, std::vector<int64_t> *moves_out, in
             }
             LAUNCHED();
         }
-        k_round_end<<<1, 1, 0, ms>>>(d_moves + r, ctr, S, d_state, r, full ? 1 : 0);
+        k_round_end<<<1, 128, 0, ms>>>(d_moves + r, ctr, S, d_state, r, full ? 1 : 0, wl_cnt,
+                                       n_wl);
         LAUNCHED();
     };
 
