@@ -129,9 +129,12 @@ def test_refine_long_segments_match_oracle(k, eps):
         assert cut_g == cut_w and np.array_equal(bw_g.numpy(), bw_w)
 
 
-@pytest.mark.parametrize("leaves,U", [(20000, 500), (30000, 29000), (30000, 40000)])
+@pytest.mark.parametrize("leaves,U", [(20000, 500), (30000, 29000), (30000, 40000),
+                                      (70000, 500)])
 def test_cluster_long_segments_match_oracle(leaves, U):
-    # every leaf proposes the hub's label in the same sub-round
+    # every leaf proposes the hub's label in the same sub-round: one contested
+    # segment per sub-round, above the shared-memory bound, selected by the
+    # whole grid
     g = star(leaves, w=3)
     gn = I.to_numpy(g)
     gn["vwgt"] = (np.arange(leaves + 1) % 4 + 1).astype(np.int32)
