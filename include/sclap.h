@@ -350,6 +350,14 @@ void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed)
  * other codes on CUDA errors.  Uses the legacy default stream. */
 int sclap_wait_selftest(int64_t limit_cycles);
 
+/* Failure detection of device allocations (the paper has no counterpart):
+ * the library's scratch allocations are counted from this call on, and the
+ * one that finds the count at `after` (>= 0) fails as if the device were out
+ * of memory, so that call returns SCLAP_ENOMEM (with part_inout restored
+ * where the entry point documents it); after == -1 turns the injection off.
+ * Process-wide; meant for tests.  SCLAP_EINVAL for after < -1. */
+int sclap_inject_alloc_failure(int64_t after);
+
 /* Copies a library-owned graph into caller-allocated device arrays of sizes
  * n+1, nnz, nnz and n (enqueued on `stream`, synchronised before return). */
 int sclap_graph_copy_out(const sclap_graph_owned *g, int64_t *xadj, int32_t *adjncy,

@@ -125,6 +125,7 @@ _SIGS = {
                                   C.c_uint64, C.POINTER(C.c_double), _VP]),
     "sclap_mlp_pack_bf16": (C.c_int, [_VP, _VP, _VP]),
     "sclap_wait_selftest": (C.c_int, [C.c_int64]),
+    "sclap_inject_alloc_failure": (C.c_int, [C.c_int64]),
     "sclap_prof_enable": (None, [C.c_int]),
     "sclap_prof_reset": (None, []),
     "sclap_prof_read": (C.c_int, [C.POINTER(Prof)]),
@@ -492,6 +493,12 @@ def sclap_vcycle(g: dict, params: dict, part: torch.Tensor, stream=None):
                  init_best=st.init_best, init_cut=st.init_cut, init_maxbw=st.init_maxbw,
                  cut=st.cut, maxbw=st.maxbw)
     return p, stats
+
+
+def inject_alloc_failure(after: int):
+    """Makes the library's scratch allocation number `after` (counted from
+    now) fail as out of memory; -1 turns the injection off (a test hook)."""
+    _check(lib().sclap_inject_alloc_failure(int(after)), "sclap_inject_alloc_failure")
 
 
 def wait_selftest(limit_cycles: int) -> int:

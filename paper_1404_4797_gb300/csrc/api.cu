@@ -793,6 +793,12 @@ int sclap_mlp_train(const float *x, const uint8_t *y, int64_t N, float *params, 
     });
 }
 
+int sclap_inject_alloc_failure(int64_t after) {
+    if (after < -1) return SCLAP_EINVAL;
+    set_alloc_failure((long long)after);
+    return SCLAP_OK;
+}
+
 int sclap_wait_selftest(int64_t limit_cycles) {
     int got = SCLAP_OK;
     const int rc = guarded([&] {

@@ -62,6 +62,7 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 // Stream-ordered device scratch taken from a private memory pool that keeps
 // freed blocks cached (so repeated calls do not pay for cudaMalloc).
 void *scratch_alloc(size_t bytes, cudaStream_t s);
+void set_alloc_failure(long long after);
 void scratch_free(void *p, cudaStream_t s);
 
 // RAII list of scratch blocks released (stream-ordered) when it goes out of scope.

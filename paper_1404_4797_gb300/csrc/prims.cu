@@ -62,9 +62,18 @@ const DevInfo &dev_info() {
     return g_dev[d];
 }
 
+// Allocation-failure injection (tests): the scratch allocation that finds
+// the counter at 0 fails as if the device were out of memory; -1 disables.
+static std::atomic<long long> g_fail_after{-1};
+void set_alloc_failure(long long after) { g_fail_after.store(after); }
+
 void *scratch_alloc(size_t bytes, cudaStream_t s) {
     const DevInfo &di = dev_info();
     void *p = nullptr;
+    long long f = g_fail_after.load();
+    while (f >= 0 && !g_fail_after.compare_exchange_weak(f, f - 1)) {
+    }
+    if (f == 0) fail(SCLAP_ENOMEM, "scratch allocation (injected)");
     cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, g_pool[di.device], s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();

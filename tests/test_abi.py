@@ -37,3 +37,12 @@ def test_binding_names_match_header():
     assert set(S.EXPORTS) <= set(declared_functions())
     S.lib()
     assert S.strerror(S.EGRAPH) == "graph failed validation"
+
+
+def test_alloc_failure_hook_rejects_bad_counts_without_a_gpu():
+    import paper_1404_4797_gb300 as S
+    S.lib()
+    with __import__("pytest").raises(S.SclapError) as e:
+        S.inject_alloc_failure(-2)
+    assert e.value.code == S.EINVAL
+    S.inject_alloc_failure(-1)  # off: no device work involved
