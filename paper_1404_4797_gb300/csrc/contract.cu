@@ -14,6 +14,8 @@ constexpr int kCThreads = 256;
 constexpr int kCEntries = 2048;
 constexpr int kCSlots = 4096;
 constexpr int kCBits = 12;
+constexpr int kAggItems = kCEntries / kCThreads;  // entries per thread and slice
+static_assert(kCEntries % kCThreads == 0, "whole entries per thread");
 
 __global__ void k_mark(int64_t n, const int32_t *lab, int32_t *mark) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -75,7 +77,7 @@ struct AggSm {
 
 // Slice t covers concatenated member entries [t*kCEntries, (t+1)*kCEntries).
 template <bool K32>
-__global__ void __launch_bounds__(kCThreads)
+__global__ void __launch_bounds__(kCThreads, 5)
     k_aggregate(DGraph g, const int32_t *members, int64_t nmem, const int64_t *mpre,
                 int64_t total, const int32_t *f2c, int cbits, unsigned long long *out_keys,
                 int32_t *out_w, unsigned long long *out_cnt) {
@@ -100,18 +102,34 @@ __global__ void __launch_bounds__(kCThreads)
         if (threadIdx.x == 0) sm.cu0 = f2c[members[sm.rowof[0]]];
         __syncthreads();
         const int32_t cu0 = sm.cu0;
-        // the same number of steps in every thread (warp-wide appends of new slots)
-        for (int lb = 0; lb < len; lb += kCThreads) {
-            const int le = lb + threadIdx.x;
-            int created = -1;
+        // all gathers of the thread's entries first (kAggItems independent
+        // load chains in flight), then the inserts
+        int32_t ecu[kAggItems], ecv[kAggItems], ew[kAggItems];
+#pragma unroll
+        for (int j = 0; j < kAggItems; j++) {
+            const int le = j * kCThreads + threadIdx.x;
+            ecu[j] = 0;
+            ecv[j] = 0;
+            ew[j] = 0;
             if (le < len) {
                 const int32_t mi = sm.rowof[le];
                 const int32_t v = __ldg(&members[mi]);
                 const int64_t idx = __ldg(&g.xadj[v]) + (e0 + le - __ldg(&mpre[mi]));
-                const int32_t cu = __ldg(&f2c[v]);
-                const int32_t cv = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
+                ecu[j] = __ldg(&f2c[v]);
+                ecv[j] = __ldg(&f2c[__ldg(&g.adjncy[idx])]);
+                ew[j] = __ldg(&g.adjwgt[idx]);
+            }
+        }
+        // the same number of steps in every thread (warp-wide appends of new slots)
+#pragma unroll
+        for (int j = 0; j < kAggItems; j++) {
+            const int le = j * kCThreads + threadIdx.x;
+            int created = -1;
+            if (le < len) {
+                const int32_t cu = ecu[j];
+                const int32_t cv = ecv[j];
                 if (cu != cv) {  // else an edge inside a cluster
-                    const int32_t w = __ldg(&g.adjwgt[idx]);
+                    const int32_t w = ew[j];
                     Key key;
                     uint32_t slot;
                     if constexpr (K32) {

@@ -152,32 +152,43 @@ inline int bit_width_u64(uint64_t x) {
 
 // ---------------------------------------------------------------- entry -> row
 
+// Largest v in [0, n) with a[v] <= key, for non-decreasing a[0..n) with
+// a[0] <= key (0 when n == 0).  Called by all lanes of one warp: every step
+// probes 32 evenly spaced points of (lo, hi], and because a is monotone the
+// lanes whose probe is <= key form a prefix, so the ballot's population count
+// picks the new interval; it shrinks 32-fold per step (five dependent loads
+// for 2^22 rows instead of 22).
+__device__ __forceinline__ int64_t warp_last_le(const int64_t *a, int64_t n, int64_t key) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = n;  // a[lo] <= key; hi == n or a[hi] > key
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t p = lo + (int64_t)(lane + 1) * step;
+        const unsigned b = __ballot_sync(0xffffffffu, p < hi && a[p] <= key);
+        const int c = __popc(b);
+        const int64_t first_false = lo + (int64_t)(c + 1) * step;
+        lo += (int64_t)c * step;
+        if (first_false < hi) hi = first_false;
+    }
+    return lo;
+}
+
 // For the entry range [e0, e0 + len) (len <= NT * PER) of a CSR with row
 // offsets xadj[0..n], writes rowof[i] = the row containing entry e0 + i.
-// Rows are found once per range (two binary searches); each row start inside
-// the range marks its position (the largest row id wins, skipping empty
-// rows), and an inclusive max-scan spreads the row ids.  All threads call it.
+// Rows are found once per range (warps 0 and 1 search the first and the last
+// row at the same time); each row start inside the range marks its position
+// (the largest row id wins, skipping empty rows), and an inclusive max-scan
+// spreads the row ids.  All threads call it.
 template <int NT, int PER>
 __device__ void block_rows(const int64_t *xadj, int64_t n, int64_t e0, int len, int32_t *rowof,
                            int32_t *scan_tmp /* >= NT/32 + 2 */) {
+    static_assert(NT >= 64 && NT % 32 == 0, "two whole warps search the rows");
     __shared__ int64_t s_rows[2];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 64) {
         // first row: largest v with xadj[v] <= e0; last: largest v with xadj[v] <= e0+len-1
-        int64_t lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (xadj[mid] <= e0) lo = mid;
-            else hi = mid;
-        }
-        s_rows[0] = lo;
-        int64_t lo2 = lo, hi2 = n;
-        const int64_t eL = e0 + len - 1;
-        while (hi2 - lo2 > 1) {
-            const int64_t mid = (lo2 + hi2) >> 1;
-            if (xadj[mid] <= eL) lo2 = mid;
-            else hi2 = mid;
-        }
-        s_rows[1] = lo2;
+        const int which = threadIdx.x >> 5;
+        const int64_t r = warp_last_le(xadj, n, which == 0 ? e0 : e0 + len - 1);
+        if ((threadIdx.x & 31) == 0) s_rows[which] = r;
     }
     for (int i = threadIdx.x; i < len; i += NT) rowof[i] = -1;
     __syncthreads();
