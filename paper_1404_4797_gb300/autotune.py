@@ -4,10 +4,11 @@ The thresholds only route rows (by their number of entries) and contested
 target segments (by their number of proposals) between kernel paths that
 compute the same selection and arbitration, so every setting gives the same
 partition; they change the speed.  For one device and one workload graph the
-tuner times candidate settings on the level-0 SCLaP sweeps (the clustering
-and refinement rounds, CUDA events), checks that all candidates return the
-same labels and partition, keeps the fastest, applies it and caches it as JSON
-keyed by the device name and a signature of the graph and the run parameters.
+tuner times candidate settings with CUDA events, either on the level-0 SCLaP
+sweeps (the clustering and refinement rounds) or on one whole multilevel
+partition, checks that all candidates return the same labels or partition,
+keeps the fastest, applies it and caches it as JSON keyed by the device name
+and a signature of the graph and the run parameters.
 """
 from __future__ import annotations
 
