@@ -875,7 +875,7 @@ int or_initial_partition(int64_t n, const int64_t *xadj, const int32_t *adjncy,
     if (k < 1 || P < 1) return OR_EINVAL;
     int32_t *rg = (int32_t *)calloc((size_t)P, sizeof(int32_t));
     uint64_t *seeds = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)P);
-    int32_t *parts = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * P ? n * P : 1));
+    int32_t *parts = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * P > 0 ? n * P : 1));
     int64_t *cuts = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
     int64_t *mxs = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
     int rc = OR_OK;
