@@ -11,6 +11,7 @@ import torch
 
 import paper_1404_4797_gb300 as S
 from paper_1404_4797_gb300 import autotune as A
+from paper_1404_4797_gb300 import build as B
 from paper_1404_4797_gb300 import inputs as I
 
 CANDS = [(32, 256, 2048, 6144), (16, 256, 2048, 6144), (32, 128, 1024, 4096)]
@@ -51,6 +52,7 @@ class _Event:
 
 @pytest.fixture
 def fake(monkeypatch):
+    B.build()
     S.lib()  # the tuning setter is a host-side value: no GPU needed
     saved = S.get_tuning()
     clock = _Clock(lambda key: 1.0 if key == FAST else 2.0 + 0.1 * key[0] / 32)

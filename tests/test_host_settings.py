@@ -7,10 +7,12 @@ import ctypes as C
 import pytest
 
 import paper_1404_4797_gb300 as S
+from paper_1404_4797_gb300 import build as B
 
 
 @pytest.fixture
 def restore():
+    B.build()
     S.lib()
     t = S.get_tuning()
     mode = S.set_launch_mode(-1)
@@ -29,6 +31,7 @@ def _set(small, med, mid, seg):
 
 def test_default_tuning():
     # a fresh process: the documented defaults
+    B.build()
     import os
     import subprocess
     import sys
