@@ -3,7 +3,7 @@ run as torch.distributed ranks on CPU (gloo), one process per rank.
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: it shows that the
 sharded design computes exactly what the single-rank oracle computes, and it is
-run by ``tests/test_sharded.py`` with 2 and 4 ranks.  The product is
+run by ``tests/test_sharded.py`` with 2, 3 and 4 ranks.  The product is
 single-GPU (several GPUs run independent replicas); this module is the
 host-side protocol a multi-GPU product would follow, with each rank's local
 arithmetic written here in numpy.

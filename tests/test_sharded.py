@@ -1,6 +1,7 @@
 """The sharded design (1-D node ranges with halos, proposal exchange to the
-target owners, owner arbitration, exscan contraction; Sec. IV.A-C) on 2 and 4
-simulated ranks (gloo, CPU processes) gives bit for bit what the single-rank
+target owners, owner arbitration, exscan contraction; Sec. IV.A-C) on 2, 3 and
+4 simulated ranks (gloo, CPU processes; 3 ranks own node ranges of unequal
+sizes) gives bit for bit what the single-rank
 oracle gives: clustering labels, refinement partitions, coarse graphs and
 projections.  Not measured on GPUs: the product runs one GPU per process."""
 import os
@@ -71,7 +72,7 @@ def _worker(rank, P, port, out_dir):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("P", [2, 4])
+@pytest.mark.parametrize("P", [2, 3, 4])
 def test_sharded_ranks_match_the_single_rank_oracle(P, tmp_path):
     mp.spawn(_worker, args=(P, _free_port(), str(tmp_path)), nprocs=P, join=True)
     res = np.load(tmp_path / "res.npy", allow_pickle=True).item()
