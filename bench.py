@@ -8,7 +8,8 @@ Workload: R-MAT scale 22 (a, b, c = 0.57, 0.19, 0.19), edge factor 16,
 symmetrised, duplicates and self-loops dropped (~4.19M nodes, ~64M undirected
 edges), unit int32 weights, k = 16, eps = 0.03, l = 3 clustering and r = 6
 refinement rounds per level (the paper's `fast` round counts), S = 4
-sub-rounds, coarsening to < 2000 nodes, 8 initial individuals.
+sub-rounds, coarsening while a level has >= 2000 nodes and shrinks by >= 5%,
+8 initial individuals.
 
 Metric: G edges/s = m_undirected / partition time (the paper reports partition
 time; edges per second is its time-per-edge convention inverted).  The JSON
