@@ -412,7 +412,9 @@ void sclap_get_tuning(sclap_tuning *t);
  * counts the algorithmic bytes it must move (12 B per scanned entry: adjncy,
  * adjwgt, the neighbour-label gather; 24 B per visited node: xadj, label,
  * vwgt, proposal, label write-back).  sclap_prof_read synchronises the device
- * and returns the totals since the last reset. */
+ * and returns the totals since the last reset.  Meant for one calling thread:
+ * while it is enabled, calls from several threads at once are not supported
+ * (the event list is not synchronised); the launch counters are atomic. */
 typedef struct {
     int64_t propose_launches;
     double propose_ms;            /* sum of event-timed launch durations          */

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/sclap.h): argument checks, graph validation,
 // overflow checks, the initial partitioner and the multilevel driver.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -13,7 +14,7 @@ using namespace sclap;
 
 namespace {
 
-bool g_validate = true;
+std::atomic<bool> g_validate{true};  // process-wide, set from any thread
 
 template <class F>
 int guarded(F &&f) {
@@ -120,7 +121,7 @@ void validate_graph(const DGraph &g, Scratch &sc) {
     if (g.n < 0 || g.nnz < 0 || g.n > INT32_MAX) fail(SCLAP_EINVAL, "graph size");
     if (g.n > 0 && (!g.xadj || !g.vwgt)) fail(SCLAP_EINVAL, "null graph array");
     if (g.nnz > 0 && (!g.adjncy || !g.adjwgt)) fail(SCLAP_EINVAL, "null graph array");
-    if (!g_validate || g.n == 0) return;
+    if (!g_validate.load() || g.n == 0) return;
     cudaStream_t s = sc.stream();
     int *bad = sc.zeros<int>(1);
     int grid = dev_info().sms * 8;
@@ -534,9 +535,7 @@ void sclap_get_tuning(sclap_tuning *t) {
 }
 
 int sclap_set_validation(int on) {
-    int old = g_validate ? 1 : 0;
-    g_validate = on != 0;
-    return old;
+    return g_validate.exchange(on != 0) ? 1 : 0;
 }
 
 void sclap_ml_defaults(sclap_ml_params *p, int32_t k, double eps, uint64_t seed) {
