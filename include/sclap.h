@@ -176,7 +176,8 @@ int contract_graph(const sclap_graph *g, const int32_t *labels, sclap_graph_owne
 int project_partition(int64_t n_fine, const int32_t *f2c, const int32_t *coarse_part,
                       int32_t *fine_part_out, void *stream);
 
-/* Cut (Sec. II.A) and block weights of a partition.
+/* Cut (Sec. II.A) and block weights of a partition.  The graph is validated
+ * like every other entry point's (SCLAP_EGRAPH; see sclap_set_validation).
  *   part        device int32[n] in [0, k); any other id returns SCLAP_EINVAL
  *   cut_out     host int64;  block_w_out host int64[k] (NULL allowed) */
 int sclap_cut(const sclap_graph *g, const int32_t *part, int32_t k, int64_t *cut_out,

@@ -824,6 +824,7 @@ int sclap_cut(const sclap_graph *gp, const int32_t *part, int32_t k, int64_t *cu
         cudaStream_t s = as_stream(stream);
         Scratch sc(s);
         DGraph g = view(gp);
+        validate_graph(g, sc);  // entry ids index part: checked before the cut kernel
         if (!in_range(g.n, part, k, sc)) fail(SCLAP_EINVAL, "part out of range");
         int64_t *d_cut = sc.get<int64_t>(1);
         int64_t *d_bw = sc.get<int64_t>(k);

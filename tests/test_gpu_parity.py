@@ -264,6 +264,14 @@ def test_errors_are_reported():
     with pytest.raises(S.SclapError) as e:
         S.sclap_cluster(bad, 10**6, 3, 4, 1)
     assert e.value.code == S.EGRAPH
+    # the cut validates the graph before it reads part[] at the neighbour ids
+    zeros = torch.zeros(3000, dtype=torch.int32, device="cuda")
+    oob = {k: v.clone() for k, v in g.items()}
+    oob["adjncy"][0] = 3000                        # neighbour id past n
+    for graph in (bad, oob):
+        with pytest.raises(S.SclapError) as e:
+            S.sclap_cut(graph, zeros, 4)
+        assert e.value.code == S.EGRAPH
     p = torch.full((3000,), 5, dtype=torch.int32, device="cuda")
     with pytest.raises(S.SclapError) as e:
         S.sclap_refine(g, 4, 0.03, 3, 4, 1, p)     # block id out of range
