@@ -334,6 +334,29 @@ def population(count: int = 32, nmin: int = 2000, nmax: int = 200000, seed: int 
     return graphs
 
 
+def ring_of_cliques(k: int, s: int, bridges: int = 1, seed: int = 1, device="cpu") -> dict:
+    """k cliques of s nodes (unit weights) in a ring: clique c is joined to
+    clique (c + 1) mod k by `bridges` edges between uniformly drawn members;
+    node ids permuted.  Returns the graph and the clique of every node (int64
+    [k*s]).  The partition into the cliques cuts total weight k * bridges
+    (repeated bridges merge and sum their weights); any partition that splits
+    a clique cuts at least s - 1."""
+    n = k * s
+    i, j = torch.triu_indices(s, s, 1, device=device)
+    base = torch.arange(k, dtype=torch.int64, device=device).repeat_interleave(i.numel()) * s
+    u = base + i.repeat(k)
+    v = base + j.repeat(k)
+    b = torch.arange(k * bridges, dtype=torch.int64, device=device)
+    c = b // bridges
+    bu = c * s + rand_below(seed, 1, b, s)
+    bv = ((c + 1) % k) * s + rand_below(seed, 2, b, s)
+    perm = permutation(n, seed, 3, device)  # old id -> new id
+    g = csr_from_edges(n, perm[torch.cat([u, bu])], perm[torch.cat([v, bv])])
+    clique = torch.empty(n, dtype=torch.int64, device=device)
+    clique[perm] = torch.arange(n, dtype=torch.int64, device=device) // s
+    return g, clique
+
+
 def path_graph(n: int, weights=None) -> dict:
     u = torch.arange(n - 1)
     v = u + 1

@@ -225,6 +225,17 @@ def test_multilevel_weighted_matches_oracle():
     assert np.array_equal(got.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("k,s,bridges", [(4, 50, 1), (16, 30, 1), (3, 100, 5)])
+def test_multilevel_planted_partition_matches_oracle(k, s, bridges):
+    # rings of cliques: with U = s the oracle recovers the cliques (cut k * bridges)
+    g, clique = I.ring_of_cliques(k, s, bridges, seed=k)
+    params = oracle.default_params(k, 0.03, seed=2, n_stop=50, U=s)
+    want, ws = oracle.multilevel(I.to_numpy(g), params)
+    got, gs = S.partition_multilevel(dev(g), params)
+    assert gs == ws and np.array_equal(got.cpu().numpy(), want)
+    assert gs["cut"] == k * bridges
+
+
 def test_repeatable_runs_are_identical():
     g = dev(I.rmat(15, 16, seed=8))
     params = oracle.default_params(16, 0.03, seed=5, n_stop=2000)

@@ -396,6 +396,40 @@ def test_multilevel_config1_shape_is_deterministic_and_balanced():
     assert st["U"] == max(1, 16384 // 40)
 
 
+PLANTED = [(2, 40, 1), (4, 50, 1), (8, 40, 2), (6, 64, 3), (16, 30, 1), (3, 100, 5)]
+
+
+@pytest.mark.parametrize("k,s,bridges", PLANTED)
+def test_multilevel_recovers_a_planted_partition(k, s, bridges):
+    # A known optimum: k cliques of s nodes in a ring, `bridges` edges between
+    # neighbouring cliques.  L_max = floor(1.03 s) < 2s, so a k-way partition
+    # either keeps every clique in its own block (cut k * bridges) or splits a
+    # clique (cut >= s - 1 > k * bridges).  With a cluster bound that admits a
+    # whole clique (U = s) the multilevel scheme of Sec. IV.E finds it.
+    g, clique = I.ring_of_cliques(k, s, bridges, seed=k)
+    g, clique = I.to_numpy(g), clique.numpy()
+    assert s - 1 > k * bridges and oracle.lmax(k * s, k, 0.03) < 2 * s
+    planted = oracle.cut(g, clique.astype(np.int32))
+    assert planted == k * bridges
+    for seed in (1, 2, 3):
+        p = oracle.default_params(k, 0.03, seed=seed, n_stop=50, U=s)
+        part, st = oracle.multilevel(g, p)
+        assert st["cut"] == planted and st["maxbw"] <= st["lmax"]
+        blocks = [set(part[clique == c].tolist()) for c in range(k)]
+        assert all(len(b) == 1 for b in blocks) and len(set().union(*blocks)) == k
+
+
+def test_planted_generator_shape():
+    g, clique = I.ring_of_cliques(5, 12, 2, seed=9)
+    g = I.to_numpy(g)
+    assert oracle.validate(g) == oracle.OK
+    assert np.bincount(clique.numpy()).tolist() == [12] * 5
+    assert int(g["adjwgt"].sum()) // 2 == 5 * 66 + 5 * 2  # clique edges + bridge weight
+    deg_in = [sum(1 for e in range(g["xadj"][v], g["xadj"][v + 1])
+                  if clique[g["adjncy"][e]] == clique[v]) for v in range(60)]
+    assert deg_in == [11] * 60  # every clique complete
+
+
 # ---------------------------------------------------------------- batched runs
 
 def _lpt_by_hand(g, k, sr):
